@@ -1,0 +1,569 @@
+"""FP64 CPU oracle of the enhanced MsRSB two-level preconditioner.
+
+TEST INFRASTRUCTURE ONLY. Only tests/, the smoke check and the CPU-baseline leg
+of bench.py may import this module; the library's product path never does.
+It shares no code with the CUDA path.
+
+Every function restates a step of Bosma, Klevtsov, Moyner, Castelletto,
+"Enhanced multiscale restriction-smoothed basis (MsRSB) preconditioning with
+applications to porous media flow and geomechanics" (arXiv 1912.06934) in plain
+numpy/scipy, slowly and in the paper's order; the passage is cited in each
+docstring. Where the paper is silent the documented reading is given inline.
+
+Matrices are scipy CSR (float64, sorted column indices). The prolongation P is
+kept on its fixed support pattern: ``pat`` is a CSR pattern (n rows, nc
+columns, sorted coarse ids per row) and ``vals`` the values on it.
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+# ----------------------------------------------------------------------------
+# a0: primal partition, coarse nodes, support regions (Sec. 2.1, Fig. 1; the
+# initial basis is the indicator of the primal block, Sec. 2.1)
+# ----------------------------------------------------------------------------
+
+
+def coarse_axis(n, H, centering):
+    """One grid axis: coarse-node coordinates c_I and the block of each point.
+
+    Cell-centred (FV): block I holds cells [I*H, min((I+1)*H, n)); its coarse
+    node is the lower-middle cell of the block (the paper only asks for a
+    representative fine cell). Vertex-centred (FE): coarse nodes sit on nodes
+    0, H, 2H, ... (the last one clamped to n-1) and each node belongs to the
+    block of its nearest coarse node, ties going to the lower one.
+    Returns (c, block) with c sorted ascending.
+    """
+    x = np.arange(n)
+    if centering == 0:
+        nb = -(-n // H)
+        c = np.array([I * H + (min((I + 1) * H, n) - I * H - 1) // 2 for I in range(nb)])
+        block = x // H
+    else:
+        nb = -(-(n - 1) // H) + 1
+        c = np.array([min(I * H, n - 1) for I in range(nb)])
+        dist = np.abs(x[:, None] - c[None, :])
+        block = np.argmin(dist, axis=1)  # argmin takes the first (lower) on ties
+    return c, block
+
+
+def axis_supports(n, c):
+    """Support of coarse node I along one axis: the open interval
+    (c_{I-1}, c_{I+1}), reaching the domain edge where there is no neighbour.
+    A point exactly on c_J (J != I) bounds I's support (support boundary); the
+    points with coordinate c_I are I's support edge. Returns a boolean
+    (n, nb) matrix S[x, I] = x in supp_I."""
+    nb = len(c)
+    S = np.zeros((n, nb), dtype=bool)
+    for I in range(nb):
+        lo = c[I - 1] if I > 0 else -1
+        hi = c[I + 1] if I + 1 < nb else n
+        S[lo + 1:hi, I] = True
+    return S
+
+
+def partition(dims, H, centering):
+    """Primal partition and the support pattern of P on a Cartesian grid.
+
+    Returns dict with
+      part[n]     primal block (flat coarse id) of every fine point,
+      cnode[nc]   flat fine index of every coarse node,
+      pat         CSR pattern (n x nc): coarse ids whose support holds the row,
+      skel[n]     True where the point lies on any coarse-node line, i.e. on a
+                  support edge of some basis (and a boundary of another).
+    Flat orders have x fastest, for fine points and coarse ids alike.
+    """
+    d = len(dims)
+    axes = [coarse_axis(dims[a], H[a], centering) for a in range(d)]
+    nbs = [len(c) for c, _ in axes]
+    n = int(np.prod(dims))
+    nc = int(np.prod(nbs))
+    coords = np.indices(dims).reshape(d, -1, order="F")
+    part = np.zeros(n, dtype=np.int64)
+    stride = 1
+    for a in range(d):
+        part += axes[a][1][coords[a]] * stride
+        stride *= nbs[a]
+    cc = np.indices(nbs).reshape(d, -1, order="F")
+    cnode = np.zeros(nc, dtype=np.int64)
+    stride = 1
+    for a in range(d):
+        cnode += axes[a][0][cc[a]] * stride
+        stride *= dims[a]
+    supp = [axis_supports(dims[a], axes[a][0]) for a in range(d)]
+    # row pattern = tensor product of the per-axis memberships
+    rows, cols = [], []
+    per_axis = [[np.flatnonzero(supp[a][x]) for x in range(dims[a])] for a in range(d)]
+    skel = np.zeros(n, dtype=bool)
+    for a in range(d):
+        skel |= np.isin(coords[a], axes[a][0])
+    for i in range(n):
+        ids = np.zeros(1, dtype=np.int64)
+        stride = 1
+        for a in range(d):
+            ids = (ids[:, None] + per_axis[a][coords[a][i]][None, :] * stride).ravel()
+            stride *= nbs[a]
+        ids.sort()
+        rows.append(np.full(len(ids), i))
+        cols.append(ids)
+    rows = np.concatenate(rows)
+    cols = np.concatenate(cols)
+    pat = sp.csr_matrix((np.ones(len(rows)), (rows, cols)), shape=(n, nc))
+    pat.sort_indices()
+    return dict(part=part, cnode=cnode, pat=pat, skel=skel, nb=tuple(nbs), nc=nc)
+
+
+def indicator(part, pat):
+    """Initial basis: P0_iJ = 1 if fine point i lies in primal block J (Sec. 2.1)."""
+    rows = np.repeat(np.arange(pat.shape[0]), np.diff(pat.indptr))
+    return (pat.indices == part[rows]).astype(np.float64)
+
+
+# ----------------------------------------------------------------------------
+# a1 / a1': M-matrix filter (Eq. 8 with Eq. 4; Alg. 1, first two steps)
+# ----------------------------------------------------------------------------
+
+
+def mmatrix_filter(A):
+    """Filtered operator of Alg. 1: A_hat = min(A, 0) entrywise, then
+    A_hat <- A_hat - diag(rowsum(A_hat)), so every row sums to zero and the
+    off-diagonals are non-positive (Eq. 8 then Eq. 4). Same pattern as A."""
+    A = sp.csr_matrix(A, copy=True)
+    A.sort_indices()
+    Ah = A.copy()
+    Ah.data = np.minimum(A.data, 0.0)
+    rowsum = np.asarray(Ah.sum(axis=1)).ravel()
+    rows = np.repeat(np.arange(A.shape[0]), np.diff(A.indptr))
+    on_diag = A.indices == rows
+    Ah.data[on_diag] -= rowsum[rows[on_diag]]
+    return Ah
+
+
+def sdc_blocks(indptr, indices, blocks):
+    """Separate-displacement-component approximation (Eq. 19-20, Remark 2):
+    from a 3x3-block CSR matrix keep, for each component l, the scalar matrix
+    A_ll made of the (l, l) entry of every block."""
+    n = len(indptr) - 1
+    return [sp.csr_matrix((blocks[:, l, l].copy(), indices.copy(), indptr.copy()), shape=(n, n))
+            for l in range(3)]
+
+
+def bsr_to_csr(indptr, indices, blocks):
+    """Scalar CSR of a 3x3-block CSR matrix, dof = 3*node + component."""
+    n = len(indptr) - 1
+    B = sp.bsr_matrix((blocks, indices, indptr), shape=(3 * n, 3 * n)).tocsr()
+    B.sort_indices()
+    return B
+
+
+# ----------------------------------------------------------------------------
+# a2: restricted smoothing of the basis (Eq. 5-6, Alg. 1)
+# ----------------------------------------------------------------------------
+
+
+def _on_pattern(Q, pat):
+    """Values of sparse Q at the entries of the pattern (zeros where absent)."""
+    rows = np.repeat(np.arange(pat.shape[0]), np.diff(pat.indptr))
+    return np.asarray(Q.tocsr()[rows, pat.indices]).ravel()
+
+
+def enhanced_msrsb(Ahat, pat, P0, skel, omega=2.0 / 3.0, tol=1e-3, n_it=10, max_iter=100):
+    """Alg. 1 (EnhancedMsRSB) on an already filtered operator.
+
+    Each pass: dP = -omega * D_hat^-1 * A_hat * P (Eq. 6); entries of dP outside
+    P's fixed support pattern are dropped, so the basis cannot grow beyond its
+    support region (the rescaling below restores partition of unity instead of
+    moving the overflow to neighbouring bases); P <- P + dP; every row of P is
+    divided by its sum; when k mod n_it == 0, e_it is the largest |dP_ij| over
+    rows i that are not on the skeleton (support edges). The loop runs while
+    e_it > tol and at most max_iter passes. Rows with D_hat_ii = 0 (no
+    off-diagonal left after filtering) get dP = 0.
+    Returns (vals, iterations, e_it, history of (k, e_it)).
+    """
+    Ahat = sp.csr_matrix(Ahat)
+    n, nc = pat.shape
+    dhat = Ahat.diagonal()
+    inv = np.zeros(n)
+    nz = dhat != 0.0
+    inv[nz] = 1.0 / dhat[nz]
+    rows = np.repeat(np.arange(n), np.diff(pat.indptr))
+    interior = ~skel[rows]
+    vals = P0.astype(np.float64).copy()
+    k = 0
+    e_it = np.inf
+    hist = []
+    while e_it > tol and k < max_iter:
+        P = sp.csr_matrix((vals, pat.indices, pat.indptr), shape=(n, nc))
+        AP = Ahat @ P
+        dP = -omega * (sp.diags(inv) @ AP)
+        dPv = _on_pattern(dP, pat)
+        vals = vals + dPv
+        rs = np.bincount(rows, weights=vals, minlength=n)
+        vals = vals / rs[rows]
+        if k % n_it == 0:
+            e_it = float(np.max(np.abs(dPv[interior]))) if interior.any() else 0.0
+            hist.append((k, e_it))
+        k += 1
+    return vals, k, e_it, hist
+
+
+def as_matrix(vals, pat):
+    return sp.csr_matrix((vals, pat.indices, pat.indptr), shape=pat.shape)
+
+
+def block_prolongation(Ps):
+    """Block-diagonal P of the SDC extension (Sec. 4): component l of fine node
+    i is interpolated from component l of the coarse nodes only. Rows are
+    3*node + l, columns 3*J + l."""
+    n, nc = Ps[0].shape
+    out = sp.lil_matrix((3 * n, 3 * nc))
+    blocks = []
+    for l, P in enumerate(Ps):
+        P = sp.coo_matrix(P)
+        blocks.append(sp.coo_matrix((P.data, (3 * P.row + l, 3 * P.col + l)), shape=(3 * n, 3 * nc)))
+    del out
+    M = blocks[0] + blocks[1] + blocks[2]
+    return sp.csr_matrix(M)
+
+
+# ----------------------------------------------------------------------------
+# a3 / a3': Galerkin coarse operator and coarse solver (Eq. 2-3, Alg. 2)
+# ----------------------------------------------------------------------------
+
+
+def galerkin(A, P):
+    """A_c = R A P with R = P^T (Galerkin restriction, Sec. 2), unfiltered A."""
+    P = sp.csr_matrix(P)
+    return (P.T @ (sp.csr_matrix(A) @ P)).tocsr()
+
+
+def coarse_factor(Ac):
+    """M_c^-1 = A_c^-1 through an LU factorisation with partial pivoting (Alg. 2)."""
+    return sla.lu_factor(Ac.toarray() if sp.issparse(Ac) else Ac)
+
+
+def coarse_solve(lu, vc):
+    return sla.lu_solve(lu, vc)
+
+
+# ----------------------------------------------------------------------------
+# smoothers (second stage): multicolour orderings, ILU(0), Gauss-Seidel
+# ----------------------------------------------------------------------------
+
+
+def parity_colours(dims):
+    """Colour of every grid point: sum_a (x_a mod 2) 2^a. Points of one colour
+    never share a 3^d stencil, so each colour class is an independent set."""
+    d = len(dims)
+    coords = np.indices(dims).reshape(d, -1, order="F")
+    col = np.zeros(coords.shape[1], dtype=np.int64)
+    for a in range(d):
+        col += (coords[a] % 2) << a
+    return col
+
+
+def colour_order(colour):
+    """Elimination order: by colour, then by natural index (stable sort)."""
+    return np.argsort(colour, kind="stable")
+
+
+_lib = None
+
+
+def _native():
+    global _lib
+    if _lib is None:
+        here = os.path.dirname(os.path.abspath(__file__))
+        src = os.path.join(here, "ilu0.c")
+        so = os.path.join(here, "libilu0_oracle.so")
+        if not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(src):
+            subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-shared", "-fPIC", "-o", so, src])
+        _lib = ctypes.CDLL(so)
+        _lib.oracle_ilu0.restype = ctypes.c_long
+    return _lib
+
+
+def ilu0(B):
+    """ILU(0) of B in B's own row order (pass B already permuted into the
+    elimination order). Returns (L unit-lower CSR without its diagonal, U CSR
+    with diagonal), both in B's pattern. Raises on a zero pivot."""
+    B = sp.csr_matrix(B, copy=True)
+    B.sort_indices()
+    n = B.shape[0]
+    ip = B.indptr.astype(np.int64)
+    ix = B.indices.astype(np.int64)
+    a = np.ascontiguousarray(B.data, dtype=np.float64)
+    lu = np.empty_like(a)
+    dpos = np.empty(n, dtype=np.int64)
+    work = np.empty(n, dtype=np.int64)
+    P = ctypes.POINTER
+    r = _native().oracle_ilu0(ctypes.c_int64(n), ip.ctypes.data_as(P(ctypes.c_int64)),
+                              ix.ctypes.data_as(P(ctypes.c_int64)), a.ctypes.data_as(P(ctypes.c_double)),
+                              lu.ctypes.data_as(P(ctypes.c_double)), dpos.ctypes.data_as(P(ctypes.c_int64)),
+                              work.ctypes.data_as(P(ctypes.c_int64)))
+    if r != 0:
+        raise ZeroDivisionError("ILU(0) zero pivot at row %d" % (r - 1))
+    F = sp.csr_matrix((lu, B.indices.copy(), B.indptr.copy()), shape=B.shape)
+    L = sp.tril(F, k=-1, format="csr")
+    U = sp.triu(F, k=0, format="csr")
+    return L, U
+
+
+class ColouredSmoother:
+    """Second-stage smoother on a colour-ordered matrix.
+
+    kind 'ilu0': M = L U, the ILU(0) factors of A permuted into colour order.
+    kind 'gs_fwd' / 'gs_bwd': block Gauss-Seidel, M = D + L (forward) or
+    M = D + U (backward) of A in colour order, with D the bdim x bdim diagonal
+    blocks. Triangular solves go colour by colour: the rows of one colour are
+    independent, so each colour is one vectorised update, which is exactly
+    sequential substitution in colour order.
+    """
+
+    def __init__(self, A, colour, kind, bdim=1):
+        self.kind = kind
+        self.bdim = bdim
+        node_order = colour_order(colour)
+        if bdim == 1:
+            order = node_order
+            dof_colour = colour
+        else:
+            order = (bdim * node_order[:, None] + np.arange(bdim)[None, :]).ravel()
+            dof_colour = np.repeat(colour, bdim)
+        self.order = order
+        self.inv_order = np.argsort(order)
+        B = sp.csr_matrix(A)[order][:, order].tocsr()
+        B.sort_indices()
+        self.B = B
+        cs = dof_colour[order]
+        self.ncol = int(cs.max()) + 1
+        self.cls = [np.flatnonzero(cs == c) for c in range(self.ncol)]
+        if kind == "ilu0":
+            self.L, self.U = ilu0(B)
+            self.udiag = self.U.diagonal()
+            self.Ustrict = sp.triu(self.U, k=1, format="csr")
+        else:
+            nn = B.shape[0] // bdim
+            node_of = np.arange(B.shape[0]) // bdim
+            Bc = B.tocoo()
+            same = node_of[Bc.row] == node_of[Bc.col]
+            Dm = sp.csr_matrix((Bc.data[same], (Bc.row[same], Bc.col[same])), shape=B.shape)
+            self.Lo = sp.csr_matrix((Bc.data[~same & (Bc.row > Bc.col)],
+                                     (Bc.row[~same & (Bc.row > Bc.col)], Bc.col[~same & (Bc.row > Bc.col)])),
+                                    shape=B.shape)
+            self.Up = sp.csr_matrix((Bc.data[~same & (Bc.row < Bc.col)],
+                                     (Bc.row[~same & (Bc.row < Bc.col)], Bc.col[~same & (Bc.row < Bc.col)])),
+                                    shape=B.shape)
+            Db = Dm.toarray().reshape(nn, bdim, nn, bdim) if B.shape[0] <= 3000 else None
+            blocks = np.zeros((nn, bdim, bdim))
+            Dc = Dm.tocoo()
+            blocks[node_of[Dc.row], Dc.row % bdim, Dc.col % bdim] = Dc.data
+            del Db
+            self.Dinv = np.linalg.inv(blocks)
+            self.node_cls = [np.unique(node_of[c]) for c in self.cls]
+
+    def solve(self, r):
+        """z = M^-1 r (r, z in the natural order)."""
+        rp = r[self.order]
+        if self.kind == "ilu0":
+            y = np.zeros_like(rp)
+            for c in range(self.ncol):  # L y = r, unit lower
+                idx = self.cls[c]
+                y[idx] = rp[idx] - self.L[idx] @ y
+            z = np.zeros_like(rp)
+            for c in reversed(range(self.ncol)):  # U z = y
+                idx = self.cls[c]
+                z[idx] = (y[idx] - self.Ustrict[idx] @ z) / self.udiag[idx]
+        else:
+            bd = self.bdim
+            z = np.zeros_like(rp)
+            seq = range(self.ncol) if self.kind == "gs_fwd" else reversed(range(self.ncol))
+            T = self.Lo if self.kind == "gs_fwd" else self.Up
+            for c in seq:
+                idx = self.cls[c]
+                rhs = rp[idx] - T[idx] @ z
+                nodes = self.node_cls[c]
+                z[idx] = np.einsum("nij,nj->ni", self.Dinv[nodes], rhs.reshape(-1, bd)).ravel()
+        return z[self.inv_order]
+
+
+# ----------------------------------------------------------------------------
+# a4: two-stage preconditioner (Alg. 3 and Alg. 4)
+# ----------------------------------------------------------------------------
+
+
+class TwoLevel:
+    """Alg. 2 set-up pieces bundled for Alg. 3/4: P, R = P^T, A_c, M_c^-1 and
+    the optional pre/post smoothers (objects with .solve)."""
+
+    def __init__(self, A, P, pre=None, post=None):
+        self.A = sp.csr_matrix(A)
+        self.P = sp.csr_matrix(P)
+        self.R = self.P.T.tocsr()
+        self.Ac = galerkin(self.A, self.P)
+        self.lu = coarse_factor(self.Ac)
+        self.pre = pre
+        self.post = post
+
+    def multiscale(self, v):
+        """Alg. 3: v_c = R v; w_c = M_c^-1 v_c; w = P w_c."""
+        vc = self.R @ v
+        wc = coarse_solve(self.lu, vc)
+        return self.P @ wc
+
+    def apply(self, v):
+        """Alg. 4 from z = 0: optional pre-smoothing, coarse correction with the
+        residual v - A z, optional post-smoothing."""
+        z = np.zeros_like(v)
+        if self.pre is not None:
+            z = z + self.pre.solve(v - self.A @ z)
+        w = self.multiscale(v - self.A @ z)
+        z = z + w
+        if self.post is not None:
+            z = z + self.post.solve(v - self.A @ z)
+        return z
+
+
+# ----------------------------------------------------------------------------
+# a5: Krylov accelerators (GMRES, right preconditioned; PCG)
+# ----------------------------------------------------------------------------
+
+
+def gmres_right(A, b, M, x0=None, rtol=1e-8, maxit=200, restart=200):
+    """Right-preconditioned GMRES with modified Gram-Schmidt Arnoldi and Givens
+    rotations (Saad, Iterative Methods, Alg. 9.5). Stops when the rotated
+    residual estimate is <= rtol ||b||; the true residual is then checked and
+    the method restarts from the current x if it is not yet met.
+    Returns (x, iterations, relres, history of estimated relative residuals)."""
+    A = sp.csr_matrix(A)
+    n = len(b)
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64)
+    bnorm = np.linalg.norm(b)
+    if bnorm == 0.0:
+        return np.zeros(n), 0, 0.0, []
+    its = 0
+    hist = []
+    while True:
+        r = b - A @ x
+        beta = np.linalg.norm(r)
+        if beta <= rtol * bnorm or its >= maxit:
+            return x, its, beta / bnorm, hist
+        m = min(restart, maxit - its)
+        V = np.zeros((m + 1, n))
+        Z = np.zeros((m, n))
+        Hh = np.zeros((m + 1, m))
+        cs = np.zeros(m)
+        sn = np.zeros(m)
+        g = np.zeros(m + 1)
+        g[0] = beta
+        V[0] = r / beta
+        j_done = 0
+        for j in range(m):
+            Z[j] = M(V[j])
+            w = A @ Z[j]
+            for i in range(j + 1):
+                Hh[i, j] = np.dot(w, V[i])
+                w = w - Hh[i, j] * V[i]
+            Hh[j + 1, j] = np.linalg.norm(w)
+            if Hh[j + 1, j] != 0.0:
+                V[j + 1] = w / Hh[j + 1, j]
+            for i in range(j):
+                t = cs[i] * Hh[i, j] + sn[i] * Hh[i + 1, j]
+                Hh[i + 1, j] = -sn[i] * Hh[i, j] + cs[i] * Hh[i + 1, j]
+                Hh[i, j] = t
+            den = np.hypot(Hh[j, j], Hh[j + 1, j])
+            cs[j] = Hh[j, j] / den
+            sn[j] = Hh[j + 1, j] / den
+            Hh[j, j] = den
+            Hh[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            its += 1
+            j_done = j + 1
+            hist.append(abs(g[j + 1]) / bnorm)
+            if abs(g[j + 1]) <= rtol * bnorm:
+                break
+        y = sla.solve_triangular(Hh[:j_done, :j_done], g[:j_done])
+        x = x + Z[:j_done].T @ y
+
+
+def pcg(A, b, M, x0=None, rtol=1e-8, maxit=500):
+    """Preconditioned conjugate gradients (Saad, Alg. 9.1) with a symmetric
+    preconditioner M; stops on the recursively updated residual <= rtol ||b||
+    and confirms with the true residual.
+    Returns (x, iterations, relres, history)."""
+    A = sp.csr_matrix(A)
+    x = np.zeros(len(b)) if x0 is None else np.array(x0, dtype=np.float64)
+    bnorm = np.linalg.norm(b)
+    r = b - A @ x
+    hist = []
+    its = 0
+    if np.linalg.norm(r) <= rtol * bnorm:
+        return x, 0, np.linalg.norm(r) / bnorm, hist
+    z = M(r)
+    p = z.copy()
+    rz = np.dot(r, z)
+    while its < maxit:
+        q = A @ p
+        alpha = rz / np.dot(p, q)
+        x = x + alpha * p
+        r = r - alpha * q
+        its += 1
+        rn = np.linalg.norm(r)
+        hist.append(rn / bnorm)
+        if rn <= rtol * bnorm:
+            rt = np.linalg.norm(b - A @ x)
+            if rt <= rtol * bnorm:
+                return x, its, rt / bnorm, hist
+            r = b - A @ x
+        z = M(r)
+        rz_new = np.dot(r, z)
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return x, its, np.linalg.norm(b - A @ x) / bnorm, hist
+
+
+# ----------------------------------------------------------------------------
+# Whole pipelines (Alg. 2 set-up + Krylov solve), as the library exposes them
+# ----------------------------------------------------------------------------
+
+
+def setup_scalar(A, dims, H, centering=0, omega=2.0 / 3.0, tol=1e-3, n_it=10, max_iter=100,
+                 smoother="ilu0"):
+    """Alg. 2 for a scalar operator (flow): partition, filter, Alg. 1, Galerkin
+    coarse operator, coarse LU and a colour-ordered ILU(0) post-smoother."""
+    A = sp.csr_matrix(A)
+    A.sort_indices()
+    part = partition(dims, H, centering)
+    Ahat = mmatrix_filter(A)
+    P0 = indicator(part["part"], part["pat"])
+    vals, its, e_it, hist = enhanced_msrsb(Ahat, part["pat"], P0, part["skel"], omega, tol, n_it, max_iter)
+    P = as_matrix(vals, part["pat"])
+    post = ColouredSmoother(A, parity_colours(dims), "ilu0") if smoother == "ilu0" else None
+    tl = TwoLevel(A, P, pre=None, post=post)
+    return dict(part=part, Ahat=Ahat, vals=vals, iters=its, e_it=e_it, hist=hist, P=P, tl=tl)
+
+
+def setup_elastic(indptr, indices, blocks, dims, H, omega=2.0 / 3.0, tol=1e-3, n_it=10, max_iter=100):
+    """Alg. 2 for 3x3-block elasticity: SDC blocks filtered per component,
+    three scalar bases on one shared pattern, block-diagonal P, Galerkin with
+    the full operator, forward/backward block Gauss-Seidel pre/post smoothers."""
+    part = partition(dims, H, 1)
+    A = bsr_to_csr(indptr, indices, blocks)
+    comps = sdc_blocks(indptr, indices, blocks)
+    P0 = indicator(part["part"], part["pat"])
+    out = []
+    for l in range(3):
+        Ahat = mmatrix_filter(comps[l])
+        out.append(enhanced_msrsb(Ahat, part["pat"], P0, part["skel"], omega, tol, n_it, max_iter))
+    Ps = [as_matrix(o[0], part["pat"]) for o in out]
+    P = block_prolongation(Ps)
+    col = parity_colours(dims)
+    pre = ColouredSmoother(A, col, "gs_fwd", bdim=3)
+    post = ColouredSmoother(A, col, "gs_bwd", bdim=3)
+    tl = TwoLevel(A, P, pre=pre, post=post)
+    return dict(part=part, comps=out, P=P, tl=tl, A=A)

@@ -1,0 +1,284 @@
+"""Finite-volume Darcy operators on uniform Cartesian grids of unit cells.
+
+The fine-scale pressure system A p = b of -div(K grad p) = q is assembled with
+the MPFA-O method (the multipoint scheme the paper's flow cases use) or with TPFA
+(the two-point scheme, exact for K-orthogonal grids). Cells are ordered with x
+fastest: flat = i0 + n0*(i1 + n1*i2). Each cell equation is the sum of fluxes
+leaving the cell, so A has a positive diagonal.
+
+Boundary conditions are given per domain side, ``bc[(axis, side)]`` with side 0 =
+low (x_axis = 0) and 1 = high, as ``("D", value)`` for a fixed pressure or
+``("N",)`` for no flow (the default).
+"""
+import itertools
+
+import numpy as np
+
+from .fields import gaussian_random_field, rotation_2d, rotation_zyx
+
+
+def _stencil_offsets(d):
+    # offsets in {-1,0,1}^d, x fastest (itertools varies the last entry fastest)
+    return [tuple(reversed(t)) for t in itertools.product((-1, 0, 1), repeat=d)]
+
+
+def _stencil_to_csr(dims, A_st):
+    """Convert a per-cell stencil array (*dims, 3^d) to CSR, keeping every
+    in-domain neighbour (the structural 3^d pattern) with sorted columns."""
+    d = len(dims)
+    n = int(np.prod(dims))
+    offs = _stencil_offsets(d)
+    coords = np.indices(dims).reshape(d, -1, order="F")  # (d, n) in flat order
+    flat = np.arange(n)
+    strides = [int(np.prod(dims[:a])) for a in range(d)]
+    rows, cols, vals = [], [], []
+    A_flat = _grid_flat(A_st, dims)
+    for s, o in enumerate(offs):
+        ok = np.ones(n, dtype=bool)
+        shift = 0
+        for a in range(d):
+            c = coords[a] + o[a]
+            ok &= (c >= 0) & (c < dims[a])
+            shift += o[a] * strides[a]
+        r = flat[ok]
+        rows.append(r)
+        cols.append(r + shift)
+        vals.append(A_flat[ok, s])
+    rows = np.concatenate(rows)
+    cols = np.concatenate(cols)
+    vals = np.concatenate(vals)
+    order = np.lexsort((cols, rows))
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    indptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(indptr, rows + 1, 1)
+    indptr = np.cumsum(indptr)
+    return indptr.astype(np.int32), cols.astype(np.int32), vals.astype(np.float64)
+
+
+def _grid_flat(a, dims):
+    """Flatten a (*dims, ...) array to (n, ...) with x fastest."""
+    n = int(np.prod(dims))
+    rest = a.shape[len(dims):]
+    return np.moveaxis(a, list(range(len(dims))), list(reversed(range(len(dims))))).reshape((n,) + rest)
+
+
+def mpfa_o(K, bc=None, wells=None):
+    """MPFA-O (eta = 0) on a uniform Cartesian grid of unit cells.
+
+    K : array (*dims, d, d), symmetric positive-definite cell tensors.
+    In every interaction region (the 2^d cells around a grid vertex) the pressure
+    is linear per cell, fixed by the cell pressure and the potentials at the
+    midpoints of the cell's d faces touching the vertex; flux continuity on each
+    of the d*2^(d-1) half-faces (or the boundary condition there) gives a local
+    system whose solution expresses every half-face flux in the cell pressures.
+    Returns (indptr, indices, data, b) with int32 CSR and float64 values.
+    """
+    bc = bc or {}
+    K = np.asarray(K, dtype=np.float64)
+    dims = K.shape[:-2]
+    d = len(dims)
+    assert K.shape[-2:] == (d, d)
+    nv = tuple(s + 1 for s in dims)
+    nvert = int(np.prod(nv))
+    offs = list(itertools.product((0, 1), repeat=d))  # local cells of a region
+    ncell = len(offs)
+    loc = {o: c for c, o in enumerate(offs)}
+    area = 0.5 ** (d - 1)
+
+    # half-faces: axis a, offsets q of the other axes
+    faces = []
+    for a in range(d):
+        for q in itertools.product((0, 1), repeat=d - 1):
+            om = tuple(list(q[:a]) + [0] + list(q[a:]))
+            op = tuple(list(q[:a]) + [1] + list(q[a:]))
+            faces.append((a, loc[om], loc[op]))
+    nf = len(faces)
+    fidx = {}
+    for f, (a, cm, cp) in enumerate(faces):
+        fidx[(cm, a)] = f
+        fidx[(cp, a)] = f
+
+    V = np.indices(nv).reshape(d, -1)  # vertex coords, C order over nv
+    pres = np.zeros((nvert, ncell), dtype=bool)
+    Kc = np.zeros((nvert, ncell, d, d))
+    for c, o in enumerate(offs):
+        cc = [V[a] - 1 + o[a] for a in range(d)]
+        ok = np.ones(nvert, dtype=bool)
+        for a in range(d):
+            ok &= (cc[a] >= 0) & (cc[a] < dims[a])
+        pres[:, c] = ok
+        idx = tuple(np.clip(cc[a], 0, dims[a] - 1) for a in range(d))
+        Kc[:, c] = K[idx] * ok[:, None, None]
+
+    # flux F_c(a) across the half-face of cell c normal to axis a (in +a
+    # direction) = sum_b U[c,a,b] * u_{f(c,b)} + Pc[c,a] * p_c
+    s = np.array([[1.0 if o[a] == 0 else -1.0 for a in range(d)] for o in offs])  # (ncell, d)
+    U = -2.0 * area * Kc * s[None, :, None, :]  # (nvert, ncell, a, b)
+    Pc = -U.sum(axis=3)  # (nvert, ncell, a)
+
+    C = np.zeros((nvert, nf, nf))
+    D = np.zeros((nvert, nf, ncell))
+    e = np.zeros((nvert, nf))
+    G = np.zeros((nvert, nf, nf))
+    Hm = np.zeros((nvert, nf, ncell))
+    side_val = {}
+    for f, (a, cm, cp) in enumerate(faces):
+        pm, pp = pres[:, cm], pres[:, cp]
+        both = pm & pp
+        only_m = pm & ~pp  # vertex on the high side of axis a
+        only_p = pp & ~pm  # vertex on the low side of axis a
+        none = ~pm & ~pp
+        kind_hi = bc.get((a, 1), ("N",))
+        kind_lo = bc.get((a, 0), ("N",))
+        dir_m = only_m & (kind_hi[0] == "D")
+        dir_p = only_p & (kind_lo[0] == "D")
+        neu_m = only_m & (kind_hi[0] != "D")
+        neu_p = only_p & (kind_lo[0] != "D")
+        ident = none | dir_m | dir_p
+        for b in range(d):
+            C[:, f, fidx[(cm, b)]] += (both | neu_m) * U[:, cm, a, b]
+            C[:, f, fidx[(cp, b)]] -= both * U[:, cp, a, b]
+            C[:, f, fidx[(cp, b)]] += neu_p * U[:, cp, a, b]
+        D[:, f, cm] -= (both | neu_m) * Pc[:, cm, a]
+        D[:, f, cp] += both * Pc[:, cp, a]
+        D[:, f, cp] -= neu_p * Pc[:, cp, a]
+        C[:, f, f] += ident
+        if kind_hi[0] == "D":
+            e[:, f] += dir_m * kind_hi[1]
+        if kind_lo[0] == "D":
+            e[:, f] += dir_p * kind_lo[1]
+        # flux from the minus cell if present, else the plus cell
+        use_m = pm
+        use_p = ~pm & pp
+        for b in range(d):
+            G[:, f, fidx[(cm, b)]] += use_m * U[:, cm, a, b]
+            G[:, f, fidx[(cp, b)]] += use_p * U[:, cp, a, b]
+        Hm[:, f, cm] += use_m * Pc[:, cm, a]
+        Hm[:, f, cp] += use_p * Pc[:, cp, a]
+        side_val[f] = (both, only_m & ~neu_m, only_p & ~neu_p)
+
+    Cinv_D = np.linalg.solve(C, D)
+    Cinv_e = np.linalg.solve(C, e[..., None])[..., 0]
+    T = np.einsum("vfg,vgc->vfc", G, Cinv_D) + Hm  # (nvert, nf, ncell)
+    t = np.einsum("vfg,vg->vf", G, Cinv_e)  # (nvert, nf)
+
+    n3 = 3 ** d
+    offs3 = _stencil_offsets(d)
+    st_index = {o: k for k, o in enumerate(offs3)}
+    A_st = np.zeros(tuple(dims) + (n3,))
+    bgrid = np.zeros(tuple(dims))
+    Tg = T.reshape(tuple(nv) + (nf, ncell))
+    tg = t.reshape(tuple(nv) + (nf,))
+
+    def add(row_off, sign, f, use_mask):
+        # rows: cell at v - 1 + row_off, over vertices where that cell exists
+        vsl = tuple(slice(1 - row_off[a], nv[a] - row_off[a]) for a in range(d))
+        csl = tuple(slice(0, dims[a]) for a in range(d))
+        m = use_mask.reshape(nv)[vsl]
+        for c, o in enumerate(offs):
+            rel = tuple(o[a] - row_off[a] for a in range(d))
+            A_st[csl + (st_index[rel],)] += sign * m * Tg[vsl + (f, c)]
+        bgrid[csl] -= sign * m * tg[vsl + (f,)]
+
+    for f, (a, cm, cp) in enumerate(faces):
+        both, bnd_m, bnd_p = side_val[f]
+        add(offs[cm], +1.0, f, both | bnd_m)
+        add(offs[cp], -1.0, f, both | bnd_p)
+
+    indptr, indices, data = _stencil_to_csr(dims, A_st)
+    b = _grid_flat(bgrid, dims).copy()
+    if wells:
+        _add_wells(indptr, indices, data, b, wells)
+    return indptr, indices, data, b
+
+
+def _add_wells(indptr, indices, data, b, wells):
+    """Bottom-hole-pressure wells: A_ii += WI, b_i += WI * p_w with WI = A_ii."""
+    for cell, pw in wells:
+        lo, hi = indptr[cell], indptr[cell + 1]
+        k = lo + int(np.searchsorted(indices[lo:hi], cell))
+        wi = data[k]
+        data[k] += wi
+        b[cell] += wi * pw
+
+
+def tpfa(K, bc=None, wells=None):
+    """Two-point flux approximation on unit cells (uses the diagonal of K only).
+
+    Face transmissibility is the harmonic mean 2 k1 k2 / (k1 + k2) of the two
+    cells' diagonal entries; a fixed-pressure boundary face has 2 k. The pattern
+    is the same 3^d structural pattern mpfa_o returns (unused entries are 0).
+    """
+    bc = bc or {}
+    K = np.asarray(K, dtype=np.float64)
+    dims = K.shape[:-2]
+    d = len(dims)
+    offs3 = _stencil_offsets(d)
+    st_index = {o: k for k, o in enumerate(offs3)}
+    A_st = np.zeros(tuple(dims) + (3 ** d,))
+    bgrid = np.zeros(tuple(dims))
+    ctr = st_index[(0,) * d]
+    for a in range(d):
+        ka = K[..., a, a]
+        lo = [slice(None)] * d
+        hi = [slice(None)] * d
+        lo[a] = slice(0, dims[a] - 1)
+        hi[a] = slice(1, dims[a])
+        k1, k2 = ka[tuple(lo)], ka[tuple(hi)]
+        T = 2.0 * k1 * k2 / (k1 + k2)
+        plus = tuple(1 if b == a else 0 for b in range(d))
+        minus = tuple(-1 if b == a else 0 for b in range(d))
+        A_st[tuple(lo) + (ctr,)] += T
+        A_st[tuple(lo) + (st_index[plus],)] -= T
+        A_st[tuple(hi) + (ctr,)] += T
+        A_st[tuple(hi) + (st_index[minus],)] -= T
+        for side in (0, 1):
+            kind = bc.get((a, side), ("N",))
+            if kind[0] != "D":
+                continue
+            sl = [slice(None)] * d
+            sl[a] = slice(0, 1) if side == 0 else slice(dims[a] - 1, dims[a])
+            sl = tuple(sl)
+            A_st[sl + (ctr,)] += 2.0 * ka[sl]
+            bgrid[sl] += 2.0 * ka[sl] * kind[1]
+    indptr, indices, data = _stencil_to_csr(dims, A_st)
+    b = _grid_flat(bgrid, dims).copy()
+    if wells:
+        _add_wells(indptr, indices, data, b, wells)
+    return indptr, indices, data, b
+
+
+def anisotropic_tensors(logk, R, ratios):
+    """Per-cell K = R diag(k * ratios) R^T with k = exp(logk)."""
+    k = np.exp(logk)
+    Dg = np.asarray(ratios, dtype=np.float64)
+    base = R @ np.diag(Dg) @ R.T
+    return k[..., None, None] * base
+
+
+def darcy_2d_case(n=64, H=8, seed=1001):
+    """2D MPFA-O case: ln k i.i.d. N(0,1), K = R(30) diag(k, 0.1k) R(30)^T,
+    p = 1 at x = 0, p = 0 at x = n, no flow on the other sides."""
+    rng = np.random.default_rng(seed)
+    logk = rng.standard_normal((n, n))
+    K = anisotropic_tensors(logk, rotation_2d(30.0), (1.0, 0.1))
+    bc = {(0, 0): ("D", 1.0), (0, 1): ("D", 0.0)}
+    indptr, indices, data, b = mpfa_o(K, bc)
+    return dict(indptr=indptr, indices=indices, data=data, b=b, dims=(n, n), H=(H, H),
+                centering=0, ncomp=1)
+
+
+def darcy_3d_case(n=64, H=8, seed=1002, sigma=3.0, corr_len=8.0, dims=None):
+    """3D MPFA-O case: ln k Gaussian random field (Gaussian covariance), tensor
+    anisotropy 10:1 rotated by Euler angles (20, 35, 0) degrees, no-flow outer
+    boundary, bottom-hole-pressure wells in two opposite corner cells."""
+    dims = tuple(dims) if dims is not None else (n, n, n)
+    rng = np.random.default_rng(seed)
+    logk = gaussian_random_field(dims, corr_len, sigma, rng)
+    K = anisotropic_tensors(logk, rotation_zyx(20.0, 35.0, 0.0), (1.0, 1.0, 0.1))
+    ncell = int(np.prod(dims))
+    wells = [(0, 1.0), (ncell - 1, 0.0)]
+    indptr, indices, data, b = mpfa_o(K, {}, wells)
+    Hs = (H,) * 3 if np.isscalar(H) else tuple(H)
+    return dict(indptr=indptr, indices=indices, data=data, b=b, dims=dims, H=Hs,
+                centering=0, ncomp=1)

@@ -1,0 +1,391 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix
+(hand-derived values, closed forms, invariants, brute force on tiny inputs)."""
+from fractions import Fraction
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import msrsb as O
+from synth.darcy import tpfa, mpfa_o, darcy_2d_case, darcy_3d_case, anisotropic_tensors
+from synth.elastic import q1_elasticity
+from synth.fields import rotation_2d
+
+
+def _csr(t):
+    A = sp.csr_matrix((t[2], t[1], t[0]))
+    A.sort_indices()
+    return A
+
+
+def _unit_tpfa(dims, bc=None):
+    d = len(dims)
+    K = np.zeros(dims + (d, d))
+    for a in range(d):
+        K[..., a, a] = 1.0
+    return _csr(tpfa(K, bc or {}))
+
+
+# ---------------- a0 partition ----------------
+
+@pytest.mark.parametrize("dims,H,cen", [((64, 64), (8, 8), 0), ((64, 64, 64), (8, 8, 8), 0),
+                                        ((49, 49, 49), (6, 6, 6), 1), ((13, 9), (3, 4), 0)])
+def test_partition_counts(dims, H, cen):
+    part = O.partition(dims, H, cen)
+    pat = part["pat"]
+    d = len(dims)
+    sizes = np.diff(pat.indptr)
+    assert sizes.min() >= 1 and sizes.max() <= 2 ** d
+    # skeleton rows are exactly those in fewer than 2^d supports, unless a
+    # domain edge cuts the support (rows before the first / after the last node)
+    assert np.all(sizes[~part["skel"]] >= 1)
+    # closed-form nnz: per axis, points with one id count 1, with two count 2
+    expect = 1
+    for a in range(d):
+        c, _ = O.coarse_axis(dims[a], H[a], cen)
+        x = np.arange(dims[a])
+        two = (x > c[0]) & (x < c[-1]) & ~np.isin(x, c)
+        expect *= int((~two).sum() + 2 * two.sum())
+    assert pat.nnz == expect
+    # every point's primal block is among its pattern ids (block within support)
+    rows = np.repeat(np.arange(pat.shape[0]), sizes)
+    hit = np.zeros(pat.shape[0], bool)
+    hit[rows[pat.indices == part["part"][rows]]] = True
+    assert hit.all()
+    # coarse node of J lies in block J and on the skeleton
+    assert np.all(part["part"][part["cnode"]] == np.arange(part["nc"]))
+    assert part["skel"][part["cnode"]].all()
+
+
+def test_partition_paper_sizes():
+    assert O.partition((64, 64), (8, 8), 0)["pat"].nnz == 113 ** 2
+    assert O.partition((49, 49, 49), (6, 6, 6), 1)["pat"].nnz == 89 ** 3
+    _, blk = O.coarse_axis(49, 6, 1)
+    assert list(np.bincount(blk)) == [4, 6, 6, 6, 6, 6, 6, 6, 3]
+
+
+def test_partition_bruteforce_supports():
+    # supports by direct definition: open interval between neighbouring nodes
+    dims, H = (10, 7), (4, 3)
+    part = O.partition(dims, H, 0)
+    cx, _ = O.coarse_axis(10, 4, 0)
+    cy, _ = O.coarse_axis(7, 3, 0)
+    pat = part["pat"].toarray() > 0
+    for x in range(10):
+        for y in range(7):
+            for Ix in range(len(cx)):
+                for Iy in range(len(cy)):
+                    inx = (Ix == 0 or x > cx[Ix - 1]) and (Ix == len(cx) - 1 or x < cx[Ix + 1])
+                    iny = (Iy == 0 or y > cy[Iy - 1]) and (Iy == len(cy) - 1 or y < cy[Iy + 1])
+                    assert pat[x + 10 * y, Ix + len(cx) * Iy] == (inx and iny)
+
+
+# ---------------- a1 filter ----------------
+
+def test_filter_invariants_mpfa():
+    c = darcy_2d_case(n=16)
+    A = _csr((c["indptr"], c["indices"], c["data"]))
+    Ah = O.mmatrix_filter(A)
+    off = Ah - sp.diags(Ah.diagonal())
+    assert off.data.max() <= 0.0
+    scale = np.asarray(abs(A).sum(axis=1)).ravel()
+    assert np.all(np.abs(np.asarray(Ah.sum(axis=1)).ravel()) <= 1e-15 * scale * 4)
+    # positive off-diagonals removed, negative ones kept verbatim
+    Ad, Ahd = A.toarray(), Ah.toarray()
+    m = ~np.eye(A.shape[0], dtype=bool)
+    assert np.array_equal(Ahd[m], np.minimum(Ad[m], 0.0))
+    # diagonal ignores A's own diagonal (wells / Dirichlet terms have no effect)
+    assert np.allclose(np.diag(Ahd), -np.minimum(Ad * m, 0).sum(axis=1), rtol=1e-15, atol=0)
+
+
+def test_filter_noop_on_mmatrix_offdiagonals():
+    A = _unit_tpfa((6, 5), {(0, 0): ("D", 1.0)})
+    Ah = O.mmatrix_filter(A)
+    assert np.array_equal((Ah - sp.diags(Ah.diagonal())).toarray(), (A - sp.diags(A.diagonal())).toarray())
+
+
+def test_sdc_blocks():
+    rng = np.random.default_rng(0)
+    e = q1_elasticity(np.exp(rng.standard_normal((2, 2, 2))), rng.uniform(0.2, 0.35, (2, 2, 2)))
+    comps = O.sdc_blocks(e["indptr"], e["indices"], e["data"])
+    full = O.bsr_to_csr(e["indptr"], e["indices"], e["data"]).toarray()
+    for l in range(3):
+        assert np.array_equal(comps[l].toarray(), full[l::3, l::3])
+
+
+# ---------------- a2 basis ----------------
+
+def _load_first_step(golden_dir):
+    rows = []
+    with open(os.path.join(golden_dir, "basis_first_step_9x3_H3.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            x, y, J, num, den = map(int, line.split())
+            rows.append((x, y, J, Fraction(num, den)))
+    return rows
+
+
+def test_basis_first_pass_hand_values(golden_dir):
+    dims, H = (9, 3), (3, 3)
+    A = _unit_tpfa(dims)
+    part = O.partition(dims, H, 0)
+    P0 = O.indicator(part["part"], part["pat"])
+    vals, k, e_it, hist = O.enhanced_msrsb(O.mmatrix_filter(A), part["pat"], P0, part["skel"],
+                                           tol=0.0, n_it=1, max_iter=1)
+    Pm = O.as_matrix(vals, part["pat"]).toarray()
+    for x, y, J, v in _load_first_step(golden_dir):
+        assert abs(Pm[x + 9 * y, J] - float(v)) < 1e-15, (x, y, J)
+    assert k == 1 and abs(e_it - 2.0 / 9.0) < 1e-15
+
+
+def _hats(n, H, cen):
+    c, _ = O.coarse_axis(n, H, cen)
+    M = np.zeros((n, len(c)))
+    for I in range(len(c)):
+        for x in range(n):
+            if I > 0 and c[I - 1] < x <= c[I]:
+                M[x, I] = (x - c[I - 1]) / (c[I] - c[I - 1])
+            elif I + 1 < len(c) and c[I] <= x < c[I + 1]:
+                M[x, I] = (c[I + 1] - x) / (c[I + 1] - c[I])
+            elif (I == 0 and x <= c[0]) or (I == len(c) - 1 and x >= c[-1]):
+                M[x, I] = 1.0
+    return M
+
+
+@pytest.mark.parametrize("dims,H", [((16, 12), (4, 4)), ((13, 9), (3, 3)), ((9, 10, 7), (3, 4, 3))])
+def test_basis_fixed_point_is_tensor_hats(dims, H):
+    # reflection-symmetric zero-row-sum stencil: the converged basis is the
+    # tensor product of 1D piecewise-linear hats through the coarse nodes
+    # (the "bilinear interpolators" of Sec. 4, Fig. 7d)
+    A = _unit_tpfa(dims)
+    part = O.partition(dims, H, 0)
+    P0 = O.indicator(part["part"], part["pat"])
+    vals, k, e_it, _ = O.enhanced_msrsb(O.mmatrix_filter(A), part["pat"], P0, part["skel"],
+                                        tol=1e-13, n_it=1, max_iter=20000)
+    full = _hats(dims[0], H[0], 0)
+    for a in range(1, len(dims)):
+        full = np.kron(_hats(dims[a], H[a], 0), full)
+    assert e_it <= 1e-13
+    assert np.abs(O.as_matrix(vals, part["pat"]).toarray() - full).max() < 1e-10
+
+
+def test_basis_fe_homogeneous_recovers_trilinear():
+    # the paper's FE demo (Sec. 4, Fig. 7d): on a homogeneous Cartesian FE mesh
+    # the filtered SDC component recovers (bi/tri)linear interpolators. The Q1
+    # stencil of one displacement component is reflection symmetric, so the
+    # fixed point is the tensor product of 1D hats through the coarse nodes.
+    e = q1_elasticity(np.ones((9, 6, 3)), 0.25 * np.ones((9, 6, 3)), fixed_bottom=False, top_traction=None)
+    comps = O.sdc_blocks(e["indptr"], e["indices"], e["data"])
+    dims = e["node_dims"]
+    part = O.partition(dims, (3, 3, 3), 1)
+    P0 = O.indicator(part["part"], part["pat"])
+    for l in range(3):
+        vals, k, e_it, _ = O.enhanced_msrsb(O.mmatrix_filter(comps[l]), part["pat"], P0, part["skel"],
+                                            tol=1e-12, n_it=1, max_iter=20000)
+        full = np.kron(_hats(4, 3, 1), np.kron(_hats(7, 3, 1), _hats(10, 3, 1)))
+        assert k > 10 and e_it <= 1e-12
+        assert np.abs(O.as_matrix(vals, part["pat"]).toarray() - full).max() < 1e-9
+
+
+def test_basis_invariants_mpfa():
+    c = darcy_3d_case(n=16)
+    A = _csr((c["indptr"], c["indices"], c["data"]))
+    part = O.partition(c["dims"], c["H"], 0)
+    P0 = O.indicator(part["part"], part["pat"])
+    vals, k, e_it, hist = O.enhanced_msrsb(O.mmatrix_filter(A), part["pat"], P0, part["skel"],
+                                           tol=0.0, n_it=10, max_iter=50)
+    P = O.as_matrix(vals, part["pat"])
+    assert np.abs(np.asarray(P.sum(axis=1)).ravel() - 1.0).max() < 1e-14
+    assert vals.min() >= 0.0 and vals.max() <= 1.0 + 1e-15
+    assert k == 50 and [h[0] for h in hist] == [0, 10, 20, 30, 40]
+    # e_it decreases between checks on the filtered operator
+    es = [h[1] for h in hist]
+    assert all(b < a for a, b in zip(es, es[1:]))
+
+
+def test_unfiltered_basis_leaves_unit_interval():
+    # Sec. 3.1 / Fig. 3c: smoothing with the unfiltered MPFA-O operator loses
+    # monotonicity (entries leave [0, 1]); the filtered operator keeps them.
+    # strong rotated anisotropy (1000:1 at 30 degrees) stands in for the
+    # paper's perturbed, 10x stretched grid: both make MPFA-O far from an M-matrix
+    n = 16
+    K = anisotropic_tensors(np.zeros((n, n)), rotation_2d(30.0), (1.0, 0.001))
+    A = _csr(mpfa_o(K, {}))
+    part = O.partition((n, n), (4, 4), 0)
+    P0 = O.indicator(part["part"], part["pat"])
+    Ah = A.copy()
+    Ah.setdiag(0)
+    Ah.eliminate_zeros()
+    Ah = (Ah - sp.diags(np.asarray(Ah.sum(axis=1)).ravel())).tocsr()  # zero row sum, not filtered
+    raw, *_ = O.enhanced_msrsb(Ah, part["pat"], P0, part["skel"], tol=0.0, max_iter=30)
+    filt, *_ = O.enhanced_msrsb(O.mmatrix_filter(A), part["pat"], P0, part["skel"], tol=0.0, max_iter=30)
+    assert raw.min() < -1e-2 or raw.max() > 1 + 1e-2
+    assert filt.min() >= 0 and filt.max() <= 1 + 1e-15
+
+
+# ---------------- a3 Galerkin ----------------
+
+def test_galerkin_identity_prolongation():
+    c = darcy_3d_case(n=6)
+    A = _csr((c["indptr"], c["indices"], c["data"]))
+    part = O.partition(c["dims"], (1, 1, 1), 0)
+    P = O.as_matrix(O.indicator(part["part"], part["pat"]), part["pat"])
+    assert np.array_equal(O.galerkin(A, P).toarray(), A.toarray())
+
+
+def test_galerkin_rowsums_and_dense():
+    c = darcy_3d_case(n=12, H=4)
+    A = _csr((c["indptr"], c["indices"], c["data"]))
+    s = O.setup_scalar(A, c["dims"], c["H"], tol=0.0, max_iter=10)
+    P = s["P"]
+    Ac = s["tl"].Ac.toarray()
+    Pd, Ad = P.toarray(), A.toarray()
+    dense = Pd.T @ Ad @ Pd
+    assert np.abs(Ac - dense).max() <= 1e-12 * np.abs(dense).max()
+    # partition of unity: A_c 1 = P^T (A 1); A has wells, so A 1 != 0 and a
+    # Galerkin product built from the filtered operator would fail this
+    lhs = Ac @ np.ones(Ac.shape[0])
+    rhs = Pd.T @ (Ad @ np.ones(A.shape[0]))
+    assert np.abs(lhs - rhs).max() <= 1e-12 * np.abs(Ac).max()
+    assert np.abs(rhs).max() > 1e-3 * np.abs(Ac).max()
+
+
+def test_galerkin_symmetric_spd_elastic():
+    rng = np.random.default_rng(1)
+    e = q1_elasticity(np.exp(rng.standard_normal((6, 6, 6))), rng.uniform(0.2, 0.35, (6, 6, 6)))
+    s = O.setup_elastic(e["indptr"], e["indices"], e["data"], e["node_dims"], (3, 3, 3), tol=0.0, max_iter=5)
+    Ac = s["tl"].Ac.toarray()
+    assert np.abs(Ac - Ac.T).max() <= 1e-13 * np.abs(Ac).max()
+    assert np.linalg.eigvalsh(Ac).min() > 0
+
+
+# ---------------- smoothers ----------------
+
+def test_parity_colouring_is_valid():
+    c = darcy_3d_case(n=6)
+    A = _csr((c["indptr"], c["indices"], c["data"]))
+    col = O.parity_colours(c["dims"])
+    r = np.repeat(np.arange(A.shape[0]), np.diff(A.indptr))
+    off = r != A.indices
+    assert np.all(col[r[off]] != col[A.indices[off]])
+    assert col.max() == 7
+
+
+def test_ilu0_defining_property():
+    c = darcy_3d_case(n=8)
+    A = _csr((c["indptr"], c["indices"], c["data"]))
+    order = O.colour_order(O.parity_colours(c["dims"]))
+    B = A[order][:, order].tocsr()
+    B.sort_indices()
+    L, U = O.ilu0(B)
+    LU = ((L + sp.eye(B.shape[0])) @ U).toarray()
+    mask = B.toarray() != 0
+    mask |= np.eye(B.shape[0], dtype=bool)
+    Bd = B.toarray()
+    assert np.abs(LU[mask] - Bd[mask]).max() <= 1e-12 * np.abs(Bd).max()
+
+
+def test_ilu0_exact_for_tridiagonal():
+    n = 40
+    rng = np.random.default_rng(2)
+    T = sp.diags([-rng.uniform(0.5, 1, n - 1), 3 + rng.uniform(0, 1, n), -rng.uniform(0.5, 1, n - 1)],
+                 [-1, 0, 1], format="csr")
+    L, U = O.ilu0(T)
+    assert np.abs(((L + sp.eye(n)) @ U - T).toarray()).max() < 1e-14
+    sm = O.ColouredSmoother(T, np.zeros(n, dtype=np.int64) + (np.arange(n) % 2), "ilu0")
+    v = rng.standard_normal(n)
+    # colour order on a chain is still a valid elimination order -> exact
+    # only in natural order; check the triangular solves satisfy L U z = v
+    z = sm.solve(v)
+    B = sm.B
+    Lp, Up = O.ilu0(B)
+    zp = z[sm.order]
+    assert np.abs(((Lp + sp.eye(n)) @ (Up @ zp)) - v[sm.order]).max() < 1e-13
+
+
+def test_block_gauss_seidel_solves_its_triangle():
+    rng = np.random.default_rng(4)
+    e = q1_elasticity(np.exp(rng.standard_normal((3, 3, 3))), rng.uniform(0.2, 0.35, (3, 3, 3)))
+    A = O.bsr_to_csr(e["indptr"], e["indices"], e["data"])
+    col = O.parity_colours(e["node_dims"])
+    v = rng.standard_normal(A.shape[0])
+    for kind in ("gs_fwd", "gs_bwd"):
+        sm = O.ColouredSmoother(A, col, kind, bdim=3)
+        z = sm.solve(v)[sm.order]
+        B = sm.B.toarray()
+        node = np.arange(B.shape[0]) // 3
+        keep = (node[:, None] == node[None, :])
+        keep |= (np.arange(B.shape[0])[:, None] > np.arange(B.shape[0])[None, :]) if kind == "gs_fwd" else \
+            (np.arange(B.shape[0])[:, None] < np.arange(B.shape[0])[None, :])
+        M = np.where(keep, B, 0.0)
+        assert np.abs(M @ z - v[sm.order]).max() < 1e-10 * np.abs(v).max()
+
+
+# ---------------- a4 two-stage apply ----------------
+
+def test_two_level_matches_error_propagation_matrix():
+    rng = np.random.default_rng(6)
+    e = q1_elasticity(np.exp(rng.standard_normal((4, 3, 3))), rng.uniform(0.2, 0.35, (4, 3, 3)))
+    s = O.setup_elastic(e["indptr"], e["indices"], e["data"], e["node_dims"], (2, 2, 2), tol=0.0, max_iter=8)
+    tl = s["tl"]
+    A = tl.A.toarray()
+    n = A.shape[0]
+    I = np.eye(n)
+    Minv = np.column_stack([tl.apply(I[:, j]) for j in range(n)])
+    Mpre = np.column_stack([tl.pre.solve(I[:, j]) for j in range(n)])
+    Mpost = np.column_stack([tl.post.solve(I[:, j]) for j in range(n)])
+    P = tl.P.toarray()
+    C = P @ np.linalg.solve(P.T @ A @ P, P.T)
+    E = (I - Mpost @ A) @ (I - C @ A) @ (I - Mpre @ A)
+    ref = (I - E) @ np.linalg.inv(A)
+    assert np.abs(Minv - ref).max() <= 1e-8 * np.abs(ref).max()
+    # forward pre / backward post Gauss-Seidel make the preconditioner symmetric
+    assert np.abs(Minv - Minv.T).max() <= 1e-8 * np.abs(Minv).max()
+
+
+def test_coarse_correction_galerkin_orthogonality():
+    c = darcy_2d_case(n=24)
+    A = _csr((c["indptr"], c["indices"], c["data"]))
+    s = O.setup_scalar(A, c["dims"], c["H"], tol=0.0, max_iter=20)
+    tl = s["tl"]
+    v = np.random.default_rng(7).standard_normal(A.shape[0])
+    r = v - A @ tl.multiscale(v)
+    assert np.abs(tl.R @ r).max() <= 1e-10 * np.abs(tl.R @ v).max()
+    w = np.random.default_rng(8).standard_normal(A.shape[0])
+    assert np.allclose(tl.apply(2 * v - 3 * w), 2 * tl.apply(v) - 3 * tl.apply(w), rtol=0, atol=1e-10)
+
+
+# ---------------- a5 Krylov ----------------
+
+def test_gmres_matches_direct_solve():
+    c = darcy_2d_case(n=32, H=8)
+    A = _csr((c["indptr"], c["indices"], c["data"]))
+    s = O.setup_scalar(A, c["dims"], c["H"])
+    x, its, rr, hist = O.gmres_right(A, c["b"], s["tl"].apply, rtol=1e-10)
+    xs = np.linalg.solve(A.toarray(), c["b"])
+    assert rr <= 1e-10
+    assert np.linalg.norm(x - xs) <= 1e-7 * np.linalg.norm(xs)
+    # the two-level preconditioner needs fewer iterations than its smoother
+    _, its_s, _, _ = O.gmres_right(A, c["b"], s["tl"].post.solve, rtol=1e-10)
+    assert its < its_s
+
+
+def test_gmres_exact_preconditioner_one_iteration():
+    c = darcy_2d_case(n=8)
+    A = _csr((c["indptr"], c["indices"], c["data"]))
+    s = O.setup_scalar(A, c["dims"], (1, 1), smoother=None)
+    x, its, rr, _ = O.gmres_right(A, c["b"], s["tl"].apply)
+    assert its == 1 and rr < 1e-12
+
+
+def test_pcg_matches_direct_solve():
+    rng = np.random.default_rng(9)
+    e = q1_elasticity(np.exp(rng.standard_normal((6, 6, 6))), rng.uniform(0.2, 0.35, (6, 6, 6)))
+    s = O.setup_elastic(e["indptr"], e["indices"], e["data"], e["node_dims"], (3, 3, 3), tol=1e-3)
+    A = s["A"]
+    x, its, rr, _ = O.pcg(A, e["b"], s["tl"].apply, rtol=1e-10)
+    xs = np.linalg.solve(A.toarray(), e["b"])
+    assert rr <= 1e-10
+    assert np.linalg.norm(x - xs) <= 1e-7 * np.linalg.norm(xs)
