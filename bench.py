@@ -1,0 +1,353 @@
+"""Benchmark: MsRSB set-up (filter + basis + Galerkin + coarse inverse +
+smoother factor) plus the Krylov solve to relative residual 1e-8, on the 3D
+Darcy workload (64^3 cells, 27-point MPFA-O, ln k Gaussian random field with
+correlation length 8 cells and sigma 3, 10:1 anisotropy rotated (20, 35, 0)
+degrees, corner well pair, 8^3-cell coarse blocks, GMRES + ILU(0) post
+smoothing). One step = one whole set-up + solve; `value` is seconds per step of
+the mixed-precision form (FP32 basis, P and smoother, FP64 Krylov and coarse
+inverse); the plain FP64 form is timed the same way and reported beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun (N > 1) every rank solves its own copy (replicas); rank 0
+prints one JSON line with the max over ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MsRSB basis build + PCG/GMRES solve s to 1e-8, HBM GB/s; mixed vs FP64 GPU"
+WORKLOAD = "3D Darcy 64^3 MPFA-O 27-point, ln k GRF (l=8, sigma=3), 10:1 aniso rot (20,35,0), corner wells, H=8^3"
+N_GRID, H_BLOCK, SEED = 64, 8, 1002
+RTOL, MAXIT = 1e-8, 300
+BASIS = dict(tol=1e-3, n_it=10, max_iter=100)
+
+
+def make_problem():
+    from synth.darcy import darcy_3d_case
+    return darcy_3d_case(n=N_GRID, H=H_BLOCK, seed=SEED)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 6:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nme, v in zip(names, parts[2:6]):
+                if v.lower().startswith("active"):
+                    reasons.add(nme)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def smooth_bytes(n, nnz, W, esize):
+    """Algorithmic bytes of one restricted-smoothing pass: the filtered operator
+    (value + packed column per nonzero), P read once and written once, the
+    per-row scale and slot mask."""
+    return nnz * (esize + 4) + n * (2 * W * esize + esize + 1)
+
+
+def gpu_arm(args, rank, world):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1912_06934_gb300 as M
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    c = make_problem()
+    n, nnz = len(c["indptr"]) - 1, len(c["indices"])
+    A = M.Mat.from_host(c["indptr"], c["indices"], c["data"], device=dev)
+    b = torch.as_tensor(c["b"], device=dev)
+    g = M.grid(c["dims"], c["H"])
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    def step(prec):
+        o = M.opts(prec=prec, **BASIS)
+        h = M.msrsb_setup(A, g, o)
+        r = h.solve(b, rtol=RTOL, maxit=MAXIT)
+        info = h.info()
+        h.destroy()
+        return r, info
+
+    def timed(prec, k):
+        ms, last = [], None
+        for _ in range(k):
+            flush.zero_()  # evict L2 between steps (not timed)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            last = step(prec)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms, last
+
+    for _ in range(args.warmup):
+        step(M.msrsb.MSRSB_F32)
+        step(M.msrsb.MSRSB_F64)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    M.msrsb_profile(True)
+    with ClockSampler(dev.index) as clk:
+        ms32, (r32, inf32) = timed(M.msrsb.MSRSB_F32, args.steps)
+        launches, sm_l32, sm_ms32 = M.msrsb_profile_read()
+        M.msrsb_profile(True)
+        ms64, (r64, inf64) = timed(M.msrsb.MSRSB_F64, args.steps)
+        launches64, sm_l64, sm_ms64 = M.msrsb_profile_read()
+    M.msrsb_profile(False)
+    torch.cuda.synchronize()
+    t32, t64 = sum(ms32), sum(ms64)
+    if world > 1:
+        t = torch.tensor([t32, t64], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t32, t64 = float(t[0]), float(t[1])
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    ip = torch.as_tensor(np.asarray(c["indptr"], dtype=np.int32)).pin_memory()
+    ix = torch.as_tensor(np.asarray(c["indices"], dtype=np.int32)).pin_memory()
+    dv = torch.as_tensor(np.asarray(c["data"], dtype=np.float64)).pin_memory()
+    bh = torch.as_tensor(c["b"]).pin_memory()
+    xh = torch.zeros_like(bh).pin_memory()
+    o32 = M.opts(prec=M.msrsb.MSRSB_F32, **BASIS)
+    e2e_t = []
+    for k in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        M.msrsb.msrsb_solve_host_ptrs(ip, ix, dv, 1, g, o32, bh, xh, RTOL, MAXIT)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            e2e_t.append(time.perf_counter() - t0)
+    resid = np.linalg.norm(c["b"] - _spmv(c, xh.numpy())) / np.linalg.norm(c["b"])
+    h2d = 4 * (n + 1) + 4 * nnz + 8 * nnz + 8 * n
+    d2h = 8 * n
+
+    hbm, peak_kind = peaks()
+    W = 8
+    per_launch32 = smooth_bytes(n, nnz, W, 4)
+    achieved = per_launch32 / (sm_ms32 / sm_l32 * 1e-3) / 1e9 if sm_l32 else None
+    per_launch64 = smooth_bytes(n, nnz, W, 8)
+    achieved64 = per_launch64 / (sm_ms64 / sm_l64 * 1e-3) / 1e9 if sm_l64 else None
+    out = {
+        "metric": METRIC,
+        "value": t32 / args.steps / 1e3,
+        "unit": "s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": t32 / args.steps,
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_cells": n, "nnz": nnz, "coarse_nodes": inf32["nc"],
+                   "basis": "omega=2/3 tol=1e-3 n_it=10 max_iter=100", "krylov": "GMRES(200) right, ILU(0) post",
+                   "rtol": RTOL, "l2": "flushed between steps (512 MB write)", "parallelism": "replicas"},
+        "mixed": {"ms_per_step": t32 / args.steps, "basis_iters": inf32["basis_iters"], "krylov_iters": r32["iters"],
+                  "relres": r32["relres"]},
+        "fp64": {"ms_per_step": t64 / args.steps, "basis_iters": inf64["basis_iters"], "krylov_iters": r64["iters"],
+                 "relres": r64["relres"], "smooth_kernel_gbs": achieved64,
+                 "smooth_kernel_us": sm_ms64 / sm_l64 * 1e3 if sm_l64 else None},
+        "speedup_mixed_vs_fp64": t64 / t32,
+        "roofline": {"kernel": "smooth_kernel<float,8> (restricted smoothing, Alg. 1)", "bound": "hbm",
+                     "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm if achieved else None, "traffic": None,
+                     "bytes_per_launch": per_launch32, "launches": sm_l32,
+                     "us_per_launch": sm_ms32 / sm_l32 * 1e3 if sm_l32 else None,
+                     "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs, burst copy)"},
+        "e2e": {"value": statistics.median(e2e_t) if e2e_t else None, "unit": "s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "relres": float(resid), "call": "msrsb_solve_host (pinned host buffers)"},
+        "gpu_launches": int(launches + launches64),
+        "gpu_launches_per_step": {"mixed": launches / args.steps, "fp64": launches64 / args.steps},
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(c)
+    return out
+
+
+def _spmv(c, x):
+    import scipy.sparse as sp
+    return sp.csr_matrix((c["data"], c["indices"], c["indptr"])) @ x
+
+
+def cpu_baseline(c, basis_passes=10, gmres_its=5):
+    """Time the FP64 oracle, as it stands, on a bounded sample of the workload:
+    partition, filter, Galerkin + coarse LU + colour-ordered ILU(0) once at
+    full size, plus `basis_passes` Alg. 1 passes and `gmres_its` GMRES
+    iterations at full size (per-pass and per-iteration seconds returned)."""
+    import scipy.sparse as sp
+    from oracle import msrsb as O
+    A = sp.csr_matrix((c["data"], c["indices"], c["indptr"]))
+    A.sort_indices()
+    t = {}
+    t0 = time.perf_counter()
+    part = O.partition(c["dims"], c["H"], 0)
+    t["partition"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    Ah = O.mmatrix_filter(A)
+    t["filter"] = time.perf_counter() - t0
+    P0 = O.indicator(part["part"], part["pat"])
+    t0 = time.perf_counter()
+    vals, k, e, _ = O.enhanced_msrsb(Ah, part["pat"], P0, part["skel"], tol=0.0, n_it=10, max_iter=basis_passes)
+    t["basis_pass"] = (time.perf_counter() - t0) / basis_passes
+    P = O.as_matrix(vals, part["pat"])
+    t0 = time.perf_counter()
+    post = O.ColouredSmoother(A, O.parity_colours(c["dims"]), "ilu0")
+    tl = O.TwoLevel(A, P, pre=None, post=post)
+    t["galerkin_lu_ilu"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    O.gmres_right(A, c["b"], tl.apply, rtol=0.0, maxit=gmres_its)
+    t["gmres_it"] = (time.perf_counter() - t0) / gmres_its
+    return t
+
+
+def oracle_counts(c):
+    """Alg. 1 passes and GMRES iterations of the FP64 oracle on the workload
+    (one full run)."""
+    import scipy.sparse as sp
+    from oracle import msrsb as O
+    A = sp.csr_matrix((c["data"], c["indices"], c["indptr"]))
+    s = O.setup_scalar(A, c["dims"], c["H"], **BASIS)
+    _, its, _, _ = O.gmres_right(A, c["b"], s["tl"].apply, rtol=RTOL, maxit=MAXIT)
+    return s["iters"], its
+
+
+def finish_cpu(out):
+    t = out.pop("cpu_baseline", None)
+    if t is None:
+        return
+    fp = out["fp64"]
+    total = (t["partition"] + t["filter"] + t["galerkin_lu_ilu"] + t["basis_pass"] * fp["basis_iters"]
+             + t["gmres_it"] * fp["krylov_iters"])
+    out["cpu_baseline"] = {"value": total, "unit": "s", "cores": 1, "kind": "oracle",
+                           "sample": "64^3 workload at full size: partition, filter, Galerkin + coarse LU + "
+                                     "colour-ordered ILU(0) once; 10 Alg. 1 passes and 5 GMRES iterations timed and "
+                                     "scaled to the FP64 pass / iteration counts (%d, %d)"
+                                     % (fp["basis_iters"], fp["krylov_iters"]),
+                           "phases_s": {k: round(v, 4) for k, v in t.items()}}
+
+
+def reference_arm(args, rank, world):
+    """The oracle as the reference implementation: one full oracle run fixes
+    the pass and iteration counts; each step then times the bounded sample of
+    cpu_baseline and scales it to one full set-up + solve."""
+    if rank != 0:
+        return None
+    c = make_problem()
+    basis_iters, krylov_iters = oracle_counts(c)
+    vals = []
+    for k in range(args.warmup + args.steps):
+        t = cpu_baseline(c, basis_passes=3, gmres_its=2)
+        total = (t["partition"] + t["filter"] + t["galerkin_lu_ilu"] + t["basis_pass"] * basis_iters
+                 + t["gmres_it"] * krylov_iters)
+        if k >= args.warmup:
+            vals.append(total)
+    v = statistics.median(vals)
+    sample = ("per step: full-size partition, filter, Galerkin + coarse LU + ILU(0) once, 3 Alg. 1 passes and "
+              "2 GMRES iterations, scaled to the oracle's own %d passes and %d iterations" % (basis_iters, krylov_iters))
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "parallelism": "replicas"},
+            "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        out = reference_arm(args, rank, world)
+        if out is not None:
+            print(json.dumps(out))
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    out = gpu_arm(args, rank, world)
+    if rank == 0:
+        finish_cpu(out)
+        print(json.dumps(out))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

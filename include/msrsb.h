@@ -1,0 +1,208 @@
+/*
+ * msrsb.h -- C ABI of a GB300 (sm_103a) implementation of the enhanced
+ * multiscale restriction-smoothed basis (MsRSB) two-level preconditioner of
+ * Bosma, Klevtsov, Moyner and Castelletto, arXiv 1912.06934.
+ *
+ * Problem statement (Sec. 2, Eq. 1-3): solve A u = f with a Krylov method
+ * preconditioned by a prolongation P built by restricted smoothing (Alg. 1),
+ * the Galerkin coarse operator A_c = P^T A P and a fine-scale smoother
+ * (Alg. 2-4).
+ *
+ * Conventions shared by every entry point
+ *  - Array arguments are DEVICE pointers unless the name ends in _h (host).
+ *    The caller allocates and owns them; no call frees or keeps them, except
+ *    msrsb_setup, which keeps a non-owning reference to A (see there).
+ *  - Integer index arrays are int32; fine rows n < 2^24 (the smoothing kernel
+ *    packs an 8-bit support mask beside each column index).
+ *  - The fine operator A is FP64 CSR (bdim = 1) or FP64 3x3 block CSR
+ *    (bdim = 3, blocks row-major, dof = 3*node + component) with sorted
+ *    column indices and the diagonal present in every row.
+ *  - Grids are Cartesian, x fastest: flat = x + nx*(y + ny*z); coarse ids use
+ *    the same ordering over the coarse grid.
+ *  - The prolongation pattern is an ELL array p_ids[n][W], W = 2^dim, entries
+ *    -1 where unused. Slot s of every row only ever holds coarse nodes of
+ *    colour s, colour(J) = sum_d (J_d mod 2) 2^d: coarse nodes whose supports
+ *    overlap differ in colour, so a node sits in the same slot in every row.
+ *    P values are p_val[comp][n][W] in the precision given by msrsb_prec.
+ *  - Work is stream-ordered on the cudaStream_t passed in. Calls that return
+ *    host values (arguments ending in _h) synchronise that stream first.
+ *  - Every call returns msrsb_status; on anything but MSRSB_OK,
+ *    msrsb_last_error() gives a message (per host thread). Outputs are then
+ *    unspecified, except for MSRSB_ENOCONV (see msrsb_solve). Nothing ever
+ *    traps or aborts the process.
+ */
+#ifndef MSRSB_H
+#define MSRSB_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MSRSB_OK = 0,
+    MSRSB_EINVAL = 1,      /* bad argument (null pointer, unsupported option) */
+    MSRSB_ESHAPE = 2,      /* inconsistent sizes */
+    MSRSB_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed */
+    MSRSB_ENOMEM = 4,      /* device allocation failed */
+    MSRSB_EBREAKDOWN = 5,  /* zero pivot (coarse inverse, ILU(0), block diagonal) or Krylov breakdown */
+    MSRSB_ENOCONV = 6,     /* Krylov iteration limit reached before the tolerance */
+    MSRSB_ETIMEOUT = 7,    /* a bounded device-side wait expired */
+    MSRSB_ENAN = 8         /* non-finite value in a residual */
+} msrsb_status;
+
+typedef enum { MSRSB_F64 = 0, MSRSB_F32 = 1 } msrsb_prec;
+typedef enum { MSRSB_SMOOTH_NONE = 0, MSRSB_SMOOTH_ILU0 = 1, MSRSB_SMOOTH_GS = 2 } msrsb_smoother;
+typedef enum { MSRSB_GMRES = 0, MSRSB_PCG = 1, MSRSB_RICHARDSON = 2 } msrsb_krylov;
+
+/* Sparse FP64 fine operator, device arrays (rowptr[nrows+1], colidx[nnz],
+ * val[nnz * bdim * bdim]). nrows and nnz count block rows / blocks. */
+typedef struct {
+    int32_t nrows, nnz, bdim;
+    const int32_t *rowptr, *colidx;
+    const double *val;
+} msrsb_mat;
+
+/* Cartesian fine grid and uniform coarse partition (Sec. 2.1).
+ * dim 2 or 3; (nx, ny, nz) fine points (cells for centering 0, nodes for
+ * centering 1; nz = 1 in 2D); (hx, hy, hz) coarse block edge in cells or
+ * elements; ncomp 1 (pressure) or 3 (displacement, with bdim = 3). */
+typedef struct {
+    int32_t dim, nx, ny, nz, hx, hy, hz, centering, ncomp;
+} msrsb_grid;
+
+/* Alg. 1 controls: omega (Eq. 6, the paper uses 2/3); e_it is checked when
+ * k mod n_it == 0 (k = 0, 1, ... counts passes); the loop stops when
+ * e_it <= tol or after max_iter passes. */
+typedef struct {
+    double omega, tol;
+    int32_t n_it, max_iter;
+} msrsb_basis_opts;
+
+typedef struct {
+    msrsb_basis_opts basis;
+    int32_t smoother;  /* msrsb_smoother: post-smoother for GMRES/Richardson;
+                          MSRSB_SMOOTH_GS = forward pre + backward post
+                          (symmetric, for PCG) */
+    int32_t pre, post; /* enable the pre / post stage of Alg. 4 */
+    int32_t krylov;    /* msrsb_krylov */
+    int32_t restart;   /* GMRES restart length (<= 512) */
+    int32_t prec;      /* msrsb_prec: F64 = all FP64; F32 = basis, P and smoother
+                          in FP32 with FP32 accumulation, Krylov vectors and
+                          the coarse operator in FP64 */
+} msrsb_opts;
+
+typedef struct msrsb_handle msrsb_handle;
+
+typedef struct {
+    int32_t n, bdim, nc, W;           /* fine rows, block size, coarse nodes, ELL width */
+    int32_t basis_iters;              /* passes of Alg. 1 performed */
+    double basis_e_it;                /* last e_it evaluated */
+    int32_t n_zero_diag;              /* rows with D_hat_ii = 0 (update skipped) */
+    int32_t ncolours;                 /* colour classes of the smoother */
+} msrsb_info;
+
+/* Sizes implied by a grid: fine points n, coarse nodes nc, ELL width W.
+ * Host only; no device work. */
+msrsb_status msrsb_partition_size(const msrsb_grid *g, int32_t *n_h, int32_t *nc_h, int32_t *W_h);
+
+/* a0. Primal partition, coarse nodes and support pattern (Sec. 2.1, Fig. 1).
+ * part[n]: primal block of each fine point; cnode[nc]: fine index of each
+ * coarse node (cell-centred: lower-middle cell of the block; vertex-centred:
+ * nodes 0, H, 2H, ...); p_ids[n][W]: coarse nodes whose support holds the
+ * point, in colour slots (support of J = open interval between J's
+ * neighbouring coarse nodes per axis, tensor product); skel[n] = 1 where the
+ * point lies on a coarse-node line of any axis. Integer results only. */
+msrsb_status msrsb_partition(const msrsb_grid *g, int32_t *part, int32_t *cnode, int32_t *p_ids,
+                             uint8_t *skel, cudaStream_t stream);
+
+/* a1 / a1'. M-matrix filter (Eq. 8 and Eq. 4; Alg. 1 first steps):
+ * A_hat_ij = min(A_ij, 0) off the diagonal, A_hat_ii = -sum_{j != i} A_hat_ij.
+ * bdim = 1: ahat_val[nnz] in A's pattern, comp must be 0.
+ * bdim = 3: separate-displacement-component block (Eq. 20, Remark 2) of
+ * component comp in {0,1,2} (the (comp, comp) entry of every block), filtered;
+ * ahat_val[nnz] in the block pattern.
+ * n_zero_diag_h (nullable) receives the number of rows whose filtered
+ * diagonal is 0 (Alg. 1 then leaves those rows unchanged). */
+msrsb_status msrsb_filter(const msrsb_mat *A, int32_t comp, double *ahat_val, int32_t *n_zero_diag_h,
+                          cudaStream_t stream);
+
+/* a2. Restricted smoothing of one scalar basis family (Eq. 6, Alg. 1).
+ * Ahat: filtered scalar operator (bdim 1). p_ids/skel as from
+ * msrsb_partition, W in {4, 8}. p_val[n][W] in precision prec: on entry the
+ * initial basis (e.g. the block indicator, or a previous P as warm start,
+ * Alg. 2), on return the smoothed, row-normalised P. Each pass forms
+ * dP = -omega D_hat^-1 A_hat P on P's pattern only, adds it, divides every
+ * row by its sum, and on check passes takes e_it = max |dP| over non-skeleton
+ * rows. iters_h, e_it_h (nullable): passes done and last e_it. */
+msrsb_status msrsb_build_basis(const msrsb_mat *Ahat, const int32_t *p_ids, const uint8_t *skel, int32_t W,
+                               const msrsb_basis_opts *opts, int32_t prec, void *p_val, int32_t *iters_h,
+                               double *e_it_h, cudaStream_t stream);
+
+/* a3. Galerkin coarse operator A_c = P^T A P (Eq. 3, Alg. 2) with the
+ * unfiltered A. For bdim = 3, P is block diagonal per component (Sec. 4):
+ * p_val holds 3 families [3][n][W]. Ac_dense[nC][nC], nC = nc * bdim,
+ * row-major, coarse dof = bdim*J + component. nC <= 8192. */
+msrsb_status msrsb_coarse_op(const msrsb_mat *A, const int32_t *p_ids, const void *p_val, int32_t prec, int32_t W,
+                             int32_t nc, double *Ac_dense, cudaStream_t stream);
+
+/* Alg. 2 set-up of the whole preconditioner: partition, filter, Alg. 1, A_c,
+ * the FP64 coarse solver M_c^-1 = A_c^-1 (Gauss-Jordan with partial pivoting)
+ * and the smoother (multicolour ILU(0), or multicolour block Gauss-Seidel).
+ * p_init (nullable, device, layout of p_val) is a warm-start basis; NULL
+ * starts from the block indicator. The handle keeps a non-owning reference
+ * to A's arrays, which must stay alive and unchanged until msrsb_destroy; it
+ * owns everything else it allocates (stream-ordered allocations on `stream`).
+ * *out receives the handle. */
+msrsb_status msrsb_setup(const msrsb_mat *A, const msrsb_grid *g, const msrsb_opts *opts, const void *p_init,
+                         msrsb_handle **out, cudaStream_t stream);
+
+/* Alg. 4 (with Alg. 3 inside) from z = 0: optional pre-smoothing, coarse
+ * correction with the residual, optional post-smoothing. v, z: FP64[n*bdim]. */
+msrsb_status msrsb_apply(msrsb_handle *h, const double *v, double *z, cudaStream_t stream);
+
+/* Krylov solve of A x = b preconditioned by Alg. 4: right-preconditioned
+ * GMRES (restarted) or PCG, until ||b - A x||_2 <= rtol ||b||_2 or maxit
+ * iterations. x: in initial guess, out solution (FP64). iters_h, relres_h
+ * receive the iteration count and the final true relative residual; hist_h
+ * (nullable, host, maxit+1 doubles) the relative residual estimate per
+ * iteration. Returns MSRSB_ENOCONV, with x holding the last iterate, when
+ * maxit is reached first. */
+msrsb_status msrsb_solve(msrsb_handle *h, const double *b, double *x, double rtol, int32_t maxit,
+                         int32_t *iters_h, double *relres_h, double *hist_h, cudaStream_t stream);
+
+/* Copies of the set-up results, for checks: p_ids[n][W], p_val[comp][n][W]
+ * (handle precision), Ac_dense[nC][nC]; any pointer may be NULL. */
+msrsb_status msrsb_get_setup(msrsb_handle *h, int32_t *p_ids, void *p_val, double *Ac_dense, cudaStream_t stream);
+msrsb_status msrsb_get_info(const msrsb_handle *h, msrsb_info *info_h);
+
+/* Releases everything the handle owns (after synchronising its stream). */
+msrsb_status msrsb_destroy(msrsb_handle *h);
+
+/* End-to-end call with HOST buffers: copies A and b to the device, runs
+ * msrsb_setup and msrsb_solve, copies x back, frees its device memory.
+ * A_h arrays and b_h, x_h are host pointers (pinned memory recommended). */
+msrsb_status msrsb_solve_host(const msrsb_mat *A_h, const msrsb_grid *g, const msrsb_opts *opts, const double *b_h,
+                              double *x_h, double rtol, int32_t maxit, int32_t *iters_h, double *relres_h,
+                              cudaStream_t stream);
+
+/* Measurement support (no counterpart in the paper). msrsb_profile(1)
+ * resets the counters and brackets every launch of the restricted-smoothing
+ * kernel (Alg. 1) with CUDA events on its stream; msrsb_profile(0) resets and
+ * stops the event timing. msrsb_profile_read returns the number of kernel
+ * launches the library made since the last reset (every kernel of csrc/, not
+ * counting CUB's sort/scan kernels), and the number and summed device time
+ * (ms) of smoothing launches that did work (launches that left at once after
+ * convergence are excluded). Host bookkeeping only. */
+msrsb_status msrsb_profile(int32_t enable);
+msrsb_status msrsb_profile_read(int64_t *launches_h, int64_t *smooth_launches_h, double *smooth_ms_h);
+
+/* Message for the last non-OK status returned on this host thread. */
+const char *msrsb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MSRSB_H */

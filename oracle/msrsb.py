@@ -128,6 +128,20 @@ def indicator(part, pat):
 # ----------------------------------------------------------------------------
 
 
+def row_sums_in_order(A):
+    """Row sums of a CSR matrix accumulated left to right in column order
+    (Eq. 4 fixes no order; this one is the reading both sides use)."""
+    A = sp.csr_matrix(A)
+    n = A.shape[0]
+    lens = np.diff(A.indptr)
+    if A.nnz == 0:
+        return np.zeros(n)
+    pos = np.arange(A.nnz) - np.repeat(A.indptr[:-1], lens)
+    M = np.zeros((n, int(lens.max())))
+    M[np.repeat(np.arange(n), lens), pos] = A.data
+    return np.cumsum(M, axis=1)[:, -1]  # trailing zeros leave the sum unchanged
+
+
 def mmatrix_filter(A):
     """Filtered operator of Alg. 1: A_hat = min(A, 0) entrywise, then
     A_hat <- A_hat - diag(rowsum(A_hat)), so every row sums to zero and the
@@ -136,7 +150,7 @@ def mmatrix_filter(A):
     A.sort_indices()
     Ah = A.copy()
     Ah.data = np.minimum(A.data, 0.0)
-    rowsum = np.asarray(Ah.sum(axis=1)).ravel()
+    rowsum = row_sums_in_order(Ah)
     rows = np.repeat(np.arange(A.shape[0]), np.diff(A.indptr))
     on_diag = A.indices == rows
     Ah.data[on_diag] -= rowsum[rows[on_diag]]
@@ -197,18 +211,35 @@ def enhanced_msrsb(Ahat, pat, P0, skel, omega=2.0 / 3.0, tol=1e-3, n_it=10, max_
     e_it = np.inf
     hist = []
     while e_it > tol and k < max_iter:
-        P = sp.csr_matrix((vals, pat.indices, pat.indptr), shape=(n, nc))
-        AP = Ahat @ P
-        dP = -omega * (sp.diags(inv) @ AP)
-        dPv = _on_pattern(dP, pat)
-        vals = vals + dPv
-        rs = np.bincount(rows, weights=vals, minlength=n)
-        vals = vals / rs[rows]
+        vals, dPv = smoothing_pass(Ahat, pat, vals, inv, omega, rows)
         if k % n_it == 0:
             e_it = float(np.max(np.abs(dPv[interior]))) if interior.any() else 0.0
             hist.append((k, e_it))
         k += 1
     return vals, k, e_it, hist
+
+
+def smoothing_pass(Ahat, pat, vals, inv, omega, rows=None):
+    """One pass of Alg. 1's loop body: dP = -omega D_hat^-1 A_hat P (Eq. 6)
+    kept on P's pattern, P + dP, rows divided by their sums. inv = 1/D_hat_ii
+    (0 where D_hat_ii = 0). Returns (new values, dP on the pattern)."""
+    n, nc = pat.shape
+    if rows is None:
+        rows = np.repeat(np.arange(n), np.diff(pat.indptr))
+    P = sp.csr_matrix((vals, pat.indices, pat.indptr), shape=(n, nc))
+    AP = Ahat @ P
+    dP = -omega * (sp.diags(inv) @ AP)
+    dPv = _on_pattern(dP, pat)
+    new = vals + dPv
+    rs = np.bincount(rows, weights=new, minlength=n)
+    return new / rs[rows], dPv
+
+
+def inverse_diagonal(Ahat):
+    d = sp.csr_matrix(Ahat).diagonal()
+    inv = np.zeros_like(d)
+    inv[d != 0.0] = 1.0 / d[d != 0.0]
+    return inv
 
 
 def as_matrix(vals, pat):

@@ -1,0 +1,8 @@
+"""GB300 (sm_103a) implementation of the enhanced MsRSB preconditioner
+(arXiv 1912.06934): C ABI in include/msrsb.h, CUDA kernels in csrc/, ctypes
+binding in msrsb.py. Importing the package does no device work."""
+from . import msrsb  # noqa: F401
+from .msrsb import (Mat, Handle, MsrsbError, grid, opts, basis_opts, load,  # noqa: F401
+                    msrsb_partition_size, msrsb_partition, msrsb_filter, msrsb_build_basis, msrsb_coarse_op,
+                    msrsb_setup, msrsb_apply, msrsb_solve, msrsb_get_setup, msrsb_get_info, msrsb_destroy,
+                    msrsb_solve_host, msrsb_profile, msrsb_profile_read)

@@ -1,0 +1,703 @@
+// Set-up (Alg. 2), two-stage apply (Alg. 3 and 4) and Krylov solves
+// (right-preconditioned GMRES, PCG, Richardson) of the enhanced MsRSB
+// preconditioner of arXiv 1912.06934, behind the C ABI of include/msrsb.h.
+#include "common.cuh"
+#include <atomic>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+
+namespace msrsb {
+
+// ---- errors --------------------------------------------------------------------
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+msrsb_status fail(msrsb_status s, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+msrsb_status cuda_fail(cudaError_t e, const char *what, const char *file, int line) {
+    set_error("CUDA error %s (%s) in %s at %s:%d", cudaGetErrorName(e), cudaGetErrorString(e), what, file, line);
+    return e == cudaErrorMemoryAllocation ? MSRSB_ENOMEM : MSRSB_ECUDA;
+}
+
+// ---- launch counting and smoothing-kernel timing ------------------------------
+static std::atomic<long long> g_launches{0};
+static std::atomic<bool> g_profiling{false};
+static std::atomic<long long> g_smooth_launches{0};
+static double g_smooth_ms = 0.0;
+static std::atomic<int> g_smooth_lock{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+bool profiling() { return g_profiling.load(std::memory_order_relaxed); }
+void add_smooth_time(int launches, double ms) {
+    while (g_smooth_lock.exchange(1)) {
+    }
+    g_smooth_launches += launches;
+    g_smooth_ms += ms;
+    g_smooth_lock.store(0);
+}
+
+// Keep freed stream-ordered memory cached in the device's default pool, so
+// repeated set-ups do not return memory to the driver at every synchronise.
+static void keep_pool_memory() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) return;
+    unsigned long long thr = ~0ULL;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    cudaGetLastError();
+}
+
+// ---- declarations from the other translation units ------------------------------------
+msrsb_status check_mat(const msrsb_mat *A);
+msrsb_status partition_launch(const msrsb_grid *g, int32_t *part, int32_t *cnode, int32_t *p_ids, uint8_t *skel,
+                              uint8_t *colour, cudaStream_t s);
+msrsb_status sell_structure(int n, const int32_t *rowptr, Sell *S, cudaStream_t s);
+template <typename T>
+msrsb_status sell_fill(const msrsb_mat *A, int comp, int raw, double omega, const int32_t *p_ids, int W, Sell *S,
+                       T *scale, uint8_t *vmask, int write_col, int *n_zero_d, cudaStream_t s);
+void sell_free(Sell *S, cudaStream_t s);
+template <typename T>
+msrsb_status indicator(int n, int W, const int32_t *part, const int32_t *p_ids, T *P, cudaStream_t s);
+template <typename T>
+msrsb_status basis_loop(int n, int W, const Sell &S, int comp, const T *scale, const uint8_t *vmask,
+                        const uint8_t *skel, T *P, const msrsb_basis_opts *o, int *iters_out, double *e_out,
+                        cudaStream_t s);
+msrsb_status build_transpose(int n, int W, int nc, const int32_t *p_ids, int32_t **pt_ptr, int32_t **pt_rows,
+                             int8_t **jslot, cudaStream_t s);
+template <typename T>
+msrsb_status galerkin(const msrsb_mat *A, int W, int nc, const int32_t *p_ids, const T *P, const int32_t *pt_ptr,
+                      const int32_t *pt_rows, const int8_t *jslot, double *Ac, cudaStream_t s);
+msrsb_status coarse_inverse(int n, const double *Ac, double *Ainv, cudaStream_t s);
+msrsb_status gemv(int n, const double *M, const double *x, double *y, cudaStream_t s);
+msrsb_status colour_classes(int n, const uint8_t *colour, int ncol, int32_t **rows, int32_t *ptr_h, cudaStream_t s);
+template <typename T>
+msrsb_status ilu0_factor(const msrsb_mat *A, const uint8_t *colour, int ncol, const int32_t *rows,
+                         const int32_t *cptr_h, int32_t *dpos, T *lu_out, cudaStream_t s);
+template <typename T>
+msrsb_status ilu0_apply(const msrsb_handle *h, const T *lu, const T *r, T *y, double *z, cudaStream_t s);
+template <typename T>
+msrsb_status block_diag_inverse(const msrsb_mat *A, T *dinv, cudaStream_t s);
+template <typename T, typename TA>
+msrsb_status gs_apply(const msrsb_handle *h, const TA *val, const T *dinv, int forward, const T *r, T *e, double *z,
+                      int assign, cudaStream_t s);
+template <typename T>
+msrsb_status convert(long n, const double *a, T *b, cudaStream_t s);
+template <typename TA, typename TX, typename TV, typename TY, typename TACC>
+msrsb_status spmv(const msrsb_mat &A, const TA *val, const TX *x, const TV *v, TY *y, bool resid, cudaStream_t s);
+template <typename TP, typename TV>
+msrsb_status restrict_op(const msrsb_handle *h, const TP *P, const TV *v, double *vc, cudaStream_t s);
+template <typename TP>
+msrsb_status prolong_op(const msrsb_handle *h, const TP *P, const double *wc, double *z, int add, cudaStream_t s);
+msrsb_status mdot(long N, int nvec, const double *V, long ldv, const double *w, double *partial, double *out,
+                  int accumulate, cudaStream_t s);
+msrsb_status norm2(long N, const double *w, double *partial, double *out, cudaStream_t s);
+msrsb_status mvsub(long N, int nvec, const double *V, long ldv, const double *h, double *w, cudaStream_t s);
+msrsb_status mvadd(long N, int nvec, const double *Z, long ldz, const double *y, double *x, cudaStream_t s);
+msrsb_status scale_by_inv(long N, const double *x, const double *den, double *y, cudaStream_t s);
+msrsb_status axpy_dev(long N, const double *num, const double *den, double sign, const double *x, double *y,
+                      cudaStream_t s);
+msrsb_status xpay_dev(long N, const double *num, const double *den, const double *z, double *p, cudaStream_t s);
+template <typename TO>
+msrsb_status copy_cast(long N, const double *x, TO *y, cudaStream_t s);
+double *pinned_scratch();
+
+constexpr int kRedBlocksHost = 304;
+
+// ---- set-up (Alg. 2) ---------------------------------------------------------------------
+
+template <typename T>
+static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s) {
+    const msrsb_mat &A = h->A;
+    const int n = h->n, W = h->W, bd = h->bdim;
+    const long nW = (long)n * W;
+    // a0: partition, support pattern, colours
+    MSRSB_TRY(dalloc(&h->part, n, s));
+    MSRSB_TRY(dalloc(&h->cnode, h->nc, s));
+    MSRSB_TRY(dalloc(&h->p_ids, nW, s));
+    MSRSB_TRY(dalloc(&h->skel, n, s));
+    MSRSB_TRY(dalloc(&h->colour, n, s));
+    MSRSB_TRY(partition_launch(&h->grid, h->part, h->cnode, h->p_ids, h->skel, h->colour, s));
+    // a1 + a2: filtered operator(s) streamed as sliced ELL, then Alg. 1 per component
+    T *P = nullptr;
+    MSRSB_TRY(dalloc(&P, nW * bd, s));
+    h->p_val = P;
+    Sell S;
+    T *scale = nullptr;
+    uint8_t *vmask = nullptr;
+    int *nzd = nullptr;
+    MSRSB_TRY(sell_structure(n, A.rowptr, &S, s));
+    MSRSB_TRY(dalloc(&scale, n, s));
+    MSRSB_TRY(dalloc(&vmask, n, s));
+    MSRSB_TRY(dalloc(&nzd, 1, s));
+    MSRSB_CUDA(cudaMemsetAsync(nzd, 0, sizeof(int), s));
+    h->basis_iters = 0;
+    for (int l = 0; l < bd; ++l) {
+        T *Pl = P + l * nW;
+        if (p_init)
+            MSRSB_CUDA(cudaMemcpyAsync(Pl, (const T *)p_init + l * nW, nW * sizeof(T), cudaMemcpyDeviceToDevice, s));
+        else
+            MSRSB_TRY(indicator<T>(n, W, h->part, h->p_ids, Pl, s));
+        MSRSB_TRY(sell_fill<T>(&A, l, 1, h->opts.basis.omega, h->p_ids, W, &S, scale, vmask, l == 0, nzd, s));
+        int it = 0;
+        double e = 0.0;
+        MSRSB_TRY(basis_loop<T>(n, W, S, l, scale, vmask, h->skel, Pl, &h->opts.basis, &it, &e, s));
+        if (it > h->basis_iters) h->basis_iters = it;
+        if (l == 0 || e > h->basis_e_it) h->basis_e_it = e;
+        dfree(S.val[l], s);
+    }
+    MSRSB_CUDA(cudaMemcpyAsync(&h->n_zero_diag, nzd, sizeof(int), cudaMemcpyDeviceToHost, s));
+    sell_free(&S, s);
+    dfree(scale, s);
+    dfree(vmask, s);
+    dfree(nzd, s);
+    // a3: Galerkin coarse operator with the unfiltered A, and its inverse
+    MSRSB_TRY(build_transpose(n, W, h->nc, h->p_ids, &h->pt_ptr, &h->pt_rows, &h->jslot, s));
+    MSRSB_TRY(dalloc(&h->Ac, (size_t)h->nC * h->nC, s));
+    MSRSB_TRY(dalloc(&h->Ainv, (size_t)h->nC * h->nC, s));
+    MSRSB_TRY(galerkin<T>(&A, W, h->nc, h->p_ids, P, h->pt_ptr, h->pt_rows, h->jslot, h->Ac, s));
+    MSRSB_TRY(coarse_inverse(h->nC, h->Ac, h->Ainv, s));
+    // smoother
+    h->ncolours = 1 << h->grid.dim;
+    h->colour_ptr_h = (int32_t *)calloc(h->ncolours + 1, sizeof(int32_t));
+    MSRSB_TRY(colour_classes(n, h->colour, h->ncolours, &h->colour_rows, h->colour_ptr_h, s));
+    const long N = (long)n * bd;
+    if (h->opts.prec == MSRSB_F32) {
+        float *alo = nullptr;
+        MSRSB_TRY(dalloc(&alo, (size_t)A.nnz * bd * bd, s));
+        MSRSB_TRY(convert<float>((long)A.nnz * bd * bd, A.val, alo, s));
+        h->a_lo = alo;
+    }
+    if (h->opts.smoother == MSRSB_SMOOTH_ILU0) {
+        if (bd != 1) return fail(MSRSB_EINVAL, "ILU(0) smoother needs a scalar operator; use MSRSB_SMOOTH_GS");
+        T *lu = nullptr;
+        MSRSB_TRY(dalloc(&lu, A.nnz, s));
+        MSRSB_TRY(dalloc(&h->diag_pos, n, s));
+        h->lu = lu;
+        MSRSB_TRY(ilu0_factor<T>(&A, h->colour, h->ncolours, h->colour_rows, h->colour_ptr_h, h->diag_pos, lu, s));
+    } else if (h->opts.smoother == MSRSB_SMOOTH_GS) {
+        if (bd != 3) return fail(MSRSB_EINVAL, "block Gauss-Seidel smoother needs a 3x3 block operator");
+        T *dinv = nullptr;
+        MSRSB_TRY(dalloc(&dinv, (size_t)n * 9, s));
+        h->dinv = dinv;
+        MSRSB_TRY(block_diag_inverse<T>(&A, dinv, s));
+    }
+    // apply workspaces
+    MSRSB_TRY(dalloc(&h->vc, h->nC, s));
+    MSRSB_TRY(dalloc(&h->wc, h->nC, s));
+    MSRSB_TRY(dalloc(&h->tmp_d, N, s));
+    T *r = nullptr, *y = nullptr;
+    MSRSB_TRY(dalloc(&r, N, s));
+    MSRSB_TRY(dalloc(&y, N, s));
+    h->r_t = r;
+    h->y_t = y;
+    MSRSB_TRY(dalloc(&h->partial, (size_t)kRedBlocksHost * 1024, s));
+    MSRSB_CUDA(cudaStreamSynchronize(s));
+    return MSRSB_OK;
+}
+
+// ---- apply (Alg. 4 with Alg. 3 inside), z = M^-1 v from z = 0 ---------------------
+
+template <typename T>
+static msrsb_status apply_t(msrsb_handle *h, const double *v, double *z, cudaStream_t s) {
+    const msrsb_mat &A = h->A;
+    const long N = (long)h->n * h->bdim;
+    const T *P = (const T *)h->p_val;
+    T *r = (T *)h->r_t, *y = (T *)h->y_t;
+    const T *aval_t = h->opts.prec == MSRSB_F32 ? (const T *)h->a_lo : (const T *)A.val;
+    const bool gs = h->opts.smoother == MSRSB_SMOOTH_GS, ilu = h->opts.smoother == MSRSB_SMOOTH_ILU0;
+    const bool pre = h->opts.pre && (gs || ilu), post = h->opts.post && (gs || ilu);
+    if (pre) {
+        // z = M_pre^-1 v
+        MSRSB_TRY(copy_cast<T>(N, v, r, s));
+        if (gs) {
+            MSRSB_TRY((gs_apply<T, T>(h, aval_t, (const T *)h->dinv, 1, r, y, z, 1, s)));
+        } else {
+            MSRSB_CUDA(cudaMemsetAsync(z, 0, N * sizeof(double), s));
+            MSRSB_TRY(ilu0_apply<T>(h, (const T *)h->lu, r, y, z, s));
+        }
+        // coarse correction of the residual v - A z
+        MSRSB_TRY((spmv<T, double, double, T, T>(A, aval_t, z, v, r, true, s)));
+        MSRSB_TRY((restrict_op<T, T>(h, P, r, h->vc, s)));
+    } else {
+        MSRSB_TRY((restrict_op<T, double>(h, P, v, h->vc, s)));
+    }
+    MSRSB_TRY(gemv(h->nC, h->Ainv, h->vc, h->wc, s));
+    MSRSB_TRY(prolong_op<T>(h, P, h->wc, z, pre ? 1 : 0, s));
+    if (post) {
+        MSRSB_TRY((spmv<T, double, double, T, T>(A, aval_t, z, v, r, true, s)));
+        if (gs)
+            MSRSB_TRY((gs_apply<T, T>(h, aval_t, (const T *)h->dinv, 0, r, y, z, 0, s)));
+        else
+            MSRSB_TRY(ilu0_apply<T>(h, (const T *)h->lu, r, y, z, s));
+    }
+    return MSRSB_OK;
+}
+
+static msrsb_status apply_any(msrsb_handle *h, const double *v, double *z, cudaStream_t s) {
+    if (h->opts.prec == MSRSB_F32) return apply_t<float>(h, v, z, s);
+    return apply_t<double>(h, v, z, s);
+}
+
+static msrsb_status fine_spmv(const msrsb_handle *h, const double *x, const double *v, double *y, bool resid,
+                              cudaStream_t s) {
+    return spmv<double, double, double, double, double>(h->A, h->A.val, x, v, y, resid, s);
+}
+
+static msrsb_status read_scalar(const double *d, double *out, cudaStream_t s) {
+    double *pin = pinned_scratch();
+    if (pin) {
+        MSRSB_CUDA(cudaMemcpyAsync(pin + 8, d, sizeof(double), cudaMemcpyDeviceToHost, s));
+        MSRSB_CUDA(cudaStreamSynchronize(s));
+        *out = ((volatile double *)pin)[8];
+    } else {
+        MSRSB_CUDA(cudaMemcpyAsync(out, d, sizeof(double), cudaMemcpyDeviceToHost, s));
+        MSRSB_CUDA(cudaStreamSynchronize(s));
+    }
+    return MSRSB_OK;
+}
+
+__global__ void vadd_kernel(int n, const double *__restrict__ a, double *__restrict__ b) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] += a[i];
+}
+msrsb_status vadd(int n, const double *a, double *b, cudaStream_t s) {
+    vadd_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, a, b);
+    MSRSB_LAUNCHED("vadd_kernel");
+    return MSRSB_OK;
+}
+
+// Krylov state on the device, m = restart length:
+// H[(m+1) x m] column-major | cs[m] | sn[m] | g[m+1] | est | beta | h2[m+1]
+struct KhLayout {
+    long H, cs, sn, g, est, beta, h2, total;
+    explicit KhLayout(int m) {
+        H = 0;
+        cs = (long)(m + 1) * m;
+        sn = cs + m;
+        g = sn + m;
+        est = g + m + 1;
+        beta = est + 1;
+        h2 = beta + 1;
+        total = h2 + m + 1 + 8;
+    }
+};
+
+// ---- GMRES (right preconditioned, flexible: Z_j = M^-1 V_j kept) ------------------------
+
+// Hessenberg column j (H[., j] in hcol) -> apply previous Givens rotations,
+// form the new one, update g; est = |g[j+1]|. State layout in kh:
+// H[(m+1) x m] column-major | cs[m] | sn[m] | g[m+1] | est
+__global__ void givens_kernel(int m, int j, double *__restrict__ kh) {
+    double *H = kh, *cs = kh + (long)(m + 1) * m, *sn = cs + m, *g = sn + m, *est = g + m + 1;
+    double *col = H + (long)j * (m + 1);
+    for (int i = 0; i < j; ++i) {
+        double t = cs[i] * col[i] + sn[i] * col[i + 1];
+        col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+        col[i] = t;
+    }
+    double a = col[j], b = col[j + 1];
+    double den = hypot(a, b);
+    double c = den != 0.0 ? a / den : 1.0, sgn = den != 0.0 ? b / den : 0.0;
+    cs[j] = c;
+    sn[j] = sgn;
+    col[j] = den;
+    col[j + 1] = 0.0;
+    g[j + 1] = -sgn * g[j];
+    g[j] = c * g[j];
+    *est = fabs(g[j + 1]);
+}
+
+// back substitution H(0:k,0:k) y = g(0:k); y written over g
+__global__ void hess_solve_kernel(int m, int k, double *__restrict__ kh) {
+    double *H = kh, *g = kh + (long)(m + 1) * m + 2 * m;
+    for (int i = k - 1; i >= 0; --i) {
+        double s = g[i];
+        for (int c = i + 1; c < k; ++c) s -= H[(long)c * (m + 1) + i] * g[c];
+        g[i] = s / H[(long)i * (m + 1) + i];
+    }
+}
+
+__global__ void gmres_init_kernel(int m, double *__restrict__ kh, const double *__restrict__ beta) {
+    double *g = kh + (long)(m + 1) * m + 2 * m;
+    for (int i = 0; i <= m; ++i) g[i] = 0.0;
+    g[0] = *beta;
+}
+
+static msrsb_status gmres(msrsb_handle *h, const double *b, double *x, double rtol, int maxit, int *iters,
+                          double *relres, double *hist, cudaStream_t s) {
+    const long N = (long)h->n * h->bdim;
+    const int m = h->krylov_m;
+    double *V = h->kv, *Z = h->kz, *kh = h->kh;
+    const KhLayout L(m);
+    double *H = kh + L.H, *est = kh + L.est, *beta = kh + L.beta, *h2 = kh + L.h2;
+    double bnorm = 0.0;
+    MSRSB_TRY(norm2(N, b, h->partial, beta, s));
+    MSRSB_TRY(read_scalar(beta, &bnorm, s));
+    int its = 0;
+    if (hist) hist[0] = 1.0;
+    if (bnorm == 0.0) {
+        MSRSB_CUDA(cudaMemsetAsync(x, 0, N * sizeof(double), s));
+        *iters = 0;
+        *relres = 0.0;
+        return MSRSB_OK;
+    }
+    for (;;) {
+        // r = b - A x, beta = |r|, V_0 = r / beta
+        MSRSB_TRY(fine_spmv(h, x, b, h->tmp_d, true, s));
+        MSRSB_TRY(norm2(N, h->tmp_d, h->partial, beta, s));
+        double bt = 0.0;
+        MSRSB_TRY(read_scalar(beta, &bt, s));
+        if (!std::isfinite(bt)) return fail(MSRSB_ENAN, "non-finite residual in GMRES");
+        *relres = bt / bnorm;
+        if (bt <= rtol * bnorm) break;
+        if (its >= maxit) {
+            *iters = its;
+            return fail(MSRSB_ENOCONV, "GMRES reached %d iterations (relres %.3e)", its, bt / bnorm);
+        }
+        MSRSB_TRY(scale_by_inv(N, h->tmp_d, beta, V, s));
+        gmres_init_kernel<<<1, 1, 0, s>>>(m, kh, beta);
+        MSRSB_LAUNCHED("gmres_init_kernel");
+        int mm = m < maxit - its ? m : maxit - its;
+        int k = 0;
+        for (int j = 0; j < mm; ++j) {
+            double *Vj = V + j * N, *Zj = Z + j * N, *w = V + (j + 1) * N;
+            MSRSB_TRY(apply_any(h, Vj, Zj, s));
+            MSRSB_TRY(fine_spmv(h, Zj, nullptr, w, false, s));
+            double *hcol = H + (long)j * (m + 1);
+            // classical Gram-Schmidt, twice
+            MSRSB_TRY(mdot(N, j + 1, V, N, w, h->partial, hcol, 0, s));
+            MSRSB_TRY(mvsub(N, j + 1, V, N, hcol, w, s));
+            MSRSB_TRY(mdot(N, j + 1, V, N, w, h->partial, h2, 0, s));
+            MSRSB_TRY(mvsub(N, j + 1, V, N, h2, w, s));
+            // hcol += second pass
+            MSRSB_TRY(vadd(j + 1, h2, hcol, s));
+            MSRSB_TRY(norm2(N, w, h->partial, hcol + j + 1, s));
+            MSRSB_TRY(scale_by_inv(N, w, hcol + j + 1, w, s));
+            givens_kernel<<<1, 1, 0, s>>>(m, j, kh);
+            MSRSB_LAUNCHED("givens_kernel");
+            ++its;
+            k = j + 1;
+            double e = 0.0;
+            MSRSB_TRY(read_scalar(est, &e, s));
+            if (hist) hist[its] = e / bnorm;
+            if (!std::isfinite(e)) return fail(MSRSB_ENAN, "non-finite residual estimate in GMRES");
+            if (e <= rtol * bnorm) break;
+        }
+        hess_solve_kernel<<<1, 1, 0, s>>>(m, k, kh);
+        MSRSB_LAUNCHED("hess_solve_kernel");
+        MSRSB_TRY(mvadd(N, k, Z, N, kh + L.g, x, s));
+    }
+    *iters = its;
+    return MSRSB_OK;
+}
+
+// ---- PCG ------------------------------------------------------------------------
+
+static msrsb_status pcg(msrsb_handle *h, const double *b, double *x, double rtol, int maxit, int *iters,
+                        double *relres, double *hist, cudaStream_t s) {
+    const long N = (long)h->n * h->bdim;
+    double *r = h->kv, *zv = h->kv + N, *p = h->kv + 2 * N, *q = h->kv + 3 * N;
+    double *sc = h->kh;  // [0] |b| [1] rz [2] rz_new [3] pq [4] |r|
+    double bnorm = 0.0;
+    MSRSB_TRY(norm2(N, b, h->partial, sc + 0, s));
+    MSRSB_TRY(read_scalar(sc + 0, &bnorm, s));
+    if (hist) hist[0] = 1.0;
+    if (bnorm == 0.0) {
+        MSRSB_CUDA(cudaMemsetAsync(x, 0, N * sizeof(double), s));
+        *iters = 0;
+        *relres = 0.0;
+        return MSRSB_OK;
+    }
+    MSRSB_TRY(fine_spmv(h, x, b, r, true, s));
+    MSRSB_TRY(apply_any(h, r, zv, s));
+    MSRSB_CUDA(cudaMemcpyAsync(p, zv, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    MSRSB_TRY(mdot(N, 1, r, N, zv, h->partial, sc + 1, 0, s));
+    int its = 0;
+    for (;;) {
+        MSRSB_TRY(fine_spmv(h, p, nullptr, q, false, s));
+        MSRSB_TRY(mdot(N, 1, p, N, q, h->partial, sc + 3, 0, s));
+        MSRSB_TRY(axpy_dev(N, sc + 1, sc + 3, 1.0, p, x, s));
+        MSRSB_TRY(axpy_dev(N, sc + 1, sc + 3, -1.0, q, r, s));
+        ++its;
+        MSRSB_TRY(norm2(N, r, h->partial, sc + 4, s));
+        double rn = 0.0;
+        MSRSB_TRY(read_scalar(sc + 4, &rn, s));
+        if (hist) hist[its] = rn / bnorm;
+        if (!std::isfinite(rn)) return fail(MSRSB_ENAN, "non-finite residual in PCG");
+        if (rn <= rtol * bnorm) {
+            MSRSB_TRY(fine_spmv(h, x, b, h->tmp_d, true, s));
+            MSRSB_TRY(norm2(N, h->tmp_d, h->partial, sc + 4, s));
+            double rt = 0.0;
+            MSRSB_TRY(read_scalar(sc + 4, &rt, s));
+            *relres = rt / bnorm;
+            if (rt <= rtol * bnorm) break;
+            MSRSB_CUDA(cudaMemcpyAsync(r, h->tmp_d, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        }
+        if (its >= maxit) {
+            *iters = its;
+            *relres = rn / bnorm;
+            return fail(MSRSB_ENOCONV, "PCG reached %d iterations (relres %.3e)", its, rn / bnorm);
+        }
+        MSRSB_TRY(apply_any(h, r, zv, s));
+        MSRSB_TRY(mdot(N, 1, r, N, zv, h->partial, sc + 2, 0, s));
+        MSRSB_TRY(xpay_dev(N, sc + 2, sc + 1, zv, p, s));
+        MSRSB_CUDA(cudaMemcpyAsync(sc + 1, sc + 2, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    *iters = its;
+    return MSRSB_OK;
+}
+
+// ---- Richardson: x += M^-1 (b - A x) ------------------------------------------------
+
+static msrsb_status richardson(msrsb_handle *h, const double *b, double *x, double rtol, int maxit, int *iters,
+                               double *relres, double *hist, cudaStream_t s) {
+    const long N = (long)h->n * h->bdim;
+    double *r = h->kv, *zv = h->kv + N, *sc = h->kh;
+    double bnorm = 0.0;
+    MSRSB_TRY(norm2(N, b, h->partial, sc, s));
+    MSRSB_TRY(read_scalar(sc, &bnorm, s));
+    if (hist) hist[0] = 1.0;
+    int its = 0;
+    for (;;) {
+        MSRSB_TRY(fine_spmv(h, x, b, r, true, s));
+        MSRSB_TRY(norm2(N, r, h->partial, sc + 1, s));
+        double rn = 0.0;
+        MSRSB_TRY(read_scalar(sc + 1, &rn, s));
+        *relres = bnorm > 0 ? rn / bnorm : 0.0;
+        if (its > 0 && hist) hist[its] = *relres;
+        if (!std::isfinite(rn)) return fail(MSRSB_ENAN, "non-finite residual in Richardson");
+        if (rn <= rtol * bnorm) break;
+        if (its >= maxit) {
+            *iters = its;
+            return fail(MSRSB_ENOCONV, "Richardson reached %d iterations (relres %.3e)", its, *relres);
+        }
+        MSRSB_TRY(apply_any(h, r, zv, s));
+        MSRSB_TRY(vadd((int)N, zv, x, s));
+        ++its;
+    }
+    *iters = its;
+    return MSRSB_OK;
+}
+
+
+static void handle_free(msrsb_handle *h) {
+    cudaStream_t s = h->stream;
+    dfree(h->part, s);
+    dfree(h->cnode, s);
+    dfree(h->p_ids, s);
+    dfree(h->skel, s);
+    dfree(h->colour, s);
+    dfree(h->colour_rows, s);
+    dfree(h->p_val, s);
+    dfree(h->pt_ptr, s);
+    dfree(h->pt_rows, s);
+    dfree(h->jslot, s);
+    dfree(h->Ac, s);
+    dfree(h->Ainv, s);
+    dfree(h->lu, s);
+    dfree(h->diag_pos, s);
+    dfree(h->dinv, s);
+    dfree(h->a_lo, s);
+    dfree(h->vc, s);
+    dfree(h->wc, s);
+    dfree(h->tmp_d, s);
+    dfree(h->r_t, s);
+    dfree(h->y_t, s);
+    dfree(h->kv, s);
+    dfree(h->kz, s);
+    dfree(h->kh, s);
+    dfree(h->partial, s);
+    if (h->own_A) {
+        dfree(*(int32_t **)&h->A.rowptr, s);
+        dfree(*(int32_t **)&h->A.colidx, s);
+        dfree(*(double **)&h->A.val, s);
+    }
+    free(h->colour_ptr_h);
+    cudaStreamSynchronize(s);
+    delete h;
+}
+
+}  // namespace msrsb
+
+using namespace msrsb;
+
+extern "C" const char *msrsb_last_error(void) { return msrsb::g_err; }
+
+extern "C" msrsb_status msrsb_profile(int32_t enable) {
+    msrsb::g_profiling.store(enable != 0);
+    msrsb::g_launches.store(0);
+    while (msrsb::g_smooth_lock.exchange(1)) {
+    }
+    msrsb::g_smooth_launches = 0;
+    msrsb::g_smooth_ms = 0.0;
+    msrsb::g_smooth_lock.store(0);
+    return MSRSB_OK;
+}
+
+extern "C" msrsb_status msrsb_profile_read(int64_t *launches_h, int64_t *smooth_launches_h, double *smooth_ms_h) {
+    if (launches_h) *launches_h = msrsb::g_launches.load();
+    while (msrsb::g_smooth_lock.exchange(1)) {
+    }
+    if (smooth_launches_h) *smooth_launches_h = msrsb::g_smooth_launches;
+    if (smooth_ms_h) *smooth_ms_h = msrsb::g_smooth_ms;
+    msrsb::g_smooth_lock.store(0);
+    return MSRSB_OK;
+}
+
+extern "C" msrsb_status msrsb_setup(const msrsb_mat *A, const msrsb_grid *g, const msrsb_opts *opts, const void *p_init,
+                                    msrsb_handle **out, cudaStream_t stream) {
+    if (!out) return fail(MSRSB_EINVAL, "out is NULL");
+    *out = nullptr;
+    MSRSB_TRY(check_mat(A));
+    if (!g || !opts) return fail(MSRSB_EINVAL, "grid or opts is NULL");
+    int32_t n = 0, nc = 0, W = 0;
+    MSRSB_TRY(msrsb_partition_size(g, &n, &nc, &W));
+    if (n != A->nrows) return fail(MSRSB_ESHAPE, "grid has %d points but A has %d block rows", n, A->nrows);
+    if (g->ncomp != A->bdim) return fail(MSRSB_ESHAPE, "grid ncomp %d != bdim %d", g->ncomp, A->bdim);
+    if ((long)nc * A->bdim > 8192) return fail(MSRSB_ESHAPE, "coarse system too large (nc*bdim = %ld > 8192)", (long)nc * A->bdim);
+    if (opts->prec != MSRSB_F64 && opts->prec != MSRSB_F32) return fail(MSRSB_EINVAL, "bad precision");
+    if (opts->basis.n_it < 1 || opts->basis.max_iter < 0) return fail(MSRSB_EINVAL, "bad basis options");
+    keep_pool_memory();
+    msrsb_handle *h = new msrsb_handle();
+    h->A = *A;
+    h->grid = *g;
+    h->opts = *opts;
+    h->n = n;
+    h->bdim = A->bdim;
+    h->nc = nc;
+    h->W = W;
+    h->nC = nc * A->bdim;
+    h->ncomp = g->ncomp;
+    h->stream = stream;
+    int m = opts->restart > 0 ? opts->restart : 200;
+    if (m > 512) m = 512;
+    h->krylov_m = m;
+    msrsb_status st = opts->prec == MSRSB_F32 ? setup_t<float>(h, p_init, stream) : setup_t<double>(h, p_init, stream);
+    if (st == MSRSB_OK) {
+        const long N = (long)n * A->bdim;
+        st = dalloc(&h->kv, (size_t)(m + 1 > 4 ? m + 1 : 4) * N, stream);
+        if (st == MSRSB_OK) st = dalloc(&h->kz, (size_t)m * N, stream);
+        if (st == MSRSB_OK) st = dalloc(&h->kh, (size_t)KhLayout(m).total, stream);
+    }
+    if (st != MSRSB_OK) {
+        std::string msg = msrsb_last_error();
+        handle_free(h);
+        set_error("%s", msg.c_str());
+        return st;
+    }
+    *out = h;
+    return MSRSB_OK;
+}
+
+extern "C" msrsb_status msrsb_apply(msrsb_handle *h, const double *v, double *z, cudaStream_t stream) {
+    if (!h || !v || !z) return fail(MSRSB_EINVAL, "NULL argument");
+    return apply_any(h, v, z, stream);
+}
+
+extern "C" msrsb_status msrsb_solve(msrsb_handle *h, const double *b, double *x, double rtol, int32_t maxit,
+                                    int32_t *iters_h, double *relres_h, double *hist_h, cudaStream_t stream) {
+    if (!h || !b || !x) return fail(MSRSB_EINVAL, "NULL argument");
+    if (!(rtol >= 0.0) || maxit < 0) return fail(MSRSB_EINVAL, "bad rtol or maxit");
+    int its = 0;
+    double rr = 0.0;
+    msrsb_status st;
+    switch (h->opts.krylov) {
+        case MSRSB_GMRES: st = gmres(h, b, x, rtol, maxit, &its, &rr, hist_h, stream); break;
+        case MSRSB_PCG: st = pcg(h, b, x, rtol, maxit, &its, &rr, hist_h, stream); break;
+        case MSRSB_RICHARDSON: st = richardson(h, b, x, rtol, maxit, &its, &rr, hist_h, stream); break;
+        default: return fail(MSRSB_EINVAL, "unknown Krylov method %d", h->opts.krylov);
+    }
+    if (iters_h) *iters_h = its;
+    if (relres_h) *relres_h = rr;
+    if (st == MSRSB_OK) MSRSB_CUDA(cudaStreamSynchronize(stream));
+    return st;
+}
+
+extern "C" msrsb_status msrsb_get_setup(msrsb_handle *h, int32_t *p_ids, void *p_val, double *Ac_dense,
+                                        cudaStream_t stream) {
+    if (!h) return fail(MSRSB_EINVAL, "handle is NULL");
+    long nW = (long)h->n * h->W;
+    size_t es = h->opts.prec == MSRSB_F32 ? sizeof(float) : sizeof(double);
+    if (p_ids) MSRSB_CUDA(cudaMemcpyAsync(p_ids, h->p_ids, nW * sizeof(int32_t), cudaMemcpyDeviceToDevice, stream));
+    if (p_val) MSRSB_CUDA(cudaMemcpyAsync(p_val, h->p_val, nW * h->bdim * es, cudaMemcpyDeviceToDevice, stream));
+    if (Ac_dense)
+        MSRSB_CUDA(cudaMemcpyAsync(Ac_dense, h->Ac, (size_t)h->nC * h->nC * sizeof(double), cudaMemcpyDeviceToDevice,
+                                   stream));
+    return MSRSB_OK;
+}
+
+extern "C" msrsb_status msrsb_get_info(const msrsb_handle *h, msrsb_info *info) {
+    if (!h || !info) return fail(MSRSB_EINVAL, "NULL argument");
+    info->n = h->n;
+    info->bdim = h->bdim;
+    info->nc = h->nc;
+    info->W = h->W;
+    info->basis_iters = h->basis_iters;
+    info->basis_e_it = h->basis_e_it;
+    info->n_zero_diag = h->n_zero_diag;
+    info->ncolours = h->ncolours;
+    return MSRSB_OK;
+}
+
+extern "C" msrsb_status msrsb_destroy(msrsb_handle *h) {
+    if (!h) return MSRSB_OK;
+    handle_free(h);
+    return MSRSB_OK;
+}
+
+extern "C" msrsb_status msrsb_solve_host(const msrsb_mat *A_h, const msrsb_grid *g, const msrsb_opts *opts,
+                                         const double *b_h, double *x_h, double rtol, int32_t maxit, int32_t *iters_h,
+                                         double *relres_h, cudaStream_t stream) {
+    if (!A_h || !b_h || !x_h) return fail(MSRSB_EINVAL, "NULL argument");
+    if (A_h->bdim != 1 && A_h->bdim != 3) return fail(MSRSB_EINVAL, "bdim must be 1 or 3");
+    const int bd = A_h->bdim, n = A_h->nrows, nnz = A_h->nnz;
+    const long N = (long)n * bd;
+    int32_t *rp = nullptr, *ci = nullptr;
+    double *va = nullptr, *b = nullptr, *x = nullptr;
+    MSRSB_TRY(dalloc(&rp, n + 1, stream));
+    MSRSB_TRY(dalloc(&ci, nnz, stream));
+    MSRSB_TRY(dalloc(&va, (size_t)nnz * bd * bd, stream));
+    MSRSB_TRY(dalloc(&b, N, stream));
+    MSRSB_TRY(dalloc(&x, N, stream));
+    MSRSB_CUDA(cudaMemcpyAsync(rp, A_h->rowptr, (n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, stream));
+    MSRSB_CUDA(cudaMemcpyAsync(ci, A_h->colidx, nnz * sizeof(int32_t), cudaMemcpyHostToDevice, stream));
+    MSRSB_CUDA(cudaMemcpyAsync(va, A_h->val, (size_t)nnz * bd * bd * sizeof(double), cudaMemcpyHostToDevice, stream));
+    MSRSB_CUDA(cudaMemcpyAsync(b, b_h, N * sizeof(double), cudaMemcpyHostToDevice, stream));
+    MSRSB_CUDA(cudaMemsetAsync(x, 0, N * sizeof(double), stream));
+    msrsb_mat Ad{n, nnz, bd, rp, ci, va};
+    msrsb_handle *h = nullptr;
+    msrsb_status st = msrsb_setup(&Ad, g, opts, nullptr, &h, stream);
+    if (st == MSRSB_OK) {
+        h->own_A = 1;
+        st = msrsb_solve(h, b, x, rtol, maxit, iters_h, relres_h, nullptr, stream);
+        if (st == MSRSB_OK || st == MSRSB_ENOCONV) {
+            cudaError_t e = cudaMemcpyAsync(x_h, x, N * sizeof(double), cudaMemcpyDeviceToHost, stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+            if (e != cudaSuccess) st = cuda_fail(e, "copy of x to the host", __FILE__, __LINE__);
+        }
+        std::string msg = msrsb_last_error();
+        msrsb_destroy(h);
+        set_error("%s", msg.c_str());
+    } else {
+        dfree(rp, stream);
+        dfree(ci, stream);
+        dfree(va, stream);
+    }
+    dfree(b, stream);
+    dfree(x, stream);
+    cudaStreamSynchronize(stream);
+    return st;
+}

@@ -1,0 +1,291 @@
+// a2: restricted smoothing of the MsRSB basis (Eq. 6 and Alg. 1 of
+// arXiv 1912.06934), the hottest kernel of the set-up.
+//
+// One thread per fine row i streams row i of the filtered operator from the
+// sliced-ELL copy (coalesced across the warp) and, for every neighbour k,
+// the W values of P's row k (one or two 16-byte vector loads). Because P's
+// pattern is stored in colour slots (coarse node J always sits in slot
+// colour(J)), P_kJ for J = ids_i[s] can only be in slot s of row k; the 8-bit
+// mask packed beside column k says which slots match. The epilogue is fused:
+// dP = -(omega / D_hat_ii) * (A_hat P)_i* on the pattern, P + dP divided by
+// its row sum, and max |dP| over non-skeleton rows into a device scalar.
+#include "common.cuh"
+
+namespace msrsb {
+
+template <typename T, int W>
+struct PRow {
+    T v[W];
+};
+
+template <typename T, int W>
+__device__ __forceinline__ void load_row(const T *__restrict__ P, long k, T (&out)[W]) {
+    static_assert((W * sizeof(T)) % 16 == 0, "row must be a multiple of 16 bytes");
+    const uint4 *src = reinterpret_cast<const uint4 *>(P + k * W);
+    uint4 *dst = reinterpret_cast<uint4 *>(out);
+#pragma unroll
+    for (int q = 0; q < (int)(W * sizeof(T) / 16); ++q) dst[q] = __ldg(src + q);
+}
+
+template <typename T, int W>
+__device__ __forceinline__ void store_row(T *__restrict__ P, long k, const T (&in)[W]) {
+    uint4 *dst = reinterpret_cast<uint4 *>(P + k * W);
+    const uint4 *src = reinterpret_cast<const uint4 *>(in);
+#pragma unroll
+    for (int q = 0; q < (int)(W * sizeof(T) / 16); ++q) dst[q] = src[q];
+}
+
+template <typename T, int W>
+__global__ void __launch_bounds__(256) smooth_kernel(int n, const int32_t *__restrict__ slice_ptr,
+                                                     const int32_t *__restrict__ scol, const T *__restrict__ sval,
+                                                     const T *__restrict__ scale, const uint8_t *__restrict__ vmask,
+                                                     const uint8_t *__restrict__ skel, const T *__restrict__ Pin,
+                                                     T *__restrict__ Pout, unsigned long long *__restrict__ emax,
+                                                     int check, const int *__restrict__ done, int *__restrict__ iters,
+                                                     int k_pass) {
+    if (*done) return;  // an earlier check met the tolerance: uniform exit
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) *iters = k_pass + 1;
+    double e_loc = 0.0;
+    if (i < n) {
+        int s = i >> 5, lane = i & 31;
+        int beg = slice_ptr[s];
+        int width = (slice_ptr[s + 1] - beg) >> 5;
+        T acc[W];
+#pragma unroll
+        for (int c = 0; c < W; ++c) acc[c] = T(0);
+        const int32_t *cp = scol + beg + lane;
+        const T *vp = sval + beg + lane;
+        for (int j = 0; j < width; ++j) {
+            unsigned pc = (unsigned)__ldg(cp + (j << 5));
+            T a = __ldg(vp + (j << 5));
+            unsigned m = pc >> kColShift;
+            if (m) {
+                T pk[W];
+                load_row<T, W>(Pin, (long)(pc & kColMask), pk);
+#pragma unroll
+                for (int c = 0; c < W; ++c)
+                    if (m & (1u << c)) acc[c] = fma(a, pk[c], acc[c]);
+            }
+        }
+        T own[W];
+        load_row<T, W>(Pin, i, own);
+        unsigned vm = vmask[i];
+        T sc = scale[i];
+        T t[W];
+        T sum = T(0), emx = T(0);
+#pragma unroll
+        for (int c = 0; c < W; ++c) {
+            if (vm & (1u << c)) {
+                T d = -sc * acc[c];
+                t[c] = own[c] + d;
+                sum += t[c];
+                emx = fmax(emx, fabs(d));
+            } else {
+                t[c] = T(0);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < W; ++c) t[c] = (vm & (1u << c)) ? t[c] / sum : T(0);
+        store_row<T, W>(Pout, i, t);
+        if (check && !skel[i]) e_loc = (double)emx;
+    }
+    if (check) {
+        e_loc = warp_max(e_loc);
+        if ((threadIdx.x & 31) == 0 && e_loc > 0.0) atomicMax(emax, dbits(e_loc));
+    }
+}
+
+__global__ void basis_check_kernel(const unsigned long long *__restrict__ emax_k, double tol, int *__restrict__ done,
+                                   double *__restrict__ e_last) {
+    if (*done) return;
+    double e = __longlong_as_double((long long)*emax_k);
+    *e_last = e;
+    if (e <= tol) *done = 1;
+}
+
+// Block indicator of the primal partition (initial basis, Sec. 2.1).
+template <typename T>
+__global__ void indicator_kernel(int n, int W, const int32_t *__restrict__ part, const int32_t *__restrict__ p_ids,
+                                 T *__restrict__ P) {
+    long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t >= (long)n * W) return;
+    long i = t / W;
+    P[t] = p_ids[t] >= 0 && p_ids[t] == part[i] ? T(1) : T(0);
+}
+
+template <typename T>
+msrsb_status indicator(int n, int W, const int32_t *part, const int32_t *p_ids, T *P, cudaStream_t s) {
+    indicator_kernel<T><<<ceil_div((long)n * W, 256), 256, 0, s>>>(n, W, part, p_ids, P);
+    MSRSB_LAUNCHED("indicator_kernel");
+    return MSRSB_OK;
+}
+template msrsb_status indicator<double>(int, int, const int32_t *, const int32_t *, double *, cudaStream_t);
+template msrsb_status indicator<float>(int, int, const int32_t *, const int32_t *, float *, cudaStream_t);
+
+// Small pinned scratch for host reads of device scalars (per host thread).
+double *pinned_scratch() {
+    static thread_local double *p = nullptr;
+    if (!p) {
+        if (cudaHostAlloc((void **)&p, 4096, cudaHostAllocPortable) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+    }
+    return p;
+}
+
+template <typename T, int W>
+static void launch_smooth(int n, const Sell &S, int comp, const T *scale, const uint8_t *vmask, const uint8_t *skel,
+                          const T *Pin, T *Pout, unsigned long long *emax, int check, const int *done, int *iters,
+                          int k, cudaStream_t s) {
+    int grid = ceil_div((long)S.nslices * kSell, 256);
+    smooth_kernel<T, W><<<grid, 256, 0, s>>>(n, S.slice_ptr, S.col, (const T *)S.val[comp], scale, vmask, skel, Pin,
+                                             Pout, emax, check, done, iters, k);
+}
+
+// Alg. 1 loop on one basis family. P (device, [n][W]) holds the initial
+// basis on entry and the result on return.
+template <typename T>
+msrsb_status basis_loop(int n, int W, const Sell &S, int comp, const T *scale, const uint8_t *vmask,
+                        const uint8_t *skel, T *P, const msrsb_basis_opts *o, int *iters_out, double *e_out,
+                        cudaStream_t s) {
+    if (W != 4 && W != 8) return fail(MSRSB_EINVAL, "W must be 4 or 8 (got %d)", W);
+    if (o->max_iter < 0 || o->n_it < 1) return fail(MSRSB_EINVAL, "need max_iter >= 0 and n_it >= 1");
+    int maxit = o->max_iter;
+    T *P2 = nullptr;
+    unsigned long long *emax = nullptr;
+    int *flags = nullptr;  // [0] done, [1] iters
+    double *e_last = nullptr;
+    MSRSB_TRY(dalloc(&P2, (size_t)n * W, s));
+    MSRSB_TRY(dalloc(&emax, maxit + 1, s));
+    MSRSB_TRY(dalloc(&flags, 2, s));
+    MSRSB_TRY(dalloc(&e_last, 1, s));
+    MSRSB_CUDA(cudaMemsetAsync(emax, 0, (maxit + 1) * sizeof(unsigned long long), s));
+    MSRSB_CUDA(cudaMemsetAsync(flags, 0, 2 * sizeof(int), s));
+    double inf = __builtin_inf();
+    MSRSB_CUDA(cudaMemcpyAsync(e_last, &inf, sizeof(double), cudaMemcpyHostToDevice, s));
+    double *pin = pinned_scratch();
+    if (pin) ((volatile int *)pin)[0] = 0;
+    cudaEvent_t ev = nullptr;
+    MSRSB_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    bool pending = false;
+    T *buf[2] = {P, P2};
+    // optional per-launch timing of the smoothing kernel (CUDA events on s)
+    const bool prof = profiling();
+    cudaEvent_t *tev = nullptr;
+    int launched = 0;
+    if (prof && maxit > 0) {
+        tev = new cudaEvent_t[2 * maxit];
+        for (int q = 0; q < 2 * maxit; ++q) MSRSB_CUDA(cudaEventCreate(&tev[q]));
+    }
+    for (int k = 0; k < maxit; ++k) {
+        int check = (k % o->n_it) == 0;
+        if (check && pending && pin && cudaEventQuery(ev) == cudaSuccess) {
+            if (((volatile int *)pin)[0] != 0) break;  // converged at an earlier check
+            pending = false;
+        }
+        if (prof) MSRSB_CUDA(cudaEventRecord(tev[2 * k], s));
+        if (W == 4)
+            launch_smooth<T, 4>(n, S, comp, scale, vmask, skel, buf[k & 1], buf[(k + 1) & 1], emax + k, check, flags,
+                                flags + 1, k, s);
+        else
+            launch_smooth<T, 8>(n, S, comp, scale, vmask, skel, buf[k & 1], buf[(k + 1) & 1], emax + k, check, flags,
+                                flags + 1, k, s);
+        MSRSB_LAUNCHED("smooth_kernel");
+        if (prof) MSRSB_CUDA(cudaEventRecord(tev[2 * k + 1], s));
+        launched = k + 1;
+        if (check) {
+            basis_check_kernel<<<1, 1, 0, s>>>(emax + k, o->tol, flags, e_last);
+            MSRSB_LAUNCHED("basis_check_kernel");
+            if (pin && !pending) {
+                // copy the done flag (as a double) for a lagged, non-blocking look
+                MSRSB_CUDA(cudaMemcpyAsync(pin, flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+                MSRSB_CUDA(cudaEventRecord(ev, s));
+                pending = true;
+            }
+        }
+    }
+    int h_flags[2] = {0, 0};
+    double h_e = 0.0;
+    MSRSB_CUDA(cudaMemcpyAsync(h_flags, flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    MSRSB_CUDA(cudaMemcpyAsync(&h_e, e_last, sizeof(double), cudaMemcpyDeviceToHost, s));
+    MSRSB_CUDA(cudaStreamSynchronize(s));
+    cudaEventDestroy(ev);
+    int iters = h_flags[1];
+    if (prof) {
+        // only the first `iters` launches did work; later ones left at once
+        double ms = 0.0;
+        for (int q = 0; q < iters && q < launched; ++q) {
+            float t = 0.f;
+            MSRSB_CUDA(cudaEventElapsedTime(&t, tev[2 * q], tev[2 * q + 1]));
+            ms += t;
+        }
+        add_smooth_time(iters < launched ? iters : launched, ms);
+        for (int q = 0; q < 2 * maxit; ++q) cudaEventDestroy(tev[q]);
+        delete[] tev;
+    }
+    if (iters & 1) MSRSB_CUDA(cudaMemcpyAsync(P, P2, (size_t)n * W * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    if (iters_out) *iters_out = iters;
+    if (e_out) *e_out = h_e;
+    dfree(P2, s);
+    dfree(emax, s);
+    dfree(flags, s);
+    dfree(e_last, s);
+    return MSRSB_OK;
+}
+template msrsb_status basis_loop<double>(int, int, const Sell &, int, const double *, const uint8_t *, const uint8_t *,
+                                         double *, const msrsb_basis_opts *, int *, double *, cudaStream_t);
+template msrsb_status basis_loop<float>(int, int, const Sell &, int, const float *, const uint8_t *, const uint8_t *,
+                                        float *, const msrsb_basis_opts *, int *, double *, cudaStream_t);
+
+msrsb_status check_mat(const msrsb_mat *A);
+msrsb_status sell_structure(int n, const int32_t *rowptr, Sell *S, cudaStream_t s);
+template <typename T>
+msrsb_status sell_fill(const msrsb_mat *A, int comp, int raw, double omega, const int32_t *p_ids, int W, Sell *S,
+                       T *scale, uint8_t *vmask, int write_col, int *n_zero_d, cudaStream_t s);
+void sell_free(Sell *S, cudaStream_t s);
+
+template <typename T>
+static msrsb_status build_basis_t(const msrsb_mat *Ahat, const int32_t *p_ids, const uint8_t *skel, int W,
+                                  const msrsb_basis_opts *o, T *P, int *iters, double *e, cudaStream_t s) {
+    int n = Ahat->nrows;
+    Sell S;
+    T *scale = nullptr;
+    uint8_t *vmask = nullptr;
+    MSRSB_TRY(sell_structure(n, Ahat->rowptr, &S, s));
+    MSRSB_TRY(dalloc(&scale, n, s));
+    MSRSB_TRY(dalloc(&vmask, n, s));
+    MSRSB_TRY(sell_fill<T>(Ahat, 0, 0, o->omega, p_ids, W, &S, scale, vmask, 1, nullptr, s));
+    msrsb_status st = basis_loop<T>(n, W, S, 0, scale, vmask, skel, P, o, iters, e, s);
+    sell_free(&S, s);
+    dfree(scale, s);
+    dfree(vmask, s);
+    return st;
+}
+
+}  // namespace msrsb
+
+using namespace msrsb;
+
+extern "C" msrsb_status msrsb_build_basis(const msrsb_mat *Ahat, const int32_t *p_ids, const uint8_t *skel, int32_t W,
+                                          const msrsb_basis_opts *opts, int32_t prec, void *p_val, int32_t *iters_h,
+                                          double *e_it_h, cudaStream_t stream) {
+    MSRSB_TRY(check_mat(Ahat));
+    if (Ahat->bdim != 1) return fail(MSRSB_EINVAL, "build_basis takes a scalar filtered operator (bdim 1)");
+    if (!p_ids || !skel || !p_val || !opts) return fail(MSRSB_EINVAL, "NULL argument");
+    int it = 0;
+    double e = 0.0;
+    msrsb_status st;
+    if (prec == MSRSB_F64)
+        st = build_basis_t<double>(Ahat, p_ids, skel, W, opts, (double *)p_val, &it, &e, stream);
+    else if (prec == MSRSB_F32)
+        st = build_basis_t<float>(Ahat, p_ids, skel, W, opts, (float *)p_val, &it, &e, stream);
+    else
+        return fail(MSRSB_EINVAL, "prec must be MSRSB_F64 or MSRSB_F32");
+    if (st != MSRSB_OK) return st;
+    MSRSB_CUDA(cudaStreamSynchronize(stream));
+    if (iters_h) *iters_h = it;
+    if (e_it_h) *e_it_h = e;
+    return MSRSB_OK;
+}

@@ -1,0 +1,144 @@
+// Shared internals of the MsRSB library: status/error plumbing, small device
+// helpers and the internal handle layout. Not part of the public ABI.
+#pragma once
+#include <cstdint>
+#include <cstdio>
+#include <cstdarg>
+#include <cuda_runtime.h>
+#include "../../include/msrsb.h"
+
+namespace msrsb {
+
+// thread-local message for msrsb_last_error()
+void set_error(const char *fmt, ...);
+msrsb_status fail(msrsb_status s, const char *fmt, ...);
+
+// Map a CUDA error to a status, recording where it happened.
+msrsb_status cuda_fail(cudaError_t e, const char *what, const char *file, int line);
+
+#define MSRSB_CUDA(call)                                                                 \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) return ::msrsb::cuda_fail(e_, #call, __FILE__, __LINE__); \
+    } while (0)
+
+// Every kernel launch of the library is followed by MSRSB_LAUNCHED, which
+// counts it (msrsb_profile_read) and turns a launch error into a status.
+void count_launch();
+#define MSRSB_LAUNCHED(name)                 \
+    do {                                     \
+        ::msrsb::count_launch();             \
+        MSRSB_CUDA(cudaGetLastError());      \
+    } while (0)
+
+#define MSRSB_TRY(expr)                       \
+    do {                                      \
+        msrsb_status s_ = (expr);             \
+        if (s_ != MSRSB_OK) return s_;        \
+    } while (0)
+
+// profiling of the restricted-smoothing kernel (see msrsb_profile)
+bool profiling();
+void add_smooth_time(int launches, double ms);
+
+constexpr int kMaxW = 8;          // 2^3 coarse slots per fine row
+constexpr int kColShift = 24;     // packed column: col | mask << 24
+constexpr int32_t kColMask = (1 << kColShift) - 1;
+constexpr int kSell = 32;         // SELL slice height (one warp)
+
+inline int ceil_div(long a, long b) { return (int)((a + b - 1) / b); }
+
+template <typename T> struct Vec;  // nothing generic
+
+// Stream-ordered allocation helper
+template <typename T>
+msrsb_status dalloc(T **p, size_t count, cudaStream_t s) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMallocAsync((void **)p, count * sizeof(T), s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MSRSB_ENOMEM, "device allocation of %zu bytes failed: %s", count * sizeof(T),
+                    cudaGetErrorString(e));
+    }
+    return MSRSB_OK;
+}
+template <typename T>
+void dfree(T *&p, cudaStream_t s) {
+    if (p) cudaFreeAsync((void *)p, s);
+    p = nullptr;
+}
+
+// Sliced-ELL (slice height 32) copy of a scalar operator, one value array
+// per component sharing one packed column array.
+struct Sell {
+    int n = 0, nslices = 0;
+    long entries = 0;
+    int32_t *slice_ptr = nullptr;  // [nslices+1] offsets (entries)
+    int32_t *col = nullptr;        // [entries] packed col | mask << 24 (mask unused outside the basis)
+    void *val[3] = {nullptr, nullptr, nullptr};
+};
+
+// ---- device helpers -------------------------------------------------------
+__device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+}  // namespace msrsb
+
+// ---- internal handle ---------------------------------------------------------
+struct msrsb_handle {
+    // problem
+    msrsb_mat A{};
+    msrsb_grid grid{};
+    msrsb_opts opts{};
+    int n = 0, bdim = 1, nc = 0, W = 4, nC = 0, ncomp = 1;
+    cudaStream_t stream = nullptr;
+    // partition
+    int32_t *part = nullptr, *cnode = nullptr, *p_ids = nullptr;
+    uint8_t *skel = nullptr;
+    uint8_t *colour = nullptr;  // fine-point colour (parity), for the smoother
+    int ncolours = 0;
+    int32_t *colour_ptr_h = nullptr;  // host copy [ncolours+1]
+    int32_t *colour_rows = nullptr;   // device [n]: fine points grouped by colour
+    // prolongation: values [ncomp][n][W] in handle precision
+    void *p_val = nullptr;
+    // CSC of P's pattern: rows of every coarse node's support, ascending
+    int32_t *pt_ptr = nullptr, *pt_rows = nullptr;
+    int8_t *jslot = nullptr;  // slot of coarse node J in every row of its support
+    // coarse operator and its inverse (FP64, dense nC x nC)
+    double *Ac = nullptr, *Ainv = nullptr;
+    // smoother factors in A's (block) pattern, handle precision
+    void *lu = nullptr;       // ILU(0): L below, U on/above the diagonal (colour order)
+    int32_t *diag_pos = nullptr;
+    void *dinv = nullptr;     // block GS: inverse 3x3 diagonal blocks [n][9]
+    void *a_lo = nullptr;     // FP32 copy of A's values (mixed precision inner residual)
+    // workspaces
+    double *vc = nullptr, *wc = nullptr, *tmp_d = nullptr;
+    void *r_t = nullptr, *y_t = nullptr;
+    // Krylov workspace
+    double *kv = nullptr, *kz = nullptr;   // GMRES V [(m+1)][N], Z [m][N]; PCG uses first columns
+    double *kh = nullptr;                  // device Hessenberg/Givens state
+    double *partial = nullptr;             // reduction partials
+    double *host_scalars = nullptr;        // pinned
+    int krylov_m = 0;
+    // info
+    int basis_iters = 0;
+    double basis_e_it = 0.0;
+    int n_zero_diag = 0;
+    int own_A = 0;  // set by msrsb_solve_host when it owns A's device copy
+};

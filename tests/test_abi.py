@@ -1,0 +1,47 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry point
+that include/msrsb.h declares (no device work)."""
+import ctypes
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "msrsb.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(msrsb_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_abi():
+    names = _declared()
+    for want in ("msrsb_filter", "msrsb_build_basis", "msrsb_coarse_op", "msrsb_setup", "msrsb_apply",
+                 "msrsb_solve", "msrsb_destroy", "msrsb_partition"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1912_06934_gb300 import msrsb as B
+    lib = ctypes.CDLL(B.lib_path())
+    for name in _declared():
+        assert hasattr(lib, name), name
+    assert set(B.EXPORTS) == set(_declared())
+
+
+def test_partition_size_host_only():
+    # msrsb_partition_size does no device work, so it runs without a GPU
+    from paper_1912_06934_gb300 import msrsb as B
+    assert B.msrsb_partition_size(B.grid((64, 64, 64), (8, 8, 8))) == (262144, 512, 8)
+    assert B.msrsb_partition_size(B.grid((49, 49, 49), (6, 6, 6), centering=1, ncomp=3)) == (117649, 729, 8)
+    assert B.msrsb_partition_size(B.grid((64, 64), (8, 8))) == (4096, 64, 4)
+
+
+def test_product_path_has_no_oracle_import():
+    pkg = os.path.join(ROOT, "paper_1912_06934_gb300")
+    for dp, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dp, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f
