@@ -141,6 +141,26 @@ msrsb_status msrsb_build_basis(const msrsb_mat *Ahat, const int32_t *p_ids, cons
                                const msrsb_basis_opts *opts, int32_t prec, void *p_val, int32_t *iters_h,
                                double *e_it_h, cudaStream_t stream);
 
+/* Allocation-free variant of msrsb_build_basis (no counterpart in the
+ * paper). For callers that cannot allocate device memory: code running under
+ * an external memory manager that already owns the GPU's memory (a serving
+ * framework's caching allocator, a memory-capped container), or host loops
+ * that must not take the allocator's locks and implicit synchronisation.
+ * Same arguments and results as msrsb_build_basis (the filtered operator is
+ * read in CSR form directly); the scratch it needs lives in one static device
+ * array of 10 MiB + 33,024 bytes that every GPU loading the library holds
+ * until the process exits. Limits: n * W <= 1,048,576, n <= 262,144 and
+ * max_iter <= 4096; larger inputs return MSRSB_ESHAPE and do nothing.
+ * The first call on a device resolves the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture. All calls on a device share the array and each call resets the
+ * parts that must start at zero: calls that overlap on the GPU (different
+ * streams or host threads at the same time) race and give wrong results.
+ * Calls no cudaMalloc, cudaFree or allocating library routine. */
+msrsb_status msrsb_build_basis_noalloc(const msrsb_mat *Ahat, const int32_t *p_ids, const uint8_t *skel,
+                                       int32_t W, const msrsb_basis_opts *opts, int32_t prec, void *p_val,
+                                       int32_t *iters_h, double *e_it_h, cudaStream_t stream);
+
 /* a3. Galerkin coarse operator A_c = P^T A P (Eq. 3, Alg. 2) with the
  * unfiltered A. For bdim = 3, P is block diagonal per component (Sec. 4):
  * p_val holds 3 families [3][n][W]. Ac_dense[nC][nC], nC = nc * bdim,

@@ -21,7 +21,8 @@ MSRSB_GMRES, MSRSB_PCG, MSRSB_RICHARDSON = 0, 1, 2
 
 EXPORTS = ["msrsb_partition_size", "msrsb_partition", "msrsb_filter", "msrsb_build_basis", "msrsb_coarse_op",
            "msrsb_setup", "msrsb_apply", "msrsb_solve", "msrsb_get_setup", "msrsb_get_info", "msrsb_destroy",
-           "msrsb_solve_host", "msrsb_profile", "msrsb_profile_read", "msrsb_last_error"]
+           "msrsb_solve_host", "msrsb_profile", "msrsb_profile_read", "msrsb_build_basis_noalloc",
+           "msrsb_last_error"]
 
 
 class MsrsbError(RuntimeError):
@@ -166,6 +167,18 @@ def msrsb_build_basis(Ahat, p_ids, skel, W, bopts, prec, p_val, stream=None):
     _check(load().msrsb_build_basis(ctypes.byref(m), _ptr(p_ids), _ptr(skel), ctypes.c_int32(W), ctypes.byref(bopts),
                                     ctypes.c_int32(prec), _ptr(p_val), ctypes.byref(it), ctypes.byref(e),
                                     _stream(stream)))
+    return it.value, e.value
+
+
+def msrsb_build_basis_noalloc(Ahat, p_ids, skel, W, bopts, prec, p_val, stream=None):
+    """Allocation-free variant of msrsb_build_basis (static device scratch;
+    see include/msrsb.h for its limits). Returns (iters, e_it)."""
+    assert p_val.dtype == _pdtype(prec) and p_val.is_contiguous()
+    it, e = ctypes.c_int32(), ctypes.c_double()
+    m = Ahat.c()
+    _check(load().msrsb_build_basis_noalloc(ctypes.byref(m), _ptr(p_ids), _ptr(skel), ctypes.c_int32(W),
+                                            ctypes.byref(bopts), ctypes.c_int32(prec), _ptr(p_val), ctypes.byref(it),
+                                            ctypes.byref(e), _stream(stream)))
     return it.value, e.value
 
 
