@@ -33,6 +33,7 @@ WORKLOAD = "3D Darcy 64^3 MPFA-O 27-point, ln k GRF (l=8, sigma=3), 10:1 aniso r
 N_GRID, H_BLOCK, SEED = 64, 8, 1002
 RTOL, MAXIT = 1e-8, 300
 BASIS = dict(tol=1e-3, n_it=10, max_iter=100)
+PHASES = ("partition", "filter_basis", "galerkin", "coarse_inverse", "smoother", "workspace")
 
 
 def make_problem():
@@ -129,10 +130,17 @@ def gpu_arm(args, rank, world):
 
     def step(prec):
         o = M.opts(prec=prec, **BASIS)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
         h = M.msrsb_setup(A, g, o)
+        e[1].record(stream)
         r = h.solve(b, rtol=RTOL, maxit=MAXIT)
+        e[2].record(stream)
         info = h.info()
         h.destroy()
+        torch.cuda.synchronize()
+        info["setup_ms"] = e[0].elapsed_time(e[1])
+        info["solve_ms"] = e[1].elapsed_time(e[2])
         return r, info
 
     def timed(prec, k):
@@ -211,9 +219,11 @@ def gpu_arm(args, rank, world):
                    "basis": "omega=2/3 tol=1e-3 n_it=10 max_iter=100", "krylov": "GMRES(200) right, ILU(0) post",
                    "rtol": RTOL, "l2": "flushed between steps (512 MB write)", "parallelism": "replicas"},
         "mixed": {"ms_per_step": t32 / args.steps, "basis_iters": inf32["basis_iters"], "krylov_iters": r32["iters"],
-                  "relres": r32["relres"]},
+                  "relres": r32["relres"], "setup_ms": inf32["setup_ms"], "solve_ms": inf32["solve_ms"],
+                  "setup_phase_ms": dict(zip(PHASES, inf32["phase_ms"]))},
         "fp64": {"ms_per_step": t64 / args.steps, "basis_iters": inf64["basis_iters"], "krylov_iters": r64["iters"],
-                 "relres": r64["relres"], "smooth_kernel_gbs": achieved64,
+                 "relres": r64["relres"], "setup_ms": inf64["setup_ms"], "solve_ms": inf64["solve_ms"],
+                 "setup_phase_ms": dict(zip(PHASES, inf64["phase_ms"])), "smooth_kernel_gbs": achieved64,
                  "smooth_kernel_us": sm_ms64 / sm_l64 * 1e3 if sm_l64 else None},
         "speedup_mixed_vs_fp64": t64 / t32,
         "roofline": {"kernel": "smooth_kernel<float,8> (restricted smoothing, Alg. 1)", "bound": "hbm",

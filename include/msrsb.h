@@ -102,6 +102,9 @@ typedef struct {
     double basis_e_it;                /* last e_it evaluated */
     int32_t n_zero_diag;              /* rows with D_hat_ii = 0 (update skipped) */
     int32_t ncolours;                 /* colour classes of the smoother */
+    double phase_ms[6];               /* set-up phases, device time (only while msrsb_profile(1) is on,
+                                         else 0): partition, filter + basis, Galerkin, coarse inverse,
+                                         smoother factor, workspace */
 } msrsb_info;
 
 /* Sizes implied by a grid: fine points n, coarse nodes nc, ELL width W.
@@ -162,11 +165,13 @@ msrsb_status msrsb_build_basis_noalloc(const msrsb_mat *Ahat, const int32_t *p_i
                                        int32_t *iters_h, double *e_it_h, cudaStream_t stream);
 
 /* a3. Galerkin coarse operator A_c = P^T A P (Eq. 3, Alg. 2) with the
- * unfiltered A. For bdim = 3, P is block diagonal per component (Sec. 4):
- * p_val holds 3 families [3][n][W]. Ac_dense[nC][nC], nC = nc * bdim,
- * row-major, coarse dof = bdim*J + component. nC <= 8192. */
-msrsb_status msrsb_coarse_op(const msrsb_mat *A, const int32_t *p_ids, const void *p_val, int32_t prec, int32_t W,
-                             int32_t nc, double *Ac_dense, cudaStream_t stream);
+ * unfiltered A. g is the grid P was built on (msrsb_partition); p_ids[n][W]
+ * in colour slots. For bdim = 3, P is block diagonal per component (Sec. 4):
+ * p_val holds 3 families [3][n][W]. Ac_dense[nC][nC], nC = nc * bdim <= 8192,
+ * row-major, coarse dof = bdim*J + component; entries outside the coarse
+ * 3^dim stencil are written as 0. Deterministic (fixed summation order). */
+msrsb_status msrsb_coarse_op(const msrsb_mat *A, const msrsb_grid *g, const int32_t *p_ids, const void *p_val,
+                             int32_t prec, double *Ac_dense, cudaStream_t stream);
 
 /* Alg. 2 set-up of the whole preconditioner: partition, filter, Alg. 1, A_c,
  * the FP64 coarse solver M_c^-1 = A_c^-1 (Gauss-Jordan with partial pivoting)

@@ -65,6 +65,10 @@ msrsb_status check_mat(const msrsb_mat *A);
 msrsb_status partition_launch(const msrsb_grid *g, int32_t *part, int32_t *cnode, int32_t *p_ids, uint8_t *skel,
                               uint8_t *colour, cudaStream_t s);
 msrsb_status sell_structure(int n, const int32_t *rowptr, Sell *S, cudaStream_t s);
+msrsb_status sell_copy(const msrsb_mat *A, bool with_f32, Sell *S, cudaStream_t s);
+template <typename TA, typename TX, typename TV, typename TY, typename TACC>
+msrsb_status sell_spmv(const Sell &S, const TA *val, const TX *x, const TV *v, TY *y, bool resid, cudaStream_t s,
+                       const int32_t *operm = nullptr);
 template <typename T>
 msrsb_status sell_fill(const msrsb_mat *A, int comp, int raw, double omega, const int32_t *p_ids, int W, Sell *S,
                        T *scale, uint8_t *vmask, int write_col, int *n_zero_d, cudaStream_t s);
@@ -78,16 +82,20 @@ msrsb_status basis_loop(int n, int W, const Sell &S, int comp, const T *scale, c
 msrsb_status build_transpose(int n, int W, int nc, const int32_t *p_ids, int32_t **pt_ptr, int32_t **pt_rows,
                              int8_t **jslot, cudaStream_t s);
 template <typename T>
-msrsb_status galerkin(const msrsb_mat *A, int W, int nc, const int32_t *p_ids, const T *P, const int32_t *pt_ptr,
-                      const int32_t *pt_rows, const int8_t *jslot, double *Ac, cudaStream_t s);
+msrsb_status galerkin(const msrsb_mat *A, const msrsb_grid *g, int W, int nc, const int32_t *p_ids, const T *P,
+                      const int32_t *pt_ptr, const int32_t *pt_rows, const int8_t *jslot, double *Ac,
+                      cudaStream_t s);
 msrsb_status coarse_inverse(int n, const double *Ac, double *Ainv, cudaStream_t s);
 msrsb_status gemv(int n, const double *M, const double *x, double *y, cudaStream_t s);
 msrsb_status colour_classes(int n, const uint8_t *colour, int ncol, int32_t **rows, int32_t *ptr_h, cudaStream_t s);
-template <typename T>
 msrsb_status ilu0_factor(const msrsb_mat *A, const uint8_t *colour, int ncol, const int32_t *rows,
-                         const int32_t *cptr_h, int32_t *dpos, T *lu_out, cudaStream_t s);
+                         const int32_t *cptr_h, int32_t *dpos, double *lu, cudaStream_t s);
 template <typename T>
-msrsb_status ilu0_apply(const msrsb_handle *h, const T *lu, const T *r, T *y, double *z, cudaStream_t s);
+msrsb_status ilu_build_ell(msrsb_handle *h, const double *lu, cudaStream_t s);
+template <typename T>
+msrsb_status ilu0_apply(const msrsb_handle *h, const T *rp, T *y, double *z, cudaStream_t s);
+template <typename TO>
+msrsb_status permute_cast(long N, const double *x, const int32_t *perm, TO *y, cudaStream_t s);
 template <typename T>
 msrsb_status block_diag_inverse(const msrsb_mat *A, T *dinv, cudaStream_t s);
 template <typename T, typename TA>
@@ -96,13 +104,16 @@ msrsb_status gs_apply(const msrsb_handle *h, const TA *val, const T *dinv, int f
 template <typename T>
 msrsb_status convert(long n, const double *a, T *b, cudaStream_t s);
 template <typename TA, typename TX, typename TV, typename TY, typename TACC>
-msrsb_status spmv(const msrsb_mat &A, const TA *val, const TX *x, const TV *v, TY *y, bool resid, cudaStream_t s);
+msrsb_status spmv(const msrsb_mat &A, const TA *val, const TX *x, const TV *v, TY *y, bool resid, cudaStream_t s,
+                  const int32_t *operm = nullptr);
 template <typename TP, typename TV>
 msrsb_status restrict_op(const msrsb_handle *h, const TP *P, const TV *v, double *vc, cudaStream_t s);
 template <typename TP>
 msrsb_status prolong_op(const msrsb_handle *h, const TP *P, const double *wc, double *z, int add, cudaStream_t s);
 msrsb_status mdot(long N, int nvec, const double *V, long ldv, const double *w, double *partial, double *out,
-                  int accumulate, cudaStream_t s);
+                  int accumulate, cudaStream_t s, const int *gate = nullptr);
+msrsb_status gs_update(long N, int nv, const double *V, long ldv, const double *hs, double *w, double *hcol, int *flag,
+                       int pass, cudaStream_t s);
 msrsb_status norm2(long N, const double *w, double *partial, double *out, cudaStream_t s);
 msrsb_status mvsub(long N, int nvec, const double *V, long ldv, const double *h, double *w, cudaStream_t s);
 msrsb_status mvadd(long N, int nvec, const double *Z, long ldz, const double *y, double *x, cudaStream_t s);
@@ -113,6 +124,7 @@ msrsb_status xpay_dev(long N, const double *num, const double *den, const double
 template <typename TO>
 msrsb_status copy_cast(long N, const double *x, TO *y, cudaStream_t s);
 double *pinned_scratch();
+constexpr int kPinnedDoubles = 8192;  // size of the pinned scratch, in doubles
 
 constexpr int kRedBlocksHost = 304;
 
@@ -123,6 +135,16 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
     const msrsb_mat &A = h->A;
     const int n = h->n, W = h->W, bd = h->bdim;
     const long nW = (long)n * W;
+    // optional phase timing (profiling mode): events at the phase boundaries
+    const bool prof = profiling();
+    cudaEvent_t ev[7] = {};
+    if (prof)
+        for (int q = 0; q < 7; ++q) MSRSB_CUDA(cudaEventCreate(&ev[q]));
+    auto mark = [&](int q) -> msrsb_status {
+        if (prof) MSRSB_CUDA(cudaEventRecord(ev[q], s));
+        return MSRSB_OK;
+    };
+    MSRSB_TRY(mark(0));
     // a0: partition, support pattern, colours
     MSRSB_TRY(dalloc(&h->part, n, s));
     MSRSB_TRY(dalloc(&h->cnode, h->nc, s));
@@ -130,6 +152,7 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
     MSRSB_TRY(dalloc(&h->skel, n, s));
     MSRSB_TRY(dalloc(&h->colour, n, s));
     MSRSB_TRY(partition_launch(&h->grid, h->part, h->cnode, h->p_ids, h->skel, h->colour, s));
+    MSRSB_TRY(mark(1));
     // a1 + a2: filtered operator(s) streamed as sliced ELL, then Alg. 1 per component
     T *P = nullptr;
     MSRSB_TRY(dalloc(&P, nW * bd, s));
@@ -163,18 +186,22 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
     dfree(scale, s);
     dfree(vmask, s);
     dfree(nzd, s);
+    MSRSB_TRY(mark(2));
     // a3: Galerkin coarse operator with the unfiltered A, and its inverse
     MSRSB_TRY(build_transpose(n, W, h->nc, h->p_ids, &h->pt_ptr, &h->pt_rows, &h->jslot, s));
     MSRSB_TRY(dalloc(&h->Ac, (size_t)h->nC * h->nC, s));
     MSRSB_TRY(dalloc(&h->Ainv, (size_t)h->nC * h->nC, s));
-    MSRSB_TRY(galerkin<T>(&A, W, h->nc, h->p_ids, P, h->pt_ptr, h->pt_rows, h->jslot, h->Ac, s));
+    MSRSB_TRY(galerkin<T>(&A, &h->grid, W, h->nc, h->p_ids, P, h->pt_ptr, h->pt_rows, h->jslot, h->Ac, s));
+    MSRSB_TRY(mark(3));
     MSRSB_TRY(coarse_inverse(h->nC, h->Ac, h->Ainv, s));
+    MSRSB_TRY(mark(4));
     // smoother
     h->ncolours = 1 << h->grid.dim;
     h->colour_ptr_h = (int32_t *)calloc(h->ncolours + 1, sizeof(int32_t));
     MSRSB_TRY(colour_classes(n, h->colour, h->ncolours, &h->colour_rows, h->colour_ptr_h, s));
     const long N = (long)n * bd;
-    if (h->opts.prec == MSRSB_F32) {
+    if (bd == 1) MSRSB_TRY(sell_copy(&A, h->opts.prec == MSRSB_F32, &h->asell, s));
+    if (h->opts.prec == MSRSB_F32 && bd != 1) {
         float *alo = nullptr;
         MSRSB_TRY(dalloc(&alo, (size_t)A.nnz * bd * bd, s));
         MSRSB_TRY(convert<float>((long)A.nnz * bd * bd, A.val, alo, s));
@@ -182,11 +209,13 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
     }
     if (h->opts.smoother == MSRSB_SMOOTH_ILU0) {
         if (bd != 1) return fail(MSRSB_EINVAL, "ILU(0) smoother needs a scalar operator; use MSRSB_SMOOTH_GS");
-        T *lu = nullptr;
+        double *lu = nullptr;
         MSRSB_TRY(dalloc(&lu, A.nnz, s));
         MSRSB_TRY(dalloc(&h->diag_pos, n, s));
-        h->lu = lu;
-        MSRSB_TRY(ilu0_factor<T>(&A, h->colour, h->ncolours, h->colour_rows, h->colour_ptr_h, h->diag_pos, lu, s));
+        MSRSB_CUDA(cudaMemcpyAsync(lu, A.val, (size_t)A.nnz * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        MSRSB_TRY(ilu0_factor(&A, h->colour, h->ncolours, h->colour_rows, h->colour_ptr_h, h->diag_pos, lu, s));
+        MSRSB_TRY(ilu_build_ell<T>(h, lu, s));
+        dfree(lu, s);
     } else if (h->opts.smoother == MSRSB_SMOOTH_GS) {
         if (bd != 3) return fail(MSRSB_EINVAL, "block Gauss-Seidel smoother needs a 3x3 block operator");
         T *dinv = nullptr;
@@ -194,6 +223,7 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
         h->dinv = dinv;
         MSRSB_TRY(block_diag_inverse<T>(&A, dinv, s));
     }
+    MSRSB_TRY(mark(5));
     // apply workspaces
     MSRSB_TRY(dalloc(&h->vc, h->nC, s));
     MSRSB_TRY(dalloc(&h->wc, h->nC, s));
@@ -204,11 +234,33 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
     h->r_t = r;
     h->y_t = y;
     MSRSB_TRY(dalloc(&h->partial, (size_t)kRedBlocksHost * 1024, s));
+    MSRSB_TRY(mark(6));
     MSRSB_CUDA(cudaStreamSynchronize(s));
+    if (prof) {
+        for (int q = 0; q < 6; ++q) {
+            float t = 0.f;
+            MSRSB_CUDA(cudaEventElapsedTime(&t, ev[q], ev[q + 1]));
+            h->phase_ms[q] = t;
+        }
+        for (int q = 0; q < 7; ++q) cudaEventDestroy(ev[q]);
+    }
     return MSRSB_OK;
 }
 
 // ---- apply (Alg. 4 with Alg. 3 inside), z = M^-1 v from z = 0 ---------------------
+
+// r = v - A z in the handle precision (FP32 values and accumulation in mixed
+// mode); scalar operators use the sliced-ELL copy, optionally writing row i
+// to position operm[i]
+template <typename T>
+static msrsb_status resid_t(const msrsb_handle *h, const T *aval_t, const double *z, const double *v, T *r,
+                            const int32_t *operm, cudaStream_t s) {
+    if (h->bdim == 1) {
+        const T *sv = (const T *)h->asell.val[h->opts.prec == MSRSB_F32 ? 1 : 0];
+        return sell_spmv<T, double, double, T, T>(h->asell, sv, z, v, r, true, s, operm);
+    }
+    return spmv<T, double, double, T, T>(h->A, aval_t, z, v, r, true, s, operm);
+}
 
 template <typename T>
 static msrsb_status apply_t(msrsb_handle *h, const double *v, double *z, cudaStream_t s) {
@@ -225,11 +277,12 @@ static msrsb_status apply_t(msrsb_handle *h, const double *v, double *z, cudaStr
         if (gs) {
             MSRSB_TRY((gs_apply<T, T>(h, aval_t, (const T *)h->dinv, 1, r, y, z, 1, s)));
         } else {
+            MSRSB_TRY(permute_cast<T>(N, v, h->pos_of, r, s));
             MSRSB_CUDA(cudaMemsetAsync(z, 0, N * sizeof(double), s));
-            MSRSB_TRY(ilu0_apply<T>(h, (const T *)h->lu, r, y, z, s));
+            MSRSB_TRY(ilu0_apply<T>(h, r, y, z, s));
         }
         // coarse correction of the residual v - A z
-        MSRSB_TRY((spmv<T, double, double, T, T>(A, aval_t, z, v, r, true, s)));
+        MSRSB_TRY(resid_t<T>(h, aval_t, z, v, r, nullptr, s));
         MSRSB_TRY((restrict_op<T, T>(h, P, r, h->vc, s)));
     } else {
         MSRSB_TRY((restrict_op<T, double>(h, P, v, h->vc, s)));
@@ -237,11 +290,14 @@ static msrsb_status apply_t(msrsb_handle *h, const double *v, double *z, cudaStr
     MSRSB_TRY(gemv(h->nC, h->Ainv, h->vc, h->wc, s));
     MSRSB_TRY(prolong_op<T>(h, P, h->wc, z, pre ? 1 : 0, s));
     if (post) {
-        MSRSB_TRY((spmv<T, double, double, T, T>(A, aval_t, z, v, r, true, s)));
-        if (gs)
+        if (gs) {
+            MSRSB_TRY(resid_t<T>(h, aval_t, z, v, r, nullptr, s));
             MSRSB_TRY((gs_apply<T, T>(h, aval_t, (const T *)h->dinv, 0, r, y, z, 0, s)));
-        else
-            MSRSB_TRY(ilu0_apply<T>(h, (const T *)h->lu, r, y, z, s));
+        } else {
+            // residual written straight into colour order for the sweeps
+            MSRSB_TRY(resid_t<T>(h, aval_t, z, v, r, h->pos_of, s));
+            MSRSB_TRY(ilu0_apply<T>(h, r, y, z, s));
+        }
     }
     return MSRSB_OK;
 }
@@ -253,6 +309,9 @@ static msrsb_status apply_any(msrsb_handle *h, const double *v, double *z, cudaS
 
 static msrsb_status fine_spmv(const msrsb_handle *h, const double *x, const double *v, double *y, bool resid,
                               cudaStream_t s) {
+    if (h->bdim == 1)
+        return sell_spmv<double, double, double, double, double>(h->asell, (const double *)h->asell.val[0], x, v, y,
+                                                                 resid, s);
     return spmv<double, double, double, double, double>(h->A, h->A.val, x, v, y, resid, s);
 }
 
@@ -280,9 +339,9 @@ msrsb_status vadd(int n, const double *a, double *b, cudaStream_t s) {
 }
 
 // Krylov state on the device, m = restart length:
-// H[(m+1) x m] column-major | cs[m] | sn[m] | g[m+1] | est | beta | h2[m+1]
+// H[(m+1) x m] column-major | cs[m] | sn[m] | g[m+1] | est | beta | h2[m+2] | est_hist[m+1] | flag
 struct KhLayout {
-    long H, cs, sn, g, est, beta, h2, total;
+    long H, cs, sn, g, est, beta, h2, hist, flag, total;
     explicit KhLayout(int m) {
         H = 0;
         cs = (long)(m + 1) * m;
@@ -291,9 +350,31 @@ struct KhLayout {
         est = g + m + 1;
         beta = est + 1;
         h2 = beta + 1;
-        total = h2 + m + 1 + 8;
+        hist = h2 + m + 2;
+        flag = hist + m + 1;
+        total = flag + 8;
     }
 };
+
+// Host-side pool of timing-free events (grows, kept per host thread).
+static cudaEvent_t *event_pool(int need) {
+    static thread_local cudaEvent_t *pool = nullptr;
+    static thread_local int cap = 0;
+    if (need > cap) {
+        cudaEvent_t *np = new cudaEvent_t[need];
+        for (int q = 0; q < cap; ++q) np[q] = pool[q];
+        for (int q = cap; q < need; ++q)
+            if (cudaEventCreateWithFlags(&np[q], cudaEventDisableTiming) != cudaSuccess) {
+                cudaGetLastError();
+                delete[] np;
+                return nullptr;
+            }
+        delete[] pool;
+        pool = np;
+        cap = need;
+    }
+    return pool;
+}
 
 // ---- GMRES (right preconditioned, flexible: Z_j = M^-1 V_j kept) ------------------------
 
@@ -301,23 +382,38 @@ struct KhLayout {
 // form the new one, update g; est = |g[j+1]|. State layout in kh:
 // H[(m+1) x m] column-major | cs[m] | sn[m] | g[m+1] | est
 __global__ void givens_kernel(int m, int j, double *__restrict__ kh) {
+    // one warp: stage column j and the rotations in shared memory, then apply
+    // them sequentially (thread 0) without global-memory round trips
+    __shared__ double col[514], c_s[512], s_s[512];
     double *H = kh, *cs = kh + (long)(m + 1) * m, *sn = cs + m, *g = sn + m, *est = g + m + 1;
-    double *col = H + (long)j * (m + 1);
-    for (int i = 0; i < j; ++i) {
-        double t = cs[i] * col[i] + sn[i] * col[i + 1];
-        col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
-        col[i] = t;
+    double *hc = H + (long)j * (m + 1);
+    for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) col[i] = hc[i];
+    for (int i = threadIdx.x; i < j; i += blockDim.x) {
+        c_s[i] = cs[i];
+        s_s[i] = sn[i];
     }
-    double a = col[j], b = col[j + 1];
-    double den = hypot(a, b);
-    double c = den != 0.0 ? a / den : 1.0, sgn = den != 0.0 ? b / den : 0.0;
-    cs[j] = c;
-    sn[j] = sgn;
-    col[j] = den;
-    col[j + 1] = 0.0;
-    g[j + 1] = -sgn * g[j];
-    g[j] = c * g[j];
-    *est = fabs(g[j + 1]);
+    __syncwarp();
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < j; ++i) {
+            double t = c_s[i] * col[i] + s_s[i] * col[i + 1];
+            col[i + 1] = -s_s[i] * col[i] + c_s[i] * col[i + 1];
+            col[i] = t;
+        }
+        double a = col[j], b = col[j + 1];
+        double den = hypot(a, b);
+        double c = den != 0.0 ? a / den : 1.0, sgn = den != 0.0 ? b / den : 0.0;
+        cs[j] = c;
+        sn[j] = sgn;
+        col[j] = den;
+        col[j + 1] = 0.0;
+        double gj = g[j];
+        g[j + 1] = -sgn * gj;
+        g[j] = c * gj;
+        *est = fabs(g[j + 1]);
+        est[2 + (m + 2) + j] = fabs(g[j + 1]);  // est_hist[j]
+    }
+    __syncwarp();
+    for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) hc[i] = col[i];
 }
 
 // back substitution H(0:k,0:k) y = g(0:k); y written over g
@@ -343,6 +439,7 @@ static msrsb_status gmres(msrsb_handle *h, const double *b, double *x, double rt
     double *V = h->kv, *Z = h->kz, *kh = h->kh;
     const KhLayout L(m);
     double *H = kh + L.H, *est = kh + L.est, *beta = kh + L.beta, *h2 = kh + L.h2;
+    int *reorth = (int *)(kh + L.flag);
     double bnorm = 0.0;
     MSRSB_TRY(norm2(N, b, h->partial, beta, s));
     MSRSB_TRY(read_scalar(beta, &bnorm, s));
@@ -371,31 +468,77 @@ static msrsb_status gmres(msrsb_handle *h, const double *b, double *x, double rt
         gmres_init_kernel<<<1, 1, 0, s>>>(m, kh, beta);
         MSRSB_LAUNCHED("gmres_init_kernel");
         int mm = m < maxit - its ? m : maxit - its;
-        int k = 0;
+        // Arnoldi steps are launched back to back; the residual estimate of
+        // step j is copied to pinned memory behind an event and looked at
+        // without blocking before later launches. Steps launched after the
+        // first converged one only add columns the solve below ignores.
+        double *pin = pinned_scratch();
+        double *pin_est = pin ? pin + 16 : nullptr;
+        cudaEvent_t *evs = event_pool(mm);
+        const bool lagged = pin_est && evs && mm <= kPinnedDoubles - 16;
+        int conv = -1, checked = 0, launched = 0;
         for (int j = 0; j < mm; ++j) {
+            if (lagged) {
+                while (checked < launched) {
+                    if (cudaEventQuery(evs[checked]) != cudaSuccess) {
+                        cudaGetLastError();
+                        // keep the host at most two steps ahead, so at most two
+                        // steps are spent after convergence
+                        if (launched - checked <= 2) break;
+                        MSRSB_CUDA(cudaEventSynchronize(evs[checked]));
+                    }
+                    double e = ((volatile double *)pin_est)[checked];
+                    if (!std::isfinite(e)) return fail(MSRSB_ENAN, "non-finite residual estimate in GMRES");
+                    if (e <= rtol * bnorm) {
+                        conv = checked;
+                        break;
+                    }
+                    ++checked;
+                }
+                if (conv >= 0) break;
+            }
             double *Vj = V + j * N, *Zj = Z + j * N, *w = V + (j + 1) * N;
             MSRSB_TRY(apply_any(h, Vj, Zj, s));
             MSRSB_TRY(fine_spmv(h, Zj, nullptr, w, false, s));
             double *hcol = H + (long)j * (m + 1);
-            // classical Gram-Schmidt, twice
-            MSRSB_TRY(mdot(N, j + 1, V, N, w, h->partial, hcol, 0, s));
-            MSRSB_TRY(mvsub(N, j + 1, V, N, hcol, w, s));
-            MSRSB_TRY(mdot(N, j + 1, V, N, w, h->partial, h2, 0, s));
-            MSRSB_TRY(mvsub(N, j + 1, V, N, h2, w, s));
-            // hcol += second pass
-            MSRSB_TRY(vadd(j + 1, h2, hcol, s));
-            MSRSB_TRY(norm2(N, w, h->partial, hcol + j + 1, s));
-            MSRSB_TRY(scale_by_inv(N, w, hcol + j + 1, w, s));
-            givens_kernel<<<1, 1, 0, s>>>(m, j, kh);
+            // classical Gram-Schmidt with the DGKS re-orthogonalisation test:
+            // one multi-dot pass (V_0..V_j and w itself, stored as V_{j+1})
+            // and one fused update + normalisation; the second pass runs on
+            // the device only when the first lost more than half of |w|^2
+            MSRSB_TRY(mdot(N, j + 2, V, N, w, h->partial, h2, 0, s));
+            MSRSB_TRY(gs_update(N, j + 1, V, N, h2, w, hcol, reorth, 1, s));
+            MSRSB_TRY(mdot(N, j + 2, V, N, w, h->partial, h2, 0, s, reorth));
+            MSRSB_TRY(gs_update(N, j + 1, V, N, h2, w, hcol, reorth, 2, s));
+            givens_kernel<<<1, 32, 0, s>>>(m, j, kh);
             MSRSB_LAUNCHED("givens_kernel");
-            ++its;
-            k = j + 1;
-            double e = 0.0;
-            MSRSB_TRY(read_scalar(est, &e, s));
-            if (hist) hist[its] = e / bnorm;
-            if (!std::isfinite(e)) return fail(MSRSB_ENAN, "non-finite residual estimate in GMRES");
-            if (e <= rtol * bnorm) break;
+            launched = j + 1;
+            if (lagged) {
+                MSRSB_CUDA(cudaMemcpyAsync(pin_est + j, kh + L.hist + j, sizeof(double), cudaMemcpyDeviceToHost, s));
+                MSRSB_CUDA(cudaEventRecord(evs[j], s));
+            } else {
+                double e = 0.0;
+                MSRSB_TRY(read_scalar(est, &e, s));
+                if (!std::isfinite(e)) return fail(MSRSB_ENAN, "non-finite residual estimate in GMRES");
+                if (hist) hist[its + j + 1] = e / bnorm;
+                if (e <= rtol * bnorm) {
+                    conv = j;
+                    break;
+                }
+            }
         }
+        if (lagged) {
+            MSRSB_CUDA(cudaStreamSynchronize(s));
+            for (int q = 0; q < launched; ++q) {
+                double e = ((volatile double *)pin_est)[q];
+                if (hist && (conv < 0 || q <= conv)) hist[its + q + 1] = e / bnorm;
+                if (conv < 0 && q >= checked) {
+                    if (!std::isfinite(e)) return fail(MSRSB_ENAN, "non-finite residual estimate in GMRES");
+                    if (e <= rtol * bnorm) conv = q;
+                }
+            }
+        }
+        const int k = conv >= 0 ? conv + 1 : launched;
+        its += k;
         hess_solve_kernel<<<1, 1, 0, s>>>(m, k, kh);
         MSRSB_LAUNCHED("hess_solve_kernel");
         MSRSB_TRY(mvadd(N, k, Z, N, kh + L.g, x, s));
@@ -507,10 +650,16 @@ static void handle_free(msrsb_handle *h) {
     dfree(h->jslot, s);
     dfree(h->Ac, s);
     dfree(h->Ainv, s);
-    dfree(h->lu, s);
+    dfree(h->ilu.lcol, s);
+    dfree(h->ilu.ucol, s);
+    dfree(h->ilu.lval, s);
+    dfree(h->ilu.uval, s);
+    dfree(h->ilu.udinv, s);
+    dfree(h->pos_of, s);
     dfree(h->diag_pos, s);
     dfree(h->dinv, s);
     dfree(h->a_lo, s);
+    sell_free(&h->asell, s);
     dfree(h->vc, s);
     dfree(h->wc, s);
     dfree(h->tmp_d, s);
@@ -649,6 +798,7 @@ extern "C" msrsb_status msrsb_get_info(const msrsb_handle *h, msrsb_info *info) 
     info->basis_e_it = h->basis_e_it;
     info->n_zero_diag = h->n_zero_diag;
     info->ncolours = h->ncolours;
+    for (int q = 0; q < 6; ++q) info->phase_ms[q] = h->phase_ms[q];
     return MSRSB_OK;
 }
 

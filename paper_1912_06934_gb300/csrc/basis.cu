@@ -57,9 +57,9 @@ __global__ void __launch_bounds__(256) smooth_kernel(int n, const int32_t *__res
         const int32_t *cp = scol + beg + lane;
         const T *vp = sval + beg + lane;
         for (int j = 0; j < width; ++j) {
-            unsigned pc = (unsigned)__ldg(cp + (j << 5));
-            T a = __ldg(vp + (j << 5));
-            unsigned m = pc >> kColShift;
+            const unsigned pc = (unsigned)__ldg(cp + (j << 5));
+            const T a = __ldg(vp + (j << 5));
+            const unsigned m = pc >> kColShift;
             if (m) {
                 T pk[W];
                 load_row<T, W>(Pin, (long)(pc & kColMask), pk);
@@ -85,8 +85,9 @@ __global__ void __launch_bounds__(256) smooth_kernel(int n, const int32_t *__res
                 t[c] = T(0);
             }
         }
+        const T rs = T(1) / sum;  // one division per row (FP64 issue slots are scarce)
 #pragma unroll
-        for (int c = 0; c < W; ++c) t[c] = (vm & (1u << c)) ? t[c] / sum : T(0);
+        for (int c = 0; c < W; ++c) t[c] = (vm & (1u << c)) ? t[c] * rs : T(0);
         store_row<T, W>(Pout, i, t);
         if (check && !skel[i]) e_loc = (double)emx;
     }
@@ -127,7 +128,7 @@ template msrsb_status indicator<float>(int, int, const int32_t *, const int32_t 
 double *pinned_scratch() {
     static thread_local double *p = nullptr;
     if (!p) {
-        if (cudaHostAlloc((void **)&p, 4096, cudaHostAllocPortable) != cudaSuccess) {
+        if (cudaHostAlloc((void **)&p, 8192 * sizeof(double), cudaHostAllocPortable) != cudaSuccess) {
             cudaGetLastError();
             p = nullptr;
         }

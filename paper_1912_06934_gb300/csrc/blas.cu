@@ -13,7 +13,7 @@ template <int G, typename TA, typename TX, typename TV, typename TY, typename TA
 __global__ void __launch_bounds__(256) csr_spmv_kernel(int n, const int32_t *__restrict__ rowptr,
                                                        const int32_t *__restrict__ colidx, const TA *__restrict__ val,
                                                        const TX *__restrict__ x, const TV *__restrict__ v,
-                                                       TY *__restrict__ y) {
+                                                       TY *__restrict__ y, const int32_t *__restrict__ operm) {
     int row = (blockIdx.x * blockDim.x + threadIdx.x) / G;
     int g = threadIdx.x % G;
     if (row >= n) return;  // whole groups leave together (n rows, G | 32)
@@ -21,19 +21,19 @@ __global__ void __launch_bounds__(256) csr_spmv_kernel(int n, const int32_t *__r
     for (int e = rowptr[row] + g; e < rowptr[row + 1]; e += G) s = fma(TACC(val[e]), TACC(x[colidx[e]]), s);
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(G == 32 ? 0xffffffffu : ((1u << G) - 1) << (threadIdx.x & 31 & ~(G - 1)), s, o, G);
-    if (g == 0) y[row] = RESID ? TY(TACC(v[row]) - s) : TY(s);
+    if (g == 0) y[operm ? operm[row] : row] = RESID ? TY(TACC(v[row]) - s) : TY(s);
 }
 
 template <typename TA, typename TX, typename TV, typename TY, typename TACC, bool RESID>
 msrsb_status csr_spmv(int n, int nnz, const int32_t *rowptr, const int32_t *colidx, const TA *val, const TX *x,
-                      const TV *v, TY *y, cudaStream_t s) {
+                      const TV *v, TY *y, const int32_t *operm, cudaStream_t s) {
     double avg = (double)nnz / n;
     if (avg > 12) {
         csr_spmv_kernel<8, TA, TX, TV, TY, TACC, RESID><<<ceil_div((long)n * 8, 256), 256, 0, s>>>(n, rowptr, colidx,
-                                                                                                   val, x, v, y);
+                                                                                                   val, x, v, y, operm);
     } else {
         csr_spmv_kernel<4, TA, TX, TV, TY, TACC, RESID><<<ceil_div((long)n * 4, 256), 256, 0, s>>>(n, rowptr, colidx,
-                                                                                                   val, x, v, y);
+                                                                                                   val, x, v, y, operm);
     }
     MSRSB_LAUNCHED("csr_spmv_kernel");
     return MSRSB_OK;
@@ -78,13 +78,17 @@ __global__ void __launch_bounds__(256) bsr_spmv_kernel(int n, const int32_t *__r
     }
 }
 
-// y = A x  (resid = false) or y = v - A x (resid = true), A of either block size
+// y = A x  (resid = false) or y = v - A x (resid = true), A of either block
+// size; for bdim 1 the result of row i may go to y[operm[i]] (operm nullable)
 template <typename TA, typename TX, typename TV, typename TY, typename TACC>
-msrsb_status spmv(const msrsb_mat &A, const TA *val, const TX *x, const TV *v, TY *y, bool resid, cudaStream_t s) {
+msrsb_status spmv(const msrsb_mat &A, const TA *val, const TX *x, const TV *v, TY *y, bool resid, cudaStream_t s,
+                  const int32_t *operm) {
     if (A.bdim == 1) {
-        if (resid) return csr_spmv<TA, TX, TV, TY, TACC, true>(A.nrows, A.nnz, A.rowptr, A.colidx, val, x, v, y, s);
-        return csr_spmv<TA, TX, TV, TY, TACC, false>(A.nrows, A.nnz, A.rowptr, A.colidx, val, x, v, y, s);
+        if (resid)
+            return csr_spmv<TA, TX, TV, TY, TACC, true>(A.nrows, A.nnz, A.rowptr, A.colidx, val, x, v, y, operm, s);
+        return csr_spmv<TA, TX, TV, TY, TACC, false>(A.nrows, A.nnz, A.rowptr, A.colidx, val, x, v, y, operm, s);
     }
+    if (operm) return fail(MSRSB_EINVAL, "output permutation is only supported for bdim 1");
     int grid = ceil_div((long)A.nrows * 4, 256);
     if (resid)
         bsr_spmv_kernel<TA, TX, TV, TY, TACC, true><<<grid, 256, 0, s>>>(A.nrows, A.rowptr, A.colidx, val, x, v, y);
@@ -95,39 +99,105 @@ msrsb_status spmv(const msrsb_mat &A, const TA *val, const TX *x, const TV *v, T
 }
 // instantiations used by the library
 template msrsb_status spmv<double, double, double, double, double>(const msrsb_mat &, const double *, const double *,
-                                                                   const double *, double *, bool, cudaStream_t);
+                                                                   const double *, double *, bool, cudaStream_t,
+                                                                   const int32_t *);
 template msrsb_status spmv<float, double, double, float, float>(const msrsb_mat &, const float *, const double *,
-                                                                const double *, float *, bool, cudaStream_t);
-template msrsb_status spmv<double, double, double, double, float>(const msrsb_mat &, const double *, const double *,
-                                                                  const double *, double *, bool, cudaStream_t);
+                                                                const double *, float *, bool, cudaStream_t,
+                                                                const int32_t *);
+
+// Sliced-ELL SpMV / residual: one thread per row, coalesced entry reads,
+// unrolled so several gathers are in flight. y[operm ? operm[i] : i] =
+// (resid ? v_i : 0) -/+ sum_k A_ik x_k.
+template <typename TA, typename TX, typename TV, typename TY, typename TACC, bool RESID>
+__global__ void __launch_bounds__(256) sell_spmv_kernel(int n, const int32_t *__restrict__ slice_ptr,
+                                                        const int32_t *__restrict__ scol, const TA *__restrict__ sval,
+                                                        const TX *__restrict__ x, const TV *__restrict__ v,
+                                                        TY *__restrict__ y, const int32_t *__restrict__ operm) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int s = i >> 5, lane = i & 31;
+    const int beg = slice_ptr[s], width = (slice_ptr[s + 1] - beg) >> 5;
+    const int32_t *cp = scol + beg + lane;
+    const TA *vp = sval + beg + lane;
+    TACC acc0 = TACC(0), acc1 = TACC(0);
+    int j = 0;
+    for (; j + 1 < width; j += 2) {
+        acc0 = fma(TACC(__ldg(vp + (j << 5))), TACC(__ldg(x + __ldg(cp + (j << 5)))), acc0);
+        acc1 = fma(TACC(__ldg(vp + ((j + 1) << 5))), TACC(__ldg(x + __ldg(cp + ((j + 1) << 5)))), acc1);
+    }
+    if (j < width) acc0 = fma(TACC(__ldg(vp + (j << 5))), TACC(__ldg(x + __ldg(cp + (j << 5)))), acc0);
+    const TACC sum = acc0 + acc1;
+    y[operm ? operm[i] : i] = RESID ? TY(TACC(v[i]) - sum) : TY(sum);
+}
+
+template <typename TA, typename TX, typename TV, typename TY, typename TACC>
+msrsb_status sell_spmv(const Sell &S, const TA *val, const TX *x, const TV *v, TY *y, bool resid, cudaStream_t s,
+                       const int32_t *operm) {
+    const int grid = ceil_div(S.n, 256);
+    if (resid)
+        sell_spmv_kernel<TA, TX, TV, TY, TACC, true><<<grid, 256, 0, s>>>(S.n, S.slice_ptr, S.col, val, x, v, y,
+                                                                          operm);
+    else
+        sell_spmv_kernel<TA, TX, TV, TY, TACC, false><<<grid, 256, 0, s>>>(S.n, S.slice_ptr, S.col, val, x, v, y,
+                                                                           operm);
+    MSRSB_LAUNCHED("sell_spmv_kernel");
+    return MSRSB_OK;
+}
+template msrsb_status sell_spmv<double, double, double, double, double>(const Sell &, const double *, const double *,
+                                                                        const double *, double *, bool, cudaStream_t,
+                                                                        const int32_t *);
+template msrsb_status sell_spmv<float, double, double, float, float>(const Sell &, const float *, const double *,
+                                                                     const double *, float *, bool, cudaStream_t,
+                                                                     const int32_t *);
 
 // ---- restriction and prolongation ------------------------------------------------
 
-// vc[J*bd + l] = sum_{i in supp(J)} P^l_{iJ} v[i*bd + l]; one warp per J, fixed order
+// vc[J*bd + l] = sum_{i in supp(J)} P^l_{iJ} v[i*bd + l]; one CTA per J,
+// thread-private sums over the support rows, fixed-order block reduction
 template <typename TP, typename TV>
-__global__ void restrict_kernel(int nc, int n, int W, int bd, const int32_t *__restrict__ pt_ptr,
-                                const int32_t *__restrict__ pt_rows, const int8_t *__restrict__ jslot,
-                                const TP *__restrict__ P, const TV *__restrict__ v, double *__restrict__ vc) {
-    int J = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    int lane = threadIdx.x & 31;
-    if (J >= nc) return;
-    int sj = jslot[J];
-    long nW = (long)n * W;
-    for (int l = 0; l < bd; ++l) {
-        double s = 0.0;
-        for (int r = pt_ptr[J] + lane; r < pt_ptr[J + 1]; r += 32) {
-            int i = pt_rows[r];
-            s = fma((double)P[l * nW + (long)i * W + sj], (double)v[(long)i * bd + l], s);
+__global__ void __launch_bounds__(256) restrict_kernel(int nc, int n, int W, int bd, const int32_t *__restrict__ pt_ptr,
+                                                       const int32_t *__restrict__ pt_rows,
+                                                       const int8_t *__restrict__ jslot, const TP *__restrict__ P,
+                                                       const TV *__restrict__ v, double *__restrict__ vc) {
+    __shared__ double red[3][8];
+    const int J = blockIdx.x;
+    const int sj = jslot[J];
+    const long nW = (long)n * W;
+    double acc[3] = {0.0, 0.0, 0.0};
+    const int r1 = pt_ptr[J + 1];
+    int r = pt_ptr[J] + threadIdx.x;
+    for (; r + (int)blockDim.x < r1; r += 2 * blockDim.x) {
+        const int i0 = pt_rows[r], i1 = pt_rows[r + blockDim.x];
+        for (int l = 0; l < bd; ++l) {
+            const double p0 = (double)P[l * nW + (long)i0 * W + sj], p1 = (double)P[l * nW + (long)i1 * W + sj];
+            const double v0 = (double)v[(long)i0 * bd + l], v1 = (double)v[(long)i1 * bd + l];
+            acc[l] = fma(p0, v0, acc[l]);
+            acc[l] = fma(p1, v1, acc[l]);
         }
-        s = warp_sum(s);
-        if (lane == 0) vc[(long)J * bd + l] = s;
+    }
+    if (r < r1) {
+        const int i = pt_rows[r];
+        for (int l = 0; l < bd; ++l)
+            acc[l] = fma((double)P[l * nW + (long)i * W + sj], (double)v[(long)i * bd + l], acc[l]);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int l = 0; l < bd; ++l) {
+        double t = warp_sum(acc[l]);
+        if (lane == 0) red[l][warp] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < bd) {
+        const int l = threadIdx.x;
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[l][w];
+        vc[(long)J * bd + l] = t;
     }
 }
 
 template <typename TP, typename TV>
 msrsb_status restrict_op(const msrsb_handle *h, const TP *P, const TV *v, double *vc, cudaStream_t s) {
-    restrict_kernel<TP, TV><<<ceil_div(h->nc, 8), 256, 0, s>>>(h->nc, h->n, h->W, h->bdim, h->pt_ptr, h->pt_rows,
-                                                              h->jslot, P, v, vc);
+    restrict_kernel<TP, TV><<<h->nc, 256, 0, s>>>(h->nc, h->n, h->W, h->bdim, h->pt_ptr, h->pt_rows, h->jslot, P, v,
+                                                  vc);
     MSRSB_LAUNCHED("restrict_kernel");
     return MSRSB_OK;
 }
@@ -138,27 +208,41 @@ template msrsb_status restrict_op<float, double>(const msrsb_handle *, const flo
 template msrsb_status restrict_op<float, float>(const msrsb_handle *, const float *, const float *, double *,
                                                 cudaStream_t);
 
-// z[i*bd + l] (+)= sum_s P^l_{is} wc[ids_is*bd + l]
-template <typename TP>
-__global__ void prolong_kernel(int n, int W, int bd, const int32_t *__restrict__ p_ids, const TP *__restrict__ P,
-                               const double *__restrict__ wc, double *__restrict__ z, int add) {
+// z[i*bd + l] (+)= sum_s P^l_{is} wc[ids_is*bd + l]; the ids and values of
+// a row are read as 16-byte vectors
+template <typename TP, int W>
+__global__ void __launch_bounds__(256) prolong_kernel(int n, int bd, const int32_t *__restrict__ p_ids,
+                                                      const TP *__restrict__ P, const double *__restrict__ wc,
+                                                      double *__restrict__ z, int add) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    long nW = (long)n * W;
+    const long nW = (long)n * W;
+    int32_t ids[W];
+    {
+        const int4 *src = reinterpret_cast<const int4 *>(p_ids + (long)i * W);
+#pragma unroll
+        for (int q = 0; q < W / 4; ++q) reinterpret_cast<int4 *>(ids)[q] = __ldg(src + q);
+    }
     for (int l = 0; l < bd; ++l) {
+        TP pv[W];
+        const uint4 *src = reinterpret_cast<const uint4 *>(P + l * nW + (long)i * W);
+#pragma unroll
+        for (int q = 0; q < (int)(W * sizeof(TP) / 16); ++q) reinterpret_cast<uint4 *>(pv)[q] = __ldg(src + q);
         double s = 0.0;
-        for (int c = 0; c < W; ++c) {
-            int J = p_ids[(long)i * W + c];
-            if (J >= 0) s = fma((double)P[l * nW + (long)i * W + c], wc[(long)J * bd + l], s);
-        }
-        long o = (long)i * bd + l;
+#pragma unroll
+        for (int c = 0; c < W; ++c)
+            if (ids[c] >= 0) s = fma((double)pv[c], wc[(long)ids[c] * bd + l], s);
+        const long o = (long)i * bd + l;
         z[o] = add ? z[o] + s : s;
     }
 }
 
 template <typename TP>
 msrsb_status prolong_op(const msrsb_handle *h, const TP *P, const double *wc, double *z, int add, cudaStream_t s) {
-    prolong_kernel<TP><<<ceil_div(h->n, 256), 256, 0, s>>>(h->n, h->W, h->bdim, h->p_ids, P, wc, z, add);
+    if (h->W == 8)
+        prolong_kernel<TP, 8><<<ceil_div(h->n, 256), 256, 0, s>>>(h->n, h->bdim, h->p_ids, P, wc, z, add);
+    else
+        prolong_kernel<TP, 4><<<ceil_div(h->n, 256), 256, 0, s>>>(h->n, h->bdim, h->p_ids, P, wc, z, add);
     MSRSB_LAUNCHED("prolong_kernel");
     return MSRSB_OK;
 }
@@ -169,33 +253,46 @@ template msrsb_status prolong_op<float>(const msrsb_handle *, const float *, con
 
 // ---- dense vector kernels for the Krylov loop ---------------------------------------
 
-constexpr int kRedBlocks = 304;  // fixed number of partial sums (2 per SM): fixed reduction order
+constexpr int kRedBlocks = 76;  // fixed number of row chunks (partial sums): fixed reduction order
 
-// partial[j * kRedBlocks + b] = sum over block b's rows of V_j[i] * w[i], j < nvec
-__global__ void __launch_bounds__(256) mdot_kernel(long N, int nvec, const double *__restrict__ V, long ldv,
-                                                   const double *__restrict__ w, double *__restrict__ partial) {
+// partial[j * gridDim.x + b] = sum over row chunk b of V_j[i] * w[i];
+// blockIdx.y = vector j. One block reduction per CTA, fixed order. When
+// `gate` is given the kernel does nothing unless *gate != 0.
+__global__ void __launch_bounds__(256) mdot_kernel(long N, const double *__restrict__ V, long ldv,
+                                                   const double *__restrict__ w, double *__restrict__ partial,
+                                                   const int *__restrict__ gate) {
+    if (gate && !*gate) return;
     __shared__ double red[8];
-    long chunk = (N + gridDim.x - 1) / gridDim.x;
-    long b0 = blockIdx.x * chunk, b1 = b0 + chunk < N ? b0 + chunk : N;
-    for (int j = 0; j < nvec; ++j) {
-        const double *vj = V + j * ldv;
-        double s = 0.0;
-        for (long i = b0 + threadIdx.x; i < b1; i += blockDim.x) s = fma(vj[i], w[i], s);
-        s = warp_sum(s);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            double t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-            t = warp_sum(t);
-            if (threadIdx.x == 0) partial[(long)j * gridDim.x + blockIdx.x] = t;
-        }
-        __syncthreads();
+    const int j = blockIdx.y;
+    const long chunk = (N + gridDim.x - 1) / gridDim.x;
+    const long b0 = blockIdx.x * chunk, b1 = b0 + chunk < N ? b0 + chunk : N;
+    const double *vj = V + j * ldv;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    const long bd = blockDim.x;
+    long i = b0 + threadIdx.x;
+    for (; i + 3 * bd < b1; i += 4 * bd) {
+        s0 = fma(vj[i], w[i], s0);
+        s1 = fma(vj[i + bd], w[i + bd], s1);
+        s2 = fma(vj[i + 2 * bd], w[i + 2 * bd], s2);
+        s3 = fma(vj[i + 3 * bd], w[i + 3 * bd], s3);
+    }
+    for (; i < b1; i += bd) s0 = fma(vj[i], w[i], s0);
+    s0 += s2;
+    s1 += s3;
+    double s = warp_sum(s0 + s1);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        t = warp_sum(t);
+        if (threadIdx.x == 0) partial[(long)j * gridDim.x + blockIdx.x] = t;
     }
 }
 
 // out[j] = (accumulate ? out[j] : 0) + sum_b partial[j][b]; block per j
 __global__ void reduce_partials_kernel(int nblk, const double *__restrict__ partial, double *__restrict__ out,
-                                       int accumulate, int sqrt_out) {
+                                       int accumulate, int sqrt_out, const int *__restrict__ gate) {
+    if (gate && !*gate) return;
     __shared__ double red[8];
     int j = blockIdx.x;
     double s = 0.0;
@@ -213,31 +310,91 @@ __global__ void reduce_partials_kernel(int nblk, const double *__restrict__ part
     }
 }
 
-// out[j] (+)= V_j . w for j < nvec
+// out[j] (+)= V_j . w for j < nvec (gate: run only if *gate != 0)
 msrsb_status mdot(long N, int nvec, const double *V, long ldv, const double *w, double *partial, double *out,
-                  int accumulate, cudaStream_t s) {
-    mdot_kernel<<<kRedBlocks, 256, 0, s>>>(N, nvec, V, ldv, w, partial);
+                  int accumulate, cudaStream_t s, const int *gate) {
+    dim3 grid(kRedBlocks, nvec);
+    mdot_kernel<<<grid, 256, 0, s>>>(N, V, ldv, w, partial, gate);
     MSRSB_LAUNCHED("mdot_kernel");
-    reduce_partials_kernel<<<nvec, 256, 0, s>>>(kRedBlocks, partial, out, accumulate, 0);
+    reduce_partials_kernel<<<nvec, 256, 0, s>>>(kRedBlocks, partial, out, accumulate, 0, gate);
     MSRSB_LAUNCHED("reduce_partials_kernel");
     return MSRSB_OK;
 }
 
 msrsb_status norm2(long N, const double *w, double *partial, double *out, cudaStream_t s) {
-    mdot_kernel<<<kRedBlocks, 256, 0, s>>>(N, 1, w, N, w, partial);
+    dim3 grid(kRedBlocks, 1);
+    mdot_kernel<<<grid, 256, 0, s>>>(N, w, N, w, partial, nullptr);
     MSRSB_LAUNCHED("mdot_kernel");
-    reduce_partials_kernel<<<1, 256, 0, s>>>(kRedBlocks, partial, out, 0, 1);
+    reduce_partials_kernel<<<1, 256, 0, s>>>(kRedBlocks, partial, out, 0, 1, nullptr);
     MSRSB_LAUNCHED("reduce_partials_kernel");
     return MSRSB_OK;
 }
 
-// w -= sum_j V_j h[j]
+// Classical Gram-Schmidt update with the DGKS test, fused with the
+// normalisation. hs[0..nv-1] = V_q . w, hs[nv] = w . w (one multi-dot pass).
+// The squared norm after the projection is hs[nv] - sum_q hs[q]^2; if it kept
+// at least half of |w|^2 (no severe cancellation) the result is normalised in
+// the same pass and H(nv, col) is set, else it is left unnormalised and *flag
+// = 1 asks for a second pass (pass 2 always normalises). Pass 1 writes H(0..nv-1,
+// col) = hs, pass 2 adds its coefficients. Every CTA takes the same decision.
+__global__ void __launch_bounds__(256) gs_update_kernel(long N, int nv, const double *__restrict__ V, long ldv,
+                                                        const double *__restrict__ hs, double *__restrict__ w,
+                                                        double *__restrict__ hcol, int *__restrict__ flag, int pass) {
+    if (pass == 2 && !*flag) return;
+    __shared__ double hsh[1024];
+    __shared__ double s_scale;
+    __shared__ int s_norm;
+    for (int q = threadIdx.x; q < nv; q += blockDim.x) hsh[q] = hs[q];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double pr = 0.0;
+        for (int q = 0; q < nv; ++q) pr = fma(hsh[q], hsh[q], pr);
+        const double ww = hs[nv];
+        const double d2 = ww - pr;
+        const int norm = pass == 2 || d2 >= 0.5 * ww;
+        const double den = norm && d2 > 0.0 ? sqrt(d2) : 0.0;
+        s_norm = norm;
+        s_scale = den > 0.0 ? 1.0 / den : (norm ? 0.0 : 1.0);
+        if (blockIdx.x == 0) {
+            for (int q = 0; q < nv; ++q) hcol[q] = pass == 1 ? hsh[q] : hcol[q] + hsh[q];
+            if (norm) hcol[nv] = den;
+            if (pass == 1) *flag = !norm;
+        }
+    }
+    __syncthreads();
+    const double sc = s_scale;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int q = 0;
+        for (; q + 3 < nv; q += 4) {
+            a0 = fma(V[q * ldv + i], hsh[q], a0);
+            a1 = fma(V[(q + 1) * ldv + i], hsh[q + 1], a1);
+            a2 = fma(V[(q + 2) * ldv + i], hsh[q + 2], a2);
+            a3 = fma(V[(q + 3) * ldv + i], hsh[q + 3], a3);
+        }
+        for (; q < nv; ++q) a0 = fma(V[q * ldv + i], hsh[q], a0);
+        w[i] = (w[i] - ((a0 + a1) + (a2 + a3))) * sc;
+    }
+}
+
+msrsb_status gs_update(long N, int nv, const double *V, long ldv, const double *hs, double *w, double *hcol, int *flag,
+                       int pass, cudaStream_t s) {
+    gs_update_kernel<<<ceil_div(N, 256) < 2048 ? ceil_div(N, 256) : 2048, 256, 0, s>>>(N, nv, V, ldv, hs, w, hcol,
+                                                                                       flag, pass);
+    MSRSB_LAUNCHED("gs_update_kernel");
+    return MSRSB_OK;
+}
+
+// w -= sum_j V_j h[j]  (h staged in shared memory)
 __global__ void mvsub_kernel(long N, int nvec, const double *__restrict__ V, long ldv, const double *__restrict__ h,
                              double *__restrict__ w) {
+    __shared__ double hs[1024];
+    for (int j = threadIdx.x; j < nvec; j += blockDim.x) hs[j] = h[j];
+    __syncthreads();
     long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (i >= N) return;
     double s = 0.0;
-    for (int j = 0; j < nvec; ++j) s = fma(V[j * ldv + i], h[j], s);
+    for (int j = 0; j < nvec; ++j) s = fma(V[j * ldv + i], hs[j], s);
     w[i] -= s;
 }
 
@@ -247,13 +404,16 @@ msrsb_status mvsub(long N, int nvec, const double *V, long ldv, const double *h,
     return MSRSB_OK;
 }
 
-// x += sum_j Z_j y[j]
+// x += sum_j Z_j y[j]  (y staged in shared memory)
 __global__ void mvadd_kernel(long N, int nvec, const double *__restrict__ Z, long ldz, const double *__restrict__ y,
                              double *__restrict__ x) {
+    __shared__ double ys[1024];
+    for (int j = threadIdx.x; j < nvec; j += blockDim.x) ys[j] = y[j];
+    __syncthreads();
     long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (i >= N) return;
     double s = 0.0;
-    for (int j = 0; j < nvec; ++j) s = fma(Z[j * ldz + i], y[j], s);
+    for (int j = 0; j < nvec; ++j) s = fma(Z[j * ldz + i], ys[j], s);
     x[i] += s;
 }
 
@@ -307,6 +467,23 @@ msrsb_status xpay_dev(long N, const double *num, const double *den, const double
     MSRSB_LAUNCHED("xpay_dev_kernel");
     return MSRSB_OK;
 }
+
+// y[perm[i]] = TO(x[i])
+template <typename TO>
+__global__ void permute_cast_kernel(long N, const double *__restrict__ x, const int32_t *__restrict__ perm,
+                                    TO *__restrict__ y) {
+    long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i < N) y[perm[i]] = TO(x[i]);
+}
+
+template <typename TO>
+msrsb_status permute_cast(long N, const double *x, const int32_t *perm, TO *y, cudaStream_t s) {
+    permute_cast_kernel<TO><<<ceil_div(N, 256), 256, 0, s>>>(N, x, perm, y);
+    MSRSB_LAUNCHED("permute_cast_kernel");
+    return MSRSB_OK;
+}
+template msrsb_status permute_cast<float>(long, const double *, const int32_t *, float *, cudaStream_t);
+template msrsb_status permute_cast<double>(long, const double *, const int32_t *, double *, cudaStream_t);
 
 template <typename TO>
 __global__ void copy_cast_kernel(long N, const double *__restrict__ x, TO *__restrict__ y) {

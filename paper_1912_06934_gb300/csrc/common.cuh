@@ -79,6 +79,16 @@ struct Sell {
     void *val[3] = {nullptr, nullptr, nullptr};
 };
 
+// ILU(0) factors per colour in ELL blocks over colour-ordered positions
+struct IluEll {
+    int ncol = 0;
+    int cptr[17] = {0};   // first position of each colour (+ end)
+    int wl[16] = {0}, wu[16] = {0};
+    long lbase[16] = {0}, ubase[16] = {0};
+    int32_t *lcol = nullptr, *ucol = nullptr;
+    void *lval = nullptr, *uval = nullptr, *udinv = nullptr;
+};
+
 // ---- device helpers -------------------------------------------------------
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
 
@@ -123,10 +133,12 @@ struct msrsb_handle {
     // coarse operator and its inverse (FP64, dense nC x nC)
     double *Ac = nullptr, *Ainv = nullptr;
     // smoother factors in A's (block) pattern, handle precision
-    void *lu = nullptr;       // ILU(0): L below, U on/above the diagonal (colour order)
+    msrsb::IluEll ilu;          // ILU(0) factors (colour order), handle precision
+    int32_t *pos_of = nullptr;  // colour-order position of every fine row
     int32_t *diag_pos = nullptr;
     void *dinv = nullptr;     // block GS: inverse 3x3 diagonal blocks [n][9]
-    void *a_lo = nullptr;     // FP32 copy of A's values (mixed precision inner residual)
+    void *a_lo = nullptr;     // FP32 copy of A's values (mixed precision inner residual, bdim 3)
+    msrsb::Sell asell;          // sliced-ELL copy of a scalar A: FP64 values [0], FP32 values [1] (mixed)
     // workspaces
     double *vc = nullptr, *wc = nullptr, *tmp_d = nullptr;
     void *r_t = nullptr, *y_t = nullptr;
@@ -141,4 +153,5 @@ struct msrsb_handle {
     double basis_e_it = 0.0;
     int n_zero_diag = 0;
     int own_A = 0;  // set by msrsb_solve_host when it owns A's device copy
+    double phase_ms[6] = {0, 0, 0, 0, 0, 0};
 };

@@ -156,6 +156,40 @@ void sell_free(Sell *S, cudaStream_t s) {
     for (int c = 0; c < 3; ++c) dfree(S->val[c], s);
 }
 
+// Plain sliced-ELL copy of a scalar CSR operator for the SpMV kernels:
+// columns (no mask) and FP64 values, optionally also FP32 values.
+__global__ void sell_copy_kernel(int n, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                                 const double *__restrict__ val, const int32_t *__restrict__ slice_ptr,
+                                 int32_t *__restrict__ scol, double *__restrict__ v64, float *__restrict__ v32) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int s = i >> 5, lane = i & 31;
+    long base = slice_ptr[s];
+    int width = (slice_ptr[s + 1] - slice_ptr[s]) / kSell;
+    int r0 = i < n ? rowptr[i] : 0, len = i < n ? rowptr[i + 1] - r0 : 0;
+    for (int j = 0; j < width; ++j) {
+        long e = base + (long)j * kSell + lane;
+        bool in = j < len;
+        scol[e] = in ? colidx[r0 + j] : (i < n ? i : 0);
+        double a = in ? val[r0 + j] : 0.0;
+        v64[e] = a;
+        if (v32) v32[e] = (float)a;
+    }
+}
+
+msrsb_status sell_copy(const msrsb_mat *A, bool with_f32, Sell *S, cudaStream_t s) {
+    MSRSB_TRY(sell_structure(A->nrows, A->rowptr, S, s));
+    double *v64 = nullptr;
+    float *v32 = nullptr;
+    MSRSB_TRY(dalloc(&v64, S->entries, s));
+    if (with_f32) MSRSB_TRY(dalloc(&v32, S->entries, s));
+    S->val[0] = v64;
+    S->val[1] = v32;
+    sell_copy_kernel<<<S->nslices, kSell, 0, s>>>(A->nrows, A->rowptr, A->colidx, A->val, S->slice_ptr, S->col, v64,
+                                                  v32);
+    MSRSB_LAUNCHED("sell_copy_kernel");
+    return MSRSB_OK;
+}
+
 msrsb_status check_mat(const msrsb_mat *A) {
     if (!A) return fail(MSRSB_EINVAL, "matrix is NULL");
     if (A->bdim != 1 && A->bdim != 3) return fail(MSRSB_EINVAL, "bdim must be 1 or 3 (got %d)", A->bdim);

@@ -3,10 +3,9 @@
 // with a block-diagonal P (Sec. 4), plus the transposed pattern of P that the
 // restriction R = P^T also uses.
 //
-// One CTA per coarse node J walks the fine rows of J's support (from the
-// transposed pattern), and for every row i, entry A_ik and slot t of row k
-// adds P_iJ A_ik P_kt into a dense shared-memory copy of coarse row J; the
-// finished row is written once. FP64 throughout.
+// Two passes, FP64, no atomics, fixed summation order: (1) every fine row
+// forms its row of A P, one entry per coarse node it couples to; (2) one CTA
+// per coarse node J sums P_iJ (A P)_i* over the rows of J's support.
 #include "common.cuh"
 #include <cub/device/device_radix_sort.cuh>
 #include <cub/device/device_scan.cuh>
@@ -68,74 +67,146 @@ msrsb_status build_transpose(int n, int W, int nc, const int32_t *p_ids, int32_t
     return MSRSB_OK;
 }
 
-// CTA per coarse node J; warps take fine rows of supp(J), lanes take the
-// entries of A's row. Shared row acc[bdim][nC].
+// Residue code of every coarse node, code(L) = sum_d (L_d mod 3) 3^d. The
+// coarse nodes met in one fine row's neighbourhood span at most three
+// consecutive coarse coordinates per axis (a row on a coarse-node line sees
+// L-1..L+1, any other row L..L+2), so their codes are all different; and every
+// L that couples with J through a fine row of supp(J) satisfies |L_d - J_d| <= 1.
+__global__ void coarse_code_kernel(int nc, int nb0, int nb1, int dim, int8_t *__restrict__ code) {
+    int L = blockIdx.x * blockDim.x + threadIdx.x;
+    if (L >= nc) return;
+    int l0 = L % nb0, l1 = (L / nb0) % nb1, l2 = L / (nb0 * nb1);
+    code[L] = (int8_t)(l0 % 3 + 3 * (l1 % 3) + (dim == 3 ? 9 * (l2 % 3) : 0));
+}
+
+// Pass 1, one thread per fine (block) row i:
+// AP[i][s][l][m] = sum_k A_ik[l][m] P^m_{k,L} over the coarse nodes L with
+// code s met through row i (FP64, fixed order: A's row order, then slots).
 template <typename T, int BD>
-__global__ void __launch_bounds__(256) galerkin_kernel(int n, int W, int nc, const int32_t *__restrict__ rowptr,
-                                                       const int32_t *__restrict__ colidx,
-                                                       const double *__restrict__ val,
-                                                       const int32_t *__restrict__ p_ids, const T *__restrict__ P,
-                                                       const int32_t *__restrict__ pt_ptr,
-                                                       const int32_t *__restrict__ pt_rows,
-                                                       const int8_t *__restrict__ jslot, double *__restrict__ Ac) {
-    extern __shared__ double acc[];  // [BD][nC]
-    const int nC = nc * BD;
-    const int J = blockIdx.x;
-    for (int t = threadIdx.x; t < BD * nC; t += blockDim.x) acc[t] = 0.0;
-    __syncthreads();
-    const int sj = jslot[J];
+__global__ void __launch_bounds__(128) ap_kernel(int n, int W, int ncode, const int32_t *__restrict__ rowptr,
+                                                 const int32_t *__restrict__ colidx, const double *__restrict__ val,
+                                                 const int32_t *__restrict__ p_ids, const T *__restrict__ P,
+                                                 const int8_t *__restrict__ code, double *__restrict__ AP) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
     const long nW = (long)n * W;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    for (int r = pt_ptr[J] + warp; r < pt_ptr[J + 1]; r += nwarps) {
-        const int i = pt_rows[r];
-        double pij[BD];
+    double acc[27 * BD * BD];
+    for (int q = 0; q < ncode * BD * BD; ++q) acc[q] = 0.0;
+    for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+        const int k = colidx[e];
+        double a[BD * BD];
 #pragma unroll
-        for (int l = 0; l < BD; ++l) pij[l] = (double)P[l * nW + (long)i * W + sj];
-        for (int e = rowptr[i] + lane; e < rowptr[i + 1]; e += 32) {
-            const int k = colidx[e];
-            double a[BD * BD];
+        for (int q = 0; q < BD * BD; ++q) a[q] = val[(long)e * BD * BD + q];
+        for (int t = 0; t < W; ++t) {
+            const int L = p_ids[(long)k * W + t];
+            if (L < 0) continue;
+            const int s = code[L];
 #pragma unroll
-            for (int q = 0; q < BD * BD; ++q) a[q] = val[(long)e * BD * BD + q];
-            for (int t = 0; t < W; ++t) {
-                const int L = p_ids[(long)k * W + t];
-                if (L < 0) continue;
+            for (int m = 0; m < BD; ++m) {
+                const double pkl = (double)P[m * nW + (long)k * W + t];
 #pragma unroll
-                for (int m = 0; m < BD; ++m) {
-                    const double pkl = (double)P[m * nW + (long)k * W + t];
-#pragma unroll
-                    for (int l = 0; l < BD; ++l) atomicAdd(&acc[l * nC + L * BD + m], pij[l] * a[l * BD + m] * pkl);
-                }
+                for (int l = 0; l < BD; ++l) acc[(s * BD + l) * BD + m] = fma(a[l * BD + m], pkl, acc[(s * BD + l) * BD + m]);
             }
         }
     }
+    double *out = AP + (long)i * ncode * BD * BD;
+    for (int q = 0; q < ncode * BD * BD; ++q) out[q] = acc[q];
+}
+
+// Pass 2, one CTA per coarse node J: A_c[J*BD+l][L*BD+m] = sum over fine rows
+// i of supp(J) (ascending) of P^l_{iJ} AP[i][code(L)][l][m]; thread-private
+// sums, then a fixed-order block reduction. Writes the whole dense row.
+template <typename T, int BD>
+__global__ void __launch_bounds__(128) ptap_kernel(int n, int W, int nc, int ncode, int dim, int nb0, int nb1, int nb2,
+                                                   const T *__restrict__ P, const int32_t *__restrict__ pt_ptr,
+                                                   const int32_t *__restrict__ pt_rows,
+                                                   const int8_t *__restrict__ jslot, const double *__restrict__ AP,
+                                                   double *__restrict__ Ac) {
+    constexpr int NQ = 27 * BD * BD;
+    __shared__ double red[NQ][4];
+    const int J = blockIdx.x;
+    const int sj = jslot[J];
+    const long nW = (long)n * W;
+    const int nq = ncode * BD * BD;
+    double acc[NQ];
+    for (int q = 0; q < nq; ++q) acc[q] = 0.0;
+    for (int r = pt_ptr[J] + threadIdx.x; r < pt_ptr[J + 1]; r += blockDim.x) {
+        const int i = pt_rows[r];
+        const double *api = AP + (long)i * nq;
+#pragma unroll
+        for (int l = 0; l < BD; ++l) {
+            const double p = (double)P[l * nW + (long)i * W + sj];
+            for (int s = 0; s < ncode; ++s)
+#pragma unroll
+                for (int m = 0; m < BD; ++m) acc[(s * BD + l) * BD + m] = fma(p, api[(s * BD + l) * BD + m], acc[(s * BD + l) * BD + m]);
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int q = 0; q < nq; ++q) {
+        double v = warp_sum(acc[q]);
+        if (lane == 0) red[q][warp] = v;
+    }
     __syncthreads();
-    for (int l = 0; l < BD; ++l)
-        for (int t = threadIdx.x; t < nC; t += blockDim.x) Ac[(long)(J * BD + l) * nC + t] = acc[l * nC + t];
+    // coarse coordinates of J
+    const int j0 = J % nb0, j1 = (J / nb0) % nb1, j2 = dim == 3 ? J / (nb0 * nb1) : 0;
+    const int nC = nc * BD;
+    for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+        const double v = (red[q][0] + red[q][1]) + (red[q][2] + red[q][3]);
+        const int m = q % BD, l = (q / BD) % BD, s = q / (BD * BD);
+        const int r0 = s % 3, r1 = (s / 3) % 3, r2 = s / 9;
+        // the coarse coordinate in {J_d-1, J_d, J_d+1} with residue r_d
+        const int L0 = j0 - 1 + ((r0 - (j0 - 1)) % 3 + 3) % 3;
+        const int L1 = j1 - 1 + ((r1 - (j1 - 1)) % 3 + 3) % 3;
+        const int L2 = dim == 3 ? j2 - 1 + ((r2 - (j2 - 1)) % 3 + 3) % 3 : 0;
+        if (L0 < 0 || L0 >= nb0 || L1 < 0 || L1 >= nb1 || L2 < 0 || L2 >= nb2) continue;
+        const int L = L0 + nb0 * (L1 + nb1 * L2);
+        Ac[(long)(J * BD + l) * nC + L * BD + m] = v;
+    }
 }
 
 template <typename T>
-msrsb_status galerkin(const msrsb_mat *A, int W, int nc, const int32_t *p_ids, const T *P, const int32_t *pt_ptr,
-                      const int32_t *pt_rows, const int8_t *jslot, double *Ac, cudaStream_t s) {
-    int BD = A->bdim;
-    long nC = (long)nc * BD;
-    size_t smem = (size_t)BD * nC * sizeof(double);
-    if (smem > 200 * 1024) return fail(MSRSB_ESHAPE, "coarse system too large for the Galerkin kernel (nC = %ld)", nC);
-    if (BD == 1) {
-        MSRSB_CUDA(cudaFuncSetAttribute(galerkin_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        galerkin_kernel<T, 1><<<nc, 256, smem, s>>>(A->nrows, W, nc, A->rowptr, A->colidx, A->val, p_ids, P, pt_ptr,
-                                                    pt_rows, jslot, Ac);
-    } else {
-        MSRSB_CUDA(cudaFuncSetAttribute(galerkin_kernel<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        galerkin_kernel<T, 3><<<nc, 256, smem, s>>>(A->nrows, W, nc, A->rowptr, A->colidx, A->val, p_ids, P, pt_ptr,
-                                                    pt_rows, jslot, Ac);
+msrsb_status galerkin(const msrsb_mat *A, const msrsb_grid *g, int W, int nc, const int32_t *p_ids, const T *P,
+                      const int32_t *pt_ptr, const int32_t *pt_rows, const int8_t *jslot, double *Ac,
+                      cudaStream_t s) {
+    const int BD = A->bdim, n = A->nrows, dim = g->dim;
+    const int ncode = dim == 3 ? 27 : 9;
+    int nb[3];
+    {
+        int nn[3] = {g->nx, g->ny, dim == 3 ? g->nz : 1};
+        int hh[3] = {g->hx, g->hy, dim == 3 ? g->hz : 1};
+        for (int d = 0; d < 3; ++d)
+            nb[d] = d >= dim ? 1 : (g->centering == 0 ? (nn[d] + hh[d] - 1) / hh[d] : (nn[d] - 1 + hh[d] - 1) / hh[d] + 1);
     }
-    MSRSB_LAUNCHED("galerkin_kernel");
+    if (nb[0] * nb[1] * nb[2] != nc) return fail(MSRSB_ESHAPE, "grid implies %d coarse nodes, got %d", nb[0] * nb[1] * nb[2], nc);
+    const long nC = (long)nc * BD;
+    int8_t *code = nullptr;
+    double *AP = nullptr;
+    MSRSB_TRY(dalloc(&code, nc, s));
+    MSRSB_TRY(dalloc(&AP, (size_t)n * ncode * BD * BD, s));
+    MSRSB_CUDA(cudaMemsetAsync(Ac, 0, (size_t)nC * nC * sizeof(double), s));
+    coarse_code_kernel<<<ceil_div(nc, 256), 256, 0, s>>>(nc, nb[0], nb[1], dim, code);
+    MSRSB_LAUNCHED("coarse_code_kernel");
+    if (BD == 1) {
+        ap_kernel<T, 1><<<ceil_div(n, 128), 128, 0, s>>>(n, W, ncode, A->rowptr, A->colidx, A->val, p_ids, P, code, AP);
+        MSRSB_LAUNCHED("ap_kernel");
+        ptap_kernel<T, 1><<<nc, 128, 0, s>>>(n, W, nc, ncode, dim, nb[0], nb[1], nb[2], P, pt_ptr, pt_rows, jslot, AP,
+                                            Ac);
+        MSRSB_LAUNCHED("ptap_kernel");
+    } else {
+        ap_kernel<T, 3><<<ceil_div(n, 128), 128, 0, s>>>(n, W, ncode, A->rowptr, A->colidx, A->val, p_ids, P, code, AP);
+        MSRSB_LAUNCHED("ap_kernel");
+        ptap_kernel<T, 3><<<nc, 128, 0, s>>>(n, W, nc, ncode, dim, nb[0], nb[1], nb[2], P, pt_ptr, pt_rows, jslot, AP,
+                                            Ac);
+        MSRSB_LAUNCHED("ptap_kernel");
+    }
+    dfree(code, s);
+    dfree(AP, s);
     return MSRSB_OK;
 }
-template msrsb_status galerkin<double>(const msrsb_mat *, int, int, const int32_t *, const double *, const int32_t *,
-                                       const int32_t *, const int8_t *, double *, cudaStream_t);
-template msrsb_status galerkin<float>(const msrsb_mat *, int, int, const int32_t *, const float *, const int32_t *,
-                                      const int32_t *, const int8_t *, double *, cudaStream_t);
+template msrsb_status galerkin<double>(const msrsb_mat *, const msrsb_grid *, int, int, const int32_t *, const double *,
+                                       const int32_t *, const int32_t *, const int8_t *, double *, cudaStream_t);
+template msrsb_status galerkin<float>(const msrsb_mat *, const msrsb_grid *, int, int, const int32_t *, const float *,
+                                      const int32_t *, const int32_t *, const int8_t *, double *, cudaStream_t);
 
 msrsb_status check_mat(const msrsb_mat *A);
 
@@ -143,20 +214,22 @@ msrsb_status check_mat(const msrsb_mat *A);
 
 using namespace msrsb;
 
-extern "C" msrsb_status msrsb_coarse_op(const msrsb_mat *A, const int32_t *p_ids, const void *p_val, int32_t prec,
-                                        int32_t W, int32_t nc, double *Ac_dense, cudaStream_t stream) {
+extern "C" msrsb_status msrsb_coarse_op(const msrsb_mat *A, const msrsb_grid *g, const int32_t *p_ids,
+                                        const void *p_val, int32_t prec, double *Ac_dense, cudaStream_t stream) {
     MSRSB_TRY(check_mat(A));
-    if (!p_ids || !p_val || !Ac_dense) return fail(MSRSB_EINVAL, "NULL argument");
-    if (W != 4 && W != 8) return fail(MSRSB_EINVAL, "W must be 4 or 8");
-    if (nc < 1 || (long)nc * A->bdim > 8192) return fail(MSRSB_ESHAPE, "nc * bdim must be in [1, 8192]");
+    if (!g || !p_ids || !p_val || !Ac_dense) return fail(MSRSB_EINVAL, "NULL argument");
+    int32_t n = 0, nc = 0, W = 0;
+    MSRSB_TRY(msrsb_partition_size(g, &n, &nc, &W));
+    if (n != A->nrows) return fail(MSRSB_ESHAPE, "grid has %d points but A has %d block rows", n, A->nrows);
+    if ((long)nc * A->bdim > 8192) return fail(MSRSB_ESHAPE, "nc * bdim must be <= 8192");
     int32_t *pt_ptr = nullptr, *pt_rows = nullptr;
     int8_t *jslot = nullptr;
     MSRSB_TRY(build_transpose(A->nrows, W, nc, p_ids, &pt_ptr, &pt_rows, &jslot, stream));
     msrsb_status st;
     if (prec == MSRSB_F64)
-        st = galerkin<double>(A, W, nc, p_ids, (const double *)p_val, pt_ptr, pt_rows, jslot, Ac_dense, stream);
+        st = galerkin<double>(A, g, W, nc, p_ids, (const double *)p_val, pt_ptr, pt_rows, jslot, Ac_dense, stream);
     else if (prec == MSRSB_F32)
-        st = galerkin<float>(A, W, nc, p_ids, (const float *)p_val, pt_ptr, pt_rows, jslot, Ac_dense, stream);
+        st = galerkin<float>(A, g, W, nc, p_ids, (const float *)p_val, pt_ptr, pt_rows, jslot, Ac_dense, stream);
     else
         st = fail(MSRSB_EINVAL, "prec must be MSRSB_F64 or MSRSB_F32");
     dfree(pt_ptr, stream);

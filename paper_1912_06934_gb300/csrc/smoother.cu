@@ -76,39 +76,63 @@ __device__ __forceinline__ int find_col(const int32_t *__restrict__ colidx, int 
     return -1;
 }
 
-// Rows of colour c. Elimination order: colour first, then index. Row i is
-// eliminated against every earlier row k in that order (row-wise IKJ); only
-// entries already in A's pattern are updated. Explicitly rounded products
-// keep the result identical to a plain sequential factorisation.
-__global__ void ilu0_colour_kernel(int cnt, const int32_t *__restrict__ rows, int c, const int32_t *__restrict__ rowptr,
-                                   const int32_t *__restrict__ colidx, const uint8_t *__restrict__ colour,
-                                   const int32_t *__restrict__ dpos, double *__restrict__ lu, int *__restrict__ status) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= cnt) return;
+// Rows of colour c, one warp per row (rows of at most 32 entries). Lane l
+// holds entry l of row i (column, colour, value) in registers. Elimination
+// order: colour first, then index. Row i is eliminated against every earlier
+// row k in that order (row-wise IKJ): l_ik = a_ik / u_kk, then every later
+// entry (i, j) that row k also holds is updated; only entries already in A's
+// pattern change. Row k (final, an earlier colour) is read once, coalesced,
+// and matched through warp shuffles. Each entry sees its updates in
+// increasing k and products are explicitly rounded, so the factors equal those
+// of a plain sequential factorisation of the colour-ordered matrix.
+__global__ void __launch_bounds__(128) ilu0_colour_kernel(int cnt, const int32_t *__restrict__ rows, int c,
+                                                          const int32_t *__restrict__ rowptr,
+                                                          const int32_t *__restrict__ colidx,
+                                                          const uint8_t *__restrict__ colour,
+                                                          const int32_t *__restrict__ dpos, double *__restrict__ lu,
+                                                          int *__restrict__ status) {
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (t >= cnt) return;  // whole warps leave together
     const int i = rows[t];
-    const int b = rowptr[i], e_end = rowptr[i + 1];
+    const int b = rowptr[i], len = rowptr[i + 1] - b;
+    if (len > 32) {
+        if (lane == 0) atomicCAS(status, 0, -(1 + i));
+        return;
+    }
+    const bool mine = lane < len;
+    const int j = mine ? colidx[b + lane] : -1;
+    const int cj = mine ? colour[j] : 255;
+    double a = mine ? lu[b + lane] : 0.0;
     for (int cc = 0; cc < c; ++cc) {
-        for (int e = b; e < e_end; ++e) {
-            const int k = colidx[e];
-            if (colour[k] != cc) continue;
+        unsigned m = __ballot_sync(0xffffffffu, cj == cc);  // entries of colour cc, ascending column
+        while (m) {
+            const int q = __ffs(m) - 1;
+            m &= m - 1;
+            const int k = __shfl_sync(0xffffffffu, j, q);
+            const double aik = __shfl_sync(0xffffffffu, a, q);
+            const int kb = rowptr[k], klen = rowptr[k + 1] - kb;
             const double ukk = lu[dpos[k]];
             if (ukk == 0.0) {
-                atomicCAS(status, 0, 1 + k);
+                if (lane == 0) atomicCAS(status, 0, 1 + k);
                 return;
             }
-            const double lik = lu[e] / ukk;
-            lu[e] = lik;
-            const int kb = rowptr[k], ke = rowptr[k + 1];
-            for (int e2 = b; e2 < e_end; ++e2) {
-                const int j = colidx[e2];
-                const int cj = colour[j];
-                if (cj < cc || (cj == cc && j <= k)) continue;  // only entries after k in the order
-                const int q = find_col(colidx, kb, ke, j);
-                if (q >= 0) lu[e2] = __dsub_rn(lu[e2], __dmul_rn(lik, lu[q]));
-            }
+            const double lik = aik / ukk;
+            if (lane == q) a = lik;
+            const int kc = lane < klen ? colidx[kb + lane] : -1;
+            const double kv = lane < klen ? lu[kb + lane] : 0.0;
+            // entries after k in the order: later colour, or same colour and larger index
+            const bool later = mine && (cj > cc || (cj == cc && j > k));
+            // find (k, j) in row k with integer work only (FP64 issue slots are scarce)
+            int hit = -1;
+            for (int r = 0; r < klen; ++r)
+                if (__shfl_sync(0xffffffffu, kc, r) == j) hit = r;
+            const double kvr = __shfl_sync(0xffffffffu, kv, hit >= 0 ? hit : 0);
+            if (later && hit >= 0) a = __dsub_rn(a, __dmul_rn(lik, kvr));
         }
     }
-    if (lu[dpos[i]] == 0.0) atomicCAS(status, 0, 1 + i);
+    if (mine) lu[b + lane] = a;
+    if (lane == 0 && lu[dpos[i]] == 0.0) atomicCAS(status, 0, 1 + i);
 }
 
 template <typename T>
@@ -127,13 +151,10 @@ template msrsb_status convert<float>(long, const double *, float *, cudaStream_t
 template msrsb_status convert<double>(long, const double *, double *, cudaStream_t);
 
 // ILU(0) of the colour-ordered scalar operator; lu_out (T, A's pattern)
-template <typename T>
 msrsb_status ilu0_factor(const msrsb_mat *A, const uint8_t *colour, int ncol, const int32_t *rows,
-                         const int32_t *cptr_h, int32_t *dpos, T *lu_out, cudaStream_t s) {
+                         const int32_t *cptr_h, int32_t *dpos, double *lu, cudaStream_t s) {
     int n = A->nrows;
-    double *lu = nullptr;
     int *status = nullptr;
-    MSRSB_TRY(dalloc(&lu, A->nnz, s));
     MSRSB_TRY(dalloc(&status, 1, s));
     MSRSB_CUDA(cudaMemsetAsync(status, 0, sizeof(int), s));
     MSRSB_CUDA(cudaMemcpyAsync(lu, A->val, (size_t)A->nnz * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -144,7 +165,6 @@ msrsb_status ilu0_factor(const msrsb_mat *A, const uint8_t *colour, int ncol, co
         MSRSB_CUDA(cudaMemcpyAsync(&h0, status, sizeof(int), cudaMemcpyDeviceToHost, s));
         MSRSB_CUDA(cudaStreamSynchronize(s));
         if (h0) {
-            dfree(lu, s);
             dfree(status, s);
             return fail(MSRSB_EINVAL, "ILU(0): row %d has no diagonal entry", h0 - 1);
         }
@@ -152,84 +172,210 @@ msrsb_status ilu0_factor(const msrsb_mat *A, const uint8_t *colour, int ncol, co
     for (int c = 0; c < ncol; ++c) {
         int cnt = cptr_h[c + 1] - cptr_h[c];
         if (cnt == 0) continue;
-        ilu0_colour_kernel<<<ceil_div(cnt, 128), 128, 0, s>>>(cnt, rows + cptr_h[c], c, A->rowptr, A->colidx, colour,
-                                                              dpos, lu, status);
+        ilu0_colour_kernel<<<ceil_div((long)cnt * 32, 128), 128, 0, s>>>(cnt, rows + cptr_h[c], c, A->rowptr,
+                                                                         A->colidx, colour, dpos, lu, status);
         MSRSB_LAUNCHED("ilu0_colour_kernel");
     }
-    MSRSB_TRY(convert<T>(A->nnz, lu, lu_out, s));
     int h = 0;
     MSRSB_CUDA(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s));
     MSRSB_CUDA(cudaStreamSynchronize(s));
-    dfree(lu, s);
     dfree(status, s);
+    if (h < 0) return fail(MSRSB_EINVAL, "ILU(0): row %d has more than 32 entries", -h - 1);
     if (h) return fail(MSRSB_EBREAKDOWN, "ILU(0): zero or missing pivot at row %d", h - 1);
     return MSRSB_OK;
 }
-template msrsb_status ilu0_factor<double>(const msrsb_mat *, const uint8_t *, int, const int32_t *, const int32_t *,
-                                          int32_t *, double *, cudaStream_t);
-template msrsb_status ilu0_factor<float>(const msrsb_mat *, const uint8_t *, int, const int32_t *, const int32_t *,
-                                         int32_t *, float *, cudaStream_t);
 
-// ---- ILU(0) sweeps ------------------------------------------------------------
 
-// forward: y_i = r_i - sum_{colour(k) < c} L_ik y_k  (unit lower)
-template <typename T>
-__global__ void ilu_lower_kernel(int cnt, const int32_t *__restrict__ rows, int c, const int32_t *__restrict__ rowptr,
-                                 const int32_t *__restrict__ colidx, const uint8_t *__restrict__ colour,
-                                 const T *__restrict__ lu, const T *__restrict__ r, T *__restrict__ y) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= cnt) return;
-    int i = rows[t];
-    T acc = r[i];
-    for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
-        int k = colidx[e];
-        if (colour[k] < c) acc = fma(-lu[e], y[k], acc);
-    }
-    y[i] = acc;
+// ---- ILU(0) sweeps on colour-ordered (permuted) vectors -----------------------
+//
+// The factors are stored per colour in ELL blocks over the colour-ordered
+// positions: for colour c with m_c rows starting at position c0, entry slot j
+// of the row at position c0 + r sits at base_c + j * m_c + r (coalesced over
+// consecutive positions). L holds the entries towards earlier colours, U those
+// towards later colours, with column indices already mapped to positions;
+// padding entries have value 0 and point at a position that is final when
+// read. udinv[pos] = 1 / u_ii.
+
+// position of every fine row in the colour order
+__global__ void pos_of_kernel(int n, const int32_t *__restrict__ rows, int32_t *__restrict__ pos) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n) pos[rows[p]] = p;
 }
 
-// backward, in place on y: e_i = (y_i - sum_{colour(k) > c} U_ik e_k) / U_ii; z_i += e_i
-template <typename T>
-__global__ void ilu_upper_kernel(int cnt, const int32_t *__restrict__ rows, int c, const int32_t *__restrict__ rowptr,
-                                 const int32_t *__restrict__ colidx, const uint8_t *__restrict__ colour,
-                                 const T *__restrict__ lu, const int32_t *__restrict__ dpos, T *__restrict__ y,
-                                 double *__restrict__ z) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= cnt) return;
-    int i = rows[t];
-    T acc = y[i];
-    for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
-        int k = colidx[e];
-        if (colour[k] > c) acc = fma(-lu[e], y[k], acc);
+// number of L (earlier-colour) and U (later-colour) entries per row: max per colour
+__global__ void ilu_width_kernel(int n, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                                 const uint8_t *__restrict__ colour, int *__restrict__ wl, int *__restrict__ wu) {
+    __shared__ int s_w[32];
+    if (threadIdx.x < 32) s_w[threadIdx.x] = 0;
+    __syncthreads();
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        int ci = colour[i], nl = 0, nu = 0;
+        for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+            int ck = colour[colidx[e]];
+            nl += ck < ci;
+            nu += ck > ci;
+        }
+        atomicMax(&s_w[ci], nl);  // block-local first: few global atomics
+        atomicMax(&s_w[16 + ci], nu);
     }
-    T ei = acc / lu[dpos[i]];
-    y[i] = ei;
-    z[i] += (double)ei;
+    __syncthreads();
+    if (threadIdx.x < 16) {
+        if (s_w[threadIdx.x]) atomicMax(wl + threadIdx.x, s_w[threadIdx.x]);
+        if (s_w[16 + threadIdx.x]) atomicMax(wu + threadIdx.x, s_w[16 + threadIdx.x]);
+    }
 }
 
 template <typename T>
-msrsb_status ilu0_apply(const msrsb_handle *h, const T *lu, const T *r, T *y, double *z, cudaStream_t s) {
+__global__ void ilu_ell_fill_kernel(int n, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                                    const uint8_t *__restrict__ colour, const double *__restrict__ lu,
+                                    const int32_t *__restrict__ dpos, const int32_t *__restrict__ pos,
+                                    const IluEll E, int32_t *__restrict__ lcol, T *__restrict__ lval,
+                                    int32_t *__restrict__ ucol, T *__restrict__ uval, T *__restrict__ udinv) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int c = colour[i], p = pos[i], r = p - E.cptr[c], m = E.cptr[c + 1] - E.cptr[c];
+    long lb = E.lbase[c], ub = E.ubase[c];
+    int nl = 0, nu = 0;
+    for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+        const int k = colidx[e], ck = colour[k];
+        if (ck < c) {
+            lcol[lb + (long)nl * m + r] = pos[k];
+            lval[lb + (long)nl * m + r] = T(lu[e]);
+            ++nl;
+        } else if (ck > c) {
+            ucol[ub + (long)nu * m + r] = pos[k];
+            uval[ub + (long)nu * m + r] = T(lu[e]);
+            ++nu;
+        }
+    }
+    // padding: a position of colour 0 (final in the forward sweep) for L, of the
+    // last colour (final in the backward sweep) for U
+    for (; nl < E.wl[c]; ++nl) {
+        lcol[lb + (long)nl * m + r] = 0;
+        lval[lb + (long)nl * m + r] = T(0);
+    }
+    for (; nu < E.wu[c]; ++nu) {
+        ucol[ub + (long)nu * m + r] = E.cptr[E.ncol - 1];
+        uval[ub + (long)nu * m + r] = T(0);
+    }
+    udinv[p] = T(1.0 / lu[dpos[i]]);
+}
+
+// Four lanes per row: lane g takes entries g, g+4, ...; shuffle reduction.
+constexpr int kSweepLanes = 4;
+
+__device__ __forceinline__ unsigned group_mask() {
+    return 0xfu << (threadIdx.x & 31 & ~(kSweepLanes - 1));
+}
+
+// forward, colour c: y_p = r_p - sum_j L_pj y_col
+template <typename T>
+__global__ void __launch_bounds__(256) ilu_lower_kernel(int c0, int m, int w, const int32_t *__restrict__ lcol,
+                                                        const T *__restrict__ lval, const T *__restrict__ r,
+                                                        T *__restrict__ y) {
+    const int q = (blockIdx.x * blockDim.x + threadIdx.x) / kSweepLanes;
+    const int g = threadIdx.x % kSweepLanes;
+    if (q >= m) return;  // whole groups leave together
+    T acc = T(0);
+    for (int j = g; j < w; j += kSweepLanes) acc = fma(lval[(long)j * m + q], y[lcol[(long)j * m + q]], acc);
+#pragma unroll
+    for (int o = kSweepLanes / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(group_mask(), acc, o, kSweepLanes);
+    if (g == 0) y[c0 + q] = r[c0 + q] - acc;
+}
+
+// backward, colour c, in place on y: e_p = (y_p - sum_j U_pj e_col) / u_pp;
+// then z[row(p)] += e_p
+template <typename T>
+__global__ void __launch_bounds__(256) ilu_upper_kernel(int c0, int m, int w, const int32_t *__restrict__ ucol,
+                                                        const T *__restrict__ uval, const T *__restrict__ udinv,
+                                                        const int32_t *__restrict__ rows, T *__restrict__ y,
+                                                        double *__restrict__ z) {
+    const int q = (blockIdx.x * blockDim.x + threadIdx.x) / kSweepLanes;
+    const int g = threadIdx.x % kSweepLanes;
+    if (q >= m) return;
+    T acc = T(0);
+    for (int j = g; j < w; j += kSweepLanes) acc = fma(uval[(long)j * m + q], y[ucol[(long)j * m + q]], acc);
+#pragma unroll
+    for (int o = kSweepLanes / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(group_mask(), acc, o, kSweepLanes);
+    if (g == 0) {
+        T e = (y[c0 + q] - acc) * udinv[c0 + q];
+        y[c0 + q] = e;
+        z[rows[c0 + q]] += (double)e;
+    }
+}
+
+// Build the per-colour ELL factors from the natural-order FP64 factors.
+template <typename T>
+msrsb_status ilu_build_ell(msrsb_handle *h, const double *lu, cudaStream_t s) {
     const msrsb_mat &A = h->A;
-    for (int c = 0; c < h->ncolours; ++c) {
-        int cnt = h->colour_ptr_h[c + 1] - h->colour_ptr_h[c];
-        if (!cnt) continue;
-        ilu_lower_kernel<T><<<ceil_div(cnt, 128), 128, 0, s>>>(cnt, h->colour_rows + h->colour_ptr_h[c], c, A.rowptr,
-                                                                A.colidx, h->colour, lu, r, y);
+    const int n = h->n, ncol = h->ncolours;
+    IluEll &E = h->ilu;
+    E.ncol = ncol;
+    int *w = nullptr;
+    MSRSB_TRY(dalloc(&h->pos_of, n, s));
+    MSRSB_TRY(dalloc(&w, 32, s));
+    MSRSB_CUDA(cudaMemsetAsync(w, 0, 32 * sizeof(int), s));
+    pos_of_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, h->colour_rows, h->pos_of);
+    MSRSB_LAUNCHED("pos_of_kernel");
+    ilu_width_kernel<<<ceil_div(n, 1024), 1024, 0, s>>>(n, A.rowptr, A.colidx, h->colour, w, w + 16);
+    MSRSB_LAUNCHED("ilu_width_kernel");
+    int hw[32];
+    MSRSB_CUDA(cudaMemcpyAsync(hw, w, 32 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    MSRSB_CUDA(cudaStreamSynchronize(s));
+    dfree(w, s);
+    long lt = 0, ut = 0;
+    for (int c = 0; c < ncol; ++c) {
+        E.cptr[c] = h->colour_ptr_h[c];
+        E.wl[c] = hw[c];
+        E.wu[c] = hw[16 + c];
+        E.lbase[c] = lt;
+        E.ubase[c] = ut;
+        long m = h->colour_ptr_h[c + 1] - h->colour_ptr_h[c];
+        lt += m * E.wl[c];
+        ut += m * E.wu[c];
+    }
+    E.cptr[ncol] = h->colour_ptr_h[ncol];
+    T *lval = nullptr, *uval = nullptr, *udinv = nullptr;
+    MSRSB_TRY(dalloc(&E.lcol, lt, s));
+    MSRSB_TRY(dalloc(&E.ucol, ut, s));
+    MSRSB_TRY(dalloc(&lval, lt, s));
+    MSRSB_TRY(dalloc(&uval, ut, s));
+    MSRSB_TRY(dalloc(&udinv, n, s));
+    E.lval = lval;
+    E.uval = uval;
+    E.udinv = udinv;
+    ilu_ell_fill_kernel<T><<<ceil_div(n, 256), 256, 0, s>>>(n, A.rowptr, A.colidx, h->colour, lu, h->diag_pos,
+                                                            h->pos_of, E, E.lcol, lval, E.ucol, uval, udinv);
+    MSRSB_LAUNCHED("ilu_ell_fill_kernel");
+    return MSRSB_OK;
+}
+template msrsb_status ilu_build_ell<double>(msrsb_handle *, const double *, cudaStream_t);
+template msrsb_status ilu_build_ell<float>(msrsb_handle *, const double *, cudaStream_t);
+
+// z += U^-1 L^-1 r, r given in colour order (rp), y a colour-order work vector
+template <typename T>
+msrsb_status ilu0_apply(const msrsb_handle *h, const T *rp, T *y, double *z, cudaStream_t s) {
+    const IluEll &E = h->ilu;
+    for (int c = 0; c < E.ncol; ++c) {
+        int m = E.cptr[c + 1] - E.cptr[c];
+        if (!m) continue;
+        ilu_lower_kernel<T><<<ceil_div((long)m * kSweepLanes, 256), 256, 0, s>>>(E.cptr[c], m, E.wl[c], E.lcol + E.lbase[c],
+                                                             (const T *)E.lval + E.lbase[c], rp, y);
         MSRSB_LAUNCHED("ilu_lower_kernel");
     }
-    for (int c = h->ncolours - 1; c >= 0; --c) {
-        int cnt = h->colour_ptr_h[c + 1] - h->colour_ptr_h[c];
-        if (!cnt) continue;
-        ilu_upper_kernel<T><<<ceil_div(cnt, 128), 128, 0, s>>>(cnt, h->colour_rows + h->colour_ptr_h[c], c, A.rowptr,
-                                                                A.colidx, h->colour, lu, h->diag_pos, y, z);
+    for (int c = E.ncol - 1; c >= 0; --c) {
+        int m = E.cptr[c + 1] - E.cptr[c];
+        if (!m) continue;
+        ilu_upper_kernel<T><<<ceil_div((long)m * kSweepLanes, 256), 256, 0, s>>>(E.cptr[c], m, E.wu[c], E.ucol + E.ubase[c],
+                                                             (const T *)E.uval + E.ubase[c], (const T *)E.udinv,
+                                                             h->colour_rows, y, z);
         MSRSB_LAUNCHED("ilu_upper_kernel");
     }
     return MSRSB_OK;
 }
-template msrsb_status ilu0_apply<double>(const msrsb_handle *, const double *, const double *, double *, double *,
-                                         cudaStream_t);
-template msrsb_status ilu0_apply<float>(const msrsb_handle *, const float *, const float *, float *, double *,
-                                        cudaStream_t);
+template msrsb_status ilu0_apply<double>(const msrsb_handle *, const double *, double *, double *, cudaStream_t);
+template msrsb_status ilu0_apply<float>(const msrsb_handle *, const float *, float *, double *, cudaStream_t);
 
 // ---- block (3x3) Gauss-Seidel -------------------------------------------------
 

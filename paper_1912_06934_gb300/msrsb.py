@@ -54,7 +54,7 @@ class c_opts(ctypes.Structure):
 class c_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("bdim", ctypes.c_int32), ("nc", ctypes.c_int32), ("W", ctypes.c_int32),
                 ("basis_iters", ctypes.c_int32), ("basis_e_it", ctypes.c_double),
-                ("n_zero_diag", ctypes.c_int32), ("ncolours", ctypes.c_int32)]
+                ("n_zero_diag", ctypes.c_int32), ("ncolours", ctypes.c_int32), ("phase_ms", ctypes.c_double * 6)]
 
 
 def lib_path():
@@ -182,12 +182,13 @@ def msrsb_build_basis_noalloc(Ahat, p_ids, skel, W, bopts, prec, p_val, stream=N
     return it.value, e.value
 
 
-def msrsb_coarse_op(A, p_ids, p_val, prec, W, nc, stream=None):
+def msrsb_coarse_op(A, g, p_ids, p_val, prec, stream=None):
+    n, nc, W = msrsb_partition_size(g)
     nC = nc * A.bdim
     Ac = torch.empty((nC, nC), dtype=torch.float64, device=A.val.device)
     m = A.c()
-    _check(load().msrsb_coarse_op(ctypes.byref(m), _ptr(p_ids), _ptr(p_val), ctypes.c_int32(prec), ctypes.c_int32(W),
-                                  ctypes.c_int32(nc), _ptr(Ac), _stream(stream)))
+    _check(load().msrsb_coarse_op(ctypes.byref(m), ctypes.byref(g), _ptr(p_ids), _ptr(p_val), ctypes.c_int32(prec),
+                                  _ptr(Ac), _stream(stream)))
     return Ac
 
 
@@ -205,7 +206,9 @@ class Handle:
     def info(self):
         inf = c_info()
         _check(load().msrsb_get_info(self._h, ctypes.byref(inf)))
-        return {k: getattr(inf, k) for k, _ in c_info._fields_}
+        out = {k: getattr(inf, k) for k, _ in c_info._fields_}
+        out["phase_ms"] = list(inf.phase_ms)
+        return out
 
     def apply(self, v, z=None, stream=None):
         z = torch.empty_like(v) if z is None else z

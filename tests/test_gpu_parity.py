@@ -185,7 +185,7 @@ def test_coarse_op_matches_oracle(M):
     p_ids, P, _, _ = _basis_case(M, c, 0, 30)
     A = M.Mat.from_host(c["indptr"], c["indices"], c["data"])
     nc = O.partition(c["dims"], c["H"], 0)["nc"]
-    Ac = M.msrsb_coarse_op(A, p_ids, P, 0, p_ids.shape[1], nc).cpu().numpy()
+    Ac = M.msrsb_coarse_op(A, M.grid(c["dims"], c["H"]), p_ids, P, 0).cpu().numpy()
     ref = O.galerkin(_csr(c), _gpu_P(p_ids, P, nc)).toarray()
     assert np.abs(Ac - ref).max() <= 1e-12 * np.abs(ref).max()
 
