@@ -33,7 +33,7 @@ WORKLOAD = "3D Darcy 64^3 MPFA-O 27-point, ln k GRF (l=8, sigma=3), 10:1 aniso r
 N_GRID, H_BLOCK, SEED = 64, 8, 1002
 RTOL, MAXIT = 1e-8, 300
 BASIS = dict(tol=1e-3, n_it=10, max_iter=100)
-PHASES = ("partition", "filter_basis", "galerkin", "coarse_inverse", "smoother", "workspace")
+PHASES = ("partition", "filter_basis", "galerkin", "coarse_inverse", "workspace", "smoother_wait")
 
 
 def make_problem():
@@ -331,6 +331,41 @@ def reference_arm(args, rank, world):
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def profile_run(args):
+    """Workloads for profilers (no timing output): 'solve' runs the mixed
+    set-up + GMRES solve of the benchmark twice; 'basis' runs three restricted
+    smoothing passes (FP32) on an N^3 grid twice (N = --grid; N = 64 is the
+    benchmark's operator, any other N uses the same generator at that size)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1912_06934_gb300 as M
+    from synth.darcy import darcy_3d_case
+    c = make_problem() if args.grid == N_GRID else darcy_3d_case(n=args.grid, H=H_BLOCK, seed=SEED)
+    A = M.Mat.from_host(c["indptr"], c["indices"], c["data"])
+    g = M.grid(c["dims"], c["H"])
+    if args.profile == "solve":
+        b = torch.as_tensor(c["b"], device="cuda")
+        o = M.opts(prec=M.msrsb.MSRSB_F32, **BASIS)
+        for _ in range(2):
+            h = M.msrsb_setup(A, g, o)
+            r = h.solve(b, rtol=RTOL, maxit=MAXIT)
+            h.destroy()
+        torch.cuda.synchronize()
+        print("profile solve: iters %d relres %.3e" % (r["iters"], r["relres"]))
+    else:
+        ahat, _ = M.msrsb_filter(A)
+        Ah = M.Mat(A.rowptr, A.colidx, ahat)
+        part, cnode, p_ids, skel = M.msrsb_partition(g)
+        P0 = ((p_ids >= 0) & (p_ids == part[:, None].to(torch.int32))).to(torch.float32).contiguous()
+        for _ in range(2):
+            P = P0.clone()
+            it, e = M.msrsb_build_basis(Ah, p_ids, skel, p_ids.shape[1], M.basis_opts(tol=0.0, max_iter=3),
+                                        M.msrsb.MSRSB_F32, P)
+        torch.cuda.synchronize()
+        print("profile basis: n %d passes %d e_it %.4f" % (c["indptr"].shape[0] - 1, it, e))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -338,7 +373,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", choices=["solve", "basis"], default=None,
+                    help="run a workload for a profiler instead of the benchmark")
+    ap.add_argument("--grid", type=int, default=N_GRID, help="grid edge for --profile")
     args = ap.parse_args()
+    if args.profile:
+        profile_run(args)
+        return
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <thread>
 
 namespace msrsb {
 
@@ -86,20 +87,24 @@ msrsb_status galerkin(const msrsb_mat *A, const msrsb_grid *g, int W, int nc, co
                       const int32_t *pt_ptr, const int32_t *pt_rows, const int8_t *jslot, double *Ac,
                       cudaStream_t s);
 msrsb_status coarse_inverse(int n, const double *Ac, double *Ainv, cudaStream_t s);
+msrsb_status coarse_inverse_launch(int n, const double *Ac, double *Ainv, CoarseInverseWork *w, cudaStream_t s);
+msrsb_status coarse_inverse_finish(CoarseInverseWork *w, cudaStream_t s);
 msrsb_status gemv(int n, const double *M, const double *x, double *y, cudaStream_t s);
 msrsb_status colour_classes(int n, const uint8_t *colour, int ncol, int32_t **rows, int32_t *ptr_h, cudaStream_t s);
+template <typename TF>
 msrsb_status ilu0_factor(const msrsb_mat *A, const uint8_t *colour, int ncol, const int32_t *rows,
-                         const int32_t *cptr_h, int32_t *dpos, double *lu, cudaStream_t s);
+                         const int32_t *cptr_h, int32_t *dpos, TF *lu, cudaStream_t s);
 template <typename T>
-msrsb_status ilu_build_ell(msrsb_handle *h, const double *lu, cudaStream_t s);
-template <typename T>
-msrsb_status ilu0_apply(const msrsb_handle *h, const T *rp, T *y, double *z, cudaStream_t s);
-template <typename TO>
-msrsb_status permute_cast(long N, const double *x, const int32_t *perm, TO *y, cudaStream_t s);
+msrsb_status ilu_build_ell(msrsb_handle *h, const T *lu, cudaStream_t s);
+
+template <typename T, typename TZ>
+msrsb_status ilu0_apply(const msrsb_handle *h, const T *rp, T *y, TZ *z, cudaStream_t s);
+template <typename TI, typename TO>
+msrsb_status permute_cast(long N, const TI *x, const int32_t *perm, TO *y, cudaStream_t s);
 template <typename T>
 msrsb_status block_diag_inverse(const msrsb_mat *A, T *dinv, cudaStream_t s);
-template <typename T, typename TA>
-msrsb_status gs_apply(const msrsb_handle *h, const TA *val, const T *dinv, int forward, const T *r, T *e, double *z,
+template <typename T, typename TA, typename TZ>
+msrsb_status gs_apply(const msrsb_handle *h, const TA *val, const T *dinv, int forward, const T *r, T *e, TZ *z,
                       int assign, cudaStream_t s);
 template <typename T>
 msrsb_status convert(long n, const double *a, T *b, cudaStream_t s);
@@ -108,27 +113,68 @@ msrsb_status spmv(const msrsb_mat &A, const TA *val, const TX *x, const TV *v, T
                   const int32_t *operm = nullptr);
 template <typename TP, typename TV>
 msrsb_status restrict_op(const msrsb_handle *h, const TP *P, const TV *v, double *vc, cudaStream_t s);
-template <typename TP>
-msrsb_status prolong_op(const msrsb_handle *h, const TP *P, const double *wc, double *z, int add, cudaStream_t s);
-msrsb_status mdot(long N, int nvec, const double *V, long ldv, const double *w, double *partial, double *out,
-                  int accumulate, cudaStream_t s, const int *gate = nullptr);
-msrsb_status gs_update(long N, int nv, const double *V, long ldv, const double *hs, double *w, double *hcol, int *flag,
+template <typename TP, typename TZ>
+msrsb_status prolong_op(const msrsb_handle *h, const TP *P, const double *wc, TZ *z, int add, cudaStream_t s);
+template <typename TV>
+msrsb_status mdot(long N, int nvec, const TV *V, long ldv, const TV *w, double *partial, double *out, int accumulate,
+                  cudaStream_t s, const int *gate = nullptr);
+template <typename TV>
+msrsb_status gs_update(long N, int nv, const TV *V, long ldv, const double *hs, TV *w, double *hcol, int *flag,
                        int pass, cudaStream_t s);
 msrsb_status norm2(long N, const double *w, double *partial, double *out, cudaStream_t s);
 msrsb_status mvsub(long N, int nvec, const double *V, long ldv, const double *h, double *w, cudaStream_t s);
-msrsb_status mvadd(long N, int nvec, const double *Z, long ldz, const double *y, double *x, cudaStream_t s);
-msrsb_status scale_by_inv(long N, const double *x, const double *den, double *y, cudaStream_t s);
+template <typename TZ>
+msrsb_status mvadd(long N, int nvec, const TZ *Z, long ldz, const double *y, double *x, cudaStream_t s);
+template <typename TY>
+msrsb_status scale_by_inv(long N, const double *x, const double *den, TY *y, cudaStream_t s);
 msrsb_status axpy_dev(long N, const double *num, const double *den, double sign, const double *x, double *y,
                       cudaStream_t s);
 msrsb_status xpay_dev(long N, const double *num, const double *den, const double *z, double *p, cudaStream_t s);
-template <typename TO>
-msrsb_status copy_cast(long N, const double *x, TO *y, cudaStream_t s);
+template <typename TI, typename TO>
+msrsb_status copy_cast(long N, const TI *x, TO *y, cudaStream_t s);
 double *pinned_scratch();
 constexpr int kPinnedDoubles = 8192;  // size of the pinned scratch, in doubles
 
 constexpr int kRedBlocksHost = 304;
 
 // ---- set-up (Alg. 2) ---------------------------------------------------------------------
+
+// Smoother and operator copies: independent of P, so the set-up runs them on
+// a side stream from a second host thread while the basis is built.
+template <typename T>
+static msrsb_status setup_smoother(msrsb_handle *h, cudaStream_t s) {
+    const msrsb_mat &A = h->A;
+    const int n = h->n, bd = h->bdim;
+    h->ncolours = 1 << h->grid.dim;
+    h->colour_ptr_h = (int32_t *)calloc(h->ncolours + 1, sizeof(int32_t));
+    MSRSB_TRY(colour_classes(n, h->colour, h->ncolours, &h->colour_rows, h->colour_ptr_h, s));
+    if (bd == 1) MSRSB_TRY(sell_copy(&A, h->opts.prec == MSRSB_F32, &h->asell, s));
+    if (h->opts.prec == MSRSB_F32 && bd != 1) {
+        float *alo = nullptr;
+        MSRSB_TRY(dalloc(&alo, (size_t)A.nnz * bd * bd, s));
+        MSRSB_TRY(convert<float>((long)A.nnz * bd * bd, A.val, alo, s));
+        h->a_lo = alo;
+    }
+    if (h->opts.smoother == MSRSB_SMOOTH_ILU0) {
+        if (bd != 1) return fail(MSRSB_EINVAL, "ILU(0) smoother needs a scalar operator; use MSRSB_SMOOTH_GS");
+        // factorised in the smoother's precision (FP32 in the mixed form)
+        T *lu = nullptr;
+        MSRSB_TRY(dalloc(&lu, A.nnz, s));
+        MSRSB_TRY(dalloc(&h->diag_pos, n, s));
+        MSRSB_TRY(convert<T>(A.nnz, A.val, lu, s));
+        MSRSB_TRY(ilu0_factor<T>(&A, h->colour, h->ncolours, h->colour_rows, h->colour_ptr_h, h->diag_pos, lu, s));
+        MSRSB_TRY(ilu_build_ell<T>(h, lu, s));
+        dfree(lu, s);
+    } else if (h->opts.smoother == MSRSB_SMOOTH_GS) {
+        if (bd != 3) return fail(MSRSB_EINVAL, "block Gauss-Seidel smoother needs a 3x3 block operator");
+        T *dinv = nullptr;
+        MSRSB_TRY(dalloc(&dinv, (size_t)n * 9, s));
+        h->dinv = dinv;
+        MSRSB_TRY(block_diag_inverse<T>(&A, dinv, s));
+    }
+    MSRSB_CUDA(cudaStreamSynchronize(s));
+    return MSRSB_OK;
+}
 
 template <typename T>
 static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s) {
@@ -153,6 +199,29 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
     MSRSB_TRY(dalloc(&h->colour, n, s));
     MSRSB_TRY(partition_launch(&h->grid, h->part, h->cnode, h->p_ids, h->skel, h->colour, s));
     MSRSB_TRY(mark(1));
+    // the smoother set-up (independent of P) on a side stream, from a second
+    // host thread, while this thread builds the basis
+    if (!h->side) MSRSB_CUDA(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+    cudaEvent_t fork = nullptr, join = nullptr;
+    MSRSB_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    MSRSB_CUDA(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+    MSRSB_CUDA(cudaEventRecord(fork, s));
+    MSRSB_CUDA(cudaStreamWaitEvent(h->side, fork, 0));
+    int dev = 0;
+    MSRSB_CUDA(cudaGetDevice(&dev));
+    msrsb_status side_st = MSRSB_OK;
+    std::string side_err;
+    std::thread side_thread([&]() {
+        cudaSetDevice(dev);
+        side_st = setup_smoother<T>(h, h->side);
+        if (side_st != MSRSB_OK) side_err = msrsb_last_error();
+    });
+    struct Joiner {
+        std::thread &t;
+        ~Joiner() {
+            if (t.joinable()) t.join();
+        }
+    } joiner{side_thread};
     // a1 + a2: filtered operator(s) streamed as sliced ELL, then Alg. 1 per component
     T *P = nullptr;
     MSRSB_TRY(dalloc(&P, nW * bd, s));
@@ -195,36 +264,8 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
     MSRSB_TRY(mark(3));
     MSRSB_TRY(coarse_inverse(h->nC, h->Ac, h->Ainv, s));
     MSRSB_TRY(mark(4));
-    // smoother
-    h->ncolours = 1 << h->grid.dim;
-    h->colour_ptr_h = (int32_t *)calloc(h->ncolours + 1, sizeof(int32_t));
-    MSRSB_TRY(colour_classes(n, h->colour, h->ncolours, &h->colour_rows, h->colour_ptr_h, s));
-    const long N = (long)n * bd;
-    if (bd == 1) MSRSB_TRY(sell_copy(&A, h->opts.prec == MSRSB_F32, &h->asell, s));
-    if (h->opts.prec == MSRSB_F32 && bd != 1) {
-        float *alo = nullptr;
-        MSRSB_TRY(dalloc(&alo, (size_t)A.nnz * bd * bd, s));
-        MSRSB_TRY(convert<float>((long)A.nnz * bd * bd, A.val, alo, s));
-        h->a_lo = alo;
-    }
-    if (h->opts.smoother == MSRSB_SMOOTH_ILU0) {
-        if (bd != 1) return fail(MSRSB_EINVAL, "ILU(0) smoother needs a scalar operator; use MSRSB_SMOOTH_GS");
-        double *lu = nullptr;
-        MSRSB_TRY(dalloc(&lu, A.nnz, s));
-        MSRSB_TRY(dalloc(&h->diag_pos, n, s));
-        MSRSB_CUDA(cudaMemcpyAsync(lu, A.val, (size_t)A.nnz * sizeof(double), cudaMemcpyDeviceToDevice, s));
-        MSRSB_TRY(ilu0_factor(&A, h->colour, h->ncolours, h->colour_rows, h->colour_ptr_h, h->diag_pos, lu, s));
-        MSRSB_TRY(ilu_build_ell<T>(h, lu, s));
-        dfree(lu, s);
-    } else if (h->opts.smoother == MSRSB_SMOOTH_GS) {
-        if (bd != 3) return fail(MSRSB_EINVAL, "block Gauss-Seidel smoother needs a 3x3 block operator");
-        T *dinv = nullptr;
-        MSRSB_TRY(dalloc(&dinv, (size_t)n * 9, s));
-        h->dinv = dinv;
-        MSRSB_TRY(block_diag_inverse<T>(&A, dinv, s));
-    }
-    MSRSB_TRY(mark(5));
     // apply workspaces
+    const long N = (long)n * bd;
     MSRSB_TRY(dalloc(&h->vc, h->nC, s));
     MSRSB_TRY(dalloc(&h->wc, h->nC, s));
     MSRSB_TRY(dalloc(&h->tmp_d, N, s));
@@ -234,6 +275,13 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
     h->r_t = r;
     h->y_t = y;
     MSRSB_TRY(dalloc(&h->partial, (size_t)kRedBlocksHost * 1024, s));
+    MSRSB_TRY(mark(5));
+    side_thread.join();
+    if (side_st != MSRSB_OK) return fail(side_st, "%s", side_err.c_str());
+    MSRSB_CUDA(cudaEventRecord(join, h->side));
+    MSRSB_CUDA(cudaStreamWaitEvent(s, join, 0));
+    cudaEventDestroy(fork);
+    cudaEventDestroy(join);
     MSRSB_TRY(mark(6));
     MSRSB_CUDA(cudaStreamSynchronize(s));
     if (prof) {
@@ -251,19 +299,21 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
 
 // r = v - A z in the handle precision (FP32 values and accumulation in mixed
 // mode); scalar operators use the sliced-ELL copy, optionally writing row i
-// to position operm[i]
-template <typename T>
-static msrsb_status resid_t(const msrsb_handle *h, const T *aval_t, const double *z, const double *v, T *r,
+// to position operm[i]. v and z are FP64 (outer Krylov) or FP32 (inner).
+template <typename T, typename TV>
+static msrsb_status resid_t(const msrsb_handle *h, const T *aval_t, const TV *z, const TV *v, T *r,
                             const int32_t *operm, cudaStream_t s) {
     if (h->bdim == 1) {
         const T *sv = (const T *)h->asell.val[h->opts.prec == MSRSB_F32 ? 1 : 0];
-        return sell_spmv<T, double, double, T, T>(h->asell, sv, z, v, r, true, s, operm);
+        return sell_spmv<T, TV, TV, T, T>(h->asell, sv, z, v, r, true, s, operm);
     }
-    return spmv<T, double, double, T, T>(h->A, aval_t, z, v, r, true, s, operm);
+    return spmv<T, TV, TV, T, T>(h->A, aval_t, z, v, r, true, s, operm);
 }
 
-template <typename T>
-static msrsb_status apply_t(msrsb_handle *h, const double *v, double *z, cudaStream_t s) {
+// Alg. 4 (Alg. 3 inside) from z = 0; the preconditioner's internals run in T,
+// its input and output vectors are TV
+template <typename T, typename TV>
+static msrsb_status apply_t(msrsb_handle *h, const TV *v, TV *z, cudaStream_t s) {
     const msrsb_mat &A = h->A;
     const long N = (long)h->n * h->bdim;
     const T *P = (const T *)h->p_val;
@@ -273,38 +323,38 @@ static msrsb_status apply_t(msrsb_handle *h, const double *v, double *z, cudaStr
     const bool pre = h->opts.pre && (gs || ilu), post = h->opts.post && (gs || ilu);
     if (pre) {
         // z = M_pre^-1 v
-        MSRSB_TRY(copy_cast<T>(N, v, r, s));
         if (gs) {
-            MSRSB_TRY((gs_apply<T, T>(h, aval_t, (const T *)h->dinv, 1, r, y, z, 1, s)));
+            MSRSB_TRY((copy_cast<TV, T>(N, v, r, s)));
+            MSRSB_TRY((gs_apply<T, T, TV>(h, aval_t, (const T *)h->dinv, 1, r, y, z, 1, s)));
         } else {
-            MSRSB_TRY(permute_cast<T>(N, v, h->pos_of, r, s));
-            MSRSB_CUDA(cudaMemsetAsync(z, 0, N * sizeof(double), s));
-            MSRSB_TRY(ilu0_apply<T>(h, r, y, z, s));
+            MSRSB_TRY((permute_cast<TV, T>(N, v, h->pos_of, r, s)));
+            MSRSB_CUDA(cudaMemsetAsync(z, 0, N * sizeof(TV), s));
+            MSRSB_TRY((ilu0_apply<T, TV>(h, r, y, z, s)));
         }
         // coarse correction of the residual v - A z
-        MSRSB_TRY(resid_t<T>(h, aval_t, z, v, r, nullptr, s));
+        MSRSB_TRY((resid_t<T, TV>(h, aval_t, z, v, r, nullptr, s)));
         MSRSB_TRY((restrict_op<T, T>(h, P, r, h->vc, s)));
     } else {
-        MSRSB_TRY((restrict_op<T, double>(h, P, v, h->vc, s)));
+        MSRSB_TRY((restrict_op<T, TV>(h, P, v, h->vc, s)));
     }
     MSRSB_TRY(gemv(h->nC, h->Ainv, h->vc, h->wc, s));
-    MSRSB_TRY(prolong_op<T>(h, P, h->wc, z, pre ? 1 : 0, s));
+    MSRSB_TRY((prolong_op<T, TV>(h, P, h->wc, z, pre ? 1 : 0, s)));
     if (post) {
         if (gs) {
-            MSRSB_TRY(resid_t<T>(h, aval_t, z, v, r, nullptr, s));
-            MSRSB_TRY((gs_apply<T, T>(h, aval_t, (const T *)h->dinv, 0, r, y, z, 0, s)));
+            MSRSB_TRY((resid_t<T, TV>(h, aval_t, z, v, r, nullptr, s)));
+            MSRSB_TRY((gs_apply<T, T, TV>(h, aval_t, (const T *)h->dinv, 0, r, y, z, 0, s)));
         } else {
             // residual written straight into colour order for the sweeps
-            MSRSB_TRY(resid_t<T>(h, aval_t, z, v, r, h->pos_of, s));
-            MSRSB_TRY(ilu0_apply<T>(h, r, y, z, s));
+            MSRSB_TRY((resid_t<T, TV>(h, aval_t, z, v, r, h->pos_of, s)));
+            MSRSB_TRY((ilu0_apply<T, TV>(h, r, y, z, s)));
         }
     }
     return MSRSB_OK;
 }
 
 static msrsb_status apply_any(msrsb_handle *h, const double *v, double *z, cudaStream_t s) {
-    if (h->opts.prec == MSRSB_F32) return apply_t<float>(h, v, z, s);
-    return apply_t<double>(h, v, z, s);
+    if (h->opts.prec == MSRSB_F32) return apply_t<float, double>(h, v, z, s);
+    return apply_t<double, double>(h, v, z, s);
 }
 
 static msrsb_status fine_spmv(const msrsb_handle *h, const double *x, const double *v, double *y, bool resid,
@@ -432,11 +482,19 @@ __global__ void gmres_init_kernel(int m, double *__restrict__ kh, const double *
     g[0] = *beta;
 }
 
-static msrsb_status gmres(msrsb_handle *h, const double *b, double *x, double rtol, int maxit, int *iters,
-                          double *relres, double *hist, cudaStream_t s) {
+// Restarted flexible GMRES with right preconditioning, FP64 Krylov vectors
+// (Z_j = M^-1 V_j kept, so the FP32 preconditioner of the mixed form is
+// handled exactly). Every cycle forms the true residual r = b - A x in FP64
+// (the refinement step of the mixed form) and ends when the rotated residual
+// estimate reaches rtol ||b|| or after m Arnoldi steps; x += Z y in FP64.
+// Iterations counted are Arnoldi steps (preconditioner applications).
+template <typename TV>
+static msrsb_status gmres_t(msrsb_handle *h, const double *b, double *x, double rtol, int maxit, double inner_tol,
+                            TV *V, TV *Z, int *iters, double *relres, double *hist, cudaStream_t s) {
+    static_assert(sizeof(TV) == sizeof(double), "Krylov vectors are FP64");
     const long N = (long)h->n * h->bdim;
     const int m = h->krylov_m;
-    double *V = h->kv, *Z = h->kz, *kh = h->kh;
+    double *kh = h->kh;
     const KhLayout L(m);
     double *H = kh + L.H, *est = kh + L.est, *beta = kh + L.beta, *h2 = kh + L.h2;
     int *reorth = (int *)(kh + L.flag);
@@ -452,7 +510,7 @@ static msrsb_status gmres(msrsb_handle *h, const double *b, double *x, double rt
         return MSRSB_OK;
     }
     for (;;) {
-        // r = b - A x, beta = |r|, V_0 = r / beta
+        // r = b - A x (FP64), beta = |r|, V_0 = r / beta
         MSRSB_TRY(fine_spmv(h, x, b, h->tmp_d, true, s));
         MSRSB_TRY(norm2(N, h->tmp_d, h->partial, beta, s));
         double bt = 0.0;
@@ -464,14 +522,16 @@ static msrsb_status gmres(msrsb_handle *h, const double *b, double *x, double rt
             *iters = its;
             return fail(MSRSB_ENOCONV, "GMRES reached %d iterations (relres %.3e)", its, bt / bnorm);
         }
-        MSRSB_TRY(scale_by_inv(N, h->tmp_d, beta, V, s));
+        MSRSB_TRY(scale_by_inv<TV>(N, h->tmp_d, beta, V, s));
         gmres_init_kernel<<<1, 1, 0, s>>>(m, kh, beta);
         MSRSB_LAUNCHED("gmres_init_kernel");
-        int mm = m < maxit - its ? m : maxit - its;
+        const int mm = m < maxit - its ? m : maxit - its;
+        const double stop = inner_tol > 0.0 ? std::max(inner_tol * bt, rtol * bnorm) : rtol * bnorm;
         // Arnoldi steps are launched back to back; the residual estimate of
         // step j is copied to pinned memory behind an event and looked at
-        // without blocking before later launches. Steps launched after the
-        // first converged one only add columns the solve below ignores.
+        // without blocking before later launches (at most two steps ahead).
+        // Steps launched after the first converged one only add columns the
+        // solve below ignores.
         double *pin = pinned_scratch();
         double *pin_est = pin ? pin + 16 : nullptr;
         cudaEvent_t *evs = event_pool(mm);
@@ -482,14 +542,12 @@ static msrsb_status gmres(msrsb_handle *h, const double *b, double *x, double rt
                 while (checked < launched) {
                     if (cudaEventQuery(evs[checked]) != cudaSuccess) {
                         cudaGetLastError();
-                        // keep the host at most two steps ahead, so at most two
-                        // steps are spent after convergence
                         if (launched - checked <= 2) break;
                         MSRSB_CUDA(cudaEventSynchronize(evs[checked]));
                     }
                     double e = ((volatile double *)pin_est)[checked];
                     if (!std::isfinite(e)) return fail(MSRSB_ENAN, "non-finite residual estimate in GMRES");
-                    if (e <= rtol * bnorm) {
+                    if (e <= stop) {
                         conv = checked;
                         break;
                     }
@@ -497,7 +555,7 @@ static msrsb_status gmres(msrsb_handle *h, const double *b, double *x, double rt
                 }
                 if (conv >= 0) break;
             }
-            double *Vj = V + j * N, *Zj = Z + j * N, *w = V + (j + 1) * N;
+            TV *Vj = V + j * N, *Zj = Z + j * N, *w = V + (j + 1) * N;
             MSRSB_TRY(apply_any(h, Vj, Zj, s));
             MSRSB_TRY(fine_spmv(h, Zj, nullptr, w, false, s));
             double *hcol = H + (long)j * (m + 1);
@@ -505,10 +563,10 @@ static msrsb_status gmres(msrsb_handle *h, const double *b, double *x, double rt
             // one multi-dot pass (V_0..V_j and w itself, stored as V_{j+1})
             // and one fused update + normalisation; the second pass runs on
             // the device only when the first lost more than half of |w|^2
-            MSRSB_TRY(mdot(N, j + 2, V, N, w, h->partial, h2, 0, s));
-            MSRSB_TRY(gs_update(N, j + 1, V, N, h2, w, hcol, reorth, 1, s));
-            MSRSB_TRY(mdot(N, j + 2, V, N, w, h->partial, h2, 0, s, reorth));
-            MSRSB_TRY(gs_update(N, j + 1, V, N, h2, w, hcol, reorth, 2, s));
+            MSRSB_TRY(mdot<TV>(N, j + 2, V, N, w, h->partial, h2, 0, s));
+            MSRSB_TRY(gs_update<TV>(N, j + 1, V, N, h2, w, hcol, reorth, 1, s));
+            MSRSB_TRY(mdot<TV>(N, j + 2, V, N, w, h->partial, h2, 0, s, reorth));
+            MSRSB_TRY(gs_update<TV>(N, j + 1, V, N, h2, w, hcol, reorth, 2, s));
             givens_kernel<<<1, 32, 0, s>>>(m, j, kh);
             MSRSB_LAUNCHED("givens_kernel");
             launched = j + 1;
@@ -520,7 +578,7 @@ static msrsb_status gmres(msrsb_handle *h, const double *b, double *x, double rt
                 MSRSB_TRY(read_scalar(est, &e, s));
                 if (!std::isfinite(e)) return fail(MSRSB_ENAN, "non-finite residual estimate in GMRES");
                 if (hist) hist[its + j + 1] = e / bnorm;
-                if (e <= rtol * bnorm) {
+                if (e <= stop) {
                     conv = j;
                     break;
                 }
@@ -533,7 +591,7 @@ static msrsb_status gmres(msrsb_handle *h, const double *b, double *x, double rt
                 if (hist && (conv < 0 || q <= conv)) hist[its + q + 1] = e / bnorm;
                 if (conv < 0 && q >= checked) {
                     if (!std::isfinite(e)) return fail(MSRSB_ENAN, "non-finite residual estimate in GMRES");
-                    if (e <= rtol * bnorm) conv = q;
+                    if (e <= stop) conv = q;
                 }
             }
         }
@@ -541,10 +599,15 @@ static msrsb_status gmres(msrsb_handle *h, const double *b, double *x, double rt
         its += k;
         hess_solve_kernel<<<1, 1, 0, s>>>(m, k, kh);
         MSRSB_LAUNCHED("hess_solve_kernel");
-        MSRSB_TRY(mvadd(N, k, Z, N, kh + L.g, x, s));
+        MSRSB_TRY(mvadd<TV>(N, k, Z, N, kh + L.g, x, s));
     }
     *iters = its;
     return MSRSB_OK;
+}
+
+static msrsb_status gmres(msrsb_handle *h, const double *b, double *x, double rtol, int maxit, int *iters,
+                          double *relres, double *hist, cudaStream_t s) {
+    return gmres_t<double>(h, b, x, rtol, maxit, 0.0, h->kv, h->kz, iters, relres, hist, s);
 }
 
 // ---- PCG ------------------------------------------------------------------------
@@ -676,6 +739,7 @@ static void handle_free(msrsb_handle *h) {
     }
     free(h->colour_ptr_h);
     cudaStreamSynchronize(s);
+    if (h->side) cudaStreamDestroy(h->side);
     delete h;
 }
 
@@ -737,8 +801,9 @@ extern "C" msrsb_status msrsb_setup(const msrsb_mat *A, const msrsb_grid *g, con
     msrsb_status st = opts->prec == MSRSB_F32 ? setup_t<float>(h, p_init, stream) : setup_t<double>(h, p_init, stream);
     if (st == MSRSB_OK) {
         const long N = (long)n * A->bdim;
-        st = dalloc(&h->kv, (size_t)(m + 1 > 4 ? m + 1 : 4) * N, stream);
-        if (st == MSRSB_OK) st = dalloc(&h->kz, (size_t)m * N, stream);
+        const bool gm = opts->krylov == MSRSB_GMRES;
+        st = dalloc(&h->kv, (size_t)(gm ? m + 1 : 4) * N, stream);
+        if (st == MSRSB_OK && gm) st = dalloc(&h->kz, (size_t)m * N, stream);
         if (st == MSRSB_OK) st = dalloc(&h->kh, (size_t)KhLayout(m).total, stream);
     }
     if (st != MSRSB_OK) {

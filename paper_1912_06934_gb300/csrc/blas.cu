@@ -104,6 +104,9 @@ template msrsb_status spmv<double, double, double, double, double>(const msrsb_m
 template msrsb_status spmv<float, double, double, float, float>(const msrsb_mat &, const float *, const double *,
                                                                 const double *, float *, bool, cudaStream_t,
                                                                 const int32_t *);
+template msrsb_status spmv<float, float, float, float, float>(const msrsb_mat &, const float *, const float *,
+                                                              const float *, float *, bool, cudaStream_t,
+                                                              const int32_t *);
 
 // Sliced-ELL SpMV / residual: one thread per row, coalesced entry reads,
 // unrolled so several gathers are in flight. y[operm ? operm[i] : i] =
@@ -149,6 +152,9 @@ template msrsb_status sell_spmv<double, double, double, double, double>(const Se
 template msrsb_status sell_spmv<float, double, double, float, float>(const Sell &, const float *, const double *,
                                                                      const double *, float *, bool, cudaStream_t,
                                                                      const int32_t *);
+template msrsb_status sell_spmv<float, float, float, float, float>(const Sell &, const float *, const float *,
+                                                                   const float *, float *, bool, cudaStream_t,
+                                                                   const int32_t *);
 
 // ---- restriction and prolongation ------------------------------------------------
 
@@ -210,10 +216,10 @@ template msrsb_status restrict_op<float, float>(const msrsb_handle *, const floa
 
 // z[i*bd + l] (+)= sum_s P^l_{is} wc[ids_is*bd + l]; the ids and values of
 // a row are read as 16-byte vectors
-template <typename TP, int W>
+template <typename TP, typename TZ, int W>
 __global__ void __launch_bounds__(256) prolong_kernel(int n, int bd, const int32_t *__restrict__ p_ids,
                                                       const TP *__restrict__ P, const double *__restrict__ wc,
-                                                      double *__restrict__ z, int add) {
+                                                      TZ *__restrict__ z, int add) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const long nW = (long)n * W;
@@ -233,23 +239,25 @@ __global__ void __launch_bounds__(256) prolong_kernel(int n, int bd, const int32
         for (int c = 0; c < W; ++c)
             if (ids[c] >= 0) s = fma((double)pv[c], wc[(long)ids[c] * bd + l], s);
         const long o = (long)i * bd + l;
-        z[o] = add ? z[o] + s : s;
+        z[o] = add ? TZ(z[o] + s) : TZ(s);
     }
 }
 
-template <typename TP>
-msrsb_status prolong_op(const msrsb_handle *h, const TP *P, const double *wc, double *z, int add, cudaStream_t s) {
+template <typename TP, typename TZ>
+msrsb_status prolong_op(const msrsb_handle *h, const TP *P, const double *wc, TZ *z, int add, cudaStream_t s) {
     if (h->W == 8)
-        prolong_kernel<TP, 8><<<ceil_div(h->n, 256), 256, 0, s>>>(h->n, h->bdim, h->p_ids, P, wc, z, add);
+        prolong_kernel<TP, TZ, 8><<<ceil_div(h->n, 256), 256, 0, s>>>(h->n, h->bdim, h->p_ids, P, wc, z, add);
     else
-        prolong_kernel<TP, 4><<<ceil_div(h->n, 256), 256, 0, s>>>(h->n, h->bdim, h->p_ids, P, wc, z, add);
+        prolong_kernel<TP, TZ, 4><<<ceil_div(h->n, 256), 256, 0, s>>>(h->n, h->bdim, h->p_ids, P, wc, z, add);
     MSRSB_LAUNCHED("prolong_kernel");
     return MSRSB_OK;
 }
-template msrsb_status prolong_op<double>(const msrsb_handle *, const double *, const double *, double *, int,
-                                         cudaStream_t);
-template msrsb_status prolong_op<float>(const msrsb_handle *, const float *, const double *, double *, int,
-                                        cudaStream_t);
+template msrsb_status prolong_op<double, double>(const msrsb_handle *, const double *, const double *, double *, int,
+                                                 cudaStream_t);
+template msrsb_status prolong_op<float, double>(const msrsb_handle *, const float *, const double *, double *, int,
+                                                cudaStream_t);
+template msrsb_status prolong_op<float, float>(const msrsb_handle *, const float *, const double *, float *, int,
+                                               cudaStream_t);
 
 // ---- dense vector kernels for the Krylov loop ---------------------------------------
 
@@ -258,16 +266,17 @@ constexpr int kRedBlocks = 76;  // fixed number of row chunks (partial sums): fi
 // partial[j * gridDim.x + b] = sum over row chunk b of V_j[i] * w[i];
 // blockIdx.y = vector j. One block reduction per CTA, fixed order. When
 // `gate` is given the kernel does nothing unless *gate != 0.
-__global__ void __launch_bounds__(256) mdot_kernel(long N, const double *__restrict__ V, long ldv,
-                                                   const double *__restrict__ w, double *__restrict__ partial,
+template <typename TV>
+__global__ void __launch_bounds__(256) mdot_kernel(long N, const TV *__restrict__ V, long ldv,
+                                                   const TV *__restrict__ w, double *__restrict__ partial,
                                                    const int *__restrict__ gate) {
     if (gate && !*gate) return;
     __shared__ double red[8];
     const int j = blockIdx.y;
     const long chunk = (N + gridDim.x - 1) / gridDim.x;
     const long b0 = blockIdx.x * chunk, b1 = b0 + chunk < N ? b0 + chunk : N;
-    const double *vj = V + j * ldv;
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    const TV *vj = V + j * ldv;
+    TV s0 = 0, s1 = 0, s2 = 0, s3 = 0;
     const long bd = blockDim.x;
     long i = b0 + threadIdx.x;
     for (; i + 3 * bd < b1; i += 4 * bd) {
@@ -279,7 +288,7 @@ __global__ void __launch_bounds__(256) mdot_kernel(long N, const double *__restr
     for (; i < b1; i += bd) s0 = fma(vj[i], w[i], s0);
     s0 += s2;
     s1 += s3;
-    double s = warp_sum(s0 + s1);
+    double s = warp_sum((double)(s0 + s1));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
     __syncthreads();
     if (threadIdx.x < 32) {
@@ -311,19 +320,24 @@ __global__ void reduce_partials_kernel(int nblk, const double *__restrict__ part
 }
 
 // out[j] (+)= V_j . w for j < nvec (gate: run only if *gate != 0)
-msrsb_status mdot(long N, int nvec, const double *V, long ldv, const double *w, double *partial, double *out,
-                  int accumulate, cudaStream_t s, const int *gate) {
+template <typename TV>
+msrsb_status mdot(long N, int nvec, const TV *V, long ldv, const TV *w, double *partial, double *out, int accumulate,
+                  cudaStream_t s, const int *gate) {
     dim3 grid(kRedBlocks, nvec);
-    mdot_kernel<<<grid, 256, 0, s>>>(N, V, ldv, w, partial, gate);
+    mdot_kernel<TV><<<grid, 256, 0, s>>>(N, V, ldv, w, partial, gate);
     MSRSB_LAUNCHED("mdot_kernel");
     reduce_partials_kernel<<<nvec, 256, 0, s>>>(kRedBlocks, partial, out, accumulate, 0, gate);
     MSRSB_LAUNCHED("reduce_partials_kernel");
     return MSRSB_OK;
 }
+template msrsb_status mdot<double>(long, int, const double *, long, const double *, double *, double *, int,
+                                   cudaStream_t, const int *);
+template msrsb_status mdot<float>(long, int, const float *, long, const float *, double *, double *, int, cudaStream_t,
+                                  const int *);
 
 msrsb_status norm2(long N, const double *w, double *partial, double *out, cudaStream_t s) {
     dim3 grid(kRedBlocks, 1);
-    mdot_kernel<<<grid, 256, 0, s>>>(N, w, N, w, partial, nullptr);
+    mdot_kernel<double><<<grid, 256, 0, s>>>(N, w, N, w, partial, nullptr);
     MSRSB_LAUNCHED("mdot_kernel");
     reduce_partials_kernel<<<1, 256, 0, s>>>(kRedBlocks, partial, out, 0, 1, nullptr);
     MSRSB_LAUNCHED("reduce_partials_kernel");
@@ -337,14 +351,19 @@ msrsb_status norm2(long N, const double *w, double *partial, double *out, cudaSt
 // the same pass and H(nv, col) is set, else it is left unnormalised and *flag
 // = 1 asks for a second pass (pass 2 always normalises). Pass 1 writes H(0..nv-1,
 // col) = hs, pass 2 adds its coefficients. Every CTA takes the same decision.
-__global__ void __launch_bounds__(256) gs_update_kernel(long N, int nv, const double *__restrict__ V, long ldv,
-                                                        const double *__restrict__ hs, double *__restrict__ w,
+template <typename TV>
+__global__ void __launch_bounds__(256) gs_update_kernel(long N, int nv, const TV *__restrict__ V, long ldv,
+                                                        const double *__restrict__ hs, TV *__restrict__ w,
                                                         double *__restrict__ hcol, int *__restrict__ flag, int pass) {
     if (pass == 2 && !*flag) return;
     __shared__ double hsh[1024];
+    __shared__ TV hst[1024];
     __shared__ double s_scale;
     __shared__ int s_norm;
-    for (int q = threadIdx.x; q < nv; q += blockDim.x) hsh[q] = hs[q];
+    for (int q = threadIdx.x; q < nv; q += blockDim.x) {
+        hsh[q] = hs[q];
+        hst[q] = TV(hs[q]);
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         double pr = 0.0;
@@ -362,28 +381,33 @@ __global__ void __launch_bounds__(256) gs_update_kernel(long N, int nv, const do
         }
     }
     __syncthreads();
-    const double sc = s_scale;
+    const TV sc = TV(s_scale);
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        TV a0 = 0, a1 = 0, a2 = 0, a3 = 0;
         int q = 0;
         for (; q + 3 < nv; q += 4) {
-            a0 = fma(V[q * ldv + i], hsh[q], a0);
-            a1 = fma(V[(q + 1) * ldv + i], hsh[q + 1], a1);
-            a2 = fma(V[(q + 2) * ldv + i], hsh[q + 2], a2);
-            a3 = fma(V[(q + 3) * ldv + i], hsh[q + 3], a3);
+            a0 = fma(V[q * ldv + i], hst[q], a0);
+            a1 = fma(V[(q + 1) * ldv + i], hst[q + 1], a1);
+            a2 = fma(V[(q + 2) * ldv + i], hst[q + 2], a2);
+            a3 = fma(V[(q + 3) * ldv + i], hst[q + 3], a3);
         }
-        for (; q < nv; ++q) a0 = fma(V[q * ldv + i], hsh[q], a0);
+        for (; q < nv; ++q) a0 = fma(V[q * ldv + i], hst[q], a0);
         w[i] = (w[i] - ((a0 + a1) + (a2 + a3))) * sc;
     }
 }
 
-msrsb_status gs_update(long N, int nv, const double *V, long ldv, const double *hs, double *w, double *hcol, int *flag,
+template <typename TV>
+msrsb_status gs_update(long N, int nv, const TV *V, long ldv, const double *hs, TV *w, double *hcol, int *flag,
                        int pass, cudaStream_t s) {
-    gs_update_kernel<<<ceil_div(N, 256) < 2048 ? ceil_div(N, 256) : 2048, 256, 0, s>>>(N, nv, V, ldv, hs, w, hcol,
-                                                                                       flag, pass);
+    gs_update_kernel<TV><<<ceil_div(N, 256) < 2048 ? ceil_div(N, 256) : 2048, 256, 0, s>>>(N, nv, V, ldv, hs, w, hcol,
+                                                                                           flag, pass);
     MSRSB_LAUNCHED("gs_update_kernel");
     return MSRSB_OK;
 }
+template msrsb_status gs_update<double>(long, int, const double *, long, const double *, double *, double *, int *, int,
+                                        cudaStream_t);
+template msrsb_status gs_update<float>(long, int, const float *, long, const double *, float *, double *, int *, int,
+                                       cudaStream_t);
 
 // w -= sum_j V_j h[j]  (h staged in shared memory)
 __global__ void mvsub_kernel(long N, int nvec, const double *__restrict__ V, long ldv, const double *__restrict__ h,
@@ -404,8 +428,9 @@ msrsb_status mvsub(long N, int nvec, const double *V, long ldv, const double *h,
     return MSRSB_OK;
 }
 
-// x += sum_j Z_j y[j]  (y staged in shared memory)
-__global__ void mvadd_kernel(long N, int nvec, const double *__restrict__ Z, long ldz, const double *__restrict__ y,
+// x += sum_j Z_j y[j]  (y staged in shared memory), x FP64
+template <typename TZ>
+__global__ void mvadd_kernel(long N, int nvec, const TZ *__restrict__ Z, long ldz, const double *__restrict__ y,
                              double *__restrict__ x) {
     __shared__ double ys[1024];
     for (int j = threadIdx.x; j < nvec; j += blockDim.x) ys[j] = y[j];
@@ -413,29 +438,36 @@ __global__ void mvadd_kernel(long N, int nvec, const double *__restrict__ Z, lon
     long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (i >= N) return;
     double s = 0.0;
-    for (int j = 0; j < nvec; ++j) s = fma(Z[j * ldz + i], ys[j], s);
+    for (int j = 0; j < nvec; ++j) s = fma((double)Z[j * ldz + i], ys[j], s);
     x[i] += s;
 }
 
-msrsb_status mvadd(long N, int nvec, const double *Z, long ldz, const double *y, double *x, cudaStream_t s) {
-    mvadd_kernel<<<ceil_div(N, 256), 256, 0, s>>>(N, nvec, Z, ldz, y, x);
+template <typename TZ>
+msrsb_status mvadd(long N, int nvec, const TZ *Z, long ldz, const double *y, double *x, cudaStream_t s) {
+    mvadd_kernel<TZ><<<ceil_div(N, 256), 256, 0, s>>>(N, nvec, Z, ldz, y, x);
     MSRSB_LAUNCHED("mvadd_kernel");
     return MSRSB_OK;
 }
+template msrsb_status mvadd<double>(long, int, const double *, long, const double *, double *, cudaStream_t);
+template msrsb_status mvadd<float>(long, int, const float *, long, const double *, double *, cudaStream_t);
 
-// y = x * (1 / *den)  (den on the device)
-__global__ void scale_kernel(long N, const double *__restrict__ x, const double *__restrict__ den, double *__restrict__ y) {
+// y = x / *den  (den on the device); y may be a narrower type
+template <typename TY>
+__global__ void scale_kernel(long N, const double *__restrict__ x, const double *__restrict__ den, TY *__restrict__ y) {
     long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (i >= N) return;
     double d = *den;
-    y[i] = d != 0.0 ? x[i] / d : 0.0;
+    y[i] = TY(d != 0.0 ? x[i] / d : 0.0);
 }
 
-msrsb_status scale_by_inv(long N, const double *x, const double *den, double *y, cudaStream_t s) {
-    scale_kernel<<<ceil_div(N, 256), 256, 0, s>>>(N, x, den, y);
+template <typename TY>
+msrsb_status scale_by_inv(long N, const double *x, const double *den, TY *y, cudaStream_t s) {
+    scale_kernel<TY><<<ceil_div(N, 256), 256, 0, s>>>(N, x, den, y);
     MSRSB_LAUNCHED("scale_kernel");
     return MSRSB_OK;
 }
+template msrsb_status scale_by_inv<double>(long, const double *, const double *, double *, cudaStream_t);
+template msrsb_status scale_by_inv<float>(long, const double *, const double *, float *, cudaStream_t);
 
 // y = a*x + y with a = num/den on the device (sign applied)
 __global__ void axpy_dev_kernel(long N, const double *__restrict__ num, const double *__restrict__ den, double sign,
@@ -469,35 +501,37 @@ msrsb_status xpay_dev(long N, const double *num, const double *den, const double
 }
 
 // y[perm[i]] = TO(x[i])
-template <typename TO>
-__global__ void permute_cast_kernel(long N, const double *__restrict__ x, const int32_t *__restrict__ perm,
+template <typename TI, typename TO>
+__global__ void permute_cast_kernel(long N, const TI *__restrict__ x, const int32_t *__restrict__ perm,
                                     TO *__restrict__ y) {
     long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (i < N) y[perm[i]] = TO(x[i]);
 }
 
-template <typename TO>
-msrsb_status permute_cast(long N, const double *x, const int32_t *perm, TO *y, cudaStream_t s) {
-    permute_cast_kernel<TO><<<ceil_div(N, 256), 256, 0, s>>>(N, x, perm, y);
+template <typename TI, typename TO>
+msrsb_status permute_cast(long N, const TI *x, const int32_t *perm, TO *y, cudaStream_t s) {
+    permute_cast_kernel<TI, TO><<<ceil_div(N, 256), 256, 0, s>>>(N, x, perm, y);
     MSRSB_LAUNCHED("permute_cast_kernel");
     return MSRSB_OK;
 }
-template msrsb_status permute_cast<float>(long, const double *, const int32_t *, float *, cudaStream_t);
-template msrsb_status permute_cast<double>(long, const double *, const int32_t *, double *, cudaStream_t);
+template msrsb_status permute_cast<double, float>(long, const double *, const int32_t *, float *, cudaStream_t);
+template msrsb_status permute_cast<double, double>(long, const double *, const int32_t *, double *, cudaStream_t);
+template msrsb_status permute_cast<float, float>(long, const float *, const int32_t *, float *, cudaStream_t);
 
-template <typename TO>
-__global__ void copy_cast_kernel(long N, const double *__restrict__ x, TO *__restrict__ y) {
+template <typename TI, typename TO>
+__global__ void copy_cast_kernel(long N, const TI *__restrict__ x, TO *__restrict__ y) {
     long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (i < N) y[i] = TO(x[i]);
 }
 
-template <typename TO>
-msrsb_status copy_cast(long N, const double *x, TO *y, cudaStream_t s) {
-    copy_cast_kernel<TO><<<ceil_div(N, 256), 256, 0, s>>>(N, x, y);
+template <typename TI, typename TO>
+msrsb_status copy_cast(long N, const TI *x, TO *y, cudaStream_t s) {
+    copy_cast_kernel<TI, TO><<<ceil_div(N, 256), 256, 0, s>>>(N, x, y);
     MSRSB_LAUNCHED("copy_cast_kernel");
     return MSRSB_OK;
 }
-template msrsb_status copy_cast<float>(long, const double *, float *, cudaStream_t);
-template msrsb_status copy_cast<double>(long, const double *, double *, cudaStream_t);
+template msrsb_status copy_cast<double, float>(long, const double *, float *, cudaStream_t);
+template msrsb_status copy_cast<double, double>(long, const double *, double *, cudaStream_t);
+template msrsb_status copy_cast<float, float>(long, const float *, float *, cudaStream_t);
 
 }  // namespace msrsb

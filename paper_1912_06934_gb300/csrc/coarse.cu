@@ -12,26 +12,32 @@ namespace cg = cooperative_groups;
 
 namespace msrsb {
 
+double *pinned_scratch();
+
 // Blocked Gauss-Jordan inversion with partial pivoting (ties to the lowest
 // row), column-major, in place. Step k (pivot row p): swap rows k and p; the
 // swapped column k is f; then every column j != k becomes
 //   x_k <- x_k / f_k,  x_i <- x_i - f_i x_k (i != k)
 // and column k becomes 1/f_k at row k and -f_i / f_k elsewhere, which leaves
 // A^-1 (with the row interchanges still to be undone on the columns).
-// Steps are taken GJ_NB at a time: every CTA loads the panel of GJ_NB columns,
-// factors it redundantly in shared memory (recording each step's pivot and
-// column f), writes back the panel columns it owns and applies the recorded
-// steps to its own other columns. One grid-wide barrier per panel.
-constexpr int GJ_NB = 4;
+// Steps are taken GJ_NB at a time: CTA 0 factors the panel of GJ_NB columns in
+// shared memory and publishes each step's pivot, 1/pivot and column f; after a
+// grid-wide barrier every CTA applies those steps to the columns it owns,
+// staged in shared memory; a second barrier ends the panel. (FP64 issue slots
+// are scarce on this GPU, so the panel is factored once, not in every CTA.)
+constexpr int GJ_NB = 8;
 constexpr int GJ_OWN = 4;  // own columns staged in shared memory at a time
 
+// Index of the largest |col[i]|, k <= i < n, ties to the lowest index. The
+// magnitudes are compared as the integer bit patterns of |x| (IEEE order of
+// non-negative doubles), keeping the search off the scarce FP64 pipe.
 __device__ __forceinline__ void block_argmax(const double *__restrict__ col, int k, int n, double *s_best, int *s_idx,
                                              double *best_out, int *idx_out) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    double best = -1.0;
+    long long best = -1;
     int bi = n;
     for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
-        double v = fabs(col[i]);
+        const long long v = __double_as_longlong(col[i]) & 0x7fffffffffffffffLL;
         if (v > best) {
             best = v;
             bi = i;
@@ -39,63 +45,201 @@ __device__ __forceinline__ void block_argmax(const double *__restrict__ col, int
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        double b2 = __shfl_xor_sync(0xffffffffu, best, o);
-        int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+        const long long b2 = __shfl_xor_sync(0xffffffffu, best, o);
+        const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
         if (b2 > best || (b2 == best && i2 < bi)) {
             best = b2;
             bi = i2;
         }
     }
+    long long *sb = reinterpret_cast<long long *>(s_best);
     if (lane == 0) {
-        s_best[warp] = best;
+        sb[warp] = best;
         s_idx[warp] = bi;
     }
     __syncthreads();
-    best = s_best[0];
+    best = sb[0];
     bi = s_idx[0];
     for (int w = 1; w < nw; ++w)
-        if (s_best[w] > best || (s_best[w] == best && s_idx[w] < bi)) {
-            best = s_best[w];
+        if (sb[w] > best || (sb[w] == best && s_idx[w] < bi)) {
+            best = sb[w];
             bi = s_idx[w];
         }
-    *best_out = best;
+    *best_out = __longlong_as_double(best < 0 ? 0 : best);
     *idx_out = bi;
     __syncthreads();  // s_best / s_idx may be reused right after
 }
 
+// Fg[GJ_NB][n]: the panel's f columns; pg[GJ_NB]: pivots; ig[GJ_NB]: 1 / pivots
 __global__ void __launch_bounds__(256) gauss_jordan_kernel(int n, double *__restrict__ X, int *__restrict__ perm,
-                                                           int *__restrict__ status) {
+                                                           double *__restrict__ Fg, int *__restrict__ pg,
+                                                           double *__restrict__ ig, int *__restrict__ status) {
     cg::grid_group grid = cg::this_grid();
     extern __shared__ double sm[];
-    double *Pn = sm;              // panel columns, [GJ_NB][n]
-    double *F = sm + GJ_NB * n;   // column f of every step, [GJ_NB][n]
-    double *Own = sm + 2 * GJ_NB * n;  // own columns being updated, [GJ_OWN][n]
+    double *Pn = sm;                   // panel columns (CTA 0) / f columns (all CTAs), [GJ_NB][n]
+    double *Own = sm + GJ_NB * n;      // own columns being updated, [GJ_OWN][n]
     __shared__ double s_best[8], s_xk[GJ_NB], s_inv[GJ_NB], s_xo[GJ_OWN];
     __shared__ int s_idx[8], s_piv[GJ_NB];
     const int cols_per = (n + gridDim.x - 1) / gridDim.x;
     const int c0 = blockIdx.x * cols_per, c1 = min(n, c0 + cols_per);
     for (int k0 = 0; k0 < n; k0 += GJ_NB) {
         const int nb = min(GJ_NB, n - k0);
-        for (int q = threadIdx.x; q < nb * n; q += blockDim.x) Pn[q] = X[(long)k0 * n + q];
+        // --- CTA 0: factor the panel ---
+        if (blockIdx.x == 0) {
+            for (int q = threadIdx.x; q < nb * n; q += blockDim.x) Pn[q] = X[(long)k0 * n + q];
+            __syncthreads();
+            bool bad = false;
+            for (int t = 0; t < nb && !bad; ++t) {
+                const int k = k0 + t;
+                double best;
+                int p;
+                block_argmax(Pn + (long)t * n, k, n, s_best, s_idx, &best, &p);
+                const double piv = p < n ? Pn[(long)t * n + p] : 0.0;
+                if (piv == 0.0 || !isfinite(piv)) {
+                    if (threadIdx.x == 0) *status = 1 + k;
+                    bad = true;
+                    break;
+                }
+                if (threadIdx.x < nb && p != k) {
+                    double a = Pn[(long)threadIdx.x * n + k];
+                    Pn[(long)threadIdx.x * n + k] = Pn[(long)threadIdx.x * n + p];
+                    Pn[(long)threadIdx.x * n + p] = a;
+                }
+                __syncthreads();
+                // publish f (column t after the swap) before it changes
+                for (int i = threadIdx.x; i < n; i += blockDim.x) Fg[(long)t * n + i] = Pn[(long)t * n + i];
+                if (threadIdx.x == 0) {
+                    const double inv = 1.0 / piv;
+                    s_inv[t] = inv;
+                    pg[t] = p;
+                    ig[t] = inv;
+                    perm[k] = p;
+                }
+                __syncthreads();
+                const double inv = s_inv[t];
+                if (threadIdx.x < nb) s_xk[threadIdx.x] = Pn[(long)threadIdx.x * n + k] * inv;
+                __syncthreads();
+                const double *f = Pn + (long)t * n;
+                for (int c = 0; c < nb; ++c) {
+                    if (c == t) continue;
+                    const double xk = s_xk[c];
+                    double *col = Pn + (long)c * n;
+                    for (int i = threadIdx.x; i < n; i += blockDim.x) col[i] = i == k ? xk : col[i] - f[i] * xk;
+                }
+                __syncthreads();
+                for (int i = threadIdx.x; i < n; i += blockDim.x) Pn[(long)t * n + i] = i == k ? inv : -f[i] * inv;
+                __syncthreads();
+            }
+            if (!bad)
+                for (int q = threadIdx.x; q < nb * n; q += blockDim.x) X[(long)k0 * n + q] = Pn[q];
+        }
+        __threadfence();
+        grid.sync();
+        if (*status) return;  // singular: every CTA leaves here
+        // --- every CTA: the panel's steps on its own columns outside the panel ---
+        if (c1 > c0) {
+            for (int q = threadIdx.x; q < nb * n; q += blockDim.x) Pn[q] = Fg[q];
+            if (threadIdx.x < nb) {
+                s_piv[threadIdx.x] = pg[threadIdx.x];
+                s_inv[threadIdx.x] = ig[threadIdx.x];
+            }
+            __syncthreads();
+            for (int a0 = c0; a0 < c1; a0 += GJ_OWN) {
+                const int na = min(GJ_OWN, c1 - a0);
+                for (int q = threadIdx.x; q < na * n; q += blockDim.x) Own[q] = X[(long)a0 * n + q];
+                __syncthreads();
+                for (int t = 0; t < nb; ++t) {
+                    const int k = k0 + t, p = s_piv[t];
+                    if (threadIdx.x < na) {
+                        const int c = threadIdx.x, j = a0 + c;
+                        if (j < k0 || j >= k0 + nb) {
+                            double x = Own[(long)c * n + k], y = Own[(long)c * n + p];
+                            if (p != k) {
+                                Own[(long)c * n + p] = x;
+                                x = y;
+                            }
+                            x *= s_inv[t];
+                            Own[(long)c * n + k] = x;
+                            s_xo[c] = x;
+                        }
+                    }
+                    __syncthreads();
+                    const double *f = Pn + (long)t * n;
+                    for (int c = 0; c < na; ++c) {
+                        const int j = a0 + c;
+                        if (j >= k0 && j < k0 + nb) continue;
+                        const double xk = s_xo[c];
+                        double *col = Own + (long)c * n;
+                        for (int i = threadIdx.x; i < n; i += blockDim.x)
+                            if (i != k) col[i] -= f[i] * xk;
+                    }
+                    __syncthreads();
+                }
+                for (int c = 0; c < na; ++c) {
+                    const int j = a0 + c;
+                    if (j >= k0 && j < k0 + nb) continue;
+                    for (int i = threadIdx.x; i < n; i += blockDim.x) X[(long)j * n + i] = Own[(long)c * n + i];
+                }
+                __syncthreads();
+            }
+        }
+        __threadfence();
+        grid.sync();
+    }
+}
+
+// Resident variant for coarse systems whose columns fit in shared memory:
+// every CTA keeps the columns it owns in shared memory for the whole
+// inversion; the next panel of GJ_RS columns is published by its owners into
+// a small double-buffered global array before each grid-wide barrier. After
+// the barrier every CTA replays the panel's steps on its shared copy of the
+// panel (to learn each step's pivot and column f) and applies them to its own
+// columns. Same arithmetic as above, one barrier per GJ_RS pivots, and no
+// per-panel traffic of the owned columns.
+constexpr int GJ_RS = 4;
+
+__global__ void __launch_bounds__(256) gauss_jordan_resident_kernel(int n, const double *__restrict__ Xin,
+                                                                    double *__restrict__ Xout,
+                                                                    double *__restrict__ pub, int *__restrict__ perm,
+                                                                    int *__restrict__ status) {
+    cg::grid_group grid = cg::this_grid();
+    extern __shared__ double sm[];
+    const int cols_per = (n + gridDim.x - 1) / gridDim.x;
+    const int c0 = blockIdx.x * cols_per, c1 = min(n, c0 + cols_per), na = max(0, c1 - c0);
+    double *Own = sm;                         // [cols_per][n]
+    double *Pnl = sm + (long)cols_per * n;    // panel copy, becomes the f columns, [GJ_RS][n]
+    __shared__ double s_best[8], s_inv[GJ_RS], s_xk[GJ_RS], s_xo[64];
+    __shared__ int s_idx[8], s_piv[GJ_RS];
+    for (int q = threadIdx.x; q < na * n; q += blockDim.x) Own[q] = Xin[(long)c0 * n + q];
+    // publish the first panel
+    for (int c = 0; c < na; ++c) {
+        const int j = c0 + c;
+        if (j < GJ_RS)
+            for (int i = threadIdx.x; i < n; i += blockDim.x) pub[(long)j * n + i] = Own[(long)c * n + i];
+    }
+    __threadfence();
+    grid.sync();
+    for (int k0 = 0, it = 0; k0 < n; k0 += GJ_RS, ++it) {
+        const int nb = min(GJ_RS, n - k0);
+        const double *pb = pub + (long)(it & 1) * GJ_RS * n;
+        for (int q = threadIdx.x; q < nb * n; q += blockDim.x) Pnl[q] = pb[q];
         __syncthreads();
-        // --- factor the panel (identical in every CTA) ---
+        // replay the panel: pivots, 1/pivots and the f columns (kept in Pnl)
         for (int t = 0; t < nb; ++t) {
             const int k = k0 + t;
             double best;
             int p;
-            block_argmax(Pn + (long)t * n, k, n, s_best, s_idx, &best, &p);
-            const double piv = p < n ? Pn[(long)t * n + p] : 0.0;
+            block_argmax(Pnl + (long)t * n, k, n, s_best, s_idx, &best, &p);
+            const double piv = p < n ? Pnl[(long)t * n + p] : 0.0;
             if (piv == 0.0 || !isfinite(piv)) {  // every CTA leaves at the same step
                 if (blockIdx.x == 0 && threadIdx.x == 0) *status = 1 + k;
                 return;
             }
-            if (threadIdx.x < nb && p != k) {
-                double a = Pn[(long)threadIdx.x * n + k];
-                Pn[(long)threadIdx.x * n + k] = Pn[(long)threadIdx.x * n + p];
-                Pn[(long)threadIdx.x * n + p] = a;
+            if (threadIdx.x >= t && threadIdx.x < nb && p != k) {
+                double a = Pnl[(long)threadIdx.x * n + k];
+                Pnl[(long)threadIdx.x * n + k] = Pnl[(long)threadIdx.x * n + p];
+                Pnl[(long)threadIdx.x * n + p] = a;
             }
-            __syncthreads();
-            for (int i = threadIdx.x; i < n; i += blockDim.x) F[(long)t * n + i] = Pn[(long)t * n + i];
             if (threadIdx.x == 0) {
                 s_piv[t] = p;
                 s_inv[t] = 1.0 / piv;
@@ -103,62 +247,62 @@ __global__ void __launch_bounds__(256) gauss_jordan_kernel(int n, double *__rest
             }
             __syncthreads();
             const double inv = s_inv[t];
-            if (threadIdx.x < nb) s_xk[threadIdx.x] = Pn[(long)threadIdx.x * n + k] * inv;
+            if (threadIdx.x > t && threadIdx.x < nb) s_xk[threadIdx.x] = Pnl[(long)threadIdx.x * n + k] * inv;
             __syncthreads();
-            for (int q = threadIdx.x; q < nb * n; q += blockDim.x) {
-                const int c = q / n, i = q - c * n;
-                const double fi = F[(long)t * n + i];
-                if (c == t)
-                    Pn[q] = i == k ? inv : -fi * inv;
-                else
-                    Pn[q] = i == k ? s_xk[c] : Pn[q] - fi * s_xk[c];
+            const double *f = Pnl + (long)t * n;
+            for (int c = t + 1; c < nb; ++c) {
+                const double xk = s_xk[c];
+                double *col = Pnl + (long)c * n;
+                for (int i = threadIdx.x; i < n; i += blockDim.x) col[i] = i == k ? xk : col[i] - f[i] * xk;
             }
             __syncthreads();
         }
-        // --- owned panel columns back to global ---
-        for (int c = 0; c < nb; ++c) {
-            const int j = k0 + c;
-            if (j < c0 || j >= c1) continue;
-            for (int i = threadIdx.x; i < n; i += blockDim.x) X[(long)j * n + i] = Pn[(long)c * n + i];
-        }
-        // --- the panel's steps on the own columns, staged in shared memory in
-        // chunks of GJ_OWN columns (panel columns are skipped: done above) ---
-        for (int a0 = c0; a0 < c1; a0 += GJ_OWN) {
-            const int na = min(GJ_OWN, c1 - a0);
-            for (int q = threadIdx.x; q < na * n; q += blockDim.x) Own[q] = X[(long)a0 * n + q];
-            __syncthreads();
-            for (int t = 0; t < nb; ++t) {
-                const int k = k0 + t, p = s_piv[t];
-                if (threadIdx.x < na) {
-                    const int c = threadIdx.x, j = a0 + c;
-                    if (j < k0 || j >= k0 + nb) {
-                        double x = Own[(long)c * n + k], y = Own[(long)c * n + p];
-                        if (p != k) {
-                            Own[(long)c * n + p] = x;
-                            x = y;
-                        }
-                        x *= s_inv[t];
-                        Own[(long)c * n + k] = x;
-                        s_xo[c] = x;
+        // the panel's steps on the owned columns
+        for (int t = 0; t < nb; ++t) {
+            const int k = k0 + t, p = s_piv[t];
+            const double inv = s_inv[t];
+            for (int c = threadIdx.x; c < na; c += blockDim.x) {
+                const int j = c0 + c;
+                double *col = Own + (long)c * n;
+                if (j == k) {
+                    s_xo[c] = 0.0;
+                } else {
+                    double x = col[k], y = col[p];
+                    if (p != k) {
+                        col[p] = x;
+                        x = y;
                     }
+                    x *= inv;
+                    col[k] = x;
+                    s_xo[c] = x;
                 }
-                __syncthreads();
-                const double *f = F + (long)t * n;
-                for (int q = threadIdx.x; q < na * n; q += blockDim.x) {
-                    const int c = q / n, i = q - c * n, j = a0 + c;
-                    if (i != k && (j < k0 || j >= k0 + nb)) Own[q] -= f[i] * s_xo[c];
-                }
-                __syncthreads();
-            }
-            for (int q = threadIdx.x; q < na * n; q += blockDim.x) {
-                const int j = a0 + q / n;
-                if (j < k0 || j >= k0 + nb) X[(long)a0 * n + q] = Own[q];
             }
             __syncthreads();
+            const double *f = Pnl + (long)t * n;
+            for (int c = 0; c < na; ++c) {
+                double *col = Own + (long)c * n;
+                if (c0 + c == k) {
+                    for (int i = threadIdx.x; i < n; i += blockDim.x) col[i] = i == k ? inv : -f[i] * inv;
+                } else {
+                    const double xk = s_xo[c];
+                    for (int i = threadIdx.x; i < n; i += blockDim.x)
+                        if (i != k) col[i] -= f[i] * xk;
+                }
+            }
+            __syncthreads();
+        }
+        // publish the next panel
+        const int n0 = k0 + GJ_RS, n1 = min(n, n0 + GJ_RS);
+        double *pn = pub + (long)((it + 1) & 1) * GJ_RS * n;
+        for (int c = 0; c < na; ++c) {
+            const int j = c0 + c;
+            if (j >= n0 && j < n1)
+                for (int i = threadIdx.x; i < n; i += blockDim.x) pn[(long)(j - n0) * n + i] = Own[(long)c * n + i];
         }
         __threadfence();
         grid.sync();
     }
+    for (int q = threadIdx.x; q < na * n; q += blockDim.x) Xout[(long)c0 * n + q] = Own[q];
 }
 
 // transpose (row-major <-> column-major), n x n
@@ -192,40 +336,96 @@ __global__ void unscramble_kernel(int n, const double *__restrict__ Xcm, const i
     }
 }
 
-// Ainv (device, n x n row-major) = inverse of Ac (device, n x n row-major, not modified).
-msrsb_status coarse_inverse(int n, const double *Ac, double *Ainv, cudaStream_t s) {
-    double *X = nullptr;
-    int *perm = nullptr, *status = nullptr;
-    MSRSB_TRY(dalloc(&X, (size_t)n * n, s));
-    MSRSB_TRY(dalloc(&perm, n, s));
-    MSRSB_TRY(dalloc(&status, 1, s));
-    dim3 tb(32, 8), tg(ceil_div(n, 32), ceil_div(n, 32));
-    transpose_kernel<<<tg, tb, 0, s>>>(n, Ac, X);
-    MSRSB_LAUNCHED("transpose_kernel");
-    MSRSB_CUDA(cudaMemsetAsync(status, 0, sizeof(int), s));
-    const size_t smem = (size_t)(2 * GJ_NB + GJ_OWN) * n * sizeof(double);
-    if (smem > 220 * 1024) return fail(MSRSB_ESHAPE, "coarse system too large for the inverse (n = %d)", n);
-    MSRSB_CUDA(cudaFuncSetAttribute(gauss_jordan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int dev = 0, sms = 0, occ = 0;
+// Ainv (device, n x n row-major) = inverse of Ac (device, n x n row-major, not
+// modified). Split in two so the set-up can overlap it with independent work:
+// coarse_inverse_launch enqueues everything on s without waiting;
+// coarse_inverse_finish waits for s, frees the work arrays and reports a
+// singular pivot.
+msrsb_status coarse_inverse_launch(int n, const double *Ac, double *Ainv, CoarseInverseWork *w, cudaStream_t s) {
+    int dev = 0, sms = 0;
     MSRSB_CUDA(cudaGetDevice(&dev));
     MSRSB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    MSRSB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gauss_jordan_kernel, 256, smem));
-    int grid = occ > 0 ? sms : 0;
-    if (grid > n) grid = n;
-    if (grid < 1) return fail(MSRSB_ECUDA, "cooperative launch not possible (occupancy %d)", occ);
-    void *args[] = {(void *)&n, (void *)&X, (void *)&perm, (void *)&status};
-    MSRSB_CUDA(cudaLaunchCooperativeKernel((void *)gauss_jordan_kernel, grid, 256, args, smem, s));
-    MSRSB_LAUNCHED("gauss_jordan_kernel");
-    unscramble_kernel<<<ceil_div(n, 128), 128, 0, s>>>(n, X, perm, Ainv);
+    MSRSB_TRY(dalloc(&w->X, (size_t)n * n, s));
+    MSRSB_TRY(dalloc(&w->perm, n, s));
+    MSRSB_TRY(dalloc(&w->status, 1, s));
+    dim3 tb(32, 8), tg(ceil_div(n, 32), ceil_div(n, 32));
+    transpose_kernel<<<tg, tb, 0, s>>>(n, Ac, w->X);
+    MSRSB_LAUNCHED("transpose_kernel");
+    MSRSB_CUDA(cudaMemsetAsync(w->status, 0, sizeof(int), s));
+    // resident variant when every CTA's columns fit in shared memory
+    const int grid_r = sms < n ? sms : n;
+    const int cols_per = (n + grid_r - 1) / grid_r;
+    const size_t smem_r = (size_t)(cols_per + GJ_RS) * n * sizeof(double);
+    double *Xres = nullptr;
+    if (smem_r <= 200 * 1024 && cols_per <= 64) {
+        int occ = 0;
+        MSRSB_CUDA(cudaFuncSetAttribute(gauss_jordan_resident_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem_r));
+        MSRSB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gauss_jordan_resident_kernel, 256, smem_r));
+        if (occ > 0) {
+            MSRSB_TRY(dalloc(&w->Fg, (size_t)2 * GJ_RS * n, s));  // publication buffer
+            MSRSB_TRY(dalloc(&Xres, (size_t)n * n, s));
+            w->Xres = Xres;
+            int nn = n;
+            void *args[] = {(void *)&nn, (void *)&w->X, (void *)&Xres, (void *)&w->Fg, (void *)&w->perm,
+                            (void *)&w->status};
+            MSRSB_CUDA(cudaLaunchCooperativeKernel((void *)gauss_jordan_resident_kernel, grid_r, 256, args, smem_r, s));
+            MSRSB_LAUNCHED("gauss_jordan_resident_kernel");
+        }
+    }
+    if (!Xres) {
+        MSRSB_TRY(dalloc(&w->Fg, (size_t)GJ_NB * n, s));
+        MSRSB_TRY(dalloc(&w->ig, GJ_NB, s));
+        MSRSB_TRY(dalloc(&w->pg, GJ_NB, s));
+        const size_t smem = (size_t)(GJ_NB + GJ_OWN) * n * sizeof(double);
+        if (smem > 220 * 1024) return fail(MSRSB_ESHAPE, "coarse system too large for the inverse (n = %d)", n);
+        MSRSB_CUDA(cudaFuncSetAttribute(gauss_jordan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int occ = 0;
+        MSRSB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gauss_jordan_kernel, 256, smem));
+        int grid = occ > 0 ? sms : 0;
+        if (grid > n) grid = n;
+        if (grid < 1) return fail(MSRSB_ECUDA, "cooperative launch not possible (occupancy %d)", occ);
+        void *args[] = {(void *)&n, (void *)&w->X, (void *)&w->perm, (void *)&w->Fg, (void *)&w->pg, (void *)&w->ig,
+                        (void *)&w->status};
+        MSRSB_CUDA(cudaLaunchCooperativeKernel((void *)gauss_jordan_kernel, grid, 256, args, smem, s));
+        MSRSB_LAUNCHED("gauss_jordan_kernel");
+    }
+    unscramble_kernel<<<ceil_div(n, 128), 128, 0, s>>>(n, Xres ? Xres : w->X, w->perm, Ainv);
     MSRSB_LAUNCHED("unscramble_kernel");
-    int h_status = 0;
-    MSRSB_CUDA(cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, s));
-    MSRSB_CUDA(cudaStreamSynchronize(s));
-    dfree(X, s);
-    dfree(perm, s);
-    dfree(status, s);
-    if (h_status) return fail(MSRSB_EBREAKDOWN, "coarse operator is singular (zero pivot at column %d)", h_status - 1);
+    // pinned destination: a copy into pageable memory would block the host
+    // until the inverse is done and defeat the overlap
+    double *pin = pinned_scratch();
+    if (pin) {
+        w->pin_status = (int *)(pin + 12);
+        MSRSB_CUDA(cudaMemcpyAsync(w->pin_status, w->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    }
     return MSRSB_OK;
+}
+
+msrsb_status coarse_inverse_finish(CoarseInverseWork *w, cudaStream_t s) {
+    if (w->pin_status) {
+        MSRSB_CUDA(cudaStreamSynchronize(s));
+        w->h_status = *(volatile int *)w->pin_status;
+    } else {
+        MSRSB_CUDA(cudaMemcpyAsync(&w->h_status, w->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+        MSRSB_CUDA(cudaStreamSynchronize(s));
+    }
+    dfree(w->X, s);
+    dfree(w->Xres, s);
+    dfree(w->Fg, s);
+    dfree(w->ig, s);
+    dfree(w->pg, s);
+    dfree(w->perm, s);
+    dfree(w->status, s);
+    if (w->h_status)
+        return fail(MSRSB_EBREAKDOWN, "coarse operator is singular (zero pivot at column %d)", w->h_status - 1);
+    return MSRSB_OK;
+}
+
+msrsb_status coarse_inverse(int n, const double *Ac, double *Ainv, cudaStream_t s) {
+    CoarseInverseWork w;
+    MSRSB_TRY(coarse_inverse_launch(n, Ac, Ainv, &w, s));
+    return coarse_inverse_finish(&w, s);
 }
 
 // y = M x, M dense n x n row-major FP64; one warp per row.

@@ -79,6 +79,14 @@ struct Sell {
     void *val[3] = {nullptr, nullptr, nullptr};
 };
 
+// work arrays of the coarse inverse while it runs (see coarse.cu)
+struct CoarseInverseWork {
+    double *X = nullptr, *Xres = nullptr, *Fg = nullptr, *ig = nullptr;
+    int *perm = nullptr, *status = nullptr, *pg = nullptr;
+    int *pin_status = nullptr;  // pinned copy of the status (slot of the pinned scratch)
+    int h_status = 0;
+};
+
 // ILU(0) factors per colour in ELL blocks over colour-ordered positions
 struct IluEll {
     int ncol = 0;
@@ -118,6 +126,7 @@ struct msrsb_handle {
     msrsb_opts opts{};
     int n = 0, bdim = 1, nc = 0, W = 4, nC = 0, ncomp = 1;
     cudaStream_t stream = nullptr;
+    cudaStream_t side = nullptr;  // set-up side stream (coarse inverse overlapped with the smoother set-up)
     // partition
     int32_t *part = nullptr, *cnode = nullptr, *p_ids = nullptr;
     uint8_t *skel = nullptr;

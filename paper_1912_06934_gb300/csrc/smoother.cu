@@ -82,15 +82,17 @@ __device__ __forceinline__ int find_col(const int32_t *__restrict__ colidx, int 
 // row k in that order (row-wise IKJ): l_ik = a_ik / u_kk, then every later
 // entry (i, j) that row k also holds is updated; only entries already in A's
 // pattern change. Row k (final, an earlier colour) is read once, coalesced,
-// and matched through warp shuffles. Each entry sees its updates in
-// increasing k and products are explicitly rounded, so the factors equal those
-// of a plain sequential factorisation of the colour-ordered matrix.
+// and matched through warp shuffles with integer work only. The pivot
+// division is replaced by a product with 1 / u_kk, stored when row k was
+// finished: FP64 issue slots are scarce on this GPU. TF is the factorisation
+// precision (FP64 for the FP64 form, FP32 for the mixed form's smoother).
+template <typename TF>
 __global__ void __launch_bounds__(128) ilu0_colour_kernel(int cnt, const int32_t *__restrict__ rows, int c,
                                                           const int32_t *__restrict__ rowptr,
                                                           const int32_t *__restrict__ colidx,
                                                           const uint8_t *__restrict__ colour,
-                                                          const int32_t *__restrict__ dpos, double *__restrict__ lu,
-                                                          int *__restrict__ status) {
+                                                          const int32_t *__restrict__ dpos, TF *__restrict__ lu,
+                                                          TF *__restrict__ rdiag, int *__restrict__ status) {
     const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (t >= cnt) return;  // whole warps leave together
@@ -103,36 +105,35 @@ __global__ void __launch_bounds__(128) ilu0_colour_kernel(int cnt, const int32_t
     const bool mine = lane < len;
     const int j = mine ? colidx[b + lane] : -1;
     const int cj = mine ? colour[j] : 255;
-    double a = mine ? lu[b + lane] : 0.0;
+    TF a = mine ? lu[b + lane] : TF(0);
     for (int cc = 0; cc < c; ++cc) {
         unsigned m = __ballot_sync(0xffffffffu, cj == cc);  // entries of colour cc, ascending column
         while (m) {
             const int q = __ffs(m) - 1;
             m &= m - 1;
             const int k = __shfl_sync(0xffffffffu, j, q);
-            const double aik = __shfl_sync(0xffffffffu, a, q);
+            const TF aik = __shfl_sync(0xffffffffu, a, q);
             const int kb = rowptr[k], klen = rowptr[k + 1] - kb;
-            const double ukk = lu[dpos[k]];
-            if (ukk == 0.0) {
-                if (lane == 0) atomicCAS(status, 0, 1 + k);
-                return;
-            }
-            const double lik = aik / ukk;
+            const TF lik = aik * rdiag[k];
             if (lane == q) a = lik;
             const int kc = lane < klen ? colidx[kb + lane] : -1;
-            const double kv = lane < klen ? lu[kb + lane] : 0.0;
+            const TF kv = lane < klen ? lu[kb + lane] : TF(0);
             // entries after k in the order: later colour, or same colour and larger index
             const bool later = mine && (cj > cc || (cj == cc && j > k));
-            // find (k, j) in row k with integer work only (FP64 issue slots are scarce)
             int hit = -1;
             for (int r = 0; r < klen; ++r)
                 if (__shfl_sync(0xffffffffu, kc, r) == j) hit = r;
-            const double kvr = __shfl_sync(0xffffffffu, kv, hit >= 0 ? hit : 0);
-            if (later && hit >= 0) a = __dsub_rn(a, __dmul_rn(lik, kvr));
+            const TF kvr = __shfl_sync(0xffffffffu, kv, hit >= 0 ? hit : 0);
+            if (later && hit >= 0) a = a - lik * kvr;
         }
     }
     if (mine) lu[b + lane] = a;
-    if (lane == 0 && lu[dpos[i]] == 0.0) atomicCAS(status, 0, 1 + i);
+    const int dq = dpos[i] - b;  // diagonal entry of row i, held by lane dq
+    const TF uii = __shfl_sync(0xffffffffu, a, dq);
+    if (lane == 0) {
+        if (uii == TF(0) || !isfinite((double)uii)) atomicCAS(status, 0, 1 + i);
+        rdiag[i] = TF(1) / uii;
+    }
 }
 
 template <typename T>
@@ -150,14 +151,17 @@ msrsb_status convert(long n, const double *a, T *b, cudaStream_t s) {
 template msrsb_status convert<float>(long, const double *, float *, cudaStream_t);
 template msrsb_status convert<double>(long, const double *, double *, cudaStream_t);
 
-// ILU(0) of the colour-ordered scalar operator; lu_out (T, A's pattern)
+// ILU(0) of the colour-ordered scalar operator, in place on lu (A's values
+// on entry, TF precision); dpos receives the diagonal positions
+template <typename TF>
 msrsb_status ilu0_factor(const msrsb_mat *A, const uint8_t *colour, int ncol, const int32_t *rows,
-                         const int32_t *cptr_h, int32_t *dpos, double *lu, cudaStream_t s) {
+                         const int32_t *cptr_h, int32_t *dpos, TF *lu, cudaStream_t s) {
     int n = A->nrows;
     int *status = nullptr;
+    TF *rdiag = nullptr;
     MSRSB_TRY(dalloc(&status, 1, s));
+    MSRSB_TRY(dalloc(&rdiag, n, s));
     MSRSB_CUDA(cudaMemsetAsync(status, 0, sizeof(int), s));
-    MSRSB_CUDA(cudaMemcpyAsync(lu, A->val, (size_t)A->nnz * sizeof(double), cudaMemcpyDeviceToDevice, s));
     diag_pos_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, A->rowptr, A->colidx, dpos, status);
     MSRSB_LAUNCHED("diag_pos_kernel");
     {
@@ -166,25 +170,31 @@ msrsb_status ilu0_factor(const msrsb_mat *A, const uint8_t *colour, int ncol, co
         MSRSB_CUDA(cudaStreamSynchronize(s));
         if (h0) {
             dfree(status, s);
+            dfree(rdiag, s);
             return fail(MSRSB_EINVAL, "ILU(0): row %d has no diagonal entry", h0 - 1);
         }
     }
     for (int c = 0; c < ncol; ++c) {
         int cnt = cptr_h[c + 1] - cptr_h[c];
         if (cnt == 0) continue;
-        ilu0_colour_kernel<<<ceil_div((long)cnt * 32, 128), 128, 0, s>>>(cnt, rows + cptr_h[c], c, A->rowptr,
-                                                                         A->colidx, colour, dpos, lu, status);
+        ilu0_colour_kernel<TF><<<ceil_div((long)cnt * 32, 128), 128, 0, s>>>(cnt, rows + cptr_h[c], c, A->rowptr,
+                                                                             A->colidx, colour, dpos, lu, rdiag,
+                                                                             status);
         MSRSB_LAUNCHED("ilu0_colour_kernel");
     }
     int h = 0;
     MSRSB_CUDA(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s));
     MSRSB_CUDA(cudaStreamSynchronize(s));
     dfree(status, s);
+    dfree(rdiag, s);
     if (h < 0) return fail(MSRSB_EINVAL, "ILU(0): row %d has more than 32 entries", -h - 1);
-    if (h) return fail(MSRSB_EBREAKDOWN, "ILU(0): zero or missing pivot at row %d", h - 1);
+    if (h) return fail(MSRSB_EBREAKDOWN, "ILU(0): zero pivot at row %d", h - 1);
     return MSRSB_OK;
 }
-
+template msrsb_status ilu0_factor<double>(const msrsb_mat *, const uint8_t *, int, const int32_t *, const int32_t *,
+                                          int32_t *, double *, cudaStream_t);
+template msrsb_status ilu0_factor<float>(const msrsb_mat *, const uint8_t *, int, const int32_t *, const int32_t *,
+                                         int32_t *, float *, cudaStream_t);
 
 // ---- ILU(0) sweeps on colour-ordered (permuted) vectors -----------------------
 //
@@ -228,7 +238,7 @@ __global__ void ilu_width_kernel(int n, const int32_t *__restrict__ rowptr, cons
 
 template <typename T>
 __global__ void ilu_ell_fill_kernel(int n, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
-                                    const uint8_t *__restrict__ colour, const double *__restrict__ lu,
+                                    const uint8_t *__restrict__ colour, const T *__restrict__ lu,
                                     const int32_t *__restrict__ dpos, const int32_t *__restrict__ pos,
                                     const IluEll E, int32_t *__restrict__ lcol, T *__restrict__ lval,
                                     int32_t *__restrict__ ucol, T *__restrict__ uval, T *__restrict__ udinv) {
@@ -259,7 +269,7 @@ __global__ void ilu_ell_fill_kernel(int n, const int32_t *__restrict__ rowptr, c
         ucol[ub + (long)nu * m + r] = E.cptr[E.ncol - 1];
         uval[ub + (long)nu * m + r] = T(0);
     }
-    udinv[p] = T(1.0 / lu[dpos[i]]);
+    udinv[p] = T(1) / lu[dpos[i]];
 }
 
 // Four lanes per row: lane g takes entries g, g+4, ...; shuffle reduction.
@@ -286,11 +296,11 @@ __global__ void __launch_bounds__(256) ilu_lower_kernel(int c0, int m, int w, co
 
 // backward, colour c, in place on y: e_p = (y_p - sum_j U_pj e_col) / u_pp;
 // then z[row(p)] += e_p
-template <typename T>
+template <typename T, typename TZ>
 __global__ void __launch_bounds__(256) ilu_upper_kernel(int c0, int m, int w, const int32_t *__restrict__ ucol,
                                                         const T *__restrict__ uval, const T *__restrict__ udinv,
                                                         const int32_t *__restrict__ rows, T *__restrict__ y,
-                                                        double *__restrict__ z) {
+                                                        TZ *__restrict__ z) {
     const int q = (blockIdx.x * blockDim.x + threadIdx.x) / kSweepLanes;
     const int g = threadIdx.x % kSweepLanes;
     if (q >= m) return;
@@ -301,13 +311,14 @@ __global__ void __launch_bounds__(256) ilu_upper_kernel(int c0, int m, int w, co
     if (g == 0) {
         T e = (y[c0 + q] - acc) * udinv[c0 + q];
         y[c0 + q] = e;
-        z[rows[c0 + q]] += (double)e;
+        const int row = rows[c0 + q];
+        z[row] = TZ(z[row] + TZ(e));
     }
 }
 
-// Build the per-colour ELL factors from the natural-order FP64 factors.
+// Build the per-colour ELL factors from the natural-order factors.
 template <typename T>
-msrsb_status ilu_build_ell(msrsb_handle *h, const double *lu, cudaStream_t s) {
+msrsb_status ilu_build_ell(msrsb_handle *h, const T *lu, cudaStream_t s) {
     const msrsb_mat &A = h->A;
     const int n = h->n, ncol = h->ncolours;
     IluEll &E = h->ilu;
@@ -351,11 +362,11 @@ msrsb_status ilu_build_ell(msrsb_handle *h, const double *lu, cudaStream_t s) {
     return MSRSB_OK;
 }
 template msrsb_status ilu_build_ell<double>(msrsb_handle *, const double *, cudaStream_t);
-template msrsb_status ilu_build_ell<float>(msrsb_handle *, const double *, cudaStream_t);
+template msrsb_status ilu_build_ell<float>(msrsb_handle *, const float *, cudaStream_t);
 
 // z += U^-1 L^-1 r, r given in colour order (rp), y a colour-order work vector
-template <typename T>
-msrsb_status ilu0_apply(const msrsb_handle *h, const T *rp, T *y, double *z, cudaStream_t s) {
+template <typename T, typename TZ>
+msrsb_status ilu0_apply(const msrsb_handle *h, const T *rp, T *y, TZ *z, cudaStream_t s) {
     const IluEll &E = h->ilu;
     for (int c = 0; c < E.ncol; ++c) {
         int m = E.cptr[c + 1] - E.cptr[c];
@@ -367,15 +378,17 @@ msrsb_status ilu0_apply(const msrsb_handle *h, const T *rp, T *y, double *z, cud
     for (int c = E.ncol - 1; c >= 0; --c) {
         int m = E.cptr[c + 1] - E.cptr[c];
         if (!m) continue;
-        ilu_upper_kernel<T><<<ceil_div((long)m * kSweepLanes, 256), 256, 0, s>>>(E.cptr[c], m, E.wu[c], E.ucol + E.ubase[c],
-                                                             (const T *)E.uval + E.ubase[c], (const T *)E.udinv,
-                                                             h->colour_rows, y, z);
+        ilu_upper_kernel<T, TZ><<<ceil_div((long)m * kSweepLanes, 256), 256, 0, s>>>(
+            E.cptr[c], m, E.wu[c], E.ucol + E.ubase[c], (const T *)E.uval + E.ubase[c], (const T *)E.udinv,
+            h->colour_rows, y, z);
         MSRSB_LAUNCHED("ilu_upper_kernel");
     }
     return MSRSB_OK;
 }
-template msrsb_status ilu0_apply<double>(const msrsb_handle *, const double *, double *, double *, cudaStream_t);
-template msrsb_status ilu0_apply<float>(const msrsb_handle *, const float *, float *, double *, cudaStream_t);
+template msrsb_status ilu0_apply<double, double>(const msrsb_handle *, const double *, double *, double *,
+                                                 cudaStream_t);
+template msrsb_status ilu0_apply<float, double>(const msrsb_handle *, const float *, float *, double *, cudaStream_t);
+template msrsb_status ilu0_apply<float, float>(const msrsb_handle *, const float *, float *, float *, cudaStream_t);
 
 // ---- block (3x3) Gauss-Seidel -------------------------------------------------
 
@@ -431,12 +444,12 @@ template msrsb_status block_diag_inverse<float>(const msrsb_mat *, float *, cuda
 
 // one colour of a block Gauss-Seidel sweep: e_i = Dinv_i (r_i - sum_{k in
 // earlier colours of this sweep} A_ik e_k); z_i += e_i (or z_i = e_i)
-template <typename T, typename TA>
+template <typename T, typename TA, typename TZ>
 __global__ void gs_colour_kernel(int cnt, const int32_t *__restrict__ rows, int c, int forward,
                                  const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
                                  const uint8_t *__restrict__ colour, const TA *__restrict__ val,
                                  const T *__restrict__ dinv, const T *__restrict__ r, T *__restrict__ e,
-                                 double *__restrict__ z, int assign) {
+                                 TZ *__restrict__ z, int assign) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= cnt) return;
     int i = rows[t];
@@ -459,34 +472,36 @@ __global__ void gs_colour_kernel(int cnt, const int32_t *__restrict__ rows, int 
     e[3 * i + 1] = x1;
     e[3 * i + 2] = x2;
     if (assign) {
-        z[3 * i] = x0;
-        z[3 * i + 1] = x1;
-        z[3 * i + 2] = x2;
+        z[3 * i] = TZ(x0);
+        z[3 * i + 1] = TZ(x1);
+        z[3 * i + 2] = TZ(x2);
     } else {
-        z[3 * i] += x0;
-        z[3 * i + 1] += x1;
-        z[3 * i + 2] += x2;
+        z[3 * i] = TZ(z[3 * i] + TZ(x0));
+        z[3 * i + 1] = TZ(z[3 * i + 1] + TZ(x1));
+        z[3 * i + 2] = TZ(z[3 * i + 2] + TZ(x2));
     }
 }
 
-template <typename T, typename TA>
-msrsb_status gs_apply(const msrsb_handle *h, const TA *val, const T *dinv, int forward, const T *r, T *e, double *z,
+template <typename T, typename TA, typename TZ>
+msrsb_status gs_apply(const msrsb_handle *h, const TA *val, const T *dinv, int forward, const T *r, T *e, TZ *z,
                       int assign, cudaStream_t s) {
     const msrsb_mat &A = h->A;
     for (int q = 0; q < h->ncolours; ++q) {
         int c = forward ? q : h->ncolours - 1 - q;
         int cnt = h->colour_ptr_h[c + 1] - h->colour_ptr_h[c];
         if (!cnt) continue;
-        gs_colour_kernel<T, TA><<<ceil_div(cnt, 128), 128, 0, s>>>(cnt, h->colour_rows + h->colour_ptr_h[c], c,
-                                                                   forward, A.rowptr, A.colidx, h->colour, val, dinv,
-                                                                   r, e, z, assign);
+        gs_colour_kernel<T, TA, TZ><<<ceil_div(cnt, 128), 128, 0, s>>>(cnt, h->colour_rows + h->colour_ptr_h[c], c,
+                                                                       forward, A.rowptr, A.colidx, h->colour, val,
+                                                                       dinv, r, e, z, assign);
         MSRSB_LAUNCHED("gs_colour_kernel");
     }
     return MSRSB_OK;
 }
-template msrsb_status gs_apply<double, double>(const msrsb_handle *, const double *, const double *, int,
-                                               const double *, double *, double *, int, cudaStream_t);
-template msrsb_status gs_apply<float, float>(const msrsb_handle *, const float *, const float *, int, const float *,
-                                             float *, double *, int, cudaStream_t);
+template msrsb_status gs_apply<double, double, double>(const msrsb_handle *, const double *, const double *, int,
+                                                       const double *, double *, double *, int, cudaStream_t);
+template msrsb_status gs_apply<float, float, double>(const msrsb_handle *, const float *, const float *, int,
+                                                     const float *, float *, double *, int, cudaStream_t);
+template msrsb_status gs_apply<float, float, float>(const msrsb_handle *, const float *, const float *, int,
+                                                    const float *, float *, float *, int, cudaStream_t);
 
 }  // namespace msrsb
