@@ -125,6 +125,13 @@ msrsb_status norm2(long N, const double *w, double *partial, double *out, cudaSt
 msrsb_status mvsub(long N, int nvec, const double *V, long ldv, const double *h, double *w, cudaStream_t s);
 template <typename TZ>
 msrsb_status mvadd(long N, int nvec, const TZ *Z, long ldz, const double *y, double *x, cudaStream_t s);
+msrsb_status df_scale(long N, const double *r, const double *beta, float *vh, float *vl, cudaStream_t s);
+msrsb_status mdot_df(long N, int nv, const float *Vh, const float *Vl, long ldv, const float *Wh, const float *Wl,
+                     double *partial, double *hs, cudaStream_t s, const int *gate = nullptr);
+msrsb_status gs_update_df(long N, int nv, const float *Vh, const float *Vl, long ldv, const double *hs, float *Wh,
+                          float *Wl, float *oh, float *ol, double *hcol, int *flag, int pass, cudaStream_t s);
+msrsb_status sell_spmv_df(const Sell &S, const double *val, const double *x, float *yh, float *yl, cudaStream_t s);
+msrsb_status df_split(long N, const double *w, float *wh, float *wl, cudaStream_t s);
 template <typename TY>
 msrsb_status scale_by_inv(long N, const double *x, const double *den, TY *y, cudaStream_t s);
 msrsb_status axpy_dev(long N, const double *num, const double *den, double sign, const double *x, double *y,
@@ -300,20 +307,20 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
 // r = v - A z in the handle precision (FP32 values and accumulation in mixed
 // mode); scalar operators use the sliced-ELL copy, optionally writing row i
 // to position operm[i]. v and z are FP64 (outer Krylov) or FP32 (inner).
-template <typename T, typename TV>
-static msrsb_status resid_t(const msrsb_handle *h, const T *aval_t, const TV *z, const TV *v, T *r,
+template <typename T, typename TZ, typename TVI>
+static msrsb_status resid_t(const msrsb_handle *h, const T *aval_t, const TZ *z, const TVI *v, T *r,
                             const int32_t *operm, cudaStream_t s) {
     if (h->bdim == 1) {
         const T *sv = (const T *)h->asell.val[h->opts.prec == MSRSB_F32 ? 1 : 0];
-        return sell_spmv<T, TV, TV, T, T>(h->asell, sv, z, v, r, true, s, operm);
+        return sell_spmv<T, TZ, TVI, T, T>(h->asell, sv, z, v, r, true, s, operm);
     }
-    return spmv<T, TV, TV, T, T>(h->A, aval_t, z, v, r, true, s, operm);
+    return spmv<T, TZ, TVI, T, T>(h->A, aval_t, z, v, r, true, s, operm);
 }
 
 // Alg. 4 (Alg. 3 inside) from z = 0; the preconditioner's internals run in T,
-// its input and output vectors are TV
-template <typename T, typename TV>
-static msrsb_status apply_t(msrsb_handle *h, const TV *v, TV *z, cudaStream_t s) {
+// its input vector is TVI and its output TZ
+template <typename T, typename TVI, typename TZ>
+static msrsb_status apply_t(msrsb_handle *h, const TVI *v, TZ *z, cudaStream_t s) {
     const msrsb_mat &A = h->A;
     const long N = (long)h->n * h->bdim;
     const T *P = (const T *)h->p_val;
@@ -324,37 +331,37 @@ static msrsb_status apply_t(msrsb_handle *h, const TV *v, TV *z, cudaStream_t s)
     if (pre) {
         // z = M_pre^-1 v
         if (gs) {
-            MSRSB_TRY((copy_cast<TV, T>(N, v, r, s)));
-            MSRSB_TRY((gs_apply<T, T, TV>(h, aval_t, (const T *)h->dinv, 1, r, y, z, 1, s)));
+            MSRSB_TRY((copy_cast<TVI, T>(N, v, r, s)));
+            MSRSB_TRY((gs_apply<T, T, TZ>(h, aval_t, (const T *)h->dinv, 1, r, y, z, 1, s)));
         } else {
-            MSRSB_TRY((permute_cast<TV, T>(N, v, h->pos_of, r, s)));
-            MSRSB_CUDA(cudaMemsetAsync(z, 0, N * sizeof(TV), s));
-            MSRSB_TRY((ilu0_apply<T, TV>(h, r, y, z, s)));
+            MSRSB_TRY((permute_cast<TVI, T>(N, v, h->pos_of, r, s)));
+            MSRSB_CUDA(cudaMemsetAsync(z, 0, N * sizeof(TZ), s));
+            MSRSB_TRY((ilu0_apply<T, TZ>(h, r, y, z, s)));
         }
         // coarse correction of the residual v - A z
-        MSRSB_TRY((resid_t<T, TV>(h, aval_t, z, v, r, nullptr, s)));
+        MSRSB_TRY((resid_t<T, TZ, TVI>(h, aval_t, z, v, r, nullptr, s)));
         MSRSB_TRY((restrict_op<T, T>(h, P, r, h->vc, s)));
     } else {
-        MSRSB_TRY((restrict_op<T, TV>(h, P, v, h->vc, s)));
+        MSRSB_TRY((restrict_op<T, TVI>(h, P, v, h->vc, s)));
     }
     MSRSB_TRY(gemv(h->nC, h->Ainv, h->vc, h->wc, s));
-    MSRSB_TRY((prolong_op<T, TV>(h, P, h->wc, z, pre ? 1 : 0, s)));
+    MSRSB_TRY((prolong_op<T, TZ>(h, P, h->wc, z, pre ? 1 : 0, s)));
     if (post) {
         if (gs) {
-            MSRSB_TRY((resid_t<T, TV>(h, aval_t, z, v, r, nullptr, s)));
-            MSRSB_TRY((gs_apply<T, T, TV>(h, aval_t, (const T *)h->dinv, 0, r, y, z, 0, s)));
+            MSRSB_TRY((resid_t<T, TZ, TVI>(h, aval_t, z, v, r, nullptr, s)));
+            MSRSB_TRY((gs_apply<T, T, TZ>(h, aval_t, (const T *)h->dinv, 0, r, y, z, 0, s)));
         } else {
             // residual written straight into colour order for the sweeps
-            MSRSB_TRY((resid_t<T, TV>(h, aval_t, z, v, r, h->pos_of, s)));
-            MSRSB_TRY((ilu0_apply<T, TV>(h, r, y, z, s)));
+            MSRSB_TRY((resid_t<T, TZ, TVI>(h, aval_t, z, v, r, h->pos_of, s)));
+            MSRSB_TRY((ilu0_apply<T, TZ>(h, r, y, z, s)));
         }
     }
     return MSRSB_OK;
 }
 
 static msrsb_status apply_any(msrsb_handle *h, const double *v, double *z, cudaStream_t s) {
-    if (h->opts.prec == MSRSB_F32) return apply_t<float, double>(h, v, z, s);
-    return apply_t<double, double>(h, v, z, s);
+    if (h->opts.prec == MSRSB_F32) return apply_t<float, double, double>(h, v, z, s);
+    return apply_t<double, double, double>(h, v, z, s);
 }
 
 static msrsb_status fine_spmv(const msrsb_handle *h, const double *x, const double *v, double *y, bool resid,
@@ -482,22 +489,27 @@ __global__ void gmres_init_kernel(int m, double *__restrict__ kh, const double *
     g[0] = *beta;
 }
 
-// Restarted flexible GMRES with right preconditioning, FP64 Krylov vectors
-// (Z_j = M^-1 V_j kept, so the FP32 preconditioner of the mixed form is
-// handled exactly). Every cycle forms the true residual r = b - A x in FP64
-// (the refinement step of the mixed form) and ends when the rotated residual
-// estimate reaches rtol ||b|| or after m Arnoldi steps; x += Z y in FP64.
-// Iterations counted are Arnoldi steps (preconditioner applications).
-template <typename TV>
-static msrsb_status gmres_t(msrsb_handle *h, const double *b, double *x, double rtol, int maxit, double inner_tol,
-                            TV *V, TV *Z, int *iters, double *relres, double *hist, cudaStream_t s) {
-    static_assert(sizeof(TV) == sizeof(double), "Krylov vectors are FP64");
+// Restarted flexible GMRES with right preconditioning (Z_j = M^-1 V_j kept,
+// so an FP32 preconditioner is handled exactly). Every cycle forms the true
+// residual r = b - A x in FP64 and ends when the rotated residual estimate
+// reaches rtol ||b|| or after m Arnoldi steps; x += Z y in FP64. Iterations
+// counted are Arnoldi steps (preconditioner applications).
+// DFV = false: FP64 Krylov vectors (the FP64 form). DFV = true (mixed form):
+// the basis V is kept in double-float (two FP32 planes, ~48-bit mantissas) so
+// the Gram-Schmidt work runs on the FP32 pipe; the preconditioner reads the
+// high plane (its FP32 input); A Z_j, Z and x stay FP64.
+template <bool DFV>
+static msrsb_status gmres_t(msrsb_handle *h, const double *b, double *x, double rtol, int maxit, int *iters,
+                            double *relres, double *hist, cudaStream_t s) {
     const long N = (long)h->n * h->bdim;
     const int m = h->krylov_m;
     double *kh = h->kh;
     const KhLayout L(m);
     double *H = kh + L.H, *est = kh + L.est, *beta = kh + L.beta, *h2 = kh + L.h2;
     int *reorth = (int *)(kh + L.flag);
+    double *V = h->kv, *Z = h->kz;                    // FP64 basis (DFV = false)
+    // double-float basis and work vector of the mixed form: [Vh | Vl | Wh | Wl]
+    float *Vh = (float *)h->kv32, *Vl = Vh + (m + 1) * N, *Wh = Vl + (m + 1) * N, *Wl = Wh + N;
     double bnorm = 0.0;
     MSRSB_TRY(norm2(N, b, h->partial, beta, s));
     MSRSB_TRY(read_scalar(beta, &bnorm, s));
@@ -522,11 +534,14 @@ static msrsb_status gmres_t(msrsb_handle *h, const double *b, double *x, double 
             *iters = its;
             return fail(MSRSB_ENOCONV, "GMRES reached %d iterations (relres %.3e)", its, bt / bnorm);
         }
-        MSRSB_TRY(scale_by_inv<TV>(N, h->tmp_d, beta, V, s));
+        if (DFV)
+            MSRSB_TRY(df_scale(N, h->tmp_d, beta, Vh, Vl, s));
+        else
+            MSRSB_TRY(scale_by_inv<double>(N, h->tmp_d, beta, V, s));
         gmres_init_kernel<<<1, 1, 0, s>>>(m, kh, beta);
         MSRSB_LAUNCHED("gmres_init_kernel");
         const int mm = m < maxit - its ? m : maxit - its;
-        const double stop = inner_tol > 0.0 ? std::max(inner_tol * bt, rtol * bnorm) : rtol * bnorm;
+        const double stop = rtol * bnorm;
         // Arnoldi steps are launched back to back; the residual estimate of
         // step j is copied to pinned memory behind an event and looked at
         // without blocking before later launches (at most two steps ahead).
@@ -555,18 +570,34 @@ static msrsb_status gmres_t(msrsb_handle *h, const double *b, double *x, double 
                 }
                 if (conv >= 0) break;
             }
-            TV *Vj = V + j * N, *Zj = Z + j * N, *w = V + (j + 1) * N;
-            MSRSB_TRY(apply_any(h, Vj, Zj, s));
-            MSRSB_TRY(fine_spmv(h, Zj, nullptr, w, false, s));
-            double *hcol = H + (long)j * (m + 1);
-            // classical Gram-Schmidt with the DGKS re-orthogonalisation test:
-            // one multi-dot pass (V_0..V_j and w itself, stored as V_{j+1})
-            // and one fused update + normalisation; the second pass runs on
-            // the device only when the first lost more than half of |w|^2
-            MSRSB_TRY(mdot<TV>(N, j + 2, V, N, w, h->partial, h2, 0, s));
-            MSRSB_TRY(gs_update<TV>(N, j + 1, V, N, h2, w, hcol, reorth, 1, s));
-            MSRSB_TRY(mdot<TV>(N, j + 2, V, N, w, h->partial, h2, 0, s, reorth));
-            MSRSB_TRY(gs_update<TV>(N, j + 1, V, N, h2, w, hcol, reorth, 2, s));
+            double *Zj = Z + j * N, *hcol = H + (long)j * (m + 1);
+            if (DFV) {
+                MSRSB_TRY((apply_t<float, float, double>(h, Vh + j * N, Zj, s)));
+                if (h->bdim == 1) {
+                    MSRSB_TRY(sell_spmv_df(h->asell, (const double *)h->asell.val[0], Zj, Wh, Wl, s));
+                } else {
+                    MSRSB_TRY(fine_spmv(h, Zj, nullptr, h->kv, false, s));
+                    MSRSB_TRY(df_split(N, h->kv, Wh, Wl, s));
+                }
+                // classical Gram-Schmidt with the DGKS test (see below), double-float vectors
+                float *oh = Vh + (j + 1) * N, *ol = Vl + (j + 1) * N;
+                MSRSB_TRY(mdot_df(N, j + 1, Vh, Vl, N, Wh, Wl, h->partial, h2, s));
+                MSRSB_TRY(gs_update_df(N, j + 1, Vh, Vl, N, h2, Wh, Wl, oh, ol, hcol, reorth, 1, s));
+                MSRSB_TRY(mdot_df(N, j + 1, Vh, Vl, N, Wh, Wl, h->partial, h2, s, reorth));
+                MSRSB_TRY(gs_update_df(N, j + 1, Vh, Vl, N, h2, Wh, Wl, oh, ol, hcol, reorth, 2, s));
+            } else {
+                double *Vj = V + j * N, *w = V + (j + 1) * N;
+                MSRSB_TRY(apply_any(h, Vj, Zj, s));
+                MSRSB_TRY(fine_spmv(h, Zj, nullptr, w, false, s));
+                // classical Gram-Schmidt with the DGKS re-orthogonalisation test:
+                // one multi-dot pass (V_0..V_j and w itself, stored as V_{j+1})
+                // and one fused update + normalisation; the second pass runs on
+                // the device only when the first lost more than half of |w|^2
+                MSRSB_TRY(mdot<double>(N, j + 2, V, N, w, h->partial, h2, 0, s));
+                MSRSB_TRY(gs_update<double>(N, j + 1, V, N, h2, w, hcol, reorth, 1, s));
+                MSRSB_TRY(mdot<double>(N, j + 2, V, N, w, h->partial, h2, 0, s, reorth));
+                MSRSB_TRY(gs_update<double>(N, j + 1, V, N, h2, w, hcol, reorth, 2, s));
+            }
             givens_kernel<<<1, 32, 0, s>>>(m, j, kh);
             MSRSB_LAUNCHED("givens_kernel");
             launched = j + 1;
@@ -599,7 +630,7 @@ static msrsb_status gmres_t(msrsb_handle *h, const double *b, double *x, double 
         its += k;
         hess_solve_kernel<<<1, 1, 0, s>>>(m, k, kh);
         MSRSB_LAUNCHED("hess_solve_kernel");
-        MSRSB_TRY(mvadd<TV>(N, k, Z, N, kh + L.g, x, s));
+        MSRSB_TRY(mvadd<double>(N, k, Z, N, kh + L.g, x, s));
     }
     *iters = its;
     return MSRSB_OK;
@@ -607,7 +638,8 @@ static msrsb_status gmres_t(msrsb_handle *h, const double *b, double *x, double 
 
 static msrsb_status gmres(msrsb_handle *h, const double *b, double *x, double rtol, int maxit, int *iters,
                           double *relres, double *hist, cudaStream_t s) {
-    return gmres_t<double>(h, b, x, rtol, maxit, 0.0, h->kv, h->kz, iters, relres, hist, s);
+    if (h->opts.prec == MSRSB_F32) return gmres_t<true>(h, b, x, rtol, maxit, iters, relres, hist, s);
+    return gmres_t<false>(h, b, x, rtol, maxit, iters, relres, hist, s);
 }
 
 // ---- PCG ------------------------------------------------------------------------
@@ -730,6 +762,7 @@ static void handle_free(msrsb_handle *h) {
     dfree(h->y_t, s);
     dfree(h->kv, s);
     dfree(h->kz, s);
+    dfree(h->kv32, s);
     dfree(h->kh, s);
     dfree(h->partial, s);
     if (h->own_A) {
@@ -802,8 +835,14 @@ extern "C" msrsb_status msrsb_setup(const msrsb_mat *A, const msrsb_grid *g, con
     if (st == MSRSB_OK) {
         const long N = (long)n * A->bdim;
         const bool gm = opts->krylov == MSRSB_GMRES;
-        st = dalloc(&h->kv, (size_t)(gm ? m + 1 : 4) * N, stream);
+        const bool dfv = gm && opts->prec == MSRSB_F32;  // double-float basis of the mixed form
+        st = dalloc(&h->kv, (size_t)(gm && !dfv ? m + 1 : 4) * N, stream);
         if (st == MSRSB_OK && gm) st = dalloc(&h->kz, (size_t)m * N, stream);
+        if (st == MSRSB_OK && dfv) {
+            float *v32 = nullptr;
+            st = dalloc(&v32, (size_t)2 * (m + 2) * N, stream);
+            h->kv32 = v32;
+        }
         if (st == MSRSB_OK) st = dalloc(&h->kh, (size_t)KhLayout(m).total, stream);
     }
     if (st != MSRSB_OK) {

@@ -107,6 +107,9 @@ template msrsb_status spmv<float, double, double, float, float>(const msrsb_mat 
 template msrsb_status spmv<float, float, float, float, float>(const msrsb_mat &, const float *, const float *,
                                                               const float *, float *, bool, cudaStream_t,
                                                               const int32_t *);
+template msrsb_status spmv<float, double, float, float, float>(const msrsb_mat &, const float *, const double *,
+                                                               const float *, float *, bool, cudaStream_t,
+                                                               const int32_t *);
 
 // Sliced-ELL SpMV / residual: one thread per row, coalesced entry reads,
 // unrolled so several gathers are in flight. y[operm ? operm[i] : i] =
@@ -155,6 +158,9 @@ template msrsb_status sell_spmv<float, double, double, float, float>(const Sell 
 template msrsb_status sell_spmv<float, float, float, float, float>(const Sell &, const float *, const float *,
                                                                    const float *, float *, bool, cudaStream_t,
                                                                    const int32_t *);
+template msrsb_status sell_spmv<float, double, float, float, float>(const Sell &, const float *, const double *,
+                                                                    const float *, float *, bool, cudaStream_t,
+                                                                    const int32_t *);
 
 // ---- restriction and prolongation ------------------------------------------------
 
@@ -533,5 +539,227 @@ msrsb_status copy_cast(long N, const TI *x, TO *y, cudaStream_t s) {
 template msrsb_status copy_cast<double, float>(long, const double *, float *, cudaStream_t);
 template msrsb_status copy_cast<double, double>(long, const double *, double *, cudaStream_t);
 template msrsb_status copy_cast<float, float>(long, const float *, float *, cudaStream_t);
+
+}  // namespace msrsb
+
+// ---- double-float Krylov vectors (mixed form) ----------------------------------------
+//
+// A Krylov vector v is stored as two FP32 planes, v = hi + lo with |lo| <= ulp(hi)/2
+// (about 48 significant bits). Products are formed exactly as p + e
+// (e = fma(a, b, -p)) and summed with error-free additions (Knuth TwoSum), so
+// dot products and updates run on the FP32 pipe with close-to-FP64 accuracy;
+// only O(1) FP64 operations per element remain.
+
+namespace msrsb {
+
+struct DF {
+    float hi, lo;
+};
+
+// Double-float arithmetic (Dekker 1971; Knuth TAOCP vol. 2, 4.2.2): a value
+// is hi + lo with |lo| <= ulp(hi)/2. The _rn intrinsics keep the compiler
+// from contracting the error-free transformations into FMAs.
+__device__ __forceinline__ DF df_from(double x) {
+    float h = (float)x;
+    return DF{h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ DF quick_two_sum(float a, float b) {  // |a| >= |b|
+    const float s = __fadd_rn(a, b);
+    return DF{s, __fadd_rn(b, -__fadd_rn(s, -a))};
+}
+__device__ __forceinline__ DF two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fadd_rn(s, -a);
+    return DF{s, __fadd_rn(__fadd_rn(a, -__fadd_rn(s, -bb)), __fadd_rn(b, -bb))};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    const DF t = two_sum(a.hi, b.hi);
+    return quick_two_sum(t.hi, __fadd_rn(t.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+    return quick_two_sum(p, e);
+}
+// s += a * b; s is an unnormalised accumulator (hi, lo), the lo*lo term is
+// below the format's precision
+__device__ __forceinline__ void df_fma_acc(DF &s, float ah, float al, float bh, float bl) {
+    const float p = __fmul_rn(ah, bh);
+    const float e = fmaf(ah, bh, -p);
+    const DF t = two_sum(s.hi, p);
+    s.hi = t.hi;
+    s.lo = __fadd_rn(s.lo, __fadd_rn(t.lo, fmaf(ah, bl, fmaf(al, bh, e))));
+}
+__device__ __forceinline__ DF df_shfl_down(DF v, int o) {
+    return DF{__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
+}
+
+// V_0 planes = r / beta
+__global__ void df_scale_kernel(long N, const double *__restrict__ r, const double *__restrict__ beta,
+                                float *__restrict__ vh, float *__restrict__ vl) {
+    long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double b = *beta;
+    const DF d = df_from(b != 0.0 ? r[i] / b : 0.0);
+    vh[i] = d.hi;
+    vl[i] = d.lo;
+}
+
+msrsb_status df_scale(long N, const double *r, const double *beta, float *vh, float *vl, cudaStream_t s) {
+    df_scale_kernel<<<ceil_div(N, 256), 256, 0, s>>>(N, r, beta, vh, vl);
+    MSRSB_LAUNCHED("df_scale_kernel");
+    return MSRSB_OK;
+}
+
+// y = A x (FP64 sliced ELL, FP64 accumulation) written as double-float planes
+__global__ void __launch_bounds__(256) sell_spmv_df_kernel(int n, const int32_t *__restrict__ slice_ptr,
+                                                           const int32_t *__restrict__ scol,
+                                                           const double *__restrict__ sval,
+                                                           const double *__restrict__ x, float *__restrict__ yh,
+                                                           float *__restrict__ yl) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int s = i >> 5, lane = i & 31;
+    const int beg = slice_ptr[s], width = (slice_ptr[s + 1] - beg) >> 5;
+    const int32_t *cp = scol + beg + lane;
+    const double *vp = sval + beg + lane;
+    double acc0 = 0.0, acc1 = 0.0;
+    int j = 0;
+    for (; j + 1 < width; j += 2) {
+        acc0 = fma(__ldg(vp + (j << 5)), __ldg(x + __ldg(cp + (j << 5))), acc0);
+        acc1 = fma(__ldg(vp + ((j + 1) << 5)), __ldg(x + __ldg(cp + ((j + 1) << 5))), acc1);
+    }
+    if (j < width) acc0 = fma(__ldg(vp + (j << 5)), __ldg(x + __ldg(cp + (j << 5))), acc0);
+    const DF d = df_from(acc0 + acc1);
+    yh[i] = d.hi;
+    yl[i] = d.lo;
+}
+
+msrsb_status sell_spmv_df(const Sell &S, const double *val, const double *x, float *yh, float *yl, cudaStream_t s) {
+    sell_spmv_df_kernel<<<ceil_div(S.n, 256), 256, 0, s>>>(S.n, S.slice_ptr, S.col, val, x, yh, yl);
+    MSRSB_LAUNCHED("sell_spmv_df_kernel");
+    return MSRSB_OK;
+}
+
+// FP64 vector to double-float planes
+__global__ void df_split_kernel(long N, const double *__restrict__ w, float *__restrict__ wh, float *__restrict__ wl) {
+    long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const DF d = df_from(w[i]);
+    wh[i] = d.hi;
+    wl[i] = d.lo;
+}
+
+msrsb_status df_split(long N, const double *w, float *wh, float *wl, cudaStream_t s) {
+    df_split_kernel<<<ceil_div(N, 256), 256, 0, s>>>(N, w, wh, wl);
+    MSRSB_LAUNCHED("df_split_kernel");
+    return MSRSB_OK;
+}
+
+// partial[q * gridDim.x + b] = sum over row chunk b of V_q . w (q < nv), and
+// for q = nv the squared norm of w; all vectors double-float, FP32 arithmetic
+// up to the per-warp results
+__global__ void __launch_bounds__(256) mdot_df_kernel(long N, int nv, const float *__restrict__ Vh,
+                                                      const float *__restrict__ Vl, long ldv,
+                                                      const float *__restrict__ Wh, const float *__restrict__ Wl,
+                                                      double *__restrict__ partial, const int *__restrict__ gate) {
+    if (gate && !*gate) return;
+    __shared__ double red[8];
+    const int q = blockIdx.y;
+    const long chunk = (N + gridDim.x - 1) / gridDim.x;
+    const long b0 = blockIdx.x * chunk, b1 = b0 + chunk < N ? b0 + chunk : N;
+    const float *vh = q < nv ? Vh + q * ldv : Wh, *vl = q < nv ? Vl + q * ldv : Wl;
+    DF s0{0.f, 0.f}, s1{0.f, 0.f};
+    long i = b0 + threadIdx.x;
+    const long bd = blockDim.x;
+    for (; i + bd < b1; i += 2 * bd) {
+        df_fma_acc(s0, vh[i], vl[i], Wh[i], Wl[i]);
+        df_fma_acc(s1, vh[i + bd], vl[i + bd], Wh[i + bd], Wl[i + bd]);
+    }
+    if (i < b1) df_fma_acc(s0, vh[i], vl[i], Wh[i], Wl[i]);
+    DF t = df_add(two_sum(s0.hi, s0.lo), two_sum(s1.hi, s1.lo));
+    for (int o = 16; o > 0; o >>= 1) t = df_add(t, df_shfl_down(t, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)t.hi + (double)t.lo;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        v = warp_sum(v);
+        if (threadIdx.x == 0) partial[(long)q * gridDim.x + blockIdx.x] = v;
+    }
+}
+
+__global__ void reduce_partials_kernel(int nblk, const double *__restrict__ partial, double *__restrict__ out,
+                                       int accumulate, int sqrt_out, const int *__restrict__ gate);
+
+// hs[q] = V_q . w (q < nv), hs[nv] = w . w
+msrsb_status mdot_df(long N, int nv, const float *Vh, const float *Vl, long ldv, const float *Wh, const float *Wl,
+                     double *partial, double *hs, cudaStream_t s, const int *gate) {
+    dim3 grid(kRedBlocks, nv + 1);
+    mdot_df_kernel<<<grid, 256, 0, s>>>(N, nv, Vh, Vl, ldv, Wh, Wl, partial, gate);
+    MSRSB_LAUNCHED("mdot_df_kernel");
+    reduce_partials_kernel<<<nv + 1, 256, 0, s>>>(kRedBlocks, partial, hs, 0, 0, gate);
+    MSRSB_LAUNCHED("reduce_partials_kernel");
+    return MSRSB_OK;
+}
+
+// Classical Gram-Schmidt update with the DGKS test (as gs_update_kernel) on
+// double-float vectors: w1 = w - sum_q V_q hs[q]; if normalised (pass 2, or
+// no severe cancellation) V_new = w1 / |w1|, else w1 goes back to w for the
+// second pass and *flag = 1.
+__global__ void __launch_bounds__(256) gs_update_df_kernel(long N, int nv, const float *__restrict__ Vh,
+                                                           const float *__restrict__ Vl, long ldv,
+                                                           const double *__restrict__ hs, float *__restrict__ Wh,
+                                                           float *__restrict__ Wl, float *__restrict__ oh,
+                                                           float *__restrict__ ol, double *__restrict__ hcol,
+                                                           int *__restrict__ flag, int pass) {
+    if (pass == 2 && !*flag) return;
+    __shared__ float hh[1024], hl[1024];
+    __shared__ DF s_scale;
+    __shared__ int s_norm;
+    for (int q = threadIdx.x; q < nv; q += blockDim.x) {
+        const DF d = df_from(-hs[q]);
+        hh[q] = d.hi;
+        hl[q] = d.lo;
+    }
+    if (threadIdx.x == 0) {
+        double pr = 0.0;
+        for (int q = 0; q < nv; ++q) pr = fma(hs[q], hs[q], pr);
+        const double ww = hs[nv];
+        const double d2 = ww - pr;
+        const int norm = pass == 2 || d2 >= 0.5 * ww;
+        const double den = norm && d2 > 0.0 ? sqrt(d2) : 0.0;
+        s_norm = norm;
+        s_scale = df_from(den > 0.0 ? 1.0 / den : (norm ? 0.0 : 1.0));
+        if (blockIdx.x == 0) {
+            for (int q = 0; q < nv; ++q) hcol[q] = pass == 1 ? hs[q] : hcol[q] + hs[q];
+            if (norm) hcol[nv] = den;
+            if (pass == 1) *flag = !norm;
+        }
+    }
+    __syncthreads();
+    const DF sc = s_scale;
+    const bool norm = s_norm;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
+        DF acc{Wh[i], Wl[i]};
+        for (int q = 0; q < nv; ++q) df_fma_acc(acc, Vh[q * ldv + i], Vl[q * ldv + i], hh[q], hl[q]);
+        const DF x = df_mul(two_sum(acc.hi, acc.lo), sc);
+        if (norm) {
+            oh[i] = x.hi;
+            ol[i] = x.lo;
+        } else {
+            Wh[i] = x.hi;
+            Wl[i] = x.lo;
+        }
+    }
+}
+
+msrsb_status gs_update_df(long N, int nv, const float *Vh, const float *Vl, long ldv, const double *hs, float *Wh,
+                          float *Wl, float *oh, float *ol, double *hcol, int *flag, int pass, cudaStream_t s) {
+    const int grid = ceil_div(N, 256) < 2048 ? (int)ceil_div(N, 256) : 2048;
+    gs_update_df_kernel<<<grid, 256, 0, s>>>(N, nv, Vh, Vl, ldv, hs, Wh, Wl, oh, ol, hcol, flag, pass);
+    MSRSB_LAUNCHED("gs_update_df_kernel");
+    return MSRSB_OK;
+}
 
 }  // namespace msrsb

@@ -153,6 +153,7 @@ struct msrsb_handle {
     void *r_t = nullptr, *y_t = nullptr;
     // Krylov workspace
     double *kv = nullptr, *kz = nullptr;   // GMRES V [(m+1)][N], Z [m][N]; PCG uses first columns
+    void *kv32 = nullptr;                  // double-float GMRES basis of the mixed form: hi, lo planes
     double *kh = nullptr;                  // device Hessenberg/Givens state
     double *partial = nullptr;             // reduction partials
     double *host_scalars = nullptr;        // pinned
