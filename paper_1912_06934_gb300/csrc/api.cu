@@ -386,12 +386,12 @@ static msrsb_status read_scalar(const double *d, double *out, cudaStream_t s) {
 }
 
 __global__ void vadd_kernel(int n, const double *__restrict__ a, double *__restrict__ b) {
+    pdl_prologue();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) b[i] += a[i];
 }
 msrsb_status vadd(int n, const double *a, double *b, cudaStream_t s) {
-    vadd_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, a, b);
-    MSRSB_LAUNCHED("vadd_kernel");
+    MSRSB_PDL((vadd_kernel), ceil_div(n, 256), 256, 0, s, n, a, b);
     return MSRSB_OK;
 }
 
@@ -439,6 +439,7 @@ static cudaEvent_t *event_pool(int need) {
 // form the new one, update g; est = |g[j+1]|. State layout in kh:
 // H[(m+1) x m] column-major | cs[m] | sn[m] | g[m+1] | est
 __global__ void givens_kernel(int m, int j, double *__restrict__ kh) {
+    pdl_prologue();
     // one warp: stage column j and the rotations in shared memory, then apply
     // them sequentially (thread 0) without global-memory round trips
     __shared__ double col[514], c_s[512], s_s[512];
@@ -475,6 +476,7 @@ __global__ void givens_kernel(int m, int j, double *__restrict__ kh) {
 
 // back substitution H(0:k,0:k) y = g(0:k); y written over g
 __global__ void hess_solve_kernel(int m, int k, double *__restrict__ kh) {
+    pdl_prologue();
     double *H = kh, *g = kh + (long)(m + 1) * m + 2 * m;
     for (int i = k - 1; i >= 0; --i) {
         double s = g[i];
@@ -484,6 +486,7 @@ __global__ void hess_solve_kernel(int m, int k, double *__restrict__ kh) {
 }
 
 __global__ void gmres_init_kernel(int m, double *__restrict__ kh, const double *__restrict__ beta) {
+    pdl_prologue();
     double *g = kh + (long)(m + 1) * m + 2 * m;
     for (int i = 0; i <= m; ++i) g[i] = 0.0;
     g[0] = *beta;
@@ -538,8 +541,7 @@ static msrsb_status gmres_t(msrsb_handle *h, const double *b, double *x, double 
             MSRSB_TRY(df_scale(N, h->tmp_d, beta, Vh, Vl, s));
         else
             MSRSB_TRY(scale_by_inv<double>(N, h->tmp_d, beta, V, s));
-        gmres_init_kernel<<<1, 1, 0, s>>>(m, kh, beta);
-        MSRSB_LAUNCHED("gmres_init_kernel");
+        MSRSB_PDL((gmres_init_kernel), 1, 1, 0, s, m, kh, beta);
         const int mm = m < maxit - its ? m : maxit - its;
         const double stop = rtol * bnorm;
         // Arnoldi steps are launched back to back; the residual estimate of
@@ -598,8 +600,7 @@ static msrsb_status gmres_t(msrsb_handle *h, const double *b, double *x, double 
                 MSRSB_TRY(mdot<double>(N, j + 2, V, N, w, h->partial, h2, 0, s, reorth));
                 MSRSB_TRY(gs_update<double>(N, j + 1, V, N, h2, w, hcol, reorth, 2, s));
             }
-            givens_kernel<<<1, 32, 0, s>>>(m, j, kh);
-            MSRSB_LAUNCHED("givens_kernel");
+            MSRSB_PDL((givens_kernel), 1, 32, 0, s, m, j, kh);
             launched = j + 1;
             if (lagged) {
                 MSRSB_CUDA(cudaMemcpyAsync(pin_est + j, kh + L.hist + j, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -628,8 +629,7 @@ static msrsb_status gmres_t(msrsb_handle *h, const double *b, double *x, double 
         }
         const int k = conv >= 0 ? conv + 1 : launched;
         its += k;
-        hess_solve_kernel<<<1, 1, 0, s>>>(m, k, kh);
-        MSRSB_LAUNCHED("hess_solve_kernel");
+        MSRSB_PDL((hess_solve_kernel), 1, 1, 0, s, m, k, kh);
         MSRSB_TRY(mvadd<double>(N, k, Z, N, kh + L.g, x, s));
     }
     *iters = its;

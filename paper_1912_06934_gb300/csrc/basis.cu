@@ -43,6 +43,7 @@ __global__ void __launch_bounds__(256) smooth_kernel(int n, const int32_t *__res
                                                      T *__restrict__ Pout, unsigned long long *__restrict__ emax,
                                                      int check, const int *__restrict__ done, int *__restrict__ iters,
                                                      int k_pass) {
+    pdl_prologue();
     if (*done) return;  // an earlier check met the tolerance: uniform exit
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) *iters = k_pass + 1;
@@ -99,6 +100,7 @@ __global__ void __launch_bounds__(256) smooth_kernel(int n, const int32_t *__res
 
 __global__ void basis_check_kernel(const unsigned long long *__restrict__ emax_k, double tol, int *__restrict__ done,
                                    double *__restrict__ e_last) {
+    pdl_prologue();
     if (*done) return;
     double e = __longlong_as_double((long long)*emax_k);
     *e_last = e;
@@ -137,12 +139,13 @@ double *pinned_scratch() {
 }
 
 template <typename T, int W>
-static void launch_smooth(int n, const Sell &S, int comp, const T *scale, const uint8_t *vmask, const uint8_t *skel,
+static msrsb_status launch_smooth(int n, const Sell &S, int comp, const T *scale, const uint8_t *vmask, const uint8_t *skel,
                           const T *Pin, T *Pout, unsigned long long *emax, int check, const int *done, int *iters,
                           int k, cudaStream_t s) {
     int grid = ceil_div((long)S.nslices * kSell, 256);
-    smooth_kernel<T, W><<<grid, 256, 0, s>>>(n, S.slice_ptr, S.col, (const T *)S.val[comp], scale, vmask, skel, Pin,
-                                             Pout, emax, check, done, iters, k);
+    MSRSB_PDL((smooth_kernel<T, W>), grid, 256, 0, s, n, S.slice_ptr, S.col, (const T *)S.val[comp], scale, vmask, skel,
+              Pin, Pout, emax, check, done, iters, k);
+    return MSRSB_OK;
 }
 
 // Alg. 1 loop on one basis family. P (device, [n][W]) holds the initial
@@ -188,17 +191,15 @@ msrsb_status basis_loop(int n, int W, const Sell &S, int comp, const T *scale, c
         }
         if (prof) MSRSB_CUDA(cudaEventRecord(tev[2 * k], s));
         if (W == 4)
-            launch_smooth<T, 4>(n, S, comp, scale, vmask, skel, buf[k & 1], buf[(k + 1) & 1], emax + k, check, flags,
-                                flags + 1, k, s);
+            MSRSB_TRY((launch_smooth<T, 4>(n, S, comp, scale, vmask, skel, buf[k & 1], buf[(k + 1) & 1], emax + k,
+                                           check, flags, flags + 1, k, s)));
         else
-            launch_smooth<T, 8>(n, S, comp, scale, vmask, skel, buf[k & 1], buf[(k + 1) & 1], emax + k, check, flags,
-                                flags + 1, k, s);
-        MSRSB_LAUNCHED("smooth_kernel");
+            MSRSB_TRY((launch_smooth<T, 8>(n, S, comp, scale, vmask, skel, buf[k & 1], buf[(k + 1) & 1], emax + k,
+                                           check, flags, flags + 1, k, s)));
         if (prof) MSRSB_CUDA(cudaEventRecord(tev[2 * k + 1], s));
         launched = k + 1;
         if (check) {
-            basis_check_kernel<<<1, 1, 0, s>>>(emax + k, o->tol, flags, e_last);
-            MSRSB_LAUNCHED("basis_check_kernel");
+            MSRSB_PDL((basis_check_kernel), 1, 1, 0, s, emax + k, o->tol, flags, e_last);
             if (pin && !pending) {
                 // copy the done flag (as a double) for a lagged, non-blocking look
                 MSRSB_CUDA(cudaMemcpyAsync(pin, flags, sizeof(int), cudaMemcpyDeviceToHost, s));

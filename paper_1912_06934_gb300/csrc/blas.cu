@@ -14,6 +14,7 @@ __global__ void __launch_bounds__(256) csr_spmv_kernel(int n, const int32_t *__r
                                                        const int32_t *__restrict__ colidx, const TA *__restrict__ val,
                                                        const TX *__restrict__ x, const TV *__restrict__ v,
                                                        TY *__restrict__ y, const int32_t *__restrict__ operm) {
+    pdl_prologue();
     int row = (blockIdx.x * blockDim.x + threadIdx.x) / G;
     int g = threadIdx.x % G;
     if (row >= n) return;  // whole groups leave together (n rows, G | 32)
@@ -29,13 +30,12 @@ msrsb_status csr_spmv(int n, int nnz, const int32_t *rowptr, const int32_t *coli
                       const TV *v, TY *y, const int32_t *operm, cudaStream_t s) {
     double avg = (double)nnz / n;
     if (avg > 12) {
-        csr_spmv_kernel<8, TA, TX, TV, TY, TACC, RESID><<<ceil_div((long)n * 8, 256), 256, 0, s>>>(n, rowptr, colidx,
-                                                                                                   val, x, v, y, operm);
+        MSRSB_PDL((csr_spmv_kernel<8, TA, TX, TV, TY, TACC, RESID>), ceil_div((long)n * 8, 256), 256, 0, s, n, rowptr,
+                  colidx, val, x, v, y, operm);
     } else {
-        csr_spmv_kernel<4, TA, TX, TV, TY, TACC, RESID><<<ceil_div((long)n * 4, 256), 256, 0, s>>>(n, rowptr, colidx,
-                                                                                                   val, x, v, y, operm);
+        MSRSB_PDL((csr_spmv_kernel<4, TA, TX, TV, TY, TACC, RESID>), ceil_div((long)n * 4, 256), 256, 0, s, n, rowptr,
+                  colidx, val, x, v, y, operm);
     }
-    MSRSB_LAUNCHED("csr_spmv_kernel");
     return MSRSB_OK;
 }
 
@@ -45,6 +45,7 @@ __global__ void __launch_bounds__(256) bsr_spmv_kernel(int n, const int32_t *__r
                                                        const int32_t *__restrict__ colidx, const TA *__restrict__ val,
                                                        const TX *__restrict__ x, const TV *__restrict__ v,
                                                        TY *__restrict__ y) {
+    pdl_prologue();
     constexpr int G = 4;
     int row = (blockIdx.x * blockDim.x + threadIdx.x) / G;
     int g = threadIdx.x % G;
@@ -91,10 +92,11 @@ msrsb_status spmv(const msrsb_mat &A, const TA *val, const TX *x, const TV *v, T
     if (operm) return fail(MSRSB_EINVAL, "output permutation is only supported for bdim 1");
     int grid = ceil_div((long)A.nrows * 4, 256);
     if (resid)
-        bsr_spmv_kernel<TA, TX, TV, TY, TACC, true><<<grid, 256, 0, s>>>(A.nrows, A.rowptr, A.colidx, val, x, v, y);
+        MSRSB_PDL((bsr_spmv_kernel<TA, TX, TV, TY, TACC, true>), grid, 256, 0, s, A.nrows, A.rowptr, A.colidx, val, x,
+                  v, y);
     else
-        bsr_spmv_kernel<TA, TX, TV, TY, TACC, false><<<grid, 256, 0, s>>>(A.nrows, A.rowptr, A.colidx, val, x, v, y);
-    MSRSB_LAUNCHED("bsr_spmv_kernel");
+        MSRSB_PDL((bsr_spmv_kernel<TA, TX, TV, TY, TACC, false>), grid, 256, 0, s, A.nrows, A.rowptr, A.colidx, val, x,
+                  v, y);
     return MSRSB_OK;
 }
 // instantiations used by the library
@@ -119,6 +121,7 @@ __global__ void __launch_bounds__(256) sell_spmv_kernel(int n, const int32_t *__
                                                         const int32_t *__restrict__ scol, const TA *__restrict__ sval,
                                                         const TX *__restrict__ x, const TV *__restrict__ v,
                                                         TY *__restrict__ y, const int32_t *__restrict__ operm) {
+    pdl_prologue();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int s = i >> 5, lane = i & 31;
@@ -141,12 +144,11 @@ msrsb_status sell_spmv(const Sell &S, const TA *val, const TX *x, const TV *v, T
                        const int32_t *operm) {
     const int grid = ceil_div(S.n, 256);
     if (resid)
-        sell_spmv_kernel<TA, TX, TV, TY, TACC, true><<<grid, 256, 0, s>>>(S.n, S.slice_ptr, S.col, val, x, v, y,
-                                                                          operm);
+        MSRSB_PDL((sell_spmv_kernel<TA, TX, TV, TY, TACC, true>), grid, 256, 0, s, S.n, S.slice_ptr, S.col, val, x, v,
+                  y, operm);
     else
-        sell_spmv_kernel<TA, TX, TV, TY, TACC, false><<<grid, 256, 0, s>>>(S.n, S.slice_ptr, S.col, val, x, v, y,
-                                                                           operm);
-    MSRSB_LAUNCHED("sell_spmv_kernel");
+        MSRSB_PDL((sell_spmv_kernel<TA, TX, TV, TY, TACC, false>), grid, 256, 0, s, S.n, S.slice_ptr, S.col, val, x, v,
+                  y, operm);
     return MSRSB_OK;
 }
 template msrsb_status sell_spmv<double, double, double, double, double>(const Sell &, const double *, const double *,
@@ -171,6 +173,7 @@ __global__ void __launch_bounds__(256) restrict_kernel(int nc, int n, int W, int
                                                        const int32_t *__restrict__ pt_rows,
                                                        const int8_t *__restrict__ jslot, const TP *__restrict__ P,
                                                        const TV *__restrict__ v, double *__restrict__ vc) {
+    pdl_prologue();
     __shared__ double red[3][8];
     const int J = blockIdx.x;
     const int sj = jslot[J];
@@ -208,9 +211,8 @@ __global__ void __launch_bounds__(256) restrict_kernel(int nc, int n, int W, int
 
 template <typename TP, typename TV>
 msrsb_status restrict_op(const msrsb_handle *h, const TP *P, const TV *v, double *vc, cudaStream_t s) {
-    restrict_kernel<TP, TV><<<h->nc, 256, 0, s>>>(h->nc, h->n, h->W, h->bdim, h->pt_ptr, h->pt_rows, h->jslot, P, v,
-                                                  vc);
-    MSRSB_LAUNCHED("restrict_kernel");
+    MSRSB_PDL((restrict_kernel<TP, TV>), h->nc, 256, 0, s, h->nc, h->n, h->W, h->bdim, h->pt_ptr, h->pt_rows, h->jslot,
+              P, v, vc);
     return MSRSB_OK;
 }
 template msrsb_status restrict_op<double, double>(const msrsb_handle *, const double *, const double *, double *,
@@ -226,6 +228,7 @@ template <typename TP, typename TZ, int W>
 __global__ void __launch_bounds__(256) prolong_kernel(int n, int bd, const int32_t *__restrict__ p_ids,
                                                       const TP *__restrict__ P, const double *__restrict__ wc,
                                                       TZ *__restrict__ z, int add) {
+    pdl_prologue();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const long nW = (long)n * W;
@@ -252,10 +255,9 @@ __global__ void __launch_bounds__(256) prolong_kernel(int n, int bd, const int32
 template <typename TP, typename TZ>
 msrsb_status prolong_op(const msrsb_handle *h, const TP *P, const double *wc, TZ *z, int add, cudaStream_t s) {
     if (h->W == 8)
-        prolong_kernel<TP, TZ, 8><<<ceil_div(h->n, 256), 256, 0, s>>>(h->n, h->bdim, h->p_ids, P, wc, z, add);
+        MSRSB_PDL((prolong_kernel<TP, TZ, 8>), ceil_div(h->n, 256), 256, 0, s, h->n, h->bdim, h->p_ids, P, wc, z, add);
     else
-        prolong_kernel<TP, TZ, 4><<<ceil_div(h->n, 256), 256, 0, s>>>(h->n, h->bdim, h->p_ids, P, wc, z, add);
-    MSRSB_LAUNCHED("prolong_kernel");
+        MSRSB_PDL((prolong_kernel<TP, TZ, 4>), ceil_div(h->n, 256), 256, 0, s, h->n, h->bdim, h->p_ids, P, wc, z, add);
     return MSRSB_OK;
 }
 template msrsb_status prolong_op<double, double>(const msrsb_handle *, const double *, const double *, double *, int,
@@ -276,6 +278,7 @@ template <typename TV>
 __global__ void __launch_bounds__(256) mdot_kernel(long N, const TV *__restrict__ V, long ldv,
                                                    const TV *__restrict__ w, double *__restrict__ partial,
                                                    const int *__restrict__ gate) {
+    pdl_prologue();
     if (gate && !*gate) return;
     __shared__ double red[8];
     const int j = blockIdx.y;
@@ -307,6 +310,7 @@ __global__ void __launch_bounds__(256) mdot_kernel(long N, const TV *__restrict_
 // out[j] = (accumulate ? out[j] : 0) + sum_b partial[j][b]; block per j
 __global__ void reduce_partials_kernel(int nblk, const double *__restrict__ partial, double *__restrict__ out,
                                        int accumulate, int sqrt_out, const int *__restrict__ gate) {
+    pdl_prologue();
     if (gate && !*gate) return;
     __shared__ double red[8];
     int j = blockIdx.x;
@@ -330,10 +334,8 @@ template <typename TV>
 msrsb_status mdot(long N, int nvec, const TV *V, long ldv, const TV *w, double *partial, double *out, int accumulate,
                   cudaStream_t s, const int *gate) {
     dim3 grid(kRedBlocks, nvec);
-    mdot_kernel<TV><<<grid, 256, 0, s>>>(N, V, ldv, w, partial, gate);
-    MSRSB_LAUNCHED("mdot_kernel");
-    reduce_partials_kernel<<<nvec, 256, 0, s>>>(kRedBlocks, partial, out, accumulate, 0, gate);
-    MSRSB_LAUNCHED("reduce_partials_kernel");
+    MSRSB_PDL((mdot_kernel<TV>), grid, 256, 0, s, N, V, ldv, w, partial, gate);
+    MSRSB_PDL((reduce_partials_kernel), nvec, 256, 0, s, kRedBlocks, partial, out, accumulate, 0, gate);
     return MSRSB_OK;
 }
 template msrsb_status mdot<double>(long, int, const double *, long, const double *, double *, double *, int,
@@ -343,10 +345,8 @@ template msrsb_status mdot<float>(long, int, const float *, long, const float *,
 
 msrsb_status norm2(long N, const double *w, double *partial, double *out, cudaStream_t s) {
     dim3 grid(kRedBlocks, 1);
-    mdot_kernel<double><<<grid, 256, 0, s>>>(N, w, N, w, partial, nullptr);
-    MSRSB_LAUNCHED("mdot_kernel");
-    reduce_partials_kernel<<<1, 256, 0, s>>>(kRedBlocks, partial, out, 0, 1, nullptr);
-    MSRSB_LAUNCHED("reduce_partials_kernel");
+    MSRSB_PDL((mdot_kernel<double>), grid, 256, 0, s, N, w, N, w, partial, nullptr);
+    MSRSB_PDL((reduce_partials_kernel), 1, 256, 0, s, kRedBlocks, partial, out, 0, 1, nullptr);
     return MSRSB_OK;
 }
 
@@ -361,6 +361,7 @@ template <typename TV>
 __global__ void __launch_bounds__(256) gs_update_kernel(long N, int nv, const TV *__restrict__ V, long ldv,
                                                         const double *__restrict__ hs, TV *__restrict__ w,
                                                         double *__restrict__ hcol, int *__restrict__ flag, int pass) {
+    pdl_prologue();
     if (pass == 2 && !*flag) return;
     __shared__ double hsh[1024];
     __shared__ TV hst[1024];
@@ -405,9 +406,8 @@ __global__ void __launch_bounds__(256) gs_update_kernel(long N, int nv, const TV
 template <typename TV>
 msrsb_status gs_update(long N, int nv, const TV *V, long ldv, const double *hs, TV *w, double *hcol, int *flag,
                        int pass, cudaStream_t s) {
-    gs_update_kernel<TV><<<ceil_div(N, 256) < 2048 ? ceil_div(N, 256) : 2048, 256, 0, s>>>(N, nv, V, ldv, hs, w, hcol,
-                                                                                           flag, pass);
-    MSRSB_LAUNCHED("gs_update_kernel");
+    MSRSB_PDL((gs_update_kernel<TV>), ceil_div(N, 256) < 2048 ? ceil_div(N, 256) : 2048, 256, 0, s, N, nv, V, ldv, hs,
+              w, hcol, flag, pass);
     return MSRSB_OK;
 }
 template msrsb_status gs_update<double>(long, int, const double *, long, const double *, double *, double *, int *, int,
@@ -418,6 +418,7 @@ template msrsb_status gs_update<float>(long, int, const float *, long, const dou
 // w -= sum_j V_j h[j]  (h staged in shared memory)
 __global__ void mvsub_kernel(long N, int nvec, const double *__restrict__ V, long ldv, const double *__restrict__ h,
                              double *__restrict__ w) {
+    pdl_prologue();
     __shared__ double hs[1024];
     for (int j = threadIdx.x; j < nvec; j += blockDim.x) hs[j] = h[j];
     __syncthreads();
@@ -429,8 +430,7 @@ __global__ void mvsub_kernel(long N, int nvec, const double *__restrict__ V, lon
 }
 
 msrsb_status mvsub(long N, int nvec, const double *V, long ldv, const double *h, double *w, cudaStream_t s) {
-    mvsub_kernel<<<ceil_div(N, 256), 256, 0, s>>>(N, nvec, V, ldv, h, w);
-    MSRSB_LAUNCHED("mvsub_kernel");
+    MSRSB_PDL((mvsub_kernel), ceil_div(N, 256), 256, 0, s, N, nvec, V, ldv, h, w);
     return MSRSB_OK;
 }
 
@@ -438,6 +438,7 @@ msrsb_status mvsub(long N, int nvec, const double *V, long ldv, const double *h,
 template <typename TZ>
 __global__ void mvadd_kernel(long N, int nvec, const TZ *__restrict__ Z, long ldz, const double *__restrict__ y,
                              double *__restrict__ x) {
+    pdl_prologue();
     __shared__ double ys[1024];
     for (int j = threadIdx.x; j < nvec; j += blockDim.x) ys[j] = y[j];
     __syncthreads();
@@ -450,8 +451,7 @@ __global__ void mvadd_kernel(long N, int nvec, const TZ *__restrict__ Z, long ld
 
 template <typename TZ>
 msrsb_status mvadd(long N, int nvec, const TZ *Z, long ldz, const double *y, double *x, cudaStream_t s) {
-    mvadd_kernel<TZ><<<ceil_div(N, 256), 256, 0, s>>>(N, nvec, Z, ldz, y, x);
-    MSRSB_LAUNCHED("mvadd_kernel");
+    MSRSB_PDL((mvadd_kernel<TZ>), ceil_div(N, 256), 256, 0, s, N, nvec, Z, ldz, y, x);
     return MSRSB_OK;
 }
 template msrsb_status mvadd<double>(long, int, const double *, long, const double *, double *, cudaStream_t);
@@ -460,6 +460,7 @@ template msrsb_status mvadd<float>(long, int, const float *, long, const double 
 // y = x / *den  (den on the device); y may be a narrower type
 template <typename TY>
 __global__ void scale_kernel(long N, const double *__restrict__ x, const double *__restrict__ den, TY *__restrict__ y) {
+    pdl_prologue();
     long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (i >= N) return;
     double d = *den;
@@ -468,8 +469,7 @@ __global__ void scale_kernel(long N, const double *__restrict__ x, const double 
 
 template <typename TY>
 msrsb_status scale_by_inv(long N, const double *x, const double *den, TY *y, cudaStream_t s) {
-    scale_kernel<TY><<<ceil_div(N, 256), 256, 0, s>>>(N, x, den, y);
-    MSRSB_LAUNCHED("scale_kernel");
+    MSRSB_PDL((scale_kernel<TY>), ceil_div(N, 256), 256, 0, s, N, x, den, y);
     return MSRSB_OK;
 }
 template msrsb_status scale_by_inv<double>(long, const double *, const double *, double *, cudaStream_t);
@@ -478,6 +478,7 @@ template msrsb_status scale_by_inv<float>(long, const double *, const double *, 
 // y = a*x + y with a = num/den on the device (sign applied)
 __global__ void axpy_dev_kernel(long N, const double *__restrict__ num, const double *__restrict__ den, double sign,
                                 const double *__restrict__ x, double *__restrict__ y) {
+    pdl_prologue();
     long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (i >= N) return;
     double a = sign * (*num / *den);
@@ -486,14 +487,14 @@ __global__ void axpy_dev_kernel(long N, const double *__restrict__ num, const do
 
 msrsb_status axpy_dev(long N, const double *num, const double *den, double sign, const double *x, double *y,
                       cudaStream_t s) {
-    axpy_dev_kernel<<<ceil_div(N, 256), 256, 0, s>>>(N, num, den, sign, x, y);
-    MSRSB_LAUNCHED("axpy_dev_kernel");
+    MSRSB_PDL((axpy_dev_kernel), ceil_div(N, 256), 256, 0, s, N, num, den, sign, x, y);
     return MSRSB_OK;
 }
 
 // p = z + (num/den) p
 __global__ void xpay_dev_kernel(long N, const double *__restrict__ num, const double *__restrict__ den,
                                 const double *__restrict__ z, double *__restrict__ p) {
+    pdl_prologue();
     long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (i >= N) return;
     double b = *num / *den;
@@ -501,8 +502,7 @@ __global__ void xpay_dev_kernel(long N, const double *__restrict__ num, const do
 }
 
 msrsb_status xpay_dev(long N, const double *num, const double *den, const double *z, double *p, cudaStream_t s) {
-    xpay_dev_kernel<<<ceil_div(N, 256), 256, 0, s>>>(N, num, den, z, p);
-    MSRSB_LAUNCHED("xpay_dev_kernel");
+    MSRSB_PDL((xpay_dev_kernel), ceil_div(N, 256), 256, 0, s, N, num, den, z, p);
     return MSRSB_OK;
 }
 
@@ -510,14 +510,14 @@ msrsb_status xpay_dev(long N, const double *num, const double *den, const double
 template <typename TI, typename TO>
 __global__ void permute_cast_kernel(long N, const TI *__restrict__ x, const int32_t *__restrict__ perm,
                                     TO *__restrict__ y) {
+    pdl_prologue();
     long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (i < N) y[perm[i]] = TO(x[i]);
 }
 
 template <typename TI, typename TO>
 msrsb_status permute_cast(long N, const TI *x, const int32_t *perm, TO *y, cudaStream_t s) {
-    permute_cast_kernel<TI, TO><<<ceil_div(N, 256), 256, 0, s>>>(N, x, perm, y);
-    MSRSB_LAUNCHED("permute_cast_kernel");
+    MSRSB_PDL((permute_cast_kernel<TI, TO>), ceil_div(N, 256), 256, 0, s, N, x, perm, y);
     return MSRSB_OK;
 }
 template msrsb_status permute_cast<double, float>(long, const double *, const int32_t *, float *, cudaStream_t);
@@ -526,14 +526,14 @@ template msrsb_status permute_cast<float, float>(long, const float *, const int3
 
 template <typename TI, typename TO>
 __global__ void copy_cast_kernel(long N, const TI *__restrict__ x, TO *__restrict__ y) {
+    pdl_prologue();
     long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (i < N) y[i] = TO(x[i]);
 }
 
 template <typename TI, typename TO>
 msrsb_status copy_cast(long N, const TI *x, TO *y, cudaStream_t s) {
-    copy_cast_kernel<TI, TO><<<ceil_div(N, 256), 256, 0, s>>>(N, x, y);
-    MSRSB_LAUNCHED("copy_cast_kernel");
+    MSRSB_PDL((copy_cast_kernel<TI, TO>), ceil_div(N, 256), 256, 0, s, N, x, y);
     return MSRSB_OK;
 }
 template msrsb_status copy_cast<double, float>(long, const double *, float *, cudaStream_t);
@@ -598,6 +598,7 @@ __device__ __forceinline__ DF df_shfl_down(DF v, int o) {
 // V_0 planes = r / beta
 __global__ void df_scale_kernel(long N, const double *__restrict__ r, const double *__restrict__ beta,
                                 float *__restrict__ vh, float *__restrict__ vl) {
+    pdl_prologue();
     long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (i >= N) return;
     const double b = *beta;
@@ -607,8 +608,7 @@ __global__ void df_scale_kernel(long N, const double *__restrict__ r, const doub
 }
 
 msrsb_status df_scale(long N, const double *r, const double *beta, float *vh, float *vl, cudaStream_t s) {
-    df_scale_kernel<<<ceil_div(N, 256), 256, 0, s>>>(N, r, beta, vh, vl);
-    MSRSB_LAUNCHED("df_scale_kernel");
+    MSRSB_PDL((df_scale_kernel), ceil_div(N, 256), 256, 0, s, N, r, beta, vh, vl);
     return MSRSB_OK;
 }
 
@@ -618,6 +618,7 @@ __global__ void __launch_bounds__(256) sell_spmv_df_kernel(int n, const int32_t 
                                                            const double *__restrict__ sval,
                                                            const double *__restrict__ x, float *__restrict__ yh,
                                                            float *__restrict__ yl) {
+    pdl_prologue();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int s = i >> 5, lane = i & 31;
@@ -637,13 +638,13 @@ __global__ void __launch_bounds__(256) sell_spmv_df_kernel(int n, const int32_t 
 }
 
 msrsb_status sell_spmv_df(const Sell &S, const double *val, const double *x, float *yh, float *yl, cudaStream_t s) {
-    sell_spmv_df_kernel<<<ceil_div(S.n, 256), 256, 0, s>>>(S.n, S.slice_ptr, S.col, val, x, yh, yl);
-    MSRSB_LAUNCHED("sell_spmv_df_kernel");
+    MSRSB_PDL((sell_spmv_df_kernel), ceil_div(S.n, 256), 256, 0, s, S.n, S.slice_ptr, S.col, val, x, yh, yl);
     return MSRSB_OK;
 }
 
 // FP64 vector to double-float planes
 __global__ void df_split_kernel(long N, const double *__restrict__ w, float *__restrict__ wh, float *__restrict__ wl) {
+    pdl_prologue();
     long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (i >= N) return;
     const DF d = df_from(w[i]);
@@ -652,8 +653,7 @@ __global__ void df_split_kernel(long N, const double *__restrict__ w, float *__r
 }
 
 msrsb_status df_split(long N, const double *w, float *wh, float *wl, cudaStream_t s) {
-    df_split_kernel<<<ceil_div(N, 256), 256, 0, s>>>(N, w, wh, wl);
-    MSRSB_LAUNCHED("df_split_kernel");
+    MSRSB_PDL((df_split_kernel), ceil_div(N, 256), 256, 0, s, N, w, wh, wl);
     return MSRSB_OK;
 }
 
@@ -664,6 +664,7 @@ __global__ void __launch_bounds__(256) mdot_df_kernel(long N, int nv, const floa
                                                       const float *__restrict__ Vl, long ldv,
                                                       const float *__restrict__ Wh, const float *__restrict__ Wl,
                                                       double *__restrict__ partial, const int *__restrict__ gate) {
+    pdl_prologue();
     if (gate && !*gate) return;
     __shared__ double red[8];
     const int q = blockIdx.y;
@@ -696,10 +697,8 @@ __global__ void reduce_partials_kernel(int nblk, const double *__restrict__ part
 msrsb_status mdot_df(long N, int nv, const float *Vh, const float *Vl, long ldv, const float *Wh, const float *Wl,
                      double *partial, double *hs, cudaStream_t s, const int *gate) {
     dim3 grid(kRedBlocks, nv + 1);
-    mdot_df_kernel<<<grid, 256, 0, s>>>(N, nv, Vh, Vl, ldv, Wh, Wl, partial, gate);
-    MSRSB_LAUNCHED("mdot_df_kernel");
-    reduce_partials_kernel<<<nv + 1, 256, 0, s>>>(kRedBlocks, partial, hs, 0, 0, gate);
-    MSRSB_LAUNCHED("reduce_partials_kernel");
+    MSRSB_PDL((mdot_df_kernel), grid, 256, 0, s, N, nv, Vh, Vl, ldv, Wh, Wl, partial, gate);
+    MSRSB_PDL((reduce_partials_kernel), nv + 1, 256, 0, s, kRedBlocks, partial, hs, 0, 0, gate);
     return MSRSB_OK;
 }
 
@@ -713,6 +712,7 @@ __global__ void __launch_bounds__(256) gs_update_df_kernel(long N, int nv, const
                                                            float *__restrict__ Wl, float *__restrict__ oh,
                                                            float *__restrict__ ol, double *__restrict__ hcol,
                                                            int *__restrict__ flag, int pass) {
+    pdl_prologue();
     if (pass == 2 && !*flag) return;
     __shared__ float hh[1024], hl[1024];
     __shared__ DF s_scale;
@@ -757,8 +757,7 @@ __global__ void __launch_bounds__(256) gs_update_df_kernel(long N, int nv, const
 msrsb_status gs_update_df(long N, int nv, const float *Vh, const float *Vl, long ldv, const double *hs, float *Wh,
                           float *Wl, float *oh, float *ol, double *hcol, int *flag, int pass, cudaStream_t s) {
     const int grid = ceil_div(N, 256) < 2048 ? (int)ceil_div(N, 256) : 2048;
-    gs_update_df_kernel<<<grid, 256, 0, s>>>(N, nv, Vh, Vl, ldv, hs, Wh, Wl, oh, ol, hcol, flag, pass);
-    MSRSB_LAUNCHED("gs_update_df_kernel");
+    MSRSB_PDL((gs_update_df_kernel), grid, 256, 0, s, N, nv, Vh, Vl, ldv, hs, Wh, Wl, oh, ol, hcol, flag, pass);
     return MSRSB_OK;
 }
 

@@ -430,6 +430,7 @@ msrsb_status coarse_inverse(int n, const double *Ac, double *Ainv, cudaStream_t 
 
 // y = M x, M dense n x n row-major FP64; one warp per row.
 __global__ void gemv_kernel(int n, const double *__restrict__ M, const double *__restrict__ x, double *__restrict__ y) {
+    pdl_prologue();
     int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     int lane = threadIdx.x & 31;
     if (row >= n) return;
@@ -441,8 +442,7 @@ __global__ void gemv_kernel(int n, const double *__restrict__ M, const double *_
 }
 
 msrsb_status gemv(int n, const double *M, const double *x, double *y, cudaStream_t s) {
-    gemv_kernel<<<ceil_div(n, 8), 256, 0, s>>>(n, M, x, y);
-    MSRSB_LAUNCHED("gemv_kernel");
+    MSRSB_PDL((gemv_kernel), ceil_div(n, 8), 256, 0, s, n, M, x, y);
     return MSRSB_OK;
 }
 

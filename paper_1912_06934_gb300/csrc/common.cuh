@@ -31,6 +31,46 @@ void count_launch();
         MSRSB_CUDA(cudaGetLastError());      \
     } while (0)
 
+// Programmatic dependent launch (PDL). A kernel launched by MSRSB_PDL may be
+// scheduled while its predecessor in the stream is still running, so it must
+// begin with pdl_prologue(): griddepcontrol.wait blocks until the preceding
+// grid has completed and its writes are visible (before any global memory
+// access of this kernel), then launch_dependents lets the next grid be
+// scheduled during this one's tail. Launched without the attribute, both
+// instructions are no-ops.
+__device__ __forceinline__ void pdl_prologue() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+    if (e == cudaErrorNotSupported || e == cudaErrorInvalidValue) {  // attribute refused: plain stream order
+        cudaGetLastError();
+        cfg.numAttrs = 0;
+        e = cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+    }
+    return e;
+}
+
+#define MSRSB_PDL(kernel, grid, block, smem, stream, ...)                                   \
+    do {                                                                                 \
+        ::msrsb::count_launch();                                                         \
+        MSRSB_CUDA(::msrsb::pdl_launch(kernel, grid, block, smem, stream, __VA_ARGS__)); \
+    } while (0)
+
 #define MSRSB_TRY(expr)                       \
     do {                                      \
         msrsb_status s_ = (expr);             \

@@ -284,6 +284,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) ilu_lower_kernel(int c0, int m, int w, const int32_t *__restrict__ lcol,
                                                         const T *__restrict__ lval, const T *__restrict__ r,
                                                         T *__restrict__ y) {
+    pdl_prologue();
     const int q = (blockIdx.x * blockDim.x + threadIdx.x) / kSweepLanes;
     const int g = threadIdx.x % kSweepLanes;
     if (q >= m) return;  // whole groups leave together
@@ -301,6 +302,7 @@ __global__ void __launch_bounds__(256) ilu_upper_kernel(int c0, int m, int w, co
                                                         const T *__restrict__ uval, const T *__restrict__ udinv,
                                                         const int32_t *__restrict__ rows, T *__restrict__ y,
                                                         TZ *__restrict__ z) {
+    pdl_prologue();
     const int q = (blockIdx.x * blockDim.x + threadIdx.x) / kSweepLanes;
     const int g = threadIdx.x % kSweepLanes;
     if (q >= m) return;
@@ -371,17 +373,14 @@ msrsb_status ilu0_apply(const msrsb_handle *h, const T *rp, T *y, TZ *z, cudaStr
     for (int c = 0; c < E.ncol; ++c) {
         int m = E.cptr[c + 1] - E.cptr[c];
         if (!m) continue;
-        ilu_lower_kernel<T><<<ceil_div((long)m * kSweepLanes, 256), 256, 0, s>>>(E.cptr[c], m, E.wl[c], E.lcol + E.lbase[c],
-                                                             (const T *)E.lval + E.lbase[c], rp, y);
-        MSRSB_LAUNCHED("ilu_lower_kernel");
+        MSRSB_PDL((ilu_lower_kernel<T>), ceil_div((long)m * kSweepLanes, 256), 256, 0, s, E.cptr[c], m, E.wl[c],
+                  E.lcol + E.lbase[c], (const T *)E.lval + E.lbase[c], rp, y);
     }
     for (int c = E.ncol - 1; c >= 0; --c) {
         int m = E.cptr[c + 1] - E.cptr[c];
         if (!m) continue;
-        ilu_upper_kernel<T, TZ><<<ceil_div((long)m * kSweepLanes, 256), 256, 0, s>>>(
-            E.cptr[c], m, E.wu[c], E.ucol + E.ubase[c], (const T *)E.uval + E.ubase[c], (const T *)E.udinv,
-            h->colour_rows, y, z);
-        MSRSB_LAUNCHED("ilu_upper_kernel");
+        MSRSB_PDL((ilu_upper_kernel<T, TZ>), ceil_div((long)m * kSweepLanes, 256), 256, 0, s, E.cptr[c], m, E.wu[c],
+                  E.ucol + E.ubase[c], (const T *)E.uval + E.ubase[c], (const T *)E.udinv, h->colour_rows, y, z);
     }
     return MSRSB_OK;
 }
@@ -450,6 +449,7 @@ __global__ void gs_colour_kernel(int cnt, const int32_t *__restrict__ rows, int 
                                  const uint8_t *__restrict__ colour, const TA *__restrict__ val,
                                  const T *__restrict__ dinv, const T *__restrict__ r, T *__restrict__ e,
                                  TZ *__restrict__ z, int assign) {
+    pdl_prologue();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= cnt) return;
     int i = rows[t];
@@ -490,10 +490,9 @@ msrsb_status gs_apply(const msrsb_handle *h, const TA *val, const T *dinv, int f
         int c = forward ? q : h->ncolours - 1 - q;
         int cnt = h->colour_ptr_h[c + 1] - h->colour_ptr_h[c];
         if (!cnt) continue;
-        gs_colour_kernel<T, TA, TZ><<<ceil_div(cnt, 128), 128, 0, s>>>(cnt, h->colour_rows + h->colour_ptr_h[c], c,
-                                                                       forward, A.rowptr, A.colidx, h->colour, val,
-                                                                       dinv, r, e, z, assign);
-        MSRSB_LAUNCHED("gs_colour_kernel");
+        MSRSB_PDL((gs_colour_kernel<T, TA, TZ>), ceil_div(cnt, 128), 128, 0, s, cnt,
+                  h->colour_rows + h->colour_ptr_h[c], c, forward, A.rowptr, A.colidx, h->colour, val, dinv, r, e, z,
+                  assign);
     }
     return MSRSB_OK;
 }
