@@ -112,6 +112,29 @@ def smooth_bytes(n, nnz, W, esize):
     return nnz * (esize + 4) + n * (2 * W * esize + esize + 1)
 
 
+# DRAM bytes (read + write) of one smooth_kernel<float,8> launch on this
+# workload, from one ncu capture of the current kernel (cold L2, so an upper
+# bound for the warm passes of the loop): profiles/smooth_kernel_f32_w8_darcy64.md
+SMOOTH_TRAFFIC_BYTES = 65194496 + 1844224
+
+
+def apply_bytes(n, nnz, nnz_p, nc, W):
+    """Algorithmic bytes of one mixed-form two-stage apply (Alg. 3 with no
+    pre-smoother, one ILU(0) post-sweep), each array counted once:
+    restriction P^T v (P^T pattern row index, P value, v: 4 + 4 + 4 per entry
+    of P), coarse solve (dense FP64 inverse n_c^2 * 8), prolongation P w_c
+    (ids + values n*W*(4 + 4), z written n*8), residual v - A z in FP32
+    (column + value per nonzero, z read 8, v 4, r written 4 per row), and the
+    two triangular sweeps of ILU(0) (column + value per factor nonzero; the
+    factors fill A's pattern; r, y, reciprocal diagonal and z per row 24)."""
+    restrict = nnz_p * 12
+    coarse = nc * nc * 8
+    prolong = n * W * 8 + n * 8
+    resid = nnz * 8 + n * 16
+    ilu = nnz * 8 + n * 24
+    return restrict + coarse + prolong + resid + ilu
+
+
 def gpu_arm(args, rank, world):
     import torch
     import __graft_entry__
@@ -176,6 +199,27 @@ def gpu_arm(args, rank, world):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         t32, t64 = float(t[0]), float(t[1])
 
+    # two-stage apply on its own: L2 flushed before every apply, event-timed
+    h = M.msrsb_setup(A, g, M.opts(prec=M.msrsb.MSRSB_F32, **BASIS))
+    p_ids = h.get_setup()[0]
+    nnz_p = int((p_ids >= 0).sum())
+    v = torch.randn(n, dtype=torch.float64, device=dev, generator=torch.Generator(device=dev).manual_seed(7))
+    z = torch.empty_like(v)
+    for _ in range(3):
+        h.apply(v, z)
+    ap_ms = []
+    for _ in range(20):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h.apply(v, z)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ap_ms.append(e0.elapsed_time(e1))
+    h.destroy()
+    ap_bytes = apply_bytes(n, nnz, nnz_p, inf32["nc"], 8)
+    ap_med = statistics.median(ap_ms)
+
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     ip = torch.as_tensor(np.asarray(c["indptr"], dtype=np.int32)).pin_memory()
     ix = torch.as_tensor(np.asarray(c["indices"], dtype=np.int32)).pin_memory()
@@ -228,10 +272,14 @@ def gpu_arm(args, rank, world):
         "speedup_mixed_vs_fp64": t64 / t32,
         "roofline": {"kernel": "smooth_kernel<float,8> (restricted smoothing, Alg. 1)", "bound": "hbm",
                      "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm if achieved else None, "traffic": None,
+                     "frac": achieved / hbm if achieved else None, "traffic": SMOOTH_TRAFFIC_BYTES,
                      "bytes_per_launch": per_launch32, "launches": sm_l32,
                      "us_per_launch": sm_ms32 / sm_l32 * 1e3 if sm_l32 else None,
                      "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs, burst copy)"},
+        "apply_roofline": {"op": "two-stage apply (Alg. 3), mixed form, L2 flushed before each", "bound": "hbm",
+                           "achieved": ap_bytes / (ap_med * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                           "frac": ap_bytes / (ap_med * 1e-3) / 1e9 / hbm, "bytes_per_apply": ap_bytes,
+                           "us_per_apply": ap_med * 1e3, "applies": len(ap_ms)},
         "e2e": {"value": statistics.median(e2e_t) if e2e_t else None, "unit": "s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "relres": float(resid), "call": "msrsb_solve_host (pinned host buffers)"},
         "gpu_launches": int(launches + launches64),
