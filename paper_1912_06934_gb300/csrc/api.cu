@@ -98,7 +98,7 @@ template <typename T>
 msrsb_status ilu_build_ell(msrsb_handle *h, const T *lu, cudaStream_t s);
 
 template <typename T, typename TZ>
-msrsb_status ilu0_apply(const msrsb_handle *h, const T *rp, T *y, TZ *z, cudaStream_t s);
+msrsb_status ilu0_apply(const msrsb_handle *h, T *ry, TZ *z, cudaStream_t s);
 template <typename TI, typename TO>
 msrsb_status permute_cast(long N, const TI *x, const int32_t *perm, TO *y, cudaStream_t s);
 template <typename T>
@@ -127,7 +127,7 @@ template <typename TZ>
 msrsb_status mvadd(long N, int nvec, const TZ *Z, long ldz, const double *y, double *x, cudaStream_t s);
 msrsb_status df_scale(long N, const double *r, const double *beta, float *vh, float *vl, cudaStream_t s);
 msrsb_status mdot_df(long N, int nv, const float *Vh, const float *Vl, long ldv, const float *Wh, const float *Wl,
-                     double *partial, double *hs, cudaStream_t s, const int *gate = nullptr);
+                     double *partial, double *hs, unsigned *counter, cudaStream_t s, const int *gate = nullptr);
 msrsb_status gs_update_df(long N, int nv, const float *Vh, const float *Vl, long ldv, const double *hs, float *Wh,
                           float *Wl, float *oh, float *ol, double *hcol, int *flag, int pass, cudaStream_t s);
 msrsb_status sell_spmv_df(const Sell &S, const double *val, const double *x, float *yh, float *yl, cudaStream_t s);
@@ -336,7 +336,7 @@ static msrsb_status apply_t(msrsb_handle *h, const TVI *v, TZ *z, cudaStream_t s
         } else {
             MSRSB_TRY((permute_cast<TVI, T>(N, v, h->pos_of, r, s)));
             MSRSB_CUDA(cudaMemsetAsync(z, 0, N * sizeof(TZ), s));
-            MSRSB_TRY((ilu0_apply<T, TZ>(h, r, y, z, s)));
+            MSRSB_TRY((ilu0_apply<T, TZ>(h, r, z, s)));
         }
         // coarse correction of the residual v - A z
         MSRSB_TRY((resid_t<T, TZ, TVI>(h, aval_t, z, v, r, nullptr, s)));
@@ -353,7 +353,7 @@ static msrsb_status apply_t(msrsb_handle *h, const TVI *v, TZ *z, cudaStream_t s
         } else {
             // residual written straight into colour order for the sweeps
             MSRSB_TRY((resid_t<T, TZ, TVI>(h, aval_t, z, v, r, h->pos_of, s)));
-            MSRSB_TRY((ilu0_apply<T, TZ>(h, r, y, z, s)));
+            MSRSB_TRY((ilu0_apply<T, TZ>(h, r, z, s)));
         }
     }
     return MSRSB_OK;
@@ -399,7 +399,7 @@ msrsb_status vadd(int n, const double *a, double *b, cudaStream_t s) {
 // H[(m+1) x m] column-major | cs[m] | sn[m] | g[m+1] | est | beta | h2[m+2] | est_hist[m+1] | flag
 struct KhLayout {
     long H, cs, sn, g, est, beta, h2, hist, flag, total;
-    explicit KhLayout(int m) {
+    __host__ __device__ explicit KhLayout(int m) {
         H = 0;
         cs = (long)(m + 1) * m;
         sn = cs + m;
@@ -452,14 +452,16 @@ __global__ void givens_kernel(int m, int j, double *__restrict__ kh) {
     }
     __syncwarp();
     if (threadIdx.x == 0) {
+        double carry = col[0];  // rotated entry i, kept in a register along the chain
         for (int i = 0; i < j; ++i) {
-            double t = c_s[i] * col[i] + s_s[i] * col[i + 1];
-            col[i + 1] = -s_s[i] * col[i] + c_s[i] * col[i + 1];
-            col[i] = t;
+            const double ci = c_s[i], si = s_s[i], nx = col[i + 1];
+            col[i] = ci * carry + si * nx;
+            carry = ci * nx - si * carry;
         }
-        double a = col[j], b = col[j + 1];
+        double a = carry, b = col[j + 1];
         double den = hypot(a, b);
-        double c = den != 0.0 ? a / den : 1.0, sgn = den != 0.0 ? b / den : 0.0;
+        const double rden = den != 0.0 ? 1.0 / den : 0.0;
+        double c = den != 0.0 ? a * rden : 1.0, sgn = b * rden;
         cs[j] = c;
         sn[j] = sgn;
         col[j] = den;
@@ -487,9 +489,11 @@ __global__ void hess_solve_kernel(int m, int k, double *__restrict__ kh) {
 
 __global__ void gmres_init_kernel(int m, double *__restrict__ kh, const double *__restrict__ beta) {
     pdl_prologue();
-    double *g = kh + (long)(m + 1) * m + 2 * m;
+    const KhLayout L(m);
+    double *g = kh + L.g;
     for (int i = 0; i <= m; ++i) g[i] = 0.0;
     g[0] = *beta;
+    *(unsigned *)(kh + L.flag + 1) = 0u;  // multi-dot counter
 }
 
 // Restarted flexible GMRES with right preconditioning (Z_j = M^-1 V_j kept,
@@ -510,6 +514,7 @@ static msrsb_status gmres_t(msrsb_handle *h, const double *b, double *x, double 
     const KhLayout L(m);
     double *H = kh + L.H, *est = kh + L.est, *beta = kh + L.beta, *h2 = kh + L.h2;
     int *reorth = (int *)(kh + L.flag);
+    unsigned *counter = (unsigned *)(kh + L.flag + 1);  // last-CTA counter of the multi-dot (kept at 0)
     double *V = h->kv, *Z = h->kz;                    // FP64 basis (DFV = false)
     // double-float basis and work vector of the mixed form: [Vh | Vl | Wh | Wl]
     float *Vh = (float *)h->kv32, *Vl = Vh + (m + 1) * N, *Wh = Vl + (m + 1) * N, *Wl = Wh + N;
@@ -551,8 +556,13 @@ static msrsb_status gmres_t(msrsb_handle *h, const double *b, double *x, double 
         // solve below ignores.
         double *pin = pinned_scratch();
         double *pin_est = pin ? pin + 16 : nullptr;
-        cudaEvent_t *evs = event_pool(mm);
+        cudaEvent_t *evs = event_pool(mm + 2);
         const bool lagged = pin_est && evs && mm <= kPinnedDoubles - 16;
+        // With lagged checks the Givens update of step j runs on the side
+        // stream: nothing on the main stream reads it before the Hessenberg
+        // solve, so it overlaps the next step's preconditioner.
+        cudaStream_t gv = lagged && h->side ? h->side : s;
+        cudaEvent_t fork_ev = evs ? evs[mm] : nullptr, join_ev = evs ? evs[mm + 1] : nullptr;
         int conv = -1, checked = 0, launched = 0;
         for (int j = 0; j < mm; ++j) {
             if (lagged) {
@@ -583,9 +593,9 @@ static msrsb_status gmres_t(msrsb_handle *h, const double *b, double *x, double 
                 }
                 // classical Gram-Schmidt with the DGKS test (see below), double-float vectors
                 float *oh = Vh + (j + 1) * N, *ol = Vl + (j + 1) * N;
-                MSRSB_TRY(mdot_df(N, j + 1, Vh, Vl, N, Wh, Wl, h->partial, h2, s));
+                MSRSB_TRY(mdot_df(N, j + 1, Vh, Vl, N, Wh, Wl, h->partial, h2, counter, s));
                 MSRSB_TRY(gs_update_df(N, j + 1, Vh, Vl, N, h2, Wh, Wl, oh, ol, hcol, reorth, 1, s));
-                MSRSB_TRY(mdot_df(N, j + 1, Vh, Vl, N, Wh, Wl, h->partial, h2, s, reorth));
+                MSRSB_TRY(mdot_df(N, j + 1, Vh, Vl, N, Wh, Wl, h->partial, h2, counter, s, reorth));
                 MSRSB_TRY(gs_update_df(N, j + 1, Vh, Vl, N, h2, Wh, Wl, oh, ol, hcol, reorth, 2, s));
             } else {
                 double *Vj = V + j * N, *w = V + (j + 1) * N;
@@ -600,11 +610,15 @@ static msrsb_status gmres_t(msrsb_handle *h, const double *b, double *x, double 
                 MSRSB_TRY(mdot<double>(N, j + 2, V, N, w, h->partial, h2, 0, s, reorth));
                 MSRSB_TRY(gs_update<double>(N, j + 1, V, N, h2, w, hcol, reorth, 2, s));
             }
-            MSRSB_PDL((givens_kernel), 1, 32, 0, s, m, j, kh);
+            if (gv != s) {
+                MSRSB_CUDA(cudaEventRecord(fork_ev, s));
+                MSRSB_CUDA(cudaStreamWaitEvent(gv, fork_ev, 0));
+            }
+            MSRSB_PDL((givens_kernel), 1, 32, 0, gv, m, j, kh);
             launched = j + 1;
             if (lagged) {
-                MSRSB_CUDA(cudaMemcpyAsync(pin_est + j, kh + L.hist + j, sizeof(double), cudaMemcpyDeviceToHost, s));
-                MSRSB_CUDA(cudaEventRecord(evs[j], s));
+                MSRSB_CUDA(cudaMemcpyAsync(pin_est + j, kh + L.hist + j, sizeof(double), cudaMemcpyDeviceToHost, gv));
+                MSRSB_CUDA(cudaEventRecord(evs[j], gv));
             } else {
                 double e = 0.0;
                 MSRSB_TRY(read_scalar(est, &e, s));
@@ -615,6 +629,10 @@ static msrsb_status gmres_t(msrsb_handle *h, const double *b, double *x, double 
                     break;
                 }
             }
+        }
+        if (gv != s) {  // join the Givens stream before the solve reads the rotations
+            MSRSB_CUDA(cudaEventRecord(join_ev, gv));
+            MSRSB_CUDA(cudaStreamWaitEvent(s, join_ev, 0));
         }
         if (lagged) {
             MSRSB_CUDA(cudaStreamSynchronize(s));

@@ -659,14 +659,18 @@ msrsb_status df_split(long N, const double *w, float *wh, float *wl, cudaStream_
 
 // partial[q * gridDim.x + b] = sum over row chunk b of V_q . w (q < nv), and
 // for q = nv the squared norm of w; all vectors double-float, FP32 arithmetic
-// up to the per-warp results
+// up to the per-warp results. The last CTA to finish (counter) sums the
+// partials of every q in a fixed order into hs[q] and resets the counter, so
+// no separate reduction launch is needed.
 __global__ void __launch_bounds__(256) mdot_df_kernel(long N, int nv, const float *__restrict__ Vh,
                                                       const float *__restrict__ Vl, long ldv,
                                                       const float *__restrict__ Wh, const float *__restrict__ Wl,
-                                                      double *__restrict__ partial, const int *__restrict__ gate) {
+                                                      double *__restrict__ partial, double *__restrict__ hs,
+                                                      unsigned *__restrict__ counter, const int *__restrict__ gate) {
     pdl_prologue();
     if (gate && !*gate) return;
     __shared__ double red[8];
+    __shared__ bool last;
     const int q = blockIdx.y;
     const long chunk = (N + gridDim.x - 1) / gridDim.x;
     const long b0 = blockIdx.x * chunk, b1 = b0 + chunk < N ? b0 + chunk : N;
@@ -686,19 +690,34 @@ __global__ void __launch_bounds__(256) mdot_df_kernel(long N, int nv, const floa
     if (threadIdx.x < 32) {
         double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
         v = warp_sum(v);
-        if (threadIdx.x == 0) partial[(long)q * gridDim.x + blockIdx.x] = v;
+        if (threadIdx.x == 0) {
+            partial[(long)q * gridDim.x + blockIdx.x] = v;
+            __threadfence();
+            const unsigned total = gridDim.x * gridDim.y;
+            last = atomicAdd(counter, 1u) == total - 1;
+        }
     }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // final sums: one warp per q, lanes over the row chunks, fixed tree
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nblk = gridDim.x;
+    for (int qq = warp; qq < (int)gridDim.y; qq += blockDim.x >> 5) {
+        const volatile double *pp = partial + (long)qq * nblk;
+        double v = 0.0;
+        for (int b = lane; b < nblk; b += 32) v += pp[b];
+        v = warp_sum(v);
+        if (lane == 0) hs[qq] = v;
+    }
+    if (threadIdx.x == 0) *counter = 0u;
 }
 
-__global__ void reduce_partials_kernel(int nblk, const double *__restrict__ partial, double *__restrict__ out,
-                                       int accumulate, int sqrt_out, const int *__restrict__ gate);
-
-// hs[q] = V_q . w (q < nv), hs[nv] = w . w
+// hs[q] = V_q . w (q < nv), hs[nv] = w . w; counter: a zeroed device word
 msrsb_status mdot_df(long N, int nv, const float *Vh, const float *Vl, long ldv, const float *Wh, const float *Wl,
-                     double *partial, double *hs, cudaStream_t s, const int *gate) {
+                     double *partial, double *hs, unsigned *counter, cudaStream_t s, const int *gate) {
     dim3 grid(kRedBlocks, nv + 1);
-    MSRSB_PDL((mdot_df_kernel), grid, 256, 0, s, N, nv, Vh, Vl, ldv, Wh, Wl, partial, gate);
-    MSRSB_PDL((reduce_partials_kernel), nv + 1, 256, 0, s, kRedBlocks, partial, hs, 0, 0, gate);
+    MSRSB_PDL((mdot_df_kernel), grid, 256, 0, s, N, nv, Vh, Vl, ldv, Wh, Wl, partial, hs, counter, gate);
     return MSRSB_OK;
 }
 

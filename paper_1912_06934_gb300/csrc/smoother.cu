@@ -279,11 +279,11 @@ __device__ __forceinline__ unsigned group_mask() {
     return 0xfu << (threadIdx.x & 31 & ~(kSweepLanes - 1));
 }
 
-// forward, colour c: y_p = r_p - sum_j L_pj y_col
+// forward, colour c, in place on y (which holds r in colour order on entry):
+// y_p = r_p - sum_j L_pj y_col. Colour 0 has no L entries, so it needs no launch.
 template <typename T>
 __global__ void __launch_bounds__(256) ilu_lower_kernel(int c0, int m, int w, const int32_t *__restrict__ lcol,
-                                                        const T *__restrict__ lval, const T *__restrict__ r,
-                                                        T *__restrict__ y) {
+                                                        const T *__restrict__ lval, T *__restrict__ y) {
     pdl_prologue();
     const int q = (blockIdx.x * blockDim.x + threadIdx.x) / kSweepLanes;
     const int g = threadIdx.x % kSweepLanes;
@@ -292,7 +292,30 @@ __global__ void __launch_bounds__(256) ilu_lower_kernel(int c0, int m, int w, co
     for (int j = g; j < w; j += kSweepLanes) acc = fma(lval[(long)j * m + q], y[lcol[(long)j * m + q]], acc);
 #pragma unroll
     for (int o = kSweepLanes / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(group_mask(), acc, o, kSweepLanes);
-    if (g == 0) y[c0 + q] = r[c0 + q] - acc;
+    if (g == 0) y[c0 + q] -= acc;
+}
+
+// the last colour has no U entries: its forward and backward stages in one
+// launch, e_p = (r_p - sum_j L_pj y_col) / u_pp, then z[row(p)] += e_p
+template <typename T, typename TZ>
+__global__ void __launch_bounds__(256) ilu_last_kernel(int c0, int m, int w, const int32_t *__restrict__ lcol,
+                                                       const T *__restrict__ lval, const T *__restrict__ udinv,
+                                                       const int32_t *__restrict__ rows, T *__restrict__ y,
+                                                       TZ *__restrict__ z) {
+    pdl_prologue();
+    const int q = (blockIdx.x * blockDim.x + threadIdx.x) / kSweepLanes;
+    const int g = threadIdx.x % kSweepLanes;
+    if (q >= m) return;
+    T acc = T(0);
+    for (int j = g; j < w; j += kSweepLanes) acc = fma(lval[(long)j * m + q], y[lcol[(long)j * m + q]], acc);
+#pragma unroll
+    for (int o = kSweepLanes / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(group_mask(), acc, o, kSweepLanes);
+    if (g == 0) {
+        const T e = (y[c0 + q] - acc) * udinv[c0 + q];
+        y[c0 + q] = e;
+        const int row = rows[c0 + q];
+        z[row] = TZ(z[row] + TZ(e));
+    }
 }
 
 // backward, colour c, in place on y: e_p = (y_p - sum_j U_pj e_col) / u_pp;
@@ -366,28 +389,33 @@ msrsb_status ilu_build_ell(msrsb_handle *h, const T *lu, cudaStream_t s) {
 template msrsb_status ilu_build_ell<double>(msrsb_handle *, const double *, cudaStream_t);
 template msrsb_status ilu_build_ell<float>(msrsb_handle *, const float *, cudaStream_t);
 
-// z += U^-1 L^-1 r, r given in colour order (rp), y a colour-order work vector
+// z += U^-1 L^-1 r, r given in colour order in ry, which the sweeps overwrite
+// (forward and backward in place): 2*ncol - 2 launches
 template <typename T, typename TZ>
-msrsb_status ilu0_apply(const msrsb_handle *h, const T *rp, T *y, TZ *z, cudaStream_t s) {
+msrsb_status ilu0_apply(const msrsb_handle *h, T *ry, TZ *z, cudaStream_t s) {
     const IluEll &E = h->ilu;
-    for (int c = 0; c < E.ncol; ++c) {
+    const int last = E.ncol - 1;
+    for (int c = 1; c < last; ++c) {
         int m = E.cptr[c + 1] - E.cptr[c];
         if (!m) continue;
         MSRSB_PDL((ilu_lower_kernel<T>), ceil_div((long)m * kSweepLanes, 256), 256, 0, s, E.cptr[c], m, E.wl[c],
-                  E.lcol + E.lbase[c], (const T *)E.lval + E.lbase[c], rp, y);
+                  E.lcol + E.lbase[c], (const T *)E.lval + E.lbase[c], ry);
     }
-    for (int c = E.ncol - 1; c >= 0; --c) {
+    if (int m = E.cptr[last + 1] - E.cptr[last])
+        MSRSB_PDL((ilu_last_kernel<T, TZ>), ceil_div((long)m * kSweepLanes, 256), 256, 0, s, E.cptr[last], m,
+                  E.wl[last], E.lcol + E.lbase[last], (const T *)E.lval + E.lbase[last], (const T *)E.udinv,
+                  h->colour_rows, ry, z);
+    for (int c = last - 1; c >= 0; --c) {
         int m = E.cptr[c + 1] - E.cptr[c];
         if (!m) continue;
         MSRSB_PDL((ilu_upper_kernel<T, TZ>), ceil_div((long)m * kSweepLanes, 256), 256, 0, s, E.cptr[c], m, E.wu[c],
-                  E.ucol + E.ubase[c], (const T *)E.uval + E.ubase[c], (const T *)E.udinv, h->colour_rows, y, z);
+                  E.ucol + E.ubase[c], (const T *)E.uval + E.ubase[c], (const T *)E.udinv, h->colour_rows, ry, z);
     }
     return MSRSB_OK;
 }
-template msrsb_status ilu0_apply<double, double>(const msrsb_handle *, const double *, double *, double *,
-                                                 cudaStream_t);
-template msrsb_status ilu0_apply<float, double>(const msrsb_handle *, const float *, float *, double *, cudaStream_t);
-template msrsb_status ilu0_apply<float, float>(const msrsb_handle *, const float *, float *, float *, cudaStream_t);
+template msrsb_status ilu0_apply<double, double>(const msrsb_handle *, double *, double *, cudaStream_t);
+template msrsb_status ilu0_apply<float, double>(const msrsb_handle *, float *, double *, cudaStream_t);
+template msrsb_status ilu0_apply<float, float>(const msrsb_handle *, float *, float *, cudaStream_t);
 
 // ---- block (3x3) Gauss-Seidel -------------------------------------------------
 
