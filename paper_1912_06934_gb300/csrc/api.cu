@@ -81,7 +81,9 @@ msrsb_status basis_loop(int n, int W, const Sell &S, int comp, const T *scale, c
                         const uint8_t *skel, T *P, const msrsb_basis_opts *o, int *iters_out, double *e_out,
                         cudaStream_t s);
 msrsb_status build_transpose(int n, int W, int nc, const int32_t *p_ids, int32_t **pt_ptr, int32_t **pt_rows,
-                             int8_t **jslot, cudaStream_t s);
+                             int8_t **jslot, int *nnzp_out, cudaStream_t s);
+template <typename TP>
+msrsb_status pt_gather(const msrsb_handle *h, const TP *P, TP *PT, cudaStream_t s);
 template <typename T>
 msrsb_status galerkin(const msrsb_mat *A, const msrsb_grid *g, int W, int nc, const int32_t *p_ids, const T *P,
                       const int32_t *pt_ptr, const int32_t *pt_rows, const int8_t *jslot, double *Ac,
@@ -127,7 +129,7 @@ template <typename TZ>
 msrsb_status mvadd(long N, int nvec, const TZ *Z, long ldz, const double *y, double *x, cudaStream_t s);
 msrsb_status df_scale(long N, const double *r, const double *beta, float *vh, float *vl, cudaStream_t s);
 msrsb_status mdot_df(long N, int nv, const float *Vh, const float *Vl, long ldv, const float *Wh, const float *Wl,
-                     double *partial, double *hs, unsigned *counter, cudaStream_t s, const int *gate = nullptr);
+                     double *partial, double *hs, cudaStream_t s, const int *gate = nullptr);
 msrsb_status gs_update_df(long N, int nv, const float *Vh, const float *Vl, long ldv, const double *hs, float *Wh,
                           float *Wl, float *oh, float *ol, double *hcol, int *flag, int pass, cudaStream_t s);
 msrsb_status sell_spmv_df(const Sell &S, const double *val, const double *x, float *yh, float *yl, cudaStream_t s);
@@ -264,10 +266,16 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
     dfree(nzd, s);
     MSRSB_TRY(mark(2));
     // a3: Galerkin coarse operator with the unfiltered A, and its inverse
-    MSRSB_TRY(build_transpose(n, W, h->nc, h->p_ids, &h->pt_ptr, &h->pt_rows, &h->jslot, s));
+    MSRSB_TRY(build_transpose(n, W, h->nc, h->p_ids, &h->pt_ptr, &h->pt_rows, &h->jslot, &h->nnz_p, s));
     MSRSB_TRY(dalloc(&h->Ac, (size_t)h->nC * h->nC, s));
     MSRSB_TRY(dalloc(&h->Ainv, (size_t)h->nC * h->nC, s));
     MSRSB_TRY(galerkin<T>(&A, &h->grid, W, h->nc, h->p_ids, P, h->pt_ptr, h->pt_rows, h->jslot, h->Ac, s));
+    {  // P's values in column order for the restriction
+        T *pt = nullptr;
+        MSRSB_TRY(dalloc(&pt, (size_t)h->nnz_p * bd, s));
+        h->pt_val = pt;
+        MSRSB_TRY(pt_gather<T>(h, P, pt, s));
+    }
     MSRSB_TRY(mark(3));
     MSRSB_TRY(coarse_inverse(h->nC, h->Ac, h->Ainv, s));
     MSRSB_TRY(mark(4));
@@ -340,9 +348,9 @@ static msrsb_status apply_t(msrsb_handle *h, const TVI *v, TZ *z, cudaStream_t s
         }
         // coarse correction of the residual v - A z
         MSRSB_TRY((resid_t<T, TZ, TVI>(h, aval_t, z, v, r, nullptr, s)));
-        MSRSB_TRY((restrict_op<T, T>(h, P, r, h->vc, s)));
+        MSRSB_TRY((restrict_op<T, T>(h, (const T *)h->pt_val, r, h->vc, s)));
     } else {
-        MSRSB_TRY((restrict_op<T, TVI>(h, P, v, h->vc, s)));
+        MSRSB_TRY((restrict_op<T, TVI>(h, (const T *)h->pt_val, v, h->vc, s)));
     }
     MSRSB_TRY(gemv(h->nC, h->Ainv, h->vc, h->wc, s));
     MSRSB_TRY((prolong_op<T, TZ>(h, P, h->wc, z, pre ? 1 : 0, s)));
@@ -493,7 +501,6 @@ __global__ void gmres_init_kernel(int m, double *__restrict__ kh, const double *
     double *g = kh + L.g;
     for (int i = 0; i <= m; ++i) g[i] = 0.0;
     g[0] = *beta;
-    *(unsigned *)(kh + L.flag + 1) = 0u;  // multi-dot counter
 }
 
 // Restarted flexible GMRES with right preconditioning (Z_j = M^-1 V_j kept,
@@ -514,7 +521,6 @@ static msrsb_status gmres_t(msrsb_handle *h, const double *b, double *x, double 
     const KhLayout L(m);
     double *H = kh + L.H, *est = kh + L.est, *beta = kh + L.beta, *h2 = kh + L.h2;
     int *reorth = (int *)(kh + L.flag);
-    unsigned *counter = (unsigned *)(kh + L.flag + 1);  // last-CTA counter of the multi-dot (kept at 0)
     double *V = h->kv, *Z = h->kz;                    // FP64 basis (DFV = false)
     // double-float basis and work vector of the mixed form: [Vh | Vl | Wh | Wl]
     float *Vh = (float *)h->kv32, *Vl = Vh + (m + 1) * N, *Wh = Vl + (m + 1) * N, *Wl = Wh + N;
@@ -593,9 +599,9 @@ static msrsb_status gmres_t(msrsb_handle *h, const double *b, double *x, double 
                 }
                 // classical Gram-Schmidt with the DGKS test (see below), double-float vectors
                 float *oh = Vh + (j + 1) * N, *ol = Vl + (j + 1) * N;
-                MSRSB_TRY(mdot_df(N, j + 1, Vh, Vl, N, Wh, Wl, h->partial, h2, counter, s));
+                MSRSB_TRY(mdot_df(N, j + 1, Vh, Vl, N, Wh, Wl, h->partial, h2, s));
                 MSRSB_TRY(gs_update_df(N, j + 1, Vh, Vl, N, h2, Wh, Wl, oh, ol, hcol, reorth, 1, s));
-                MSRSB_TRY(mdot_df(N, j + 1, Vh, Vl, N, Wh, Wl, h->partial, h2, counter, s, reorth));
+                MSRSB_TRY(mdot_df(N, j + 1, Vh, Vl, N, Wh, Wl, h->partial, h2, s, reorth));
                 MSRSB_TRY(gs_update_df(N, j + 1, Vh, Vl, N, h2, Wh, Wl, oh, ol, hcol, reorth, 2, s));
             } else {
                 double *Vj = V + j * N, *w = V + (j + 1) * N;
@@ -761,6 +767,7 @@ static void handle_free(msrsb_handle *h) {
     dfree(h->pt_ptr, s);
     dfree(h->pt_rows, s);
     dfree(h->jslot, s);
+    dfree(h->pt_val, s);
     dfree(h->Ac, s);
     dfree(h->Ainv, s);
     dfree(h->ilu.lcol, s);

@@ -23,16 +23,10 @@ __device__ __forceinline__ void load_row(const T *__restrict__ P, long k, T (&ou
     static_assert((W * sizeof(T)) % 16 == 0, "row must be a multiple of 16 bytes");
     constexpr int B = W * (int)sizeof(T);
     if constexpr (B % 32 == 0) {
-        // 256-bit vector loads (sm_100 and later): a warp's 32 rows of 32 bytes
-        // are read in half the L1 wavefronts of two 128-bit loads
         const char *src = reinterpret_cast<const char *>(P + k * W);
         unsigned u[B / 4];
 #pragma unroll
-        for (int q = 0; q < B / 32; ++q)
-            asm("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                : "=r"(u[8 * q]), "=r"(u[8 * q + 1]), "=r"(u[8 * q + 2]), "=r"(u[8 * q + 3]), "=r"(u[8 * q + 4]),
-                  "=r"(u[8 * q + 5]), "=r"(u[8 * q + 6]), "=r"(u[8 * q + 7])
-                : "l"(src + 32 * q));
+        for (int q = 0; q < B / 32; ++q) ld_nc_v8(src + 32 * q, *reinterpret_cast<unsigned(*)[8]>(u + 8 * q));
         memcpy(out, u, B);
     } else {
         const uint4 *src = reinterpret_cast<const uint4 *>(P + k * W);

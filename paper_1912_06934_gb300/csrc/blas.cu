@@ -167,24 +167,24 @@ template msrsb_status sell_spmv<float, double, float, float, float>(const Sell &
 // ---- restriction and prolongation ------------------------------------------------
 
 // vc[J*bd + l] = sum_{i in supp(J)} P^l_{iJ} v[i*bd + l]; one CTA per J,
-// thread-private sums over the support rows, fixed-order block reduction
+// thread-private sums over the support rows, fixed-order block reduction.
+// PT holds P's values in the order of pt_rows (column J's entries
+// contiguous, component l at l*nnzp), so the reads of P are coalesced.
 template <typename TP, typename TV>
-__global__ void __launch_bounds__(256) restrict_kernel(int nc, int n, int W, int bd, const int32_t *__restrict__ pt_ptr,
+__global__ void __launch_bounds__(256) restrict_kernel(int nc, int nnzp, int bd, const int32_t *__restrict__ pt_ptr,
                                                        const int32_t *__restrict__ pt_rows,
-                                                       const int8_t *__restrict__ jslot, const TP *__restrict__ P,
-                                                       const TV *__restrict__ v, double *__restrict__ vc) {
+                                                       const TP *__restrict__ PT, const TV *__restrict__ v,
+                                                       double *__restrict__ vc) {
     pdl_prologue();
     __shared__ double red[3][8];
     const int J = blockIdx.x;
-    const int sj = jslot[J];
-    const long nW = (long)n * W;
     double acc[3] = {0.0, 0.0, 0.0};
     const int r1 = pt_ptr[J + 1];
     int r = pt_ptr[J] + threadIdx.x;
     for (; r + (int)blockDim.x < r1; r += 2 * blockDim.x) {
         const int i0 = pt_rows[r], i1 = pt_rows[r + blockDim.x];
         for (int l = 0; l < bd; ++l) {
-            const double p0 = (double)P[l * nW + (long)i0 * W + sj], p1 = (double)P[l * nW + (long)i1 * W + sj];
+            const double p0 = (double)PT[(long)l * nnzp + r], p1 = (double)PT[(long)l * nnzp + r + blockDim.x];
             const double v0 = (double)v[(long)i0 * bd + l], v1 = (double)v[(long)i1 * bd + l];
             acc[l] = fma(p0, v0, acc[l]);
             acc[l] = fma(p1, v1, acc[l]);
@@ -192,8 +192,7 @@ __global__ void __launch_bounds__(256) restrict_kernel(int nc, int n, int W, int
     }
     if (r < r1) {
         const int i = pt_rows[r];
-        for (int l = 0; l < bd; ++l)
-            acc[l] = fma((double)P[l * nW + (long)i * W + sj], (double)v[(long)i * bd + l], acc[l]);
+        for (int l = 0; l < bd; ++l) acc[l] = fma((double)PT[(long)l * nnzp + r], (double)v[(long)i * bd + l], acc[l]);
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int l = 0; l < bd; ++l) {
@@ -210,11 +209,32 @@ __global__ void __launch_bounds__(256) restrict_kernel(int nc, int n, int W, int
 }
 
 template <typename TP, typename TV>
-msrsb_status restrict_op(const msrsb_handle *h, const TP *P, const TV *v, double *vc, cudaStream_t s) {
-    MSRSB_PDL((restrict_kernel<TP, TV>), h->nc, 256, 0, s, h->nc, h->n, h->W, h->bdim, h->pt_ptr, h->pt_rows, h->jslot,
-              P, v, vc);
+msrsb_status restrict_op(const msrsb_handle *h, const TP *PT, const TV *v, double *vc, cudaStream_t s) {
+    MSRSB_PDL((restrict_kernel<TP, TV>), h->nc, 256, 0, s, h->nc, h->nnz_p, h->bdim, h->pt_ptr, h->pt_rows, PT, v,
+              vc);
     return MSRSB_OK;
 }
+
+// PT[l*nnzp + r] = P^l[pt_rows[r]][jslot[J]] for r in J's range (once per set-up)
+template <typename TP>
+__global__ void pt_gather_kernel(int nnzp, long nW, int W, int bd, const int32_t *__restrict__ pt_ptr,
+                                 const int32_t *__restrict__ pt_rows, const int8_t *__restrict__ jslot,
+                                 const TP *__restrict__ P, TP *__restrict__ PT) {
+    const int J = blockIdx.x, sj = jslot[J];
+    for (int r = pt_ptr[J] + threadIdx.x; r < pt_ptr[J + 1]; r += blockDim.x)
+        for (int l = 0; l < bd; ++l) PT[(long)l * nnzp + r] = P[l * nW + (long)pt_rows[r] * W + sj];
+}
+
+template <typename TP>
+msrsb_status pt_gather(const msrsb_handle *h, const TP *P, TP *PT, cudaStream_t s) {
+    pt_gather_kernel<TP><<<h->nc, 256, 0, s>>>(h->nnz_p, (long)h->n * h->W, h->W, h->bdim, h->pt_ptr, h->pt_rows,
+                                               h->jslot, P, PT);
+    MSRSB_LAUNCHED("pt_gather_kernel");
+    return MSRSB_OK;
+}
+template msrsb_status pt_gather<double>(const msrsb_handle *, const double *, double *, cudaStream_t);
+template msrsb_status pt_gather<float>(const msrsb_handle *, const float *, float *, cudaStream_t);
+
 template msrsb_status restrict_op<double, double>(const msrsb_handle *, const double *, const double *, double *,
                                                   cudaStream_t);
 template msrsb_status restrict_op<float, double>(const msrsb_handle *, const float *, const double *, double *,
@@ -223,7 +243,24 @@ template msrsb_status restrict_op<float, float>(const msrsb_handle *, const floa
                                                 cudaStream_t);
 
 // z[i*bd + l] (+)= sum_s P^l_{is} wc[ids_is*bd + l]; the ids and values of
-// a row are read as 16-byte vectors
+// a row are read as 256-bit (or 128-bit) vectors
+template <typename T, int W>
+__device__ __forceinline__ void load32(const T *__restrict__ p, T (&out)[W]) {
+    constexpr int B = W * (int)sizeof(T);
+    if constexpr (B % 32 == 0) {
+        unsigned u[B / 4];
+#pragma unroll
+        for (int q = 0; q < B / 32; ++q)
+            ld_nc_v8(reinterpret_cast<const char *>(p) + 32 * q, *reinterpret_cast<unsigned(*)[8]>(u + 8 * q));
+        memcpy(out, u, B);
+    } else {
+        static_assert(B % 16 == 0, "record must be a multiple of 16 bytes");
+#pragma unroll
+        for (int q = 0; q < B / 16; ++q)
+            reinterpret_cast<uint4 *>(out)[q] = __ldg(reinterpret_cast<const uint4 *>(p) + q);
+    }
+}
+
 template <typename TP, typename TZ, int W>
 __global__ void __launch_bounds__(256) prolong_kernel(int n, int bd, const int32_t *__restrict__ p_ids,
                                                       const TP *__restrict__ P, const double *__restrict__ wc,
@@ -233,16 +270,10 @@ __global__ void __launch_bounds__(256) prolong_kernel(int n, int bd, const int32
     if (i >= n) return;
     const long nW = (long)n * W;
     int32_t ids[W];
-    {
-        const int4 *src = reinterpret_cast<const int4 *>(p_ids + (long)i * W);
-#pragma unroll
-        for (int q = 0; q < W / 4; ++q) reinterpret_cast<int4 *>(ids)[q] = __ldg(src + q);
-    }
+    load32<int32_t, W>(p_ids + (long)i * W, ids);
     for (int l = 0; l < bd; ++l) {
         TP pv[W];
-        const uint4 *src = reinterpret_cast<const uint4 *>(P + l * nW + (long)i * W);
-#pragma unroll
-        for (int q = 0; q < (int)(W * sizeof(TP) / 16); ++q) reinterpret_cast<uint4 *>(pv)[q] = __ldg(src + q);
+        load32<TP, W>(P + l * nW + (long)i * W, pv);
         double s = 0.0;
 #pragma unroll
         for (int c = 0; c < W; ++c)
@@ -659,18 +690,14 @@ msrsb_status df_split(long N, const double *w, float *wh, float *wl, cudaStream_
 
 // partial[q * gridDim.x + b] = sum over row chunk b of V_q . w (q < nv), and
 // for q = nv the squared norm of w; all vectors double-float, FP32 arithmetic
-// up to the per-warp results. The last CTA to finish (counter) sums the
-// partials of every q in a fixed order into hs[q] and resets the counter, so
-// no separate reduction launch is needed.
+// up to the per-warp results
 __global__ void __launch_bounds__(256) mdot_df_kernel(long N, int nv, const float *__restrict__ Vh,
                                                       const float *__restrict__ Vl, long ldv,
                                                       const float *__restrict__ Wh, const float *__restrict__ Wl,
-                                                      double *__restrict__ partial, double *__restrict__ hs,
-                                                      unsigned *__restrict__ counter, const int *__restrict__ gate) {
+                                                      double *__restrict__ partial, const int *__restrict__ gate) {
     pdl_prologue();
     if (gate && !*gate) return;
     __shared__ double red[8];
-    __shared__ bool last;
     const int q = blockIdx.y;
     const long chunk = (N + gridDim.x - 1) / gridDim.x;
     const long b0 = blockIdx.x * chunk, b1 = b0 + chunk < N ? b0 + chunk : N;
@@ -690,34 +717,19 @@ __global__ void __launch_bounds__(256) mdot_df_kernel(long N, int nv, const floa
     if (threadIdx.x < 32) {
         double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
         v = warp_sum(v);
-        if (threadIdx.x == 0) {
-            partial[(long)q * gridDim.x + blockIdx.x] = v;
-            __threadfence();
-            const unsigned total = gridDim.x * gridDim.y;
-            last = atomicAdd(counter, 1u) == total - 1;
-        }
+        if (threadIdx.x == 0) partial[(long)q * gridDim.x + blockIdx.x] = v;
     }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    // final sums: one warp per q, lanes over the row chunks, fixed tree
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nblk = gridDim.x;
-    for (int qq = warp; qq < (int)gridDim.y; qq += blockDim.x >> 5) {
-        const volatile double *pp = partial + (long)qq * nblk;
-        double v = 0.0;
-        for (int b = lane; b < nblk; b += 32) v += pp[b];
-        v = warp_sum(v);
-        if (lane == 0) hs[qq] = v;
-    }
-    if (threadIdx.x == 0) *counter = 0u;
 }
 
-// hs[q] = V_q . w (q < nv), hs[nv] = w . w; counter: a zeroed device word
+__global__ void reduce_partials_kernel(int nblk, const double *__restrict__ partial, double *__restrict__ out,
+                                       int accumulate, int sqrt_out, const int *__restrict__ gate);
+
+// hs[q] = V_q . w (q < nv), hs[nv] = w . w
 msrsb_status mdot_df(long N, int nv, const float *Vh, const float *Vl, long ldv, const float *Wh, const float *Wl,
-                     double *partial, double *hs, unsigned *counter, cudaStream_t s, const int *gate) {
+                     double *partial, double *hs, cudaStream_t s, const int *gate) {
     dim3 grid(kRedBlocks, nv + 1);
-    MSRSB_PDL((mdot_df_kernel), grid, 256, 0, s, N, nv, Vh, Vl, ldv, Wh, Wl, partial, hs, counter, gate);
+    MSRSB_PDL((mdot_df_kernel), grid, 256, 0, s, N, nv, Vh, Vl, ldv, Wh, Wl, partial, gate);
+    MSRSB_PDL((reduce_partials_kernel), nv + 1, 256, 0, s, kRedBlocks, partial, hs, 0, 0, gate);
     return MSRSB_OK;
 }
 

@@ -150,6 +150,15 @@ __device__ __forceinline__ float warp_sum(float v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
+// 32 bytes from a 32-byte aligned address through the read-only path, as
+// one 256-bit vector load (sm_100 and later): a warp reading 32 consecutive
+// 32-byte records needs half the L1 wavefronts of two 128-bit loads
+__device__ __forceinline__ void ld_nc_v8(const void *p, unsigned (&u)[8]) {
+    asm("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7])
+        : "l"(p));
+}
+
 __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -179,6 +188,8 @@ struct msrsb_handle {
     // CSC of P's pattern: rows of every coarse node's support, ascending
     int32_t *pt_ptr = nullptr, *pt_rows = nullptr;
     int8_t *jslot = nullptr;  // slot of coarse node J in every row of its support
+    int nnz_p = 0;             // entries of P's pattern (per component)
+    void *pt_val = nullptr;    // P's values in pt_rows order [ncomp][nnz_p], handle precision
     // coarse operator and its inverse (FP64, dense nC x nC)
     double *Ac = nullptr, *Ainv = nullptr;
     // smoother factors in A's (block) pattern, handle precision

@@ -29,7 +29,7 @@ __global__ void pt_pairs_kernel(long nW, int W, const int32_t *__restrict__ p_id
 // Transposed pattern of P: pt_ptr[nc+1], pt_rows[nnz(P)] (rows ascending per
 // coarse node; a stable radix sort keeps the row order). Also jslot[nc].
 msrsb_status build_transpose(int n, int W, int nc, const int32_t *p_ids, int32_t **pt_ptr, int32_t **pt_rows,
-                             int8_t **jslot, cudaStream_t s) {
+                             int8_t **jslot, int *nnzp_out, cudaStream_t s) {
     long nW = (long)n * W;
     int32_t *keys = nullptr, *vals = nullptr, *keys2 = nullptr, *vals2 = nullptr, *count = nullptr;
     MSRSB_TRY(dalloc(&keys, nW, s));
@@ -56,6 +56,7 @@ msrsb_status build_transpose(int n, int W, int nc, const int32_t *p_ids, int32_t
     MSRSB_CUDA(cudaMemcpyAsync(&nnzp, *pt_ptr + nc, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     MSRSB_CUDA(cudaStreamSynchronize(s));
     MSRSB_TRY(dalloc(pt_rows, nnzp, s));
+    if (nnzp_out) *nnzp_out = nnzp;
     MSRSB_CUDA(cudaMemcpyAsync(*pt_rows, vals2, (size_t)nnzp * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
     dfree(tmp, s);
     dfree(keys, s);
@@ -224,7 +225,7 @@ extern "C" msrsb_status msrsb_coarse_op(const msrsb_mat *A, const msrsb_grid *g,
     if ((long)nc * A->bdim > 8192) return fail(MSRSB_ESHAPE, "nc * bdim must be <= 8192");
     int32_t *pt_ptr = nullptr, *pt_rows = nullptr;
     int8_t *jslot = nullptr;
-    MSRSB_TRY(build_transpose(A->nrows, W, nc, p_ids, &pt_ptr, &pt_rows, &jslot, stream));
+    MSRSB_TRY(build_transpose(A->nrows, W, nc, p_ids, &pt_ptr, &pt_rows, &jslot, nullptr, stream));
     msrsb_status st;
     if (prec == MSRSB_F64)
         st = galerkin<double>(A, g, W, nc, p_ids, (const double *)p_val, pt_ptr, pt_rows, jslot, Ac_dense, stream);
