@@ -8,6 +8,7 @@
 #include <cstring>
 #include <string>
 #include <thread>
+#include <future>
 
 namespace msrsb {
 
@@ -220,8 +221,21 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
     MSRSB_CUDA(cudaGetDevice(&dev));
     msrsb_status side_st = MSRSB_OK;
     std::string side_err;
+    // the transposed pattern of P (needs only the partition) is built first
+    // on the side stream; the Galerkin product waits for it below
+    cudaEvent_t tr_ev = nullptr;
+    MSRSB_CUDA(cudaEventCreateWithFlags(&tr_ev, cudaEventDisableTiming));
+    std::promise<msrsb_status> tr_done;
+    std::future<msrsb_status> tr_status = tr_done.get_future();
+    std::string tr_err;
     std::thread side_thread([&]() {
         cudaSetDevice(dev);
+        msrsb_status st =
+            build_transpose(n, W, h->nc, h->p_ids, &h->pt_ptr, &h->pt_rows, &h->jslot, &h->nnz_p, h->side);
+        if (st == MSRSB_OK && cudaEventRecord(tr_ev, h->side) != cudaSuccess)
+            st = fail(MSRSB_ECUDA, "event record failed");
+        if (st != MSRSB_OK) tr_err = msrsb_last_error();
+        tr_done.set_value(st);
         side_st = setup_smoother<T>(h, h->side);
         if (side_st != MSRSB_OK) side_err = msrsb_last_error();
     });
@@ -266,7 +280,11 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
     dfree(nzd, s);
     MSRSB_TRY(mark(2));
     // a3: Galerkin coarse operator with the unfiltered A, and its inverse
-    MSRSB_TRY(build_transpose(n, W, h->nc, h->p_ids, &h->pt_ptr, &h->pt_rows, &h->jslot, &h->nnz_p, s));
+    {
+        const msrsb_status st = tr_status.get();
+        if (st != MSRSB_OK) return fail(st, "%s", tr_err.c_str());
+        MSRSB_CUDA(cudaStreamWaitEvent(s, tr_ev, 0));
+    }
     MSRSB_TRY(dalloc(&h->Ac, (size_t)h->nC * h->nC, s));
     MSRSB_TRY(dalloc(&h->Ainv, (size_t)h->nC * h->nC, s));
     MSRSB_TRY(galerkin<T>(&A, &h->grid, W, h->nc, h->p_ids, P, h->pt_ptr, h->pt_rows, h->jslot, h->Ac, s));
@@ -297,6 +315,7 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
     MSRSB_CUDA(cudaStreamWaitEvent(s, join, 0));
     cudaEventDestroy(fork);
     cudaEventDestroy(join);
+    cudaEventDestroy(tr_ev);
     MSRSB_TRY(mark(6));
     MSRSB_CUDA(cudaStreamSynchronize(s));
     if (prof) {
@@ -484,15 +503,27 @@ __global__ void givens_kernel(int m, int j, double *__restrict__ kh) {
     for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) hc[i] = col[i];
 }
 
-// back substitution H(0:k,0:k) y = g(0:k); y written over g
+// back substitution H(0:k,0:k) y = g(0:k); y written over g. Column
+// oriented: once y_c is known, thread i < c removes H(i,c) y_c from g_i.
 __global__ void hess_solve_kernel(int m, int k, double *__restrict__ kh) {
     pdl_prologue();
-    double *H = kh, *g = kh + (long)(m + 1) * m + 2 * m;
-    for (int i = k - 1; i >= 0; --i) {
-        double s = g[i];
-        for (int c = i + 1; c < k; ++c) s -= H[(long)c * (m + 1) + i] * g[c];
-        g[i] = s / H[(long)i * (m + 1) + i];
+    const KhLayout L(m);
+    const double *H = kh + L.H;
+    double *g = kh + L.g;
+    __shared__ double gs[1024];
+    __shared__ double yc;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) gs[i] = g[i];
+    __syncthreads();
+    for (int c = k - 1; c >= 0; --c) {
+        const double *hc = H + (long)c * (m + 1);
+        if (threadIdx.x == 0) yc = gs[c] / hc[c];
+        __syncthreads();
+        const double y = yc;
+        for (int i = threadIdx.x; i < c; i += blockDim.x) gs[i] -= hc[i] * y;
+        if (threadIdx.x == 0) gs[c] = y;
+        __syncthreads();
     }
+    for (int i = threadIdx.x; i < k; i += blockDim.x) g[i] = gs[i];
 }
 
 __global__ void gmres_init_kernel(int m, double *__restrict__ kh, const double *__restrict__ beta) {
@@ -653,7 +684,7 @@ static msrsb_status gmres_t(msrsb_handle *h, const double *b, double *x, double 
         }
         const int k = conv >= 0 ? conv + 1 : launched;
         its += k;
-        MSRSB_PDL((hess_solve_kernel), 1, 1, 0, s, m, k, kh);
+        MSRSB_PDL((hess_solve_kernel), 1, 256, 0, s, m, k, kh);
         MSRSB_TRY(mvadd<double>(N, k, Z, N, kh + L.g, x, s));
     }
     *iters = its;

@@ -318,21 +318,36 @@ __global__ void transpose_kernel(int n, const double *__restrict__ a, double *__
         if (x < n && y + q < n) b[(long)(y + q) * n + x] = tile[threadIdx.x][threadIdx.y + q];
 }
 
-// out (row-major) = X (column-major) with the row interchanges undone on the
-// columns in reverse order; one output row per thread
-__global__ void unscramble_kernel(int n, const double *__restrict__ Xcm, const int *__restrict__ perm,
-                                  double *__restrict__ out) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double *orow = out + (long)i * n;
-    for (int j = 0; j < n; ++j) orow[j] = Xcm[(long)j * n + i];
+// The row interchanges of the elimination, undone on the columns in reverse
+// order, are one fixed permutation of the columns: src[j] = the column of X
+// that ends up in column j. One thread; the chain of swaps is sequential.
+__global__ void unscramble_index_kernel(int n, const int *__restrict__ perm, int *__restrict__ src) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    for (int j = 0; j < n; ++j) src[j] = j;
     for (int k = n - 1; k >= 0; --k) {
-        int p = perm[k];
+        const int p = perm[k];
         if (p != k) {
-            double t = orow[k];
-            orow[k] = orow[p];
-            orow[p] = t;
+            const int t = src[k];
+            src[k] = src[p];
+            src[p] = t;
         }
+    }
+}
+
+// out (row-major) = X (column-major) with its columns permuted by src:
+// out[i][j] = X[src[j]][i], through 32 x 32 shared-memory tiles
+__global__ void unscramble_kernel(int n, const double *__restrict__ Xcm, const int *__restrict__ src,
+                                  double *__restrict__ out) {
+    __shared__ double tile[32][33];
+    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+    for (int q = threadIdx.y; q < 32; q += 8) {  // read column src[j0+q], rows i0..i0+31
+        const int j = j0 + q, i = i0 + threadIdx.x;
+        if (j < n && i < n) tile[q][threadIdx.x] = Xcm[(long)src[j] * n + i];
+    }
+    __syncthreads();
+    for (int q = threadIdx.y; q < 32; q += 8) {  // write row i0+q, columns j0..j0+31
+        const int i = i0 + q, j = j0 + threadIdx.x;
+        if (i < n && j < n) out[(long)i * n + j] = tile[threadIdx.x][q];
     }
 }
 
@@ -390,7 +405,11 @@ msrsb_status coarse_inverse_launch(int n, const double *Ac, double *Ainv, Coarse
         MSRSB_CUDA(cudaLaunchCooperativeKernel((void *)gauss_jordan_kernel, grid, 256, args, smem, s));
         MSRSB_LAUNCHED("gauss_jordan_kernel");
     }
-    unscramble_kernel<<<ceil_div(n, 128), 128, 0, s>>>(n, Xres ? Xres : w->X, w->perm, Ainv);
+    MSRSB_TRY(dalloc(&w->src, n, s));
+    unscramble_index_kernel<<<1, 1, 0, s>>>(n, w->perm, w->src);
+    MSRSB_LAUNCHED("unscramble_index_kernel");
+    unscramble_kernel<<<dim3(ceil_div(n, 32), ceil_div(n, 32)), dim3(32, 8), 0, s>>>(n, Xres ? Xres : w->X, w->src,
+                                                                                   Ainv);
     MSRSB_LAUNCHED("unscramble_kernel");
     // pinned destination: a copy into pageable memory would block the host
     // until the inverse is done and defeat the overlap
@@ -416,6 +435,7 @@ msrsb_status coarse_inverse_finish(CoarseInverseWork *w, cudaStream_t s) {
     dfree(w->ig, s);
     dfree(w->pg, s);
     dfree(w->perm, s);
+    dfree(w->src, s);
     dfree(w->status, s);
     if (w->h_status)
         return fail(MSRSB_EBREAKDOWN, "coarse operator is singular (zero pivot at column %d)", w->h_status - 1);

@@ -122,7 +122,7 @@ struct Sell {
 // work arrays of the coarse inverse while it runs (see coarse.cu)
 struct CoarseInverseWork {
     double *X = nullptr, *Xres = nullptr, *Fg = nullptr, *ig = nullptr;
-    int *perm = nullptr, *status = nullptr, *pg = nullptr;
+    int *perm = nullptr, *status = nullptr, *pg = nullptr, *src = nullptr;
     int *pin_status = nullptr;  // pinned copy of the status (slot of the pinned scratch)
     int h_status = 0;
 };

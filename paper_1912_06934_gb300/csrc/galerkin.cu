@@ -13,16 +13,27 @@
 namespace msrsb {
 
 // (key = coarse id, value = fine row) for every used slot of p_ids
-__global__ void pt_pairs_kernel(long nW, int W, const int32_t *__restrict__ p_ids, int32_t *__restrict__ keys,
+// keys/vals: (coarse node, row) for every pattern entry of P (-1 slots get a
+// key past every node); count[J] = entries of column J; jslot[J] = J's slot.
+// One thread per row; for every slot the warp's rows that share a coarse node
+// add their count with one atomic.
+__global__ void pt_pairs_kernel(int n, int W, const int32_t *__restrict__ p_ids, int32_t *__restrict__ keys,
                                 int32_t *__restrict__ vals, int32_t *__restrict__ count, int8_t *__restrict__ jslot) {
-    long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (t >= nW) return;
-    int32_t J = p_ids[t];
-    keys[t] = J >= 0 ? J : 0x7fffffff;
-    vals[t] = (int32_t)(t / W);
-    if (J >= 0) {
-        atomicAdd(count + J, 1);
-        jslot[J] = (int8_t)(t % W);  // the same slot in every row (colour slots)
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = i < n;
+    const int lane = threadIdx.x & 31;
+    for (int c = 0; c < W; ++c) {
+        const long t = (long)i * W + c;
+        const int32_t J = live ? p_ids[t] : -1;
+        if (live) {
+            keys[t] = J >= 0 ? J : 0x7fffffff;
+            vals[t] = i;
+        }
+        const unsigned same = __match_any_sync(0xffffffffu, J);
+        if (J >= 0 && lane == __ffs(same) - 1) {
+            atomicAdd(count + J, __popc(same));
+            jslot[J] = (int8_t)c;  // the same slot in every row (colour slots)
+        }
     }
 }
 
@@ -40,7 +51,7 @@ msrsb_status build_transpose(int n, int W, int nc, const int32_t *p_ids, int32_t
     MSRSB_TRY(dalloc(pt_ptr, nc + 1, s));
     MSRSB_TRY(dalloc(jslot, nc, s));
     MSRSB_CUDA(cudaMemsetAsync(count, 0, (nc + 1) * sizeof(int32_t), s));
-    pt_pairs_kernel<<<ceil_div(nW, 256), 256, 0, s>>>(nW, W, p_ids, keys, vals, count, *jslot);
+    pt_pairs_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, W, p_ids, keys, vals, count, *jslot);
     MSRSB_LAUNCHED("pt_pairs_kernel");
     size_t tmp1 = 0, tmp2 = 0;
     int bits = 1;

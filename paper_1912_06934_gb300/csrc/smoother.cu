@@ -16,9 +16,15 @@ __global__ void iota_kernel(int n, int32_t *__restrict__ v) {
     if (i < n) v[i] = i;
 }
 
+// count[c] += rows of colour c (c < 16): per-CTA histogram, then 16 atomics
 __global__ void colour_count_kernel(int n, const uint8_t *__restrict__ colour, int32_t *__restrict__ count) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) atomicAdd(count + colour[i], 1);
+    __shared__ int hist[16];
+    if (threadIdx.x < 16) hist[threadIdx.x] = 0;
+    __syncthreads();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        atomicAdd(hist + colour[i], 1);
+    __syncthreads();
+    if (threadIdx.x < 16 && hist[threadIdx.x]) atomicAdd(count + threadIdx.x, hist[threadIdx.x]);
 }
 
 // rows grouped by colour (ascending index within a colour); host copy of the
@@ -33,7 +39,7 @@ msrsb_status colour_classes(int n, const uint8_t *colour, int ncol, int32_t **ro
     iota_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, idx);
     MSRSB_LAUNCHED("iota_kernel");
     MSRSB_CUDA(cudaMemsetAsync(count, 0, 16 * sizeof(int32_t), s));
-    colour_count_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, colour, count);
+    colour_count_kernel<<<ceil_div(n, 256) < 304 ? ceil_div(n, 256) : 304, 256, 0, s>>>(n, colour, count);
     MSRSB_LAUNCHED("colour_count_kernel");
     size_t tmp = 0;
     MSRSB_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp, colour, keys2, idx, *rows, n, 0, 8, s));
