@@ -651,7 +651,10 @@ static msrsb_status gmres_t(msrsb_handle *h, const double *b, double *x, double 
                 MSRSB_CUDA(cudaEventRecord(fork_ev, s));
                 MSRSB_CUDA(cudaStreamWaitEvent(gv, fork_ev, 0));
             }
-            MSRSB_PDL((givens_kernel), 1, 32, 0, gv, m, j, kh);
+            // launched without programmatic dependence: on the side stream it
+            // follows a wait on the main stream's event, which must hold in full
+            givens_kernel<<<1, 32, 0, gv>>>(m, j, kh);
+            MSRSB_LAUNCHED("givens_kernel");
             launched = j + 1;
             if (lagged) {
                 MSRSB_CUDA(cudaMemcpyAsync(pin_est + j, kh + L.hist + j, sizeof(double), cudaMemcpyDeviceToHost, gv));
@@ -684,7 +687,8 @@ static msrsb_status gmres_t(msrsb_handle *h, const double *b, double *x, double 
         }
         const int k = conv >= 0 ? conv + 1 : launched;
         its += k;
-        MSRSB_PDL((hess_solve_kernel), 1, 256, 0, s, m, k, kh);
+        hess_solve_kernel<<<1, 256, 0, s>>>(m, k, kh);  // follows the wait on the Givens stream: no PDL
+        MSRSB_LAUNCHED("hess_solve_kernel");
         MSRSB_TRY(mvadd<double>(N, k, Z, N, kh + L.g, x, s));
     }
     *iters = its;

@@ -613,14 +613,15 @@ __device__ __forceinline__ DF df_mul(DF a, DF b) {
     e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
     return quick_two_sum(p, e);
 }
-// s += a * b; s is an unnormalised accumulator (hi, lo), the lo*lo term is
-// below the format's precision
+// s += a * b in double-float, renormalised after every step so that the low
+// word stays within half an ulp of the high word (an unnormalised low word
+// collects every rounding error and limits long sums to ~1e-13); the lo*lo
+// term is below the format's precision
 __device__ __forceinline__ void df_fma_acc(DF &s, float ah, float al, float bh, float bl) {
     const float p = __fmul_rn(ah, bh);
     const float e = fmaf(ah, bh, -p);
     const DF t = two_sum(s.hi, p);
-    s.hi = t.hi;
-    s.lo = __fadd_rn(s.lo, __fadd_rn(t.lo, fmaf(ah, bl, fmaf(al, bh, e))));
+    s = two_sum(t.hi, __fadd_rn(s.lo, __fadd_rn(t.lo, fmaf(ah, bl, fmaf(al, bh, e)))));
 }
 __device__ __forceinline__ DF df_shfl_down(DF v, int o) {
     return DF{__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};

@@ -7,6 +7,7 @@
 // sequential triangular solves.
 #include "common.cuh"
 #include <cooperative_groups.h>
+#include <mutex>
 
 namespace cg = cooperative_groups;
 
@@ -27,6 +28,12 @@ double *pinned_scratch();
 // are scarce on this GPU, so the panel is factored once, not in every CTA.)
 constexpr int GJ_NB = 8;
 constexpr int GJ_OWN = 4;  // own columns staged in shared memory at a time
+
+// Values that another CTA of the same kernel wrote (the published panel, the
+// pivots, columns written back by their owners, the status word) are read
+// with __ldcg, through L2: the L1 of an SM is not coherent with writes from
+// other SMs, and a plain load after the grid barrier may return a stale line
+// cached from an earlier use of the same buffer.
 
 // Index of the largest |col[i]|, k <= i < n, ties to the lowest index. The
 // magnitudes are compared as the integer bit patterns of |x| (IEEE order of
@@ -86,7 +93,7 @@ __global__ void __launch_bounds__(256) gauss_jordan_kernel(int n, double *__rest
         const int nb = min(GJ_NB, n - k0);
         // --- CTA 0: factor the panel ---
         if (blockIdx.x == 0) {
-            for (int q = threadIdx.x; q < nb * n; q += blockDim.x) Pn[q] = X[(long)k0 * n + q];
+            for (int q = threadIdx.x; q < nb * n; q += blockDim.x) Pn[q] = __ldcg(X + (long)k0 * n + q);
             __syncthreads();
             bool bad = false;
             for (int t = 0; t < nb && !bad; ++t) {
@@ -135,18 +142,18 @@ __global__ void __launch_bounds__(256) gauss_jordan_kernel(int n, double *__rest
         }
         __threadfence();
         grid.sync();
-        if (*status) return;  // singular: every CTA leaves here
+        if (__ldcg(status)) return;  // singular: every CTA leaves here
         // --- every CTA: the panel's steps on its own columns outside the panel ---
         if (c1 > c0) {
-            for (int q = threadIdx.x; q < nb * n; q += blockDim.x) Pn[q] = Fg[q];
+            for (int q = threadIdx.x; q < nb * n; q += blockDim.x) Pn[q] = __ldcg(Fg + q);
             if (threadIdx.x < nb) {
-                s_piv[threadIdx.x] = pg[threadIdx.x];
-                s_inv[threadIdx.x] = ig[threadIdx.x];
+                s_piv[threadIdx.x] = __ldcg(pg + threadIdx.x);
+                s_inv[threadIdx.x] = __ldcg(ig + threadIdx.x);
             }
             __syncthreads();
             for (int a0 = c0; a0 < c1; a0 += GJ_OWN) {
                 const int na = min(GJ_OWN, c1 - a0);
-                for (int q = threadIdx.x; q < na * n; q += blockDim.x) Own[q] = X[(long)a0 * n + q];
+                for (int q = threadIdx.x; q < na * n; q += blockDim.x) Own[q] = __ldcg(X + (long)a0 * n + q);
                 __syncthreads();
                 for (int t = 0; t < nb; ++t) {
                     const int k = k0 + t, p = s_piv[t];
@@ -211,6 +218,7 @@ __global__ void __launch_bounds__(256) gauss_jordan_resident_kernel(int n, const
     __shared__ double s_best[8], s_inv[GJ_RS], s_xk[GJ_RS], s_xo[64];
     __shared__ int s_idx[8], s_piv[GJ_RS];
     for (int q = threadIdx.x; q < na * n; q += blockDim.x) Own[q] = Xin[(long)c0 * n + q];
+    __syncthreads();  // the publication below reads elements other threads loaded
     // publish the first panel
     for (int c = 0; c < na; ++c) {
         const int j = c0 + c;
@@ -222,7 +230,7 @@ __global__ void __launch_bounds__(256) gauss_jordan_resident_kernel(int n, const
     for (int k0 = 0, it = 0; k0 < n; k0 += GJ_RS, ++it) {
         const int nb = min(GJ_RS, n - k0);
         const double *pb = pub + (long)(it & 1) * GJ_RS * n;
-        for (int q = threadIdx.x; q < nb * n; q += blockDim.x) Pnl[q] = pb[q];
+        for (int q = threadIdx.x; q < nb * n; q += blockDim.x) Pnl[q] = __ldcg(pb + q);
         __syncthreads();
         // replay the panel: pivots, 1/pivots and the f columns (kept in Pnl)
         for (int t = 0; t < nb; ++t) {
@@ -351,6 +359,9 @@ __global__ void unscramble_kernel(int n, const double *__restrict__ Xcm, const i
     }
 }
 
+constexpr int kGjResidentSmemMax = 200 * 1024;  // dynamic shared memory limits of the two kernels
+constexpr int kGjSmemMax = 220 * 1024;
+
 // Ainv (device, n x n row-major) = inverse of Ac (device, n x n row-major, not
 // modified). Split in two so the set-up can overlap it with independent work:
 // coarse_inverse_launch enqueues everything on s without waiting;
@@ -372,10 +383,12 @@ msrsb_status coarse_inverse_launch(int n, const double *Ac, double *Ainv, Coarse
     const int cols_per = (n + grid_r - 1) / grid_r;
     const size_t smem_r = (size_t)(cols_per + GJ_RS) * n * sizeof(double);
     double *Xres = nullptr;
-    if (smem_r <= 200 * 1024 && cols_per <= 64) {
+    if (smem_r <= (size_t)kGjResidentSmemMax && cols_per <= 64) {
         int occ = 0;
+        // the attribute is per function, shared by every host thread: always
+        // the same (largest) value, so concurrent set-ups cannot undercut it
         MSRSB_CUDA(cudaFuncSetAttribute(gauss_jordan_resident_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)smem_r));
+                                        kGjResidentSmemMax));
         MSRSB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gauss_jordan_resident_kernel, 256, smem_r));
         if (occ > 0) {
             MSRSB_TRY(dalloc(&w->Fg, (size_t)2 * GJ_RS * n, s));  // publication buffer
@@ -393,8 +406,9 @@ msrsb_status coarse_inverse_launch(int n, const double *Ac, double *Ainv, Coarse
         MSRSB_TRY(dalloc(&w->ig, GJ_NB, s));
         MSRSB_TRY(dalloc(&w->pg, GJ_NB, s));
         const size_t smem = (size_t)(GJ_NB + GJ_OWN) * n * sizeof(double);
-        if (smem > 220 * 1024) return fail(MSRSB_ESHAPE, "coarse system too large for the inverse (n = %d)", n);
-        MSRSB_CUDA(cudaFuncSetAttribute(gauss_jordan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if (smem > (size_t)kGjSmemMax) return fail(MSRSB_ESHAPE, "coarse system too large for the inverse (n = %d)", n);
+        MSRSB_CUDA(cudaFuncSetAttribute(gauss_jordan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        kGjSmemMax));
         int occ = 0;
         MSRSB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gauss_jordan_kernel, 256, smem));
         int grid = occ > 0 ? sms : 0;
@@ -442,7 +456,14 @@ msrsb_status coarse_inverse_finish(CoarseInverseWork *w, cudaStream_t s) {
     return MSRSB_OK;
 }
 
+// One coarse inverse at a time in the process: its kernel waits on grid-wide
+// barriers, so two of them (set-ups of different problems on different
+// streams) are never in flight together; the lock is held until this one
+// has finished on the device.
+static std::mutex g_coarse_inverse_lock;
+
 msrsb_status coarse_inverse(int n, const double *Ac, double *Ainv, cudaStream_t s) {
+    std::lock_guard<std::mutex> lock(g_coarse_inverse_lock);
     CoarseInverseWork w;
     MSRSB_TRY(coarse_inverse_launch(n, Ac, Ainv, &w, s));
     return coarse_inverse_finish(&w, s);

@@ -37,7 +37,9 @@ void count_launch();
 // grid has completed and its writes are visible (before any global memory
 // access of this kernel), then launch_dependents lets the next grid be
 // scheduled during this one's tail. Launched without the attribute, both
-// instructions are no-ops.
+// instructions are no-ops. A kernel whose stream just waited on another
+// stream's event is launched without the attribute, so that the cross-stream
+// dependence holds in full.
 __device__ __forceinline__ void pdl_prologue() {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
