@@ -32,6 +32,7 @@ METRIC = "MsRSB basis build + PCG/GMRES solve s to 1e-8, HBM GB/s; mixed vs FP64
 WORKLOAD = "3D Darcy 64^3 MPFA-O 27-point, ln k GRF (l=8, sigma=3), 10:1 aniso rot (20,35,0), corner wells, H=8^3"
 N_GRID, H_BLOCK, SEED = 64, 8, 1002
 RTOL, MAXIT = 1e-8, 300
+ENS_MAXIT = 2000  # ensemble solves: random right-hand sides may need several GMRES(200) cycles
 BASIS = dict(tol=1e-3, n_it=10, max_iter=100)
 PHASES = ("partition", "filter_basis", "galerkin", "coarse_inverse", "workspace", "smoother_wait")
 
@@ -199,6 +200,23 @@ def gpu_arm(args, rank, world):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         t32, t64 = float(t[0]), float(t[1])
 
+    # error of each mixed-form result against the FP64 form on the same input
+    # (not timed): P, A_c, one preconditioner apply, the solution
+    hs = {pr: M.msrsb_setup(A, g, M.opts(prec=pr, **BASIS)) for pr in (M.msrsb.MSRSB_F64, M.msrsb.MSRSB_F32)}
+    (_, P64, Ac64), (_, P32, Ac32) = [hs[pr].get_setup() for pr in (M.msrsb.MSRSB_F64, M.msrsb.MSRSB_F32)]
+    vprobe = torch.randn(n, dtype=torch.float64, device=dev, generator=torch.Generator(device=dev).manual_seed(11))
+    z64, z32 = [hs[pr].apply(vprobe) for pr in (M.msrsb.MSRSB_F64, M.msrsb.MSRSB_F32)]
+    x64, x32 = [hs[pr].solve(b, rtol=RTOL, maxit=MAXIT)["x"] for pr in (M.msrsb.MSRSB_F64, M.msrsb.MSRSB_F32)]
+    mixed_err = {
+        "P_max_abs": float((P32[0].double() - P64[0]).abs().max()),
+        "Ac_rel": float((Ac32 - Ac64).norm() / Ac64.norm()),
+        "apply_rel": float((z32 - z64).norm() / z64.norm()),
+        "x_rel": float((x32 - x64).norm() / x64.norm()),
+        "what": "mixed-form result against the FP64 form (both GPU; the FP64 form is within the oracle tolerances)",
+    }
+    for hh in hs.values():
+        hh.destroy()
+
     # two-stage apply on its own: L2 flushed before every apply, event-timed
     h = M.msrsb_setup(A, g, M.opts(prec=M.msrsb.MSRSB_F32, **BASIS))
     p_ids = h.get_setup()[0]
@@ -270,6 +288,7 @@ def gpu_arm(args, rank, world):
                  "setup_phase_ms": dict(zip(PHASES, inf64["phase_ms"])), "smooth_kernel_gbs": achieved64,
                  "smooth_kernel_us": sm_ms64 / sm_l64 * 1e3 if sm_l64 else None},
         "speedup_mixed_vs_fp64": t64 / t32,
+        "mixed_error_vs_fp64": mixed_err,
         "roofline": {"kernel": "smooth_kernel<float,8> (restricted smoothing, Alg. 1)", "bound": "hbm",
                      "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm if achieved else None, "traffic": SMOOTH_TRAFFIC_BYTES,
@@ -289,6 +308,11 @@ def gpu_arm(args, rank, world):
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(c)
     return out
+
+
+def _csr(c):
+    import scipy.sparse as sp
+    return sp.csr_matrix((c["data"], c["indices"], c["indptr"]))
 
 
 def _spmv(c, x):
@@ -414,6 +438,61 @@ def profile_run(args):
         print("profile basis: n %d passes %d e_it %.4f" % (c["indptr"].shape[0] - 1, it, e))
 
 
+def ensemble_run(args):
+    """Ensemble throughput (msrsb_solve_ensemble): R seeded 3D Darcy
+    realisations (field and stencil as the main workload; grid edges drawn
+    from --ens-edges, seed 1004; fields seed 40000 + r), 8 right-hand sides
+    b = A xi with xi ~ N(0, 1) each (seed 50000 + r), mixed form, GMRES to
+    1e-8; the whole ensemble timed at concurrency 1 and at --ens-conc.
+    Prints one JSON line."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1912_06934_gb300 as M
+    from synth.darcy import darcy_3d_case
+    edges = [int(e) for e in args.ens_edges.split(",")]
+    rng = np.random.default_rng(1004)
+    sizes = [int(rng.choice(edges)) for _ in range(args.ens_R)]
+    nrhs = 8
+    probs, rows = [], 0
+    for r, e in enumerate(sizes):
+        c = darcy_3d_case(n=e, H=H_BLOCK, seed=40000 + r)
+        A = M.Mat.from_host(c["indptr"], c["indices"], c["data"])
+        g = M.grid(c["dims"], c["H"])
+        rr = np.random.default_rng(50000 + r)
+        Ah = _csr(c)
+        # b = A xi: a raw N(0, 1) b on a sigma = 3 field can sit at FP64's
+        # attainable-accuracy floor (~1e-8), in the FP64 form as well
+        B = torch.as_tensor(np.stack([Ah @ rr.standard_normal(len(c["b"])) for _ in range(nrhs)]), device="cuda")
+        probs.append((A, g, B, torch.zeros_like(B)))
+        rows += len(c["b"])
+    o = M.opts(prec=M.msrsb.MSRSB_F32, **BASIS)
+    out = {}
+    for conc in (1, args.ens_conc):
+        M.msrsb_solve_ensemble(probs, o, RTOL, ENS_MAXIT, conc)  # warm-up
+        ts = []
+        for _ in range(3):
+            for P_ in probs:
+                P_[3].zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = M.msrsb_solve_ensemble(probs, o, RTOL, ENS_MAXIT, conc)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        t = statistics.median(ts)
+        its = [i for r_ in res for i in r_[0]]
+        out[conc] = {"s": t, "solves_per_s": len(probs) * nrhs / t, "mean_iters": float(np.mean(its)),
+                     "max_relres": float(max(x for r_ in res for x in r_[1]))}
+    line = {"metric": "ensemble: MsRSB set-up + 8 GMRES solves per realisation, realisations per second",
+            "value": args.ens_R / out[args.ens_conc]["s"], "unit": "realisations/s", "higher_is_better": True,
+            "n_gpus": 1, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "ensemble of %d 3D Darcy realisations, edges %s (rows %d), 8 rhs b = A xi each, "
+                       "H=8^3" % (args.ens_R, sizes, rows), "concurrency": args.ens_conc},
+            "sequential": out[1], "concurrent": out[args.ens_conc],
+            "speedup_concurrent_vs_sequential": out[1]["s"] / out[args.ens_conc]["s"]}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -424,9 +503,16 @@ def main():
     ap.add_argument("--profile", choices=["solve", "basis"], default=None,
                     help="run a workload for a profiler instead of the benchmark")
     ap.add_argument("--grid", type=int, default=N_GRID, help="grid edge for --profile")
+    ap.add_argument("--ensemble", action="store_true", help="ensemble throughput instead of the benchmark")
+    ap.add_argument("--ens-R", type=int, default=12)
+    ap.add_argument("--ens-edges", default="32,48,64")
+    ap.add_argument("--ens-conc", type=int, default=6)
     args = ap.parse_args()
     if args.profile:
         profile_run(args)
+        return
+    if args.ensemble:
+        ensemble_run(args)
         return
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))

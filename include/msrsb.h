@@ -214,6 +214,36 @@ msrsb_status msrsb_solve_host(const msrsb_mat *A_h, const msrsb_grid *g, const m
                               double *x_h, double rtol, int32_t maxit, int32_t *iters_h, double *relres_h,
                               cudaStream_t stream);
 
+/* Ensembles (the paper solves one problem at a time; this is the Alg. 2
+ * set-up followed by solves with Alg. 4, applied to many independent
+ * problems, e.g. permeability realisations of different grid sizes, each with
+ * several right-hand sides). One problem: its operator (device arrays, as for
+ * msrsb_setup), grid, nrhs right-hand sides b (device, FP64, nrhs*n*bdim,
+ * right-hand side r at offset r*n*bdim) and solutions x (device, same layout;
+ * in: initial guesses, out: solutions), and host arrays iters_h[nrhs],
+ * relres_h[nrhs] for the per-solve results. */
+typedef struct {
+    const msrsb_mat *A;
+    const msrsb_grid *g;
+    const double *b;
+    double *x;
+    int32_t nrhs;
+    int32_t *iters_h;
+    double *relres_h;
+    msrsb_status status; /* out: this problem's status (MSRSB_OK, or its first error) */
+} msrsb_problem;
+
+/* Runs msrsb_setup, nrhs x msrsb_solve and msrsb_destroy for every problem,
+ * `concurrency` problems at a time (1..64), each on a stream of its own from
+ * a pool of host threads; the set-ups and solves of different problems
+ * overlap on the GPU. Every problem's results are those its own
+ * setup/solve/destroy sequence gives (the kernels are deterministic).
+ * Returns MSRSB_OK when every problem succeeded, else the status of the
+ * lowest-numbered failed problem (each problem's own status is in
+ * probs[i].status). Blocks until all problems are done. */
+msrsb_status msrsb_solve_ensemble(int32_t nprob, msrsb_problem *probs, const msrsb_opts *opts, double rtol,
+                                  int32_t maxit, int32_t concurrency);
+
 /* Measurement support (no counterpart in the paper). msrsb_profile(1)
  * resets the counters and brackets every launch of the restricted-smoothing
  * kernel (Alg. 1) with CUDA events on its stream; msrsb_profile(0) resets and

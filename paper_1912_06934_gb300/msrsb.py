@@ -22,7 +22,7 @@ MSRSB_GMRES, MSRSB_PCG, MSRSB_RICHARDSON = 0, 1, 2
 EXPORTS = ["msrsb_partition_size", "msrsb_partition", "msrsb_filter", "msrsb_build_basis", "msrsb_coarse_op",
            "msrsb_setup", "msrsb_apply", "msrsb_solve", "msrsb_get_setup", "msrsb_get_info", "msrsb_destroy",
            "msrsb_solve_host", "msrsb_profile", "msrsb_profile_read", "msrsb_build_basis_noalloc",
-           "msrsb_last_error"]
+           "msrsb_solve_ensemble", "msrsb_last_error"]
 
 
 class MsrsbError(RuntimeError):
@@ -55,6 +55,12 @@ class c_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("bdim", ctypes.c_int32), ("nc", ctypes.c_int32), ("W", ctypes.c_int32),
                 ("basis_iters", ctypes.c_int32), ("basis_e_it", ctypes.c_double),
                 ("n_zero_diag", ctypes.c_int32), ("ncolours", ctypes.c_int32), ("phase_ms", ctypes.c_double * 6)]
+
+
+class c_problem(ctypes.Structure):
+    _fields_ = [("A", ctypes.POINTER(c_mat)), ("g", ctypes.POINTER(c_grid)), ("b", ctypes.c_void_p),
+                ("x", ctypes.c_void_p), ("nrhs", ctypes.c_int32), ("iters_h", ctypes.POINTER(ctypes.c_int32)),
+                ("relres_h", ctypes.POINTER(ctypes.c_double)), ("status", ctypes.c_int)]
 
 
 def lib_path():
@@ -312,3 +318,27 @@ def msrsb_solve_host_ptrs(indptr, indices, data, bdim, g, o, b, x, rtol=1e-8, ma
                                    ctypes.c_double(rtol), ctypes.c_int32(maxit), ctypes.byref(it), ctypes.byref(rr),
                                    _stream(stream)))
     return it.value, rr.value
+
+
+def msrsb_solve_ensemble(problems, o, rtol=1e-8, maxit=200, concurrency=4):
+    """problems: list of (Mat, grid, B, X) with B, X CUDA FP64 tensors of shape
+    (nrhs, n*bdim) (X: initial guesses, overwritten by the solutions). Returns
+    (iters, relres, status) per problem. The calls run on streams of the
+    library's own, so the current stream is synchronised first."""
+    torch.cuda.current_stream().synchronize()
+    keep, arr = [], (c_problem * len(problems))()
+    for i, (A, g, B, X) in enumerate(problems):
+        assert B.dtype == torch.float64 and X.dtype == torch.float64 and B.is_contiguous() and X.is_contiguous()
+        nrhs = B.shape[0]
+        m = A.c()
+        its = (ctypes.c_int32 * max(nrhs, 1))()
+        rr = (ctypes.c_double * max(nrhs, 1))()
+        keep.append((m, g, its, rr, nrhs))
+        arr[i] = c_problem(ctypes.pointer(m), ctypes.pointer(g), B.data_ptr(), X.data_ptr(), nrhs,
+                           ctypes.cast(its, ctypes.POINTER(ctypes.c_int32)),
+                           ctypes.cast(rr, ctypes.POINTER(ctypes.c_double)), 0)
+    st = load().msrsb_solve_ensemble(ctypes.c_int32(len(problems)), arr, ctypes.byref(o), ctypes.c_double(rtol),
+                                     ctypes.c_int32(maxit), ctypes.c_int32(concurrency))
+    out = [(list(k[2])[:k[4]], list(k[3])[:k[4]], arr[i].status) for i, k in enumerate(keep)]
+    _check(st)
+    return out
