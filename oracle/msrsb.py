@@ -422,6 +422,26 @@ class ColouredSmoother:
         return z[self.inv_order]
 
 
+class L1Jacobi:
+    """l1-Jacobi smoother, the first of the three pre/post-smoother choices of
+    the mechanics experiments (Sec. 4, "2 sweeps of l1-Jacobi"). Reading: the
+    pointwise l1 diagonal d_i = sum_j |a_ij| over the scalar row i (for 3x3
+    blocks, the row of the expanded scalar matrix); one sweep is
+    z <- z + D_l1^-1 (r - A z) from z = 0, and solve(r) returns z after
+    `sweeps` sweeps, so M^-1 is a fixed symmetric polynomial in D^-1 A."""
+
+    def __init__(self, A, sweeps=2):
+        self.A = sp.csr_matrix(A)
+        self.d = np.asarray(abs(self.A).sum(axis=1)).ravel()
+        self.sweeps = sweeps
+
+    def solve(self, r):
+        z = np.zeros_like(r)
+        for _ in range(self.sweeps):
+            z = z + (r - self.A @ z) / self.d
+        return z
+
+
 # ----------------------------------------------------------------------------
 # a4: two-stage preconditioner (Alg. 3 and Alg. 4)
 # ----------------------------------------------------------------------------
@@ -431,7 +451,7 @@ class TwoLevel:
     """Alg. 2 set-up pieces bundled for Alg. 3/4: P, R = P^T, A_c, M_c^-1 and
     the optional pre/post smoothers (objects with .solve)."""
 
-    def __init__(self, A, P, pre=None, post=None):
+    def __init__(self, A, P, pre=None, post=None, coarse=True):
         self.A = sp.csr_matrix(A)
         self.P = sp.csr_matrix(P)
         self.R = self.P.T.tocsr()
@@ -439,6 +459,7 @@ class TwoLevel:
         self.lu = coarse_factor(self.Ac)
         self.pre = pre
         self.post = post
+        self.coarse = coarse  # False: the smoothing-only baseline of Sec. 3.2 and Sec. 4
 
     def multiscale(self, v):
         """Alg. 3: v_c = R v; w_c = M_c^-1 v_c; w = P w_c."""
@@ -452,8 +473,8 @@ class TwoLevel:
         z = np.zeros_like(v)
         if self.pre is not None:
             z = z + self.pre.solve(v - self.A @ z)
-        w = self.multiscale(v - self.A @ z)
-        z = z + w
+        if self.coarse:
+            z = z + self.multiscale(v - self.A @ z)
         if self.post is not None:
             z = z + self.post.solve(v - self.A @ z)
         return z
@@ -522,6 +543,27 @@ def gmres_right(A, b, M, x0=None, rtol=1e-8, maxit=200, restart=200):
         x = x + Z[:j_done].T @ y
 
 
+def richardson(A, b, M, x0=None, rtol=1e-8, maxit=200):
+    """Preconditioned Richardson iteration, the stand-alone use of the
+    two-stage operator in Sec. 3.2: x <- x + M^-1 (b - A x), stopping when the
+    true relative residual is <= rtol. Returns (x, iterations, relres,
+    history)."""
+    A = sp.csr_matrix(A)
+    x = np.zeros(len(b)) if x0 is None else np.array(x0, dtype=np.float64)
+    bnorm = np.linalg.norm(b)
+    hist = []
+    its = 0
+    while True:
+        r = b - A @ x
+        rr = np.linalg.norm(r) / bnorm
+        if its > 0:
+            hist.append(rr)
+        if rr <= rtol or its >= maxit:
+            return x, its, rr, hist
+        x = x + M(r)
+        its += 1
+
+
 def pcg(A, b, M, x0=None, rtol=1e-8, maxit=500):
     """Preconditioned conjugate gradients (Saad, Alg. 9.1) with a symmetric
     preconditioner M; stops on the recursively updated residual <= rtol ||b||
@@ -564,7 +606,7 @@ def pcg(A, b, M, x0=None, rtol=1e-8, maxit=500):
 
 
 def setup_scalar(A, dims, H, centering=0, omega=2.0 / 3.0, tol=1e-3, n_it=10, max_iter=100,
-                 smoother="ilu0"):
+                 smoother="ilu0", coarse=True):
     """Alg. 2 for a scalar operator (flow): partition, filter, Alg. 1, Galerkin
     coarse operator, coarse LU and a colour-ordered ILU(0) post-smoother."""
     A = sp.csr_matrix(A)
@@ -575,14 +617,17 @@ def setup_scalar(A, dims, H, centering=0, omega=2.0 / 3.0, tol=1e-3, n_it=10, ma
     vals, its, e_it, hist = enhanced_msrsb(Ahat, part["pat"], P0, part["skel"], omega, tol, n_it, max_iter)
     P = as_matrix(vals, part["pat"])
     post = ColouredSmoother(A, parity_colours(dims), "ilu0") if smoother == "ilu0" else None
-    tl = TwoLevel(A, P, pre=None, post=post)
+    tl = TwoLevel(A, P, pre=None, post=post, coarse=coarse)
     return dict(part=part, Ahat=Ahat, vals=vals, iters=its, e_it=e_it, hist=hist, P=P, tl=tl)
 
 
-def setup_elastic(indptr, indices, blocks, dims, H, omega=2.0 / 3.0, tol=1e-3, n_it=10, max_iter=100):
+def setup_elastic(indptr, indices, blocks, dims, H, omega=2.0 / 3.0, tol=1e-3, n_it=10, max_iter=100,
+                  smoother="gs", sweeps=2, coarse=True):
     """Alg. 2 for 3x3-block elasticity: SDC blocks filtered per component,
     three scalar bases on one shared pattern, block-diagonal P, Galerkin with
-    the full operator, forward/backward block Gauss-Seidel pre/post smoothers."""
+    the full operator, and a symmetric pair of pre/post smoothers: forward /
+    backward block Gauss-Seidel ("gs"), or `sweeps` l1-Jacobi sweeps each
+    ("l1jac"). coarse=False gives the smoothing-only baseline."""
     part = partition(dims, H, 1)
     A = bsr_to_csr(indptr, indices, blocks)
     comps = sdc_blocks(indptr, indices, blocks)
@@ -593,8 +638,11 @@ def setup_elastic(indptr, indices, blocks, dims, H, omega=2.0 / 3.0, tol=1e-3, n
         out.append(enhanced_msrsb(Ahat, part["pat"], P0, part["skel"], omega, tol, n_it, max_iter))
     Ps = [as_matrix(o[0], part["pat"]) for o in out]
     P = block_prolongation(Ps)
-    col = parity_colours(dims)
-    pre = ColouredSmoother(A, col, "gs_fwd", bdim=3)
-    post = ColouredSmoother(A, col, "gs_bwd", bdim=3)
-    tl = TwoLevel(A, P, pre=pre, post=post)
+    if smoother == "l1jac":
+        pre = post = L1Jacobi(A, sweeps)
+    else:
+        col = parity_colours(dims)
+        pre = ColouredSmoother(A, col, "gs_fwd", bdim=3)
+        post = ColouredSmoother(A, col, "gs_bwd", bdim=3)
+    tl = TwoLevel(A, P, pre=pre, post=post, coarse=coarse)
     return dict(part=part, comps=out, P=P, tl=tl, A=A)

@@ -6,10 +6,11 @@ import os
 import numpy as np
 import pytest
 import scipy.sparse as sp
+import scipy.sparse.linalg as sla
 
 from oracle import msrsb as O
 from synth.darcy import tpfa, mpfa_o, darcy_2d_case, darcy_3d_case, anisotropic_tensors
-from synth.elastic import q1_elasticity
+from synth.elastic import q1_elasticity, elastic_3d_case
 from synth.fields import rotation_2d
 
 
@@ -389,3 +390,59 @@ def test_pcg_matches_direct_solve():
     xs = np.linalg.solve(A.toarray(), e["b"])
     assert rr <= 1e-10
     assert np.linalg.norm(x - xs) <= 1e-7 * np.linalg.norm(xs)
+
+
+# ---------------- N4: l1-Jacobi smoother, smoothing-only baseline, Richardson ----------------
+
+def test_l1_jacobi_exact_on_a_diagonal_matrix():
+    d = np.array([2.0, 5.0, 0.5, 3.0])
+    A = sp.diags(d).tocsr()
+    r = np.array([1.0, -2.0, 3.0, 0.25])
+    for sweeps in (1, 2, 3):
+        assert np.allclose(O.L1Jacobi(A, sweeps).solve(r), r / d, rtol=0, atol=1e-15)
+
+
+def test_l1_jacobi_two_sweeps_hand_values():
+    # tridiag(-1, 2, -1), n = 5: d = (3, 4, 4, 4, 3); r = e_2 (0-based). Sweep 1:
+    # z = (0, 0, 1/4, 0, 0); r - A z = (0, 1/4, 1/2, 1/4, 0); sweep 2 adds that / d.
+    A = sp.diags([-np.ones(4), 2 * np.ones(5), -np.ones(4)], [-1, 0, 1]).tocsr()
+    r = np.zeros(5)
+    r[2] = 1.0
+    z = O.L1Jacobi(A, 2).solve(r)
+    assert np.allclose(z, [0.0, 1 / 16, 3 / 8, 1 / 16, 0.0], rtol=0, atol=1e-15)
+
+
+def test_l1_jacobi_two_stage_operator_is_symmetric():
+    c = elastic_3d_case(ne=4, H=2)
+    st = O.setup_elastic(c["indptr"], c["indices"], c["data"], c["dims"], c["H"], tol=0.0, max_iter=10,
+                         smoother="l1jac", sweeps=2)
+    rng = np.random.default_rng(2)
+    n = st["A"].shape[0]
+    v, w = rng.standard_normal(n), rng.standard_normal(n)
+    a, b = v @ st["tl"].apply(w), w @ st["tl"].apply(v)
+    assert abs(a - b) <= 1e-12 * (abs(a) + abs(b))
+    # and PCG with it converges to a dense solve
+    x, its, rr, _ = O.pcg(st["A"], c["b"], st["tl"].apply, rtol=1e-10, maxit=300)
+    xd = np.linalg.solve(st["A"].toarray(), c["b"])
+    assert rr <= 1e-10 and np.linalg.norm(x - xd) <= 1e-8 * np.linalg.norm(xd)
+
+
+def test_richardson_exact_preconditioner_one_step():
+    A = sp.diags([-np.ones(9), 3 * np.ones(10), -np.ones(9)], [-1, 0, 1]).tocsc()
+    b = np.arange(10.0)
+    solve = sla.splu(A).solve
+    x, its, rr, _ = O.richardson(A, b, solve, rtol=1e-12, maxit=5)
+    assert its == 1 and rr <= 1e-14
+
+
+def test_richardson_multiscale_vs_smoothing_only():
+    # Sec. 3.2: MsRSB + ILU(0) as a stand-alone Richardson iteration converges,
+    # ILU(0) alone does not within 150 iterations
+    c = darcy_2d_case()
+    A = sp.csr_matrix((c["data"], c["indices"], c["indptr"]))
+    ms = O.setup_scalar(A, c["dims"], c["H"], tol=1e-3, max_iter=100)
+    so = O.setup_scalar(A, c["dims"], c["H"], tol=1e-3, max_iter=100, coarse=False)
+    _, its_ms, rr_ms, _ = O.richardson(A, c["b"], ms["tl"].apply, rtol=1e-8, maxit=150)
+    _, its_so, rr_so, _ = O.richardson(A, c["b"], so["tl"].apply, rtol=1e-8, maxit=150)
+    assert rr_ms <= 1e-8 and its_ms < 150
+    assert rr_so > 1e-8
