@@ -54,7 +54,7 @@ typedef enum {
 } msrsb_status;
 
 typedef enum { MSRSB_F64 = 0, MSRSB_F32 = 1 } msrsb_prec;
-typedef enum { MSRSB_SMOOTH_NONE = 0, MSRSB_SMOOTH_ILU0 = 1, MSRSB_SMOOTH_GS = 2 } msrsb_smoother;
+typedef enum { MSRSB_SMOOTH_NONE = 0, MSRSB_SMOOTH_ILU0 = 1, MSRSB_SMOOTH_GS = 2, MSRSB_SMOOTH_L1JAC = 3 } msrsb_smoother;
 typedef enum { MSRSB_GMRES = 0, MSRSB_PCG = 1, MSRSB_RICHARDSON = 2 } msrsb_krylov;
 
 /* Sparse FP64 fine operator, device arrays (rowptr[nrows+1], colidx[nnz],
@@ -85,13 +85,20 @@ typedef struct {
     msrsb_basis_opts basis;
     int32_t smoother;  /* msrsb_smoother: post-smoother for GMRES/Richardson;
                           MSRSB_SMOOTH_GS = forward pre + backward post
-                          (symmetric, for PCG) */
-    int32_t pre, post; /* enable the pre / post stage of Alg. 4 */
+                          (symmetric, for PCG); MSRSB_SMOOTH_L1JAC = l1-Jacobi
+                          sweeps z += D_l1^-1 (v - A z), d_i = sum_j |a_ij| over
+                          the scalar row (Sec. 4: "2 sweeps of l1-Jacobi"),
+                          scalar or 3x3 block operators */
+    int32_t pre, post; /* enable the pre / post stage of Alg. 4; for
+                          MSRSB_SMOOTH_L1JAC the number of sweeps of each */
     int32_t krylov;    /* msrsb_krylov */
     int32_t restart;   /* GMRES restart length (<= 512) */
     int32_t prec;      /* msrsb_prec: F64 = all FP64; F32 = basis, P and smoother
                           in FP32 with FP32 accumulation, Krylov vectors and
                           the coarse operator in FP64 */
+    int32_t no_coarse; /* 1: leave out the multiscale stage (Alg. 3) of the
+                          apply, the smoothing-only baseline of Sec. 3.2 and
+                          Sec. 4; 0 (default): the two-stage operator */
 } msrsb_opts;
 
 typedef struct msrsb_handle msrsb_handle;

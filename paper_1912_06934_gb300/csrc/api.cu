@@ -99,6 +99,10 @@ msrsb_status ilu0_factor(const msrsb_mat *A, const uint8_t *colour, int ncol, co
                          const int32_t *cptr_h, int32_t *dpos, TF *lu, cudaStream_t s);
 template <typename T>
 msrsb_status ilu_build_ell(msrsb_handle *h, const T *lu, cudaStream_t s);
+template <typename T>
+msrsb_status l1_diag(const msrsb_mat *A, T *dinv, cudaStream_t s);
+template <typename T, typename TZ, typename TR>
+msrsb_status l1_update(long N, const T *dinv, const TR *r, TZ *z, int from_zero, cudaStream_t s);
 
 template <typename T, typename TZ>
 msrsb_status ilu0_apply(const msrsb_handle *h, T *ry, TZ *z, cudaStream_t s);
@@ -181,6 +185,11 @@ static msrsb_status setup_smoother(msrsb_handle *h, cudaStream_t s) {
         MSRSB_TRY(dalloc(&dinv, (size_t)n * 9, s));
         h->dinv = dinv;
         MSRSB_TRY(block_diag_inverse<T>(&A, dinv, s));
+    } else if (h->opts.smoother == MSRSB_SMOOTH_L1JAC) {
+        T *dinv = nullptr;  // reciprocal l1 row norms, [n*bdim]
+        MSRSB_TRY(dalloc(&dinv, (size_t)n * bd, s));
+        h->dinv = dinv;
+        MSRSB_TRY(l1_diag<T>(&A, dinv, s));
     }
     MSRSB_CUDA(cudaStreamSynchronize(s));
     return MSRSB_OK;
@@ -354,29 +363,48 @@ static msrsb_status apply_t(msrsb_handle *h, const TVI *v, TZ *z, cudaStream_t s
     T *r = (T *)h->r_t, *y = (T *)h->y_t;
     const T *aval_t = h->opts.prec == MSRSB_F32 ? (const T *)h->a_lo : (const T *)A.val;
     const bool gs = h->opts.smoother == MSRSB_SMOOTH_GS, ilu = h->opts.smoother == MSRSB_SMOOTH_ILU0;
-    const bool pre = h->opts.pre && (gs || ilu), post = h->opts.post && (gs || ilu);
+    const bool l1 = h->opts.smoother == MSRSB_SMOOTH_L1JAC;
+    const bool pre = h->opts.pre && (gs || ilu || l1), post = h->opts.post && (gs || ilu || l1);
+    const bool coarse = !h->opts.no_coarse;
+    const T *dinv = (const T *)h->dinv;
     if (pre) {
         // z = M_pre^-1 v
         if (gs) {
             MSRSB_TRY((copy_cast<TVI, T>(N, v, r, s)));
-            MSRSB_TRY((gs_apply<T, T, TZ>(h, aval_t, (const T *)h->dinv, 1, r, y, z, 1, s)));
+            MSRSB_TRY((gs_apply<T, T, TZ>(h, aval_t, dinv, 1, r, y, z, 1, s)));
+        } else if (l1) {
+            MSRSB_TRY((l1_update<T, TZ, TVI>(N, dinv, v, z, 1, s)));  // first sweep from z = 0
+            for (int k = 1; k < h->opts.pre; ++k) {
+                MSRSB_TRY((resid_t<T, TZ, TVI>(h, aval_t, z, v, r, nullptr, s)));
+                MSRSB_TRY((l1_update<T, TZ, T>(N, dinv, r, z, 0, s)));
+            }
         } else {
             MSRSB_TRY((permute_cast<TVI, T>(N, v, h->pos_of, r, s)));
             MSRSB_CUDA(cudaMemsetAsync(z, 0, N * sizeof(TZ), s));
             MSRSB_TRY((ilu0_apply<T, TZ>(h, r, z, s)));
         }
-        // coarse correction of the residual v - A z
-        MSRSB_TRY((resid_t<T, TZ, TVI>(h, aval_t, z, v, r, nullptr, s)));
-        MSRSB_TRY((restrict_op<T, T>(h, (const T *)h->pt_val, r, h->vc, s)));
-    } else {
-        MSRSB_TRY((restrict_op<T, TVI>(h, (const T *)h->pt_val, v, h->vc, s)));
     }
-    MSRSB_TRY(gemv(h->nC, h->Ainv, h->vc, h->wc, s));
-    MSRSB_TRY((prolong_op<T, TZ>(h, P, h->wc, z, pre ? 1 : 0, s)));
+    if (coarse) {
+        if (pre) {  // coarse correction of the residual v - A z
+            MSRSB_TRY((resid_t<T, TZ, TVI>(h, aval_t, z, v, r, nullptr, s)));
+            MSRSB_TRY((restrict_op<T, T>(h, (const T *)h->pt_val, r, h->vc, s)));
+        } else {
+            MSRSB_TRY((restrict_op<T, TVI>(h, (const T *)h->pt_val, v, h->vc, s)));
+        }
+        MSRSB_TRY(gemv(h->nC, h->Ainv, h->vc, h->wc, s));
+        MSRSB_TRY((prolong_op<T, TZ>(h, P, h->wc, z, pre ? 1 : 0, s)));
+    } else if (!pre) {
+        MSRSB_CUDA(cudaMemsetAsync(z, 0, N * sizeof(TZ), s));  // smoothing only, from z = 0
+    }
     if (post) {
         if (gs) {
             MSRSB_TRY((resid_t<T, TZ, TVI>(h, aval_t, z, v, r, nullptr, s)));
-            MSRSB_TRY((gs_apply<T, T, TZ>(h, aval_t, (const T *)h->dinv, 0, r, y, z, 0, s)));
+            MSRSB_TRY((gs_apply<T, T, TZ>(h, aval_t, dinv, 0, r, y, z, 0, s)));
+        } else if (l1) {
+            for (int k = 0; k < h->opts.post; ++k) {
+                MSRSB_TRY((resid_t<T, TZ, TVI>(h, aval_t, z, v, r, nullptr, s)));
+                MSRSB_TRY((l1_update<T, TZ, T>(N, dinv, r, z, 0, s)));
+            }
         } else {
             // residual written straight into colour order for the sweeps
             MSRSB_TRY((resid_t<T, TZ, TVI>(h, aval_t, z, v, r, h->pos_of, s)));
@@ -876,6 +904,11 @@ extern "C" msrsb_status msrsb_setup(const msrsb_mat *A, const msrsb_grid *g, con
     if ((long)nc * A->bdim > 8192) return fail(MSRSB_ESHAPE, "coarse system too large (nc*bdim = %ld > 8192)", (long)nc * A->bdim);
     if (opts->prec != MSRSB_F64 && opts->prec != MSRSB_F32) return fail(MSRSB_EINVAL, "bad precision");
     if (opts->basis.n_it < 1 || opts->basis.max_iter < 0) return fail(MSRSB_EINVAL, "bad basis options");
+    if (opts->smoother < MSRSB_SMOOTH_NONE || opts->smoother > MSRSB_SMOOTH_L1JAC)
+        return fail(MSRSB_EINVAL, "unknown smoother %d", opts->smoother);
+    if (opts->pre < 0 || opts->post < 0 || opts->pre > 64 || opts->post > 64)
+        return fail(MSRSB_EINVAL, "pre/post must be 0..64 (got %d, %d)", opts->pre, opts->post);
+    if (opts->no_coarse != 0 && opts->no_coarse != 1) return fail(MSRSB_EINVAL, "no_coarse must be 0 or 1");
     keep_pool_memory();
     msrsb_handle *h = new msrsb_handle();
     h->A = *A;

@@ -538,4 +538,57 @@ template msrsb_status gs_apply<float, float, double>(const msrsb_handle *, const
 template msrsb_status gs_apply<float, float, float>(const msrsb_handle *, const float *, const float *, int,
                                                     const float *, float *, float *, int, cudaStream_t);
 
+// ---- l1-Jacobi (Sec. 4: "2 sweeps of l1-Jacobi") ----------------------------------
+
+// dinv[i*bd + l] = 1 / sum_j |a_(i*bd+l),j| over the scalar row (all blocks of
+// block row i, row l of each); 0 for an empty row
+template <typename T>
+__global__ void l1_diag_kernel(int n, int bd, const int32_t *__restrict__ rowptr, const double *__restrict__ val,
+                               T *__restrict__ dinv) {
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t >= (long)n * bd) return;
+    const int i = (int)(t / bd), l = (int)(t % bd);
+    double s = 0.0;
+    for (int e = rowptr[i]; e < rowptr[i + 1]; ++e)
+        for (int m = 0; m < bd; ++m) s += fabs(val[((long)e * bd + l) * bd + m]);
+    dinv[t] = s > 0.0 ? T(1.0 / s) : T(0);
+}
+
+template <typename T>
+msrsb_status l1_diag(const msrsb_mat *A, T *dinv, cudaStream_t s) {
+    const long N = (long)A->nrows * A->bdim;
+    l1_diag_kernel<T><<<ceil_div(N, 256), 256, 0, s>>>(A->nrows, A->bdim, A->rowptr, (const double *)A->val, dinv);
+    MSRSB_LAUNCHED("l1_diag_kernel");
+    return MSRSB_OK;
+}
+template msrsb_status l1_diag<double>(const msrsb_mat *, double *, cudaStream_t);
+template msrsb_status l1_diag<float>(const msrsb_mat *, float *, cudaStream_t);
+
+// one l1-Jacobi update, z += dinv * r (r the residual v - A z in the smoother
+// precision), or from z = 0: z = dinv * v
+template <typename T, typename TZ, typename TR>
+__global__ void l1_update_kernel(long N, const T *__restrict__ dinv, const TR *__restrict__ r, TZ *__restrict__ z,
+                                 int from_zero) {
+    pdl_prologue();
+    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const T u = dinv[i] * T(r[i]);
+    z[i] = from_zero ? TZ(u) : TZ(z[i] + TZ(u));
+}
+
+template <typename T, typename TZ, typename TR>
+msrsb_status l1_update(long N, const T *dinv, const TR *r, TZ *z, int from_zero, cudaStream_t s) {
+    MSRSB_PDL((l1_update_kernel<T, TZ, TR>), ceil_div(N, 256), 256, 0, s, N, dinv, r, z, from_zero);
+    return MSRSB_OK;
+}
+template msrsb_status l1_update<double, double, double>(long, const double *, const double *, double *, int,
+                                                        cudaStream_t);
+template msrsb_status l1_update<float, double, float>(long, const float *, const float *, double *, int, cudaStream_t);
+template msrsb_status l1_update<float, double, double>(long, const float *, const double *, double *, int,
+                                                       cudaStream_t);
+template msrsb_status l1_update<float, float, float>(long, const float *, const float *, float *, int, cudaStream_t);
+template msrsb_status l1_update<double, double, float>(long, const double *, const float *, double *, int,
+                                                       cudaStream_t);
+template msrsb_status l1_update<float, float, double>(long, const float *, const double *, float *, int, cudaStream_t);
+
 }  // namespace msrsb

@@ -1,0 +1,115 @@
+"""Second-stage variants of Sec. 3.2 and Sec. 4 against the oracle: the
+l1-Jacobi smoother (pre and post sweeps), the smoothing-only baseline (no
+multiscale stage), and the stand-alone Richardson iteration.
+
+Tolerances as in test_gpu_parity: one application of the preconditioner within
+1e-10 relative (FP64 form); Krylov/Richardson solves to relative residual 1e-8
+(recomputed here) with iteration counts within +-1 of the oracle's."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+torch = pytest.importorskip("torch")
+
+from oracle import msrsb as O  # noqa: E402
+from synth.darcy import darcy_2d_case, darcy_3d_case  # noqa: E402
+from synth.elastic import elastic_3d_case  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1912_06934_gb300 as M
+    return M
+
+
+def _elastic(M, c, **kw):
+    A = M.Mat.from_host(c["indptr"], c["indices"], c["data"], bdim=3)
+    g = M.grid(c["dims"], c["H"], centering=1, ncomp=3)
+    return M.msrsb_setup(A, g, M.opts(**kw))
+
+
+@pytest.mark.parametrize("coarse", [1, 0])
+def test_l1_jacobi_apply_matches_oracle_elastic(M, coarse):
+    B = M.msrsb
+    c = elastic_3d_case(ne=8, H=4)
+    h = _elastic(M, c, smoother=B.MSRSB_SMOOTH_L1JAC, pre=2, post=2, krylov=B.MSRSB_PCG, tol=0.0, max_iter=20,
+                 no_coarse=1 - coarse)
+    ref = O.setup_elastic(c["indptr"], c["indices"], c["data"], c["dims"], c["H"], tol=0.0, max_iter=20,
+                          smoother="l1jac", sweeps=2, coarse=bool(coarse))
+    v = np.random.default_rng(5).standard_normal(ref["A"].shape[0])
+    z = h.apply(torch.as_tensor(v, device="cuda")).cpu().numpy()
+    zr = ref["tl"].apply(v)
+    assert np.linalg.norm(z - zr) <= 1e-10 * np.linalg.norm(zr)
+    h.destroy()
+
+
+def test_l1_jacobi_apply_matches_oracle_scalar(M):
+    B = M.msrsb
+    c = darcy_3d_case(n=16)
+    A = M.Mat.from_host(c["indptr"], c["indices"], c["data"])
+    h = M.msrsb_setup(A, M.grid(c["dims"], c["H"]),
+                      M.opts(smoother=B.MSRSB_SMOOTH_L1JAC, pre=1, post=3, tol=0.0, max_iter=20))
+    Ah = sp.csr_matrix((c["data"], c["indices"], c["indptr"]))
+    ref = O.setup_scalar(Ah, c["dims"], c["H"], tol=0.0, max_iter=20, smoother=None)
+    tl = O.TwoLevel(Ah, ref["P"], pre=O.L1Jacobi(Ah, 1), post=O.L1Jacobi(Ah, 3))
+    v = np.random.default_rng(6).standard_normal(Ah.shape[0])
+    z = h.apply(torch.as_tensor(v, device="cuda")).cpu().numpy()
+    zr = tl.apply(v)
+    assert np.linalg.norm(z - zr) <= 1e-10 * np.linalg.norm(zr)
+    h.destroy()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_pcg_l1_jacobi_elastic(M, prec):
+    B = M.msrsb
+    c = elastic_3d_case(ne=12, H=6)
+    h = _elastic(M, c, smoother=B.MSRSB_SMOOTH_L1JAC, pre=2, post=2, krylov=B.MSRSB_PCG, tol=1e-3, max_iter=100,
+                 prec=prec)
+    ref = O.setup_elastic(c["indptr"], c["indices"], c["data"], c["dims"], c["H"], tol=1e-3, max_iter=100,
+                          smoother="l1jac", sweeps=2)
+    _, its_ref, _, _ = O.pcg(ref["A"], c["b"], ref["tl"].apply, rtol=1e-8, maxit=500)
+    r = h.solve(torch.as_tensor(c["b"], device="cuda"), rtol=1e-8, maxit=500)
+    x = r["x"].cpu().numpy()
+    assert np.linalg.norm(c["b"] - ref["A"] @ x) <= 1e-8 * np.linalg.norm(c["b"])
+    if prec == 0:
+        assert abs(r["iters"] - its_ref) <= 1
+    else:
+        assert abs(r["iters"] - its_ref) <= 2
+    h.destroy()
+
+
+def test_richardson_matches_oracle_and_beats_smoothing_only(M):
+    B = M.msrsb
+    c = darcy_2d_case()
+    A = M.Mat.from_host(c["indptr"], c["indices"], c["data"])
+    g = M.grid(c["dims"], c["H"])
+    Ah = sp.csr_matrix((c["data"], c["indices"], c["indptr"]))
+    ref = O.setup_scalar(Ah, c["dims"], c["H"], tol=1e-3, max_iter=100)
+    _, its_ref, _, _ = O.richardson(Ah, c["b"], ref["tl"].apply, rtol=1e-8, maxit=300)
+    h = M.msrsb_setup(A, g, M.opts(krylov=B.MSRSB_RICHARDSON, tol=1e-3, max_iter=100))
+    r = h.solve(torch.as_tensor(c["b"], device="cuda"), rtol=1e-8, maxit=300)
+    x = r["x"].cpu().numpy()
+    assert np.linalg.norm(c["b"] - Ah @ x) <= 1e-8 * np.linalg.norm(c["b"])
+    assert abs(r["iters"] - its_ref) <= 1
+    h.destroy()
+    # smoothing only (ILU(0) alone): no convergence within 150 iterations
+    h = M.msrsb_setup(A, g, M.opts(krylov=B.MSRSB_RICHARDSON, tol=1e-3, max_iter=100, no_coarse=1))
+    r = h.solve(torch.as_tensor(c["b"], device="cuda"), rtol=1e-8, maxit=150, raise_on_noconv=False)
+    assert r["iters"] == 150 and r["relres"] > 1e-8
+    h.destroy()
+
+
+def test_bad_smoother_options_are_rejected(M):
+    c = darcy_2d_case(n=16, H=4)
+    A = M.Mat.from_host(c["indptr"], c["indices"], c["data"])
+    g = M.grid(c["dims"], c["H"])
+    for kw in (dict(smoother=7), dict(pre=-1), dict(post=65), dict(no_coarse=2)):
+        with pytest.raises(M.MsrsbError) as ei:
+            M.msrsb_setup(A, g, M.opts(**kw))
+        assert ei.value.status == M.msrsb.MSRSB_EINVAL
