@@ -21,6 +21,7 @@ import subprocess
 import numpy as np
 import scipy.linalg as sla
 import scipy.sparse as sp
+import scipy.sparse.linalg as spla
 
 # ----------------------------------------------------------------------------
 # a0: primal partition, coarse nodes, support regions (Sec. 2.1, Fig. 1; the
@@ -646,3 +647,55 @@ def setup_elastic(indptr, indices, blocks, dims, H, omega=2.0 / 3.0, tol=1e-3, n
         post = ColouredSmoother(A, col, "gs_bwd", bdim=3)
     tl = TwoLevel(A, P, pre=pre, post=post, coarse=coarse)
     return dict(part=part, comps=out, P=P, tl=tl, A=A)
+
+
+# ----------------------------------------------------------------------------
+# N3: adjoint gradient of a pressure objective with respect to log-permeability
+# ----------------------------------------------------------------------------
+
+
+def tpfa_objective_gradient(dims, logk, obs, p_obs):
+    """J(theta) = sum_o (p[obs_o] - p_obs_o)^2 for the two-point flux system of
+    isotropic cells k = exp(theta) (unit cells, face transmissibility
+    T = 2 k_L k_R / (k_L + k_R), p = 1 on the x = 0 face and p = 0 on the
+    x = nx face through half-cell transmissibility 2 k, no flow elsewhere;
+    cells x fastest), and dJ/dtheta by the adjoint method: A p = b,
+    A^T lambda = dJ/dp, dJ/dtheta = lambda^T (db/dtheta - dA/dtheta p), with
+    dT/dtheta_L = 2 k_L k_R^2 / (k_L + k_R)^2 (and symmetrically for R).
+    Direct sparse solves in FP64. Returns (J, grad, p)."""
+    dims = tuple(dims)
+    d = len(dims)
+    n = int(np.prod(dims))
+    k = np.exp(np.asarray(logk, dtype=np.float64))
+    idx = np.arange(n).reshape(dims[::-1])
+    fl, fr = [], []
+    for a in range(d):
+        ax = d - 1 - a
+        fl.append(np.take(idx, np.arange(dims[a] - 1), axis=ax).ravel())
+        fr.append(np.take(idx, np.arange(1, dims[a]), axis=ax).ravel())
+    fl, fr = np.concatenate(fl), np.concatenate(fr)
+    kl, kr = k[fl], k[fr]
+    T = 2.0 * kl * kr / (kl + kr)
+    west = np.take(idx, [0], axis=d - 1).ravel()
+    east = np.take(idx, [dims[0] - 1], axis=d - 1).ravel()
+    rows = np.concatenate([fl, fr, fl, fr, west, east])
+    cols = np.concatenate([fl, fr, fr, fl, west, east])
+    data = np.concatenate([T, T, -T, -T, 2.0 * k[west], 2.0 * k[east]])
+    A = sp.csr_matrix((data, (rows, cols)), shape=(n, n))
+    b = np.zeros(n)
+    np.add.at(b, west, 2.0 * k[west])
+    p = spla.spsolve(A.tocsc(), b)
+    r = p[obs] - p_obs
+    J = float(r @ r)
+    gp = np.zeros(n)
+    np.add.at(gp, obs, 2.0 * r)
+    lam = spla.spsolve(A.T.tocsc(), gp)
+    dT_l = 2.0 * kl * kr * kr / (kl + kr) ** 2
+    dT_r = 2.0 * kr * kl * kl / (kl + kr) ** 2
+    flux = (lam[fl] - lam[fr]) * (p[fl] - p[fr])
+    grad = np.zeros(n)
+    np.add.at(grad, fl, -dT_l * flux)
+    np.add.at(grad, fr, -dT_r * flux)
+    np.add.at(grad, west, 2.0 * k[west] * lam[west] * (1.0 - p[west]))
+    np.add.at(grad, east, -2.0 * k[east] * lam[east] * p[east])
+    return J, grad, p

@@ -446,3 +446,35 @@ def test_richardson_multiscale_vs_smoothing_only():
     _, its_so, rr_so, _ = O.richardson(A, c["b"], so["tl"].apply, rtol=1e-8, maxit=150)
     assert rr_ms <= 1e-8 and its_ms < 150
     assert rr_so > 1e-8
+
+
+# ---------------- N3: adjoint gradient of a TPFA objective ----------------
+
+def test_adjoint_gradient_matches_brute_force_differences():
+    # every cell of a 4 x 3 x 2 grid, central differences of J itself
+    dims = (4, 3, 2)
+    n = 24
+    rng = np.random.default_rng(4)
+    logk = rng.standard_normal(n)
+    obs = np.array([1, 7, 13, 22])
+    p_obs = rng.uniform(0.2, 0.8, size=4)
+    J, g, _ = O.tpfa_objective_gradient(dims, logk, obs, p_obs)
+    eps = 1e-5
+    fd = np.empty(n)
+    for c in range(n):
+        e = np.zeros(n)
+        e[c] = eps
+        fd[c] = (O.tpfa_objective_gradient(dims, logk + e, obs, p_obs)[0]
+                 - O.tpfa_objective_gradient(dims, logk - e, obs, p_obs)[0]) / (2 * eps)
+    assert np.abs(g - fd).max() <= 1e-7 * np.abs(fd).max()
+
+
+def test_adjoint_gradient_zero_at_the_observed_field():
+    # p_obs equal to the model's own pressures: J = 0 and dJ/dtheta = 0
+    dims = (5, 4)
+    rng = np.random.default_rng(5)
+    logk = rng.standard_normal(20)
+    obs = np.array([2, 9, 17])
+    _, _, p = O.tpfa_objective_gradient(dims, logk, obs, np.zeros(3))
+    J, g, _ = O.tpfa_objective_gradient(dims, logk, obs, p[obs])
+    assert J <= 1e-28 and np.abs(g).max() <= 1e-14
