@@ -251,6 +251,24 @@ typedef struct {
 msrsb_status msrsb_solve_ensemble(int32_t nprob, msrsb_problem *probs, const msrsb_opts *opts, double rtol,
                                   int32_t maxit, int32_t concurrency);
 
+/* Adjoint support (the paper has no adjoint; an objective J(x) of the
+ * solution of A x = b has dJ/db = lambda and dJ/dA_ij = -lambda_i x_j with
+ * A^T lambda = dJ/dx).
+ * msrsb_transpose_values: for a structurally symmetric A (columns ascending
+ * in every row), writes the values of A^T in A's own pattern into val_t
+ * (device, same length as A->val, must not alias it): val_t at entry (i, j)
+ * is A(j, i), 3x3 blocks transposed. A's rowptr/colidx with val_t form A^T,
+ * on which msrsb_setup builds the MsRSB preconditioner of the adjoint system.
+ * Returns MSRSB_ESHAPE when an entry has no mirror entry. Synchronises the
+ * stream. */
+msrsb_status msrsb_transpose_values(const msrsb_mat *A, double *val_t, cudaStream_t stream);
+
+/* grad (device, same layout as A->val) = alpha * lambda x^T restricted to A's
+ * pattern: entry (i, j) gets alpha * lam[i] * x[j] (blocks: row l of block
+ * row i, column m of block column j). With alpha = -1 this is dJ/dA. */
+msrsb_status msrsb_pattern_outer(const msrsb_mat *A, double alpha, const double *lam, const double *x, double *grad,
+                                 cudaStream_t stream);
+
 /* Measurement support (no counterpart in the paper). msrsb_profile(1)
  * resets the counters and brackets every launch of the restricted-smoothing
  * kernel (Alg. 1) with CUDA events on its stream; msrsb_profile(0) resets and

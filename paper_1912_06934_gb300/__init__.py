@@ -6,4 +6,5 @@ from .msrsb import (Mat, Handle, MsrsbError, grid, opts, basis_opts, load,  # no
                     msrsb_partition_size, msrsb_partition, msrsb_filter, msrsb_build_basis, msrsb_coarse_op,
                     msrsb_setup, msrsb_apply, msrsb_solve, msrsb_get_setup, msrsb_get_info, msrsb_destroy,
                     msrsb_solve_host, msrsb_profile, msrsb_profile_read,
-                    msrsb_build_basis_noalloc, msrsb_solve_ensemble)
+                    msrsb_build_basis_noalloc, msrsb_solve_ensemble, msrsb_transpose_values,
+                    msrsb_pattern_outer)

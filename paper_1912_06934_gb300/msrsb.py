@@ -22,7 +22,7 @@ MSRSB_GMRES, MSRSB_PCG, MSRSB_RICHARDSON = 0, 1, 2
 EXPORTS = ["msrsb_partition_size", "msrsb_partition", "msrsb_filter", "msrsb_build_basis", "msrsb_coarse_op",
            "msrsb_setup", "msrsb_apply", "msrsb_solve", "msrsb_get_setup", "msrsb_get_info", "msrsb_destroy",
            "msrsb_solve_host", "msrsb_profile", "msrsb_profile_read", "msrsb_build_basis_noalloc",
-           "msrsb_solve_ensemble", "msrsb_last_error"]
+           "msrsb_solve_ensemble", "msrsb_transpose_values", "msrsb_pattern_outer", "msrsb_last_error"]
 
 
 class MsrsbError(RuntimeError):
@@ -341,4 +341,19 @@ def msrsb_solve_ensemble(problems, o, rtol=1e-8, maxit=200, concurrency=4):
                                      ctypes.c_int32(maxit), ctypes.c_int32(concurrency))
     out = [(list(k[2])[:k[4]], list(k[3])[:k[4]], arr[i].status) for i, k in enumerate(keep)]
     _check(st)
+    return out
+
+
+def msrsb_transpose_values(A, stream=None):
+    """Values of A^T in A's (structurally symmetric) pattern, as a new tensor."""
+    out = torch.empty_like(A.val)
+    _check(load().msrsb_transpose_values(ctypes.byref(A.c()), _ptr(out), _stream(stream)))
+    return out
+
+
+def msrsb_pattern_outer(A, alpha, lam, x, stream=None):
+    """alpha * lam x^T on A's pattern (same layout as A.val)."""
+    out = torch.empty_like(A.val)
+    _check(load().msrsb_pattern_outer(ctypes.byref(A.c()), ctypes.c_double(alpha), _ptr(lam), _ptr(x), _ptr(out),
+                                      _stream(stream)))
     return out
