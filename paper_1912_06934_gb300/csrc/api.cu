@@ -92,7 +92,7 @@ msrsb_status galerkin(const msrsb_mat *A, const msrsb_grid *g, int W, int nc, co
 msrsb_status coarse_inverse(int n, const double *Ac, double *Ainv, cudaStream_t s);
 msrsb_status coarse_inverse_launch(int n, const double *Ac, double *Ainv, CoarseInverseWork *w, cudaStream_t s);
 msrsb_status coarse_inverse_finish(CoarseInverseWork *w, cudaStream_t s);
-msrsb_status gemv(int n, const double *M, const double *x, double *y, cudaStream_t s);
+msrsb_status gemv(int n, const double *M, const double *x, double *y, float *y32, cudaStream_t s);
 msrsb_status colour_classes(int n, const uint8_t *colour, int ncol, int32_t **rows, int32_t *ptr_h, cudaStream_t s);
 template <typename TF>
 msrsb_status ilu0_factor(const msrsb_mat *A, const uint8_t *colour, int ncol, const int32_t *rows,
@@ -121,7 +121,8 @@ msrsb_status spmv(const msrsb_mat &A, const TA *val, const TX *x, const TV *v, T
 template <typename TP, typename TV>
 msrsb_status restrict_op(const msrsb_handle *h, const TP *P, const TV *v, double *vc, cudaStream_t s);
 template <typename TP, typename TZ>
-msrsb_status prolong_op(const msrsb_handle *h, const TP *P, const double *wc, TZ *z, int add, cudaStream_t s);
+msrsb_status prolong_op(const msrsb_handle *h, const TP *P, const double *wc, const float *wc32, TZ *z, float *z32,
+                        int add, cudaStream_t s);
 template <typename TV>
 msrsb_status mdot(long N, int nvec, const TV *V, long ldv, const TV *w, double *partial, double *out, int accumulate,
                   cudaStream_t s, const int *gate = nullptr);
@@ -310,6 +311,8 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
     const long N = (long)n * bd;
     MSRSB_TRY(dalloc(&h->vc, h->nC, s));
     MSRSB_TRY(dalloc(&h->wc, h->nC, s));
+    MSRSB_TRY(dalloc(&h->wc32, h->nC, s));
+    if (h->opts.prec == MSRSB_F32 && h->bdim == 1) MSRSB_TRY(dalloc(&h->z32, (size_t)h->n, s));
     MSRSB_TRY(dalloc(&h->tmp_d, N, s));
     T *r = nullptr, *y = nullptr;
     MSRSB_TRY(dalloc(&r, N, s));
@@ -353,6 +356,18 @@ static msrsb_status resid_t(const msrsb_handle *h, const T *aval_t, const TZ *z,
     return spmv<T, TZ, TVI, T, T>(h->A, aval_t, z, v, r, true, s, operm);
 }
 
+// r = v - A z for a scalar operator in the mixed form, reading the FP32 copy
+// of z that the prolongation left
+template <typename T, typename TVI>
+static msrsb_status resid_z32(const msrsb_handle *h, const float *z32, const TVI *v, T *r, const int32_t *operm,
+                              cudaStream_t s) {
+    if constexpr (sizeof(T) == 4)
+        return sell_spmv<float, float, TVI, float, float>(h->asell, (const float *)h->asell.val[1], z32, v, r, true, s,
+                                                          operm);
+    else
+        return fail(MSRSB_EINVAL, "FP32 residual requested in the FP64 form");
+}
+
 // Alg. 4 (Alg. 3 inside) from z = 0; the preconditioner's internals run in T,
 // its input vector is TVI and its output TZ
 template <typename T, typename TVI, typename TZ>
@@ -367,6 +382,9 @@ static msrsb_status apply_t(msrsb_handle *h, const TVI *v, TZ *z, cudaStream_t s
     const bool pre = h->opts.pre && (gs || ilu || l1), post = h->opts.post && (gs || ilu || l1);
     const bool coarse = !h->opts.no_coarse;
     const T *dinv = (const T *)h->dinv;
+    // scalar mixed form: the coarse stage also leaves z in FP32, which the
+    // first post-smoothing residual reads (it rounds z to FP32 all the same)
+    float *z32 = (coarse && post && (ilu || l1) && sizeof(T) == 4 && sizeof(TZ) == 8) ? h->z32 : nullptr;
     if (pre) {
         // z = M_pre^-1 v
         if (gs) {
@@ -391,8 +409,8 @@ static msrsb_status apply_t(msrsb_handle *h, const TVI *v, TZ *z, cudaStream_t s
         } else {
             MSRSB_TRY((restrict_op<T, TVI>(h, (const T *)h->pt_val, v, h->vc, s)));
         }
-        MSRSB_TRY(gemv(h->nC, h->Ainv, h->vc, h->wc, s));
-        MSRSB_TRY((prolong_op<T, TZ>(h, P, h->wc, z, pre ? 1 : 0, s)));
+        MSRSB_TRY(gemv(h->nC, h->Ainv, h->vc, h->wc, sizeof(T) == 4 ? h->wc32 : nullptr, s));
+        MSRSB_TRY((prolong_op<T, TZ>(h, P, h->wc, h->wc32, z, z32, pre ? 1 : 0, s)));
     } else if (!pre) {
         MSRSB_CUDA(cudaMemsetAsync(z, 0, N * sizeof(TZ), s));  // smoothing only, from z = 0
     }
@@ -402,12 +420,18 @@ static msrsb_status apply_t(msrsb_handle *h, const TVI *v, TZ *z, cudaStream_t s
             MSRSB_TRY((gs_apply<T, T, TZ>(h, aval_t, dinv, 0, r, y, z, 0, s)));
         } else if (l1) {
             for (int k = 0; k < h->opts.post; ++k) {
-                MSRSB_TRY((resid_t<T, TZ, TVI>(h, aval_t, z, v, r, nullptr, s)));
+                if (k == 0 && z32)
+                    MSRSB_TRY((resid_z32<T, TVI>(h, z32, v, r, nullptr, s)));
+                else
+                    MSRSB_TRY((resid_t<T, TZ, TVI>(h, aval_t, z, v, r, nullptr, s)));
                 MSRSB_TRY((l1_update<T, TZ, T>(N, dinv, r, z, 0, s)));
             }
         } else {
             // residual written straight into colour order for the sweeps
-            MSRSB_TRY((resid_t<T, TZ, TVI>(h, aval_t, z, v, r, h->pos_of, s)));
+            if (z32)
+                MSRSB_TRY((resid_z32<T, TVI>(h, z32, v, r, h->pos_of, s)));
+            else
+                MSRSB_TRY((resid_t<T, TZ, TVI>(h, aval_t, z, v, r, h->pos_of, s)));
             MSRSB_TRY((ilu0_apply<T, TZ>(h, r, z, s)));
         }
     }
@@ -845,6 +869,8 @@ static void handle_free(msrsb_handle *h) {
     sell_free(&h->asell, s);
     dfree(h->vc, s);
     dfree(h->wc, s);
+    dfree(h->wc32, s);
+    dfree(h->z32, s);
     dfree(h->tmp_d, s);
     dfree(h->r_t, s);
     dfree(h->y_t, s);

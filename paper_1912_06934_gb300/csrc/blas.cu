@@ -3,6 +3,7 @@
 // BSR), restriction R = P^T, prolongation P, multi-vector dot products with a
 // fixed reduction order, and the vector updates.
 #include "common.cuh"
+#include <type_traits>
 
 namespace msrsb {
 
@@ -160,6 +161,9 @@ template msrsb_status sell_spmv<float, double, double, float, float>(const Sell 
 template msrsb_status sell_spmv<float, float, float, float, float>(const Sell &, const float *, const float *,
                                                                    const float *, float *, bool, cudaStream_t,
                                                                    const int32_t *);
+template msrsb_status sell_spmv<float, float, double, float, float>(const Sell &, const float *, const float *,
+                                                                    const double *, float *, bool, cudaStream_t,
+                                                                    const int32_t *);
 template msrsb_status sell_spmv<float, double, float, float, float>(const Sell &, const float *, const double *,
                                                                     const float *, float *, bool, cudaStream_t,
                                                                     const int32_t *);
@@ -170,33 +174,37 @@ template msrsb_status sell_spmv<float, double, float, float, float>(const Sell &
 // thread-private sums over the support rows, fixed-order block reduction.
 // PT holds P's values in the order of pt_rows (column J's entries
 // contiguous, component l at l*nnzp), so the reads of P are coalesced.
+// With FP32 P and FP32 v (the mixed form) the thread sums run in FP32 and
+// only the block reduction in FP64: conversions and FMAs on the narrow FP64
+// pipe of this GPU would otherwise bound the kernel.
 template <typename TP, typename TV>
 __global__ void __launch_bounds__(256) restrict_kernel(int nc, int nnzp, int bd, const int32_t *__restrict__ pt_ptr,
                                                        const int32_t *__restrict__ pt_rows,
                                                        const TP *__restrict__ PT, const TV *__restrict__ v,
                                                        double *__restrict__ vc) {
     pdl_prologue();
+    using ACC = typename std::conditional<sizeof(TP) == 4 && sizeof(TV) == 4, float, double>::type;
     __shared__ double red[3][8];
     const int J = blockIdx.x;
-    double acc[3] = {0.0, 0.0, 0.0};
+    ACC acc[3] = {ACC(0), ACC(0), ACC(0)};
     const int r1 = pt_ptr[J + 1];
     int r = pt_ptr[J] + threadIdx.x;
     for (; r + (int)blockDim.x < r1; r += 2 * blockDim.x) {
         const int i0 = pt_rows[r], i1 = pt_rows[r + blockDim.x];
         for (int l = 0; l < bd; ++l) {
-            const double p0 = (double)PT[(long)l * nnzp + r], p1 = (double)PT[(long)l * nnzp + r + blockDim.x];
-            const double v0 = (double)v[(long)i0 * bd + l], v1 = (double)v[(long)i1 * bd + l];
+            const ACC p0 = (ACC)PT[(long)l * nnzp + r], p1 = (ACC)PT[(long)l * nnzp + r + blockDim.x];
+            const ACC v0 = (ACC)v[(long)i0 * bd + l], v1 = (ACC)v[(long)i1 * bd + l];
             acc[l] = fma(p0, v0, acc[l]);
             acc[l] = fma(p1, v1, acc[l]);
         }
     }
     if (r < r1) {
         const int i = pt_rows[r];
-        for (int l = 0; l < bd; ++l) acc[l] = fma((double)PT[(long)l * nnzp + r], (double)v[(long)i * bd + l], acc[l]);
+        for (int l = 0; l < bd; ++l) acc[l] = fma((ACC)PT[(long)l * nnzp + r], (ACC)v[(long)i * bd + l], acc[l]);
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int l = 0; l < bd; ++l) {
-        double t = warp_sum(acc[l]);
+        double t = warp_sum((double)acc[l]);
         if (lane == 0) red[l][warp] = t;
     }
     __syncthreads();
@@ -264,7 +272,8 @@ __device__ __forceinline__ void load32(const T *__restrict__ p, T (&out)[W]) {
 template <typename TP, typename TZ, int W>
 __global__ void __launch_bounds__(256) prolong_kernel(int n, int bd, const int32_t *__restrict__ p_ids,
                                                       const TP *__restrict__ P, const double *__restrict__ wc,
-                                                      TZ *__restrict__ z, int add) {
+                                                      const float *__restrict__ wc32, TZ *__restrict__ z,
+                                                      float *__restrict__ z32, int add) {
     pdl_prologue();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -274,29 +283,42 @@ __global__ void __launch_bounds__(256) prolong_kernel(int n, int bd, const int32
     for (int l = 0; l < bd; ++l) {
         TP pv[W];
         load32<TP, W>(P + l * nW + (long)i * W, pv);
-        double s = 0.0;
+        // FP32 P: products and sum in FP32 against the FP32 copy of w_c (off
+        // the FP64 pipe); FP64 P: FP64 throughout
+        TP s = TP(0);
 #pragma unroll
-        for (int c = 0; c < W; ++c)
-            if (ids[c] >= 0) s = fma((double)pv[c], wc[(long)ids[c] * bd + l], s);
+        for (int c = 0; c < W; ++c) {
+            if (ids[c] < 0) continue;
+            const long q = (long)ids[c] * bd + l;
+            if constexpr (sizeof(TP) == 4) s = fmaf(pv[c], wc32[q], s);
+            else s = fma(pv[c], wc[q], s);
+        }
         const long o = (long)i * bd + l;
-        z[o] = add ? TZ(z[o] + s) : TZ(s);
+        const TZ zn = add ? TZ(z[o] + TZ(s)) : TZ(s);
+        z[o] = zn;
+        if (z32) z32[o] = add ? float(zn) : float(s);
     }
 }
 
+// z (+)= P w_c; wc32 (FP32 copy of w_c) is read when P is FP32; z32
+// (nullable) receives an FP32 copy of the new z
 template <typename TP, typename TZ>
-msrsb_status prolong_op(const msrsb_handle *h, const TP *P, const double *wc, TZ *z, int add, cudaStream_t s) {
+msrsb_status prolong_op(const msrsb_handle *h, const TP *P, const double *wc, const float *wc32, TZ *z, float *z32,
+                        int add, cudaStream_t s) {
     if (h->W == 8)
-        MSRSB_PDL((prolong_kernel<TP, TZ, 8>), ceil_div(h->n, 256), 256, 0, s, h->n, h->bdim, h->p_ids, P, wc, z, add);
+        MSRSB_PDL((prolong_kernel<TP, TZ, 8>), ceil_div(h->n, 256), 256, 0, s, h->n, h->bdim, h->p_ids, P, wc, wc32, z,
+                  z32, add);
     else
-        MSRSB_PDL((prolong_kernel<TP, TZ, 4>), ceil_div(h->n, 256), 256, 0, s, h->n, h->bdim, h->p_ids, P, wc, z, add);
+        MSRSB_PDL((prolong_kernel<TP, TZ, 4>), ceil_div(h->n, 256), 256, 0, s, h->n, h->bdim, h->p_ids, P, wc, wc32, z,
+                  z32, add);
     return MSRSB_OK;
 }
-template msrsb_status prolong_op<double, double>(const msrsb_handle *, const double *, const double *, double *, int,
-                                                 cudaStream_t);
-template msrsb_status prolong_op<float, double>(const msrsb_handle *, const float *, const double *, double *, int,
-                                                cudaStream_t);
-template msrsb_status prolong_op<float, float>(const msrsb_handle *, const float *, const double *, float *, int,
-                                               cudaStream_t);
+template msrsb_status prolong_op<double, double>(const msrsb_handle *, const double *, const double *, const float *,
+                                                 double *, float *, int, cudaStream_t);
+template msrsb_status prolong_op<float, double>(const msrsb_handle *, const float *, const double *, const float *,
+                                                double *, float *, int, cudaStream_t);
+template msrsb_status prolong_op<float, float>(const msrsb_handle *, const float *, const double *, const float *,
+                                               float *, float *, int, cudaStream_t);
 
 // ---- dense vector kernels for the Krylov loop ---------------------------------------
 

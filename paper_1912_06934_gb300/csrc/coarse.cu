@@ -469,8 +469,10 @@ msrsb_status coarse_inverse(int n, const double *Ac, double *Ainv, cudaStream_t 
     return coarse_inverse_finish(&w, s);
 }
 
-// y = M x, M dense n x n row-major FP64; one warp per row.
-__global__ void gemv_kernel(int n, const double *__restrict__ M, const double *__restrict__ x, double *__restrict__ y) {
+// y = M x, M dense n x n row-major FP64; one warp per row; y32 (nullable)
+// receives an FP32 copy of y.
+__global__ void gemv_kernel(int n, const double *__restrict__ M, const double *__restrict__ x, double *__restrict__ y,
+                            float *__restrict__ y32) {
     pdl_prologue();
     int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     int lane = threadIdx.x & 31;
@@ -479,11 +481,14 @@ __global__ void gemv_kernel(int n, const double *__restrict__ M, const double *_
     double s = 0.0;
     for (int j = lane; j < n; j += 32) s = fma(mr[j], x[j], s);
     s = warp_sum(s);
-    if (lane == 0) y[row] = s;
+    if (lane == 0) {
+        y[row] = s;
+        if (y32) y32[row] = (float)s;
+    }
 }
 
-msrsb_status gemv(int n, const double *M, const double *x, double *y, cudaStream_t s) {
-    MSRSB_PDL((gemv_kernel), ceil_div(n, 8), 256, 0, s, n, M, x, y);
+msrsb_status gemv(int n, const double *M, const double *x, double *y, float *y32, cudaStream_t s) {
+    MSRSB_PDL((gemv_kernel), ceil_div(n, 8), 256, 0, s, n, M, x, y, y32);
     return MSRSB_OK;
 }
 

@@ -203,6 +203,8 @@ struct msrsb_handle {
     msrsb::Sell asell;          // sliced-ELL copy of a scalar A: FP64 values [0], FP32 values [1] (mixed)
     // workspaces
     double *vc = nullptr, *wc = nullptr, *tmp_d = nullptr;
+    float *wc32 = nullptr;  // FP32 copy of w_c (FP32 prolongation)
+    float *z32 = nullptr;   // FP32 copy of z after the coarse stage (scalar mixed form)
     void *r_t = nullptr, *y_t = nullptr;
     // Krylov workspace
     double *kv = nullptr, *kz = nullptr;   // GMRES V [(m+1)][N], Z [m][N]; PCG uses first columns

@@ -105,7 +105,9 @@ def test_coarse_correction_concurrent_setups(M, prec):
     rows, slots = np.nonzero(ids >= 0)
     Pm = sp.csr_matrix((P[rows, slots], (rows, ids[rows, slots])), shape=(ids.shape[0], Ac.shape[0]))
     z_host = Pm @ np.linalg.solve(Ac, Pm.T @ v.cpu().numpy())
-    assert np.linalg.norm(z - z_host) <= 1e-8 * np.linalg.norm(z_host)
+    # the mixed form prolongs in FP32: each z_i is a sum of at most 8 products
+    # of non-negative weights (a partition of unity), relative error <= 8 u_32
+    assert np.linalg.norm(z - z_host) <= (1e-8 if prec == 0 else 1e-6) * np.linalg.norm(z_host)
     results = [None] * 6
     streams = [torch.cuda.Stream() for _ in range(6)]
 
