@@ -747,11 +747,65 @@ __global__ void __launch_bounds__(256) mdot_df_kernel(long N, int nv, const floa
 __global__ void reduce_partials_kernel(int nblk, const double *__restrict__ partial, double *__restrict__ out,
                                        int accumulate, int sqrt_out, const int *__restrict__ gate);
 
+// As mdot_df_kernel with 16-byte loads: every thread takes four consecutive
+// elements of each plane per load (row chunks in units of four elements),
+// so that enough bytes are in flight to keep HBM busy. Requires N and ldv
+// divisible by 4 and 16-byte aligned planes.
+__global__ void __launch_bounds__(256) mdot_df4_kernel(long N4, int nv, const float4 *__restrict__ Vh,
+                                                       const float4 *__restrict__ Vl, long ldv4,
+                                                       const float4 *__restrict__ Wh, const float4 *__restrict__ Wl,
+                                                       double *__restrict__ partial, const int *__restrict__ gate) {
+    pdl_prologue();
+    if (gate && !*gate) return;
+    __shared__ double red[8];
+    const int q = blockIdx.y;
+    const long chunk = (N4 + gridDim.x - 1) / gridDim.x;
+    const long b0 = blockIdx.x * chunk, b1 = b0 + chunk < N4 ? b0 + chunk : N4;
+    const float4 *vh = q < nv ? Vh + q * ldv4 : Wh, *vl = q < nv ? Vl + q * ldv4 : Wl;
+    DF s0{0.f, 0.f}, s1{0.f, 0.f};
+    long i = b0 + threadIdx.x;
+    const long bd = blockDim.x;
+    for (; i + bd < b1; i += 2 * bd) {
+        const float4 a = __ldg(vh + i), al = __ldg(vl + i), w = __ldg(Wh + i), wl = __ldg(Wl + i);
+        const float4 c = __ldg(vh + i + bd), cl = __ldg(vl + i + bd), x = __ldg(Wh + i + bd), xl = __ldg(Wl + i + bd);
+        df_fma_acc(s0, a.x, al.x, w.x, wl.x);
+        df_fma_acc(s1, a.y, al.y, w.y, wl.y);
+        df_fma_acc(s0, a.z, al.z, w.z, wl.z);
+        df_fma_acc(s1, a.w, al.w, w.w, wl.w);
+        df_fma_acc(s0, c.x, cl.x, x.x, xl.x);
+        df_fma_acc(s1, c.y, cl.y, x.y, xl.y);
+        df_fma_acc(s0, c.z, cl.z, x.z, xl.z);
+        df_fma_acc(s1, c.w, cl.w, x.w, xl.w);
+    }
+    if (i < b1) {
+        const float4 a = __ldg(vh + i), al = __ldg(vl + i), w = __ldg(Wh + i), wl = __ldg(Wl + i);
+        df_fma_acc(s0, a.x, al.x, w.x, wl.x);
+        df_fma_acc(s1, a.y, al.y, w.y, wl.y);
+        df_fma_acc(s0, a.z, al.z, w.z, wl.z);
+        df_fma_acc(s1, a.w, al.w, w.w, wl.w);
+    }
+    DF t = df_add(two_sum(s0.hi, s0.lo), two_sum(s1.hi, s1.lo));
+    for (int o = 16; o > 0; o >>= 1) t = df_add(t, df_shfl_down(t, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)t.hi + (double)t.lo;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        v = warp_sum(v);
+        if (threadIdx.x == 0) partial[(long)q * gridDim.x + blockIdx.x] = v;
+    }
+}
+
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
+
 // hs[q] = V_q . w (q < nv), hs[nv] = w . w
 msrsb_status mdot_df(long N, int nv, const float *Vh, const float *Vl, long ldv, const float *Wh, const float *Wl,
                      double *partial, double *hs, cudaStream_t s, const int *gate) {
     dim3 grid(kRedBlocks, nv + 1);
-    MSRSB_PDL((mdot_df_kernel), grid, 256, 0, s, N, nv, Vh, Vl, ldv, Wh, Wl, partial, gate);
+    if (N % 4 == 0 && ldv % 4 == 0 && aligned16(Vh) && aligned16(Vl) && aligned16(Wh) && aligned16(Wl))
+        MSRSB_PDL((mdot_df4_kernel), grid, 256, 0, s, N / 4, nv, (const float4 *)Vh, (const float4 *)Vl, ldv / 4,
+                  (const float4 *)Wh, (const float4 *)Wl, partial, gate);
+    else
+        MSRSB_PDL((mdot_df_kernel), grid, 256, 0, s, N, nv, Vh, Vl, ldv, Wh, Wl, partial, gate);
     MSRSB_PDL((reduce_partials_kernel), nv + 1, 256, 0, s, kRedBlocks, partial, hs, 0, 0, gate);
     return MSRSB_OK;
 }
@@ -808,8 +862,94 @@ __global__ void __launch_bounds__(256) gs_update_df_kernel(long N, int nv, const
     }
 }
 
+// As gs_update_df_kernel with 16-byte loads, four consecutive elements per
+// thread (same arithmetic per element, so the same results), and the
+// projection's squared norm summed by one warp instead of one thread.
+// Requires N and ldv divisible by 4 and 16-byte aligned planes.
+__device__ __forceinline__ void df_out4(float4 &h, float4 &l, const DF *a, DF sc) {
+    DF x = df_mul(two_sum(a[0].hi, a[0].lo), sc);
+    h.x = x.hi, l.x = x.lo;
+    x = df_mul(two_sum(a[1].hi, a[1].lo), sc);
+    h.y = x.hi, l.y = x.lo;
+    x = df_mul(two_sum(a[2].hi, a[2].lo), sc);
+    h.z = x.hi, l.z = x.lo;
+    x = df_mul(two_sum(a[3].hi, a[3].lo), sc);
+    h.w = x.hi, l.w = x.lo;
+}
+
+__global__ void __launch_bounds__(256) gs_update_df4_kernel(long N4, int nv, const float4 *__restrict__ Vh,
+                                                            const float4 *__restrict__ Vl, long ldv4,
+                                                            const double *__restrict__ hs, float4 *Wh, float4 *Wl,
+                                                            float4 *__restrict__ oh, float4 *__restrict__ ol,
+                                                            double *__restrict__ hcol, int *__restrict__ flag,
+                                                            int pass) {
+    pdl_prologue();
+    if (pass == 2 && !*flag) return;
+    __shared__ float hh[1024], hl[1024];
+    __shared__ DF s_scale;
+    __shared__ int s_norm;
+    for (int q = threadIdx.x; q < nv; q += blockDim.x) {
+        const DF d = df_from(-hs[q]);
+        hh[q] = d.hi;
+        hl[q] = d.lo;
+    }
+    if (threadIdx.x < 32) {
+        double pr = 0.0;
+        for (int q = threadIdx.x; q < nv; q += 32) pr = fma(hs[q], hs[q], pr);
+        pr = warp_sum(pr);
+        const double ww = hs[nv];
+        const double d2 = ww - pr;
+        const int norm = pass == 2 || d2 >= 0.5 * ww;
+        const double den = norm && d2 > 0.0 ? sqrt(d2) : 0.0;
+        if (threadIdx.x == 0) {
+            s_norm = norm;
+            s_scale = df_from(den > 0.0 ? 1.0 / den : (norm ? 0.0 : 1.0));
+        }
+        if (blockIdx.x == 0) {
+            for (int q = threadIdx.x; q < nv; q += 32) hcol[q] = pass == 1 ? hs[q] : hcol[q] + hs[q];
+            if (threadIdx.x == 0) {
+                if (norm) hcol[nv] = den;
+                if (pass == 1) *flag = !norm;
+            }
+        }
+    }
+    __syncthreads();
+    const DF sc = s_scale;
+    const bool norm = s_norm;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N4; i += (long)gridDim.x * blockDim.x) {
+        const float4 wh = Wh[i], wl = Wl[i];
+        DF a[4] = {{wh.x, wl.x}, {wh.y, wl.y}, {wh.z, wl.z}, {wh.w, wl.w}};
+#pragma unroll 2
+        for (int q = 0; q < nv; ++q) {
+            const float4 vh = __ldg(Vh + q * ldv4 + i), vl = __ldg(Vl + q * ldv4 + i);
+            const float ch = hh[q], cl = hl[q];
+            df_fma_acc(a[0], vh.x, vl.x, ch, cl);
+            df_fma_acc(a[1], vh.y, vl.y, ch, cl);
+            df_fma_acc(a[2], vh.z, vl.z, ch, cl);
+            df_fma_acc(a[3], vh.w, vl.w, ch, cl);
+        }
+        float4 h, l;
+        df_out4(h, l, a, sc);
+        if (norm) {
+            oh[i] = h;
+            ol[i] = l;
+        } else {
+            Wh[i] = h;
+            Wl[i] = l;
+        }
+    }
+}
+
 msrsb_status gs_update_df(long N, int nv, const float *Vh, const float *Vl, long ldv, const double *hs, float *Wh,
                           float *Wl, float *oh, float *ol, double *hcol, int *flag, int pass, cudaStream_t s) {
+    if (N % 4 == 0 && ldv % 4 == 0 && aligned16(Vh) && aligned16(Vl) && aligned16(Wh) && aligned16(Wl) &&
+        aligned16(oh) && aligned16(ol)) {
+        const long N4 = N / 4;
+        const int grid = ceil_div(N4, 256) < 2048 ? (int)ceil_div(N4, 256) : 2048;
+        MSRSB_PDL((gs_update_df4_kernel), grid, 256, 0, s, N4, nv, (const float4 *)Vh, (const float4 *)Vl, ldv / 4,
+                  hs, (float4 *)Wh, (float4 *)Wl, (float4 *)oh, (float4 *)ol, hcol, flag, pass);
+        return MSRSB_OK;
+    }
     const int grid = ceil_div(N, 256) < 2048 ? (int)ceil_div(N, 256) : 2048;
     MSRSB_PDL((gs_update_df_kernel), grid, 256, 0, s, N, nv, Vh, Vl, ldv, hs, Wh, Wl, oh, ol, hcol, flag, pass);
     return MSRSB_OK;
