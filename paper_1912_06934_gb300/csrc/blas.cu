@@ -177,33 +177,53 @@ template msrsb_status sell_spmv<float, double, float, float, float>(const Sell &
 // With FP32 P and FP32 v (the mixed form) the thread sums run in FP32 and
 // only the block reduction in FP64: conversions and FMAs on the narrow FP64
 // pipe of this GPU would otherwise bound the kernel.
-template <typename TP, typename TV>
-__global__ void __launch_bounds__(256) restrict_kernel(int nc, int nnzp, int bd, const int32_t *__restrict__ pt_ptr,
+// P's pattern and values are fixed for a solve: each thread loads its first
+// kRestrictPre support rows and their component-0 values before
+// griddepcontrol.wait, so that those loads overlap the previous kernel; the
+// summation order (ascending r) is the same either way.
+constexpr int kRestrictPre = 16;
+
+template <typename TP, typename TV, int BD>
+__global__ void __launch_bounds__(256, 3) restrict_kernel(int nc, int nnzp, const int32_t *__restrict__ pt_ptr,
                                                        const int32_t *__restrict__ pt_rows,
                                                        const TP *__restrict__ PT, const TV *__restrict__ v,
                                                        double *__restrict__ vc) {
-    pdl_prologue();
     using ACC = typename std::conditional<sizeof(TP) == 4 && sizeof(TV) == 4, float, double>::type;
-    __shared__ double red[3][8];
+    constexpr int bd = BD;
+    __shared__ double red[BD][8];
     const int J = blockIdx.x;
-    ACC acc[3] = {ACC(0), ACC(0), ACC(0)};
-    const int r1 = pt_ptr[J + 1];
-    int r = pt_ptr[J] + threadIdx.x;
-    for (; r + (int)blockDim.x < r1; r += 2 * blockDim.x) {
-        const int i0 = pt_rows[r], i1 = pt_rows[r + blockDim.x];
-        for (int l = 0; l < bd; ++l) {
-            const ACC p0 = (ACC)PT[(long)l * nnzp + r], p1 = (ACC)PT[(long)l * nnzp + r + blockDim.x];
-            const ACC v0 = (ACC)v[(long)i0 * bd + l], v1 = (ACC)v[(long)i1 * bd + l];
-            acc[l] = fma(p0, v0, acc[l]);
-            acc[l] = fma(p1, v1, acc[l]);
-        }
+    const int bs = blockDim.x;
+    const int r0 = __ldg(pt_ptr + J) + threadIdx.x, r1 = __ldg(pt_ptr + J + 1);
+    int ri[kRestrictPre];
+    TP p0[kRestrictPre];
+#pragma unroll
+    for (int t = 0; t < kRestrictPre; ++t) {
+        const int r = r0 + t * bs;
+        ri[t] = r < r1 ? __ldg(pt_rows + r) : 0;
+        p0[t] = r < r1 ? __ldg(PT + r) : TP(0);
     }
-    if (r < r1) {
+    pdl_prologue();
+    ACC acc[BD];
+#pragma unroll
+    for (int l = 0; l < BD; ++l) acc[l] = ACC(0);
+#pragma unroll
+    for (int t = 0; t < kRestrictPre; ++t) {
+        const int r = r0 + t * bs;
+        if (r < r1)
+#pragma unroll
+            for (int l = 0; l < BD; ++l) {
+                const ACC p = (ACC)(l == 0 ? p0[t] : PT[(long)l * nnzp + r]);
+                acc[l] = fma(p, (ACC)v[(long)ri[t] * bd + l], acc[l]);
+            }
+    }
+    for (int r = r0 + kRestrictPre * bs; r < r1; r += bs) {
         const int i = pt_rows[r];
-        for (int l = 0; l < bd; ++l) acc[l] = fma((ACC)PT[(long)l * nnzp + r], (ACC)v[(long)i * bd + l], acc[l]);
+#pragma unroll
+        for (int l = 0; l < BD; ++l) acc[l] = fma((ACC)PT[(long)l * nnzp + r], (ACC)v[(long)i * bd + l], acc[l]);
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int l = 0; l < bd; ++l) {
+#pragma unroll
+    for (int l = 0; l < BD; ++l) {
         double t = warp_sum((double)acc[l]);
         if (lane == 0) red[l][warp] = t;
     }
@@ -218,8 +238,10 @@ __global__ void __launch_bounds__(256) restrict_kernel(int nc, int nnzp, int bd,
 
 template <typename TP, typename TV>
 msrsb_status restrict_op(const msrsb_handle *h, const TP *PT, const TV *v, double *vc, cudaStream_t s) {
-    MSRSB_PDL((restrict_kernel<TP, TV>), h->nc, 256, 0, s, h->nc, h->nnz_p, h->bdim, h->pt_ptr, h->pt_rows, PT, v,
-              vc);
+    if (h->bdim == 3)
+        MSRSB_PDL((restrict_kernel<TP, TV, 3>), h->nc, 256, 0, s, h->nc, h->nnz_p, h->pt_ptr, h->pt_rows, PT, v, vc);
+    else
+        MSRSB_PDL((restrict_kernel<TP, TV, 1>), h->nc, 256, 0, s, h->nc, h->nnz_p, h->pt_ptr, h->pt_rows, PT, v, vc);
     return MSRSB_OK;
 }
 
@@ -274,15 +296,26 @@ __global__ void __launch_bounds__(256) prolong_kernel(int n, int bd, const int32
                                                       const TP *__restrict__ P, const double *__restrict__ wc,
                                                       const float *__restrict__ wc32, TZ *__restrict__ z,
                                                       float *__restrict__ z32, int add) {
-    pdl_prologue();
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    // slot ids and component-0 values of P are fixed for a solve: loaded
+    // before griddepcontrol.wait, overlapping the previous kernel
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const long nW = (long)n * W;
     int32_t ids[W];
-    load32<int32_t, W>(p_ids + (long)i * W, ids);
+    TP p0[W];
+    if (i < n) {
+        load32<int32_t, W>(p_ids + (long)i * W, ids);
+        load32<TP, W>(P + (long)i * W, p0);
+    }
+    pdl_prologue();
+    if (i >= n) return;
     for (int l = 0; l < bd; ++l) {
         TP pv[W];
-        load32<TP, W>(P + l * nW + (long)i * W, pv);
+        if (l == 0) {
+#pragma unroll
+            for (int c = 0; c < W; ++c) pv[c] = p0[c];
+        } else {
+            load32<TP, W>(P + l * nW + (long)i * W, pv);
+        }
         // FP32 P: products and sum in FP32 against the FP32 copy of w_c (off
         // the FP64 pipe); FP64 P: FP64 throughout
         TP s = TP(0);

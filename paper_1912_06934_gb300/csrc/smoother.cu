@@ -286,19 +286,58 @@ __device__ __forceinline__ unsigned group_mask() {
     return ((1u << kSweepLanes) - 1u) << (threadIdx.x & 31 & ~(kSweepLanes - 1));
 }
 
+// The factors (columns, values, inverse diagonal, row map) are fixed for a
+// solve, so each lane loads its first kSweepPre entries of them before
+// griddepcontrol.wait: those loads overlap the previous stage's tail and
+// leave the critical path; only the gathers of y wait for the previous
+// stage. Rows wider than kSweepLanes * kSweepPre entries finish with plain
+// loads after the wait. The summation order is the same either way.
+constexpr int kSweepPre = 8;
+
+template <typename T>
+struct SweepRow {
+    int32_t col[kSweepPre];
+    T val[kSweepPre];
+};
+
+template <typename T>
+__device__ __forceinline__ void sweep_prefetch(SweepRow<T> &R, int q, int g, int m, int w,
+                                               const int32_t *__restrict__ cols, const T *__restrict__ vals) {
+#pragma unroll
+    for (int t = 0; t < kSweepPre; ++t) {
+        const int j = g + t * kSweepLanes;
+        R.col[t] = j < w ? __ldg(cols + (long)j * m + q) : 0;
+        R.val[t] = j < w ? __ldg(vals + (long)j * m + q) : T(0);
+    }
+}
+
+// sum_j F_pj y_col over the lane's entries, then over the row's lanes
+template <typename T>
+__device__ __forceinline__ T sweep_dot(const SweepRow<T> &R, int q, int g, int m, int w,
+                                       const int32_t *__restrict__ cols, const T *__restrict__ vals, const T *y) {
+    T acc = T(0);
+#pragma unroll
+    for (int t = 0; t < kSweepPre; ++t)
+        if (g + t * kSweepLanes < w) acc = fma(R.val[t], y[R.col[t]], acc);
+    for (int j = g + kSweepPre * kSweepLanes; j < w; j += kSweepLanes)
+        acc = fma(vals[(long)j * m + q], y[cols[(long)j * m + q]], acc);
+#pragma unroll
+    for (int o = kSweepLanes / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(group_mask(), acc, o, kSweepLanes);
+    return acc;
+}
+
 // forward, colour c, in place on y (which holds r in colour order on entry):
 // y_p = r_p - sum_j L_pj y_col. Colour 0 has no L entries, so it needs no launch.
 template <typename T>
 __global__ void __launch_bounds__(256) ilu_lower_kernel(int c0, int m, int w, const int32_t *__restrict__ lcol,
                                                         const T *__restrict__ lval, T *__restrict__ y) {
-    pdl_prologue();
     const int q = (blockIdx.x * blockDim.x + threadIdx.x) / kSweepLanes;
     const int g = threadIdx.x % kSweepLanes;
+    SweepRow<T> R;
+    if (q < m) sweep_prefetch(R, q, g, m, w, lcol, lval);
+    pdl_prologue();
     if (q >= m) return;  // whole groups leave together
-    T acc = T(0);
-    for (int j = g; j < w; j += kSweepLanes) acc = fma(lval[(long)j * m + q], y[lcol[(long)j * m + q]], acc);
-#pragma unroll
-    for (int o = kSweepLanes / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(group_mask(), acc, o, kSweepLanes);
+    const T acc = sweep_dot(R, q, g, m, w, lcol, lval, y);
     if (g == 0) y[c0 + q] -= acc;
 }
 
@@ -309,18 +348,24 @@ __global__ void __launch_bounds__(256) ilu_last_kernel(int c0, int m, int w, con
                                                        const T *__restrict__ lval, const T *__restrict__ udinv,
                                                        const int32_t *__restrict__ rows, T *__restrict__ y,
                                                        TZ *__restrict__ z) {
-    pdl_prologue();
     const int q = (blockIdx.x * blockDim.x + threadIdx.x) / kSweepLanes;
     const int g = threadIdx.x % kSweepLanes;
+    SweepRow<T> R;
+    T di = T(0);
+    int row = 0;
+    if (q < m) {
+        sweep_prefetch(R, q, g, m, w, lcol, lval);
+        if (g == 0) {
+            di = __ldg(udinv + c0 + q);
+            row = __ldg(rows + c0 + q);
+        }
+    }
+    pdl_prologue();
     if (q >= m) return;
-    T acc = T(0);
-    for (int j = g; j < w; j += kSweepLanes) acc = fma(lval[(long)j * m + q], y[lcol[(long)j * m + q]], acc);
-#pragma unroll
-    for (int o = kSweepLanes / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(group_mask(), acc, o, kSweepLanes);
+    const T acc = sweep_dot(R, q, g, m, w, lcol, lval, y);
     if (g == 0) {
-        const T e = (y[c0 + q] - acc) * udinv[c0 + q];
+        const T e = (y[c0 + q] - acc) * di;
         y[c0 + q] = e;
-        const int row = rows[c0 + q];
         z[row] = TZ(z[row] + TZ(e));
     }
 }
@@ -332,18 +377,24 @@ __global__ void __launch_bounds__(256) ilu_upper_kernel(int c0, int m, int w, co
                                                         const T *__restrict__ uval, const T *__restrict__ udinv,
                                                         const int32_t *__restrict__ rows, T *__restrict__ y,
                                                         TZ *__restrict__ z) {
-    pdl_prologue();
     const int q = (blockIdx.x * blockDim.x + threadIdx.x) / kSweepLanes;
     const int g = threadIdx.x % kSweepLanes;
+    SweepRow<T> R;
+    T di = T(0);
+    int row = 0;
+    if (q < m) {
+        sweep_prefetch(R, q, g, m, w, ucol, uval);
+        if (g == 0) {
+            di = __ldg(udinv + c0 + q);
+            row = __ldg(rows + c0 + q);
+        }
+    }
+    pdl_prologue();
     if (q >= m) return;
-    T acc = T(0);
-    for (int j = g; j < w; j += kSweepLanes) acc = fma(uval[(long)j * m + q], y[ucol[(long)j * m + q]], acc);
-#pragma unroll
-    for (int o = kSweepLanes / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(group_mask(), acc, o, kSweepLanes);
+    const T acc = sweep_dot(R, q, g, m, w, ucol, uval, y);
     if (g == 0) {
-        T e = (y[c0 + q] - acc) * udinv[c0 + q];
+        const T e = (y[c0 + q] - acc) * di;
         y[c0 + q] = e;
-        const int row = rows[c0 + q];
         z[row] = TZ(z[row] + TZ(e));
     }
 }
