@@ -117,20 +117,52 @@ template msrsb_status spmv<float, double, float, float, float>(const msrsb_mat &
 // Sliced-ELL SpMV / residual: one thread per row, coalesced entry reads,
 // unrolled so several gathers are in flight. y[operm ? operm[i] : i] =
 // (resid ? v_i : 0) -/+ sum_k A_ik x_k.
+// A's sliced-ELL copy is fixed for a solve: every row's first kSellPre
+// entries (columns and values) are loaded before griddepcontrol.wait, so
+// that they overlap the previous kernel; only the gathers of x wait. Entry j
+// goes to accumulator j mod 2 in ascending j, as in the loop after it.
+constexpr int kSellPre = 8;
+
+template <typename TA>
+struct SellRow {
+    int beg = 0, width = 0;
+    int32_t col[kSellPre];
+    TA val[kSellPre];
+};
+
+template <typename TA>
+__device__ __forceinline__ void sell_prefetch(SellRow<TA> &R, int i, const int32_t *__restrict__ slice_ptr,
+                                              const int32_t *__restrict__ scol, const TA *__restrict__ sval) {
+    const int sl = i >> 5, lane = i & 31;
+    R.beg = __ldg(slice_ptr + sl);
+    R.width = (__ldg(slice_ptr + sl + 1) - R.beg) >> 5;
+#pragma unroll
+    for (int t = 0; t < kSellPre; ++t) {
+        R.col[t] = t < R.width ? __ldg(scol + R.beg + lane + (t << 5)) : 0;
+        R.val[t] = t < R.width ? __ldg(sval + R.beg + lane + (t << 5)) : TA(0);
+    }
+}
+
 template <typename TA, typename TX, typename TV, typename TY, typename TACC, bool RESID>
 __global__ void __launch_bounds__(256) sell_spmv_kernel(int n, const int32_t *__restrict__ slice_ptr,
                                                         const int32_t *__restrict__ scol, const TA *__restrict__ sval,
                                                         const TX *__restrict__ x, const TV *__restrict__ v,
                                                         TY *__restrict__ y, const int32_t *__restrict__ operm) {
-    pdl_prologue();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    SellRow<TA> R;
+    if (i < n) sell_prefetch(R, i, slice_ptr, scol, sval);
+    pdl_prologue();
     if (i >= n) return;
-    const int s = i >> 5, lane = i & 31;
-    const int beg = slice_ptr[s], width = (slice_ptr[s + 1] - beg) >> 5;
-    const int32_t *cp = scol + beg + lane;
-    const TA *vp = sval + beg + lane;
+    const int width = R.width;
+    const int32_t *cp = scol + R.beg + (i & 31);
+    const TA *vp = sval + R.beg + (i & 31);
     TACC acc0 = TACC(0), acc1 = TACC(0);
-    int j = 0;
+#pragma unroll
+    for (int t = 0; t < kSellPre; t += 2) {
+        if (t < width) acc0 = fma(TACC(R.val[t]), TACC(__ldg(x + R.col[t])), acc0);
+        if (t + 1 < width) acc1 = fma(TACC(R.val[t + 1]), TACC(__ldg(x + R.col[t + 1])), acc1);
+    }
+    int j = kSellPre;
     for (; j + 1 < width; j += 2) {
         acc0 = fma(TACC(__ldg(vp + (j << 5))), TACC(__ldg(x + __ldg(cp + (j << 5)))), acc0);
         acc1 = fma(TACC(__ldg(vp + ((j + 1) << 5))), TACC(__ldg(x + __ldg(cp + ((j + 1) << 5)))), acc1);
@@ -705,15 +737,21 @@ __global__ void __launch_bounds__(256) sell_spmv_df_kernel(int n, const int32_t 
                                                            const double *__restrict__ sval,
                                                            const double *__restrict__ x, float *__restrict__ yh,
                                                            float *__restrict__ yl) {
-    pdl_prologue();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    SellRow<double> R;
+    if (i < n) sell_prefetch(R, i, slice_ptr, scol, sval);
+    pdl_prologue();
     if (i >= n) return;
-    const int s = i >> 5, lane = i & 31;
-    const int beg = slice_ptr[s], width = (slice_ptr[s + 1] - beg) >> 5;
-    const int32_t *cp = scol + beg + lane;
-    const double *vp = sval + beg + lane;
+    const int width = R.width;
+    const int32_t *cp = scol + R.beg + (i & 31);
+    const double *vp = sval + R.beg + (i & 31);
     double acc0 = 0.0, acc1 = 0.0;
-    int j = 0;
+#pragma unroll
+    for (int t = 0; t < kSellPre; t += 2) {
+        if (t < width) acc0 = fma(R.val[t], __ldg(x + R.col[t]), acc0);
+        if (t + 1 < width) acc1 = fma(R.val[t + 1], __ldg(x + R.col[t + 1]), acc1);
+    }
+    int j = kSellPre;
     for (; j + 1 < width; j += 2) {
         acc0 = fma(__ldg(vp + (j << 5)), __ldg(x + __ldg(cp + (j << 5))), acc0);
         acc1 = fma(__ldg(vp + ((j + 1) << 5)), __ldg(x + __ldg(cp + ((j + 1) << 5))), acc1);

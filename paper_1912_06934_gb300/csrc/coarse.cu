@@ -471,15 +471,25 @@ msrsb_status coarse_inverse(int n, const double *Ac, double *Ainv, cudaStream_t 
 
 // y = M x, M dense n x n row-major FP64; one warp per row; y32 (nullable)
 // receives an FP32 copy of y.
+// M (the coarse inverse) is fixed for a solve: each lane loads its first
+// kGemvPre entries of the row before griddepcontrol.wait; only x waits.
+constexpr int kGemvPre = 16;
+
 __global__ void gemv_kernel(int n, const double *__restrict__ M, const double *__restrict__ x, double *__restrict__ y,
                             float *__restrict__ y32) {
-    pdl_prologue();
-    int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    int lane = threadIdx.x & 31;
-    if (row >= n) return;
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
     const double *mr = M + (long)row * n;
+    double m[kGemvPre];
+#pragma unroll
+    for (int t = 0; t < kGemvPre; ++t) m[t] = row < n && lane + 32 * t < n ? __ldg(mr + lane + 32 * t) : 0.0;
+    pdl_prologue();
+    if (row >= n) return;
     double s = 0.0;
-    for (int j = lane; j < n; j += 32) s = fma(mr[j], x[j], s);
+#pragma unroll
+    for (int t = 0; t < kGemvPre; ++t)
+        if (lane + 32 * t < n) s = fma(m[t], x[lane + 32 * t], s);
+    for (int j = lane + 32 * kGemvPre; j < n; j += 32) s = fma(mr[j], x[j], s);
     s = warp_sum(s);
     if (lane == 0) {
         y[row] = s;
