@@ -238,6 +238,16 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
     std::promise<msrsb_status> tr_done;
     std::future<msrsb_status> tr_status = tr_done.get_future();
     std::string tr_err;
+    // The smoother set-up is held back until the main stream reaches the
+    // coarse inverse: the smoothing passes are bandwidth-bound and would share
+    // HBM with it, while the cooperative Gauss-Jordan kernel (one CTA per SM,
+    // barrier-latency-bound) leaves most warp slots and bandwidth idle. The
+    // main thread hands over an event recorded at that point, or nullptr when
+    // it leaves early.
+    std::promise<cudaEvent_t> go;
+    std::future<cudaEvent_t> go_at = go.get_future();
+    cudaEvent_t go_ev = nullptr;
+    MSRSB_CUDA(cudaEventCreateWithFlags(&go_ev, cudaEventDisableTiming));
     std::thread side_thread([&]() {
         cudaSetDevice(dev);
         msrsb_status st =
@@ -246,7 +256,14 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
             st = fail(MSRSB_ECUDA, "event record failed");
         if (st != MSRSB_OK) tr_err = msrsb_last_error();
         tr_done.set_value(st);
-        side_st = setup_smoother<T>(h, h->side);
+        cudaEvent_t e = go_at.get();
+        if (!e) {
+            side_st = fail(MSRSB_EINVAL, "set-up left before the smoother set-up");
+        } else if (cudaStreamWaitEvent(h->side, e, 0) != cudaSuccess) {
+            side_st = fail(MSRSB_ECUDA, "stream wait failed");
+        } else {
+            side_st = setup_smoother<T>(h, h->side);
+        }
         if (side_st != MSRSB_OK) side_err = msrsb_last_error();
     });
     struct Joiner {
@@ -255,6 +272,17 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
             if (t.joinable()) t.join();
         }
     } joiner{side_thread};
+    // declared after the joiner, so destroyed first: an early return releases
+    // the side thread before it is joined
+    struct Release {
+        std::promise<cudaEvent_t> &p;
+        bool done = false;
+        void operator()(cudaEvent_t e) {
+            if (!done) p.set_value(e);
+            done = true;
+        }
+        ~Release() { (*this)(nullptr); }
+    } release{go};
     // a1 + a2: filtered operator(s) streamed as sliced ELL, then Alg. 1 per component
     T *P = nullptr;
     MSRSB_TRY(dalloc(&P, nW * bd, s));
@@ -305,6 +333,8 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
         MSRSB_TRY(pt_gather<T>(h, P, pt, s));
     }
     MSRSB_TRY(mark(3));
+    MSRSB_CUDA(cudaEventRecord(go_ev, s));
+    release(go_ev);
     MSRSB_TRY(coarse_inverse(h->nC, h->Ac, h->Ainv, s));
     MSRSB_TRY(mark(4));
     // apply workspaces
@@ -328,6 +358,7 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
     cudaEventDestroy(fork);
     cudaEventDestroy(join);
     cudaEventDestroy(tr_ev);
+    cudaEventDestroy(go_ev);
     MSRSB_TRY(mark(6));
     MSRSB_CUDA(cudaStreamSynchronize(s));
     if (prof) {

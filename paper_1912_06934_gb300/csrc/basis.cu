@@ -184,13 +184,17 @@ msrsb_status basis_loop(int n, int W, const Sell &S, int comp, const T *scale, c
     MSRSB_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     bool pending = false;
     T *buf[2] = {P, P2};
-    // optional per-launch timing of the smoothing kernel (CUDA events on s)
-    const bool prof = profiling();
-    cudaEvent_t *tev = nullptr;
+    // optional timing of the smoothing passes (profiling mode): one CUDA event
+    // pair around the whole loop on s, so that consecutive passes keep their
+    // programmatic overlap; the average pass = loop time / passes that worked
+    // (an upper bound: the loop also holds the lagged convergence checks)
+    const bool prof = profiling() && maxit > 0;
+    cudaEvent_t tev[2] = {nullptr, nullptr};
     int launched = 0;
-    if (prof && maxit > 0) {
-        tev = new cudaEvent_t[2 * maxit];
-        for (int q = 0; q < 2 * maxit; ++q) MSRSB_CUDA(cudaEventCreate(&tev[q]));
+    if (prof) {
+        MSRSB_CUDA(cudaEventCreate(&tev[0]));
+        MSRSB_CUDA(cudaEventCreate(&tev[1]));
+        MSRSB_CUDA(cudaEventRecord(tev[0], s));
     }
     for (int k = 0; k < maxit; ++k) {
         int check = (k % o->n_it) == 0;
@@ -198,14 +202,12 @@ msrsb_status basis_loop(int n, int W, const Sell &S, int comp, const T *scale, c
             if (((volatile int *)pin)[0] != 0) break;  // converged at an earlier check
             pending = false;
         }
-        if (prof) MSRSB_CUDA(cudaEventRecord(tev[2 * k], s));
         if (W == 4)
             MSRSB_TRY((launch_smooth<T, 4>(n, S, comp, scale, vmask, skel, buf[k & 1], buf[(k + 1) & 1], emax + k,
                                            check, flags, flags + 1, k, s)));
         else
             MSRSB_TRY((launch_smooth<T, 8>(n, S, comp, scale, vmask, skel, buf[k & 1], buf[(k + 1) & 1], emax + k,
                                            check, flags, flags + 1, k, s)));
-        if (prof) MSRSB_CUDA(cudaEventRecord(tev[2 * k + 1], s));
         launched = k + 1;
         if (check) {
             MSRSB_PDL((basis_check_kernel), 1, 1, 0, s, emax + k, o->tol, flags, e_last);
@@ -217,6 +219,7 @@ msrsb_status basis_loop(int n, int W, const Sell &S, int comp, const T *scale, c
             }
         }
     }
+    if (prof) MSRSB_CUDA(cudaEventRecord(tev[1], s));
     int h_flags[2] = {0, 0};
     double h_e = 0.0;
     MSRSB_CUDA(cudaMemcpyAsync(h_flags, flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -226,15 +229,11 @@ msrsb_status basis_loop(int n, int W, const Sell &S, int comp, const T *scale, c
     int iters = h_flags[1];
     if (prof) {
         // only the first `iters` launches did work; later ones left at once
-        double ms = 0.0;
-        for (int q = 0; q < iters && q < launched; ++q) {
-            float t = 0.f;
-            MSRSB_CUDA(cudaEventElapsedTime(&t, tev[2 * q], tev[2 * q + 1]));
-            ms += t;
-        }
-        add_smooth_time(iters < launched ? iters : launched, ms);
-        for (int q = 0; q < 2 * maxit; ++q) cudaEventDestroy(tev[q]);
-        delete[] tev;
+        float t = 0.f;
+        MSRSB_CUDA(cudaEventElapsedTime(&t, tev[0], tev[1]));
+        add_smooth_time(iters < launched ? iters : launched, t);
+        cudaEventDestroy(tev[0]);
+        cudaEventDestroy(tev[1]);
     }
     if (iters & 1) MSRSB_CUDA(cudaMemcpyAsync(P, P2, (size_t)n * W * sizeof(T), cudaMemcpyDeviceToDevice, s));
     if (iters_out) *iters_out = iters;
