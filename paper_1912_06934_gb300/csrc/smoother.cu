@@ -5,6 +5,7 @@
 // triangular sweep is one kernel launch per colour. The oracle factors the
 // same colour-ordered matrix, so both sides compute the same operator.
 #include "common.cuh"
+#include <climits>
 #include <cub/device/device_radix_sort.cuh>
 
 namespace msrsb {
@@ -87,20 +88,33 @@ __device__ __forceinline__ int find_col(const int32_t *__restrict__ colidx, int 
 // order: colour first, then index. Row i is eliminated against every earlier
 // row k in that order (row-wise IKJ): l_ik = a_ik / u_kk, then every later
 // entry (i, j) that row k also holds is updated; only entries already in A's
-// pattern change. Row k (final, an earlier colour) is read once, coalesced,
-// and matched through warp shuffles with integer work only. The pivot
-// division is replaced by a product with 1 / u_kk, stored when row k was
-// finished: FP64 issue slots are scarce on this GPU. TF is the factorisation
-// precision (FP64 for the FP64 form, FP32 for the mixed form's smoother).
+// pattern change. The pivot division is replaced by a product with 1 / u_kk,
+// stored when row k was finished: FP64 issue slots are scarce on this GPU.
+// TF is the factorisation precision (FP64 for the FP64 form, FP32 for the
+// mixed form's smoother).
+//
+// Loads are kept off the elimination's sequential chain: every lower entry's
+// row extent and 1 / u_kk are read once, in parallel over the lanes; the rows
+// k of up to kIluBatch lower entries of one colour class (final rows of an
+// earlier colour) are staged together in shared memory; and each lane finds
+// its column in row k by a branchless lower-bound search over the 32 staged
+// (padded) columns. The arithmetic and its order are those of the plain
+// row-by-row elimination.
+constexpr int kIluBatch = 8;
+constexpr int kIluWarps = 4;  // warps per CTA (128 threads)
+
 template <typename TF>
-__global__ void __launch_bounds__(128) ilu0_colour_kernel(int cnt, const int32_t *__restrict__ rows, int c,
-                                                          const int32_t *__restrict__ rowptr,
-                                                          const int32_t *__restrict__ colidx,
-                                                          const uint8_t *__restrict__ colour,
-                                                          const int32_t *__restrict__ dpos, TF *__restrict__ lu,
-                                                          TF *__restrict__ rdiag, int *__restrict__ status) {
+__global__ void __launch_bounds__(32 * kIluWarps) ilu0_colour_kernel(int cnt, const int32_t *__restrict__ rows, int c,
+                                                                    const int32_t *__restrict__ rowptr,
+                                                                    const int32_t *__restrict__ colidx,
+                                                                    const uint8_t *__restrict__ colour,
+                                                                    const int32_t *__restrict__ dpos,
+                                                                    TF *__restrict__ lu, TF *__restrict__ rdiag,
+                                                                    int *__restrict__ status) {
+    __shared__ int32_t s_kc[kIluWarps][kIluBatch][32];
+    __shared__ TF s_kv[kIluWarps][kIluBatch][32];
     const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (t >= cnt) return;  // whole warps leave together
     const int i = rows[t];
     const int b = rowptr[i], len = rowptr[i + 1] - b;
@@ -112,25 +126,57 @@ __global__ void __launch_bounds__(128) ilu0_colour_kernel(int cnt, const int32_t
     const int j = mine ? colidx[b + lane] : -1;
     const int cj = mine ? colour[j] : 255;
     TF a = mine ? lu[b + lane] : TF(0);
+    // row k = j of every lower entry: extent (at most 32 entries are staged;
+    // a longer row k has already raised the status) and 1 / u_kk
+    int kb = 0, kl = 0;
+    TF rd = TF(0);
+    if (mine && cj < c) {
+        kb = rowptr[j];
+        kl = min(rowptr[j + 1] - kb, 32);
+        rd = rdiag[j];
+    }
+    int32_t(*const kc)[32] = s_kc[w];
+    TF(*const kv)[32] = s_kv[w];
     for (int cc = 0; cc < c; ++cc) {
         unsigned m = __ballot_sync(0xffffffffu, cj == cc);  // entries of colour cc, ascending column
         while (m) {
-            const int q = __ffs(m) - 1;
-            m &= m - 1;
-            const int k = __shfl_sync(0xffffffffu, j, q);
-            const TF aik = __shfl_sync(0xffffffffu, a, q);
-            const int kb = rowptr[k], klen = rowptr[k + 1] - kb;
-            const TF lik = aik * rdiag[k];
-            if (lane == q) a = lik;
-            const int kc = lane < klen ? colidx[kb + lane] : -1;
-            const TF kv = lane < klen ? lu[kb + lane] : TF(0);
-            // entries after k in the order: later colour, or same colour and larger index
-            const bool later = mine && (cj > cc || (cj == cc && j > k));
-            int hit = -1;
-            for (int r = 0; r < klen; ++r)
-                if (__shfl_sync(0xffffffffu, kc, r) == j) hit = r;
-            const TF kvr = __shfl_sync(0xffffffffu, kv, hit >= 0 ? hit : 0);
-            if (later && hit >= 0) a = a - lik * kvr;
+            int qs[kIluBatch];
+            int nb = 0;
+#pragma unroll
+            for (int u = 0; u < kIluBatch; ++u) {
+                qs[u] = m ? __ffs(m) - 1 : 0;
+                if (m) {
+                    m &= m - 1;
+                    ++nb;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kIluBatch; ++u) {
+                if (u < nb) {
+                    const int ub = __shfl_sync(0xffffffffu, kb, qs[u]), ul = __shfl_sync(0xffffffffu, kl, qs[u]);
+                    kc[u][lane] = lane < ul ? colidx[ub + lane] : INT_MAX;
+                    kv[u][lane] = lane < ul ? lu[ub + lane] : TF(0);
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int u = 0; u < kIluBatch; ++u) {
+                if (u < nb) {
+                    const int q = qs[u];
+                    const int k = __shfl_sync(0xffffffffu, j, q);
+                    const TF lik = __shfl_sync(0xffffffffu, a, q) * __shfl_sync(0xffffffffu, rd, q);
+                    if (lane == q) a = lik;
+                    // entries after k in the order: later colour, or same colour and larger index
+                    const bool later = mine && (cj > cc || (cj == cc && j > k));
+                    const int32_t *rk = kc[u];
+                    int p = 0;
+#pragma unroll
+                    for (int step = 16; step >= 1; step >>= 1)
+                        if (rk[p + step - 1] < j) p += step;
+                    if (later && rk[p] == j) a = a - lik * kv[u][p];
+                }
+            }
+            __syncwarp();  // the next batch overwrites the staged rows
         }
     }
     if (mine) lu[b + lane] = a;
@@ -183,9 +229,8 @@ msrsb_status ilu0_factor(const msrsb_mat *A, const uint8_t *colour, int ncol, co
     for (int c = 0; c < ncol; ++c) {
         int cnt = cptr_h[c + 1] - cptr_h[c];
         if (cnt == 0) continue;
-        ilu0_colour_kernel<TF><<<ceil_div((long)cnt * 32, 128), 128, 0, s>>>(cnt, rows + cptr_h[c], c, A->rowptr,
-                                                                             A->colidx, colour, dpos, lu, rdiag,
-                                                                             status);
+        ilu0_colour_kernel<TF><<<ceil_div((long)cnt * 32, 32 * kIluWarps), 32 * kIluWarps, 0, s>>>(
+            cnt, rows + cptr_h[c], c, A->rowptr, A->colidx, colour, dpos, lu, rdiag, status);
         MSRSB_LAUNCHED("ilu0_colour_kernel");
     }
     int h = 0;
