@@ -106,17 +106,34 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def smooth_bytes(n, nnz, W, esize):
-    """Algorithmic bytes of one restricted-smoothing pass: the filtered operator
-    (value + packed column per nonzero), P read once and written once, the
-    per-row scale and slot mask."""
-    return nnz * (esize + 4) + n * (2 * W * esize + esize + 1)
+def smooth_bytes(n, nnz_hat, W, esize):
+    """Algorithmic bytes of one restricted-smoothing pass: the entries of the
+    filtered operator that the pass needs (value + packed column each), P read
+    once and written once, the per-row scale and slot mask."""
+    return nnz_hat * (esize + 4) + n * (2 * W * esize + esize + 1)
+
+
+def kept_entries(c, ids):
+    """Entries of the filtered operator a restricted-smoothing pass needs
+    (Alg. 1 with the filter of Eq. 8): every diagonal, and every negative
+    off-diagonal a_ik (the filter zeroes the positive ones) whose row k holds
+    one of row i's coarse nodes in the same slot. ids: P's slot ids [n][W]."""
+    ip, ix, a = (np.asarray(c[k]) for k in ("indptr", "indices", "data"))
+    n = len(ip) - 1
+    r = np.repeat(np.arange(n), np.diff(ip))
+    off = (ix != r) & (a < 0)
+    ri, ki = r[off], ix[off]
+    share = np.zeros(len(ri), dtype=bool)
+    for s in range(ids.shape[1]):
+        share |= (ids[ri, s] >= 0) & (ids[ri, s] == ids[ki, s])
+    return n + int(share.sum())
 
 
 # DRAM bytes (read + write) of one smooth_kernel<float,8> launch on this
-# workload, from one ncu capture of the current kernel (cold L2, so an upper
-# bound for the warm passes of the loop): profiles/smooth_kernel_f32_w8_darcy64.md
-SMOOTH_TRAFFIC_BYTES = 65194496 + 1781504
+# workload, from one ncu capture of the current kernel and operator layout
+# (cold L2, so an upper bound for the warm passes of the loop):
+# profiles/smooth_kernel_f32_w8_darcy64.md
+SMOOTH_TRAFFIC_BYTES = 40150784 + 106752
 
 
 def apply_bytes(n, nnz, nnz_p, nc, W):
@@ -221,6 +238,7 @@ def gpu_arm(args, rank, world):
     h = M.msrsb_setup(A, g, M.opts(prec=M.msrsb.MSRSB_F32, **BASIS))
     p_ids = h.get_setup()[0]
     nnz_p = int((p_ids >= 0).sum())
+    nnz_hat = kept_entries(c, p_ids.cpu().numpy())
     v = torch.randn(n, dtype=torch.float64, device=dev, generator=torch.Generator(device=dev).manual_seed(7))
     z = torch.empty_like(v)
     for _ in range(3):
@@ -260,9 +278,9 @@ def gpu_arm(args, rank, world):
 
     hbm, peak_kind = peaks()
     W = 8
-    per_launch32 = smooth_bytes(n, nnz, W, 4)
+    per_launch32 = smooth_bytes(n, nnz_hat, W, 4)
     achieved = per_launch32 / (sm_ms32 / sm_l32 * 1e-3) / 1e9 if sm_l32 else None
-    per_launch64 = smooth_bytes(n, nnz, W, 8)
+    per_launch64 = smooth_bytes(n, nnz_hat, W, 8)
     achieved64 = per_launch64 / (sm_ms64 / sm_l64 * 1e-3) / 1e9 if sm_l64 else None
     out = {
         "metric": METRIC,
@@ -292,7 +310,7 @@ def gpu_arm(args, rank, world):
         "roofline": {"kernel": "smooth_kernel<float,8> (restricted smoothing, Alg. 1)", "bound": "hbm",
                      "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm if achieved else None, "traffic": SMOOTH_TRAFFIC_BYTES,
-                     "bytes_per_launch": per_launch32, "launches": sm_l32,
+                     "bytes_per_launch": per_launch32, "filtered_entries": nnz_hat, "launches": sm_l32,
                      "us_per_launch": sm_ms32 / sm_l32 * 1e3 if sm_l32 else None,
                      "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs, burst copy)"},
         "apply_roofline": {"op": "two-stage apply (Alg. 3), mixed form, L2 flushed before each", "bound": "hbm",

@@ -66,7 +66,7 @@ static void keep_pool_memory() {
 msrsb_status check_mat(const msrsb_mat *A);
 msrsb_status partition_launch(const msrsb_grid *g, int32_t *part, int32_t *cnode, int32_t *p_ids, uint8_t *skel,
                               uint8_t *colour, cudaStream_t s);
-msrsb_status sell_structure(int n, const int32_t *rowptr, Sell *S, cudaStream_t s);
+msrsb_status sell_structure(int n, const int32_t *rowptr, Sell *S, cudaStream_t s, const SellKeep *kept);
 msrsb_status sell_copy(const msrsb_mat *A, bool with_f32, Sell *S, cudaStream_t s);
 template <typename TA, typename TX, typename TV, typename TY, typename TACC>
 msrsb_status sell_spmv(const Sell &S, const TA *val, const TX *x, const TV *v, TY *y, bool resid, cudaStream_t s,
@@ -287,11 +287,9 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
     T *P = nullptr;
     MSRSB_TRY(dalloc(&P, nW * bd, s));
     h->p_val = P;
-    Sell S;
     T *scale = nullptr;
     uint8_t *vmask = nullptr;
     int *nzd = nullptr;
-    MSRSB_TRY(sell_structure(n, A.rowptr, &S, s));
     MSRSB_TRY(dalloc(&scale, n, s));
     MSRSB_TRY(dalloc(&vmask, n, s));
     MSRSB_TRY(dalloc(&nzd, 1, s));
@@ -303,16 +301,24 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
             MSRSB_CUDA(cudaMemcpyAsync(Pl, (const T *)p_init + l * nW, nW * sizeof(T), cudaMemcpyDeviceToDevice, s));
         else
             MSRSB_TRY(indicator<T>(n, W, h->part, h->p_ids, Pl, s));
-        MSRSB_TRY(sell_fill<T>(&A, l, 1, h->opts.basis.omega, h->p_ids, W, &S, scale, vmask, l == 0, nzd, s));
+        // the filtered operator of this component, its kept entries only
+        Sell S;
+        SellKeep keep;
+        keep.A = &A;
+        keep.comp = l;
+        keep.raw = 1;
+        keep.W = W;
+        keep.p_ids = h->p_ids;
+        MSRSB_TRY(sell_structure(n, A.rowptr, &S, s, &keep));
+        MSRSB_TRY(sell_fill<T>(&A, l, 1, h->opts.basis.omega, h->p_ids, W, &S, scale, vmask, 1, nzd, s));
         int it = 0;
         double e = 0.0;
         MSRSB_TRY(basis_loop<T>(n, W, S, l, scale, vmask, h->skel, Pl, &h->opts.basis, &it, &e, s));
         if (it > h->basis_iters) h->basis_iters = it;
         if (l == 0 || e > h->basis_e_it) h->basis_e_it = e;
-        dfree(S.val[l], s);
+        sell_free(&S, s);
     }
     MSRSB_CUDA(cudaMemcpyAsync(&h->n_zero_diag, nzd, sizeof(int), cudaMemcpyDeviceToHost, s));
-    sell_free(&S, s);
     dfree(scale, s);
     dfree(vmask, s);
     dfree(nzd, s);

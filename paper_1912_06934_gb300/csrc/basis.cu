@@ -250,7 +250,7 @@ template msrsb_status basis_loop<float>(int, int, const Sell &, int, const float
                                         float *, const msrsb_basis_opts *, int *, double *, cudaStream_t);
 
 msrsb_status check_mat(const msrsb_mat *A);
-msrsb_status sell_structure(int n, const int32_t *rowptr, Sell *S, cudaStream_t s);
+msrsb_status sell_structure(int n, const int32_t *rowptr, Sell *S, cudaStream_t s, const SellKeep *kept);
 template <typename T>
 msrsb_status sell_fill(const msrsb_mat *A, int comp, int raw, double omega, const int32_t *p_ids, int W, Sell *S,
                        T *scale, uint8_t *vmask, int write_col, int *n_zero_d, cudaStream_t s);
@@ -263,7 +263,13 @@ static msrsb_status build_basis_t(const msrsb_mat *Ahat, const int32_t *p_ids, c
     Sell S;
     T *scale = nullptr;
     uint8_t *vmask = nullptr;
-    MSRSB_TRY(sell_structure(n, Ahat->rowptr, &S, s));
+    SellKeep keep;  // Ahat is given filtered: keep its nonzero entries that share a slot
+    keep.A = Ahat;
+    keep.comp = 0;
+    keep.raw = 0;
+    keep.W = W;
+    keep.p_ids = p_ids;
+    MSRSB_TRY(sell_structure(n, Ahat->rowptr, &S, s, &keep));
     MSRSB_TRY(dalloc(&scale, n, s));
     MSRSB_TRY(dalloc(&vmask, n, s));
     MSRSB_TRY(sell_fill<T>(Ahat, 0, 0, o->omega, p_ids, W, &S, scale, vmask, 1, nullptr, s));

@@ -121,6 +121,14 @@ struct Sell {
     void *val[3] = {nullptr, nullptr, nullptr};
 };
 
+// Selects the entries of A_hat (component comp of A, filtered here when raw is
+// set) that the smoothing kernel streams, for sell_structure (see filter.cu).
+struct SellKeep {
+    const msrsb_mat *A = nullptr;
+    int comp = 0, raw = 1, W = 8;
+    const int32_t *p_ids = nullptr;
+};
+
 // work arrays of the coarse inverse while it runs (see coarse.cu)
 struct CoarseInverseWork {
     double *X = nullptr, *Xres = nullptr, *Fg = nullptr, *ig = nullptr;

@@ -44,12 +44,54 @@ __global__ void sell_width_kernel(int n, const int32_t *__restrict__ rowptr, int
     if ((threadIdx.x & 31) == 0 && i < ((n + 31) & ~31)) sizes[i >> 5] = len * kSell;
 }
 
-// Fill the sliced-ELL operator used by the smoothing kernel. For every entry
-// (i, k) the packed column holds k and an 8-bit mask whose bit s is set when
-// slot s of rows i and k holds the same coarse node (P_kJ contributes to
-// row i's entry J). Values: the filtered operator A_hat (component comp) when
-// `raw` is set the filter is applied here, else val already holds A_hat.
-// scale[i] = omega / D_hat_ii, or 0 where D_hat_ii = 0 (row left unchanged).
+// Slot mask of entry (i, k): bit s set when slot s of rows i and k holds the
+// same coarse node (P_kJ contributes to row i's entry J).
+__device__ __forceinline__ unsigned slot_mask(const int32_t (&my)[kMaxW], const int32_t *__restrict__ p_ids, int W,
+                                              int k) {
+    unsigned m = 0;
+    for (int c = 0; c < W; ++c) {
+        const int32_t id = p_ids[(long)k * W + c];
+        if (my[c] >= 0 && id == my[c]) m |= 1u << c;
+    }
+    return m;
+}
+
+// Off-diagonal value of A_hat (component comp) at entry e: min(a, 0) when the
+// filter is applied here (raw), else the given value.
+__device__ __forceinline__ double hat_offdiag(const double *__restrict__ val, long e, int bdim, int comp, int raw) {
+    return raw ? fmin(scalar_entry(val, e, bdim, comp), 0.0) : val[e];
+}
+
+// The smoothing kernel streams only the entries that can change P: the
+// diagonal, and off-diagonal entries of A_hat that are nonzero and share a
+// slot with row i. The filter zeroes every positive off-diagonal of A
+// (about half of a rotated anisotropic MPFA stencil), so this halves the
+// operator bytes of every smoothing pass. Width of every 32-row slice (times
+// 32) in kept entries.
+__global__ void sell_kept_width_kernel(int n, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                                       const double *__restrict__ val, int bdim, int comp, int raw,
+                                       const int32_t *__restrict__ p_ids, int W, int32_t *__restrict__ sizes) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int len = 0;
+    if (i < n) {
+        int32_t my[kMaxW];
+        for (int c = 0; c < W; ++c) my[c] = p_ids[(long)i * W + c];
+        for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+            const int k = colidx[e];
+            if (k == i || (hat_offdiag(val, e, bdim, comp, raw) != 0.0 && slot_mask(my, p_ids, W, k) != 0)) ++len;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) len = max(len, __shfl_xor_sync(0xffffffffu, len, o));
+    if ((threadIdx.x & 31) == 0 && i < ((n + 31) & ~31)) sizes[i >> 5] = len * kSell;
+}
+
+// Fill the sliced-ELL operator used by the smoothing kernel with the kept
+// entries of every row (see above), in CSR order: for each, the packed column
+// holds k and its slot mask. Values: the filtered operator A_hat (component
+// comp); when `raw` is set the filter is applied here, else val already holds
+// A_hat. scale[i] = omega / D_hat_ii, or 0 where D_hat_ii = 0 (row left
+// unchanged).
 template <typename T>
 __global__ void sell_fill_kernel(int n, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
                                  const double *__restrict__ val, int bdim, int comp, int raw, double omega,
@@ -78,25 +120,21 @@ __global__ void sell_fill_kernel(int n, const int32_t *__restrict__ rowptr, cons
         for (int e = rowptr[i]; e < rowptr[i + 1]; ++e)
             if (colidx[e] == i) dh = val[e];
     }
-    int r0 = rowptr[i], len = rowptr[i + 1] - r0;
-    for (int j = 0; j < width; ++j) {
-        long e = base + (long)j * kSell + lane;
-        if (j < len) {
-            int k = colidx[r0 + j];
-            double a = raw ? (k == i ? dh : fmin(scalar_entry(val, r0 + j, bdim, comp), 0.0)) : val[r0 + j];
-            if (write_col) {
-                unsigned m = 0;
-                for (int c = 0; c < W; ++c) {
-                    int32_t id = p_ids[(long)k * W + c];
-                    if (my[c] >= 0 && id == my[c]) m |= 1u << c;
-                }
-                scol[e] = (int32_t)((unsigned)k | (m << kColShift));
-            }
-            sval[e] = T(a);
-        } else {
-            if (write_col) scol[e] = i;  // mask 0: contributes nothing
-            sval[e] = T(0);
-        }
+    int j = 0;
+    for (int r = rowptr[i]; r < rowptr[i + 1] && j < width; ++r) {
+        const int k = colidx[r];
+        const double a = k == i ? dh : hat_offdiag(val, r, bdim, comp, raw);
+        const unsigned m = slot_mask(my, p_ids, W, k);
+        if (k != i && (a == 0.0 || m == 0)) continue;  // cannot change P
+        const long e = base + (long)j * kSell + lane;
+        if (write_col) scol[e] = (int32_t)((unsigned)k | (m << kColShift));
+        sval[e] = T(a);
+        ++j;
+    }
+    for (; j < width; ++j) {
+        const long e = base + (long)j * kSell + lane;
+        if (write_col) scol[e] = i;  // mask 0: contributes nothing
+        sval[e] = T(0);
     }
     scale[i] = dh != 0.0 ? T(omega / dh) : T(0);
     if (vmask) {
@@ -108,16 +146,25 @@ __global__ void sell_fill_kernel(int n, const int32_t *__restrict__ rowptr, cons
     if (n_zero && dh == 0.0) atomicAdd(n_zero, 1);
 }
 
-// Build the slice structure (widths + offsets) of the scalar pattern of A.
-msrsb_status sell_structure(int n, const int32_t *rowptr, Sell *S, cudaStream_t s) {
+// Build the slice structure (widths + offsets): of the scalar pattern of A
+// (kept == nullptr), or of the entries the smoothing kernel keeps for
+// component kept->comp (see sell_kept_width_kernel).
+msrsb_status sell_structure(int n, const int32_t *rowptr, Sell *S, cudaStream_t s, const SellKeep *kept) {
     S->n = n;
     S->nslices = ceil_div(n, kSell);
     int32_t *sizes = nullptr;
     MSRSB_TRY(dalloc(&sizes, S->nslices + 1, s));
     MSRSB_TRY(dalloc(&S->slice_ptr, S->nslices + 1, s));
     MSRSB_CUDA(cudaMemsetAsync(sizes, 0, (S->nslices + 1) * sizeof(int32_t), s));
-    sell_width_kernel<<<ceil_div((long)S->nslices * kSell, 256), 256, 0, s>>>(n, rowptr, sizes);
-    MSRSB_LAUNCHED("sell_width_kernel");
+    if (kept) {
+        const msrsb_mat *A = kept->A;
+        sell_kept_width_kernel<<<ceil_div((long)S->nslices * kSell, 256), 256, 0, s>>>(
+            n, A->rowptr, A->colidx, A->val, A->bdim, kept->comp, kept->raw, kept->p_ids, kept->W, sizes);
+        MSRSB_LAUNCHED("sell_kept_width_kernel");
+    } else {
+        sell_width_kernel<<<ceil_div((long)S->nslices * kSell, 256), 256, 0, s>>>(n, rowptr, sizes);
+        MSRSB_LAUNCHED("sell_width_kernel");
+    }
     size_t tmp = 0;
     MSRSB_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp, sizes, S->slice_ptr, S->nslices + 1, s));
     void *tbuf = nullptr;
@@ -177,7 +224,7 @@ __global__ void sell_copy_kernel(int n, const int32_t *__restrict__ rowptr, cons
 }
 
 msrsb_status sell_copy(const msrsb_mat *A, bool with_f32, Sell *S, cudaStream_t s) {
-    MSRSB_TRY(sell_structure(A->nrows, A->rowptr, S, s));
+    MSRSB_TRY(sell_structure(A->nrows, A->rowptr, S, s, nullptr));
     double *v64 = nullptr;
     float *v32 = nullptr;
     MSRSB_TRY(dalloc(&v64, S->entries, s));
