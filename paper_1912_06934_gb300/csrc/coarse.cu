@@ -195,73 +195,136 @@ __global__ void __launch_bounds__(256) gauss_jordan_kernel(int n, double *__rest
     }
 }
 
-// Resident variant for coarse systems whose columns fit in shared memory:
-// every CTA keeps the columns it owns in shared memory for the whole
-// inversion; the next panel of GJ_RS columns is published by its owners into
-// a small double-buffered global array before each grid-wide barrier. After
-// the barrier every CTA replays the panel's steps on its shared copy of the
-// panel (to learn each step's pivot and column f) and applies them to its own
-// columns. Same arithmetic as above, one barrier per GJ_RS pivots, and no
-// per-panel traffic of the owned columns.
+// Resident look-ahead variant for coarse systems whose columns fit in shared
+// memory. Every CTA keeps whole panels of GJ_RS columns (cols_per, a multiple
+// of GJ_RS) in shared memory for the whole inversion. The owner of panel q
+// factors it as soon as it has applied panels 0..q-1 to its columns (argmax,
+// row swap, 1/pivot and the f columns, as in the steps above) and publishes
+// the result in panel q's own slot of a global array, then raises a
+// publication counter to q+1; every other CTA applies panel q to its columns
+// once the counter has reached q+1. The counter replaces a grid-wide barrier
+// per panel, and the panel is factored once instead of in every CTA: the
+// critical path is the chain of panel owners. Same arithmetic as the steps
+// above, in the same order. The launch is cooperative (all CTAs co-resident),
+// every wait is bounded, and a zero pivot publishes an abort (-1) that
+// releases every waiting CTA.
 constexpr int GJ_RS = 4;
+constexpr int kGjSpinLimit = 1 << 23;               // polls of the counter, 64 ns naps between them
+constexpr unsigned long long kGjWaitNs = 500000000ull;  // and at most 0.5 s of wall time per wait
+constexpr int kGjTimeout = -2;                          // status: a wait for a panel gave up
 
-__global__ void __launch_bounds__(256) gauss_jordan_resident_kernel(int n, const double *__restrict__ Xin,
+__device__ __forceinline__ int load_counter(const int *c) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(c) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__global__ void __launch_bounds__(256) gauss_jordan_resident_kernel(int n, int cols_per,
+                                                                    const double *__restrict__ Xin,
                                                                     double *__restrict__ Xout,
-                                                                    double *__restrict__ pub, int *__restrict__ perm,
-                                                                    int *__restrict__ status) {
-    cg::grid_group grid = cg::this_grid();
+                                                                    double *__restrict__ pubF, int *__restrict__ pubP,
+                                                                    double *__restrict__ pubI, int *counter,
+                                                                    int *__restrict__ perm, int *status) {
     extern __shared__ double sm[];
-    const int cols_per = (n + gridDim.x - 1) / gridDim.x;
     const int c0 = blockIdx.x * cols_per, c1 = min(n, c0 + cols_per), na = max(0, c1 - c0);
+    if (na == 0) return;
     double *Own = sm;                         // [cols_per][n]
-    double *Pnl = sm + (long)cols_per * n;    // panel copy, becomes the f columns, [GJ_RS][n]
+    double *Pnl = sm + (long)cols_per * n;    // panel being applied: its f columns, [GJ_RS][n]
     __shared__ double s_best[8], s_inv[GJ_RS], s_xk[GJ_RS], s_xo[64];
-    __shared__ int s_idx[8], s_piv[GJ_RS];
+    __shared__ int s_idx[8], s_piv[GJ_RS], s_stop;
     for (int q = threadIdx.x; q < na * n; q += blockDim.x) Own[q] = Xin[(long)c0 * n + q];
-    __syncthreads();  // the publication below reads elements other threads loaded
-    // publish the first panel
-    for (int c = 0; c < na; ++c) {
-        const int j = c0 + c;
-        if (j < GJ_RS)
-            for (int i = threadIdx.x; i < n; i += blockDim.x) pub[(long)j * n + i] = Own[(long)c * n + i];
-    }
-    __threadfence();
-    grid.sync();
-    for (int k0 = 0, it = 0; k0 < n; k0 += GJ_RS, ++it) {
-        const int nb = min(GJ_RS, n - k0);
-        const double *pb = pub + (long)(it & 1) * GJ_RS * n;
-        for (int q = threadIdx.x; q < nb * n; q += blockDim.x) Pnl[q] = __ldcg(pb + q);
-        __syncthreads();
-        // replay the panel: pivots, 1/pivots and the f columns (kept in Pnl)
-        for (int t = 0; t < nb; ++t) {
-            const int k = k0 + t;
-            double best;
-            int p;
-            block_argmax(Pnl + (long)t * n, k, n, s_best, s_idx, &best, &p);
-            const double piv = p < n ? Pnl[(long)t * n + p] : 0.0;
-            if (piv == 0.0 || !isfinite(piv)) {  // every CTA leaves at the same step
-                if (blockIdx.x == 0 && threadIdx.x == 0) *status = 1 + k;
-                return;
+    if (threadIdx.x == 0) s_stop = 0;
+    __syncthreads();
+    const int npan = (n + GJ_RS - 1) / GJ_RS;
+    for (int pq = 0; pq < npan; ++pq) {
+        const int k0 = pq * GJ_RS, nb = min(GJ_RS, n - k0);
+        if (k0 >= c0 && k0 < c1) {
+            // owner: factor the panel from the own columns k0.., publish it
+            const long o0 = (long)(k0 - c0) * n;
+            for (int q = threadIdx.x; q < nb * n; q += blockDim.x) Pnl[q] = Own[o0 + q];
+            __syncthreads();
+            for (int t = 0; t < nb; ++t) {
+                const int k = k0 + t;
+                double best;
+                int p;
+                block_argmax(Pnl + (long)t * n, k, n, s_best, s_idx, &best, &p);
+                const double piv = p < n ? Pnl[(long)t * n + p] : 0.0;
+                if (piv == 0.0 || !isfinite(piv)) {  // singular: stop every CTA
+                    if (threadIdx.x == 0) {
+                        atomicCAS(status, 0, 1 + k);
+                        __threadfence();
+                        atomicExch(counter, -1);
+                    }
+                    return;
+                }
+                if (threadIdx.x >= t && threadIdx.x < nb && p != k) {
+                    double a = Pnl[(long)threadIdx.x * n + k];
+                    Pnl[(long)threadIdx.x * n + k] = Pnl[(long)threadIdx.x * n + p];
+                    Pnl[(long)threadIdx.x * n + p] = a;
+                }
+                if (threadIdx.x == 0) {
+                    s_piv[t] = p;
+                    s_inv[t] = 1.0 / piv;
+                    perm[k] = p;
+                }
+                __syncthreads();
+                const double inv = s_inv[t];
+                if (threadIdx.x > t && threadIdx.x < nb) s_xk[threadIdx.x] = Pnl[(long)threadIdx.x * n + k] * inv;
+                __syncthreads();
+                const double *f = Pnl + (long)t * n;
+                for (int c = t + 1; c < nb; ++c) {
+                    const double xk = s_xk[c];
+                    double *col = Pnl + (long)c * n;
+                    for (int i = threadIdx.x; i < n; i += blockDim.x) col[i] = i == k ? xk : col[i] - f[i] * xk;
+                }
+                __syncthreads();
             }
-            if (threadIdx.x >= t && threadIdx.x < nb && p != k) {
-                double a = Pnl[(long)threadIdx.x * n + k];
-                Pnl[(long)threadIdx.x * n + k] = Pnl[(long)threadIdx.x * n + p];
-                Pnl[(long)threadIdx.x * n + p] = a;
+            double *pf = pubF + (long)pq * GJ_RS * n;
+            for (int q = threadIdx.x; q < nb * n; q += blockDim.x) pf[q] = Pnl[q];
+            if (threadIdx.x < nb) {
+                pubP[pq * GJ_RS + threadIdx.x] = s_piv[threadIdx.x];
+                pubI[pq * GJ_RS + threadIdx.x] = s_inv[threadIdx.x];
             }
+            __threadfence();
+            __syncthreads();
+            // panels are published in order, so the counter holds pq here unless
+            // another CTA has aborted (-1), which must stay
+            if (threadIdx.x == 0) atomicCAS(counter, pq, pq + 1);
+        } else {
+            // wait until panel pq is published (bounded), then fetch it through L2
             if (threadIdx.x == 0) {
-                s_piv[t] = p;
-                s_inv[t] = 1.0 / piv;
-                if (blockIdx.x == 0) perm[k] = p;
+                const unsigned long long t0 = global_ns();
+                int it = 0;
+                for (;;) {
+                    const int v = load_counter(counter);
+                    if (v > pq) break;
+                    if (v < 0) {
+                        s_stop = 1;
+                        break;
+                    }
+                    if (++it > kGjSpinLimit || global_ns() - t0 > kGjWaitNs) {  // give up, release the others
+                        atomicCAS(status, 0, kGjTimeout);
+                        __threadfence();
+                        atomicExch(counter, -1);
+                        s_stop = 1;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+                __threadfence();
             }
             __syncthreads();
-            const double inv = s_inv[t];
-            if (threadIdx.x > t && threadIdx.x < nb) s_xk[threadIdx.x] = Pnl[(long)threadIdx.x * n + k] * inv;
-            __syncthreads();
-            const double *f = Pnl + (long)t * n;
-            for (int c = t + 1; c < nb; ++c) {
-                const double xk = s_xk[c];
-                double *col = Pnl + (long)c * n;
-                for (int i = threadIdx.x; i < n; i += blockDim.x) col[i] = i == k ? xk : col[i] - f[i] * xk;
+            if (s_stop) return;
+            const double *pf = pubF + (long)pq * GJ_RS * n;
+            for (int q = threadIdx.x; q < nb * n; q += blockDim.x) Pnl[q] = __ldcg(pf + q);
+            if (threadIdx.x < nb) {
+                s_piv[threadIdx.x] = __ldcg(pubP + pq * GJ_RS + threadIdx.x);
+                s_inv[threadIdx.x] = __ldcg(pubI + pq * GJ_RS + threadIdx.x);
             }
             __syncthreads();
         }
@@ -299,16 +362,6 @@ __global__ void __launch_bounds__(256) gauss_jordan_resident_kernel(int n, const
             }
             __syncthreads();
         }
-        // publish the next panel
-        const int n0 = k0 + GJ_RS, n1 = min(n, n0 + GJ_RS);
-        double *pn = pub + (long)((it + 1) & 1) * GJ_RS * n;
-        for (int c = 0; c < na; ++c) {
-            const int j = c0 + c;
-            if (j >= n0 && j < n1)
-                for (int i = threadIdx.x; i < n; i += blockDim.x) pn[(long)(j - n0) * n + i] = Own[(long)c * n + i];
-        }
-        __threadfence();
-        grid.sync();
     }
     for (int q = threadIdx.x; q < na * n; q += blockDim.x) Xout[(long)c0 * n + q] = Own[q];
 }
@@ -373,14 +426,16 @@ msrsb_status coarse_inverse_launch(int n, const double *Ac, double *Ainv, Coarse
     MSRSB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     MSRSB_TRY(dalloc(&w->X, (size_t)n * n, s));
     MSRSB_TRY(dalloc(&w->perm, n, s));
-    MSRSB_TRY(dalloc(&w->status, 1, s));
+    MSRSB_TRY(dalloc(&w->status, 2, s));  // [0] status, [1] publication counter of the resident variant
     dim3 tb(32, 8), tg(ceil_div(n, 32), ceil_div(n, 32));
     transpose_kernel<<<tg, tb, 0, s>>>(n, Ac, w->X);
     MSRSB_LAUNCHED("transpose_kernel");
-    MSRSB_CUDA(cudaMemsetAsync(w->status, 0, sizeof(int), s));
-    // resident variant when every CTA's columns fit in shared memory
-    const int grid_r = sms < n ? sms : n;
-    const int cols_per = (n + grid_r - 1) / grid_r;
+    MSRSB_CUDA(cudaMemsetAsync(w->status, 0, 2 * sizeof(int), s));
+    // resident look-ahead variant when every CTA's panels fit in shared memory
+    const int per_cta = ceil_div(n, (long)GJ_RS * sms);   // panels per CTA
+    const int cols_per = GJ_RS * per_cta;
+    const int grid_r = ceil_div(n, cols_per);
+    const int npan = ceil_div(n, GJ_RS);
     const size_t smem_r = (size_t)(cols_per + GJ_RS) * n * sizeof(double);
     double *Xres = nullptr;
     if (smem_r <= (size_t)kGjResidentSmemMax && cols_per <= 64) {
@@ -390,13 +445,17 @@ msrsb_status coarse_inverse_launch(int n, const double *Ac, double *Ainv, Coarse
         MSRSB_CUDA(cudaFuncSetAttribute(gauss_jordan_resident_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         kGjResidentSmemMax));
         MSRSB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gauss_jordan_resident_kernel, 256, smem_r));
-        if (occ > 0) {
-            MSRSB_TRY(dalloc(&w->Fg, (size_t)2 * GJ_RS * n, s));  // publication buffer
+        if (occ > 0 && grid_r <= occ * sms) {
+            // publication slots: every panel's f columns, pivots, reciprocal pivots
+            MSRSB_TRY(dalloc(&w->Fg, (size_t)npan * GJ_RS * n, s));
+            MSRSB_TRY(dalloc(&w->pg, (size_t)npan * GJ_RS, s));
+            MSRSB_TRY(dalloc(&w->ig, (size_t)npan * GJ_RS, s));
             MSRSB_TRY(dalloc(&Xres, (size_t)n * n, s));
             w->Xres = Xres;
-            int nn = n;
-            void *args[] = {(void *)&nn, (void *)&w->X, (void *)&Xres, (void *)&w->Fg, (void *)&w->perm,
-                            (void *)&w->status};
+            int nn = n, cp = cols_per;
+            int *counter = w->status + 1;
+            void *args[] = {(void *)&nn,    (void *)&cp,   (void *)&w->X,    (void *)&Xres,   (void *)&w->Fg,
+                            (void *)&w->pg, (void *)&w->ig, (void *)&counter, (void *)&w->perm, (void *)&w->status};
             MSRSB_CUDA(cudaLaunchCooperativeKernel((void *)gauss_jordan_resident_kernel, grid_r, 256, args, smem_r, s));
             MSRSB_LAUNCHED("gauss_jordan_resident_kernel");
         }
@@ -451,6 +510,8 @@ msrsb_status coarse_inverse_finish(CoarseInverseWork *w, cudaStream_t s) {
     dfree(w->perm, s);
     dfree(w->src, s);
     dfree(w->status, s);
+    if (w->h_status == kGjTimeout)
+        return fail(MSRSB_ETIMEOUT, "coarse inverse: a wait for a published panel gave up");
     if (w->h_status)
         return fail(MSRSB_EBREAKDOWN, "coarse operator is singular (zero pivot at column %d)", w->h_status - 1);
     return MSRSB_OK;
