@@ -270,15 +270,26 @@ msrsb_status msrsb_pattern_outer(const msrsb_mat *A, double alpha, const double 
                                  cudaStream_t stream);
 
 /* Measurement support (no counterpart in the paper). msrsb_profile(1)
- * resets the counters and brackets every launch of the restricted-smoothing
- * kernel (Alg. 1) with CUDA events on its stream; msrsb_profile(0) resets and
+ * resets the counters and brackets every Alg. 1 loop (the restricted-smoothing
+ * passes of one basis family) with one pair of CUDA events on its stream, so
+ * that the passes keep their programmatic overlap; msrsb_profile(0) resets and
  * stops the event timing. msrsb_profile_read returns the number of kernel
  * launches the library made since the last reset (every kernel of csrc/, not
- * counting CUB's sort/scan kernels), and the number and summed device time
- * (ms) of smoothing launches that did work (launches that left at once after
- * convergence are excluded). Host bookkeeping only. */
+ * counting CUB's sort/scan kernels), the number of smoothing launches that did
+ * work (launches that left at once after convergence are excluded) and the
+ * summed device time (ms) of the loops they ran in. Host bookkeeping only. */
 msrsb_status msrsb_profile(int32_t enable);
 msrsb_status msrsb_profile_read(int64_t *launches_h, int64_t *smooth_launches_h, double *smooth_ms_h);
+
+/* Self-test of the bounded device-side wait (no counterpart in the paper).
+ * The coarse inverse's CTAs wait on a publication counter with a wall-time and
+ * poll limit, after which the waiting CTA records a time-out status and
+ * releases the others. This launches one thread waiting on a counter that
+ * nothing raises, with a limit of limit_ms (0 < limit_ms <= 1000), and
+ * synchronises `stream`. Returns MSRSB_ETIMEOUT when the wait gave up and
+ * reported it as designed (the expected outcome; the context stays usable),
+ * MSRSB_EINVAL for a bad limit or any other outcome. */
+msrsb_status msrsb_wait_selftest(double limit_ms, cudaStream_t stream);
 
 /* Message for the last non-OK status returned on this host thread. */
 const char *msrsb_last_error(void);

@@ -93,6 +93,7 @@ msrsb_status coarse_inverse(int n, const double *Ac, double *Ainv, cudaStream_t 
 msrsb_status coarse_inverse_launch(int n, const double *Ac, double *Ainv, CoarseInverseWork *w, cudaStream_t s);
 msrsb_status coarse_inverse_finish(CoarseInverseWork *w, cudaStream_t s);
 msrsb_status gemv(int n, const double *M, const double *x, double *y, float *y32, cudaStream_t s);
+msrsb_status wait_selftest(double limit_ms, cudaStream_t s);
 msrsb_status colour_classes(int n, const uint8_t *colour, int ncol, int32_t **rows, int32_t *ptr_h, cudaStream_t s);
 template <typename TF>
 msrsb_status ilu0_factor(const msrsb_mat *A, const uint8_t *colour, int ncol, const int32_t *rows,
@@ -942,6 +943,10 @@ extern "C" msrsb_status msrsb_profile(int32_t enable) {
     msrsb::g_smooth_ms = 0.0;
     msrsb::g_smooth_lock.store(0);
     return MSRSB_OK;
+}
+
+extern "C" msrsb_status msrsb_wait_selftest(double limit_ms, cudaStream_t stream) {
+    return msrsb::wait_selftest(limit_ms, stream);
 }
 
 extern "C" msrsb_status msrsb_profile_read(int64_t *launches_h, int64_t *smooth_launches_h, double *smooth_ms_h) {

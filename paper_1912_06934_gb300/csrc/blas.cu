@@ -163,6 +163,7 @@ __global__ void __launch_bounds__(256) sell_spmv_kernel(int n, const int32_t *__
         if (t + 1 < width) acc1 = fma(TACC(R.val[t + 1]), TACC(__ldg(x + R.col[t + 1])), acc1);
     }
     int j = kSellPre;
+#pragma unroll 4
     for (; j + 1 < width; j += 2) {
         acc0 = fma(TACC(__ldg(vp + (j << 5))), TACC(__ldg(x + __ldg(cp + (j << 5)))), acc0);
         acc1 = fma(TACC(__ldg(vp + ((j + 1) << 5))), TACC(__ldg(x + __ldg(cp + ((j + 1) << 5)))), acc1);
@@ -752,6 +753,7 @@ __global__ void __launch_bounds__(256) sell_spmv_df_kernel(int n, const int32_t 
         if (t + 1 < width) acc1 = fma(R.val[t + 1], __ldg(x + R.col[t + 1]), acc1);
     }
     int j = kSellPre;
+#pragma unroll 4
     for (; j + 1 < width; j += 2) {
         acc0 = fma(__ldg(vp + (j << 5)), __ldg(x + __ldg(cp + (j << 5))), acc0);
         acc1 = fma(__ldg(vp + ((j + 1) << 5)), __ldg(x + __ldg(cp + ((j + 1) << 5))), acc1);

@@ -224,6 +224,31 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
+// One thread waits until *counter > pq. Returns true when the caller may go
+// on; false when another CTA aborted (*counter < 0) or when the wait gave up
+// after kGjSpinLimit polls or limit_ns of wall time, in which case it records
+// kGjTimeout in *status and publishes the abort itself, releasing every other
+// waiter. Acquire ordering: data published before the counter was raised is
+// visible (through L2) after a true return.
+__device__ bool wait_counter_above(int *counter, int pq, int *status, unsigned long long limit_ns) {
+    const unsigned long long t0 = global_ns();
+    int it = 0;
+    for (;;) {
+        const int v = load_counter(counter);
+        if (v > pq) break;
+        if (v < 0) return false;
+        if (++it > kGjSpinLimit || global_ns() - t0 > limit_ns) {
+            atomicCAS(status, 0, kGjTimeout);
+            __threadfence();
+            atomicExch(counter, -1);
+            return false;
+        }
+        __nanosleep(64);
+    }
+    __threadfence();
+    return true;
+}
+
 __global__ void __launch_bounds__(256) gauss_jordan_resident_kernel(int n, int cols_per,
                                                                     const double *__restrict__ Xin,
                                                                     double *__restrict__ Xout,
@@ -297,27 +322,7 @@ __global__ void __launch_bounds__(256) gauss_jordan_resident_kernel(int n, int c
             if (threadIdx.x == 0) atomicCAS(counter, pq, pq + 1);
         } else {
             // wait until panel pq is published (bounded), then fetch it through L2
-            if (threadIdx.x == 0) {
-                const unsigned long long t0 = global_ns();
-                int it = 0;
-                for (;;) {
-                    const int v = load_counter(counter);
-                    if (v > pq) break;
-                    if (v < 0) {
-                        s_stop = 1;
-                        break;
-                    }
-                    if (++it > kGjSpinLimit || global_ns() - t0 > kGjWaitNs) {  // give up, release the others
-                        atomicCAS(status, 0, kGjTimeout);
-                        __threadfence();
-                        atomicExch(counter, -1);
-                        s_stop = 1;
-                        break;
-                    }
-                    __nanosleep(64);
-                }
-                __threadfence();
-            }
+            if (threadIdx.x == 0 && !wait_counter_above(counter, pq, status, kGjWaitNs)) s_stop = 1;
             __syncthreads();
             if (s_stop) return;
             const double *pf = pubF + (long)pq * GJ_RS * n;
@@ -556,6 +561,27 @@ __global__ void gemv_kernel(int n, const double *__restrict__ M, const double *_
         y[row] = s;
         if (y32) y32[row] = (float)s;
     }
+}
+
+// The bounded wait of the coarse inverse on a counter that nothing raises:
+// one thread waits until its limit and must report the time-out.
+__global__ void wait_selftest_kernel(int *counter, int *status, unsigned long long limit_ns) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) wait_counter_above(counter, 0, status, limit_ns);
+}
+
+msrsb_status wait_selftest(double limit_ms, cudaStream_t s) {
+    if (!(limit_ms > 0.0 && limit_ms <= 1000.0)) return fail(MSRSB_EINVAL, "limit_ms must be in (0, 1000]");
+    int *d = nullptr;  // [0] counter, [1] status
+    MSRSB_TRY(dalloc(&d, 2, s));
+    MSRSB_CUDA(cudaMemsetAsync(d, 0, 2 * sizeof(int), s));
+    wait_selftest_kernel<<<1, 32, 0, s>>>(d, d + 1, (unsigned long long)(limit_ms * 1e6));
+    MSRSB_LAUNCHED("wait_selftest_kernel");
+    int h[2] = {0, 0};
+    MSRSB_CUDA(cudaMemcpyAsync(h, d, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    MSRSB_CUDA(cudaStreamSynchronize(s));
+    dfree(d, s);
+    if (h[1] == kGjTimeout && h[0] == -1) return fail(MSRSB_ETIMEOUT, "bounded wait expired as expected");
+    return fail(MSRSB_EINVAL, "bounded wait self-test: status %d, counter %d", h[1], h[0]);
 }
 
 msrsb_status gemv(int n, const double *M, const double *x, double *y, float *y32, cudaStream_t s) {

@@ -21,7 +21,7 @@ MSRSB_GMRES, MSRSB_PCG, MSRSB_RICHARDSON = 0, 1, 2
 
 EXPORTS = ["msrsb_partition_size", "msrsb_partition", "msrsb_filter", "msrsb_build_basis", "msrsb_coarse_op",
            "msrsb_setup", "msrsb_apply", "msrsb_solve", "msrsb_get_setup", "msrsb_get_info", "msrsb_destroy",
-           "msrsb_solve_host", "msrsb_profile", "msrsb_profile_read", "msrsb_build_basis_noalloc",
+           "msrsb_solve_host", "msrsb_profile", "msrsb_profile_read", "msrsb_wait_selftest", "msrsb_build_basis_noalloc",
            "msrsb_solve_ensemble", "msrsb_transpose_values", "msrsb_pattern_outer", "msrsb_last_error"]
 
 
@@ -282,6 +282,15 @@ def msrsb_destroy(h):
 
 def msrsb_profile(enable):
     _check(load().msrsb_profile(ctypes.c_int32(1 if enable else 0)))
+
+
+def msrsb_wait_selftest(limit_ms=20.0, stream=None):
+    """Run the bounded-wait self-test (see include/msrsb.h); returns the raw
+    status, MSRSB_ETIMEOUT when the wait expired and reported it."""
+    L = load()
+    L.msrsb_wait_selftest.restype = ctypes.c_int
+    L.msrsb_wait_selftest.argtypes = [ctypes.c_double, ctypes.c_void_p]
+    return int(L.msrsb_wait_selftest(float(limit_ms), _stream(stream)))
 
 
 def msrsb_profile_read():

@@ -45,3 +45,14 @@ def test_product_path_has_no_oracle_import():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dp, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
+
+
+def test_wait_selftest_rejects_bad_limits_on_the_host():
+    # the limit is checked before any device work, so this runs without a GPU
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1912_06934_gb300 import msrsb as B
+    lib = B.load()
+    lib.msrsb_wait_selftest.argtypes = [ctypes.c_double, ctypes.c_void_p]
+    for lim in (0.0, -1.0, 1000.5, float("nan")):
+        assert lib.msrsb_wait_selftest(lim, None) == B.MSRSB_EINVAL
