@@ -176,6 +176,81 @@ __global__ void __launch_bounds__(128) ptap_kernel(int n, int W, int nc, int nco
     }
 }
 
+// Scalar operators: the same two passes with the accumulators off local
+// memory. Pass 1 keeps each thread's NCODE sums in a shared-memory column
+// (the code index is data-dependent) and writes the CTA's contiguous block
+// of AP coalesced; pass 2 takes the code count as a compile-time constant so
+// that its sums stay in registers. Same FMA sequence per sum as above.
+constexpr int kAp1Threads = 128;
+
+template <typename T, int NCODE>
+__global__ void __launch_bounds__(kAp1Threads) ap1_kernel(int n, int W, const int32_t *__restrict__ rowptr,
+                                                         const int32_t *__restrict__ colidx,
+                                                         const double *__restrict__ val,
+                                                         const int32_t *__restrict__ p_ids, const T *__restrict__ P,
+                                                         const int8_t *__restrict__ code, double *__restrict__ AP) {
+    __shared__ double s_acc[NCODE][kAp1Threads];
+    const int tx = threadIdx.x, i0 = blockIdx.x * kAp1Threads, i = i0 + tx;
+#pragma unroll
+    for (int q = 0; q < NCODE; ++q) s_acc[q][tx] = 0.0;
+    if (i < n) {
+        for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+            const int k = colidx[e];
+            const double a = val[e];
+            for (int t = 0; t < W; ++t) {
+                const int L = p_ids[(long)k * W + t];
+                if (L < 0) continue;
+                const int sc = code[L];
+                s_acc[sc][tx] = fma(a, (double)P[(long)k * W + t], s_acc[sc][tx]);
+            }
+        }
+    }
+    __syncthreads();
+    const int rows = min(kAp1Threads, n - i0);
+    double *out = AP + (long)i0 * NCODE;
+    for (int idx = tx; idx < rows * NCODE; idx += kAp1Threads) out[idx] = s_acc[idx % NCODE][idx / NCODE];
+}
+
+template <typename T, int NCODE>
+__global__ void __launch_bounds__(128) ptap1_kernel(int n, int W, int nc, int dim, int nb0, int nb1, int nb2,
+                                                    const T *__restrict__ P, const int32_t *__restrict__ pt_ptr,
+                                                    const int32_t *__restrict__ pt_rows,
+                                                    const int8_t *__restrict__ jslot, const double *__restrict__ AP,
+                                                    double *__restrict__ Ac) {
+    __shared__ double red[NCODE][4];
+    const int J = blockIdx.x;
+    const int sj = jslot[J];
+    double acc[NCODE];
+#pragma unroll
+    for (int q = 0; q < NCODE; ++q) acc[q] = 0.0;
+    for (int r = pt_ptr[J] + threadIdx.x; r < pt_ptr[J + 1]; r += blockDim.x) {
+        const int i = pt_rows[r];
+        const double *api = AP + (long)i * NCODE;
+        const double p = (double)P[(long)i * W + sj];
+#pragma unroll
+        for (int q = 0; q < NCODE; ++q) acc[q] = fma(p, api[q], acc[q]);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NCODE; ++q) {
+        const double v = warp_sum(acc[q]);
+        if (lane == 0) red[q][warp] = v;
+    }
+    __syncthreads();
+    const int j0 = J % nb0, j1 = (J / nb0) % nb1, j2 = dim == 3 ? J / (nb0 * nb1) : 0;
+    for (int q = threadIdx.x; q < NCODE; q += blockDim.x) {
+        const double v = (red[q][0] + red[q][1]) + (red[q][2] + red[q][3]);
+        const int r0 = q % 3, r1 = (q / 3) % 3, r2 = q / 9;
+        // the coarse coordinate in {J_d-1, J_d, J_d+1} with residue r_d
+        const int L0 = j0 - 1 + ((r0 - (j0 - 1)) % 3 + 3) % 3;
+        const int L1 = j1 - 1 + ((r1 - (j1 - 1)) % 3 + 3) % 3;
+        const int L2 = dim == 3 ? j2 - 1 + ((r2 - (j2 - 1)) % 3 + 3) % 3 : 0;
+        if (L0 < 0 || L0 >= nb0 || L1 < 0 || L1 >= nb1 || L2 < 0 || L2 >= nb2) continue;
+        const int L = L0 + nb0 * (L1 + nb1 * L2);
+        Ac[(long)J * nc + L] = v;
+    }
+}
+
 template <typename T>
 msrsb_status galerkin(const msrsb_mat *A, const msrsb_grid *g, int W, int nc, const int32_t *p_ids, const T *P,
                       const int32_t *pt_ptr, const int32_t *pt_rows, const int8_t *jslot, double *Ac,
@@ -198,12 +273,18 @@ msrsb_status galerkin(const msrsb_mat *A, const msrsb_grid *g, int W, int nc, co
     MSRSB_CUDA(cudaMemsetAsync(Ac, 0, (size_t)nC * nC * sizeof(double), s));
     coarse_code_kernel<<<ceil_div(nc, 256), 256, 0, s>>>(nc, nb[0], nb[1], dim, code);
     MSRSB_LAUNCHED("coarse_code_kernel");
-    if (BD == 1) {
-        ap_kernel<T, 1><<<ceil_div(n, 128), 128, 0, s>>>(n, W, ncode, A->rowptr, A->colidx, A->val, p_ids, P, code, AP);
-        MSRSB_LAUNCHED("ap_kernel");
-        ptap_kernel<T, 1><<<nc, 128, 0, s>>>(n, W, nc, ncode, dim, nb[0], nb[1], nb[2], P, pt_ptr, pt_rows, jslot, AP,
-                                            Ac);
-        MSRSB_LAUNCHED("ptap_kernel");
+    if (BD == 1 && ncode == 27) {
+        ap1_kernel<T, 27><<<ceil_div(n, kAp1Threads), kAp1Threads, 0, s>>>(n, W, A->rowptr, A->colidx, A->val, p_ids,
+                                                                           P, code, AP);
+        MSRSB_LAUNCHED("ap1_kernel");
+        ptap1_kernel<T, 27><<<nc, 128, 0, s>>>(n, W, nc, dim, nb[0], nb[1], nb[2], P, pt_ptr, pt_rows, jslot, AP, Ac);
+        MSRSB_LAUNCHED("ptap1_kernel");
+    } else if (BD == 1) {
+        ap1_kernel<T, 9><<<ceil_div(n, kAp1Threads), kAp1Threads, 0, s>>>(n, W, A->rowptr, A->colidx, A->val, p_ids,
+                                                                          P, code, AP);
+        MSRSB_LAUNCHED("ap1_kernel");
+        ptap1_kernel<T, 9><<<nc, 128, 0, s>>>(n, W, nc, dim, nb[0], nb[1], nb[2], P, pt_ptr, pt_rows, jslot, AP, Ac);
+        MSRSB_LAUNCHED("ptap1_kernel");
     } else {
         ap_kernel<T, 3><<<ceil_div(n, 128), 128, 0, s>>>(n, W, ncode, A->rowptr, A->colidx, A->val, p_ids, P, code, AP);
         MSRSB_LAUNCHED("ap_kernel");
