@@ -242,7 +242,8 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
     // The smoother set-up is held back until the main stream reaches the
     // coarse inverse: the smoothing passes are bandwidth-bound and would share
     // HBM with it, while the cooperative Gauss-Jordan kernel (one CTA per SM,
-    // barrier-latency-bound) leaves most warp slots and bandwidth idle. The
+    // bound by the latency of its chain of panel owners) leaves most warp
+    // slots and bandwidth idle. The
     // main thread hands over an event recorded at that point, or nullptr when
     // it leaves early.
     std::promise<cudaEvent_t> go;

@@ -1,9 +1,12 @@
 // a3': coarse solver M_c^-1 = A_c^-1 (Alg. 2 of arXiv 1912.06934), FP64.
 //
 // The dense coarse operator is inverted once per set-up by blocked
-// Gauss-Jordan elimination with partial pivoting in one cooperative kernel
-// (one grid-wide barrier per panel of pivots). Each application of the coarse
-// solver (Alg. 3) is then one dense FP64 matrix-vector product instead of two
+// Gauss-Jordan elimination with partial pivoting in one cooperative kernel:
+// when every CTA's columns fit in shared memory, the look-ahead variant (each
+// panel of pivots factored once by the CTA that owns it and published behind
+// a counter the others wait on, bounded); otherwise the streaming variant
+// below (grid-wide barriers per panel). Each application of the coarse solver
+// (Alg. 3) is then one dense FP64 matrix-vector product instead of two
 // sequential triangular solves.
 #include "common.cuh"
 #include <cooperative_groups.h>
@@ -522,10 +525,11 @@ msrsb_status coarse_inverse_finish(CoarseInverseWork *w, cudaStream_t s) {
     return MSRSB_OK;
 }
 
-// One coarse inverse at a time in the process: its kernel waits on grid-wide
-// barriers, so two of them (set-ups of different problems on different
-// streams) are never in flight together; the lock is held until this one
-// has finished on the device.
+// One coarse inverse at a time in the process: its CTAs wait on one another
+// (grid-wide barriers, or the look-ahead variant's publication counter), so
+// two of them (set-ups of different problems on different streams) are never
+// in flight together; the lock is held until this one has finished on the
+// device.
 static std::mutex g_coarse_inverse_lock;
 
 msrsb_status coarse_inverse(int n, const double *Ac, double *Ainv, cudaStream_t s) {
