@@ -1,0 +1,49 @@
+"""Host logic of bench.py (no GPU): the algorithmic bytes of a restricted-
+smoothing pass count the entries of the filtered operator that the pass
+needs, i.e. every diagonal and every negative off-diagonal a_ik (the filter
+of Eq. 8 zeroes the positive ones) whose rows i and k share a coarse node;
+checked against the oracle's support pattern on a 16^3 MPFA-O case."""
+import numpy as np
+import scipy.sparse as sp
+
+import bench
+from oracle import msrsb as O
+from synth.darcy import darcy_3d_case
+
+
+def _colour_slot_ids(part):
+    # coarse node J sits in slot sum_d (J_d mod 2) 2^d of every row it supports
+    pat, nb = part["pat"], part["nb"]
+    n = pat.shape[0]
+    J = np.arange(part["nc"])
+    jc = (J % nb[0], (J // nb[0]) % nb[1], J // (nb[0] * nb[1]))
+    slot = (jc[0] % 2) + 2 * (jc[1] % 2) + 4 * (jc[2] % 2)
+    rows = np.repeat(np.arange(n), np.diff(pat.indptr))
+    assert np.bincount(rows * 8 + slot[pat.indices], minlength=8 * n).max() <= 1  # no two nodes share a slot
+    ids = -np.ones((n, 8), dtype=np.int64)
+    ids[rows, slot[pat.indices]] = pat.indices
+    return ids
+
+
+def test_kept_entries_match_the_support_pattern():
+    c = darcy_3d_case(n=16, H=4)
+    part = O.partition(c["dims"], c["H"], 0)
+    ids = _colour_slot_ids(part)
+    A = sp.csr_matrix((c["data"], c["indices"], c["indptr"])).tocoo()
+    n = A.shape[0]
+    off = (A.row != A.col) & (A.data < 0)
+    shared = (part["pat"] @ part["pat"].T).tocsr()
+    share = np.asarray(shared[A.row[off], A.col[off]]).ravel() > 0
+    assert bench.kept_entries(c, ids) == n + int(share.sum())
+    # the filter keeps exactly these off-diagonal values nonzero
+    Ah = O.mmatrix_filter(sp.csr_matrix((c["data"], c["indices"], c["indptr"]))).tocoo()
+    nz_off = (Ah.row != Ah.col) & (Ah.data != 0)
+    assert int(nz_off.sum()) == int(off.sum())
+    # about half of the rotated anisotropic stencil is positive off-diagonal
+    assert 0.3 < 1 - (n + off.sum()) / A.nnz < 0.7
+
+
+def test_smooth_bytes_per_kept_entry():
+    # value + packed column per kept entry; P read and written, scale, slot mask per row
+    assert bench.smooth_bytes(10, 100, 8, 4) == 100 * 8 + 10 * (2 * 8 * 4 + 4 + 1)
+    assert bench.smooth_bytes(10, 100, 8, 8) == 100 * 12 + 10 * (2 * 8 * 8 + 8 + 1)
