@@ -119,7 +119,7 @@ typedef struct {
  * Host only; no device work. */
 msrsb_status msrsb_partition_size(const msrsb_grid *g, int32_t *n_h, int32_t *nc_h, int32_t *W_h);
 
-/* a0. Primal partition, coarse nodes and support pattern (Sec. 2.1, Fig. 1).
+/* Primal partition, coarse nodes and support pattern (Sec. 2.1, Fig. 1).
  * part[n]: primal block of each fine point; cnode[nc]: fine index of each
  * coarse node (cell-centred: lower-middle cell of the block; vertex-centred:
  * nodes 0, H, 2H, ...); p_ids[n][W]: coarse nodes whose support holds the
@@ -129,7 +129,7 @@ msrsb_status msrsb_partition_size(const msrsb_grid *g, int32_t *n_h, int32_t *nc
 msrsb_status msrsb_partition(const msrsb_grid *g, int32_t *part, int32_t *cnode, int32_t *p_ids,
                              uint8_t *skel, cudaStream_t stream);
 
-/* a1 / a1'. M-matrix filter (Eq. 8 and Eq. 4; Alg. 1 first steps):
+/* M-matrix filter (Eq. 8 and Eq. 4; Alg. 1 first steps):
  * A_hat_ij = min(A_ij, 0) off the diagonal, A_hat_ii = -sum_{j != i} A_hat_ij.
  * bdim = 1: ahat_val[nnz] in A's pattern, comp must be 0.
  * bdim = 3: separate-displacement-component block (Eq. 20, Remark 2) of
@@ -140,7 +140,7 @@ msrsb_status msrsb_partition(const msrsb_grid *g, int32_t *part, int32_t *cnode,
 msrsb_status msrsb_filter(const msrsb_mat *A, int32_t comp, double *ahat_val, int32_t *n_zero_diag_h,
                           cudaStream_t stream);
 
-/* a2. Restricted smoothing of one scalar basis family (Eq. 6, Alg. 1).
+/* Restricted smoothing of one scalar basis family (Eq. 6, Alg. 1).
  * Ahat: filtered scalar operator (bdim 1). p_ids/skel as from
  * msrsb_partition, W in {4, 8}. p_val[n][W] in precision prec: on entry the
  * initial basis (e.g. the block indicator, or a previous P as warm start,
@@ -172,7 +172,7 @@ msrsb_status msrsb_build_basis_noalloc(const msrsb_mat *Ahat, const int32_t *p_i
                                        int32_t W, const msrsb_basis_opts *opts, int32_t prec, void *p_val,
                                        int32_t *iters_h, double *e_it_h, cudaStream_t stream);
 
-/* a3. Galerkin coarse operator A_c = P^T A P (Eq. 3, Alg. 2) with the
+/* Galerkin coarse operator A_c = P^T A P (Eq. 3, Alg. 2) with the
  * unfiltered A. g is the grid P was built on (msrsb_partition); p_ids[n][W]
  * in colour slots. For bdim = 3, P is block diagonal per component (Sec. 4):
  * p_val holds 3 families [3][n][W]. Ac_dense[nC][nC], nC = nc * bdim <= 8192,

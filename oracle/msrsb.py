@@ -24,7 +24,7 @@ import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
 # ----------------------------------------------------------------------------
-# a0: primal partition, coarse nodes, support regions (Sec. 2.1, Fig. 1; the
+# primal partition, coarse nodes, support regions (Sec. 2.1, Fig. 1; the
 # initial basis is the indicator of the primal block, Sec. 2.1)
 # ----------------------------------------------------------------------------
 
@@ -125,7 +125,7 @@ def indicator(part, pat):
 
 
 # ----------------------------------------------------------------------------
-# a1 / a1': M-matrix filter (Eq. 8 with Eq. 4; Alg. 1, first two steps)
+# M-matrix filter (Eq. 8 with Eq. 4; Alg. 1, first two steps)
 # ----------------------------------------------------------------------------
 
 
@@ -176,7 +176,7 @@ def bsr_to_csr(indptr, indices, blocks):
 
 
 # ----------------------------------------------------------------------------
-# a2: restricted smoothing of the basis (Eq. 5-6, Alg. 1)
+# restricted smoothing of the basis (Eq. 5-6, Alg. 1)
 # ----------------------------------------------------------------------------
 
 
@@ -263,7 +263,7 @@ def block_prolongation(Ps):
 
 
 # ----------------------------------------------------------------------------
-# a3 / a3': Galerkin coarse operator and coarse solver (Eq. 2-3, Alg. 2)
+# Galerkin coarse operator and coarse solver (Eq. 2-3, Alg. 2)
 # ----------------------------------------------------------------------------
 
 
@@ -444,7 +444,7 @@ class L1Jacobi:
 
 
 # ----------------------------------------------------------------------------
-# a4: two-stage preconditioner (Alg. 3 and Alg. 4)
+# two-stage preconditioner (Alg. 3 and Alg. 4)
 # ----------------------------------------------------------------------------
 
 
@@ -482,7 +482,7 @@ class TwoLevel:
 
 
 # ----------------------------------------------------------------------------
-# a5: Krylov accelerators (GMRES, right preconditioned; PCG)
+# Krylov accelerators (GMRES, right preconditioned; PCG)
 # ----------------------------------------------------------------------------
 
 
@@ -650,7 +650,7 @@ def setup_elastic(indptr, indices, blocks, dims, H, omega=2.0 / 3.0, tol=1e-3, n
 
 
 # ----------------------------------------------------------------------------
-# N3: adjoint gradient of a pressure objective with respect to log-permeability
+# adjoint gradient of a pressure objective with respect to log-permeability
 # ----------------------------------------------------------------------------
 
 

@@ -212,7 +212,7 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
         return MSRSB_OK;
     };
     MSRSB_TRY(mark(0));
-    // a0: partition, support pattern, colours
+    // partition, support pattern, colours
     MSRSB_TRY(dalloc(&h->part, n, s));
     MSRSB_TRY(dalloc(&h->cnode, h->nc, s));
     MSRSB_TRY(dalloc(&h->p_ids, nW, s));
@@ -285,7 +285,7 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
         }
         ~Release() { (*this)(nullptr); }
     } release{go};
-    // a1 + a2: filtered operator(s) streamed as sliced ELL, then Alg. 1 per component
+    // filtered operator(s) streamed as sliced ELL, then Alg. 1 per component
     T *P = nullptr;
     MSRSB_TRY(dalloc(&P, nW * bd, s));
     h->p_val = P;
@@ -325,7 +325,7 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
     dfree(vmask, s);
     dfree(nzd, s);
     MSRSB_TRY(mark(2));
-    // a3: Galerkin coarse operator with the unfiltered A, and its inverse
+    // Galerkin coarse operator with the unfiltered A, and its inverse
     {
         const msrsb_status st = tr_status.get();
         if (st != MSRSB_OK) return fail(st, "%s", tr_err.c_str());

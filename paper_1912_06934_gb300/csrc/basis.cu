@@ -1,4 +1,4 @@
-// a2: restricted smoothing of the MsRSB basis (Eq. 6 and Alg. 1 of
+// restricted smoothing of the MsRSB basis (Eq. 6 and Alg. 1 of
 // arXiv 1912.06934), the hottest kernel of the set-up.
 //
 // One thread per fine row i streams row i of the filtered operator from the

@@ -1,4 +1,4 @@
-// a3': coarse solver M_c^-1 = A_c^-1 (Alg. 2 of arXiv 1912.06934), FP64.
+// coarse solver M_c^-1 = A_c^-1 (Alg. 2 of arXiv 1912.06934), FP64.
 //
 // The dense coarse operator is inverted once per set-up by blocked
 // Gauss-Jordan elimination with partial pivoting in one cooperative kernel:

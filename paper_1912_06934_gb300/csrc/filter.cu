@@ -1,4 +1,4 @@
-// a1 / a1': the M-matrix filter of Alg. 1 (Eq. 8 then Eq. 4), scalar and
+// the M-matrix filter of Alg. 1 (Eq. 8 then Eq. 4), scalar and
 // separate-displacement-component (Eq. 20, Remark 2), and the sliced-ELL
 // copy of the filtered operator that the smoothing kernel streams.
 #include "common.cuh"

@@ -1,4 +1,4 @@
-// a3: Galerkin coarse operator A_c = P^T A P (Eq. 3, Alg. 2 of
+// Galerkin coarse operator A_c = P^T A P (Eq. 3, Alg. 2 of
 // arXiv 1912.06934) with the unfiltered fine operator, scalar or 3x3 block
 // with a block-diagonal P (Sec. 4), plus the transposed pattern of P that the
 // restriction R = P^T also uses.

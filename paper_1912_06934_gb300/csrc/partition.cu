@@ -1,4 +1,4 @@
-// a0: primal coarse partition, coarse nodes and the support pattern of P
+// primal coarse partition, coarse nodes and the support pattern of P
 // (Sec. 2.1 and Fig. 1 of arXiv 1912.06934; initial basis = block indicator).
 // Pure index arithmetic: one thread per fine point.
 #include "common.cuh"

@@ -50,7 +50,7 @@ def _pattern_sets(p_ids):
     return [tuple(sorted(r[r >= 0])) for r in ids]
 
 
-# ---------------- a0 partition (bit exact) ----------------
+# ---------------- partition (bit exact) ----------------
 
 @pytest.mark.parametrize("dims,H,cen", [((64, 64), (8, 8), 0), ((24, 24, 24), (8, 8, 8), 0),
                                         ((20, 18, 13), (8, 6, 4), 0), ((13, 13, 13), (6, 6, 6), 1),
@@ -78,7 +78,7 @@ def test_partition_bitexact(M, dims, H, cen):
     assert np.array_equal(col, s)
 
 
-# ---------------- a1 filter (same order of operations -> exact) ----------------
+# ---------------- filter (same order of operations -> exact) ----------------
 
 def test_filter_exact_scalar(M):
     c = darcy_3d_case(n=16)
@@ -101,7 +101,7 @@ def test_filter_exact_sdc(M):
         assert nz == nfixed  # fixed nodes keep only their diagonal
 
 
-# ---------------- a2 basis ----------------
+# ---------------- basis ----------------
 
 def _basis_case(M, c, prec, iters, tol=0.0, n_it=10):
     A = M.Mat.from_host(c["indptr"], c["indices"], c["data"])
@@ -178,7 +178,7 @@ def test_basis_one_pass_at_full_size(M):
     assert np.abs(rs - 1).max() <= 1e-14 and got.min() >= 0 and got.max() <= 1 + 1e-15
 
 
-# ---------------- a3 Galerkin ----------------
+# ---------------- Galerkin ----------------
 
 def test_coarse_op_matches_oracle(M):
     c = darcy_3d_case(n=24)

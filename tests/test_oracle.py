@@ -28,7 +28,7 @@ def _unit_tpfa(dims, bc=None):
     return _csr(tpfa(K, bc or {}))
 
 
-# ---------------- a0 partition ----------------
+# ---------------- partition ----------------
 
 @pytest.mark.parametrize("dims,H,cen", [((64, 64), (8, 8), 0), ((64, 64, 64), (8, 8, 8), 0),
                                         ((49, 49, 49), (6, 6, 6), 1), ((13, 9), (3, 4), 0)])
@@ -82,7 +82,7 @@ def test_partition_bruteforce_supports():
                     assert pat[x + 10 * y, Ix + len(cx) * Iy] == (inx and iny)
 
 
-# ---------------- a1 filter ----------------
+# ---------------- filter ----------------
 
 def test_filter_invariants_mpfa():
     c = darcy_2d_case(n=16)
@@ -115,7 +115,7 @@ def test_sdc_blocks():
         assert np.array_equal(comps[l].toarray(), full[l::3, l::3])
 
 
-# ---------------- a2 basis ----------------
+# ---------------- basis ----------------
 
 def _load_first_step(golden_dir):
     rows = []
@@ -226,7 +226,7 @@ def test_unfiltered_basis_leaves_unit_interval():
     assert filt.min() >= 0 and filt.max() <= 1 + 1e-15
 
 
-# ---------------- a3 Galerkin ----------------
+# ---------------- Galerkin ----------------
 
 def test_galerkin_identity_prolongation():
     c = darcy_3d_case(n=6)
@@ -324,7 +324,7 @@ def test_block_gauss_seidel_solves_its_triangle():
         assert np.abs(M @ z - v[sm.order]).max() < 1e-10 * np.abs(v).max()
 
 
-# ---------------- a4 two-stage apply ----------------
+# ---------------- two-stage apply ----------------
 
 def test_two_level_matches_error_propagation_matrix():
     rng = np.random.default_rng(6)
@@ -358,7 +358,7 @@ def test_coarse_correction_galerkin_orthogonality():
     assert np.allclose(tl.apply(2 * v - 3 * w), 2 * tl.apply(v) - 3 * tl.apply(w), rtol=0, atol=1e-10)
 
 
-# ---------------- a5 Krylov ----------------
+# ---------------- Krylov ----------------
 
 def test_gmres_matches_direct_solve():
     c = darcy_2d_case(n=32, H=8)
@@ -392,7 +392,7 @@ def test_pcg_matches_direct_solve():
     assert np.linalg.norm(x - xs) <= 1e-7 * np.linalg.norm(xs)
 
 
-# ---------------- N4: l1-Jacobi smoother, smoothing-only baseline, Richardson ----------------
+# ---------------- l1-Jacobi smoother, smoothing-only baseline, Richardson ----------------
 
 def test_l1_jacobi_exact_on_a_diagonal_matrix():
     d = np.array([2.0, 5.0, 0.5, 3.0])
@@ -448,7 +448,7 @@ def test_richardson_multiscale_vs_smoothing_only():
     assert rr_so > 1e-8
 
 
-# ---------------- N3: adjoint gradient of a TPFA objective ----------------
+# ---------------- adjoint gradient of a TPFA objective ----------------
 
 def test_adjoint_gradient_matches_brute_force_differences():
     # every cell of a 4 x 3 x 2 grid, central differences of J itself
