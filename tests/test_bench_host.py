@@ -47,3 +47,18 @@ def test_smooth_bytes_per_kept_entry():
     # value + packed column per kept entry; P read and written, scale, slot mask per row
     assert bench.smooth_bytes(10, 100, 8, 4) == 100 * 8 + 10 * (2 * 8 * 4 + 4 + 1)
     assert bench.smooth_bytes(10, 100, 8, 8) == 100 * 12 + 10 * (2 * 8 * 8 + 8 + 1)
+
+
+def test_clock_summary_reads_clocks_and_throttle_reasons():
+    c = bench.ClockSampler()
+    c.lines = ["2070, 2070, Not Active, Not Active, Not Active, Not Active",
+               "1980, 2070, Not Active, Not Active, Not Active, Active",
+               "2070, 2070, Not Active, Active, Not Active, Not Active",
+               "[N/A], 2070, Not Active, Not Active, Not Active, Not Active",  # unreadable sample: skipped
+               "garbage"]
+    s = c.summary()
+    assert s["samples"] == 3
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
+    empty = bench.ClockSampler().summary()
+    assert empty["samples"] == 0 and empty["reasons"] == ["unsampled"]
