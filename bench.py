@@ -51,6 +51,15 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def max_over_ranks(values, device):
+    """Elementwise maximum of `values` over the ranks of the initialised
+    process group (every rank gets it): a run is as slow as its slowest rank."""
+    import torch
+    t = torch.tensor(values, device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(v) for v in t]
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle sampling during the timed region."""
 
@@ -213,9 +222,7 @@ def gpu_arm(args, rank, world):
     torch.cuda.synchronize()
     t32, t64 = sum(ms32), sum(ms64)
     if world > 1:
-        t = torch.tensor([t32, t64], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t32, t64 = float(t[0]), float(t[1])
+        t32, t64 = max_over_ranks([t32, t64], dev)
 
     # error of each mixed-form result against the FP64 form on the same input
     # (not timed): P, A_c, one preconditioner apply, the solution

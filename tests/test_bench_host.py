@@ -62,3 +62,32 @@ def test_clock_summary_reads_clocks_and_throttle_reasons():
     assert s["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
     empty = bench.ClockSampler().summary()
     assert empty["samples"] == 0 and empty["reasons"] == ["unsampled"]
+
+
+def _max_rank(rank, world, port, out):
+    import os
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        out[rank] = bench.max_over_ranks([1.0 + rank, 10.0 - rank], "cpu")
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_with_two_gloo_ranks():
+    import socket
+    import torch.multiprocessing as mp
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as mgr:
+        out = mgr.dict()
+        procs = [ctx.Process(target=_max_rank, args=(r, 2, port, out)) for r in range(2)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(timeout=120)
+            assert p.exitcode == 0
+        assert out[0] == [2.0, 10.0] and out[1] == [2.0, 10.0]
