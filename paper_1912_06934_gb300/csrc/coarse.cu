@@ -395,7 +395,10 @@ __global__ void unscramble_index_kernel(int n, const int *__restrict__ perm, int
     for (int j = 0; j < n; ++j) src[j] = j;
     for (int k = n - 1; k >= 0; --k) {
         const int p = perm[k];
-        if (p != k) {
+        // after a zero pivot or a time-out the elimination stopped early and
+        // later entries of perm were never written: skip anything out of range
+        // (the status already reports the failure; the result is discarded)
+        if (p != k && p >= 0 && p < n) {
             const int t = src[k];
             src[k] = src[p];
             src[p] = t;
