@@ -56,3 +56,13 @@ def test_wait_selftest_rejects_bad_limits_on_the_host():
     lib.msrsb_wait_selftest.argtypes = [ctypes.c_double, ctypes.c_void_p]
     for lim in (0.0, -1.0, 1000.5, float("nan")):
         assert lib.msrsb_wait_selftest(lim, None) == B.MSRSB_EINVAL
+
+
+def test_binding_constants_match_the_header():
+    # every enumerator of include/msrsb.h has the same value in the binding
+    from paper_1912_06934_gb300 import msrsb as B
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "msrsb.h")).read(), flags=re.S)
+    found = dict((k, int(v)) for k, v in re.findall(r"\b(MSRSB_[A-Z0-9_]+)\s*=\s*(\d+)", src))
+    assert len(found) >= 18
+    for name, value in found.items():
+        assert getattr(B, name) == value, name
