@@ -158,12 +158,15 @@ msrsb_status msrsb_build_basis(const msrsb_mat *Ahat, const int32_t *p_ids, cons
  * framework's caching allocator, a memory-capped container), or host loops
  * that must not take the allocator's locks and implicit synchronisation.
  * Same arguments and results as msrsb_build_basis (the filtered operator is
- * read in CSR form directly); the scratch it needs lives in one static device
- * array of 10 MiB + 33,024 bytes that every GPU loading the library holds
- * until the process exits. Limits: n * W <= 1,048,576, n <= 262,144 and
- * max_iter <= 4096; larger inputs return MSRSB_ESHAPE and do nothing.
- * The first call on a device resolves the array's device address (once per
- * device, with that device current); make that first call before any stream
+ * read in CSR form directly; the row normalisation divides where
+ * msrsb_build_basis multiplies by a reciprocal, so results agree to rounding);
+ * the scratch it needs lives in one static device array of 10 MiB + 33,288
+ * bytes that every GPU loading the library holds until the process exits.
+ * Limits: n * W <= 1,048,576, n <= 262,144 and max_iter <= 4096; larger
+ * inputs return MSRSB_ESHAPE and do nothing.
+ * Every call looks up the array's device address on the current device
+ * (cudaGetSymbolAddress); the first call on a device also loads the
+ * library's device code there, so make that first call before any stream
  * capture. All calls on a device share the array and each call resets the
  * parts that must start at zero: calls that overlap on the GPU (different
  * streams or host threads at the same time) race and give wrong results.
@@ -280,6 +283,16 @@ msrsb_status msrsb_pattern_outer(const msrsb_mat *A, double alpha, const double 
  * summed device time (ms) of the loops they ran in. Host bookkeeping only. */
 msrsb_status msrsb_profile(int32_t enable);
 msrsb_status msrsb_profile_read(int64_t *launches_h, int64_t *smooth_launches_h, double *smooth_ms_h);
+
+/* Arithmetic-rate probe (measurement support, no counterpart in the paper):
+ * launches blocks_per_sm (1..64) CTAs of 256 threads per SM, every thread
+ * running 8 independent chains of 2048 fused multiply-adds in precision prec
+ * (MSRSB_F64 or MSRSB_F32), and returns the best rate of 5 event-timed
+ * launches in fma_per_s_h (FMAs per second, host) and that launch's time in
+ * ms_h. The roofline denominator for kernels bound by the FP64 or FP32 pipe.
+ * Synchronises `stream`. */
+msrsb_status msrsb_fma_rate(int32_t prec, int32_t blocks_per_sm, double *fma_per_s_h, double *ms_h,
+                            cudaStream_t stream);
 
 /* Self-test of the bounded device-side wait (no counterpart in the paper).
  * The coarse inverse's CTAs wait on a publication counter with a wall-time and

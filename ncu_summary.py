@@ -1,9 +1,9 @@
 """Summaries of Nsight Compute CSV output as markdown tables.
 
-    python -m paper_1912_06934_gb300.ncu_summary launches LAUNCHES.csv
+    python ncu_summary.py launches LAUNCHES.csv
         per kernel: launches, total gpu__time_duration, share of the total
         (input: ncu --metrics gpu__time_duration.sum --csv --log-file ...)
-    python -m paper_1912_06934_gb300.ncu_summary raw RAW.csv
+    python ncu_summary.py raw RAW.csv
         per captured launch: the DRAM, throughput, tensor/FP pipe, occupancy
         and stall counters used for the roofline
         (input: ncu -i REPORT.ncu-rep --page raw --csv > RAW.csv)

@@ -252,14 +252,11 @@ def block_prolongation(Ps):
     i is interpolated from component l of the coarse nodes only. Rows are
     3*node + l, columns 3*J + l."""
     n, nc = Ps[0].shape
-    out = sp.lil_matrix((3 * n, 3 * nc))
     blocks = []
     for l, P in enumerate(Ps):
         P = sp.coo_matrix(P)
         blocks.append(sp.coo_matrix((P.data, (3 * P.row + l, 3 * P.col + l)), shape=(3 * n, 3 * nc)))
-    del out
-    M = blocks[0] + blocks[1] + blocks[2]
-    return sp.csr_matrix(M)
+    return sp.csr_matrix(blocks[0] + blocks[1] + blocks[2])
 
 
 # ----------------------------------------------------------------------------
@@ -346,19 +343,28 @@ def ilu0(B):
 
 
 class ColouredSmoother:
-    """Second-stage smoother on a colour-ordered matrix.
+    """Second-stage smoother (ILU(0), Sec. 3.2; block Gauss-Seidel, Sec. 4.2-4.3).
 
-    kind 'ilu0': M = L U, the ILU(0) factors of A permuted into colour order.
+    kind 'ilu0': M = L U, the ILU(0) factors of A in the elimination order.
     kind 'gs_fwd' / 'gs_bwd': block Gauss-Seidel, M = D + L (forward) or
-    M = D + U (backward) of A in colour order, with D the bdim x bdim diagonal
-    blocks. Triangular solves go colour by colour: the rows of one colour are
-    independent, so each colour is one vectorised update, which is exactly
-    sequential substitution in colour order.
+    M = D + U (backward) of A in the elimination order, with D the
+    bdim x bdim diagonal blocks.
+
+    The paper's MATLAB setting eliminates in the natural order (colour=None
+    here): the triangular solves are sequential substitutions. With a colour
+    array, the order is colour by colour, natural inside a colour (the order
+    the GPU uses); the rows of one colour are independent, so each colour is
+    one vectorised update, which is exactly sequential substitution in that
+    order.
     """
 
     def __init__(self, A, colour, kind, bdim=1):
         self.kind = kind
         self.bdim = bdim
+        A = sp.csr_matrix(A)
+        self.natural = colour is None
+        if self.natural:
+            colour = np.zeros(A.shape[0] // bdim, dtype=np.int64)
         node_order = colour_order(colour)
         if bdim == 1:
             order = node_order
@@ -368,7 +374,7 @@ class ColouredSmoother:
             dof_colour = np.repeat(colour, bdim)
         self.order = order
         self.inv_order = np.argsort(order)
-        B = sp.csr_matrix(A)[order][:, order].tocsr()
+        B = A[order][:, order].tocsr()
         B.sort_indices()
         self.B = B
         cs = dof_colour[order]
@@ -383,24 +389,35 @@ class ColouredSmoother:
             node_of = np.arange(B.shape[0]) // bdim
             Bc = B.tocoo()
             same = node_of[Bc.row] == node_of[Bc.col]
-            Dm = sp.csr_matrix((Bc.data[same], (Bc.row[same], Bc.col[same])), shape=B.shape)
-            self.Lo = sp.csr_matrix((Bc.data[~same & (Bc.row > Bc.col)],
-                                     (Bc.row[~same & (Bc.row > Bc.col)], Bc.col[~same & (Bc.row > Bc.col)])),
-                                    shape=B.shape)
-            self.Up = sp.csr_matrix((Bc.data[~same & (Bc.row < Bc.col)],
-                                     (Bc.row[~same & (Bc.row < Bc.col)], Bc.col[~same & (Bc.row < Bc.col)])),
-                                    shape=B.shape)
-            Db = Dm.toarray().reshape(nn, bdim, nn, bdim) if B.shape[0] <= 3000 else None
+            lo = ~same & (Bc.row > Bc.col)
+            up = ~same & (Bc.row < Bc.col)
+            self.Lo = sp.csr_matrix((Bc.data[lo], (Bc.row[lo], Bc.col[lo])), shape=B.shape)
+            self.Up = sp.csr_matrix((Bc.data[up], (Bc.row[up], Bc.col[up])), shape=B.shape)
             blocks = np.zeros((nn, bdim, bdim))
-            Dc = Dm.tocoo()
-            blocks[node_of[Dc.row], Dc.row % bdim, Dc.col % bdim] = Dc.data
-            del Db
+            blocks[node_of[Bc.row[same]], Bc.row[same] % bdim, Bc.col[same] % bdim] = Bc.data[same]
             self.Dinv = np.linalg.inv(blocks)
             self.node_cls = [np.unique(node_of[c]) for c in self.cls]
+            if self.natural:
+                # (D + T) z = r  <=>  (I + T D^-1) (D z) = r, and T D^-1 keeps
+                # T's strict block triangle, so one unit triangular solve
+                # followed by the block-diagonal product gives z
+                Dm = sp.bsr_matrix((self.Dinv, np.arange(nn), np.arange(nn + 1)), shape=B.shape).tocsr()
+                T = self.Lo if kind == "gs_fwd" else self.Up
+                self.Dm = Dm
+                self.TD = sp.csr_matrix(T @ Dm)
+                self.TD.sort_indices()
 
     def solve(self, r):
         """z = M^-1 r (r, z in the natural order)."""
         rp = r[self.order]
+        if self.natural:
+            if self.kind == "ilu0":
+                y = spla.spsolve_triangular(self.L, rp, lower=True, unit_diagonal=True)
+                z = spla.spsolve_triangular(self.U, y, lower=False)
+            else:
+                y = spla.spsolve_triangular(self.TD, rp, lower=self.kind == "gs_fwd", unit_diagonal=True)
+                z = self.Dm @ y
+            return z[self.inv_order]
         if self.kind == "ilu0":
             y = np.zeros_like(rp)
             for c in range(self.ncol):  # L y = r, unit lower
@@ -607,9 +624,11 @@ def pcg(A, b, M, x0=None, rtol=1e-8, maxit=500):
 
 
 def setup_scalar(A, dims, H, centering=0, omega=2.0 / 3.0, tol=1e-3, n_it=10, max_iter=100,
-                 smoother="ilu0", coarse=True):
+                 smoother="ilu0", coarse=True, order="colour"):
     """Alg. 2 for a scalar operator (flow): partition, filter, Alg. 1, Galerkin
-    coarse operator, coarse LU and a colour-ordered ILU(0) post-smoother."""
+    coarse operator, coarse LU and an ILU(0) post-smoother, eliminated in the
+    parity-colour order (order="colour", the GPU's) or in the natural order
+    (order="natural", the paper's MATLAB setting)."""
     A = sp.csr_matrix(A)
     A.sort_indices()
     part = partition(dims, H, centering)
@@ -617,18 +636,20 @@ def setup_scalar(A, dims, H, centering=0, omega=2.0 / 3.0, tol=1e-3, n_it=10, ma
     P0 = indicator(part["part"], part["pat"])
     vals, its, e_it, hist = enhanced_msrsb(Ahat, part["pat"], P0, part["skel"], omega, tol, n_it, max_iter)
     P = as_matrix(vals, part["pat"])
-    post = ColouredSmoother(A, parity_colours(dims), "ilu0") if smoother == "ilu0" else None
+    col = parity_colours(dims) if order == "colour" else None
+    post = ColouredSmoother(A, col, "ilu0") if smoother == "ilu0" else None
     tl = TwoLevel(A, P, pre=None, post=post, coarse=coarse)
     return dict(part=part, Ahat=Ahat, vals=vals, iters=its, e_it=e_it, hist=hist, P=P, tl=tl)
 
 
 def setup_elastic(indptr, indices, blocks, dims, H, omega=2.0 / 3.0, tol=1e-3, n_it=10, max_iter=100,
-                  smoother="gs", sweeps=2, coarse=True):
+                  smoother="gs", sweeps=2, coarse=True, order="colour"):
     """Alg. 2 for 3x3-block elasticity: SDC blocks filtered per component,
     three scalar bases on one shared pattern, block-diagonal P, Galerkin with
     the full operator, and a symmetric pair of pre/post smoothers: forward /
     backward block Gauss-Seidel ("gs"), or `sweeps` l1-Jacobi sweeps each
-    ("l1jac"). coarse=False gives the smoothing-only baseline."""
+    ("l1jac"). coarse=False gives the smoothing-only baseline. order as in
+    setup_scalar (Gauss-Seidel only)."""
     part = partition(dims, H, 1)
     A = bsr_to_csr(indptr, indices, blocks)
     comps = sdc_blocks(indptr, indices, blocks)
@@ -642,7 +663,7 @@ def setup_elastic(indptr, indices, blocks, dims, H, omega=2.0 / 3.0, tol=1e-3, n
     if smoother == "l1jac":
         pre = post = L1Jacobi(A, sweeps)
     else:
-        col = parity_colours(dims)
+        col = parity_colours(dims) if order == "colour" else None
         pre = ColouredSmoother(A, col, "gs_fwd", bdim=3)
         post = ColouredSmoother(A, col, "gs_bwd", bdim=3)
     tl = TwoLevel(A, P, pre=pre, post=post, coarse=coarse)

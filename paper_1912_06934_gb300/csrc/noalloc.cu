@@ -10,8 +10,11 @@
 // their solver loop. The paper has no counterpart.
 //
 // The kernel reads the filtered operator directly in CSR form (no sliced-ELL
-// copy is built) and compares coarse ids in the colour slots on the fly; the
-// arithmetic and its order are those of the sliced-ELL kernel.
+// copy is built) and compares coarse ids in the colour slots on the fly. The
+// products are accumulated in the same CSR order as in the sliced-ELL kernel,
+// but the row normalisation divides every entry by the row sum where that
+// kernel multiplies by one reciprocal, so the two agree to rounding, not bit
+// for bit.
 #include "common.cuh"
 
 namespace msrsb {
@@ -25,31 +28,27 @@ constexpr size_t kOffScale = kOffP2 + kNoAllocMaxPW * sizeof(double);
 constexpr size_t kOffEmax = kOffScale + kNoAllocMaxRows * sizeof(double);
 constexpr size_t kOffFlags = kOffEmax + (kNoAllocMaxIter + 1) * sizeof(unsigned long long);
 constexpr size_t kOffElast = kOffFlags + 256;
-constexpr size_t kNoAllocBytes = kOffElast + 256;  // 10 MiB + 33,024 bytes per device
+constexpr size_t kNoAllocBytes = kOffElast + 256;  // 10 MiB + 33,288 bytes per device
+static_assert(kNoAllocBytes == 10u * 1024u * 1024u + 33288u, "documented size of the static scratch");
 
 // Shared by every call on a device; contents persist from the previous call.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-// Device address of the scratch array, resolved once per device (host code
-// may not use the symbol itself: it names a host-side stand-in).
-constexpr int kMaxDevices = 64;
-static void *g_scratch_addr[kMaxDevices] = {nullptr};
-
+// Device address of the scratch array on the current device. Host code may
+// not use the symbol itself (it names a host-side stand-in), so every call
+// looks the address up with the device current; nothing is cached, so a
+// context that was reset and re-created gets its own address.
 static msrsb_status scratch_address(unsigned char **out) {
     int dev = 0;
     MSRSB_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return fail(MSRSB_EINVAL, "device ordinal %d beyond %d", dev, kMaxDevices);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            cudaGetLastError();
-            return fail(MSRSB_ECUDA, "cudaGetSymbolAddress of the static scratch failed on device %d: %s", dev,
-                        cudaGetErrorString(e));
-        }
-        g_scratch_addr[dev] = p;
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return fail(MSRSB_ECUDA, "cudaGetSymbolAddress of the static scratch failed on device %d: %s", dev,
+                    cudaGetErrorString(e));
     }
-    *out = (unsigned char *)g_scratch_addr[dev];
+    *out = (unsigned char *)p;
     return MSRSB_OK;
 }
 

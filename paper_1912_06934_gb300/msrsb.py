@@ -22,7 +22,7 @@ MSRSB_GMRES, MSRSB_PCG, MSRSB_RICHARDSON = 0, 1, 2
 EXPORTS = ["msrsb_partition_size", "msrsb_partition", "msrsb_filter", "msrsb_build_basis", "msrsb_coarse_op",
            "msrsb_setup", "msrsb_apply", "msrsb_solve", "msrsb_get_setup", "msrsb_get_info", "msrsb_destroy",
            "msrsb_solve_host", "msrsb_profile", "msrsb_profile_read", "msrsb_wait_selftest", "msrsb_build_basis_noalloc",
-           "msrsb_solve_ensemble", "msrsb_transpose_values", "msrsb_pattern_outer", "msrsb_last_error"]
+           "msrsb_solve_ensemble", "msrsb_transpose_values", "msrsb_pattern_outer", "msrsb_fma_rate", "msrsb_last_error"]
 
 
 class MsrsbError(RuntimeError):
@@ -291,6 +291,14 @@ def msrsb_wait_selftest(limit_ms=20.0, stream=None):
     L.msrsb_wait_selftest.restype = ctypes.c_int
     L.msrsb_wait_selftest.argtypes = [ctypes.c_double, ctypes.c_void_p]
     return int(L.msrsb_wait_selftest(float(limit_ms), _stream(stream)))
+
+
+def msrsb_fma_rate(prec, blocks_per_sm=8, stream=None):
+    """(FMAs per second, ms of the best launch) of the arithmetic-rate probe."""
+    r, ms = ctypes.c_double(), ctypes.c_double()
+    _check(load().msrsb_fma_rate(ctypes.c_int32(prec), ctypes.c_int32(blocks_per_sm), ctypes.byref(r),
+                                 ctypes.byref(ms), _stream(stream)))
+    return r.value, ms.value
 
 
 def msrsb_profile_read():

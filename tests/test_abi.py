@@ -66,3 +66,28 @@ def test_binding_constants_match_the_header():
     assert len(found) >= 18
     for name, value in found.items():
         assert getattr(B, name) == value, name
+
+
+_ALLOC = re.compile(r"\b(cudaMalloc\w*|cudaFree\w*|cudaHostAlloc|cudaMallocHost|dalloc|dfree|malloc|calloc|realloc|"
+                    r"free|new|cub)\b")
+
+
+def _strip_comments(src):
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    return re.sub(r'"(?:\\.|[^"\\])*"', '""', src)
+
+
+def test_noalloc_entry_point_names_no_allocation_call():
+    """msrsb_build_basis_noalloc is for callers that cannot allocate device
+    memory: its translation unit, and the argument check it calls from another
+    one, name no allocation or free routine of CUDA, CUB, C or C++."""
+    csrc = os.path.join(ROOT, "paper_1912_06934_gb300", "csrc")
+    code = _strip_comments(open(os.path.join(csrc, "noalloc.cu")).read())
+    assert not _ALLOC.findall(code)
+    # the only function of another translation unit it calls
+    calls = set(re.findall(r"\b([a-z_]+)\s*\(", code)) - set(re.findall(r"\b([a-z_]+)\s*\([^;{]*\)\s*\{", code))
+    assert "check_mat" in calls
+    filt = _strip_comments(open(os.path.join(csrc, "filter.cu")).read())
+    body = re.search(r"msrsb_status check_mat\(const msrsb_mat \*A\) \{(.*?)\n\}", filt, flags=re.S).group(1)
+    assert not _ALLOC.findall(body)

@@ -2,7 +2,9 @@
 smoothing pass count the entries of the filtered operator that the pass
 needs, i.e. every diagonal and every negative off-diagonal a_ik (the filter
 of Eq. 8 zeroes the positive ones) whose rows i and k share a coarse node;
-checked against the oracle's support pattern on a 16^3 MPFA-O case."""
+checked against the oracle's support pattern on a 16^3 MPFA-O case. The
+multiply-adds of a pass (the FP64 pipe roofline) count the coarse nodes each
+such pair of rows shares."""
 import numpy as np
 import scipy.sparse as sp
 
@@ -33,8 +35,11 @@ def test_kept_entries_match_the_support_pattern():
     n = A.shape[0]
     off = (A.row != A.col) & (A.data < 0)
     shared = (part["pat"] @ part["pat"].T).tocsr()
-    share = np.asarray(shared[A.row[off], A.col[off]]).ravel() > 0
-    assert bench.kept_entries(c, ids) == n + int(share.sum())
+    common = np.asarray(shared[A.row[off], A.col[off]]).ravel()
+    kept, matches = bench.kept_entries(c, ids)
+    assert kept == n + int((common > 0).sum())
+    # multiply-adds of A_hat P on P's pattern: coarse nodes rows i and k share
+    assert matches == int(common.sum())
     # the filter keeps exactly these off-diagonal values nonzero
     Ah = O.mmatrix_filter(sp.csr_matrix((c["data"], c["indices"], c["indptr"]))).tocoo()
     nz_off = (Ah.row != Ah.col) & (Ah.data != 0)

@@ -8,8 +8,8 @@ configuration.
   recomputed here in FP64, within +-1 iteration of the oracle.
 - 3D elasticity 48^3 Q1 elements (352,947 dofs): one GPU smoothing pass of
   every SDC component equals the oracle's pass applied to the GPU's previous
-  iterate; the FP64 PCG solve (block Gauss-Seidel pre/post) matches the
-  oracle's iteration count within +-1 and the mixed one reaches 1e-8.
+  iterate; the PCG solve (block Gauss-Seidel pre/post) reaches 1e-8 within
+  +-1 of the oracle's iteration count in both forms.
 """
 import numpy as np
 import pytest
@@ -127,6 +127,5 @@ def test_elastic48_pcg(M, elastic48):
         r = h.solve(torch.as_tensor(b, device="cuda"), rtol=1e-8, maxit=500)
         x = r["x"].cpu().numpy()
         assert np.linalg.norm(b - A @ x) / np.linalg.norm(b) <= 1e-8
-        if prec == 0:
-            assert abs(r["iters"] - its_ref) <= 1
+        assert abs(r["iters"] - its_ref) <= 1, (prec, r["iters"], its_ref)
         h.destroy()

@@ -1,7 +1,7 @@
-"""The text summariser behind profiles/ (no GPU): per-kernel launch counts,
+"""The Nsight Compute text summariser (no GPU): per-kernel launch counts,
 totals and shares from an ncu launch list, with units converted and template
 arguments kept; and the raw-page table of the roofline counters."""
-from paper_1912_06934_gb300 import ncu_summary as S
+import ncu_summary as S
 
 HEAD = ('"ID","Process ID","Process Name","Host Name","Kernel Name","Context","Stream","Block Size","Grid Size",'
         '"Device","CC","Section Name","Metric Name","Metric Unit","Metric Value"\n')

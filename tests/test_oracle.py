@@ -274,18 +274,25 @@ def test_parity_colouring_is_valid():
     assert col.max() == 7
 
 
-def test_ilu0_defining_property():
+@pytest.mark.parametrize("order", ["colour", "natural"])
+def test_ilu0_defining_property(order):
+    """(L U)_ij = A_ij on A's pattern, in either elimination order."""
     c = darcy_3d_case(n=8)
     A = _csr((c["indptr"], c["indices"], c["data"]))
-    order = O.colour_order(O.parity_colours(c["dims"]))
-    B = A[order][:, order].tocsr()
-    B.sort_indices()
-    L, U = O.ilu0(B)
+    sm = O.ColouredSmoother(A, O.parity_colours(c["dims"]) if order == "colour" else None, "ilu0")
+    if order == "natural":
+        assert np.array_equal(sm.order, np.arange(A.shape[0]))
+    B = sm.B
+    L, U = sm.L, sm.U
     LU = ((L + sp.eye(B.shape[0])) @ U).toarray()
     mask = B.toarray() != 0
     mask |= np.eye(B.shape[0], dtype=bool)
     Bd = B.toarray()
     assert np.abs(LU[mask] - Bd[mask]).max() <= 1e-12 * np.abs(Bd).max()
+    # the smoother inverts exactly its own factors: L U (M^-1 v) = v
+    v = np.random.default_rng(3).standard_normal(A.shape[0])
+    zp = sm.solve(v)[sm.order]
+    assert np.abs((L + sp.eye(B.shape[0])) @ (U @ zp) - v[sm.order]).max() < 1e-11 * np.abs(v).max()
 
 
 def test_ilu0_exact_for_tridiagonal():
@@ -295,22 +302,28 @@ def test_ilu0_exact_for_tridiagonal():
                  [-1, 0, 1], format="csr")
     L, U = O.ilu0(T)
     assert np.abs(((L + sp.eye(n)) @ U - T).toarray()).max() < 1e-14
-    sm = O.ColouredSmoother(T, np.zeros(n, dtype=np.int64) + (np.arange(n) % 2), "ilu0")
     v = rng.standard_normal(n)
-    # colour order on a chain is still a valid elimination order -> exact
-    # only in natural order; check the triangular solves satisfy L U z = v
+    # natural order on a chain: no fill, so ILU(0) is the exact LU and the
+    # smoother is T^-1
+    nat = O.ColouredSmoother(T, None, "ilu0")
+    assert np.abs(T @ nat.solve(v) - v).max() < 1e-13
+    sm = O.ColouredSmoother(T, np.zeros(n, dtype=np.int64) + (np.arange(n) % 2), "ilu0")
+    # red-black order on a chain drops fill, so it is not exact; check that
+    # the triangular solves satisfy L U z = v in that order
     z = sm.solve(v)
     B = sm.B
     Lp, Up = O.ilu0(B)
     zp = z[sm.order]
     assert np.abs(((Lp + sp.eye(n)) @ (Up @ zp)) - v[sm.order]).max() < 1e-13
+    assert np.abs(T @ z - v).max() > 1e-6
 
 
-def test_block_gauss_seidel_solves_its_triangle():
+@pytest.mark.parametrize("order", ["colour", "natural"])
+def test_block_gauss_seidel_solves_its_triangle(order):
     rng = np.random.default_rng(4)
     e = q1_elasticity(np.exp(rng.standard_normal((3, 3, 3))), rng.uniform(0.2, 0.35, (3, 3, 3)))
     A = O.bsr_to_csr(e["indptr"], e["indices"], e["data"])
-    col = O.parity_colours(e["node_dims"])
+    col = O.parity_colours(e["node_dims"]) if order == "colour" else None
     v = rng.standard_normal(A.shape[0])
     for kind in ("gs_fwd", "gs_bwd"):
         sm = O.ColouredSmoother(A, col, kind, bdim=3)
@@ -322,6 +335,44 @@ def test_block_gauss_seidel_solves_its_triangle():
             (np.arange(B.shape[0])[:, None] < np.arange(B.shape[0])[None, :])
         M = np.where(keep, B, 0.0)
         assert np.abs(M @ z - v[sm.order]).max() < 1e-10 * np.abs(v).max()
+
+
+def test_block_prolongation_interleaves_components():
+    """Sec. 4: component l of every fine node is interpolated from component l
+    of the coarse nodes only, with that component's own basis. Three different
+    bases on one pattern (the block indicator, a smoothed basis, random
+    row-normalised values): column 3J+l of P is basis l of coarse node J on
+    rows 3i+l and zero on the other components, and the rows of each
+    component block sum to the identity (sum_J P[3i+l, 3J+m] = delta_lm)."""
+    dims, H = (5, 5, 5), (2, 2, 2)
+    part = O.partition(dims, H, 1)
+    pat, nc = part["pat"], part["nc"]
+    n = pat.shape[0]
+    rng = np.random.default_rng(12)
+    b0 = O.indicator(part["part"], pat)
+    Ah = O.mmatrix_filter(_unit_tpfa(dims))
+    b1 = O.enhanced_msrsb(Ah, pat, b0, part["skel"], tol=0.0, max_iter=7)[0]
+    r = rng.uniform(0.1, 1.0, pat.nnz)
+    rows = np.repeat(np.arange(n), np.diff(pat.indptr))
+    b2 = r / np.bincount(rows, weights=r)[rows]
+    Ps = [O.as_matrix(b, pat) for b in (b0, b1, b2)]
+    assert not np.allclose(b0, b1) and not np.allclose(b1, b2)
+    Pb = O.block_prolongation(Ps)
+    assert Pb.shape == (3 * n, 3 * nc)
+    dense = [P.toarray() for P in Ps]
+    for J in range(nc):
+        for l in range(3):
+            e = np.zeros(3 * nc)
+            e[3 * J + l] = 1.0
+            col = (Pb @ e).reshape(n, 3)
+            assert np.array_equal(col[:, l], dense[l][:, J])
+            assert not col[:, [m for m in range(3) if m != l]].any()
+    for m in range(3):
+        ones_m = np.zeros(3 * nc)
+        ones_m[m::3] = 1.0
+        s = (Pb @ ones_m).reshape(n, 3)
+        for l in range(3):
+            assert np.abs(s[:, l] - (1.0 if l == m else 0.0)).max() <= 1e-14
 
 
 # ---------------- two-stage apply ----------------
