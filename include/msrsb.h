@@ -176,17 +176,31 @@ msrsb_status msrsb_build_basis_noalloc(const msrsb_mat *Ahat, const int32_t *p_i
                                        int32_t *iters_h, double *e_it_h, cudaStream_t stream);
 
 /* Galerkin coarse operator A_c = P^T A P (Eq. 3, Alg. 2) with the
- * unfiltered A. g is the grid P was built on (msrsb_partition); p_ids[n][W]
- * in colour slots. For bdim = 3, P is block diagonal per component (Sec. 4):
- * p_val holds 3 families [3][n][W]. Ac_dense[nC][nC], nC = nc * bdim <= 8192,
- * row-major, coarse dof = bdim*J + component; entries outside the coarse
- * 3^dim stencil are written as 0. Deterministic (fixed summation order). */
+ * unfiltered A, as a block CSR matrix. g is the grid P was built on
+ * (msrsb_partition); p_ids[n][W] in colour slots. For bdim = 3, P is block
+ * diagonal per component (Sec. 4): p_val holds 3 families [3][n][W].
+ * A_c has nc block rows of bdim x bdim blocks (coarse dof = bdim*J +
+ * component); row J stores the coarse nodes at most one coarse step from J on
+ * every axis (its 3^dim stencil), columns ascending: ac_rowptr[nc+1],
+ * ac_colidx[nnzb], ac_val[nnzb][bdim][bdim] (row-major blocks), device
+ * arrays owned by the caller. *nnzb_h (host, required) receives the number
+ * of blocks, prod_d (3 nb_d - 2) for nb_d coarse nodes along axis d. With
+ * ac_val == NULL the call only sets *nnzb_h (no device work), so a caller can
+ * size the arrays first. Deterministic (fixed summation order). */
 msrsb_status msrsb_coarse_op(const msrsb_mat *A, const msrsb_grid *g, const int32_t *p_ids, const void *p_val,
-                             int32_t prec, double *Ac_dense, cudaStream_t stream);
+                             int32_t prec, int32_t *ac_rowptr, int32_t *ac_colidx, double *ac_val,
+                             int32_t *nnzb_h, cudaStream_t stream);
 
 /* Alg. 2 set-up of the whole preconditioner: partition, filter, Alg. 1, A_c,
- * the FP64 coarse solver M_c^-1 = A_c^-1 (Gauss-Jordan with partial pivoting)
- * and the smoother (multicolour ILU(0), or multicolour block Gauss-Seidel).
+ * the FP64 coarse solver M_c^-1 = A_c^-1 and the smoother (multicolour
+ * ILU(0), multicolour block Gauss-Seidel, or l1-Jacobi). The coarse solver is
+ * an exact block LU of A_c over the planes of the coarse grid along its last
+ * axis (z in 3D, y in 2D): the dense inverse of each plane's Schur
+ * complement, by Gauss-Jordan elimination with partial pivoting inside the
+ * plane. A plane holds nb_x * nb_y * bdim (3D) or nb_x * bdim (2D) coarse
+ * unknowns; beyond about 640 of them (one thread-block cluster's shared
+ * memory) the dense inverse of the whole A_c is used instead, which needs
+ * nc * bdim <= 8192, else MSRSB_ESHAPE. A zero pivot gives MSRSB_EBREAKDOWN.
  * p_init (nullable, device, layout of p_val) is a warm-start basis; NULL
  * starts from the block indicator. The handle keeps a non-owning reference
  * to A's arrays, which must stay alive and unchanged until msrsb_destroy; it
@@ -210,7 +224,8 @@ msrsb_status msrsb_solve(msrsb_handle *h, const double *b, double *x, double rto
                          int32_t *iters_h, double *relres_h, double *hist_h, cudaStream_t stream);
 
 /* Copies of the set-up results, for checks: p_ids[n][W], p_val[comp][n][W]
- * (handle precision), Ac_dense[nC][nC]; any pointer may be NULL. */
+ * (handle precision), Ac_dense[nC][nC] (A_c expanded to a dense row-major
+ * matrix, nC = nc * bdim); any pointer may be NULL. */
 msrsb_status msrsb_get_setup(msrsb_handle *h, int32_t *p_ids, void *p_val, double *Ac_dense, cudaStream_t stream);
 msrsb_status msrsb_get_info(const msrsb_handle *h, msrsb_info *info_h);
 

@@ -93,6 +93,13 @@ msrsb_status coarse_inverse(int n, const double *Ac, double *Ainv, cudaStream_t 
 msrsb_status coarse_inverse_launch(int n, const double *Ac, double *Ainv, CoarseInverseWork *w, cudaStream_t s);
 msrsb_status coarse_inverse_finish(CoarseInverseWork *w, cudaStream_t s);
 msrsb_status gemv(int n, const double *M, const double *x, double *y, float *y32, cudaStream_t s);
+void coarse_extent(const msrsb_grid *g, int nb[3]);
+msrsb_status stencil_to_dense(int dim, const int nb[3], int bd, const double *Acs, double *dense, cudaStream_t s);
+bool planes_fit(int dim, const int nb[3], int bd);
+msrsb_status plane_factor(int dim, const int nb[3], int bd, const double *Acs, CoarsePlanes *cp, cudaStream_t s);
+msrsb_status plane_solve(int dim, const int nb[3], int bd, const double *Acs, const CoarsePlanes *cp,
+                         const double *vc, double *wc, float *wc32, cudaStream_t s);
+void plane_free(CoarsePlanes *cp, cudaStream_t s);
 msrsb_status wait_selftest(double limit_ms, cudaStream_t s);
 msrsb_status colour_classes(int n, const uint8_t *colour, int ncol, int32_t **rows, int32_t *ptr_h, cudaStream_t s);
 template <typename TF>
@@ -331,9 +338,10 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
         if (st != MSRSB_OK) return fail(st, "%s", tr_err.c_str());
         MSRSB_CUDA(cudaStreamWaitEvent(s, tr_ev, 0));
     }
-    MSRSB_TRY(dalloc(&h->Ac, (size_t)h->nC * h->nC, s));
-    MSRSB_TRY(dalloc(&h->Ainv, (size_t)h->nC * h->nC, s));
-    MSRSB_TRY(galerkin<T>(&A, &h->grid, W, h->nc, h->p_ids, P, h->pt_ptr, h->pt_rows, h->jslot, h->Ac, s));
+    coarse_extent(&h->grid, h->nb);
+    const int nq = h->grid.dim == 3 ? 27 : 9;
+    MSRSB_TRY(dalloc(&h->Acs, (size_t)h->nc * nq * bd * bd, s));
+    MSRSB_TRY(galerkin<T>(&A, &h->grid, W, h->nc, h->p_ids, P, h->pt_ptr, h->pt_rows, h->jslot, h->Acs, s));
     {  // P's values in column order for the restriction
         T *pt = nullptr;
         MSRSB_TRY(dalloc(&pt, (size_t)h->nnz_p * bd, s));
@@ -343,7 +351,20 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
     MSRSB_TRY(mark(3));
     MSRSB_CUDA(cudaEventRecord(go_ev, s));
     release(go_ev);
-    MSRSB_TRY(coarse_inverse(h->nC, h->Ac, h->Ainv, s));
+    if (planes_fit(h->grid.dim, h->nb, bd)) {
+        MSRSB_TRY(plane_factor(h->grid.dim, h->nb, bd, h->Acs, &h->planes, s));
+    } else {
+        if (h->nC > 8192)
+            return fail(MSRSB_ESHAPE, "coarse planes of %d unknowns exceed one cluster and n_C = %d exceeds the "
+                        "dense inverse's 8192", h->nb[0] * (h->grid.dim == 3 ? h->nb[1] : 1) * bd, h->nC);
+        double *Ac = nullptr;
+        MSRSB_TRY(dalloc(&Ac, (size_t)h->nC * h->nC, s));
+        MSRSB_TRY(dalloc(&h->Ainv, (size_t)h->nC * h->nC, s));
+        MSRSB_TRY(stencil_to_dense(h->grid.dim, h->nb, bd, h->Acs, Ac, s));
+        msrsb_status st = coarse_inverse(h->nC, Ac, h->Ainv, s);
+        dfree(Ac, s);
+        MSRSB_TRY(st);
+    }
     MSRSB_TRY(mark(4));
     // apply workspaces
     const long N = (long)n * bd;
@@ -448,7 +469,11 @@ static msrsb_status apply_t(msrsb_handle *h, const TVI *v, TZ *z, cudaStream_t s
         } else {
             MSRSB_TRY((restrict_op<T, TVI>(h, (const T *)h->pt_val, v, h->vc, s)));
         }
-        MSRSB_TRY(gemv(h->nC, h->Ainv, h->vc, h->wc, sizeof(T) == 4 ? h->wc32 : nullptr, s));
+        if (h->Ainv)
+            MSRSB_TRY(gemv(h->nC, h->Ainv, h->vc, h->wc, sizeof(T) == 4 ? h->wc32 : nullptr, s));
+        else
+            MSRSB_TRY(plane_solve(h->grid.dim, h->nb, h->bdim, h->Acs, &h->planes, h->vc, h->wc,
+                                  sizeof(T) == 4 ? h->wc32 : nullptr, s));
         MSRSB_TRY((prolong_op<T, TZ>(h, P, h->wc, h->wc32, z, z32, pre ? 1 : 0, s)));
     } else if (!pre) {
         MSRSB_CUDA(cudaMemsetAsync(z, 0, N * sizeof(TZ), s));  // smoothing only, from z = 0
@@ -894,8 +919,9 @@ static void handle_free(msrsb_handle *h) {
     dfree(h->pt_rows, s);
     dfree(h->jslot, s);
     dfree(h->pt_val, s);
-    dfree(h->Ac, s);
+    dfree(h->Acs, s);
     dfree(h->Ainv, s);
+    plane_free(&h->planes, s);
     dfree(h->ilu.lcol, s);
     dfree(h->ilu.ucol, s);
     dfree(h->ilu.lval, s);
@@ -970,7 +996,6 @@ extern "C" msrsb_status msrsb_setup(const msrsb_mat *A, const msrsb_grid *g, con
     MSRSB_TRY(msrsb_partition_size(g, &n, &nc, &W));
     if (n != A->nrows) return fail(MSRSB_ESHAPE, "grid has %d points but A has %d block rows", n, A->nrows);
     if (g->ncomp != A->bdim) return fail(MSRSB_ESHAPE, "grid ncomp %d != bdim %d", g->ncomp, A->bdim);
-    if ((long)nc * A->bdim > 8192) return fail(MSRSB_ESHAPE, "coarse system too large (nc*bdim = %ld > 8192)", (long)nc * A->bdim);
     if (opts->prec != MSRSB_F64 && opts->prec != MSRSB_F32) return fail(MSRSB_EINVAL, "bad precision");
     if (opts->basis.n_it < 1 || opts->basis.max_iter < 0) return fail(MSRSB_EINVAL, "bad basis options");
     if (opts->smoother < MSRSB_SMOOTH_NONE || opts->smoother > MSRSB_SMOOTH_L1JAC)
@@ -1048,9 +1073,7 @@ extern "C" msrsb_status msrsb_get_setup(msrsb_handle *h, int32_t *p_ids, void *p
     size_t es = h->opts.prec == MSRSB_F32 ? sizeof(float) : sizeof(double);
     if (p_ids) MSRSB_CUDA(cudaMemcpyAsync(p_ids, h->p_ids, nW * sizeof(int32_t), cudaMemcpyDeviceToDevice, stream));
     if (p_val) MSRSB_CUDA(cudaMemcpyAsync(p_val, h->p_val, nW * h->bdim * es, cudaMemcpyDeviceToDevice, stream));
-    if (Ac_dense)
-        MSRSB_CUDA(cudaMemcpyAsync(Ac_dense, h->Ac, (size_t)h->nC * h->nC * sizeof(double), cudaMemcpyDeviceToDevice,
-                                   stream));
+    if (Ac_dense) MSRSB_TRY(stencil_to_dense(h->grid.dim, h->nb, h->bdim, h->Acs, Ac_dense, stream));
     return MSRSB_OK;
 }
 

@@ -1,0 +1,483 @@
+// Coarse solver M_c^-1 = A_c^-1 (Alg. 2 and Alg. 3 of arXiv 1912.06934) in
+// FP64, built on the 3^d stencil of the Galerkin operator.
+//
+// A_c couples a coarse node only with the coarse nodes at most one coarse
+// step away on every axis (Eq. 3 with the support regions of Sec. 2.1).
+// Numbered plane by plane along the last grid axis (z in 3D, y in 2D), A_c is
+// block tridiagonal: D_k on the diagonal (the couplings inside plane k),
+// L_k = A_c[k][k-1] and U_k = A_c[k][k+1]. Its block LU factorisation
+//   S_0 = D_0,  S_k = D_k - L_k S_{k-1}^-1 U_{k-1},
+// needs only the inverse of each plane's dense Schur complement S_k (m x m,
+// m = nodes per plane x block size) and G_k = S_k^-1 U_k: np m^3 multiply-adds
+// instead of the (np m)^3 of a dense inverse. A_c^-1 v is then
+//   y_0 = S_0^-1 v_0,  y_k = S_k^-1 (v_k - L_k y_{k-1}),
+//   w_{np-1} = y_{np-1},  w_k = y_k - G_k w_{k+1},
+// that is 2 np - 1 dependent dense matrix-vector products.
+//
+// Every S_k is inverted by Gauss-Jordan elimination with partial pivoting
+// inside the plane (ties to the lowest row; magnitudes compared through the
+// integer order of their FP64 bit patterns). Both the factorisation and the
+// application run as one thread-block cluster (up to 16 CTAs on 16 SMs) whose
+// CTAs own contiguous columns (factorisation) or rows (application) and
+// exchange pivot columns and partial vectors through distributed shared
+// memory, with hardware cluster barriers between steps (no spin waits).
+#include "common.cuh"
+#include <cooperative_groups.h>
+#include <mutex>
+
+namespace cg = cooperative_groups;
+
+namespace msrsb {
+
+// Offsets and sizes of the plane structure. Node J of the coarse grid
+// (x fastest) lies in plane k = J / PN at in-plane index u = J % PN; dof
+// J * bd + l of A_c is row u * bd + l of plane k. Stencil entry q of a node
+// couples it with the node at offset (q%3 - 1, (q/3)%3 - 1, q/9 - 1); with NI
+// in-plane offsets a (9 in 3D, 3 in 2D) and plane offset o in {-1, 0, 1},
+// q = a + NI * (o + 1).
+struct PlaneGeom {
+    int dim, nb0, nb1, bd;
+    int np;   // planes
+    int PN;   // coarse nodes per plane
+    int m;    // rows of a plane = PN * bd
+    int NI;   // in-plane stencil offsets
+    int nq;   // stencil entries per node (3^dim)
+};
+
+// In-plane neighbour of local node u at in-plane offset a, or -1.
+__device__ __forceinline__ int plane_nbr(const PlaneGeom &G, int u, int a) {
+    if (G.dim == 3) {
+        const int u0 = u % G.nb0 + a % 3 - 1, u1 = u / G.nb0 + a / 3 - 1;
+        return (u0 < 0 || u0 >= G.nb0 || u1 < 0 || u1 >= G.nb1) ? -1 : u0 + G.nb0 * u1;
+    }
+    const int u0 = u + a - 1;
+    return (u0 < 0 || u0 >= G.nb0) ? -1 : u0;
+}
+
+// In-plane offset index a with node v = plane_nbr(u, a), or -1 if v is not
+// adjacent to u.
+__device__ __forceinline__ int plane_offset(const PlaneGeom &G, int u, int v) {
+    if (G.dim == 3) {
+        const int d0 = v % G.nb0 - u % G.nb0, d1 = v / G.nb0 - u / G.nb0;
+        return (d0 < -1 || d0 > 1 || d1 < -1 || d1 > 1) ? -1 : (d0 + 1) + 3 * (d1 + 1);
+    }
+    const int d0 = v - u;
+    return (d0 < -1 || d0 > 1) ? -1 : d0 + 1;
+}
+
+// Stencil value: row (node J, component l), stencil entry q, column component c.
+__device__ __forceinline__ double st_val(const double *__restrict__ Acs, const PlaneGeom &G, int J, int q, int l,
+                                         int c) {
+    return Acs[(((long)J * G.nq + q) * G.bd + l) * G.bd + c];
+}
+
+constexpr int kPlaneThreads = 256;
+constexpr int kPlaneMaxCols = 128;  // columns of a plane one CTA of the factorisation owns
+
+// Factorisation. Outputs (row-major m x m per plane): X_k with
+// S_k^-1 = X_k Pi_k (Pi_k the row interchanges of the elimination, kept as
+// the gather pi_k: (Pi_k v)[i] = v[pi_k[i]]), and G_k = S_k^-1 U_k.
+// status[0] = 1 + (global row) on a zero pivot.
+__global__ void __launch_bounds__(kPlaneThreads) plane_factor_kernel(PlaneGeom G, const double *__restrict__ Acs,
+                                                                     double *__restrict__ X, double *__restrict__ Gm,
+                                                                     int *__restrict__ pi, int *__restrict__ status) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank(), nct = (int)cluster.num_blocks();
+    const int m = G.m, bd = G.bd, NI = G.NI;
+    const int cw = (m + nct - 1) / nct;
+    const int c0 = rank * cw, c1 = min(m, c0 + cw), ncol = max(0, c1 - c0);
+    const int tid = threadIdx.x;
+    extern __shared__ double sm[];
+    double *Sown = sm;                       // own columns of S_k, column-major [cw][m]
+    double *fbuf = Sown + (long)cw * m;      // published pivot column, double buffered [2][m]
+    double *floc = fbuf + 2 * m;             // local copy of the pivot column [m]
+    int *piv_hist = (int *)(floc + m);       // pivot row of every step [m]
+    int *pil = piv_hist + m;                 // gather pi [m]
+    int *pinv = pil + m;                     // inverse of pi [m]
+    __shared__ double s_inv[2], s_xk[kPlaneMaxCols];
+    __shared__ int s_p[2], s_bad[2];
+    __shared__ double s_best[8];
+    __shared__ int s_idx[8];
+    for (int k = 0; k < G.np; ++k) {
+        // ---- S_k = D_k - L_k G_{k-1}, own columns ----
+        const int Jbase = k * G.PN;
+        for (int idx = tid; idx < ncol * m; idx += kPlaneThreads) {
+            const int jl = idx / m, i = idx - jl * m;
+            const int j = c0 + jl;
+            const int ui = i / bd, l = i - ui * bd, uj = j / bd, mj = j - uj * bd;
+            const int a = plane_offset(G, ui, uj);
+            double v = a >= 0 ? st_val(Acs, G, Jbase + ui, a + NI, l, mj) : 0.0;
+            if (k > 0) {
+                const double *Gp = Gm + (long)(k - 1) * m * m;
+                for (int b = 0; b < NI; ++b) {
+                    const int t = plane_nbr(G, ui, b);
+                    if (t < 0) continue;
+                    for (int c = 0; c < bd; ++c)
+                        v = fma(-st_val(Acs, G, Jbase + ui, b, l, c), Gp[(long)(t * bd + c) * m + j], v);
+                }
+            }
+            Sown[(long)jl * m + i] = v;
+        }
+        __syncthreads();
+        // ---- Gauss-Jordan with partial pivoting, one pivot per step ----
+        for (int kk = 0; kk < m; ++kk) {
+            const int owner = kk / cw, buf = kk & 1;
+            if (rank == owner) {
+                double *col = Sown + (long)(kk - c0) * m;
+                // largest |col[i]|, kk <= i < m, ties to the lowest index
+                long long best = -1;
+                int bi = m;
+                for (int i = kk + tid; i < m; i += kPlaneThreads) {
+                    const long long v = __double_as_longlong(col[i]) & 0x7fffffffffffffffLL;
+                    if (v > best) {
+                        best = v;
+                        bi = i;
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const long long b2 = __shfl_xor_sync(0xffffffffu, best, o);
+                    const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+                    if (b2 > best || (b2 == best && i2 < bi)) {
+                        best = b2;
+                        bi = i2;
+                    }
+                }
+                long long *sb = reinterpret_cast<long long *>(s_best);
+                if ((tid & 31) == 0) {
+                    sb[tid >> 5] = best;
+                    s_idx[tid >> 5] = bi;
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    long long bb = sb[0];
+                    int bj = s_idx[0];
+                    for (int w = 1; w < kPlaneThreads / 32; ++w)
+                        if (sb[w] > bb || (sb[w] == bb && s_idx[w] < bj)) {
+                            bb = sb[w];
+                            bj = s_idx[w];
+                        }
+                    const double pv = bj < m ? col[bj] : 0.0;
+                    const int bad = (bj >= m || pv == 0.0 || !isfinite(pv)) ? 1 : 0;
+                    if (!bad && bj != kk) {
+                        const double t = col[kk];
+                        col[kk] = col[bj];
+                        col[bj] = t;
+                    }
+                    s_p[buf] = bj < m ? bj : kk;
+                    s_bad[buf] = bad;
+                    s_inv[buf] = bad ? 0.0 : 1.0 / pv;
+                }
+                __syncthreads();
+                for (int i = tid; i < m; i += kPlaneThreads) fbuf[buf * m + i] = col[i];
+            }
+            cluster.sync();  // the owner's pivot column is published
+            const int *op = cluster.map_shared_rank(s_p, owner);
+            const int *ob = cluster.map_shared_rank(s_bad, owner);
+            const double *oi = cluster.map_shared_rank(s_inv, owner);
+            const double *of = cluster.map_shared_rank(fbuf, owner) + buf * m;
+            const int p = op[buf], bad = ob[buf];
+            const double inv = oi[buf];
+            if (bad) {
+                if (rank == 0 && tid == 0) *status = 1 + k * m + kk;
+                cluster.sync();  // no CTA leaves while another may still read its shared memory
+                return;
+            }
+            for (int i = tid; i < m; i += kPlaneThreads) floc[i] = of[i];
+            if (tid == 0) piv_hist[kk] = p;
+            if (tid < ncol) {  // row interchange and scaled pivot-row entry of every own column but kk
+                const int j = c0 + tid;
+                if (j != kk) {
+                    double *cj = Sown + (long)tid * m;
+                    double x = cj[kk];
+                    if (p != kk) {
+                        const double y = cj[p];
+                        cj[p] = x;
+                        x = y;
+                    }
+                    x *= inv;
+                    cj[kk] = x;
+                    s_xk[tid] = x;
+                }
+            }
+            __syncthreads();
+            for (int idx = tid; idx < ncol * m; idx += kPlaneThreads) {
+                const int jl = idx / m, i = idx - jl * m;
+                double *cj = Sown + (long)jl * m;
+                if (c0 + jl == kk)
+                    cj[i] = i == kk ? inv : -floc[i] * inv;
+                else if (i != kk)
+                    cj[i] = fma(-floc[i], s_xk[jl], cj[i]);
+            }
+            __syncthreads();
+        }
+        // ---- the gather pi_k and its inverse (every CTA, from the pivot history) ----
+        if (tid == 0) {
+            for (int i = 0; i < m; ++i) pil[i] = i;
+            for (int kk = 0; kk < m; ++kk) {
+                const int p = piv_hist[kk];
+                const int t = pil[kk];
+                pil[kk] = pil[p];
+                pil[p] = t;
+            }
+            for (int i = 0; i < m; ++i) pinv[pil[i]] = i;
+        }
+        __syncthreads();
+        // ---- X_k (own columns, row-major in global) and pi_k ----
+        double *Xk = X + (long)k * m * m;
+        for (int idx = tid; idx < ncol * m; idx += kPlaneThreads) {
+            const int i = idx / ncol, jl = idx - i * ncol;
+            Xk[(long)i * m + c0 + jl] = Sown[(long)jl * m + i];
+        }
+        if (rank == 0)
+            for (int i = tid; i < m; i += kPlaneThreads) pi[(long)k * m + i] = pil[i];
+        cluster.sync();  // every CTA's X_k columns are final
+        // ---- G_k = X_k Pi_k U_k, own columns j (rows of plane k+1) ----
+        if (k + 1 < G.np) {
+            double *Gk = Gm + (long)k * m * m;
+            const int Jnext = (k + 1) * G.PN;
+            for (int idx = tid; idx < ncol * m; idx += kPlaneThreads) {
+                const int i = idx / ncol, jl = idx - i * ncol;
+                const int j = c0 + jl, uj = j / bd, mj = j - uj * bd;
+                double v = 0.0;
+                // rows s of plane k with U_k[s][j] != 0: the in-plane neighbours of uj
+                for (int a = 0; a < NI; ++a) {
+                    const int us = plane_nbr(G, uj, a);
+                    if (us < 0) continue;
+                    const int q = plane_offset(G, us, uj) + 2 * NI;  // from s up to j: plane offset +1
+                    for (int ls = 0; ls < bd; ++ls) {
+                        const double u = st_val(Acs, G, Jbase + us, q, ls, mj);
+                        const int cc = pinv[us * bd + ls];
+                        const int ow = cc / cw;
+                        const double *xc = cluster.map_shared_rank(Sown, ow) + (long)(cc - ow * cw) * m;
+                        v = fma(xc[i], u, v);
+                    }
+                }
+                (void)Jnext;
+                Gk[(long)i * m + j] = v;
+            }
+        }
+        cluster.sync();  // remote reads of this plane's X columns are done before they are overwritten
+    }
+}
+
+// Application w = A_c^-1 v through the plane factors. vc, wc: FP64 [np*m]
+// in coarse dof order; wc32 (nullable) an FP32 copy of w.
+__global__ void __launch_bounds__(kPlaneThreads) plane_solve_kernel(PlaneGeom G, const double *__restrict__ Acs,
+                                                                    const double *__restrict__ X,
+                                                                    const double *__restrict__ Gm,
+                                                                    const int *__restrict__ pi,
+                                                                    const double *__restrict__ vc,
+                                                                    double *__restrict__ wc, float *__restrict__ wc32) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank(), nct = (int)cluster.num_blocks();
+    const int m = G.m, bd = G.bd, NI = G.NI;
+    const int rw = (m + nct - 1) / nct;
+    const int r0 = rank * rw, r1 = min(m, r0 + rw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    extern __shared__ double sm[];
+    double *ybuf = sm;          // full plane vector, double buffered [2][m] (written by every CTA)
+    double *t = ybuf + 2 * m;   // right-hand side of the plane [m]
+    double *tp = t + m;         // t gathered by pi [m]
+    pdl_prologue();
+    // ---- forward: y_k = X_k Pi_k (v_k - L_k y_{k-1}) ----
+    for (int k = 0; k < G.np; ++k) {
+        const double *yprev = ybuf + ((k + 1) & 1) * m;
+        const int Jbase = k * G.PN;
+        for (int j = tid; j < m; j += kPlaneThreads) {
+            const int uj = j / bd, l = j - uj * bd;
+            double v = vc[(long)(Jbase + uj) * bd + l];
+            if (k > 0)
+                for (int b = 0; b < NI; ++b) {
+                    const int tn = plane_nbr(G, uj, b);
+                    if (tn < 0) continue;
+                    for (int c = 0; c < bd; ++c) v = fma(-st_val(Acs, G, Jbase + uj, b, l, c), yprev[tn * bd + c], v);
+                }
+            t[j] = v;
+        }
+        __syncthreads();
+        const int *pk = pi + (long)k * m;
+        for (int j = tid; j < m; j += kPlaneThreads) tp[j] = t[pk[j]];
+        __syncthreads();
+        const double *Xk = X + (long)k * m * m;
+        double *ynew = ybuf + (k & 1) * m;
+        for (int i = r0 + warp; i < r1; i += kPlaneThreads / 32) {
+            const double *xr = Xk + (long)i * m;
+            double s = 0.0;
+            for (int j = lane; j < m; j += 32) s = fma(__ldg(xr + j), tp[j], s);
+            s = warp_sum(s);
+            if (lane == 0) {
+                for (int r = 0; r < nct; ++r) cluster.map_shared_rank(ynew, r)[i] = s;
+                wc[(long)(Jbase + i / bd) * bd + i % bd] = s;
+            }
+        }
+        cluster.sync();
+    }
+    // ---- backward: w_{np-1} = y_{np-1}; w_k = y_k - G_k w_{k+1} ----
+    {
+        const int k = G.np - 1;
+        if (wc32)
+            for (int i = r0 + tid; i < r1; i += kPlaneThreads) {
+                const long q = (long)(k * G.PN + i / bd) * bd + i % bd;
+                wc32[q] = (float)ybuf[(k & 1) * m + i];
+            }
+    }
+    for (int k = G.np - 2; k >= 0; --k) {
+        const double *wnext = ybuf + ((k + 1) & 1) * m;
+        double *wnew = ybuf + (k & 1) * m;
+        const double *Gk = Gm + (long)k * m * m;
+        const int Jbase = k * G.PN;
+        for (int i = r0 + warp; i < r1; i += kPlaneThreads / 32) {
+            const double *gr = Gk + (long)i * m;
+            double s = 0.0;
+            for (int j = lane; j < m; j += 32) s = fma(__ldg(gr + j), wnext[j], s);
+            s = warp_sum(s);
+            if (lane == 0) {
+                const long q = (long)(Jbase + i / bd) * bd + i % bd;
+                const double w = wc[q] - s;
+                for (int r = 0; r < nct; ++r) cluster.map_shared_rank(wnew, r)[i] = w;
+                wc[q] = w;
+                if (wc32) wc32[q] = (float)w;
+            }
+        }
+        cluster.sync();
+    }
+}
+
+// ---- host side ----------------------------------------------------------------------
+
+static size_t factor_smem(int m, int nct) {
+    const int cw = (m + nct - 1) / nct;
+    return (size_t)cw * m * sizeof(double) + 3 * (size_t)m * sizeof(double) + 3 * (size_t)m * sizeof(int);
+}
+static size_t solve_smem(int m) { return 4 * (size_t)m * sizeof(double); }
+
+constexpr size_t kPlaneSmemMax = 220 * 1024;
+
+static cudaLaunchConfig_t cluster_cfg(cudaLaunchAttribute *attr, int nct, size_t smem, cudaStream_t s, bool pdl) {
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = nct;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nct);
+    cfg.blockDim = dim3(kPlaneThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 2 : 1;
+    return cfg;
+}
+
+// Cluster size for planes of m rows: the largest of 16 (where the device
+// allows non-portable clusters), 8, 4, 2, 1, not above m, whose shared memory
+// fits and which the device can schedule; 0 if none.
+static int plane_cluster(int m) {
+    static int cap = 0;  // set once per process; the attributes are per function
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cap = 8;
+        if (cudaFuncSetAttribute(plane_factor_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                cudaSuccess &&
+            cudaFuncSetAttribute(plane_solve_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                cudaSuccess)
+            cap = 16;
+        cudaFuncSetAttribute(plane_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPlaneSmemMax);
+        cudaFuncSetAttribute(plane_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPlaneSmemMax);
+        cudaGetLastError();
+    });
+    if (m < 1 || solve_smem(m) > kPlaneSmemMax) return 0;
+    for (int nct = cap; nct >= 1; nct >>= 1) {
+        if (nct > m) continue;
+        const int cw = (m + nct - 1) / nct;
+        const size_t sf = factor_smem(m, nct);
+        if (cw > kPlaneMaxCols || sf > kPlaneSmemMax) return 0;  // smaller clusters need more per CTA
+        cudaLaunchAttribute attr[2];
+        cudaLaunchConfig_t cf = cluster_cfg(attr, nct, sf, nullptr, false);
+        cudaLaunchConfig_t cs = cluster_cfg(attr, nct, solve_smem(m), nullptr, false);
+        int nf = 0, ns = 0;
+        if (cudaOccupancyMaxActiveClusters(&nf, plane_factor_kernel, &cf) != cudaSuccess ||
+            cudaOccupancyMaxActiveClusters(&ns, plane_solve_kernel, &cs) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        if (nf > 0 && ns > 0) return nct;
+    }
+    return 0;
+}
+
+static void plane_geom(int dim, const int nb[3], int bd, PlaneGeom *G) {
+    G->dim = dim;
+    G->nb0 = nb[0];
+    G->nb1 = dim == 3 ? nb[1] : 1;
+    G->bd = bd;
+    G->np = dim == 3 ? nb[2] : nb[1];
+    G->PN = dim == 3 ? nb[0] * nb[1] : nb[0];
+    G->m = G->PN * bd;
+    G->NI = dim == 3 ? 9 : 3;
+    G->nq = dim == 3 ? 27 : 9;
+}
+
+// Whether the plane factorisation serves this coarse grid (one cluster holds
+// a plane); otherwise the caller uses the dense inverse.
+bool planes_fit(int dim, const int nb[3], int bd) {
+    PlaneGeom G;
+    plane_geom(dim, nb, bd, &G);
+    return plane_cluster(G.m) > 0;
+}
+
+msrsb_status plane_factor(int dim, const int nb[3], int bd, const double *Acs, CoarsePlanes *cp, cudaStream_t s) {
+    PlaneGeom G;
+    plane_geom(dim, nb, bd, &G);
+    const int nct = plane_cluster(G.m);
+    if (!nct) return fail(MSRSB_ESHAPE, "coarse planes of %d unknowns do not fit one thread-block cluster", G.m);
+    cp->m = G.m;
+    cp->np = G.np;
+    cp->nct = nct;
+    const long mm = (long)G.m * G.m;
+    MSRSB_TRY(dalloc(&cp->X, (size_t)G.np * mm, s));
+    MSRSB_TRY(dalloc(&cp->G, (size_t)(G.np > 1 ? G.np - 1 : 1) * mm, s));
+    MSRSB_TRY(dalloc(&cp->pi, (size_t)G.np * G.m, s));
+    int *status = nullptr;
+    MSRSB_TRY(dalloc(&status, 1, s));
+    MSRSB_CUDA(cudaMemsetAsync(status, 0, sizeof(int), s));
+    cudaLaunchAttribute attr[2];
+    cudaLaunchConfig_t cfg = cluster_cfg(attr, nct, factor_smem(G.m, nct), s, false);
+    count_launch();
+    MSRSB_CUDA(cudaLaunchKernelEx(&cfg, plane_factor_kernel, G, Acs, cp->X, cp->G, cp->pi, status));
+    int h = 0;
+    MSRSB_CUDA(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MSRSB_CUDA(cudaStreamSynchronize(s));
+    dfree(status, s);
+    if (h) return fail(MSRSB_EBREAKDOWN, "coarse operator is singular (zero pivot at coarse row %d)", h - 1);
+    return MSRSB_OK;
+}
+
+msrsb_status plane_solve(int dim, const int nb[3], int bd, const double *Acs, const CoarsePlanes *cp,
+                         const double *vc, double *wc, float *wc32, cudaStream_t s) {
+    PlaneGeom G;
+    plane_geom(dim, nb, bd, &G);
+    cudaLaunchAttribute attr[2];
+    cudaLaunchConfig_t cfg = cluster_cfg(attr, cp->nct, solve_smem(G.m), s, true);
+    count_launch();
+    cudaError_t e = cudaLaunchKernelEx(&cfg, plane_solve_kernel, G, Acs, (const double *)cp->X,
+                                       (const double *)cp->G, (const int *)cp->pi, vc, wc, wc32);
+    if (e == cudaErrorNotSupported || e == cudaErrorInvalidValue) {  // programmatic serialisation refused
+        cudaGetLastError();
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, plane_solve_kernel, G, Acs, (const double *)cp->X, (const double *)cp->G,
+                               (const int *)cp->pi, vc, wc, wc32);
+    }
+    MSRSB_CUDA(e);
+    return MSRSB_OK;
+}
+
+void plane_free(CoarsePlanes *cp, cudaStream_t s) {
+    dfree(cp->X, s);
+    dfree(cp->G, s);
+    dfree(cp->pi, s);
+}
+
+}  // namespace msrsb

@@ -137,6 +137,15 @@ struct CoarseInverseWork {
     int h_status = 0;
 };
 
+// Block-LU factors of the coarse operator over coarse planes (see
+// coarse_planes.cu): per plane X_k (m x m, row-major) with S_k^-1 = X_k Pi_k,
+// the gather pi_k, and G_k = S_k^-1 U_k.
+struct CoarsePlanes {
+    int m = 0, np = 0, nct = 0;
+    double *X = nullptr, *G = nullptr;
+    int *pi = nullptr;
+};
+
 // ILU(0) factors per colour in ELL blocks over colour-ordered positions
 struct IluEll {
     int ncol = 0;
@@ -200,8 +209,13 @@ struct msrsb_handle {
     int8_t *jslot = nullptr;  // slot of coarse node J in every row of its support
     int nnz_p = 0;             // entries of P's pattern (per component)
     void *pt_val = nullptr;    // P's values in pt_rows order [ncomp][nnz_p], handle precision
-    // coarse operator and its inverse (FP64, dense nC x nC)
-    double *Ac = nullptr, *Ainv = nullptr;
+    // coarse operator as its 3^dim stencil Acs[nc][3^dim][bdim][bdim] (FP64),
+    // and the coarse solver: block-LU factors over coarse planes, or (when a
+    // plane does not fit one thread-block cluster) the dense inverse
+    double *Acs = nullptr;
+    int nb[3] = {1, 1, 1};
+    msrsb::CoarsePlanes planes;
+    double *Ainv = nullptr;
     // smoother factors in A's (block) pattern, handle precision
     msrsb::IluEll ilu;          // ILU(0) factors (colour order), handle precision
     int32_t *pos_of = nullptr;  // colour-order position of every fine row

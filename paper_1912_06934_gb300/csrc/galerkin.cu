@@ -127,13 +127,14 @@ __global__ void __launch_bounds__(128) ap_kernel(int n, int W, int ncode, const 
 
 // Pass 2, one CTA per coarse node J: A_c[J*BD+l][L*BD+m] = sum over fine rows
 // i of supp(J) (ascending) of P^l_{iJ} AP[i][code(L)][l][m]; thread-private
-// sums, then a fixed-order block reduction. Writes the whole dense row.
+// sums, then a fixed-order block reduction. Writes J's whole stencil row:
+// Acs[J][q][l][m], q = sum_d (L_d - J_d + 1) 3^d, zero where L is off the grid.
 template <typename T, int BD>
 __global__ void __launch_bounds__(128) ptap_kernel(int n, int W, int nc, int ncode, int dim, int nb0, int nb1, int nb2,
                                                    const T *__restrict__ P, const int32_t *__restrict__ pt_ptr,
                                                    const int32_t *__restrict__ pt_rows,
                                                    const int8_t *__restrict__ jslot, const double *__restrict__ AP,
-                                                   double *__restrict__ Ac) {
+                                                   double *__restrict__ Acs) {
     constexpr int NQ = 27 * BD * BD;
     __shared__ double red[NQ][4];
     const int J = blockIdx.x;
@@ -161,7 +162,6 @@ __global__ void __launch_bounds__(128) ptap_kernel(int n, int W, int nc, int nco
     __syncthreads();
     // coarse coordinates of J
     const int j0 = J % nb0, j1 = (J / nb0) % nb1, j2 = dim == 3 ? J / (nb0 * nb1) : 0;
-    const int nC = nc * BD;
     for (int q = threadIdx.x; q < nq; q += blockDim.x) {
         const double v = (red[q][0] + red[q][1]) + (red[q][2] + red[q][3]);
         const int m = q % BD, l = (q / BD) % BD, s = q / (BD * BD);
@@ -170,9 +170,9 @@ __global__ void __launch_bounds__(128) ptap_kernel(int n, int W, int nc, int nco
         const int L0 = j0 - 1 + ((r0 - (j0 - 1)) % 3 + 3) % 3;
         const int L1 = j1 - 1 + ((r1 - (j1 - 1)) % 3 + 3) % 3;
         const int L2 = dim == 3 ? j2 - 1 + ((r2 - (j2 - 1)) % 3 + 3) % 3 : 0;
-        if (L0 < 0 || L0 >= nb0 || L1 < 0 || L1 >= nb1 || L2 < 0 || L2 >= nb2) continue;
-        const int L = L0 + nb0 * (L1 + nb1 * L2);
-        Ac[(long)(J * BD + l) * nC + L * BD + m] = v;
+        const bool in = !(L0 < 0 || L0 >= nb0 || L1 < 0 || L1 >= nb1 || L2 < 0 || L2 >= nb2);
+        const int qo = (L0 - j0 + 1) + 3 * (L1 - j1 + 1) + (dim == 3 ? 9 * (L2 - j2 + 1) : 0);
+        Acs[(((long)J * ncode + qo) * BD + l) * BD + m] = in ? v : 0.0;
     }
 }
 
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(128) ptap1_kernel(int n, int W, int nc, int di
                                                     const T *__restrict__ P, const int32_t *__restrict__ pt_ptr,
                                                     const int32_t *__restrict__ pt_rows,
                                                     const int8_t *__restrict__ jslot, const double *__restrict__ AP,
-                                                    double *__restrict__ Ac) {
+                                                    double *__restrict__ Acs) {
     __shared__ double red[NCODE][4];
     const int J = blockIdx.x;
     const int sj = jslot[J];
@@ -245,12 +245,22 @@ __global__ void __launch_bounds__(128) ptap1_kernel(int n, int W, int nc, int di
         const int L0 = j0 - 1 + ((r0 - (j0 - 1)) % 3 + 3) % 3;
         const int L1 = j1 - 1 + ((r1 - (j1 - 1)) % 3 + 3) % 3;
         const int L2 = dim == 3 ? j2 - 1 + ((r2 - (j2 - 1)) % 3 + 3) % 3 : 0;
-        if (L0 < 0 || L0 >= nb0 || L1 < 0 || L1 >= nb1 || L2 < 0 || L2 >= nb2) continue;
-        const int L = L0 + nb0 * (L1 + nb1 * L2);
-        Ac[(long)J * nc + L] = v;
+        const bool in = !(L0 < 0 || L0 >= nb0 || L1 < 0 || L1 >= nb1 || L2 < 0 || L2 >= nb2);
+        const int qo = (L0 - j0 + 1) + 3 * (L1 - j1 + 1) + (dim == 3 ? 9 * (L2 - j2 + 1) : 0);
+        Acs[(long)J * NCODE + qo] = in ? v : 0.0;
     }
 }
 
+// Coarse-grid extent per axis implied by a grid (1 beyond its dimension).
+void coarse_extent(const msrsb_grid *g, int nb[3]) {
+    const int dim = g->dim;
+    int nn[3] = {g->nx, g->ny, dim == 3 ? g->nz : 1};
+    int hh[3] = {g->hx, g->hy, dim == 3 ? g->hz : 1};
+    for (int d = 0; d < 3; ++d)
+        nb[d] = d >= dim ? 1 : (g->centering == 0 ? (nn[d] + hh[d] - 1) / hh[d] : (nn[d] - 1 + hh[d] - 1) / hh[d] + 1);
+}
+
+// A_c = P^T A P as the coarse stencil Acs[nc][3^dim][bd][bd] (see ptap_kernel).
 template <typename T>
 msrsb_status galerkin(const msrsb_mat *A, const msrsb_grid *g, int W, int nc, const int32_t *p_ids, const T *P,
                       const int32_t *pt_ptr, const int32_t *pt_rows, const int8_t *jslot, double *Ac,
@@ -258,19 +268,12 @@ msrsb_status galerkin(const msrsb_mat *A, const msrsb_grid *g, int W, int nc, co
     const int BD = A->bdim, n = A->nrows, dim = g->dim;
     const int ncode = dim == 3 ? 27 : 9;
     int nb[3];
-    {
-        int nn[3] = {g->nx, g->ny, dim == 3 ? g->nz : 1};
-        int hh[3] = {g->hx, g->hy, dim == 3 ? g->hz : 1};
-        for (int d = 0; d < 3; ++d)
-            nb[d] = d >= dim ? 1 : (g->centering == 0 ? (nn[d] + hh[d] - 1) / hh[d] : (nn[d] - 1 + hh[d] - 1) / hh[d] + 1);
-    }
+    coarse_extent(g, nb);
     if (nb[0] * nb[1] * nb[2] != nc) return fail(MSRSB_ESHAPE, "grid implies %d coarse nodes, got %d", nb[0] * nb[1] * nb[2], nc);
-    const long nC = (long)nc * BD;
     int8_t *code = nullptr;
     double *AP = nullptr;
     MSRSB_TRY(dalloc(&code, nc, s));
     MSRSB_TRY(dalloc(&AP, (size_t)n * ncode * BD * BD, s));
-    MSRSB_CUDA(cudaMemsetAsync(Ac, 0, (size_t)nC * nC * sizeof(double), s));
     coarse_code_kernel<<<ceil_div(nc, 256), 256, 0, s>>>(nc, nb[0], nb[1], dim, code);
     MSRSB_LAUNCHED("coarse_code_kernel");
     if (BD == 1 && ncode == 27) {
@@ -301,32 +304,129 @@ template msrsb_status galerkin<double>(const msrsb_mat *, const msrsb_grid *, in
 template msrsb_status galerkin<float>(const msrsb_mat *, const msrsb_grid *, int, int, const int32_t *, const float *,
                                       const int32_t *, const int32_t *, const int8_t *, double *, cudaStream_t);
 
+// ---- the coarse stencil as a dense matrix or block CSR ------------------------------
+
+__device__ __forceinline__ int stencil_nbr(int J, int q, int dim, int nb0, int nb1, int nb2) {
+    const int j0 = J % nb0, j1 = (J / nb0) % nb1, j2 = J / (nb0 * nb1);
+    const int L0 = j0 + q % 3 - 1, L1 = j1 + (q / 3) % 3 - 1, L2 = dim == 3 ? j2 + q / 9 - 1 : 0;
+    if (L0 < 0 || L0 >= nb0 || L1 < 0 || L1 >= nb1 || L2 < 0 || L2 >= nb2) return -1;
+    return L0 + nb0 * (L1 + nb1 * L2);
+}
+
+// dense[(J*bd + l) * nC + L*bd + m] = Acs[J][q][l][m] for the stencil's
+// neighbours L (the rest of the matrix must be zero on entry)
+__global__ void stencil_dense_kernel(int nc, int dim, int nb0, int nb1, int nb2, int bd, const double *__restrict__ Acs,
+                                     double *__restrict__ dense) {
+    const int nq = dim == 3 ? 27 : 9;
+    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long)nc * nq) return;
+    const int J = (int)(idx / nq), q = (int)(idx % nq);
+    const int L = stencil_nbr(J, q, dim, nb0, nb1, nb2);
+    if (L < 0) return;
+    const long nC = (long)nc * bd;
+    for (int l = 0; l < bd; ++l)
+        for (int m = 0; m < bd; ++m) dense[((long)J * bd + l) * nC + (long)L * bd + m] = Acs[((idx * bd) + l) * bd + m];
+}
+
+msrsb_status stencil_to_dense(int dim, const int nb[3], int bd, const double *Acs, double *dense, cudaStream_t s) {
+    const int nc = nb[0] * nb[1] * nb[2], nq = dim == 3 ? 27 : 9;
+    const long nC = (long)nc * bd;
+    MSRSB_CUDA(cudaMemsetAsync(dense, 0, (size_t)nC * nC * sizeof(double), s));
+    stencil_dense_kernel<<<ceil_div((long)nc * nq, 256), 256, 0, s>>>(nc, dim, nb[0], nb[1], nb[2], bd, Acs, dense);
+    MSRSB_LAUNCHED("stencil_dense_kernel");
+    return MSRSB_OK;
+}
+
+// Block CSR of the stencil: row J holds its in-grid neighbours in ascending
+// column order (stencil entries are ordered by the z, then y, then x offset,
+// which is the order of the lexicographic coarse index). One thread per row;
+// the row start is the count of in-grid neighbours of every earlier row, a
+// product of per-axis counts summed in closed form.
+__device__ __forceinline__ long axis_prefix(int j, int nb) {
+    // sum over i < j of the in-grid neighbours of coarse coordinate i on one axis
+    if (nb == 1) return j;
+    if (j == 0) return 0;
+    return 2 + 3L * (j - 1) - (j == nb ? 1 : 0);
+}
+__device__ __forceinline__ int axis_count(int j, int nb) { return nb == 1 ? 1 : 3 - (j == 0) - (j == nb - 1); }
+
+__global__ void stencil_bsr_kernel(int nc, int dim, int nb0, int nb1, int nb2, int bd, const double *__restrict__ Acs,
+                                   int32_t *__restrict__ rowptr, int32_t *__restrict__ colidx,
+                                   double *__restrict__ val) {
+    const int J = blockIdx.x * blockDim.x + threadIdx.x;
+    if (J >= nc) return;
+    const int nq = dim == 3 ? 27 : 9;
+    const int j0 = J % nb0, j1 = (J / nb0) % nb1, j2 = J / (nb0 * nb1);
+    // rows before J: full z-slabs, then full y-lines of J's slab, then x
+    const long tot0 = axis_prefix(nb0, nb0), tot1 = axis_prefix(nb1, nb1);
+    const long before = axis_prefix(j2, nb2) * tot1 * tot0 + (long)axis_count(j2, nb2) * (axis_prefix(j1, nb1) * tot0 +
+                        (long)axis_count(j1, nb1) * axis_prefix(j0, nb0));
+    long pos = before;
+    rowptr[J] = (int32_t)before;
+    if (J == nc - 1) rowptr[nc] = (int32_t)(before + (long)axis_count(j0, nb0) * axis_count(j1, nb1) * axis_count(j2, nb2));
+    for (int q = 0; q < nq; ++q) {
+        const int L = stencil_nbr(J, q, dim, nb0, nb1, nb2);
+        if (L < 0) continue;
+        colidx[pos] = L;
+        for (int t = 0; t < bd * bd; ++t) val[pos * bd * bd + t] = Acs[((long)J * nq + q) * bd * bd + t];
+        ++pos;
+    }
+}
+
+msrsb_status stencil_to_bsr(int dim, const int nb[3], int bd, const double *Acs, int32_t *rowptr, int32_t *colidx,
+                            double *val, cudaStream_t s) {
+    const int nc = nb[0] * nb[1] * nb[2];
+    stencil_bsr_kernel<<<ceil_div(nc, 128), 128, 0, s>>>(nc, dim, nb[0], nb[1], nb[2], bd, Acs, rowptr, colidx, val);
+    MSRSB_LAUNCHED("stencil_bsr_kernel");
+    return MSRSB_OK;
+}
+
 msrsb_status check_mat(const msrsb_mat *A);
 
 }  // namespace msrsb
 
 using namespace msrsb;
 
+// Number of stored blocks of A_c: pairs of coarse nodes at most one coarse
+// step apart on every axis, prod_d (3 nb_d - 2).
+static long coarse_nnzb(const int nb[3], int dim) {
+    long r = 1;
+    for (int d = 0; d < dim; ++d) r *= nb[d] >= 2 ? 3L * nb[d] - 2 : 1;
+    return r;
+}
+
 extern "C" msrsb_status msrsb_coarse_op(const msrsb_mat *A, const msrsb_grid *g, const int32_t *p_ids,
-                                        const void *p_val, int32_t prec, double *Ac_dense, cudaStream_t stream) {
+                                        const void *p_val, int32_t prec, int32_t *ac_rowptr, int32_t *ac_colidx,
+                                        double *ac_val, int32_t *nnzb_h, cudaStream_t stream) {
     MSRSB_TRY(check_mat(A));
-    if (!g || !p_ids || !p_val || !Ac_dense) return fail(MSRSB_EINVAL, "NULL argument");
+    if (!g || !nnzb_h) return fail(MSRSB_EINVAL, "NULL argument");
     int32_t n = 0, nc = 0, W = 0;
     MSRSB_TRY(msrsb_partition_size(g, &n, &nc, &W));
     if (n != A->nrows) return fail(MSRSB_ESHAPE, "grid has %d points but A has %d block rows", n, A->nrows);
-    if ((long)nc * A->bdim > 8192) return fail(MSRSB_ESHAPE, "nc * bdim must be <= 8192");
+    int nb[3];
+    coarse_extent(g, nb);
+    const long nnzb = coarse_nnzb(nb, g->dim);
+    if (nnzb > INT32_MAX) return fail(MSRSB_ESHAPE, "coarse operator has more than 2^31 blocks");
+    *nnzb_h = (int32_t)nnzb;
+    if (!ac_val) return MSRSB_OK;  // size query
+    if (!p_ids || !p_val || !ac_rowptr || !ac_colidx) return fail(MSRSB_EINVAL, "NULL argument");
+    const int bd = A->bdim, nq = g->dim == 3 ? 27 : 9;
     int32_t *pt_ptr = nullptr, *pt_rows = nullptr;
     int8_t *jslot = nullptr;
+    double *Acs = nullptr;
     MSRSB_TRY(build_transpose(A->nrows, W, nc, p_ids, &pt_ptr, &pt_rows, &jslot, nullptr, stream));
+    MSRSB_TRY(dalloc(&Acs, (size_t)nc * nq * bd * bd, stream));
     msrsb_status st;
     if (prec == MSRSB_F64)
-        st = galerkin<double>(A, g, W, nc, p_ids, (const double *)p_val, pt_ptr, pt_rows, jslot, Ac_dense, stream);
+        st = galerkin<double>(A, g, W, nc, p_ids, (const double *)p_val, pt_ptr, pt_rows, jslot, Acs, stream);
     else if (prec == MSRSB_F32)
-        st = galerkin<float>(A, g, W, nc, p_ids, (const float *)p_val, pt_ptr, pt_rows, jslot, Ac_dense, stream);
+        st = galerkin<float>(A, g, W, nc, p_ids, (const float *)p_val, pt_ptr, pt_rows, jslot, Acs, stream);
     else
         st = fail(MSRSB_EINVAL, "prec must be MSRSB_F64 or MSRSB_F32");
+    if (st == MSRSB_OK) st = stencil_to_bsr(g->dim, nb, bd, Acs, ac_rowptr, ac_colidx, ac_val, stream);
     dfree(pt_ptr, stream);
     dfree(pt_rows, stream);
     dfree(jslot, stream);
+    dfree(Acs, stream);
     return st;
 }

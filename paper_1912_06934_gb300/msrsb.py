@@ -189,13 +189,20 @@ def msrsb_build_basis_noalloc(Ahat, p_ids, skel, W, bopts, prec, p_val, stream=N
 
 
 def msrsb_coarse_op(A, g, p_ids, p_val, prec, stream=None):
+    """A_c = P^T A P as block CSR device tensors (rowptr[nc+1], colidx[nnzb],
+    val[nnzb, bdim, bdim])."""
     n, nc, W = msrsb_partition_size(g)
-    nC = nc * A.bdim
-    Ac = torch.empty((nC, nC), dtype=torch.float64, device=A.val.device)
     m = A.c()
+    nnzb = ctypes.c_int32()
+    _check(load().msrsb_coarse_op(ctypes.byref(m), ctypes.byref(g), None, None, ctypes.c_int32(prec), None, None,
+                                  None, ctypes.byref(nnzb), _stream(stream)))
+    dev = A.val.device
+    rowptr = torch.empty(nc + 1, dtype=torch.int32, device=dev)
+    colidx = torch.empty(nnzb.value, dtype=torch.int32, device=dev)
+    val = torch.empty((nnzb.value, A.bdim, A.bdim), dtype=torch.float64, device=dev)
     _check(load().msrsb_coarse_op(ctypes.byref(m), ctypes.byref(g), _ptr(p_ids), _ptr(p_val), ctypes.c_int32(prec),
-                                  _ptr(Ac), _stream(stream)))
-    return Ac
+                                  _ptr(rowptr), _ptr(colidx), _ptr(val), ctypes.byref(nnzb), _stream(stream)))
+    return rowptr, colidx, val
 
 
 class Handle:
