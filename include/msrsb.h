@@ -54,8 +54,15 @@ typedef enum {
 } msrsb_status;
 
 typedef enum { MSRSB_F64 = 0, MSRSB_F32 = 1 } msrsb_prec;
-typedef enum { MSRSB_SMOOTH_NONE = 0, MSRSB_SMOOTH_ILU0 = 1, MSRSB_SMOOTH_GS = 2, MSRSB_SMOOTH_L1JAC = 3 } msrsb_smoother;
+typedef enum {
+    MSRSB_SMOOTH_NONE = 0,
+    MSRSB_SMOOTH_ILU0 = 1,
+    MSRSB_SMOOTH_GS = 2,
+    MSRSB_SMOOTH_L1JAC = 3,
+    MSRSB_SMOOTH_IC0 = 4
+} msrsb_smoother;
 typedef enum { MSRSB_GMRES = 0, MSRSB_PCG = 1, MSRSB_RICHARDSON = 2 } msrsb_krylov;
+typedef enum { MSRSB_RESTRICT_GALERKIN = 0, MSRSB_RESTRICT_FV = 1 } msrsb_restriction;
 
 /* Sparse FP64 fine operator, device arrays (rowptr[nrows+1], colidx[nnz],
  * val[nnz * bdim * bdim]). nrows and nnz count block rows / blocks. */
@@ -88,7 +95,14 @@ typedef struct {
                           (symmetric, for PCG); MSRSB_SMOOTH_L1JAC = l1-Jacobi
                           sweeps z += D_l1^-1 (v - A z), d_i = sum_j |a_ij| over
                           the scalar row (Sec. 4: "2 sweeps of l1-Jacobi"),
-                          scalar or 3x3 block operators */
+                          scalar or 3x3 block operators; MSRSB_SMOOTH_IC0 =
+                          incomplete Cholesky IC(0) (Sec. 4.1, 4.3), the same
+                          M = L U before and after the coarse stage: for 3x3
+                          blocks the incomplete factorisation on A's block
+                          pattern in the node colour order (equal to the
+                          pointwise one in that order, since the pattern is
+                          made of whole blocks); for scalar operators ILU(0),
+                          which is IC(0) for a symmetric A */
     int32_t pre, post; /* enable the pre / post stage of Alg. 4; for
                           MSRSB_SMOOTH_L1JAC the number of sweeps of each */
     int32_t krylov;    /* msrsb_krylov */
@@ -99,6 +113,14 @@ typedef struct {
     int32_t no_coarse; /* 1: leave out the multiscale stage (Alg. 3) of the
                           apply, the smoothing-only baseline of Sec. 3.2 and
                           Sec. 4; 0 (default): the two-stage operator */
+    int32_t restriction; /* msrsb_restriction (Sec. 2, Alg. 2): GALERKIN (default),
+                          R = P^T; FV, the Petrov-Galerkin choice of the
+                          multiscale finite-volume method: R_Ji = 1 for the
+                          fine points i of primal block J (every component),
+                          so A_c = R A P sums the fine equations over each
+                          block and the coarse correction conserves mass
+                          block by block. A_c is then not symmetric: not
+                          with MSRSB_PCG */
 } msrsb_opts;
 
 typedef struct msrsb_handle msrsb_handle;

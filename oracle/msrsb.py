@@ -345,7 +345,11 @@ def ilu0(B):
 class ColouredSmoother:
     """Second-stage smoother (ILU(0), Sec. 3.2; block Gauss-Seidel, Sec. 4.2-4.3).
 
-    kind 'ilu0': M = L U, the ILU(0) factors of A in the elimination order.
+    kind 'ilu0': M = L U, the ILU(0) factors of A in the elimination order;
+    for a symmetric positive definite A these are the IC(0) factors
+    (U = diag(U) L^T), the incomplete Cholesky smoother of Sec. 4.1 and 4.3.
+    With bdim > 1 the order keeps the dofs of a node together (nodes by
+    colour, components inside a node).
     kind 'gs_fwd' / 'gs_bwd': block Gauss-Seidel, M = D + L (forward) or
     M = D + U (backward) of A in the elimination order, with D the
     bdim x bdim diagonal blocks.
@@ -410,7 +414,9 @@ class ColouredSmoother:
     def solve(self, r):
         """z = M^-1 r (r, z in the natural order)."""
         rp = r[self.order]
-        if self.natural:
+        if self.natural or (self.kind == "ilu0" and self.bdim > 1):
+            # sequential substitution (dofs of one node are coupled, so a
+            # colour class is not an independent set when bdim > 1)
             if self.kind == "ilu0":
                 y = spla.spsolve_triangular(self.L, rp, lower=True, unit_diagonal=True)
                 z = spla.spsolve_triangular(self.U, y, lower=False)
@@ -465,15 +471,31 @@ class L1Jacobi:
 # ----------------------------------------------------------------------------
 
 
-class TwoLevel:
-    """Alg. 2 set-up pieces bundled for Alg. 3/4: P, R = P^T, A_c, M_c^-1 and
-    the optional pre/post smoothers (objects with .solve)."""
+def fv_restriction(part, nc, bdim=1):
+    """Petrov-Galerkin restriction of Sec. 2 in its finite-volume form (the
+    MSFV choice): R_Ji = 1 when fine point i lies in primal coarse block J,
+    so the coarse equations are sums of fine equations over each block and
+    the coarse problem keeps discrete mass conservation. For bdim > 1 the
+    same indicator acts on every component (row bdim*J + l, column
+    bdim*i + l). Returns an (nc*bdim) x (n*bdim) CSR matrix."""
+    part = np.asarray(part)
+    n = len(part)
+    rows = (bdim * part[:, None] + np.arange(bdim)[None, :]).ravel()
+    cols = (bdim * np.arange(n)[:, None] + np.arange(bdim)[None, :]).ravel()
+    return sp.csr_matrix((np.ones(n * bdim), (rows, cols)), shape=(nc * bdim, n * bdim))
 
-    def __init__(self, A, P, pre=None, post=None, coarse=True):
+
+class TwoLevel:
+    """Alg. 2 set-up pieces bundled for Alg. 3/4: P, the restriction R (P^T,
+    the Galerkin choice, unless R is given: e.g. fv_restriction, the
+    Petrov-Galerkin choice of Alg. 2), A_c = R A P, M_c^-1 and the optional
+    pre/post smoothers (objects with .solve)."""
+
+    def __init__(self, A, P, pre=None, post=None, coarse=True, R=None):
         self.A = sp.csr_matrix(A)
         self.P = sp.csr_matrix(P)
-        self.R = self.P.T.tocsr()
-        self.Ac = galerkin(self.A, self.P)
+        self.R = self.P.T.tocsr() if R is None else sp.csr_matrix(R)
+        self.Ac = (self.R @ (self.A @ self.P)).tocsr() if R is not None else galerkin(self.A, self.P)
         self.lu = coarse_factor(self.Ac)
         self.pre = pre
         self.post = post
@@ -624,11 +646,12 @@ def pcg(A, b, M, x0=None, rtol=1e-8, maxit=500):
 
 
 def setup_scalar(A, dims, H, centering=0, omega=2.0 / 3.0, tol=1e-3, n_it=10, max_iter=100,
-                 smoother="ilu0", coarse=True, order="colour"):
+                 smoother="ilu0", coarse=True, order="colour", restriction="galerkin"):
     """Alg. 2 for a scalar operator (flow): partition, filter, Alg. 1, Galerkin
     coarse operator, coarse LU and an ILU(0) post-smoother, eliminated in the
     parity-colour order (order="colour", the GPU's) or in the natural order
-    (order="natural", the paper's MATLAB setting)."""
+    (order="natural", the paper's MATLAB setting). restriction "galerkin"
+    (R = P^T) or "fv" (the finite-volume Petrov-Galerkin R of fv_restriction)."""
     A = sp.csr_matrix(A)
     A.sort_indices()
     part = partition(dims, H, centering)
@@ -638,7 +661,8 @@ def setup_scalar(A, dims, H, centering=0, omega=2.0 / 3.0, tol=1e-3, n_it=10, ma
     P = as_matrix(vals, part["pat"])
     col = parity_colours(dims) if order == "colour" else None
     post = ColouredSmoother(A, col, "ilu0") if smoother == "ilu0" else None
-    tl = TwoLevel(A, P, pre=None, post=post, coarse=coarse)
+    R = fv_restriction(part["part"], part["nc"]) if restriction == "fv" else None
+    tl = TwoLevel(A, P, pre=None, post=post, coarse=coarse, R=R)
     return dict(part=part, Ahat=Ahat, vals=vals, iters=its, e_it=e_it, hist=hist, P=P, tl=tl)
 
 
@@ -648,8 +672,10 @@ def setup_elastic(indptr, indices, blocks, dims, H, omega=2.0 / 3.0, tol=1e-3, n
     three scalar bases on one shared pattern, block-diagonal P, Galerkin with
     the full operator, and a symmetric pair of pre/post smoothers: forward /
     backward block Gauss-Seidel ("gs"), or `sweeps` l1-Jacobi sweeps each
-    ("l1jac"). coarse=False gives the smoothing-only baseline. order as in
-    setup_scalar (Gauss-Seidel only)."""
+    ("l1jac"), or IC(0) ("ic0", Sec. 4.1 and 4.3: M = L L^T-type incomplete
+    Cholesky, the same M before and after the coarse stage). coarse=False
+    gives the smoothing-only baseline. order as in setup_scalar (Gauss-Seidel
+    and IC(0))."""
     part = partition(dims, H, 1)
     A = bsr_to_csr(indptr, indices, blocks)
     comps = sdc_blocks(indptr, indices, blocks)
@@ -662,6 +688,8 @@ def setup_elastic(indptr, indices, blocks, dims, H, omega=2.0 / 3.0, tol=1e-3, n
     P = block_prolongation(Ps)
     if smoother == "l1jac":
         pre = post = L1Jacobi(A, sweeps)
+    elif smoother == "ic0":
+        pre = post = ColouredSmoother(A, parity_colours(dims) if order == "colour" else None, "ilu0", bdim=3)
     else:
         col = parity_colours(dims) if order == "colour" else None
         pre = ColouredSmoother(A, col, "gs_fwd", bdim=3)

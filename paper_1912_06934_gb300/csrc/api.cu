@@ -87,7 +87,7 @@ template <typename TP>
 msrsb_status pt_gather(const msrsb_handle *h, const TP *P, TP *PT, cudaStream_t s);
 template <typename T>
 msrsb_status galerkin(const msrsb_mat *A, const msrsb_grid *g, int W, int nc, const int32_t *p_ids, const T *P,
-                      const int32_t *pt_ptr, const int32_t *pt_rows, const int8_t *jslot, double *Ac,
+                      const T *Pl, const int32_t *pt_ptr, const int32_t *pt_rows, const int8_t *jslot, double *Ac,
                       cudaStream_t s);
 msrsb_status coarse_inverse(int n, const double *Ac, double *Ainv, cudaStream_t s);
 msrsb_status coarse_inverse_launch(int n, const double *Ac, double *Ainv, CoarseInverseWork *w, cudaStream_t s);
@@ -100,6 +100,12 @@ msrsb_status plane_factor(int dim, const int nb[3], int bd, const double *Acs, C
 msrsb_status plane_solve(int dim, const int nb[3], int bd, const double *Acs, const CoarsePlanes *cp,
                          const double *vc, double *wc, float *wc32, cudaStream_t s);
 void plane_free(CoarsePlanes *cp, cudaStream_t s);
+msrsb_status plane_inverse(int dim, const int nb[3], int bd, const double *Acs, const CoarsePlanes *cp, double *Ainv,
+                           cudaStream_t s);
+// Coarse systems up to this size are applied through an explicit inverse
+// (formed from the plane factors): one dense product per application
+// instead of 2 n_planes - 1 dependent steps.
+constexpr int kDenseCoarseMax = 1024;
 msrsb_status wait_selftest(double limit_ms, cudaStream_t s);
 msrsb_status colour_classes(int n, const uint8_t *colour, int ncol, int32_t **rows, int32_t *ptr_h, cudaStream_t s);
 template <typename TF>
@@ -109,6 +115,10 @@ template <typename T>
 msrsb_status ilu_build_ell(msrsb_handle *h, const T *lu, cudaStream_t s);
 template <typename T>
 msrsb_status l1_diag(const msrsb_mat *A, T *dinv, cudaStream_t s);
+template <typename T>
+msrsb_status bic0_factor(const msrsb_handle *h, T *lu, T *uinv, cudaStream_t s);
+template <typename T, typename TZ>
+msrsb_status bic0_apply(const msrsb_handle *h, const T *lu, const T *uinv, T *r, TZ *z, int assign, cudaStream_t s);
 template <typename T, typename TZ, typename TR>
 msrsb_status l1_update(long N, const T *dinv, const TR *r, TZ *z, int from_zero, cudaStream_t s);
 
@@ -178,8 +188,18 @@ static msrsb_status setup_smoother(msrsb_handle *h, cudaStream_t s) {
         MSRSB_TRY(convert<float>((long)A.nnz * bd * bd, A.val, alo, s));
         h->a_lo = alo;
     }
-    if (h->opts.smoother == MSRSB_SMOOTH_ILU0) {
-        if (bd != 1) return fail(MSRSB_EINVAL, "ILU(0) smoother needs a scalar operator; use MSRSB_SMOOTH_GS");
+    const bool ilu = h->opts.smoother == MSRSB_SMOOTH_ILU0 || (h->opts.smoother == MSRSB_SMOOTH_IC0 && bd == 1);
+    if (h->opts.smoother == MSRSB_SMOOTH_IC0 && bd == 3) {
+        // block IC(0) in the node colour order, factors in A's block pattern
+        T *lu = nullptr, *uinv = nullptr;
+        MSRSB_TRY(dalloc(&lu, (size_t)A.nnz * 9, s));
+        MSRSB_TRY(dalloc(&uinv, (size_t)n * 9, s));
+        MSRSB_TRY(convert<T>((long)A.nnz * 9, A.val, lu, s));
+        h->bic_lu = lu;
+        h->dinv = uinv;
+        MSRSB_TRY(bic0_factor<T>(h, lu, uinv, s));
+    } else if (ilu) {
+        if (bd != 1) return fail(MSRSB_EINVAL, "ILU(0) smoother needs a scalar operator; use MSRSB_SMOOTH_GS or IC0");
         // factorised in the smoother's precision (FP32 in the mixed form)
         T *lu = nullptr;
         MSRSB_TRY(dalloc(&lu, A.nnz, s));
@@ -341,18 +361,31 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
     coarse_extent(&h->grid, h->nb);
     const int nq = h->grid.dim == 3 ? 27 : 9;
     MSRSB_TRY(dalloc(&h->Acs, (size_t)h->nc * nq * bd * bd, s));
-    MSRSB_TRY(galerkin<T>(&A, &h->grid, W, h->nc, h->p_ids, P, h->pt_ptr, h->pt_rows, h->jslot, h->Acs, s));
+    // restriction R = Pl^T: P (Galerkin) or the block indicator on P's pattern
+    // (finite-volume Petrov-Galerkin; the initial basis of Alg. 1)
+    T *Pl = P;
+    if (h->opts.restriction == MSRSB_RESTRICT_FV) {
+        MSRSB_TRY(dalloc(&Pl, nW * bd, s));
+        for (int l = 0; l < bd; ++l) MSRSB_TRY(indicator<T>(n, W, h->part, h->p_ids, Pl + l * nW, s));
+    }
+    MSRSB_TRY(galerkin<T>(&A, &h->grid, W, h->nc, h->p_ids, P, Pl, h->pt_ptr, h->pt_rows, h->jslot, h->Acs, s));
     {  // P's values in column order for the restriction
         T *pt = nullptr;
         MSRSB_TRY(dalloc(&pt, (size_t)h->nnz_p * bd, s));
         h->pt_val = pt;
-        MSRSB_TRY(pt_gather<T>(h, P, pt, s));
+        MSRSB_TRY(pt_gather<T>(h, Pl, pt, s));
+        if (Pl != P) dfree(Pl, s);
     }
     MSRSB_TRY(mark(3));
     MSRSB_CUDA(cudaEventRecord(go_ev, s));
     release(go_ev);
     if (planes_fit(h->grid.dim, h->nb, bd)) {
         MSRSB_TRY(plane_factor(h->grid.dim, h->nb, bd, h->Acs, &h->planes, s));
+        if (h->nC <= kDenseCoarseMax) {
+            MSRSB_TRY(dalloc(&h->Ainv, (size_t)h->nC * h->nC, s));
+            MSRSB_TRY(plane_inverse(h->grid.dim, h->nb, bd, h->Acs, &h->planes, h->Ainv, s));
+            plane_free(&h->planes, s);
+        }
     } else {
         if (h->nC > 8192)
             return fail(MSRSB_ESHAPE, "coarse planes of %d unknowns exceed one cluster and n_C = %d exceeds the "
@@ -437,9 +470,11 @@ static msrsb_status apply_t(msrsb_handle *h, const TVI *v, TZ *z, cudaStream_t s
     const T *P = (const T *)h->p_val;
     T *r = (T *)h->r_t, *y = (T *)h->y_t;
     const T *aval_t = h->opts.prec == MSRSB_F32 ? (const T *)h->a_lo : (const T *)A.val;
-    const bool gs = h->opts.smoother == MSRSB_SMOOTH_GS, ilu = h->opts.smoother == MSRSB_SMOOTH_ILU0;
+    const bool gs = h->opts.smoother == MSRSB_SMOOTH_GS;
+    const bool ic = h->opts.smoother == MSRSB_SMOOTH_IC0 && h->bdim == 3;
+    const bool ilu = h->opts.smoother == MSRSB_SMOOTH_ILU0 || (h->opts.smoother == MSRSB_SMOOTH_IC0 && h->bdim == 1);
     const bool l1 = h->opts.smoother == MSRSB_SMOOTH_L1JAC;
-    const bool pre = h->opts.pre && (gs || ilu || l1), post = h->opts.post && (gs || ilu || l1);
+    const bool pre = h->opts.pre && (gs || ilu || l1 || ic), post = h->opts.post && (gs || ilu || l1 || ic);
     const bool coarse = !h->opts.no_coarse;
     const T *dinv = (const T *)h->dinv;
     // scalar mixed form: the coarse stage also leaves z in FP32, which the
@@ -450,6 +485,9 @@ static msrsb_status apply_t(msrsb_handle *h, const TVI *v, TZ *z, cudaStream_t s
         if (gs) {
             MSRSB_TRY((copy_cast<TVI, T>(N, v, r, s)));
             MSRSB_TRY((gs_apply<T, T, TZ>(h, aval_t, dinv, 1, r, y, z, 1, s)));
+        } else if (ic) {
+            MSRSB_TRY((copy_cast<TVI, T>(N, v, r, s)));
+            MSRSB_TRY((bic0_apply<T, TZ>(h, (const T *)h->bic_lu, dinv, r, z, 1, s)));
         } else if (l1) {
             MSRSB_TRY((l1_update<T, TZ, TVI>(N, dinv, v, z, 1, s)));  // first sweep from z = 0
             for (int k = 1; k < h->opts.pre; ++k) {
@@ -482,6 +520,9 @@ static msrsb_status apply_t(msrsb_handle *h, const TVI *v, TZ *z, cudaStream_t s
         if (gs) {
             MSRSB_TRY((resid_t<T, TZ, TVI>(h, aval_t, z, v, r, nullptr, s)));
             MSRSB_TRY((gs_apply<T, T, TZ>(h, aval_t, dinv, 0, r, y, z, 0, s)));
+        } else if (ic) {
+            MSRSB_TRY((resid_t<T, TZ, TVI>(h, aval_t, z, v, r, nullptr, s)));
+            MSRSB_TRY((bic0_apply<T, TZ>(h, (const T *)h->bic_lu, dinv, r, z, 0, s)));
         } else if (l1) {
             for (int k = 0; k < h->opts.post; ++k) {
                 if (k == 0 && z32)
@@ -930,6 +971,7 @@ static void handle_free(msrsb_handle *h) {
     dfree(h->pos_of, s);
     dfree(h->diag_pos, s);
     dfree(h->dinv, s);
+    dfree(h->bic_lu, s);
     dfree(h->a_lo, s);
     sell_free(&h->asell, s);
     dfree(h->vc, s);
@@ -998,11 +1040,15 @@ extern "C" msrsb_status msrsb_setup(const msrsb_mat *A, const msrsb_grid *g, con
     if (g->ncomp != A->bdim) return fail(MSRSB_ESHAPE, "grid ncomp %d != bdim %d", g->ncomp, A->bdim);
     if (opts->prec != MSRSB_F64 && opts->prec != MSRSB_F32) return fail(MSRSB_EINVAL, "bad precision");
     if (opts->basis.n_it < 1 || opts->basis.max_iter < 0) return fail(MSRSB_EINVAL, "bad basis options");
-    if (opts->smoother < MSRSB_SMOOTH_NONE || opts->smoother > MSRSB_SMOOTH_L1JAC)
+    if (opts->smoother < MSRSB_SMOOTH_NONE || opts->smoother > MSRSB_SMOOTH_IC0)
         return fail(MSRSB_EINVAL, "unknown smoother %d", opts->smoother);
     if (opts->pre < 0 || opts->post < 0 || opts->pre > 64 || opts->post > 64)
         return fail(MSRSB_EINVAL, "pre/post must be 0..64 (got %d, %d)", opts->pre, opts->post);
     if (opts->no_coarse != 0 && opts->no_coarse != 1) return fail(MSRSB_EINVAL, "no_coarse must be 0 or 1");
+    if (opts->restriction != MSRSB_RESTRICT_GALERKIN && opts->restriction != MSRSB_RESTRICT_FV)
+        return fail(MSRSB_EINVAL, "unknown restriction %d", opts->restriction);
+    if (opts->restriction == MSRSB_RESTRICT_FV && opts->krylov == MSRSB_PCG)
+        return fail(MSRSB_EINVAL, "the finite-volume restriction gives a non-symmetric preconditioner; use GMRES");
     keep_pool_memory();
     msrsb_handle *h = new msrsb_handle();
     h->A = *A;

@@ -344,6 +344,75 @@ __global__ void __launch_bounds__(kPlaneThreads) plane_solve_kernel(PlaneGeom G,
     }
 }
 
+// The explicit inverse A_c^-1 (row-major n_C x n_C) from the plane factors,
+// for coarse systems small enough that one dense product per application
+// beats the dependent plane steps: CTA b builds the columns
+// kInvCols*b .. kInvCols*b + kInvCols-1, the same recurrences as
+// plane_solve_kernel applied to identity columns, independent across CTAs.
+constexpr int kInvCols = 4;
+
+__global__ void __launch_bounds__(kPlaneThreads) plane_inverse_kernel(PlaneGeom G, const double *__restrict__ Acs,
+                                                                      const double *__restrict__ X,
+                                                                      const double *__restrict__ Gm,
+                                                                      const int *__restrict__ pi,
+                                                                      double *__restrict__ Ainv) {
+    const int m = G.m, bd = G.bd, NI = G.NI, nC = G.np * m;
+    const int c0 = blockIdx.x * kInvCols, ncols = min(kInvCols, nC - c0);
+    const int tid = threadIdx.x;
+    extern __shared__ double sm[];
+    double *Wc = sm;                           // the columns being built, [nC][kInvCols]
+    double *t = Wc + (long)nC * kInvCols;      // [m][kInvCols]
+    double *tp = t + (long)m * kInvCols;       // [m][kInvCols]
+    for (int k = 0; k < G.np; ++k) {
+        const int Jbase = k * G.PN;
+        for (int idx = tid; idx < m * kInvCols; idx += kPlaneThreads) {
+            const int j = idx / kInvCols, q = idx - j * kInvCols;
+            const int uj = j / bd, l = j - uj * bd;
+            double v = (c0 + q == k * m + j) ? 1.0 : 0.0;
+            if (k > 0)
+                for (int b = 0; b < NI; ++b) {
+                    const int tn = plane_nbr(G, uj, b);
+                    if (tn < 0) continue;
+                    for (int c = 0; c < bd; ++c)
+                        v = fma(-st_val(Acs, G, Jbase + uj, b, l, c),
+                                Wc[((long)(k - 1) * m + tn * bd + c) * kInvCols + q], v);
+                }
+            t[idx] = v;
+        }
+        __syncthreads();
+        const int *pk = pi + (long)k * m;
+        for (int idx = tid; idx < m * kInvCols; idx += kPlaneThreads) {
+            const int j = idx / kInvCols, q = idx - j * kInvCols;
+            tp[idx] = t[pk[j] * kInvCols + q];
+        }
+        __syncthreads();
+        const double *Xk = X + (long)k * m * m;
+        for (int idx = tid; idx < m * kInvCols; idx += kPlaneThreads) {
+            const int i = idx / kInvCols, q = idx - i * kInvCols;
+            const double *xr = Xk + (long)i * m;
+            double s = 0.0;
+            for (int j = 0; j < m; ++j) s = fma(__ldg(xr + j), tp[j * kInvCols + q], s);
+            Wc[((long)k * m + i) * kInvCols + q] = s;
+        }
+        __syncthreads();
+    }
+    for (int k = G.np - 2; k >= 0; --k) {
+        const double *Gk = Gm + (long)k * m * m;
+        for (int idx = tid; idx < m * kInvCols; idx += kPlaneThreads) {
+            const int i = idx / kInvCols, q = idx - i * kInvCols;
+            const double *gr = Gk + (long)i * m;
+            double s = 0.0;
+            for (int j = 0; j < m; ++j) s = fma(__ldg(gr + j), Wc[((long)(k + 1) * m + j) * kInvCols + q], s);
+            Wc[((long)k * m + i) * kInvCols + q] -= s;
+        }
+        __syncthreads();
+    }
+    for (int idx = tid; idx < nC * ncols; idx += kPlaneThreads) {
+        const int row = idx / ncols, q = idx - row * ncols;
+        Ainv[(long)row * nC + c0 + q] = Wc[(long)row * kInvCols + q];
+    }
+}
+
 // ---- host side ----------------------------------------------------------------------
 
 static size_t factor_smem(int m, int nct) {
@@ -471,6 +540,24 @@ msrsb_status plane_solve(int dim, const int nb[3], int bd, const double *Acs, co
                                (const int *)cp->pi, vc, wc, wc32);
     }
     MSRSB_CUDA(e);
+    return MSRSB_OK;
+}
+
+// Ainv (n_C x n_C row-major) = A_c^-1 from the plane factors.
+msrsb_status plane_inverse(int dim, const int nb[3], int bd, const double *Acs, const CoarsePlanes *cp, double *Ainv,
+                           cudaStream_t s) {
+    PlaneGeom G;
+    plane_geom(dim, nb, bd, &G);
+    const long nC = (long)G.np * G.m;
+    const size_t smem = ((size_t)nC + 2 * G.m) * kInvCols * sizeof(double);
+    if (smem > kPlaneSmemMax) return fail(MSRSB_ESHAPE, "explicit coarse inverse too large (n_C = %ld)", nC);
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaFuncSetAttribute(plane_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPlaneSmemMax);
+        cudaGetLastError();
+    });
+    plane_inverse_kernel<<<ceil_div(nC, kInvCols), kPlaneThreads, smem, s>>>(G, Acs, cp->X, cp->G, cp->pi, Ainv);
+    MSRSB_LAUNCHED("plane_inverse_kernel");
     return MSRSB_OK;
 }
 

@@ -220,7 +220,8 @@ struct msrsb_handle {
     msrsb::IluEll ilu;          // ILU(0) factors (colour order), handle precision
     int32_t *pos_of = nullptr;  // colour-order position of every fine row
     int32_t *diag_pos = nullptr;
-    void *dinv = nullptr;     // block GS: inverse 3x3 diagonal blocks [n][9]
+    void *dinv = nullptr;     // block GS: inverse 3x3 diagonal blocks [n][9]; IC(0): U_ii^-1 [n][9]
+    void *bic_lu = nullptr;   // block IC(0) factors in A's block pattern [nnz][9]
     void *a_lo = nullptr;     // FP32 copy of A's values (mixed precision inner residual, bdim 3)
     msrsb::Sell asell;          // sliced-ELL copy of a scalar A: FP64 values [0], FP32 values [1] (mixed)
     // workspaces

@@ -260,10 +260,12 @@ void coarse_extent(const msrsb_grid *g, int nb[3]) {
         nb[d] = d >= dim ? 1 : (g->centering == 0 ? (nn[d] + hh[d] - 1) / hh[d] : (nn[d] - 1 + hh[d] - 1) / hh[d] + 1);
 }
 
-// A_c = P^T A P as the coarse stencil Acs[nc][3^dim][bd][bd] (see ptap_kernel).
+// A_c = R A P as the coarse stencil Acs[nc][3^dim][bd][bd] (see ptap_kernel),
+// with R = Pl^T: Pl = P (Galerkin), or the block indicator on P's pattern
+// (the finite-volume Petrov-Galerkin restriction).
 template <typename T>
 msrsb_status galerkin(const msrsb_mat *A, const msrsb_grid *g, int W, int nc, const int32_t *p_ids, const T *P,
-                      const int32_t *pt_ptr, const int32_t *pt_rows, const int8_t *jslot, double *Ac,
+                      const T *Pl, const int32_t *pt_ptr, const int32_t *pt_rows, const int8_t *jslot, double *Ac,
                       cudaStream_t s) {
     const int BD = A->bdim, n = A->nrows, dim = g->dim;
     const int ncode = dim == 3 ? 27 : 9;
@@ -280,18 +282,18 @@ msrsb_status galerkin(const msrsb_mat *A, const msrsb_grid *g, int W, int nc, co
         ap1_kernel<T, 27><<<ceil_div(n, kAp1Threads), kAp1Threads, 0, s>>>(n, W, A->rowptr, A->colidx, A->val, p_ids,
                                                                            P, code, AP);
         MSRSB_LAUNCHED("ap1_kernel");
-        ptap1_kernel<T, 27><<<nc, 128, 0, s>>>(n, W, nc, dim, nb[0], nb[1], nb[2], P, pt_ptr, pt_rows, jslot, AP, Ac);
+        ptap1_kernel<T, 27><<<nc, 128, 0, s>>>(n, W, nc, dim, nb[0], nb[1], nb[2], Pl, pt_ptr, pt_rows, jslot, AP, Ac);
         MSRSB_LAUNCHED("ptap1_kernel");
     } else if (BD == 1) {
         ap1_kernel<T, 9><<<ceil_div(n, kAp1Threads), kAp1Threads, 0, s>>>(n, W, A->rowptr, A->colidx, A->val, p_ids,
                                                                           P, code, AP);
         MSRSB_LAUNCHED("ap1_kernel");
-        ptap1_kernel<T, 9><<<nc, 128, 0, s>>>(n, W, nc, dim, nb[0], nb[1], nb[2], P, pt_ptr, pt_rows, jslot, AP, Ac);
+        ptap1_kernel<T, 9><<<nc, 128, 0, s>>>(n, W, nc, dim, nb[0], nb[1], nb[2], Pl, pt_ptr, pt_rows, jslot, AP, Ac);
         MSRSB_LAUNCHED("ptap1_kernel");
     } else {
         ap_kernel<T, 3><<<ceil_div(n, 128), 128, 0, s>>>(n, W, ncode, A->rowptr, A->colidx, A->val, p_ids, P, code, AP);
         MSRSB_LAUNCHED("ap_kernel");
-        ptap_kernel<T, 3><<<nc, 128, 0, s>>>(n, W, nc, ncode, dim, nb[0], nb[1], nb[2], P, pt_ptr, pt_rows, jslot, AP,
+        ptap_kernel<T, 3><<<nc, 128, 0, s>>>(n, W, nc, ncode, dim, nb[0], nb[1], nb[2], Pl, pt_ptr, pt_rows, jslot, AP,
                                             Ac);
         MSRSB_LAUNCHED("ptap_kernel");
     }
@@ -300,9 +302,11 @@ msrsb_status galerkin(const msrsb_mat *A, const msrsb_grid *g, int W, int nc, co
     return MSRSB_OK;
 }
 template msrsb_status galerkin<double>(const msrsb_mat *, const msrsb_grid *, int, int, const int32_t *, const double *,
-                                       const int32_t *, const int32_t *, const int8_t *, double *, cudaStream_t);
+                                       const double *, const int32_t *, const int32_t *, const int8_t *, double *,
+                                       cudaStream_t);
 template msrsb_status galerkin<float>(const msrsb_mat *, const msrsb_grid *, int, int, const int32_t *, const float *,
-                                      const int32_t *, const int32_t *, const int8_t *, double *, cudaStream_t);
+                                      const float *, const int32_t *, const int32_t *, const int8_t *, double *,
+                                      cudaStream_t);
 
 // ---- the coarse stencil as a dense matrix or block CSR ------------------------------
 
@@ -418,9 +422,11 @@ extern "C" msrsb_status msrsb_coarse_op(const msrsb_mat *A, const msrsb_grid *g,
     MSRSB_TRY(dalloc(&Acs, (size_t)nc * nq * bd * bd, stream));
     msrsb_status st;
     if (prec == MSRSB_F64)
-        st = galerkin<double>(A, g, W, nc, p_ids, (const double *)p_val, pt_ptr, pt_rows, jslot, Acs, stream);
+        st = galerkin<double>(A, g, W, nc, p_ids, (const double *)p_val, (const double *)p_val, pt_ptr, pt_rows,
+                              jslot, Acs, stream);
     else if (prec == MSRSB_F32)
-        st = galerkin<float>(A, g, W, nc, p_ids, (const float *)p_val, pt_ptr, pt_rows, jslot, Acs, stream);
+        st = galerkin<float>(A, g, W, nc, p_ids, (const float *)p_val, (const float *)p_val, pt_ptr, pt_rows, jslot,
+                             Acs, stream);
     else
         st = fail(MSRSB_EINVAL, "prec must be MSRSB_F64 or MSRSB_F32");
     if (st == MSRSB_OK) st = stencil_to_bsr(g->dim, nb, bd, Acs, ac_rowptr, ac_colidx, ac_val, stream);

@@ -634,6 +634,211 @@ template msrsb_status gs_apply<float, float, double>(const msrsb_handle *, const
 template msrsb_status gs_apply<float, float, float>(const msrsb_handle *, const float *, const float *, int,
                                                     const float *, float *, float *, int, cudaStream_t);
 
+// ---- block incomplete factorisation: IC(0) of Sec. 4.1 and 4.3 -------------------------
+//
+// 3x3-block ILU(0) of A in the node colour order (nodes by parity colour,
+// the three components of a node together), on A's block pattern. A's
+// pattern is made of whole 3x3 blocks, so eliminating a node's three dofs one
+// by one with no fill outside the pattern fills exactly what eliminating the
+// block at once fills: this is the pointwise ILU(0) in that order, and for a
+// symmetric positive definite A it is IC(0) (U = D L^T). The factors replace
+// A's values (L below, U on and above the diagonal in the colour order); the
+// inverse diagonal blocks U_ii^-1 are kept for the backward sweep.
+
+// m = a^-1 for a 3x3 block (adjugate / determinant); false if singular
+template <typename T>
+__device__ __forceinline__ bool inv3(const T a[9], T m[9]) {
+    const T c00 = a[4] * a[8] - a[5] * a[7], c01 = a[5] * a[6] - a[3] * a[8], c02 = a[3] * a[7] - a[4] * a[6];
+    const T det = a[0] * c00 + a[1] * c01 + a[2] * c02;
+    if (det == T(0) || !isfinite(det)) return false;
+    const T id = T(1) / det;
+    m[0] = c00 * id;
+    m[1] = (a[2] * a[7] - a[1] * a[8]) * id;
+    m[2] = (a[1] * a[5] - a[2] * a[4]) * id;
+    m[3] = c01 * id;
+    m[4] = (a[0] * a[8] - a[2] * a[6]) * id;
+    m[5] = (a[2] * a[3] - a[0] * a[5]) * id;
+    m[6] = c02 * id;
+    m[7] = (a[1] * a[6] - a[0] * a[7]) * id;
+    m[8] = (a[0] * a[4] - a[1] * a[3]) * id;
+    return true;
+}
+
+// One colour of the factorisation, one warp per node i of colour c, lane q
+// owning block entry q of row i. Lower neighbours k (colours < c, whose rows
+// are final) are eliminated in colour order: L_ik = A_ik U_kk^-1, then every
+// later entry j of row i with a block (k, j) in row k gets A_ij -= L_ik U_kj.
+template <typename T>
+__global__ void __launch_bounds__(256) bic0_factor_kernel(int cnt, const int32_t *__restrict__ rows, int c,
+                                                          const int32_t *__restrict__ rowptr,
+                                                          const int32_t *__restrict__ colidx,
+                                                          const uint8_t *__restrict__ colour, T *__restrict__ lu,
+                                                          T *__restrict__ uinv, int *__restrict__ status) {
+    const int w = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (w >= cnt) return;  // warp-uniform
+    const int i = rows[w];
+    const int e0 = rowptr[i], len = rowptr[i + 1] - e0;
+    const bool own = lane < len;
+    const int j = own ? colidx[e0 + lane] : -1;
+    const int cj = own ? colour[j] : 255;
+    T a[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) a[q] = own ? lu[(long)(e0 + lane) * 9 + q] : T(0);
+    for (int cc = 0; cc < c; ++cc) {
+        unsigned mask = __ballot_sync(0xffffffffu, own && cj == cc);
+        while (mask) {
+            const int src = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const int k = __shfl_sync(0xffffffffu, j, src);
+            T l[9];
+            if (lane == src) {
+                T ui[9];
+#pragma unroll
+                for (int q = 0; q < 9; ++q) ui[q] = uinv[(long)k * 9 + q];
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+#pragma unroll
+                    for (int t = 0; t < 3; ++t)
+                        l[r * 3 + t] = a[r * 3] * ui[t] + a[r * 3 + 1] * ui[3 + t] + a[r * 3 + 2] * ui[6 + t];
+#pragma unroll
+                for (int q = 0; q < 9; ++q) a[q] = l[q];
+            }
+#pragma unroll
+            for (int q = 0; q < 9; ++q) l[q] = __shfl_sync(0xffffffffu, l[q], src);
+            if (own && cj > cc) {
+                // U_kj: block (k, j) of row k, if the pattern has it
+                int lo = rowptr[k], hi = rowptr[k + 1];
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (colidx[mid] < j)
+                        lo = mid + 1;
+                    else
+                        hi = mid;
+                }
+                if (lo < rowptr[k + 1] && colidx[lo] == j) {
+                    const T *u = lu + (long)lo * 9;
+                    T uk[9];
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) uk[q] = u[q];
+#pragma unroll
+                    for (int r = 0; r < 3; ++r)
+#pragma unroll
+                        for (int t = 0; t < 3; ++t)
+                            a[r * 3 + t] -= l[r * 3] * uk[t] + l[r * 3 + 1] * uk[3 + t] + l[r * 3 + 2] * uk[6 + t];
+                }
+            }
+        }
+    }
+    if (own) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) lu[(long)(e0 + lane) * 9 + q] = a[q];
+        if (j == i) {
+            T m[9];
+            if (!inv3(a, m)) atomicCAS(status, 0, 1 + i);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) uinv[(long)i * 9 + q] = m[q];
+        }
+    }
+}
+
+template <typename T>
+msrsb_status bic0_factor(const msrsb_handle *h, T *lu, T *uinv, cudaStream_t s) {
+    const msrsb_mat &A = h->A;
+    int *status = nullptr;
+    MSRSB_TRY(dalloc(&status, 1, s));
+    MSRSB_CUDA(cudaMemsetAsync(status, 0, sizeof(int), s));
+    for (int c = 0; c < h->ncolours; ++c) {
+        const int cnt = h->colour_ptr_h[c + 1] - h->colour_ptr_h[c];
+        if (!cnt) continue;
+        bic0_factor_kernel<T><<<ceil_div((long)cnt * 32, 256), 256, 0, s>>>(
+            cnt, h->colour_rows + h->colour_ptr_h[c], c, A.rowptr, A.colidx, h->colour, lu, uinv, status);
+        MSRSB_LAUNCHED("bic0_factor_kernel");
+    }
+    int hs = 0;
+    MSRSB_CUDA(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MSRSB_CUDA(cudaStreamSynchronize(s));
+    dfree(status, s);
+    if (hs) return fail(MSRSB_EBREAKDOWN, "IC(0): singular pivot block at node %d", hs - 1);
+    return MSRSB_OK;
+}
+template msrsb_status bic0_factor<double>(const msrsb_handle *, double *, double *, cudaStream_t);
+template msrsb_status bic0_factor<float>(const msrsb_handle *, float *, float *, cudaStream_t);
+
+// One colour of the IC(0) application, in place on r (one thread per node):
+// forward, y_i = r_i - sum_{colour(k) < c} L_ik y_k; backward,
+// e_i = U_ii^-1 (y_i - sum_{colour(j) > c} U_ij e_j), then z_i = e_i (assign)
+// or z_i += e_i.
+template <typename T, typename TZ>
+__global__ void __launch_bounds__(128) bic0_colour_kernel(int cnt, const int32_t *__restrict__ rows, int c,
+                                                          int forward, const int32_t *__restrict__ rowptr,
+                                                          const int32_t *__restrict__ colidx,
+                                                          const uint8_t *__restrict__ colour,
+                                                          const T *__restrict__ lu, const T *__restrict__ uinv,
+                                                          T *__restrict__ r, TZ *__restrict__ z, int assign) {
+    pdl_prologue();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= cnt) return;
+    const int i = rows[t];
+    T a0 = r[3 * i], a1 = r[3 * i + 1], a2 = r[3 * i + 2];
+    for (int q = rowptr[i]; q < rowptr[i + 1]; ++q) {
+        const int k = colidx[q];
+        const int ck = colour[k];
+        if (forward ? ck >= c : ck <= c) continue;
+        const T *b = lu + (long)q * 9;
+        const T e0 = r[3 * k], e1 = r[3 * k + 1], e2 = r[3 * k + 2];
+        a0 -= b[0] * e0 + b[1] * e1 + b[2] * e2;
+        a1 -= b[3] * e0 + b[4] * e1 + b[5] * e2;
+        a2 -= b[6] * e0 + b[7] * e1 + b[8] * e2;
+    }
+    if (forward) {
+        r[3 * i] = a0;
+        r[3 * i + 1] = a1;
+        r[3 * i + 2] = a2;
+        return;
+    }
+    const T *d = uinv + (long)i * 9;
+    const T x0 = d[0] * a0 + d[1] * a1 + d[2] * a2;
+    const T x1 = d[3] * a0 + d[4] * a1 + d[5] * a2;
+    const T x2 = d[6] * a0 + d[7] * a1 + d[8] * a2;
+    r[3 * i] = x0;
+    r[3 * i + 1] = x1;
+    r[3 * i + 2] = x2;
+    if (assign) {
+        z[3 * i] = TZ(x0);
+        z[3 * i + 1] = TZ(x1);
+        z[3 * i + 2] = TZ(x2);
+    } else {
+        z[3 * i] = TZ(z[3 * i] + TZ(x0));
+        z[3 * i + 1] = TZ(z[3 * i + 1] + TZ(x1));
+        z[3 * i + 2] = TZ(z[3 * i + 2] + TZ(x2));
+    }
+}
+
+// z (+)= M^-1 r with M = L U the block IC(0) factors; r is overwritten.
+template <typename T, typename TZ>
+msrsb_status bic0_apply(const msrsb_handle *h, const T *lu, const T *uinv, T *r, TZ *z, int assign, cudaStream_t s) {
+    const msrsb_mat &A = h->A;
+    for (int c = 1; c < h->ncolours; ++c) {  // colour 0 has no lower neighbours: y = r there
+        const int cnt = h->colour_ptr_h[c + 1] - h->colour_ptr_h[c];
+        if (!cnt) continue;
+        MSRSB_PDL((bic0_colour_kernel<T, TZ>), ceil_div(cnt, 128), 128, 0, s, cnt,
+                  h->colour_rows + h->colour_ptr_h[c], c, 1, A.rowptr, A.colidx, h->colour, lu, uinv, r, z, assign);
+    }
+    for (int c = h->ncolours - 1; c >= 0; --c) {
+        const int cnt = h->colour_ptr_h[c + 1] - h->colour_ptr_h[c];
+        if (!cnt) continue;
+        MSRSB_PDL((bic0_colour_kernel<T, TZ>), ceil_div(cnt, 128), 128, 0, s, cnt,
+                  h->colour_rows + h->colour_ptr_h[c], c, 0, A.rowptr, A.colidx, h->colour, lu, uinv, r, z, assign);
+    }
+    return MSRSB_OK;
+}
+template msrsb_status bic0_apply<double, double>(const msrsb_handle *, const double *, const double *, double *,
+                                                 double *, int, cudaStream_t);
+template msrsb_status bic0_apply<float, double>(const msrsb_handle *, const float *, const float *, float *, double *,
+                                                int, cudaStream_t);
+template msrsb_status bic0_apply<float, float>(const msrsb_handle *, const float *, const float *, float *, float *,
+                                               int, cudaStream_t);
+
 // ---- l1-Jacobi (Sec. 4: "2 sweeps of l1-Jacobi") ----------------------------------
 
 // dinv[i*bd + l] = 1 / sum_j |a_(i*bd+l),j| over the scalar row (all blocks of

@@ -111,3 +111,94 @@ def test_bad_smoother_options_are_rejected(M):
         with pytest.raises(M.MsrsbError) as ei:
             M.msrsb_setup(A, g, M.opts(**kw))
         assert ei.value.status == M.msrsb.MSRSB_EINVAL
+
+
+@pytest.mark.parametrize("case", ["2d", "3d"])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_fv_restriction_matches_oracle(M, case, prec):
+    """The Petrov-Galerkin (finite-volume) restriction of Alg. 2: A_c = R A P
+    with R the primal-block indicator, against the oracle: A_c within 1e-12 of
+    its largest entry and one apply within 1e-10 (FP64 form; 2e-5 mixed, the
+    bound of the mixed-form tests), GMRES to 1e-8 within +-1 iteration."""
+    B = M.msrsb
+    c = darcy_2d_case(n=64, H=8) if case == "2d" else darcy_3d_case(n=24)
+    A = M.Mat.from_host(c["indptr"], c["indices"], c["data"])
+    g = M.grid(c["dims"], c["H"])
+    basis = dict(tol=1e-3, n_it=10, max_iter=100)
+    h = M.msrsb_setup(A, g, M.opts(restriction=B.MSRSB_RESTRICT_FV, prec=prec, **basis))
+    Ah = sp.csr_matrix((c["data"], c["indices"], c["indptr"]))
+    ref = O.setup_scalar(Ah, c["dims"], c["H"], restriction="fv", **basis)
+    _, _, Ac = h.get_setup()
+    Acr = ref["tl"].Ac.toarray()
+    assert np.abs(Ac.cpu().numpy() - Acr).max() <= (1e-12 if prec == 0 else 2e-5) * np.abs(Acr).max()
+    v = np.random.default_rng(9).standard_normal(Ah.shape[0])
+    z = h.apply(torch.as_tensor(v, device="cuda")).cpu().numpy()
+    zr = ref["tl"].apply(v)
+    assert np.linalg.norm(z - zr) <= (1e-10 if prec == 0 else 2e-5) * np.linalg.norm(zr)
+    _, its_ref, _, _ = O.gmres_right(Ah, c["b"], ref["tl"].apply, rtol=1e-8, maxit=300)
+    r = h.solve(torch.as_tensor(c["b"], device="cuda"), rtol=1e-8, maxit=300)
+    x = r["x"].cpu().numpy()
+    assert np.linalg.norm(c["b"] - Ah @ x) <= 1e-8 * np.linalg.norm(c["b"])
+    assert abs(r["iters"] - its_ref) <= 1
+    h.destroy()
+
+
+def test_fv_restriction_with_pcg_is_rejected(M):
+    B = M.msrsb
+    c = elastic_3d_case(ne=4, H=2)
+    A = M.Mat.from_host(c["indptr"], c["indices"], c["data"], bdim=3)
+    g = M.grid(c["dims"], c["H"], centering=1, ncomp=3)
+    with pytest.raises(M.MsrsbError) as ei:
+        M.msrsb_setup(A, g, M.opts(smoother=B.MSRSB_SMOOTH_GS, pre=1, post=1, krylov=B.MSRSB_PCG,
+                                   restriction=B.MSRSB_RESTRICT_FV))
+    assert ei.value.status == B.MSRSB_EINVAL
+
+
+@pytest.mark.parametrize("ne,H", [(8, 4), (12, 6)])
+def test_ic0_apply_matches_oracle_elastic(M, ne, H):
+    """IC(0) pre/post (Sec. 4.1, 4.3): the GPU's 3x3-block incomplete
+    factorisation in the node colour order against the oracle's pointwise
+    ILU(0) of the SPD operator in the same order (IC(0)); one application of
+    the two-stage operator within 1e-10 relative."""
+    B = M.msrsb
+    c = elastic_3d_case(ne=ne, H=H)
+    h = _elastic(M, c, smoother=B.MSRSB_SMOOTH_IC0, pre=1, post=1, krylov=B.MSRSB_PCG, tol=0.0, max_iter=20)
+    ref = O.setup_elastic(c["indptr"], c["indices"], c["data"], c["dims"], c["H"], tol=0.0, max_iter=20,
+                          smoother="ic0")
+    v = np.random.default_rng(12).standard_normal(ref["A"].shape[0])
+    z = h.apply(torch.as_tensor(v, device="cuda")).cpu().numpy()
+    zr = ref["tl"].apply(v)
+    assert np.linalg.norm(z - zr) <= 1e-10 * np.linalg.norm(zr)
+    h.destroy()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_pcg_ic0_elastic(M, prec):
+    """PCG with IC(0) pre/post to 1e-8, within +-1 of the oracle's count."""
+    B = M.msrsb
+    c = elastic_3d_case(ne=16, H=4)
+    basis = dict(tol=1e-3, n_it=10, max_iter=100)
+    h = _elastic(M, c, smoother=B.MSRSB_SMOOTH_IC0, pre=1, post=1, krylov=B.MSRSB_PCG, prec=prec, **basis)
+    ref = O.setup_elastic(c["indptr"], c["indices"], c["data"], c["dims"], c["H"], smoother="ic0", **basis)
+    _, its_ref, _, _ = O.pcg(ref["A"], c["b"], ref["tl"].apply, rtol=1e-8, maxit=500)
+    r = h.solve(torch.as_tensor(c["b"], device="cuda"), rtol=1e-8, maxit=500)
+    x = r["x"].cpu().numpy()
+    assert np.linalg.norm(c["b"] - ref["A"] @ x) <= 1e-8 * np.linalg.norm(c["b"])
+    assert abs(r["iters"] - its_ref) <= 1, (r["iters"], its_ref)
+    h.destroy()
+
+
+def test_ic0_on_a_scalar_operator_is_ilu0(M):
+    """For a scalar operator IC0 is ILU(0) (identical for a symmetric A):
+    the same code path, so the applications agree bit for bit."""
+    B = M.msrsb
+    c = darcy_3d_case(n=16)
+    A = M.Mat.from_host(c["indptr"], c["indices"], c["data"])
+    g = M.grid(c["dims"], c["H"])
+    v = torch.as_tensor(np.random.default_rng(13).standard_normal(A.nrows), device="cuda")
+    z = []
+    for sm in (B.MSRSB_SMOOTH_ILU0, B.MSRSB_SMOOTH_IC0):
+        h = M.msrsb_setup(A, g, M.opts(smoother=sm, tol=0.0, max_iter=10))
+        z.append(h.apply(v).cpu().numpy())
+        h.destroy()
+    assert np.array_equal(z[0], z[1])

@@ -337,6 +337,72 @@ def test_block_gauss_seidel_solves_its_triangle(order):
         assert np.abs(M @ z - v[sm.order]).max() < 1e-10 * np.abs(v).max()
 
 
+@pytest.mark.parametrize("order", ["colour", "natural"])
+def test_ic0_factors_are_symmetric_and_match_a_on_the_pattern(order):
+    """IC(0) (Sec. 4.1, 4.3) as ILU(0) of the SPD elasticity operator in node
+    order: L U = A on A's pattern and U = diag(U) L^T, i.e. M = L D L^T."""
+    rng = np.random.default_rng(14)
+    e = q1_elasticity(np.exp(rng.standard_normal((3, 3, 3))), rng.uniform(0.2, 0.35, (3, 3, 3)))
+    A = O.bsr_to_csr(e["indptr"], e["indices"], e["data"])
+    sm = O.ColouredSmoother(A, O.parity_colours(e["node_dims"]) if order == "colour" else None, "ilu0", bdim=3)
+    B = sm.B.toarray()
+    L = sm.L.toarray() + np.eye(B.shape[0])
+    U = sm.U.toarray()
+    mask = B != 0
+    assert np.abs((L @ U)[mask] - B[mask]).max() <= 1e-12 * np.abs(B).max()
+    assert np.abs(U - np.diag(np.diag(U)) @ L.T).max() <= 1e-12 * np.abs(U).max()
+    assert np.diag(U).min() > 0
+
+
+def test_ic0_is_exact_on_a_chain_of_blocks():
+    """On a block-tridiagonal SPD matrix (a chain of nodes with 3x3 blocks)
+    the natural-order IC(0) drops no fill, so M = A; the parity order (red-
+    black nodes) drops fill and is not exact."""
+    rng = np.random.default_rng(15)
+    nn = 12
+    blocks = []
+    rows = []
+    cols = []
+    for i in range(nn):
+        for j in (i - 1, i, i + 1):
+            if 0 <= j < nn:
+                rows.append(i)
+                cols.append(j)
+    off = {}
+    for i in range(nn - 1):
+        off[i] = -rng.uniform(0.2, 0.5, (3, 3))
+    data = []
+    for i, j in zip(rows, cols):
+        if i == j:
+            data.append(np.eye(3) * 4 + 0.1 * np.ones((3, 3)))
+        elif j == i + 1:
+            data.append(off[i])
+        else:
+            data.append(off[j].T)
+    indptr = np.searchsorted(rows, np.arange(nn + 1))
+    A = O.bsr_to_csr(indptr, np.array(cols), np.array(data))
+    assert np.linalg.eigvalsh(A.toarray()).min() > 0
+    v = rng.standard_normal(3 * nn)
+    nat = O.ColouredSmoother(A, None, "ilu0", bdim=3)
+    assert np.abs(A @ nat.solve(v) - v).max() <= 1e-12 * np.abs(v).max()
+    rb = O.ColouredSmoother(A, np.arange(nn) % 2, "ilu0", bdim=3)
+    assert np.abs(A @ rb.solve(v) - v).max() > 1e-6
+
+
+def test_ic0_two_stage_operator_is_symmetric():
+    """IC(0) before and after the coarse stage gives a symmetric two-stage
+    operator, as PCG needs (Sec. 4)."""
+    rng = np.random.default_rng(16)
+    e = q1_elasticity(np.exp(rng.standard_normal((4, 3, 3))), rng.uniform(0.2, 0.35, (4, 3, 3)))
+    s = O.setup_elastic(e["indptr"], e["indices"], e["data"], e["node_dims"], (2, 2, 2), tol=0.0, max_iter=8,
+                        smoother="ic0")
+    n = s["A"].shape[0]
+    I = np.eye(n)
+    Minv = np.column_stack([s["tl"].apply(I[:, j]) for j in range(n)])
+    assert np.abs(Minv - Minv.T).max() <= 1e-10 * np.abs(Minv).max()
+    assert np.linalg.eigvalsh(0.5 * (Minv + Minv.T)).min() > 0
+
+
 def test_block_prolongation_interleaves_components():
     """Sec. 4: component l of every fine node is interpolated from component l
     of the coarse nodes only, with that component's own basis. Three different
@@ -407,6 +473,65 @@ def test_coarse_correction_galerkin_orthogonality():
     assert np.abs(tl.R @ r).max() <= 1e-10 * np.abs(tl.R @ v).max()
     w = np.random.default_rng(8).standard_normal(A.shape[0])
     assert np.allclose(tl.apply(2 * v - 3 * w), 2 * tl.apply(v) - 3 * tl.apply(w), rtol=0, atol=1e-10)
+
+
+def test_fv_restriction_is_the_block_indicator():
+    """Petrov-Galerkin R of Sec. 2 (the MSFV choice): row J sums the fine
+    equations of primal block J; checked against blocks from cell coordinates
+    (cell x lies in block x // H per axis) and, for 3x3 blocks, per component."""
+    dims, H = (10, 7, 5), (4, 4, 2)
+    part = O.partition(dims, H, 0)
+    coords = np.indices(dims).reshape(3, -1, order="F")
+    nb = [-(-d // h) for d, h in zip(dims, H)]
+    blk = coords[0] // H[0] + nb[0] * (coords[1] // H[1] + nb[1] * (coords[2] // H[2]))
+    R = O.fv_restriction(part["part"], part["nc"]).toarray()
+    assert R.shape == (part["nc"], coords.shape[1])
+    assert np.array_equal(R, (blk[None, :] == np.arange(part["nc"])[:, None]).astype(float))
+    R3 = O.fv_restriction(part["part"], part["nc"], bdim=3).toarray()
+    for l in range(3):
+        assert np.array_equal(R3[l::3, l::3], R)
+        for m in range(3):
+            if m != l:
+                assert not R3[l::3, m::3].any()
+
+
+def test_fv_restriction_conserves_mass_on_every_coarse_block():
+    """The finite-volume restriction makes the coarse correction conservative
+    (Sec. 2): the residual v - A P A_c^-1 R v sums to zero over every primal
+    block, while the Galerkin choice (R = P^T) does not give this."""
+    c = darcy_2d_case(n=24)
+    A = _csr((c["indptr"], c["indices"], c["data"]))
+    fv = O.setup_scalar(A, c["dims"], c["H"], tol=0.0, max_iter=20, restriction="fv")
+    ga = O.setup_scalar(A, c["dims"], c["H"], tol=0.0, max_iter=20)
+    v = np.random.default_rng(17).standard_normal(A.shape[0])
+    Rb = O.fv_restriction(fv["part"]["part"], fv["part"]["nc"])
+    r_fv = v - A @ fv["tl"].multiscale(v)
+    r_ga = v - A @ ga["tl"].multiscale(v)
+    assert np.abs(Rb @ r_fv).max() <= 1e-10 * np.abs(Rb @ v).max()
+    assert np.abs(Rb @ r_ga).max() > 1e-6 * np.abs(Rb @ v).max()
+    # A_c = R A P with P's rows summing to one: A_c 1 = R (A 1)
+    Ac = fv["tl"].Ac
+    assert np.abs(Ac @ np.ones(Ac.shape[0]) - Rb @ (A @ np.ones(A.shape[0]))).max() <= 1e-12 * abs(Ac).max()
+
+
+def test_two_level_fv_matches_error_propagation_matrix():
+    """Alg. 4 with the Petrov-Galerkin restriction equals (I - E) A^-1 with
+    E = (I - M_post^-1 A)(I - P A_c^-1 R A), A_c = R A P, on a dense case."""
+    c = darcy_2d_case(n=12, H=4)
+    A = _csr((c["indptr"], c["indices"], c["data"]))
+    s = O.setup_scalar(A, c["dims"], c["H"], tol=0.0, max_iter=10, restriction="fv")
+    tl = s["tl"]
+    Ad = A.toarray()
+    n = Ad.shape[0]
+    I = np.eye(n)
+    Minv = np.column_stack([tl.apply(I[:, j]) for j in range(n)])
+    Mpost = np.column_stack([tl.post.solve(I[:, j]) for j in range(n)])
+    P = tl.P.toarray()
+    R = O.fv_restriction(s["part"]["part"], s["part"]["nc"]).toarray()
+    C = P @ np.linalg.solve(R @ Ad @ P, R)
+    E = (I - Mpost @ Ad) @ (I - C @ Ad)
+    ref = (I - E) @ np.linalg.inv(Ad)
+    assert np.abs(Minv - ref).max() <= 1e-8 * np.abs(ref).max()
 
 
 # ---------------- Krylov ----------------
