@@ -300,6 +300,30 @@ def colour_order(colour):
     return np.argsort(colour, kind="stable")
 
 
+def line_block_order(dims):
+    """Elimination order by line blocks: the grid is cut into blocks of whole
+    x-lines, 2 lines high in y (and 2 deep in z in 3D); blocks are coloured by
+    the parity of their y (and z) block index (2 colours in 2D, 4 in 3D), so
+    blocks of one colour never share a 3^d stencil; the order is colour, then
+    block, then the natural order inside the block (x fastest). Returns
+    (order, colour of every point, block of every point, sub-line of every
+    point inside its block)."""
+    d = len(dims)
+    coords = np.indices(dims).reshape(d, -1, order="F")
+    nbk = [-(-dims[a] // 2) for a in range(1, d)]
+    colour = np.zeros(coords.shape[1], dtype=np.int64)
+    block = np.zeros(coords.shape[1], dtype=np.int64)
+    sub = np.zeros(coords.shape[1], dtype=np.int64)
+    st = 1
+    for a in range(1, d):
+        colour += ((coords[a] // 2) % 2) << (a - 1)
+        block += (coords[a] // 2) * st
+        sub += (coords[a] % 2) << (a - 1)
+        st *= nbk[a - 1]
+    order = np.lexsort((coords[0], sub, block, colour))
+    return order, colour, block, sub
+
+
 _lib = None
 
 
@@ -362,14 +386,18 @@ class ColouredSmoother:
     order.
     """
 
-    def __init__(self, A, colour, kind, bdim=1):
+    def __init__(self, A, colour, kind, bdim=1, order=None):
+        """colour: per-point colours (colour order), or None with order None
+        (natural order); order: an explicit elimination order of the points
+        (e.g. line_block_order), solved by sequential substitution."""
         self.kind = kind
         self.bdim = bdim
         A = sp.csr_matrix(A)
-        self.natural = colour is None
-        if self.natural:
+        # sequential substitution unless the order is by independent colours
+        self.natural = colour is None or order is not None
+        if colour is None:
             colour = np.zeros(A.shape[0] // bdim, dtype=np.int64)
-        node_order = colour_order(colour)
+        node_order = colour_order(colour) if order is None else np.asarray(order)
         if bdim == 1:
             order = node_order
             dof_colour = colour
@@ -649,8 +677,9 @@ def setup_scalar(A, dims, H, centering=0, omega=2.0 / 3.0, tol=1e-3, n_it=10, ma
                  smoother="ilu0", coarse=True, order="colour", restriction="galerkin"):
     """Alg. 2 for a scalar operator (flow): partition, filter, Alg. 1, Galerkin
     coarse operator, coarse LU and an ILU(0) post-smoother, eliminated in the
-    parity-colour order (order="colour", the GPU's) or in the natural order
-    (order="natural", the paper's MATLAB setting). restriction "galerkin"
+    parity-colour order (order="colour"), by line blocks (order="lines",
+    line_block_order) or in the natural order (order="natural", the paper's
+    MATLAB setting). restriction "galerkin"
     (R = P^T) or "fv" (the finite-volume Petrov-Galerkin R of fv_restriction)."""
     A = sp.csr_matrix(A)
     A.sort_indices()
@@ -659,8 +688,12 @@ def setup_scalar(A, dims, H, centering=0, omega=2.0 / 3.0, tol=1e-3, n_it=10, ma
     P0 = indicator(part["part"], part["pat"])
     vals, its, e_it, hist = enhanced_msrsb(Ahat, part["pat"], P0, part["skel"], omega, tol, n_it, max_iter)
     P = as_matrix(vals, part["pat"])
-    col = parity_colours(dims) if order == "colour" else None
-    post = ColouredSmoother(A, col, "ilu0") if smoother == "ilu0" else None
+    if order == "lines":
+        lo, lcol, _, _ = line_block_order(dims)
+        post = ColouredSmoother(A, lcol, "ilu0", order=lo) if smoother == "ilu0" else None
+    else:
+        col = parity_colours(dims) if order == "colour" else None
+        post = ColouredSmoother(A, col, "ilu0") if smoother == "ilu0" else None
     R = fv_restriction(part["part"], part["nc"]) if restriction == "fv" else None
     tl = TwoLevel(A, P, pre=None, post=post, coarse=coarse, R=R)
     return dict(part=part, Ahat=Ahat, vals=vals, iters=its, e_it=e_it, hist=hist, P=P, tl=tl)

@@ -261,87 +261,143 @@ __global__ void __launch_bounds__(kPlaneThreads) plane_factor_kernel(PlaneGeom G
     }
 }
 
+// Asynchronous global -> shared copies (cp.async) for the staged solve; the
+// waits are the hardware's group waits.
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
 // Application w = A_c^-1 v through the plane factors. vc, wc: FP64 [np*m]
-// in coarse dof order; wc32 (nullable) an FP32 copy of w.
+// in coarse dof order; wc32 (nullable) an FP32 copy of w. Steps
+// s = 0 .. 2 np - 2: forward planes k = s, then backward planes
+// k = 2 np - 2 - s. With stage set, every step's own rows of its matrix (a
+// contiguous block of the row-major X_k or G_k), the lower couplings of the
+// stencil and the gather pi_k are copied to shared memory asynchronously two
+// steps ahead (double buffered; they do not depend on the recurrence), so
+// that each step waits only on the cluster barrier and its own arithmetic.
 __global__ void __launch_bounds__(kPlaneThreads) plane_solve_kernel(PlaneGeom G, const double *__restrict__ Acs,
                                                                     const double *__restrict__ X,
                                                                     const double *__restrict__ Gm,
                                                                     const int *__restrict__ pi,
                                                                     const double *__restrict__ vc,
-                                                                    double *__restrict__ wc, float *__restrict__ wc32) {
+                                                                    double *__restrict__ wc, float *__restrict__ wc32,
+                                                                    int stage) {
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank(), nct = (int)cluster.num_blocks();
-    const int m = G.m, bd = G.bd, NI = G.NI;
+    const int m = G.m, bd = G.bd, NI = G.NI, np = G.np;
     const int rw = (m + nct - 1) / nct;
-    const int r0 = rank * rw, r1 = min(m, r0 + rw);
+    const int r0 = rank * rw, r1 = min(m, r0 + rw), nr = max(0, r1 - r0);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nsteps = 2 * np - 1;
+    const int lowc = NI * bd * bd;  // lower-coupling values per node, contiguous in the stencil
     extern __shared__ double sm[];
     double *ybuf = sm;          // full plane vector, double buffered [2][m] (written by every CTA)
     double *t = ybuf + 2 * m;   // right-hand side of the plane [m]
     double *tp = t + m;         // t gathered by pi [m]
-    pdl_prologue();
-    // ---- forward: y_k = X_k Pi_k (v_k - L_k y_{k-1}) ----
-    for (int k = 0; k < G.np; ++k) {
-        const double *yprev = ybuf + ((k + 1) & 1) * m;
-        const int Jbase = k * G.PN;
-        for (int j = tid; j < m; j += kPlaneThreads) {
-            const int uj = j / bd, l = j - uj * bd;
-            double v = vc[(long)(Jbase + uj) * bd + l];
-            if (k > 0)
-                for (int b = 0; b < NI; ++b) {
-                    const int tn = plane_nbr(G, uj, b);
-                    if (tn < 0) continue;
-                    for (int c = 0; c < bd; ++c) v = fma(-st_val(Acs, G, Jbase + uj, b, l, c), yprev[tn * bd + c], v);
+    double *mat = tp + m;       // staged rows [2][rw*m]
+    double *stc = mat + 2 * (long)rw * m;             // staged lower couplings [2][PN*lowc]
+    int *spi = (int *)(stc + 2 * (long)G.PN * lowc);  // staged pi [2][m]
+    auto issue = [&](int st, int buf) {
+        if (stage && st < nsteps) {
+            const bool fwd = st < np;
+            const int k = fwd ? st : 2 * np - 2 - st;
+            const double *M = (fwd ? X : Gm) + (long)k * m * m + (long)r0 * m;
+            double *dst = mat + (long)buf * rw * m;
+            for (int q = tid; q < nr * m; q += kPlaneThreads) cp_async8(dst + q, M + q);
+            if (fwd) {
+                for (int q = tid; q < m; q += kPlaneThreads) cp_async4(spi + buf * m + q, pi + (long)k * m + q);
+                if (k > 0) {
+                    double *sd = stc + (long)buf * G.PN * lowc;
+                    const double *src = Acs + (long)k * G.PN * G.nq * bd * bd;
+                    for (int q = tid; q < G.PN * lowc; q += kPlaneThreads) {
+                        const int u = q / lowc, r = q - u * lowc;
+                        cp_async8(sd + q, src + (long)u * G.nq * bd * bd + r);
+                    }
                 }
-            t[j] = v;
-        }
-        __syncthreads();
-        const int *pk = pi + (long)k * m;
-        for (int j = tid; j < m; j += kPlaneThreads) tp[j] = t[pk[j]];
-        __syncthreads();
-        const double *Xk = X + (long)k * m * m;
-        double *ynew = ybuf + (k & 1) * m;
-        for (int i = r0 + warp; i < r1; i += kPlaneThreads / 32) {
-            const double *xr = Xk + (long)i * m;
-            double s = 0.0;
-            for (int j = lane; j < m; j += 32) s = fma(__ldg(xr + j), tp[j], s);
-            s = warp_sum(s);
-            if (lane == 0) {
-                for (int r = 0; r < nct; ++r) cluster.map_shared_rank(ynew, r)[i] = s;
-                wc[(long)(Jbase + i / bd) * bd + i % bd] = s;
             }
         }
+        cp_async_commit();  // one group per step, empty or not
+    };
+    // the factors are fixed for a solve: the first two steps' copies start
+    // before the wait on the previous kernel
+    issue(0, 0);
+    issue(1, 1);
+    pdl_prologue();
+    for (int st = 0; st < nsteps; ++st) {
+        const int buf = st & 1;
+        cp_async_wait1();
+        __syncthreads();
+        const double *Mrows = stage ? mat + (long)buf * rw * m : nullptr;
+        if (st < np) {  // ---- forward: y_k = X_k Pi_k (v_k - L_k y_{k-1}) ----
+            const int k = st;
+            const double *yprev = ybuf + ((k + 1) & 1) * m;
+            const int Jbase = k * G.PN;
+            const double *sl = stc + (long)buf * G.PN * lowc;
+            for (int j = tid; j < m; j += kPlaneThreads) {
+                const int uj = j / bd, l = j - uj * bd;
+                double v = vc[(long)(Jbase + uj) * bd + l];
+                if (k > 0)
+                    for (int b = 0; b < NI; ++b) {
+                        const int tn = plane_nbr(G, uj, b);
+                        if (tn < 0) continue;
+                        for (int c = 0; c < bd; ++c) {
+                            const double a = stage ? sl[(long)uj * lowc + (b * bd + l) * bd + c]
+                                                   : st_val(Acs, G, Jbase + uj, b, l, c);
+                            v = fma(-a, yprev[tn * bd + c], v);
+                        }
+                    }
+                t[j] = v;
+            }
+            __syncthreads();
+            const int *pk = stage ? spi + buf * m : pi + (long)k * m;
+            for (int j = tid; j < m; j += kPlaneThreads) tp[j] = t[pk[j]];
+            __syncthreads();
+            const double *Xk = X + (long)k * m * m;
+            double *ynew = ybuf + (k & 1) * m;
+            for (int i = r0 + warp; i < r1; i += kPlaneThreads / 32) {
+                const double *xr = stage ? Mrows + (long)(i - r0) * m : Xk + (long)i * m;
+                double s = 0.0;
+                for (int j = lane; j < m; j += 32) s = fma(xr[j], tp[j], s);
+                s = warp_sum(s);
+                if (lane == 0) {
+                    for (int r = 0; r < nct; ++r) cluster.map_shared_rank(ynew, r)[i] = s;
+                    const long q = (long)(Jbase + i / bd) * bd + i % bd;
+                    wc[q] = s;
+                    if (wc32 && k == np - 1) wc32[q] = (float)s;
+                }
+            }
+        } else {  // ---- backward: w_k = y_k - G_k w_{k+1} ----
+            const int k = 2 * np - 2 - st;
+            const double *wnext = ybuf + ((k + 1) & 1) * m;
+            double *wnew = ybuf + (k & 1) * m;
+            const double *Gk = Gm + (long)k * m * m;
+            const int Jbase = k * G.PN;
+            for (int i = r0 + warp; i < r1; i += kPlaneThreads / 32) {
+                const double *gr = stage ? Mrows + (long)(i - r0) * m : Gk + (long)i * m;
+                double s = 0.0;
+                for (int j = lane; j < m; j += 32) s = fma(gr[j], wnext[j], s);
+                s = warp_sum(s);
+                if (lane == 0) {
+                    const long q = (long)(Jbase + i / bd) * bd + i % bd;
+                    const double w = wc[q] - s;
+                    for (int r = 0; r < nct; ++r) cluster.map_shared_rank(wnew, r)[i] = w;
+                    wc[q] = w;
+                    if (wc32) wc32[q] = (float)w;
+                }
+            }
+        }
+        __syncthreads();  // this step's staged buffers are no longer read
+        issue(st + 2, buf);
         cluster.sync();
     }
-    // ---- backward: w_{np-1} = y_{np-1}; w_k = y_k - G_k w_{k+1} ----
-    {
-        const int k = G.np - 1;
-        if (wc32)
-            for (int i = r0 + tid; i < r1; i += kPlaneThreads) {
-                const long q = (long)(k * G.PN + i / bd) * bd + i % bd;
-                wc32[q] = (float)ybuf[(k & 1) * m + i];
-            }
-    }
-    for (int k = G.np - 2; k >= 0; --k) {
-        const double *wnext = ybuf + ((k + 1) & 1) * m;
-        double *wnew = ybuf + (k & 1) * m;
-        const double *Gk = Gm + (long)k * m * m;
-        const int Jbase = k * G.PN;
-        for (int i = r0 + warp; i < r1; i += kPlaneThreads / 32) {
-            const double *gr = Gk + (long)i * m;
-            double s = 0.0;
-            for (int j = lane; j < m; j += 32) s = fma(__ldg(gr + j), wnext[j], s);
-            s = warp_sum(s);
-            if (lane == 0) {
-                const long q = (long)(Jbase + i / bd) * bd + i % bd;
-                const double w = wc[q] - s;
-                for (int r = 0; r < nct; ++r) cluster.map_shared_rank(wnew, r)[i] = w;
-                wc[q] = w;
-                if (wc32) wc32[q] = (float)w;
-            }
-        }
-        cluster.sync();
-    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 // The explicit inverse A_c^-1 (row-major n_C x n_C) from the plane factors,
@@ -420,6 +476,12 @@ static size_t factor_smem(int m, int nct) {
     return (size_t)cw * m * sizeof(double) + 3 * (size_t)m * sizeof(double) + 3 * (size_t)m * sizeof(int);
 }
 static size_t solve_smem(int m) { return 4 * (size_t)m * sizeof(double); }
+// with the staged copies (see plane_solve_kernel)
+static size_t solve_smem_staged(const PlaneGeom &G, int nct) {
+    const int rw = (G.m + nct - 1) / nct;
+    return solve_smem(G.m) + 2 * (size_t)rw * G.m * sizeof(double) +
+           2 * (size_t)G.PN * G.NI * G.bd * G.bd * sizeof(double) + 2 * (size_t)G.m * sizeof(int);
+}
 
 constexpr size_t kPlaneSmemMax = 220 * 1024;
 
@@ -505,6 +567,17 @@ msrsb_status plane_factor(int dim, const int nb[3], int bd, const double *Acs, C
     cp->m = G.m;
     cp->np = G.np;
     cp->nct = nct;
+    cp->stage = 0;
+    {  // staged application where its shared memory fits and the cluster can be scheduled with it
+        const size_t ss = solve_smem_staged(G, nct);
+        if (ss <= kPlaneSmemMax) {
+            cudaLaunchAttribute a2[2];
+            cudaLaunchConfig_t cs = cluster_cfg(a2, nct, ss, nullptr, false);
+            int ns = 0;
+            if (cudaOccupancyMaxActiveClusters(&ns, plane_solve_kernel, &cs) == cudaSuccess && ns > 0) cp->stage = 1;
+            cudaGetLastError();
+        }
+    }
     const long mm = (long)G.m * G.m;
     MSRSB_TRY(dalloc(&cp->X, (size_t)G.np * mm, s));
     MSRSB_TRY(dalloc(&cp->G, (size_t)(G.np > 1 ? G.np - 1 : 1) * mm, s));
@@ -528,16 +601,18 @@ msrsb_status plane_solve(int dim, const int nb[3], int bd, const double *Acs, co
                          const double *vc, double *wc, float *wc32, cudaStream_t s) {
     PlaneGeom G;
     plane_geom(dim, nb, bd, &G);
+    const int stage = cp->stage;
+    const size_t staged = solve_smem_staged(G, cp->nct);
     cudaLaunchAttribute attr[2];
-    cudaLaunchConfig_t cfg = cluster_cfg(attr, cp->nct, solve_smem(G.m), s, true);
+    cudaLaunchConfig_t cfg = cluster_cfg(attr, cp->nct, stage ? staged : solve_smem(G.m), s, true);
     count_launch();
     cudaError_t e = cudaLaunchKernelEx(&cfg, plane_solve_kernel, G, Acs, (const double *)cp->X,
-                                       (const double *)cp->G, (const int *)cp->pi, vc, wc, wc32);
+                                       (const double *)cp->G, (const int *)cp->pi, vc, wc, wc32, stage);
     if (e == cudaErrorNotSupported || e == cudaErrorInvalidValue) {  // programmatic serialisation refused
         cudaGetLastError();
         cfg.numAttrs = 1;
         e = cudaLaunchKernelEx(&cfg, plane_solve_kernel, G, Acs, (const double *)cp->X, (const double *)cp->G,
-                               (const int *)cp->pi, vc, wc, wc32);
+                               (const int *)cp->pi, vc, wc, wc32, stage);
     }
     MSRSB_CUDA(e);
     return MSRSB_OK;

@@ -13,6 +13,7 @@ low (x_axis = 0) and 1 = high, as ``("D", value)`` for a fixed pressure or
 import itertools
 
 import numpy as np
+import scipy.sparse as sp
 
 from .fields import gaussian_random_field, rotation_2d, rotation_zyx
 
@@ -282,3 +283,175 @@ def darcy_3d_case(n=64, H=8, seed=1002, sigma=3.0, corr_len=8.0, dims=None):
     Hs = (H,) * 3 if np.isscalar(H) else tuple(H)
     return dict(indptr=indptr, indices=indices, data=data, b=b, dims=dims, H=Hs,
                 centering=0, ncomp=1)
+
+
+# ----------------------------------------------------------------------------
+# MPFA-O on rough (perturbed) quadrilateral grids, 2D (Sec. 3.1 and 3.2)
+# ----------------------------------------------------------------------------
+
+
+def perturbed_grid(nx, ny, lx, ly, amp, rng, stretch_y=1.0):
+    """Node coordinates (nx+1, ny+1) of a structured quadrilateral grid over
+    [0, lx] x [0, ly*stretch_y]: interior nodes moved in x and y by amp * dx *
+    psi, psi ~ U(-1/2, 1/2) (Sec. 3.2: amp = 0.2), boundary nodes fixed."""
+    dx, dy = lx / nx, ly / ny
+    X, Y = np.meshgrid(np.arange(nx + 1) * dx, np.arange(ny + 1) * dy, indexing="ij")
+    px = amp * dx * (rng.uniform(size=X.shape) - 0.5)
+    py = amp * dx * (rng.uniform(size=X.shape) - 0.5)
+    inner = np.zeros(X.shape, dtype=bool)
+    inner[1:-1, 1:-1] = True
+    X = X + np.where(inner, px, 0.0)
+    Y = (Y + np.where(inner, py, 0.0)) * stretch_y
+    return X, Y
+
+
+def mpfa_o_quads(X, Y, K, bc=None):
+    """MPFA-O (continuity points at the edge midpoints) on a structured 2D
+    quadrilateral grid with node coordinates X, Y (nx+1, ny+1) and cell
+    tensors K (nx, ny, 2, 2); cells flat i + nx*j.
+
+    In the interaction region of every node (up to four cells around it, four
+    half-edges towards the neighbouring nodes) the pressure is linear in each
+    cell, through the cell pressure at the cell centre (mean of its corners)
+    and the potentials u_e at the midpoints of its two edges touching the node;
+    the outward half-edge flux is -n^T K grad p with n the half-edge normal
+    scaled by its length. Flux continuity on interior half-edges and the
+    boundary condition on boundary ones (bc[(axis, side)] = ("D", value or
+    f(x, y)) for Dirichlet, absent for no flow; axis 0: the x = min / max
+    sides, axis 1: y) give a local system u = C^-1 (D p + e), which expresses
+    every half-edge flux in the cell pressures.
+    Returns (indptr, indices, data, b): int32 CSR (9-point stencil) and b."""
+    bc = bc or {}
+    X = np.asarray(X, dtype=np.float64)
+    Y = np.asarray(Y, dtype=np.float64)
+    K = np.asarray(K, dtype=np.float64)
+    nx, ny = K.shape[:2]
+    ncell = nx * ny
+    xc = 0.25 * (X[:-1, :-1] + X[1:, :-1] + X[1:, 1:] + X[:-1, 1:])
+    yc = 0.25 * (Y[:-1, :-1] + Y[1:, :-1] + Y[1:, 1:] + Y[:-1, 1:])
+    I, J = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1), indexing="ij")
+    I, J = I.ravel(), J.ravel()
+    nv = I.size
+    xv, yv = X[I, J], Y[I, J]
+
+    def node(di, dj):  # neighbour node coordinates (clipped where absent)
+        ii, jj = np.clip(I + di, 0, nx), np.clip(J + dj, 0, ny)
+        return X[ii, jj], Y[ii, jj], (I + di >= 0) & (I + di <= nx) & (J + dj >= 0) & (J + dj <= ny)
+
+    # half-edges E, W, N, S: continuity point, normal from cell a to cell b
+    hx, hy, hok, mid, nrm = [], [], [], [], []
+    for di, dj in ((1, 0), (-1, 0), (0, 1), (0, -1)):
+        x2, y2, ok = node(di, dj)
+        mx, my = 0.5 * (xv + x2), 0.5 * (yv + y2)
+        hxe, hye = mx - xv, my - yv
+        mid.append((mx, my))
+        hok.append(ok)
+        if (di, dj) in ((1, 0), (0, -1)):  # left normal
+            nrm.append((-hye, hxe))
+        else:  # right normal
+            nrm.append((hye, -hxe))
+    # local cells SW, SE, NW, NE and their (a, b) roles on the half-edges
+    cells = [(-1, -1), (0, -1), (-1, 0), (0, 0)]
+    cid, cok = [], []
+    for ci, cj in cells:
+        ii, jj = I + ci, J + cj
+        ok = (ii >= 0) & (ii < nx) & (jj >= 0) & (jj < ny)
+        cok.append(ok)
+        cid.append(np.where(ok, np.clip(ii, 0, nx - 1) + nx * np.clip(jj, 0, ny - 1), 0))
+    # half-edge e: (cell a, cell b); E: SE|NE, W: SW|NW, N: NW|NE, S: SW|SE
+    pair = [(1, 3), (0, 2), (2, 3), (0, 1)]
+    # half-edges of each cell (in a fixed order)
+    cedges = [(1, 3), (0, 3), (1, 2), (0, 2)]
+    # w[c][e] (nv, 2): outward flux of cell c through its half-edge e in terms
+    # of (u_e1 - p_c, u_e2 - p_c): -n^T K R^-1
+    W = np.zeros((nv, 4, 4, 2))  # [vertex, cell, half-edge, k]
+    for c in range(4):
+        ci, cj = cells[c]
+        ii, jj = np.clip(I + ci, 0, nx - 1), np.clip(J + cj, 0, ny - 1)
+        Kc = K[ii, jj]
+        xcc, ycc = xc[ii, jj], yc[ii, jj]
+        e1, e2 = cedges[c]
+        R = np.stack([np.stack([mid[e1][0] - xcc, mid[e1][1] - ycc], -1),
+                      np.stack([mid[e2][0] - xcc, mid[e2][1] - ycc], -1)], 1)  # (nv, 2, 2)
+        R[~cok[c]] = np.eye(2)
+        Rinv = np.linalg.inv(R)
+        for e in (e1, e2):
+            sgn = 1.0 if pair[e][0] == c else -1.0
+            n = sgn * np.stack(nrm[e], -1)  # (nv, 2) outward normal of c
+            W[:, c, e] = -np.einsum("vi,vij,vjk->vk", n, Kc, Rinv)
+    # local system C u = D p + ebc over the 4 half-edges
+    C = np.zeros((nv, 4, 4))
+    D = np.zeros((nv, 4, 4))
+    ebc = np.zeros((nv, 4))
+    flux_cells = []  # (e, c, mask) contributions to the cell balances
+    for e in range(4):
+        a, b = pair[e]
+        pa, pb = cok[a], cok[b]
+        both = pa & pb & hok[e]
+        one = (pa ^ pb) & hok[e]
+        absent = ~(both | one)
+        # the boundary side of a one-sided half-edge
+        if e in (0, 1):  # E, W: on y = min (cells above only) or y = max
+            side_key = np.where(pb, 0, 1)  # only the upper cell b present -> bottom side
+            axis = 1
+        else:  # N, S: on x = min (only the right cell b) or x = max
+            side_key = np.where(pb, 0, 1)
+            axis = 0
+        mx, my = mid[e]
+        dir_mask = np.zeros(nv, dtype=bool)
+        dval = np.zeros(nv)
+        for side in (0, 1):
+            kind = bc.get((axis, side))
+            if kind is not None and kind[0] == "D":
+                msk = one & (side_key == side)
+                dir_mask |= msk
+                v = kind[1](mx, my) if callable(kind[1]) else np.full(nv, float(kind[1]))
+                dval = np.where(msk, v, dval)
+        neu = one & ~dir_mask
+        ident = absent | dir_mask
+        # continuity: F_a + F_b = 0; Neumann: F_present = 0
+        for c in (a, b):
+            use = both | (neu & cok[c])
+            e1, e2 = cedges[c]
+            C[:, e, e1] += np.where(use, W[:, c, e, 0], 0.0)
+            C[:, e, e2] += np.where(use, W[:, c, e, 1], 0.0)
+            D[:, e, c] += np.where(use, W[:, c, e, 0] + W[:, c, e, 1], 0.0)
+        C[:, e, e] += ident
+        ebc[:, e] = np.where(dir_mask, dval, 0.0)
+        for c in (a, b):
+            flux_cells.append((e, c, cok[c] & (both | dir_mask)))
+    Cinv = np.linalg.inv(C)
+    Up = np.einsum("vij,vjk->vik", Cinv, D)  # u = Up p + ue
+    ue = np.einsum("vij,vj->vi", Cinv, ebc)
+    rows, cols, vals = [], [], []
+    b = np.zeros(ncell)
+    for e, c, msk in flux_cells:
+        e1, e2 = cedges[c]
+        w1, w2 = W[:, c, e, 0], W[:, c, e, 1]
+        coef = w1[:, None] * Up[:, e1, :] + w2[:, None] * Up[:, e2, :]  # d F / d p_local
+        coef[:, c] -= w1 + w2
+        const = w1 * ue[:, e1] + w2 * ue[:, e2]
+        for cc in range(4):
+            m2 = msk & cok[cc]
+            rows.append(cid[c][m2])
+            cols.append(cid[cc][m2])
+            vals.append(coef[m2, cc])
+        np.add.at(b, cid[c][msk], -const[msk])
+    A = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(ncell, ncell))
+    A.sum_duplicates()
+    A.sort_indices()
+    return A.indptr.astype(np.int32), A.indices.astype(np.int32), A.data.astype(np.float64), b
+
+
+def darcy_2d_perturbed_case(n=100, H=5, seed=1006, lx=20.0, ly=150.0, amp=0.2):
+    """The 2D MPFA-O test of Sec. 3.2: an n x n grid on an lx x ly domain with
+    interior nodes perturbed by amp * dx * U(-1/2, 1/2) in x and y, the tensor
+    [[100, 25], [25, 100]] in every cell, unit pressure drop from x = 0 (p = 1)
+    to x = lx (p = 0), no flow at the other sides, coarse blocks of H x H
+    cells."""
+    rng = np.random.default_rng(seed)
+    X, Y = perturbed_grid(n, n, lx, ly, amp, rng)
+    K = np.broadcast_to(np.array([[100.0, 25.0], [25.0, 100.0]]), (n, n, 2, 2)).copy()
+    indptr, indices, data, b = mpfa_o_quads(X, Y, K, {(0, 0): ("D", 1.0), (0, 1): ("D", 0.0)})
+    return dict(indptr=indptr, indices=indices, data=data, b=b, dims=(n, n), H=(H, H), centering=0, ncomp=1,
+                X=X, Y=Y)

@@ -274,12 +274,16 @@ def test_parity_colouring_is_valid():
     assert col.max() == 7
 
 
-@pytest.mark.parametrize("order", ["colour", "natural"])
+@pytest.mark.parametrize("order", ["colour", "natural", "lines"])
 def test_ilu0_defining_property(order):
-    """(L U)_ij = A_ij on A's pattern, in either elimination order."""
-    c = darcy_3d_case(n=8)
+    """(L U)_ij = A_ij on A's pattern, in every elimination order."""
+    c = darcy_3d_case(dims=(8, 7, 5))
     A = _csr((c["indptr"], c["indices"], c["data"]))
-    sm = O.ColouredSmoother(A, O.parity_colours(c["dims"]) if order == "colour" else None, "ilu0")
+    if order == "lines":
+        lo, lcol, _, _ = O.line_block_order(c["dims"])
+        sm = O.ColouredSmoother(A, lcol, "ilu0", order=lo)
+    else:
+        sm = O.ColouredSmoother(A, O.parity_colours(c["dims"]) if order == "colour" else None, "ilu0")
     if order == "natural":
         assert np.array_equal(sm.order, np.arange(A.shape[0]))
     B = sm.B
@@ -293,6 +297,35 @@ def test_ilu0_defining_property(order):
     v = np.random.default_rng(3).standard_normal(A.shape[0])
     zp = sm.solve(v)[sm.order]
     assert np.abs((L + sp.eye(B.shape[0])) @ (U @ zp) - v[sm.order]).max() < 1e-11 * np.abs(v).max()
+
+
+@pytest.mark.parametrize("dims", [(9, 7, 5), (6, 5), (5, 4, 4)])
+def test_line_block_order_structure(dims):
+    """The line-block order: blocks of one colour never share a 3^d stencil
+    (each colour stage is independent across blocks), and inside a block a
+    point's earlier neighbours are the previous point of its own x-line
+    (sub-line) or points of the block's earlier sub-lines: the structure the
+    GPU sweep relies on (a recurrence along x per sub-line)."""
+    c = darcy_3d_case(dims=dims) if len(dims) == 3 else darcy_2d_case(n=dims[0], H=2)
+    if len(dims) == 2:
+        dims = c["dims"]
+    A = _csr((c["indptr"], c["indices"], c["data"])).tocoo()
+    order, colour, block, sub = O.line_block_order(dims)
+    n = A.shape[0]
+    assert np.array_equal(np.sort(order), np.arange(n))
+    pos = np.empty(n, dtype=np.int64)
+    pos[order] = np.arange(n)
+    x = np.arange(n) % dims[0]
+    off = A.row != A.col
+    r, k = A.row[off], A.col[off]
+    same_colour = colour[r] == colour[k]
+    assert np.all(block[r][same_colour] == block[k][same_colour])  # same colour: same block only
+    earlier_in_block = (block[r] == block[k]) & (pos[k] < pos[r])
+    rec = earlier_in_block & (sub[r] == sub[k])
+    assert np.all(x[k][rec] == x[r][rec] - 1)
+    assert np.all(sub[k][earlier_in_block & ~rec] < sub[r][earlier_in_block & ~rec])
+    ncol = 2 ** (len(dims) - 1)
+    assert colour.max() == ncol - 1
 
 
 def test_ilu0_exact_for_tridiagonal():
