@@ -63,6 +63,7 @@ typedef enum {
 } msrsb_smoother;
 typedef enum { MSRSB_GMRES = 0, MSRSB_PCG = 1, MSRSB_RICHARDSON = 2 } msrsb_krylov;
 typedef enum { MSRSB_RESTRICT_GALERKIN = 0, MSRSB_RESTRICT_FV = 1 } msrsb_restriction;
+typedef enum { MSRSB_ORDER_LINES = 0, MSRSB_ORDER_PARITY = 1 } msrsb_ordering;
 
 /* Sparse FP64 fine operator, device arrays (rowptr[nrows+1], colidx[nnz],
  * val[nnz * bdim * bdim]). nrows and nnz count block rows / blocks. */
@@ -121,6 +122,16 @@ typedef struct {
                           block and the coarse correction conserves mass
                           block by block. A_c is then not symmetric: not
                           with MSRSB_PCG */
+    int32_t ordering;    /* msrsb_ordering: elimination order of the scalar
+                          ILU(0) smoother. LINES (default): blocks of whole
+                          x-lines, 2 lines high in y (and 2 deep in z), the
+                          blocks coloured by the parity of their y (z) index
+                          (2 colours in 2D, 4 in 3D), natural order inside a
+                          block; grids with nx <= 256 (wider ones use PARITY).
+                          PARITY: points coloured by coordinate parity (4 / 8
+                          colours), natural order inside a colour. The paper
+                          eliminates in the natural order; both are parallel
+                          orders, LINES the closer one */
 } msrsb_opts;
 
 typedef struct msrsb_handle msrsb_handle;

@@ -674,7 +674,7 @@ def pcg(A, b, M, x0=None, rtol=1e-8, maxit=500):
 
 
 def setup_scalar(A, dims, H, centering=0, omega=2.0 / 3.0, tol=1e-3, n_it=10, max_iter=100,
-                 smoother="ilu0", coarse=True, order="colour", restriction="galerkin"):
+                 smoother="ilu0", coarse=True, order="lines", restriction="galerkin"):
     """Alg. 2 for a scalar operator (flow): partition, filter, Alg. 1, Galerkin
     coarse operator, coarse LU and an ILU(0) post-smoother, eliminated in the
     parity-colour order (order="colour"), by line blocks (order="lines",

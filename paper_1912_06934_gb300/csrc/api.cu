@@ -124,6 +124,18 @@ msrsb_status l1_update(long N, const T *dinv, const TR *r, TZ *z, int from_zero,
 
 template <typename T, typename TZ>
 msrsb_status ilu0_apply(const msrsb_handle *h, T *ry, TZ *z, cudaStream_t s);
+bool lines_fit(const msrsb_grid *g);
+template <typename TF>
+msrsb_status lines_setup(msrsb_handle *h, TF *lu, cudaStream_t s);
+template <typename T, typename TZ>
+msrsb_status lines_apply(const msrsb_handle *h, T *ry, TZ *z, cudaStream_t s);
+void lines_free(IluLines *L, cudaStream_t s);
+// z += M^-1 r for the ILU(0) smoother, r in the smoother's order
+template <typename T, typename TZ>
+static msrsb_status ilu_any(const msrsb_handle *h, T *ry, TZ *z, cudaStream_t s) {
+    if (h->use_lines) return lines_apply<T, TZ>(h, ry, z, s);
+    return ilu0_apply<T, TZ>(h, ry, z, s);
+}
 template <typename TI, typename TO>
 msrsb_status permute_cast(long N, const TI *x, const int32_t *perm, TO *y, cudaStream_t s);
 template <typename T>
@@ -203,10 +215,16 @@ static msrsb_status setup_smoother(msrsb_handle *h, cudaStream_t s) {
         // factorised in the smoother's precision (FP32 in the mixed form)
         T *lu = nullptr;
         MSRSB_TRY(dalloc(&lu, A.nnz, s));
-        MSRSB_TRY(dalloc(&h->diag_pos, n, s));
         MSRSB_TRY(convert<T>(A.nnz, A.val, lu, s));
-        MSRSB_TRY(ilu0_factor<T>(&A, h->colour, h->ncolours, h->colour_rows, h->colour_ptr_h, h->diag_pos, lu, s));
-        MSRSB_TRY(ilu_build_ell<T>(h, lu, s));
+        if (h->opts.ordering == MSRSB_ORDER_LINES && lines_fit(&h->grid)) {
+            h->use_lines = 1;
+            MSRSB_TRY(lines_setup<T>(h, lu, s));
+        } else {
+            MSRSB_TRY(dalloc(&h->diag_pos, n, s));
+            MSRSB_TRY(
+                ilu0_factor<T>(&A, h->colour, h->ncolours, h->colour_rows, h->colour_ptr_h, h->diag_pos, lu, s));
+            MSRSB_TRY(ilu_build_ell<T>(h, lu, s));
+        }
         dfree(lu, s);
     } else if (h->opts.smoother == MSRSB_SMOOTH_GS) {
         if (bd != 3) return fail(MSRSB_EINVAL, "block Gauss-Seidel smoother needs a 3x3 block operator");
@@ -497,7 +515,7 @@ static msrsb_status apply_t(msrsb_handle *h, const TVI *v, TZ *z, cudaStream_t s
         } else {
             MSRSB_TRY((permute_cast<TVI, T>(N, v, h->pos_of, r, s)));
             MSRSB_CUDA(cudaMemsetAsync(z, 0, N * sizeof(TZ), s));
-            MSRSB_TRY((ilu0_apply<T, TZ>(h, r, z, s)));
+            MSRSB_TRY((ilu_any<T, TZ>(h, r, z, s)));
         }
     }
     if (coarse) {
@@ -537,7 +555,7 @@ static msrsb_status apply_t(msrsb_handle *h, const TVI *v, TZ *z, cudaStream_t s
                 MSRSB_TRY((resid_z32<T, TVI>(h, z32, v, r, h->pos_of, s)));
             else
                 MSRSB_TRY((resid_t<T, TZ, TVI>(h, aval_t, z, v, r, h->pos_of, s)));
-            MSRSB_TRY((ilu0_apply<T, TZ>(h, r, z, s)));
+            MSRSB_TRY((ilu_any<T, TZ>(h, r, z, s)));
         }
     }
     return MSRSB_OK;
@@ -963,6 +981,7 @@ static void handle_free(msrsb_handle *h) {
     dfree(h->Acs, s);
     dfree(h->Ainv, s);
     plane_free(&h->planes, s);
+    lines_free(&h->lines, s);
     dfree(h->ilu.lcol, s);
     dfree(h->ilu.ucol, s);
     dfree(h->ilu.lval, s);
@@ -1045,6 +1064,8 @@ extern "C" msrsb_status msrsb_setup(const msrsb_mat *A, const msrsb_grid *g, con
     if (opts->pre < 0 || opts->post < 0 || opts->pre > 64 || opts->post > 64)
         return fail(MSRSB_EINVAL, "pre/post must be 0..64 (got %d, %d)", opts->pre, opts->post);
     if (opts->no_coarse != 0 && opts->no_coarse != 1) return fail(MSRSB_EINVAL, "no_coarse must be 0 or 1");
+    if (opts->ordering != MSRSB_ORDER_LINES && opts->ordering != MSRSB_ORDER_PARITY)
+        return fail(MSRSB_EINVAL, "unknown ordering %d", opts->ordering);
     if (opts->restriction != MSRSB_RESTRICT_GALERKIN && opts->restriction != MSRSB_RESTRICT_FV)
         return fail(MSRSB_EINVAL, "unknown restriction %d", opts->restriction);
     if (opts->restriction == MSRSB_RESTRICT_FV && opts->krylov == MSRSB_PCG)

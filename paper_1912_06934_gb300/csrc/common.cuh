@@ -157,6 +157,21 @@ struct IluEll {
     void *lval = nullptr, *uval = nullptr, *udinv = nullptr;
 };
 
+// ILU(0) factors in the line-block order (see ilu_lines.cu): positions by
+// colour, block, line, x; per colour the parallel parts of L and U as ELL
+// blocks (columns as positions), per position the line recurrence
+// coefficients and 1 / u_pp.
+struct IluLines {
+    int nx = 0, ncol = 0;
+    int cptr[5] = {0};  // first position of each colour (+ end)
+    int bptr[5] = {0};  // first block of each colour (+ end)
+    int wl[4] = {0}, wu[4] = {0};
+    long lbase[4] = {0}, ubase[4] = {0};
+    int32_t *rows = nullptr, *blk_start = nullptr, *blk_nsub = nullptr;
+    int32_t *lcol = nullptr, *ucol = nullptr;
+    void *lval = nullptr, *uval = nullptr, *lrec = nullptr, *urec = nullptr, *udinv = nullptr;
+};
+
 // ---- device helpers -------------------------------------------------------
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
 
@@ -219,6 +234,8 @@ struct msrsb_handle {
     double *Ainv = nullptr;
     // smoother factors in A's (block) pattern, handle precision
     msrsb::IluEll ilu;          // ILU(0) factors (colour order), handle precision
+    msrsb::IluLines lines;      // ILU(0) factors (line-block order), handle precision
+    int use_lines = 0;          // the ILU(0) smoother uses the line-block order
     int32_t *pos_of = nullptr;  // colour-order position of every fine row
     int32_t *diag_pos = nullptr;
     void *dinv = nullptr;     // block GS: inverse 3x3 diagonal blocks [n][9]; IC(0): U_ii^-1 [n][9]

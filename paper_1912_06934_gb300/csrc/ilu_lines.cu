@@ -1,0 +1,546 @@
+// ILU(0) smoother (second stage of Alg. 4) in a line-block elimination order.
+//
+// The grid is cut into blocks of whole x-lines, 2 lines high in y (and 2 deep
+// in z in 3D). Blocks are coloured by the parity of their y (and z) block
+// index, 2 colours in 2D and 4 in 3D, so two blocks of one colour never share
+// a 3^dim stencil. The order is colour, then block, then the natural order
+// inside the block (x fastest): each block keeps the natural order of the
+// paper's MATLAB setting over its 2 (or 4) lines, and the strong couplings
+// along x stay inside the sequential chains. Compared with a pointwise parity
+// colouring this is a much stronger smoother on anisotropic and stretched
+// grids, with fewer launches per application (2 C - 1 for C colours).
+//
+// Inside a block, the earlier neighbours of point (x, q) (q its line inside
+// the block) are the previous point (x-1, q) of its own line and points of the
+// block's earlier lines. A triangular sweep therefore takes the lines of a
+// block in turn: every other contribution is gathered in parallel, and what
+// remains is the first-order recurrence y_x = s_x - l_x y_{x-1} along the
+// line, solved by a warp scan of affine maps. The factorisation runs one CTA
+// per block, one warp per line, on a wavefront: line q trails line q-1 by two
+// points, since (x, q) needs (x+1, q-1).
+#include "common.cuh"
+#include <climits>
+#include <vector>
+#include <cub/device/device_radix_sort.cuh>
+
+namespace msrsb {
+
+constexpr int kLinesMaxCpl = 8;  // x-chunks of 32 points per line: nx <= 256
+
+void diag_pos_launch(int n, const int32_t *rowptr, const int32_t *colidx, int32_t *dpos, int *status, cudaStream_t s);
+
+// sort key of every row: colour, block, line inside the block, x
+__global__ void line_key_kernel(int n, int dim, int nx, int ny, int nz, uint32_t *__restrict__ key,
+                                int32_t *__restrict__ idx) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int x = i % nx, y = (i / nx) % ny, z = dim == 3 ? i / (nx * ny) : 0;
+    const int by = y >> 1, bz = z >> 1, nby = (ny + 1) >> 1, nbz = dim == 3 ? (nz + 1) >> 1 : 1;
+    const int c = (by & 1) | (dim == 3 ? ((bz & 1) << 1) : 0);
+    const int sub = (y & 1) | (dim == 3 ? ((z & 1) << 1) : 0);
+    const long blk = (long)by + (long)nby * bz;
+    key[i] = (uint32_t)((((long)c * nby * nbz + blk) * 4 + sub) * nx + x);
+    idx[i] = i;
+}
+
+__global__ void lines_pos_kernel(int n, const int32_t *__restrict__ rows, int32_t *__restrict__ pos) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n) pos[rows[p]] = p;
+}
+
+// ---- factorisation --------------------------------------------------------------------
+
+constexpr int kLBatch = 8;
+
+// One row, one warp: lane l holds entry l of row i. The row's earlier
+// entries (position below pos[i]) are eliminated in position order: rows k
+// of up to kLBatch of them are staged in shared memory, l_ik = a_ik / u_kk
+// (as a product with the stored 1 / u_kk), then every later entry (i, j) that
+// row k also holds gets a_ij -= l_ik u_kj.
+template <typename TF>
+__device__ void lines_eliminate(int i, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                                const int32_t *__restrict__ pos, const int32_t *__restrict__ dpos, TF *__restrict__ lu,
+                                TF *__restrict__ rdiag, int *__restrict__ status, int32_t (*kc)[32], TF (*kv)[32]) {
+    const int lane = threadIdx.x & 31;
+    const int b = rowptr[i], len = rowptr[i + 1] - b;
+    if (len > 32) {
+        if (lane == 0) atomicCAS(status, 0, -(1 + i));
+        return;
+    }
+    const bool mine = lane < len;
+    const int j = mine ? colidx[b + lane] : -1;
+    const int pj = mine ? pos[j] : INT_MAX;
+    const int pi_ = pos[i];
+    TF a = mine ? lu[b + lane] : TF(0);
+    const bool lower = mine && pj < pi_;
+    int rank = 0;  // place of this lower entry in the position order
+    for (int o = 0; o < 32; ++o) {
+        const int po = __shfl_sync(0xffffffffu, pj, o);
+        const bool lo = __shfl_sync(0xffffffffu, lower, o);
+        rank += (lower && lo && po < pj) ? 1 : 0;
+    }
+    const int nlow = __popc(__ballot_sync(0xffffffffu, lower));
+    int kb = 0, kl = 0;
+    TF rd = TF(0);
+    if (lower) {
+        kb = rowptr[j];
+        kl = min(rowptr[j + 1] - kb, 32);
+        rd = rdiag[j];
+    }
+    for (int t0 = 0; t0 < nlow; t0 += kLBatch) {
+        const int nb = min(kLBatch, nlow - t0);
+        int qs[kLBatch];
+#pragma unroll
+        for (int u = 0; u < kLBatch; ++u) {
+            const unsigned bm = __ballot_sync(0xffffffffu, lower && rank == t0 + u);
+            qs[u] = bm ? __ffs(bm) - 1 : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < kLBatch; ++u) {
+            if (u < nb) {
+                const int ub = __shfl_sync(0xffffffffu, kb, qs[u]), ul = __shfl_sync(0xffffffffu, kl, qs[u]);
+                kc[u][lane] = lane < ul ? colidx[ub + lane] : INT_MAX;
+                kv[u][lane] = lane < ul ? lu[ub + lane] : TF(0);
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < kLBatch; ++u) {
+            if (u < nb) {
+                const int q = qs[u];
+                const TF lik = __shfl_sync(0xffffffffu, a, q) * __shfl_sync(0xffffffffu, rd, q);
+                const int pk = __shfl_sync(0xffffffffu, pj, q);
+                if (lane == q) a = lik;
+                const bool later = mine && pj > pk;
+                const int32_t *rk = kc[u];
+                int p = 0;
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1)
+                    if (rk[p + step - 1] < j) p += step;
+                if (later && rk[p] == j) a = a - lik * kv[u][p];
+            }
+        }
+        __syncwarp();  // the next batch overwrites the staged rows
+    }
+    if (mine) lu[b + lane] = a;
+    const int dq = dpos[i] - b;
+    const TF uii = __shfl_sync(0xffffffffu, a, dq);
+    if (lane == 0) {
+        if (uii == TF(0) || !isfinite((double)uii)) atomicCAS(status, 0, 1 + i);
+        rdiag[i] = TF(1) / uii;
+    }
+    __syncwarp();
+}
+
+// One colour: CTA b0 + blockIdx.x handles one block, warp q its line q; at
+// time step T warp q factors point x = T - 2 q of its line.
+template <typename TF>
+__global__ void __launch_bounds__(128) lines_factor_kernel(int b0, const int32_t *__restrict__ blk_start,
+                                                           const int32_t *__restrict__ blk_nsub, int nx,
+                                                           const int32_t *__restrict__ rows,
+                                                           const int32_t *__restrict__ rowptr,
+                                                           const int32_t *__restrict__ colidx,
+                                                           const int32_t *__restrict__ pos,
+                                                           const int32_t *__restrict__ dpos, TF *__restrict__ lu,
+                                                           TF *__restrict__ rdiag, int *__restrict__ status) {
+    __shared__ int32_t s_kc[4][kLBatch][32];
+    __shared__ TF s_kv[4][kLBatch][32];
+    const int b = b0 + blockIdx.x, q = threadIdx.x >> 5;
+    const int start = blk_start[b], nsub = blk_nsub[b];
+    const int steps = nx + 2 * (nsub - 1);
+    for (int T = 0; T < steps; ++T) {
+        const int x = T - 2 * q;
+        if (q < nsub && x >= 0 && x < nx)
+            lines_eliminate<TF>(rows[start + q * nx + x], rowptr, colidx, pos, dpos, lu, rdiag, status, s_kc[q],
+                                s_kv[q]);
+        __syncthreads();  // points of this step are final before the next step reads them
+    }
+}
+
+// ---- factors for the sweeps -------------------------------------------------------------
+//
+// Per position p (the order above): the earlier entries other than the line
+// predecessor (x-1, same line) in an ELL block of its colour (columns as
+// positions), lrec[p] = the entry towards the line predecessor (0 at x = 0);
+// the later entries other than the line successor likewise, urec[p] towards
+// (x+1, same line); udinv[p] = 1 / u_pp.
+
+__global__ void lines_width_kernel(int n, int nx, const int32_t *__restrict__ rowptr,
+                                   const int32_t *__restrict__ colidx, const int32_t *__restrict__ pos,
+                                   const int32_t *__restrict__ ccol, int *__restrict__ wl, int *__restrict__ wu) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int p = pos[i], x = i % nx;
+    int nl = 0, nu = 0;
+    for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+        const int k = colidx[e], pk = pos[k];
+        if (pk < p && !(k == i - 1 && x > 0)) ++nl;
+        if (pk > p && !(k == i + 1 && x < nx - 1)) ++nu;
+    }
+    const int c = ccol[i];
+    atomicMax(wl + c, nl);
+    atomicMax(wu + c, nu);
+}
+
+template <typename T>
+__global__ void lines_fill_kernel(int n, int nx, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                                  const T *__restrict__ lu, const int32_t *__restrict__ dpos,
+                                  const int32_t *__restrict__ pos, const int32_t *__restrict__ ccol, const IluLines L,
+                                  int32_t *__restrict__ lcol, T *__restrict__ lval, int32_t *__restrict__ ucol,
+                                  T *__restrict__ uval, T *__restrict__ lrec, T *__restrict__ urec,
+                                  T *__restrict__ udinv) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int c = ccol[i], p = pos[i], x = i % nx;
+    const int r = p - L.cptr[c], m = L.cptr[c + 1] - L.cptr[c];
+    const long lb = L.lbase[c], ub = L.ubase[c];
+    int nl = 0, nu = 0;
+    T lr = T(0), ur = T(0);
+    for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+        const int k = colidx[e], pk = pos[k];
+        if (pk < p) {
+            if (k == i - 1 && x > 0) {
+                lr = lu[e];
+            } else {
+                lcol[lb + (long)nl * m + r] = pk;
+                lval[lb + (long)nl * m + r] = lu[e];
+                ++nl;
+            }
+        } else if (pk > p) {
+            if (k == i + 1 && x < nx - 1) {
+                ur = lu[e];
+            } else {
+                ucol[ub + (long)nu * m + r] = pk;
+                uval[ub + (long)nu * m + r] = lu[e];
+                ++nu;
+            }
+        }
+    }
+    // padding: value 0 at the row's own position (read, multiplied by 0)
+    for (; nl < L.wl[c]; ++nl) {
+        lcol[lb + (long)nl * m + r] = p;
+        lval[lb + (long)nl * m + r] = T(0);
+    }
+    for (; nu < L.wu[c]; ++nu) {
+        ucol[ub + (long)nu * m + r] = p;
+        uval[ub + (long)nu * m + r] = T(0);
+    }
+    lrec[p] = lr;
+    urec[p] = ur;
+    udinv[p] = T(1) / lu[dpos[i]];
+}
+
+__global__ void lines_colour_of_kernel(int n, const int32_t *__restrict__ rows, const IluLines L,
+                                       int32_t *__restrict__ ccol) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    int c = 0;
+    while (c + 1 < L.ncol && p >= L.cptr[c + 1]) ++c;
+    ccol[rows[p]] = c;
+}
+
+// ---- sweeps ---------------------------------------------------------------------------------
+
+// one step of an affine warp scan: (A, B) represents y_out = A + B y_in; the
+// inclusive scan composes lane 0's map first
+template <typename T>
+__device__ __forceinline__ void affine_scan(T &A, T &B, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const T Ap = __shfl_up_sync(0xffffffffu, A, o), Bp = __shfl_up_sync(0xffffffffu, B, o);
+        if (lane >= o) {
+            A = fma(B, Ap, A);
+            B = B * Bp;
+        }
+    }
+}
+
+// Forward sweep of one line of a block (positions lp .. lp + nx - 1), in place
+// on y: y_x = (y_x - sum_par L y) - lrec_x y_{x-1}.
+template <typename T, int CPL>
+__device__ __forceinline__ void line_forward(int lp, int nx, int c0, int m, int w, const int32_t *__restrict__ lcol,
+                                             const T *__restrict__ lval, const T *__restrict__ lrec, T *y) {
+    const int lane = threadIdx.x & 31;
+    T s[CPL], l[CPL];
+#pragma unroll
+    for (int t = 0; t < CPL; ++t) {
+        const int x = t * 32 + lane;
+        if (x < nx) {
+            const int p = lp + x, r = p - c0;
+            T acc = T(0);
+            for (int j = 0; j < w; ++j) acc = fma(lval[(long)j * m + r], y[lcol[(long)j * m + r]], acc);
+            s[t] = y[p] - acc;
+            l[t] = lrec[p];
+        } else {
+            s[t] = T(0);
+            l[t] = T(-1);  // identity map past the end of the line
+        }
+    }
+    T carry = T(0);
+#pragma unroll
+    for (int t = 0; t < CPL; ++t) {
+        if (t * 32 >= nx) break;
+        T A = s[t], B = -l[t];
+        affine_scan(A, B, lane);
+        const T prev = __shfl_up_sync(0xffffffffu, fma(B, carry, A), 1);
+        const T yin = lane == 0 ? carry : prev;
+        const T yv = s[t] - l[t] * yin;
+        if (t * 32 + lane < nx) y[lp + t * 32 + lane] = yv;
+        carry = __shfl_sync(0xffffffffu, fma(B, carry, A), 31);
+    }
+    __syncwarp();
+}
+
+// Backward sweep of one line, in place on y (which holds the forward result):
+// e_x = udinv_x ((y_x - sum_par U e) - urec_x e_{x+1}); z[row] += e_x.
+template <typename T, typename TZ, int CPL>
+__device__ __forceinline__ void line_backward(int lp, int nx, int c0, int m, int w, const int32_t *__restrict__ ucol,
+                                              const T *__restrict__ uval, const T *__restrict__ urec,
+                                              const T *__restrict__ udinv, const int32_t *__restrict__ rows, T *y,
+                                              TZ *__restrict__ z) {
+    const int lane = threadIdx.x & 31;
+    T a[CPL], bb[CPL];
+#pragma unroll
+    for (int t = 0; t < CPL; ++t) {
+        const int k = t * 32 + lane, x = nx - 1 - k;  // chunks from the end of the line
+        if (k < nx) {
+            const int p = lp + x, r = p - c0;
+            T acc = T(0);
+            for (int j = 0; j < w; ++j) acc = fma(uval[(long)j * m + r], y[ucol[(long)j * m + r]], acc);
+            const T d = udinv[p];
+            a[t] = d * (y[p] - acc);
+            bb[t] = -d * urec[p];
+        } else {
+            a[t] = T(0);
+            bb[t] = T(1);
+        }
+    }
+    T carry = T(0);
+#pragma unroll
+    for (int t = 0; t < CPL; ++t) {
+        if (t * 32 >= nx) break;
+        T A = a[t], B = bb[t];
+        affine_scan(A, B, lane);
+        const T prev = __shfl_up_sync(0xffffffffu, fma(B, carry, A), 1);
+        const T zin = lane == 0 ? carry : prev;
+        const T ev = fma(bb[t], zin, a[t]);
+        const int k = t * 32 + lane;
+        if (k < nx) {
+            const int p = lp + nx - 1 - k;
+            y[p] = ev;
+            const int row = rows[p];
+            z[row] = TZ(z[row] + TZ(ev));
+        }
+        carry = __shfl_sync(0xffffffffu, fma(B, carry, A), 31);
+    }
+    __syncwarp();
+}
+
+// mode 0: forward over the block's lines; 1: backward; 2: forward then
+// backward (the last colour). One warp per block.
+template <typename T, typename TZ, int CPL>
+__global__ void __launch_bounds__(128) lines_sweep_kernel(int mode, int b0, int nblk,
+                                                          const int32_t *__restrict__ blk_start,
+                                                          const int32_t *__restrict__ blk_nsub, int nx, int c0, int m,
+                                                          int wl, const int32_t *__restrict__ lcol,
+                                                          const T *__restrict__ lval, const T *__restrict__ lrec,
+                                                          int wu, const int32_t *__restrict__ ucol,
+                                                          const T *__restrict__ uval, const T *__restrict__ urec,
+                                                          const T *__restrict__ udinv,
+                                                          const int32_t *__restrict__ rows, T *__restrict__ y,
+                                                          TZ *__restrict__ z) {
+    pdl_prologue();
+    const int wb = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (wb >= nblk) return;  // whole warps leave together
+    const int b = b0 + wb;
+    const int start = blk_start[b], nsub = blk_nsub[b];
+    if (mode != 1)
+        for (int q = 0; q < nsub; ++q) line_forward<T, CPL>(start + q * nx, nx, c0, m, wl, lcol, lval, lrec, y);
+    if (mode != 0)
+        for (int q = nsub - 1; q >= 0; --q)
+            line_backward<T, TZ, CPL>(start + q * nx, nx, c0, m, wu, ucol, uval, urec, udinv, rows, y, z);
+}
+
+// ---- host side ---------------------------------------------------------------------------------
+
+bool lines_fit(const msrsb_grid *g) { return g->nx >= 1 && g->nx <= 32 * kLinesMaxCpl && (g->dim == 2 || g->dim == 3); }
+
+// Order, block table and ILU(0) factors of a scalar operator in the
+// line-block order; lu holds A's values (TF) on entry and is overwritten.
+template <typename TF>
+msrsb_status lines_setup(msrsb_handle *h, TF *lu, cudaStream_t s) {
+    const msrsb_mat &A = h->A;
+    const msrsb_grid &g = h->grid;
+    const int n = h->n, dim = g.dim, nx = g.nx, ny = g.ny, nz = dim == 3 ? g.nz : 1;
+    IluLines &L = h->lines;
+    L.nx = nx;
+    L.ncol = dim == 3 ? 4 : 2;
+    // ---- the order: sort rows by (colour, block, line, x) ----
+    uint32_t *key = nullptr, *key2 = nullptr;
+    int32_t *idx = nullptr;
+    MSRSB_TRY(dalloc(&key, n, s));
+    MSRSB_TRY(dalloc(&key2, n, s));
+    MSRSB_TRY(dalloc(&idx, n, s));
+    MSRSB_TRY(dalloc(&L.rows, n, s));
+    MSRSB_TRY(dalloc(&h->pos_of, n, s));
+    line_key_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, dim, nx, ny, nz, key, idx);
+    MSRSB_LAUNCHED("line_key_kernel");
+    size_t tmp = 0;
+    MSRSB_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp, key, key2, idx, L.rows, n, 0, 32, s));
+    char *tb = nullptr;
+    MSRSB_TRY(dalloc(&tb, tmp, s));
+    MSRSB_CUDA(cub::DeviceRadixSort::SortPairs(tb, tmp, key, key2, idx, L.rows, n, 0, 32, s));
+    dfree(tb, s);
+    dfree(key, s);
+    dfree(key2, s);
+    dfree(idx, s);
+    lines_pos_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, L.rows, h->pos_of);
+    MSRSB_LAUNCHED("lines_pos_kernel");
+    // ---- block table (host): blocks of each colour in block order ----
+    const int nby = (ny + 1) / 2, nbz = dim == 3 ? (nz + 1) / 2 : 1;
+    std::vector<int32_t> bstart, bnsub;
+    int run = 0;
+    for (int c = 0; c < L.ncol; ++c) {
+        L.cptr[c] = run;
+        L.bptr[c] = (int)bstart.size();
+        for (int bz = 0; bz < nbz; ++bz)
+            for (int by = 0; by < nby; ++by) {
+                const int cc = (by & 1) | (dim == 3 ? ((bz & 1) << 1) : 0);
+                if (cc != c) continue;
+                const int sy = ny - 2 * by < 2 ? 1 : 2, sz = dim == 3 ? (nz - 2 * bz < 2 ? 1 : 2) : 1;
+                bstart.push_back(run);
+                bnsub.push_back(sy * sz);
+                run += sy * sz * nx;
+            }
+    }
+    L.cptr[L.ncol] = run;
+    L.bptr[L.ncol] = (int)bstart.size();
+    if (run != n) return fail(MSRSB_ESHAPE, "line blocks cover %d of %d rows", run, n);
+    const int nblk = (int)bstart.size();
+    MSRSB_TRY(dalloc(&L.blk_start, nblk, s));
+    MSRSB_TRY(dalloc(&L.blk_nsub, nblk, s));
+    MSRSB_CUDA(cudaMemcpyAsync(L.blk_start, bstart.data(), nblk * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    MSRSB_CUDA(cudaMemcpyAsync(L.blk_nsub, bnsub.data(), nblk * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    // ---- factorisation, colour by colour ----
+    int *status = nullptr;
+    TF *rdiag = nullptr;
+    int32_t *dpos = nullptr, *ccol = nullptr;
+    MSRSB_TRY(dalloc(&status, 1, s));
+    MSRSB_TRY(dalloc(&rdiag, n, s));
+    MSRSB_TRY(dalloc(&dpos, n, s));
+    MSRSB_TRY(dalloc(&ccol, n, s));
+    MSRSB_CUDA(cudaMemsetAsync(status, 0, sizeof(int), s));
+    diag_pos_launch(n, A.rowptr, A.colidx, dpos, status, s);
+    MSRSB_LAUNCHED("diag_pos_kernel");
+    for (int c = 0; c < L.ncol; ++c) {
+        const int nb = L.bptr[c + 1] - L.bptr[c];
+        if (!nb) continue;
+        lines_factor_kernel<TF><<<nb, 128, 0, s>>>(L.bptr[c], L.blk_start, L.blk_nsub, nx, L.rows, A.rowptr, A.colidx,
+                                                   h->pos_of, dpos, lu, rdiag, status);
+        MSRSB_LAUNCHED("lines_factor_kernel");
+    }
+    int hs = 0;
+    MSRSB_CUDA(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MSRSB_CUDA(cudaStreamSynchronize(s));
+    dfree(rdiag, s);
+    if (hs) {
+        dfree(status, s);
+        dfree(dpos, s);
+        dfree(ccol, s);
+        if (hs < 0) return fail(MSRSB_EINVAL, "ILU(0): row %d has more than 32 entries", -hs - 1);
+        return fail(MSRSB_EBREAKDOWN, "ILU(0): zero pivot at row %d", hs - 1);
+    }
+    // ---- per-colour ELL blocks of the parallel parts, line coefficients ----
+    lines_colour_of_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, L.rows, L, ccol);
+    MSRSB_LAUNCHED("lines_colour_of_kernel");
+    int *w = nullptr;
+    MSRSB_TRY(dalloc(&w, 8, s));
+    MSRSB_CUDA(cudaMemsetAsync(w, 0, 8 * sizeof(int), s));
+    lines_width_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, nx, A.rowptr, A.colidx, h->pos_of, ccol, w, w + 4);
+    MSRSB_LAUNCHED("lines_width_kernel");
+    int hw[8];
+    MSRSB_CUDA(cudaMemcpyAsync(hw, w, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    MSRSB_CUDA(cudaStreamSynchronize(s));
+    dfree(w, s);
+    long lt = 0, ut = 0;
+    for (int c = 0; c < L.ncol; ++c) {
+        L.wl[c] = hw[c];
+        L.wu[c] = hw[4 + c];
+        L.lbase[c] = lt;
+        L.ubase[c] = ut;
+        const long m = L.cptr[c + 1] - L.cptr[c];
+        lt += m * L.wl[c];
+        ut += m * L.wu[c];
+    }
+    TF *lval = nullptr, *uval = nullptr, *lrec = nullptr, *urec = nullptr, *udinv = nullptr;
+    MSRSB_TRY(dalloc(&L.lcol, lt, s));
+    MSRSB_TRY(dalloc(&L.ucol, ut, s));
+    MSRSB_TRY(dalloc(&lval, lt, s));
+    MSRSB_TRY(dalloc(&uval, ut, s));
+    MSRSB_TRY(dalloc(&lrec, n, s));
+    MSRSB_TRY(dalloc(&urec, n, s));
+    MSRSB_TRY(dalloc(&udinv, n, s));
+    L.lval = lval;
+    L.uval = uval;
+    L.lrec = lrec;
+    L.urec = urec;
+    L.udinv = udinv;
+    lines_fill_kernel<TF><<<ceil_div(n, 256), 256, 0, s>>>(n, nx, A.rowptr, A.colidx, lu, dpos, h->pos_of, ccol, L,
+                                                           L.lcol, lval, L.ucol, uval, lrec, urec, udinv);
+    MSRSB_LAUNCHED("lines_fill_kernel");
+    dfree(status, s);
+    dfree(dpos, s);
+    dfree(ccol, s);
+    return MSRSB_OK;
+}
+template msrsb_status lines_setup<double>(msrsb_handle *, double *, cudaStream_t);
+template msrsb_status lines_setup<float>(msrsb_handle *, float *, cudaStream_t);
+
+template <typename T, typename TZ, int CPL>
+static msrsb_status lines_apply_t(const msrsb_handle *h, T *ry, TZ *z, cudaStream_t s) {
+    const IluLines &L = h->lines;
+    const int last = L.ncol - 1;
+    auto launch = [&](int mode, int c) -> msrsb_status {
+        const int nb = L.bptr[c + 1] - L.bptr[c];
+        if (!nb) return MSRSB_OK;
+        const int m = L.cptr[c + 1] - L.cptr[c];
+        MSRSB_PDL((lines_sweep_kernel<T, TZ, CPL>), ceil_div((long)nb * 32, 128), 128, 0, s, mode, L.bptr[c], nb,
+                  L.blk_start, L.blk_nsub, L.nx, L.cptr[c], m, L.wl[c], L.lcol + L.lbase[c],
+                  (const T *)L.lval + L.lbase[c], (const T *)L.lrec, L.wu[c], L.ucol + L.ubase[c],
+                  (const T *)L.uval + L.ubase[c], (const T *)L.urec, (const T *)L.udinv, L.rows, ry, z);
+        return MSRSB_OK;
+    };
+    for (int c = 0; c < last; ++c) MSRSB_TRY(launch(0, c));
+    MSRSB_TRY(launch(2, last));
+    for (int c = last - 1; c >= 0; --c) MSRSB_TRY(launch(1, c));
+    return MSRSB_OK;
+}
+
+// z += U^-1 L^-1 r with r given in the line-block order in ry (overwritten):
+// 2 C - 1 launches for C colours
+template <typename T, typename TZ>
+msrsb_status lines_apply(const msrsb_handle *h, T *ry, TZ *z, cudaStream_t s) {
+    const int nx = h->lines.nx;
+    if (nx <= 32) return lines_apply_t<T, TZ, 1>(h, ry, z, s);
+    if (nx <= 64) return lines_apply_t<T, TZ, 2>(h, ry, z, s);
+    if (nx <= 128) return lines_apply_t<T, TZ, 4>(h, ry, z, s);
+    return lines_apply_t<T, TZ, 8>(h, ry, z, s);
+}
+template msrsb_status lines_apply<double, double>(const msrsb_handle *, double *, double *, cudaStream_t);
+template msrsb_status lines_apply<float, double>(const msrsb_handle *, float *, double *, cudaStream_t);
+template msrsb_status lines_apply<float, float>(const msrsb_handle *, float *, float *, cudaStream_t);
+
+void lines_free(IluLines *L, cudaStream_t s) {
+    dfree(L->rows, s);
+    dfree(L->blk_start, s);
+    dfree(L->blk_nsub, s);
+    dfree(L->lcol, s);
+    dfree(L->ucol, s);
+    dfree(L->lval, s);
+    dfree(L->uval, s);
+    dfree(L->lrec, s);
+    dfree(L->urec, s);
+    dfree(L->udinv, s);
+}
+
+}  // namespace msrsb

@@ -72,6 +72,10 @@ __global__ void diag_pos_kernel(int n, const int32_t *__restrict__ rowptr, const
     if (p < 0) atomicCAS(status, 0, 1 + i);
 }
 
+void diag_pos_launch(int n, const int32_t *rowptr, const int32_t *colidx, int32_t *dpos, int *status, cudaStream_t s) {
+    diag_pos_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, rowptr, colidx, dpos, status);
+}
+
 __device__ __forceinline__ int find_col(const int32_t *__restrict__ colidx, int lo, int hi, int j) {
     while (lo < hi) {
         int mid = (lo + hi) >> 1;

@@ -19,6 +19,7 @@ MSRSB_F64, MSRSB_F32 = 0, 1
 MSRSB_SMOOTH_NONE, MSRSB_SMOOTH_ILU0, MSRSB_SMOOTH_GS, MSRSB_SMOOTH_L1JAC, MSRSB_SMOOTH_IC0 = 0, 1, 2, 3, 4
 MSRSB_GMRES, MSRSB_PCG, MSRSB_RICHARDSON = 0, 1, 2
 MSRSB_RESTRICT_GALERKIN, MSRSB_RESTRICT_FV = 0, 1
+MSRSB_ORDER_LINES, MSRSB_ORDER_PARITY = 0, 1
 
 EXPORTS = ["msrsb_partition_size", "msrsb_partition", "msrsb_filter", "msrsb_build_basis", "msrsb_coarse_op",
            "msrsb_setup", "msrsb_apply", "msrsb_solve", "msrsb_get_setup", "msrsb_get_info", "msrsb_destroy",
@@ -49,7 +50,8 @@ class c_basis_opts(ctypes.Structure):
 class c_opts(ctypes.Structure):
     _fields_ = [("basis", c_basis_opts), ("smoother", ctypes.c_int32), ("pre", ctypes.c_int32),
                 ("post", ctypes.c_int32), ("krylov", ctypes.c_int32), ("restart", ctypes.c_int32),
-                ("prec", ctypes.c_int32), ("no_coarse", ctypes.c_int32), ("restriction", ctypes.c_int32)]
+                ("prec", ctypes.c_int32), ("no_coarse", ctypes.c_int32), ("restriction", ctypes.c_int32),
+                ("ordering", ctypes.c_int32)]
 
 
 class c_info(ctypes.Structure):
@@ -133,9 +135,10 @@ def basis_opts(omega=2.0 / 3.0, tol=1e-3, n_it=10, max_iter=100):
 
 
 def opts(omega=2.0 / 3.0, tol=1e-3, n_it=10, max_iter=100, smoother=MSRSB_SMOOTH_ILU0, pre=0, post=1,
-         krylov=MSRSB_GMRES, restart=200, prec=MSRSB_F64, no_coarse=0, restriction=MSRSB_RESTRICT_GALERKIN):
+         krylov=MSRSB_GMRES, restart=200, prec=MSRSB_F64, no_coarse=0, restriction=MSRSB_RESTRICT_GALERKIN,
+         ordering=MSRSB_ORDER_LINES):
     return c_opts(basis_opts(omega, tol, n_it, max_iter), smoother, pre, post, krylov, restart, prec, no_coarse,
-                  restriction)
+                  restriction, ordering)
 
 
 def _pdtype(prec):
