@@ -320,6 +320,32 @@ msrsb_status msrsb_transpose_values(const msrsb_mat *A, double *val_t, cudaStrea
 msrsb_status msrsb_pattern_outer(const msrsb_mat *A, double alpha, const double *lam, const double *x, double *grad,
                                  cudaStream_t stream);
 
+/* MPFA-O Darcy operator of a 3D grid of unit cells and its adjoint
+ * derivative (the paper has no adjoint; this differentiates the forward model
+ * that the preconditioner serves). Cell tensors K_c = exp(theta_c) K_hat_c,
+ * K_hat [n][9] row-major 3x3, theta [n], cells x fastest; MPFA-O with the
+ * continuity points at the half-face midpoints (the O-method on unit cells),
+ * no-flow outer faces, bottom-hole-pressure wells at the cells
+ * well_cells_h[w] (host) with pressures well_pw_h[w]: A_ii += WI_i,
+ * b_i = WI_i p_w, WI_i the MPFA-O diagonal A_ii. g must be 3D, cell-centred,
+ * ncomp 1.
+ * msrsb_mpfa_assemble: val (device, nnz) in the caller's CSR pattern
+ * rowptr/colidx, which must be each cell's in-grid 3x3x3 neighbours in
+ * ascending order; b (device, n). Interaction regions are solved in FP64,
+ * rows gathered in a fixed order (deterministic). Synchronises the stream.
+ * msrsb_mpfa_gradient: grad (device, n) = -lambda^T (dA/dtheta_c) p +
+ * lambda^T (db/dtheta_c) for every cell c, i.e. dJ/dtheta when A p = b and
+ * A^T lambda = dJ/dp (lambda, p device vectors). Per interaction region the
+ * local system C u = D p and its adjoint C^T mu = G^T w are solved (w the
+ * differences of lambda across the half-faces) and each cell's share is
+ * gathered in a fixed order. */
+msrsb_status msrsb_mpfa_assemble(const msrsb_grid *g, const double *K_hat, const double *theta, int32_t nwells,
+                                 const int32_t *well_cells_h, const double *well_pw_h, const int32_t *rowptr,
+                                 const int32_t *colidx, double *val, double *b, cudaStream_t stream);
+msrsb_status msrsb_mpfa_gradient(const msrsb_grid *g, const double *K_hat, const double *theta, int32_t nwells,
+                                 const int32_t *well_cells_h, const double *well_pw_h, const double *lam,
+                                 const double *p, double *grad, cudaStream_t stream);
+
 /* Measurement support (no counterpart in the paper). msrsb_profile(1)
  * resets the counters and brackets every Alg. 1 loop (the restricted-smoothing
  * passes of one basis family) with one pair of CUDA events on its stream, so

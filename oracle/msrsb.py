@@ -781,3 +781,142 @@ def tpfa_objective_gradient(dims, logk, obs, p_obs):
     np.add.at(grad, west, 2.0 * k[west] * lam[west] * (1.0 - p[west]))
     np.add.at(grad, east, -2.0 * k[east] * lam[east] * p[east])
     return J, grad, p
+
+
+# ----------------------------------------------------------------------------
+# adjoint gradient through MPFA-O (3D, unit cells): dJ/d ln k per cell
+# ----------------------------------------------------------------------------
+
+
+def mpfa_region_parts(K, dims):
+    """The interaction regions of MPFA-O (continuity points at the half-face
+    midpoints) on a 3D grid of unit cells with no-flow outer faces, split by
+    cell: for every grid vertex (C order over the (nx+1, ny+1, nz+1) vertex
+    grid) and each of its 8 cell slots s (offset o in {0,1}^3, cell = vertex -
+    1 + o), the K-dependent parts C_s, D_s, G_s, H_s of the local system
+    C u = D p, half-face fluxes F = G u + H p (C also has a constant identity
+    part on half-faces with no cell). Half-face f (axis a, minus slot, plus
+    slot) carries the flux from its minus cell to its plus cell. Per cell s,
+    the linear reconstruction through the cell pressure and the potentials u
+    at the midpoints of its 3 half-faces gives the flux across its half-face
+    normal to axis a: sum_b U[a, b] (u_b - p_s), U = -2 (1/4) K_s sign_b.
+    Returns dict(C0, Cs, Ds, Gs, Hs, cells, present, faces)."""
+    d = 3
+    nv = tuple(s + 1 for s in dims)
+    nvert = int(np.prod(nv))
+    offs = [(i, j, k) for i in (0, 1) for j in (0, 1) for k in (0, 1)]
+    loc = {o: s for s, o in enumerate(offs)}
+    faces = []
+    for a in range(d):
+        for q0 in (0, 1):
+            for q1 in (0, 1):
+                q = [q0, q1]
+                om = tuple(q[:a] + [0] + q[a:])
+                op = tuple(q[:a] + [1] + q[a:])
+                faces.append((a, loc[om], loc[op]))
+    fof = {}  # (slot, axis) -> half-face
+    for f, (a, sm, sp_) in enumerate(faces):
+        fof[(sm, a)] = f
+        fof[(sp_, a)] = f
+    V = np.indices(nv).reshape(d, -1)
+    cells = np.zeros((nvert, 8), dtype=np.int64)
+    present = np.zeros((nvert, 8), dtype=bool)
+    Kc = np.zeros((nvert, 8, 3, 3))
+    for s, o in enumerate(offs):
+        cc = [V[a] - 1 + o[a] for a in range(d)]
+        ok = np.ones(nvert, dtype=bool)
+        for a in range(d):
+            ok &= (cc[a] >= 0) & (cc[a] < dims[a])
+        present[:, s] = ok
+        ci = [np.clip(cc[a], 0, dims[a] - 1) for a in range(d)]
+        cells[:, s] = ci[0] + dims[0] * (ci[1] + dims[1] * ci[2])
+        Kc[:, s] = K[ci[0], ci[1], ci[2]] * ok[:, None, None]
+    sign = np.array([[1.0 if o[b] == 0 else -1.0 for b in range(d)] for o in offs])
+    U = -2.0 * 0.25 * Kc * sign[None, :, None, :]  # (nvert, slot, a, b)
+    nf = 12
+    C0 = np.zeros((nvert, nf, nf))
+    Cs = np.zeros((8, nvert, nf, nf))
+    Ds = np.zeros((8, nvert, nf, 8))
+    Gs = np.zeros((8, nvert, nf, nf))
+    Hs = np.zeros((8, nvert, nf, 8))
+    for f, (a, sm, sp_) in enumerate(faces):
+        pm, pp = present[:, sm], present[:, sp_]
+        both = pm & pp
+        only_m, only_p = pm & ~pp, pp & ~pm
+        # continuity F_m = F_p, or no flow F = 0 from the one present cell
+        use_m = both | only_m
+        for b in range(d):
+            Cs[sm, :, f, fof[(sm, b)]] += use_m * U[:, sm, a, b]
+            Cs[sp_, :, f, fof[(sp_, b)]] -= both * U[:, sp_, a, b]
+            Cs[sp_, :, f, fof[(sp_, b)]] += only_p * U[:, sp_, a, b]
+        Ds[sm, :, f, sm] += use_m * U[:, sm, a, :].sum(axis=1)
+        Ds[sp_, :, f, sp_] -= both * U[:, sp_, a, :].sum(axis=1)
+        Ds[sp_, :, f, sp_] += only_p * U[:, sp_, a, :].sum(axis=1)
+        C0[:, f, f] += ~(pm | pp)
+        # the half-face flux, from the minus cell if present
+        gm, gp = pm, ~pm & pp
+        for b in range(d):
+            Gs[sm, :, f, fof[(sm, b)]] += gm * U[:, sm, a, b]
+            Gs[sp_, :, f, fof[(sp_, b)]] += gp * U[:, sp_, a, b]
+        Hs[sm, :, f, sm] -= gm * U[:, sm, a, :].sum(axis=1)
+        Hs[sp_, :, f, sp_] -= gp * U[:, sp_, a, :].sum(axis=1)
+    return dict(C0=C0, Cs=Cs, Ds=Ds, Gs=Gs, Hs=Hs, cells=cells, present=present, faces=faces)
+
+
+def mpfa_lam_dA_p(parts, lam, p):
+    """g_c = lam^T (dA/d ln k_c) p for the MPFA-O matrix of a grid of unit
+    cells with no-flow outer faces (K_c = k_c K_hat_c, so dK_c/d ln k_c = K_c
+    and each local matrix's cell-c part is its derivative). Per interaction
+    region: u = C^-1 D p, w_f = lam(minus cell) - lam(plus cell) on half-faces
+    between two cells (no-flow half-faces carry no flux), mu = C^-T G^T w, and
+    the region adds w^T (G_c u + H_c p) + mu^T (D_c p - C_c u) to cell c."""
+    C = parts["C0"] + parts["Cs"].sum(axis=0)
+    D = parts["Ds"].sum(axis=0)
+    G = parts["Gs"].sum(axis=0)
+    cells, present = parts["cells"], parts["present"]
+    pl = np.where(present, p[cells], 0.0)
+    ll = np.where(present, lam[cells], 0.0)
+    w = np.zeros((cells.shape[0], 12))
+    for f, (a, sm, sp_) in enumerate(parts["faces"]):
+        both = present[:, sm] & present[:, sp_]
+        w[:, f] = both * (ll[:, sm] - ll[:, sp_])
+    u = np.linalg.solve(C, np.einsum("vfc,vc->vf", D, pl)[..., None])[..., 0]
+    Gtw = np.einsum("vgf,vg->vf", G, w)
+    mu = np.linalg.solve(np.transpose(C, (0, 2, 1)), Gtw[..., None])[..., 0]
+    g = np.zeros(len(p))
+    for s in range(8):
+        t = (np.einsum("vf,vfg,vg->v", w, parts["Gs"][s], u) + np.einsum("vf,vfc,vc->v", w, parts["Hs"][s], pl)
+             + np.einsum("vf,vfc,vc->v", mu, parts["Ds"][s], pl) - np.einsum("vf,vfg,vg->v", mu, parts["Cs"][s], u))
+        np.add.at(g, cells[present[:, s], s], t[present[:, s]])
+    return g
+
+
+def mpfa_objective_gradient(K_hat, logk, wells, obs, p_obs, A=None, b=None):
+    """J(theta) = sum_o (p[obs_o] - p_obs_o)^2 for MPFA-O Darcy flow on unit
+    cells with K_c = exp(theta_c) K_hat_c, no-flow outer faces and
+    bottom-hole-pressure wells (A_ii += WI_i, b_i = WI_i p_w, WI_i = the MPFA-O
+    diagonal A_ii), and dJ/dtheta by the adjoint method: A p = b,
+    A^T lambda = dJ/dp = 2 (p - p_obs) on the observation cells, and
+    dJ/dtheta_c = -lambda^T (dA/dtheta_c) p + lambda^T db/dtheta_c, where the
+    wells add -lambda_i (p_i - p_w) dA_ii/dtheta_c. A, b (optional) are the
+    assembled system at theta (scipy CSR, vector). Direct sparse solves in
+    FP64. Returns (J, grad, p)."""
+    dims = K_hat.shape[:3]
+    K = np.exp(np.asarray(logk)).reshape(dims, order="F")[..., None, None] * K_hat
+    parts = mpfa_region_parts(K, dims)
+    if A is None:
+        raise ValueError("pass the assembled system (A, b)")
+    A = sp.csr_matrix(A)
+    p = spla.spsolve(A.tocsc(), b)
+    r = p[obs] - p_obs
+    J = float(r @ r)
+    gp = np.zeros(len(p))
+    np.add.at(gp, obs, 2.0 * r)
+    lam = spla.spsolve(A.T.tocsc(), gp)
+    grad = -mpfa_lam_dA_p(parts, lam, p)
+    n = len(p)
+    for cell, pw in wells:
+        e = np.zeros(n)
+        e[cell] = 1.0
+        grad -= lam[cell] * (p[cell] - pw) * mpfa_lam_dA_p(parts, e, e)
+    return J, grad, p

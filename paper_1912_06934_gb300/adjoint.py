@@ -11,6 +11,12 @@ dJ/dA = -lambda x^T on the pattern (msrsb_pattern_outer). Every step of the
 solves and of the gradient runs in the library's kernels; torch only chains
 them with the forward model.
 
+MsrsbMpfaSolve is the same for the MPFA-O Darcy model of the 27-point
+workloads (3D unit cells, K_c = exp(theta_c) K_hat_c, no-flow outer faces,
+bottom-hole-pressure wells): p = A(theta)^-1 b(theta), assembled on the GPU
+(msrsb_mpfa_assemble), with dJ/dtheta = -lambda^T (dA/dtheta) p + lambda^T
+(db/dtheta) from the interaction regions' local systems (msrsb_mpfa_gradient).
+
 tpfa_darcy builds A(log k) and b(log k) of a two-point flux discretisation on
 a Cartesian grid of unit cells (isotropic k, harmonic-mean face
 transmissibilities, p = 1 on the x = 0 face and p = 0 on the x = nx face, no
@@ -20,7 +26,8 @@ dJ/db back to dJ/d log k.
 import numpy as np
 import torch
 
-from .msrsb import Mat, msrsb_pattern_outer, msrsb_setup, msrsb_transpose_values
+from .msrsb import (Mat, msrsb_mpfa_assemble, msrsb_mpfa_gradient, msrsb_pattern_outer, msrsb_setup,
+                    msrsb_transpose_values)
 
 
 class MsrsbSolve(torch.autograd.Function):
@@ -51,6 +58,42 @@ class MsrsbSolve(torch.autograd.Function):
         gvals = msrsb_pattern_outer(A, -1.0, lam, x) if ctx.needs_input_grad[0] else None
         gb = lam if ctx.needs_input_grad[1] else None
         return gvals, gb, None, None, None, None
+
+
+class MsrsbMpfaSolve(torch.autograd.Function):
+    """p = A(theta)^-1 b(theta) for the MPFA-O model. Inputs: theta (CUDA
+    FP64, n), model = (grid, K_hat (n, 3, 3) CUDA FP64, wells [(cell, p_w)],
+    rowptr, colidx of the 27-point pattern), o (msrsb_opts), rtol, maxit."""
+
+    @staticmethod
+    def forward(ctx, theta, model, o, rtol, maxit):
+        g, K_hat, wells, rowptr, colidx = model
+        th = theta.detach().contiguous()
+        val, b = msrsb_mpfa_assemble(g, K_hat, th, wells, rowptr, colidx)
+        A = Mat(rowptr, colidx, val)
+        h = msrsb_setup(A, g, o)
+        p = h.solve(b, rtol=rtol, maxit=maxit)["x"]
+        h.destroy()
+        ctx.save_for_backward(th, val, p)
+        ctx.meta = (model, o, rtol, maxit)
+        return p
+
+    @staticmethod
+    def backward(ctx, gp):
+        th, val, p = ctx.saved_tensors
+        (g, K_hat, wells, rowptr, colidx), o, rtol, maxit = ctx.meta
+        A = Mat(rowptr, colidx, val)
+        At = Mat(rowptr, colidx, msrsb_transpose_values(A))
+        h = msrsb_setup(At, g, o)
+        lam = h.solve(gp.contiguous(), rtol=rtol, maxit=maxit)["x"]
+        h.destroy()
+        return msrsb_mpfa_gradient(g, K_hat, th, wells, lam, p), None, None, None, None
+
+
+def msrsb_mpfa_solve_diff(theta, model, o, rtol=1e-10, maxit=500):
+    """Differentiable p = A(theta)^-1 b(theta) of the MPFA-O model (see
+    MsrsbMpfaSolve)."""
+    return MsrsbMpfaSolve.apply(theta, model, o, rtol, maxit)
 
 
 def msrsb_solve_diff(vals, b, pattern, o, rtol=1e-10, maxit=500):

@@ -330,6 +330,14 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
         }
         ~Release() { (*this)(nullptr); }
     } release{go};
+    // The line-block ILU(0) factorisation is latency-bound (one CTA per line
+    // block, a wavefront of dependent rows), so it overlaps the basis build
+    // without competing for bandwidth: release it at once.
+    if (h->opts.smoother == MSRSB_SMOOTH_ILU0 && bd == 1 && h->opts.ordering == MSRSB_ORDER_LINES &&
+        lines_fit(&h->grid)) {
+        MSRSB_CUDA(cudaEventRecord(go_ev, s));
+        release(go_ev);
+    }
     // filtered operator(s) streamed as sliced ELL, then Alg. 1 per component
     T *P = nullptr;
     MSRSB_TRY(dalloc(&P, nW * bd, s));

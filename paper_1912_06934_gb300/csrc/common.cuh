@@ -165,11 +165,14 @@ struct IluLines {
     int nx = 0, ncol = 0;
     int cptr[5] = {0};  // first position of each colour (+ end)
     int bptr[5] = {0};  // first block of each colour (+ end)
-    int wl[4] = {0}, wu[4] = {0};
-    long lbase[4] = {0}, ubase[4] = {0};
+    int wl[4] = {0}, wu[4] = {0};    // off-block entries per point, per colour
+    int wli[4] = {0}, wui[4] = {0};  // in-block entries (the block's other lines) per point
+    long lbase[4] = {0}, ubase[4] = {0}, libase[4] = {0}, uibase[4] = {0};
     int32_t *rows = nullptr, *blk_start = nullptr, *blk_nsub = nullptr;
-    int32_t *lcol = nullptr, *ucol = nullptr;
-    void *lval = nullptr, *uval = nullptr, *lrec = nullptr, *urec = nullptr, *udinv = nullptr;
+    int32_t *lcol = nullptr, *ucol = nullptr;  // off-block columns (positions)
+    int16_t *lidx = nullptr, *uidx = nullptr;  // in-block entries: index inside the block
+    void *lval = nullptr, *uval = nullptr, *lvin = nullptr, *uvin = nullptr;
+    void *lrec = nullptr, *urec = nullptr, *udinv = nullptr;
 };
 
 // ---- device helpers -------------------------------------------------------

@@ -159,71 +159,108 @@ __global__ void __launch_bounds__(128) lines_factor_kernel(int b0, const int32_t
 
 // ---- factors for the sweeps -------------------------------------------------------------
 //
-// Per position p (the order above): the earlier entries other than the line
-// predecessor (x-1, same line) in an ELL block of its colour (columns as
-// positions), lrec[p] = the entry towards the line predecessor (0 at x = 0);
-// the later entries other than the line successor likewise, urec[p] towards
-// (x+1, same line); udinv[p] = 1 / u_pp.
+// Per position p (the order above) the earlier entries split three ways: the
+// line predecessor (x-1, same line): lrec[p]; entries of the block's earlier
+// lines: an in-block ELL block of its colour (index of the column inside the
+// block, value); all others (earlier colours): an off-block ELL block
+// (columns as positions). The later entries likewise (urec towards
+// (x+1, same line)); udinv[p] = 1 / u_pp.
 
-__global__ void lines_width_kernel(int n, int nx, const int32_t *__restrict__ rowptr,
+// first position of the block of row i and whether row k is in that block
+__device__ __forceinline__ bool same_block(int i, int k, int nx, int ny) {
+    const int yi = (i / nx) % ny, zi = i / (nx * ny), yk = (k / nx) % ny, zk = k / (nx * ny);
+    return (yi >> 1) == (yk >> 1) && (zi >> 1) == (zk >> 1);
+}
+__device__ __forceinline__ int block_first_row(int i, int nx, int ny) {
+    const int y = (i / nx) % ny, z = i / (nx * ny);
+    return nx * ((y & ~1) + ny * (z & ~1));
+}
+
+__global__ void lines_width_kernel(int n, int nx, int ny, const int32_t *__restrict__ rowptr,
                                    const int32_t *__restrict__ colidx, const int32_t *__restrict__ pos,
-                                   const int32_t *__restrict__ ccol, int *__restrict__ wl, int *__restrict__ wu) {
+                                   const int32_t *__restrict__ ccol, int *__restrict__ w) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int p = pos[i], x = i % nx;
-    int nl = 0, nu = 0;
+    int nl = 0, nu = 0, nli = 0, nui = 0;
     for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
         const int k = colidx[e], pk = pos[k];
-        if (pk < p && !(k == i - 1 && x > 0)) ++nl;
-        if (pk > p && !(k == i + 1 && x < nx - 1)) ++nu;
+        if (pk < p && !(k == i - 1 && x > 0)) {
+            if (same_block(i, k, nx, ny)) ++nli;
+            else ++nl;
+        }
+        if (pk > p && !(k == i + 1 && x < nx - 1)) {
+            if (same_block(i, k, nx, ny)) ++nui;
+            else ++nu;
+        }
     }
     const int c = ccol[i];
-    atomicMax(wl + c, nl);
-    atomicMax(wu + c, nu);
+    atomicMax(w + c, nl);
+    atomicMax(w + 4 + c, nu);
+    atomicMax(w + 8 + c, nli);
+    atomicMax(w + 12 + c, nui);
 }
 
 template <typename T>
-__global__ void lines_fill_kernel(int n, int nx, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
-                                  const T *__restrict__ lu, const int32_t *__restrict__ dpos,
-                                  const int32_t *__restrict__ pos, const int32_t *__restrict__ ccol, const IluLines L,
-                                  int32_t *__restrict__ lcol, T *__restrict__ lval, int32_t *__restrict__ ucol,
-                                  T *__restrict__ uval, T *__restrict__ lrec, T *__restrict__ urec,
-                                  T *__restrict__ udinv) {
+__global__ void lines_fill_kernel(int n, int nx, int ny, const int32_t *__restrict__ rowptr,
+                                  const int32_t *__restrict__ colidx, const T *__restrict__ lu,
+                                  const int32_t *__restrict__ dpos, const int32_t *__restrict__ pos,
+                                  const int32_t *__restrict__ ccol, const IluLines L, T *__restrict__ lval,
+                                  T *__restrict__ uval, T *__restrict__ lvin, T *__restrict__ uvin,
+                                  T *__restrict__ lrec, T *__restrict__ urec, T *__restrict__ udinv) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int c = ccol[i], p = pos[i], x = i % nx;
     const int r = p - L.cptr[c], m = L.cptr[c + 1] - L.cptr[c];
-    const long lb = L.lbase[c], ub = L.ubase[c];
-    int nl = 0, nu = 0;
+    const int bst = pos[block_first_row(i, nx, ny)];
+    const long lb = L.lbase[c], ub = L.ubase[c], lib = L.libase[c], uib = L.uibase[c];
+    int nl = 0, nu = 0, nli = 0, nui = 0;
     T lr = T(0), ur = T(0);
     for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
         const int k = colidx[e], pk = pos[k];
+        const bool inb = same_block(i, k, nx, ny);
         if (pk < p) {
             if (k == i - 1 && x > 0) {
                 lr = lu[e];
+            } else if (inb) {
+                L.lidx[lib + (long)nli * m + r] = (int16_t)(pk - bst);
+                lvin[lib + (long)nli * m + r] = lu[e];
+                ++nli;
             } else {
-                lcol[lb + (long)nl * m + r] = pk;
+                L.lcol[lb + (long)nl * m + r] = pk;
                 lval[lb + (long)nl * m + r] = lu[e];
                 ++nl;
             }
         } else if (pk > p) {
             if (k == i + 1 && x < nx - 1) {
                 ur = lu[e];
+            } else if (inb) {
+                L.uidx[uib + (long)nui * m + r] = (int16_t)(pk - bst);
+                uvin[uib + (long)nui * m + r] = lu[e];
+                ++nui;
             } else {
-                ucol[ub + (long)nu * m + r] = pk;
+                L.ucol[ub + (long)nu * m + r] = pk;
                 uval[ub + (long)nu * m + r] = lu[e];
                 ++nu;
             }
         }
     }
-    // padding: value 0 at the row's own position (read, multiplied by 0)
+    // padding: value 0 at the point itself (read, multiplied by 0)
     for (; nl < L.wl[c]; ++nl) {
-        lcol[lb + (long)nl * m + r] = p;
+        L.lcol[lb + (long)nl * m + r] = p;
         lval[lb + (long)nl * m + r] = T(0);
     }
     for (; nu < L.wu[c]; ++nu) {
-        ucol[ub + (long)nu * m + r] = p;
+        L.ucol[ub + (long)nu * m + r] = p;
         uval[ub + (long)nu * m + r] = T(0);
+    }
+    for (; nli < L.wli[c]; ++nli) {
+        L.lidx[lib + (long)nli * m + r] = (int16_t)(p - bst);
+        lvin[lib + (long)nli * m + r] = T(0);
+    }
+    for (; nui < L.wui[c]; ++nui) {
+        L.uidx[uib + (long)nui * m + r] = (int16_t)(p - bst);
+        uvin[uib + (long)nui * m + r] = T(0);
     }
     lrec[p] = lr;
     urec[p] = ur;
@@ -255,110 +292,134 @@ __device__ __forceinline__ void affine_scan(T &A, T &B, int lane) {
     }
 }
 
-// Forward sweep of one line of a block (positions lp .. lp + nx - 1), in place
-// on y: y_x = (y_x - sum_par L y) - lrec_x y_{x-1}.
+// Chunked recurrence over one line held in shared memory: v_x = a_x + b_x v_{x-1}
+// (k = 0, 1, ... in processing order); a, b per chunk in registers; the
+// result overwrites sm[idx(k)].
 template <typename T, int CPL>
-__device__ __forceinline__ void line_forward(int lp, int nx, int c0, int m, int w, const int32_t *__restrict__ lcol,
-                                             const T *__restrict__ lval, const T *__restrict__ lrec, T *y) {
-    const int lane = threadIdx.x & 31;
-    T s[CPL], l[CPL];
-#pragma unroll
-    for (int t = 0; t < CPL; ++t) {
-        const int x = t * 32 + lane;
-        if (x < nx) {
-            const int p = lp + x, r = p - c0;
-            T acc = T(0);
-            for (int j = 0; j < w; ++j) acc = fma(lval[(long)j * m + r], y[lcol[(long)j * m + r]], acc);
-            s[t] = y[p] - acc;
-            l[t] = lrec[p];
-        } else {
-            s[t] = T(0);
-            l[t] = T(-1);  // identity map past the end of the line
-        }
-    }
+__device__ __forceinline__ void line_scan(const T (&a)[CPL], const T (&b)[CPL], int nx, int lane, T (&out)[CPL]) {
     T carry = T(0);
 #pragma unroll
     for (int t = 0; t < CPL; ++t) {
         if (t * 32 >= nx) break;
-        T A = s[t], B = -l[t];
+        T A = a[t], B = b[t];
         affine_scan(A, B, lane);
         const T prev = __shfl_up_sync(0xffffffffu, fma(B, carry, A), 1);
-        const T yin = lane == 0 ? carry : prev;
-        const T yv = s[t] - l[t] * yin;
-        if (t * 32 + lane < nx) y[lp + t * 32 + lane] = yv;
+        const T vin = lane == 0 ? carry : prev;
+        out[t] = fma(b[t], vin, a[t]);
         carry = __shfl_sync(0xffffffffu, fma(B, carry, A), 31);
     }
-    __syncwarp();
 }
 
-// Backward sweep of one line, in place on y (which holds the forward result):
-// e_x = udinv_x ((y_x - sum_par U e) - urec_x e_{x+1}); z[row] += e_x.
-template <typename T, typename TZ, int CPL>
-__device__ __forceinline__ void line_backward(int lp, int nx, int c0, int m, int w, const int32_t *__restrict__ ucol,
-                                              const T *__restrict__ uval, const T *__restrict__ urec,
-                                              const T *__restrict__ udinv, const int32_t *__restrict__ rows, T *y,
-                                              TZ *__restrict__ z) {
-    const int lane = threadIdx.x & 31;
-    T a[CPL], bb[CPL];
-#pragma unroll
-    for (int t = 0; t < CPL; ++t) {
-        const int k = t * 32 + lane, x = nx - 1 - k;  // chunks from the end of the line
-        if (k < nx) {
-            const int p = lp + x, r = p - c0;
-            T acc = T(0);
-            for (int j = 0; j < w; ++j) acc = fma(uval[(long)j * m + r], y[ucol[(long)j * m + r]], acc);
-            const T d = udinv[p];
-            a[t] = d * (y[p] - acc);
-            bb[t] = -d * urec[p];
-        } else {
-            a[t] = T(0);
-            bb[t] = T(1);
-        }
-    }
-    T carry = T(0);
-#pragma unroll
-    for (int t = 0; t < CPL; ++t) {
-        if (t * 32 >= nx) break;
-        T A = a[t], B = bb[t];
-        affine_scan(A, B, lane);
-        const T prev = __shfl_up_sync(0xffffffffu, fma(B, carry, A), 1);
-        const T zin = lane == 0 ? carry : prev;
-        const T ev = fma(bb[t], zin, a[t]);
-        const int k = t * 32 + lane;
-        if (k < nx) {
-            const int p = lp + nx - 1 - k;
-            y[p] = ev;
-            const int row = rows[p];
-            z[row] = TZ(z[row] + TZ(ev));
-        }
-        carry = __shfl_sync(0xffffffffu, fma(B, carry, A), 31);
-    }
-    __syncwarp();
-}
+constexpr int kLinesWarps = 4;  // blocks (warps) per CTA of the sweeps
 
 // mode 0: forward over the block's lines; 1: backward; 2: forward then
-// backward (the last colour). One warp per block.
+// backward (the last colour). One warp per block; the block's values live in
+// shared memory while its lines are processed.
 template <typename T, typename TZ, int CPL>
-__global__ void __launch_bounds__(128) lines_sweep_kernel(int mode, int b0, int nblk,
-                                                          const int32_t *__restrict__ blk_start,
-                                                          const int32_t *__restrict__ blk_nsub, int nx, int c0, int m,
-                                                          int wl, const int32_t *__restrict__ lcol,
-                                                          const T *__restrict__ lval, const T *__restrict__ lrec,
-                                                          int wu, const int32_t *__restrict__ ucol,
-                                                          const T *__restrict__ uval, const T *__restrict__ urec,
-                                                          const T *__restrict__ udinv,
-                                                          const int32_t *__restrict__ rows, T *__restrict__ y,
-                                                          TZ *__restrict__ z) {
+__global__ void __launch_bounds__(32 * kLinesWarps) lines_sweep_kernel(
+    int mode, int b0, int nblk, const int32_t *__restrict__ blk_start, const int32_t *__restrict__ blk_nsub, int nx,
+    int c0, int m, int wl, const int32_t *__restrict__ lcol, const T *__restrict__ lval, int wli,
+    const int16_t *__restrict__ lidx, const T *__restrict__ lvin, const T *__restrict__ lrec, int wu,
+    const int32_t *__restrict__ ucol, const T *__restrict__ uval, int wui, const int16_t *__restrict__ uidx,
+    const T *__restrict__ uvin, const T *__restrict__ urec, const T *__restrict__ udinv,
+    const int32_t *__restrict__ rows, T *__restrict__ y, TZ *__restrict__ z) {
+    __shared__ T s_blk[kLinesWarps][4 * 32 * CPL];
     pdl_prologue();
-    const int wb = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int wb = blockIdx.x * kLinesWarps + wid;
     if (wb >= nblk) return;  // whole warps leave together
     const int b = b0 + wb;
-    const int start = blk_start[b], nsub = blk_nsub[b];
-    if (mode != 1)
-        for (int q = 0; q < nsub; ++q) line_forward<T, CPL>(start + q * nx, nx, c0, m, wl, lcol, lval, lrec, y);
-    if (mode != 0)
-        for (int q = nsub - 1; q >= 0; --q)
-            line_backward<T, TZ, CPL>(start + q * nx, nx, c0, m, wu, ucol, uval, urec, udinv, rows, y, z);
+    const int st = blk_start[b], nsub = blk_nsub[b];
+    T *sm = s_blk[wid];
+    if (mode != 1) {
+        // off-block part of every point of the block: s = r - sum_off L y
+        for (int q = 0; q < nsub; ++q)
+#pragma unroll
+            for (int t = 0; t < CPL; ++t) {
+                const int x = t * 32 + lane;
+                if (x < nx) {
+                    const int li = q * nx + x, r = st + li - c0;
+                    T acc = T(0);
+                    for (int j = 0; j < wl; ++j) acc = fma(lval[(long)j * m + r], y[lcol[(long)j * m + r]], acc);
+                    sm[li] = y[st + li] - acc;
+                }
+            }
+        __syncwarp();
+        for (int q = 0; q < nsub; ++q) {
+            T a[CPL], bb[CPL], out[CPL];
+#pragma unroll
+            for (int t = 0; t < CPL; ++t) {
+                const int x = t * 32 + lane;
+                a[t] = T(0);
+                bb[t] = T(1);  // identity past the end of the line
+                if (x < nx) {
+                    const int li = q * nx + x, r = st + li - c0;
+                    T acc = sm[li];
+                    for (int j = 0; j < wli; ++j) acc = fma(-lvin[(long)j * m + r], sm[lidx[(long)j * m + r]], acc);
+                    a[t] = acc;
+                    bb[t] = -lrec[st + li];
+                }
+            }
+            line_scan<T, CPL>(a, bb, nx, lane, out);
+#pragma unroll
+            for (int t = 0; t < CPL; ++t) {
+                const int x = t * 32 + lane;
+                if (x < nx) {
+                    sm[q * nx + x] = out[t];
+                    y[st + q * nx + x] = out[t];
+                }
+            }
+            __syncwarp();
+        }
+    } else {
+        for (int li = lane; li < nsub * nx; li += 32) sm[li] = y[st + li];
+        __syncwarp();
+    }
+    if (mode == 0) return;
+    // backward: t = y - sum_off U e in place, then the lines from the last:
+    // e_x = udinv_x ((t_x - sum_in U e) - urec_x e_{x+1})
+    for (int q = 0; q < nsub; ++q)
+#pragma unroll
+        for (int t = 0; t < CPL; ++t) {
+            const int x = t * 32 + lane;
+            if (x < nx) {
+                const int li = q * nx + x, r = st + li - c0;
+                T acc = T(0);
+                for (int j = 0; j < wu; ++j) acc = fma(uval[(long)j * m + r], y[ucol[(long)j * m + r]], acc);
+                sm[li] -= acc;
+            }
+        }
+    __syncwarp();
+    for (int q = nsub - 1; q >= 0; --q) {
+        T a[CPL], bb[CPL], out[CPL];
+#pragma unroll
+        for (int t = 0; t < CPL; ++t) {
+            const int k = t * 32 + lane, x = nx - 1 - k;  // chunks from the end of the line
+            a[t] = T(0);
+            bb[t] = T(1);
+            if (k < nx) {
+                const int li = q * nx + x, r = st + li - c0;
+                T acc = sm[li];
+                for (int j = 0; j < wui; ++j) acc = fma(-uvin[(long)j * m + r], sm[uidx[(long)j * m + r]], acc);
+                const T d = udinv[st + li];
+                a[t] = d * acc;
+                bb[t] = -d * urec[st + li];
+            }
+        }
+        line_scan<T, CPL>(a, bb, nx, lane, out);
+#pragma unroll
+        for (int t = 0; t < CPL; ++t) {
+            const int k = t * 32 + lane;
+            if (k < nx) {
+                const int li = q * nx + nx - 1 - k;
+                sm[li] = out[t];
+                y[st + li] = out[t];
+                const int row = rows[st + li];
+                z[row] = TZ(z[row] + TZ(out[t]));
+            }
+        }
+        __syncwarp();
+    }
 }
 
 // ---- host side ---------------------------------------------------------------------------------
@@ -454,39 +515,52 @@ msrsb_status lines_setup(msrsb_handle *h, TF *lu, cudaStream_t s) {
     lines_colour_of_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, L.rows, L, ccol);
     MSRSB_LAUNCHED("lines_colour_of_kernel");
     int *w = nullptr;
-    MSRSB_TRY(dalloc(&w, 8, s));
-    MSRSB_CUDA(cudaMemsetAsync(w, 0, 8 * sizeof(int), s));
-    lines_width_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, nx, A.rowptr, A.colidx, h->pos_of, ccol, w, w + 4);
+    MSRSB_TRY(dalloc(&w, 16, s));
+    MSRSB_CUDA(cudaMemsetAsync(w, 0, 16 * sizeof(int), s));
+    lines_width_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, nx, ny, A.rowptr, A.colidx, h->pos_of, ccol, w);
     MSRSB_LAUNCHED("lines_width_kernel");
-    int hw[8];
-    MSRSB_CUDA(cudaMemcpyAsync(hw, w, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    int hw[16];
+    MSRSB_CUDA(cudaMemcpyAsync(hw, w, 16 * sizeof(int), cudaMemcpyDeviceToHost, s));
     MSRSB_CUDA(cudaStreamSynchronize(s));
     dfree(w, s);
-    long lt = 0, ut = 0;
+    long lt = 0, ut = 0, lit = 0, uit = 0;
     for (int c = 0; c < L.ncol; ++c) {
         L.wl[c] = hw[c];
         L.wu[c] = hw[4 + c];
+        L.wli[c] = hw[8 + c];
+        L.wui[c] = hw[12 + c];
         L.lbase[c] = lt;
         L.ubase[c] = ut;
+        L.libase[c] = lit;
+        L.uibase[c] = uit;
         const long m = L.cptr[c + 1] - L.cptr[c];
         lt += m * L.wl[c];
         ut += m * L.wu[c];
+        lit += m * L.wli[c];
+        uit += m * L.wui[c];
     }
-    TF *lval = nullptr, *uval = nullptr, *lrec = nullptr, *urec = nullptr, *udinv = nullptr;
+    TF *lval = nullptr, *uval = nullptr, *lvin = nullptr, *uvin = nullptr, *lrec = nullptr, *urec = nullptr,
+       *udinv = nullptr;
     MSRSB_TRY(dalloc(&L.lcol, lt, s));
     MSRSB_TRY(dalloc(&L.ucol, ut, s));
+    MSRSB_TRY(dalloc(&L.lidx, lit, s));
+    MSRSB_TRY(dalloc(&L.uidx, uit, s));
     MSRSB_TRY(dalloc(&lval, lt, s));
     MSRSB_TRY(dalloc(&uval, ut, s));
+    MSRSB_TRY(dalloc(&lvin, lit, s));
+    MSRSB_TRY(dalloc(&uvin, uit, s));
     MSRSB_TRY(dalloc(&lrec, n, s));
     MSRSB_TRY(dalloc(&urec, n, s));
     MSRSB_TRY(dalloc(&udinv, n, s));
     L.lval = lval;
     L.uval = uval;
+    L.lvin = lvin;
+    L.uvin = uvin;
     L.lrec = lrec;
     L.urec = urec;
     L.udinv = udinv;
-    lines_fill_kernel<TF><<<ceil_div(n, 256), 256, 0, s>>>(n, nx, A.rowptr, A.colidx, lu, dpos, h->pos_of, ccol, L,
-                                                           L.lcol, lval, L.ucol, uval, lrec, urec, udinv);
+    lines_fill_kernel<TF><<<ceil_div(n, 256), 256, 0, s>>>(n, nx, ny, A.rowptr, A.colidx, lu, dpos, h->pos_of, ccol, L,
+                                                           lval, uval, lvin, uvin, lrec, urec, udinv);
     MSRSB_LAUNCHED("lines_fill_kernel");
     dfree(status, s);
     dfree(dpos, s);
@@ -504,10 +578,12 @@ static msrsb_status lines_apply_t(const msrsb_handle *h, T *ry, TZ *z, cudaStrea
         const int nb = L.bptr[c + 1] - L.bptr[c];
         if (!nb) return MSRSB_OK;
         const int m = L.cptr[c + 1] - L.cptr[c];
-        MSRSB_PDL((lines_sweep_kernel<T, TZ, CPL>), ceil_div((long)nb * 32, 128), 128, 0, s, mode, L.bptr[c], nb,
-                  L.blk_start, L.blk_nsub, L.nx, L.cptr[c], m, L.wl[c], L.lcol + L.lbase[c],
-                  (const T *)L.lval + L.lbase[c], (const T *)L.lrec, L.wu[c], L.ucol + L.ubase[c],
-                  (const T *)L.uval + L.ubase[c], (const T *)L.urec, (const T *)L.udinv, L.rows, ry, z);
+        MSRSB_PDL((lines_sweep_kernel<T, TZ, CPL>), ceil_div(nb, kLinesWarps), 32 * kLinesWarps, 0, s, mode,
+                  L.bptr[c], nb, L.blk_start, L.blk_nsub, L.nx, L.cptr[c], m, L.wl[c], L.lcol + L.lbase[c],
+                  (const T *)L.lval + L.lbase[c], L.wli[c], L.lidx + L.libase[c], (const T *)L.lvin + L.libase[c],
+                  (const T *)L.lrec, L.wu[c], L.ucol + L.ubase[c], (const T *)L.uval + L.ubase[c], L.wui[c],
+                  L.uidx + L.uibase[c], (const T *)L.uvin + L.uibase[c], (const T *)L.urec, (const T *)L.udinv,
+                  L.rows, ry, z);
         return MSRSB_OK;
     };
     for (int c = 0; c < last; ++c) MSRSB_TRY(launch(0, c));
@@ -531,6 +607,10 @@ template msrsb_status lines_apply<float, double>(const msrsb_handle *, float *, 
 template msrsb_status lines_apply<float, float>(const msrsb_handle *, float *, float *, cudaStream_t);
 
 void lines_free(IluLines *L, cudaStream_t s) {
+    dfree(L->lidx, s);
+    dfree(L->uidx, s);
+    dfree(L->lvin, s);
+    dfree(L->uvin, s);
     dfree(L->rows, s);
     dfree(L->blk_start, s);
     dfree(L->blk_nsub, s);

@@ -24,7 +24,7 @@ MSRSB_ORDER_LINES, MSRSB_ORDER_PARITY = 0, 1
 EXPORTS = ["msrsb_partition_size", "msrsb_partition", "msrsb_filter", "msrsb_build_basis", "msrsb_coarse_op",
            "msrsb_setup", "msrsb_apply", "msrsb_solve", "msrsb_get_setup", "msrsb_get_info", "msrsb_destroy",
            "msrsb_solve_host", "msrsb_profile", "msrsb_profile_read", "msrsb_wait_selftest", "msrsb_build_basis_noalloc",
-           "msrsb_solve_ensemble", "msrsb_transpose_values", "msrsb_pattern_outer", "msrsb_fma_rate", "msrsb_last_error"]
+           "msrsb_solve_ensemble", "msrsb_transpose_values", "msrsb_pattern_outer", "msrsb_fma_rate", "msrsb_mpfa_assemble", "msrsb_mpfa_gradient", "msrsb_last_error"]
 
 
 class MsrsbError(RuntimeError):
@@ -371,6 +371,38 @@ def msrsb_solve_ensemble(problems, o, rtol=1e-8, maxit=200, concurrency=4):
     out = [(list(k[2])[:k[4]], list(k[3])[:k[4]], arr[i].status) for i, k in enumerate(keep)]
     _check(st)
     return out
+
+
+def _wells(wells):
+    import numpy as np
+    cells = np.ascontiguousarray([w[0] for w in wells], dtype=np.int32)
+    pw = np.ascontiguousarray([w[1] for w in wells], dtype=np.float64)
+    return len(wells), cells, pw
+
+
+def msrsb_mpfa_assemble(g, K_hat, theta, wells, rowptr, colidx, stream=None):
+    """MPFA-O values (in the given 27-point CSR pattern) and b for cell
+    log-permeabilities theta; K_hat (n, 3, 3) and theta device FP64 tensors;
+    wells a list of (cell, pressure). Returns (val, b)."""
+    nw, wc, wp = _wells(wells)
+    val = torch.empty(colidx.numel(), dtype=torch.float64, device=theta.device)
+    b = torch.empty(theta.numel(), dtype=torch.float64, device=theta.device)
+    _check(load().msrsb_mpfa_assemble(ctypes.byref(g), _ptr(K_hat.contiguous()), _ptr(theta.contiguous()),
+                                      ctypes.c_int32(nw), ctypes.c_void_p(wc.ctypes.data),
+                                      ctypes.c_void_p(wp.ctypes.data), _ptr(rowptr), _ptr(colidx), _ptr(val), _ptr(b),
+                                      _stream(stream)))
+    return val, b
+
+
+def msrsb_mpfa_gradient(g, K_hat, theta, wells, lam, p, stream=None):
+    """dJ/dtheta = -lambda^T dA/dtheta p + lambda^T db/dtheta (device tensor)."""
+    nw, wc, wp = _wells(wells)
+    grad = torch.empty_like(theta)
+    _check(load().msrsb_mpfa_gradient(ctypes.byref(g), _ptr(K_hat.contiguous()), _ptr(theta.contiguous()),
+                                      ctypes.c_int32(nw), ctypes.c_void_p(wc.ctypes.data),
+                                      ctypes.c_void_p(wp.ctypes.data), _ptr(lam.contiguous()), _ptr(p.contiguous()),
+                                      _ptr(grad), _stream(stream)))
+    return grad
 
 
 def msrsb_transpose_values(A, stream=None):
