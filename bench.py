@@ -426,6 +426,23 @@ def run_extra_config(M, name, c, kind, flush, stream, dev, steps, warmup, hbm, p
     return out
 
 
+def device_case(M, n, seed, sigma):
+    """The 3D Darcy case (27-point MPFA-O, GRF ln k with correlation length 8
+    and the given sigma, rotated 10:1 anisotropy, corner wells, 8^3 blocks)
+    assembled on the device by msrsb_mpfa_assemble (the same operator as the
+    host generator builds, far faster at 128^3), returned as host arrays."""
+    import torch
+    from synth.darcy import darcy_3d_field, pattern27
+    dims = (n, n, n)
+    theta, K_hat, wells = darcy_3d_field(dims, seed, sigma=sigma)
+    ip, ix = pattern27(dims)
+    g = M.grid(dims, (H_BLOCK,) * 3)
+    val, b = M.msrsb.msrsb_mpfa_assemble(g, torch.as_tensor(K_hat, device="cuda"), torch.as_tensor(theta, device="cuda"),
+                                         wells, torch.as_tensor(ip, device="cuda"), torch.as_tensor(ix, device="cuda"))
+    return dict(indptr=ip, indices=ix, data=val.cpu().numpy(), b=b.cpu().numpy(), dims=dims, H=(H_BLOCK,) * 3,
+                centering=0, ncomp=1)
+
+
 def gpu_arm(args, rank, world):
     import torch
     import __graft_entry__
@@ -576,7 +593,7 @@ def gpu_arm(args, rank, world):
         cfg["elastic48"] = dict(workload=WORKLOAD_C3, **run_extra_config(
             M, "elastic48", c3, "elastic", flush, stream, dev, CFG_STEPS, CFG_WARMUP, hbm, peak_kind, pk))
         del c3
-        c5 = darcy_3d_case(n=128, H=8, seed=1005, sigma=2.0)
+        c5 = device_case(M, 128, 1005, 2.0)
         cfg["darcy128"] = dict(workload=WORKLOAD_C5, **run_extra_config(
             M, "darcy128", c5, "scalar", flush, stream, dev, CFG_STEPS, CFG_WARMUP, hbm, peak_kind, pk))
         del c5
@@ -738,33 +755,44 @@ def profile_run(args):
 
 
 def ensemble_run(args):
-    """Ensemble throughput (msrsb_solve_ensemble): R seeded 3D Darcy
-    realisations (field and stencil as the main workload; grid edges drawn
-    from --ens-edges, seed 1004; fields seed 40000 + r), 8 right-hand sides
-    b = A xi with xi ~ N(0, 1) each (seed 50000 + r), mixed form, GMRES to
-    1e-8; the whole ensemble timed at concurrency 1 and at --ens-conc.
-    Prints one JSON line."""
+    """Ensemble throughput (msrsb_solve_ensemble) on the batched-ensemble
+    workload: R seeded 3D Darcy realisations (field and stencil as the main
+    workload: MPFA-O 27-point, ln k Gaussian random field l = 8, sigma = 3,
+    10:1 anisotropy rotated (20, 35, 0), corner wells; grid edges drawn
+    uniformly from --ens-edges with seed 1004; fields seed 40000 + r; the
+    operators assembled on the device by msrsb_mpfa_assemble), 8 right-hand
+    sides b = A xi with xi ~ N(0, 1) each (seed 50000 + r), mixed form, GMRES
+    to 1e-8, 8^3-cell blocks; the whole ensemble timed at concurrency 1 and at
+    --ens-conc. Prints one JSON line."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
     import paper_1912_06934_gb300 as M
-    from synth.darcy import darcy_3d_case
+    from synth.darcy import darcy_3d_field, pattern27
     edges = [int(e) for e in args.ens_edges.split(",")]
     rng = np.random.default_rng(1004)
     sizes = [int(rng.choice(edges)) for _ in range(args.ens_R)]
     nrhs = 8
-    probs, rows = [], 0
+    probs, rows, nnz_tot = [], 0, 0
     for r, e in enumerate(sizes):
-        c = darcy_3d_case(n=e, H=H_BLOCK, seed=40000 + r)
-        A = M.Mat.from_host(c["indptr"], c["indices"], c["data"])
-        g = M.grid(c["dims"], c["H"])
-        rr = np.random.default_rng(50000 + r)
-        Ah = _csr(c)
+        dims = (e, e, e)
+        theta, K_hat, wells = darcy_3d_field(dims, 40000 + r)
+        ip, ix = pattern27(dims)
+        rowptr = torch.as_tensor(ip, device="cuda")
+        colidx = torch.as_tensor(ix, device="cuda")
+        g = M.grid(dims, (H_BLOCK,) * 3)
+        val, _ = M.msrsb.msrsb_mpfa_assemble(g, torch.as_tensor(K_hat, device="cuda"),
+                                             torch.as_tensor(theta, device="cuda"), wells, rowptr, colidx)
+        A = M.Mat(rowptr, colidx, val)
+        n = len(theta)
         # b = A xi: a raw N(0, 1) b on a sigma = 3 field can sit at FP64's
         # attainable-accuracy floor (~1e-8), in the FP64 form as well
-        B = torch.as_tensor(np.stack([Ah @ rr.standard_normal(len(c["b"])) for _ in range(nrhs)]), device="cuda")
+        As = torch.sparse_csr_tensor(rowptr.long(), colidx.long(), val, size=(n, n))
+        xi = torch.as_tensor(np.random.default_rng(50000 + r).standard_normal((nrhs, n)), device="cuda")
+        B = (As @ xi.T).T.contiguous()
         probs.append((A, g, B, torch.zeros_like(B)))
-        rows += len(c["b"])
+        rows += n
+        nnz_tot += len(ix)
     o = M.opts(prec=M.msrsb.MSRSB_F32, **BASIS)
     out = {}
     for conc in (1, args.ens_conc):
@@ -785,8 +813,9 @@ def ensemble_run(args):
     line = {"metric": "ensemble: MsRSB set-up + 8 GMRES solves per realisation, realisations per second",
             "value": args.ens_R / out[args.ens_conc]["s"], "unit": "realisations/s", "higher_is_better": True,
             "n_gpus": 1, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": "ensemble of %d 3D Darcy realisations, edges %s (rows %d), 8 rhs b = A xi each, "
-                       "H=8^3" % (args.ens_R, sizes, rows), "concurrency": args.ens_conc},
+            "config": {"workload": "ensemble of %d 3D Darcy realisations (MPFA-O 27-point, GRF l=8 sigma=3), edges "
+                       "drawn from %s: %s (rows %d, nnz %d), 8 rhs b = A xi each, H=8^3" %
+                       (args.ens_R, edges, sizes, rows, nnz_tot), "concurrency": args.ens_conc},
             "sequential": out[1], "concurrent": out[args.ens_conc],
             "speedup_concurrent_vs_sequential": out[1]["s"] / out[args.ens_conc]["s"]}
     print(json.dumps(line))
@@ -805,8 +834,8 @@ def main():
                     help="run a workload for a profiler instead of the benchmark")
     ap.add_argument("--grid", type=int, default=N_GRID, help="grid edge for --profile")
     ap.add_argument("--ensemble", action="store_true", help="ensemble throughput instead of the benchmark")
-    ap.add_argument("--ens-R", type=int, default=12)
-    ap.add_argument("--ens-edges", default="32,48,64")
+    ap.add_argument("--ens-R", type=int, default=64)
+    ap.add_argument("--ens-edges", default="32,48,64,80,96")
     ap.add_argument("--ens-conc", type=int, default=6)
     args = ap.parse_args()
     if args.oracle_step:  # cpu_baseline leg in a process of its own (thread count from the environment)

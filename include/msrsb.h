@@ -256,6 +256,10 @@ msrsb_status msrsb_apply(msrsb_handle *h, const double *v, double *z, cudaStream
 msrsb_status msrsb_solve(msrsb_handle *h, const double *b, double *x, double rtol, int32_t maxit,
                          int32_t *iters_h, double *relres_h, double *hist_h, cudaStream_t stream);
 
+/* y = A x for a fine operator (FP64 CSR or 3x3 block CSR, device arrays;
+ * x, y FP64 [nrows * bdim], not aliased). Stream-ordered. */
+msrsb_status msrsb_spmv(const msrsb_mat *A, const double *x, double *y, cudaStream_t stream);
+
 /* Copies of the set-up results, for checks: p_ids[n][W], p_val[comp][n][W]
  * (handle precision), Ac_dense[nC][nC] (A_c expanded to a dense row-major
  * matrix, nC = nc * bdim); any pointer may be NULL. */

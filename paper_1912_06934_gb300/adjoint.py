@@ -26,8 +26,22 @@ dJ/db back to dJ/d log k.
 import numpy as np
 import torch
 
-from .msrsb import (Mat, msrsb_mpfa_assemble, msrsb_mpfa_gradient, msrsb_pattern_outer, msrsb_setup,
+from .msrsb import (Mat, msrsb_mpfa_assemble, msrsb_mpfa_gradient, msrsb_pattern_outer, msrsb_setup, msrsb_spmv,
                     msrsb_transpose_values)
+
+
+def _refined_solve(h, A, b, rtol, maxit, refine):
+    """x = A^-1 b by the MsRSB-preconditioned solve, then `refine` steps of
+    iterative refinement (r = b - A x in FP64, x += A^-1 r): each step
+    carries the solve's relative tolerance to the correction, past what one
+    Krylov solve attains on ill-conditioned well problems."""
+    x = h.solve(b, rtol=rtol, maxit=maxit)["x"]
+    for _ in range(refine):
+        r = b - msrsb_spmv(A, x)
+        if float(torch.linalg.vector_norm(r)) == 0.0:
+            break
+        x = x + h.solve(r, rtol=rtol, maxit=maxit)["x"]
+    return x
 
 
 class MsrsbSolve(torch.autograd.Function):
@@ -63,37 +77,38 @@ class MsrsbSolve(torch.autograd.Function):
 class MsrsbMpfaSolve(torch.autograd.Function):
     """p = A(theta)^-1 b(theta) for the MPFA-O model. Inputs: theta (CUDA
     FP64, n), model = (grid, K_hat (n, 3, 3) CUDA FP64, wells [(cell, p_w)],
-    rowptr, colidx of the 27-point pattern), o (msrsb_opts), rtol, maxit."""
+    rowptr, colidx of the 27-point pattern), o (msrsb_opts), rtol, maxit,
+    refine (iterative-refinement steps after each solve)."""
 
     @staticmethod
-    def forward(ctx, theta, model, o, rtol, maxit):
+    def forward(ctx, theta, model, o, rtol, maxit, refine):
         g, K_hat, wells, rowptr, colidx = model
         th = theta.detach().contiguous()
         val, b = msrsb_mpfa_assemble(g, K_hat, th, wells, rowptr, colidx)
         A = Mat(rowptr, colidx, val)
         h = msrsb_setup(A, g, o)
-        p = h.solve(b, rtol=rtol, maxit=maxit)["x"]
+        p = _refined_solve(h, A, b, rtol, maxit, refine)
         h.destroy()
         ctx.save_for_backward(th, val, p)
-        ctx.meta = (model, o, rtol, maxit)
+        ctx.meta = (model, o, rtol, maxit, refine)
         return p
 
     @staticmethod
     def backward(ctx, gp):
         th, val, p = ctx.saved_tensors
-        (g, K_hat, wells, rowptr, colidx), o, rtol, maxit = ctx.meta
+        (g, K_hat, wells, rowptr, colidx), o, rtol, maxit, refine = ctx.meta
         A = Mat(rowptr, colidx, val)
         At = Mat(rowptr, colidx, msrsb_transpose_values(A))
         h = msrsb_setup(At, g, o)
-        lam = h.solve(gp.contiguous(), rtol=rtol, maxit=maxit)["x"]
+        lam = _refined_solve(h, At, gp.contiguous(), rtol, maxit, refine)
         h.destroy()
-        return msrsb_mpfa_gradient(g, K_hat, th, wells, lam, p), None, None, None, None
+        return msrsb_mpfa_gradient(g, K_hat, th, wells, lam, p), None, None, None, None, None
 
 
-def msrsb_mpfa_solve_diff(theta, model, o, rtol=1e-10, maxit=500):
+def msrsb_mpfa_solve_diff(theta, model, o, rtol=1e-10, maxit=500, refine=0):
     """Differentiable p = A(theta)^-1 b(theta) of the MPFA-O model (see
     MsrsbMpfaSolve)."""
-    return MsrsbMpfaSolve.apply(theta, model, o, rtol, maxit)
+    return MsrsbMpfaSolve.apply(theta, model, o, rtol, maxit, refine)
 
 
 def msrsb_solve_diff(vals, b, pattern, o, rtol=1e-10, maxit=500):

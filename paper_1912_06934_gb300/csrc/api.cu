@@ -330,14 +330,6 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
         }
         ~Release() { (*this)(nullptr); }
     } release{go};
-    // The line-block ILU(0) factorisation is latency-bound (one CTA per line
-    // block, a wavefront of dependent rows), so it overlaps the basis build
-    // without competing for bandwidth: release it at once.
-    if (h->opts.smoother == MSRSB_SMOOTH_ILU0 && bd == 1 && h->opts.ordering == MSRSB_ORDER_LINES &&
-        lines_fit(&h->grid)) {
-        MSRSB_CUDA(cudaEventRecord(go_ev, s));
-        release(go_ev);
-    }
     // filtered operator(s) streamed as sliced ELL, then Alg. 1 per component
     T *P = nullptr;
     MSRSB_TRY(dalloc(&P, nW * bd, s));
@@ -1150,6 +1142,13 @@ extern "C" msrsb_status msrsb_get_setup(msrsb_handle *h, int32_t *p_ids, void *p
     if (p_val) MSRSB_CUDA(cudaMemcpyAsync(p_val, h->p_val, nW * h->bdim * es, cudaMemcpyDeviceToDevice, stream));
     if (Ac_dense) MSRSB_TRY(stencil_to_dense(h->grid.dim, h->nb, h->bdim, h->Acs, Ac_dense, stream));
     return MSRSB_OK;
+}
+
+extern "C" msrsb_status msrsb_spmv(const msrsb_mat *A, const double *x, double *y, cudaStream_t stream) {
+    MSRSB_TRY(check_mat(A));
+    if (!x || !y) return fail(MSRSB_EINVAL, "NULL argument");
+    if (x == y) return fail(MSRSB_EINVAL, "x and y must not alias");
+    return spmv<double, double, double, double, double>(*A, A->val, x, nullptr, y, false, stream);
 }
 
 extern "C" msrsb_status msrsb_get_info(const msrsb_handle *h, msrsb_info *info) {

@@ -58,9 +58,10 @@ constexpr int kLBatch = 8;
 // (as a product with the stored 1 / u_kk), then every later entry (i, j) that
 // row k also holds gets a_ij -= l_ik u_kj.
 template <typename TF>
-__device__ void lines_eliminate(int i, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
-                                const int32_t *__restrict__ pos, const int32_t *__restrict__ dpos, TF *__restrict__ lu,
-                                TF *__restrict__ rdiag, int *__restrict__ status, int32_t (*kc)[32], TF (*kv)[32]) {
+__device__ void lines_eliminate(int i, int plo, int phi, bool last, const int32_t *__restrict__ rowptr,
+                                const int32_t *__restrict__ colidx, const int32_t *__restrict__ pos,
+                                const int32_t *__restrict__ dpos, TF *__restrict__ lu, TF *__restrict__ rdiag,
+                                int *__restrict__ status, int32_t (*kc)[32], TF (*kv)[32]) {
     const int lane = threadIdx.x & 31;
     const int b = rowptr[i], len = rowptr[i + 1] - b;
     if (len > 32) {
@@ -72,7 +73,10 @@ __device__ void lines_eliminate(int i, const int32_t *__restrict__ rowptr, const
     const int pj = mine ? pos[j] : INT_MAX;
     const int pi_ = pos[i];
     TF a = mine ? lu[b + lane] : TF(0);
-    const bool lower = mine && pj < pi_;
+    // this call eliminates the earlier entries with positions in
+    // [plo, min(pos[i], phi)); `last`: the row is then final and its 1 / u_ii
+    // is stored
+    const bool lower = mine && pj < min(pi_, phi) && pj >= plo;
     int rank = 0;  // place of this lower entry in the position order
     for (int o = 0; o < 32; ++o) {
         const int po = __shfl_sync(0xffffffffu, pj, o);
@@ -123,19 +127,40 @@ __device__ void lines_eliminate(int i, const int32_t *__restrict__ rowptr, const
         __syncwarp();  // the next batch overwrites the staged rows
     }
     if (mine) lu[b + lane] = a;
-    const int dq = dpos[i] - b;
-    const TF uii = __shfl_sync(0xffffffffu, a, dq);
-    if (lane == 0) {
-        if (uii == TF(0) || !isfinite((double)uii)) atomicCAS(status, 0, 1 + i);
-        rdiag[i] = TF(1) / uii;
+    if (last) {
+        const int dq = dpos[i] - b;
+        const TF uii = __shfl_sync(0xffffffffu, a, dq);
+        if (lane == 0) {
+            if (uii == TF(0) || !isfinite((double)uii)) atomicCAS(status, 0, 1 + i);
+            rdiag[i] = TF(1) / uii;
+        }
     }
     __syncwarp();
 }
 
-// One colour: CTA b0 + blockIdx.x handles one block, warp q its line q; at
-// time step T warp q factors point x = T - 2 q of its line.
+// Phase 1 of one colour, every row at once (one warp per row): the earlier
+// entries of earlier colours (positions below c0, all final) come first in
+// the order, so they are eliminated in parallel before the in-block ones.
 template <typename TF>
-__global__ void __launch_bounds__(128) lines_factor_kernel(int b0, const int32_t *__restrict__ blk_start,
+__global__ void __launch_bounds__(128) lines_factor_off_kernel(int c0, int cnt, const int32_t *__restrict__ rows,
+                                                               const int32_t *__restrict__ rowptr,
+                                                               const int32_t *__restrict__ colidx,
+                                                               const int32_t *__restrict__ pos,
+                                                               const int32_t *__restrict__ dpos, TF *__restrict__ lu,
+                                                               TF *__restrict__ rdiag, int *__restrict__ status) {
+    __shared__ int32_t s_kc[4][kLBatch][32];
+    __shared__ TF s_kv[4][kLBatch][32];
+    const int w = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5), q = threadIdx.x >> 5;
+    if (w >= cnt) return;  // whole warps leave together
+    const int i = rows[c0 + w];
+    lines_eliminate<TF>(i, 0, c0, false, rowptr, colidx, pos, dpos, lu, rdiag, status, s_kc[q], s_kv[q]);
+}
+
+// Phase 2 of one colour: the in-block earlier entries (positions from c0 on).
+// CTA b0 + blockIdx.x handles one block, warp q its line q; at time step T
+// warp q finishes point x = T - 2 q of its line.
+template <typename TF>
+__global__ void __launch_bounds__(128) lines_factor_kernel(int c0, int b0, const int32_t *__restrict__ blk_start,
                                                            const int32_t *__restrict__ blk_nsub, int nx,
                                                            const int32_t *__restrict__ rows,
                                                            const int32_t *__restrict__ rowptr,
@@ -151,8 +176,8 @@ __global__ void __launch_bounds__(128) lines_factor_kernel(int b0, const int32_t
     for (int T = 0; T < steps; ++T) {
         const int x = T - 2 * q;
         if (q < nsub && x >= 0 && x < nx)
-            lines_eliminate<TF>(rows[start + q * nx + x], rowptr, colidx, pos, dpos, lu, rdiag, status, s_kc[q],
-                                s_kv[q]);
+            lines_eliminate<TF>(rows[start + q * nx + x], c0, INT_MAX, true, rowptr, colidx, pos, dpos, lu, rdiag,
+                                status, s_kc[q], s_kv[q]);
         __syncthreads();  // points of this step are final before the next step reads them
     }
 }
@@ -292,133 +317,109 @@ __device__ __forceinline__ void affine_scan(T &A, T &B, int lane) {
     }
 }
 
-// Chunked recurrence over one line held in shared memory: v_x = a_x + b_x v_{x-1}
-// (k = 0, 1, ... in processing order); a, b per chunk in registers; the
-// result overwrites sm[idx(k)].
-template <typename T, int CPL>
-__device__ __forceinline__ void line_scan(const T (&a)[CPL], const T (&b)[CPL], int nx, int lane, T (&out)[CPL]) {
-    T carry = T(0);
-#pragma unroll
-    for (int t = 0; t < CPL; ++t) {
-        if (t * 32 >= nx) break;
-        T A = a[t], B = b[t];
-        affine_scan(A, B, lane);
-        const T prev = __shfl_up_sync(0xffffffffu, fma(B, carry, A), 1);
-        const T vin = lane == 0 ? carry : prev;
-        out[t] = fma(b[t], vin, a[t]);
-        carry = __shfl_sync(0xffffffffu, fma(B, carry, A), 31);
+// The recurrence v_k = a_k + b_k v_{k-1}, v_-1 = 0, along one line (k in
+// processing order, the lanes of the line's warps in k order), two-level: an
+// affine warp scan, then the composed maps of the line's earlier warps (wl
+// of them, through wA / wB in shared memory) applied as the carry. Every
+// thread of the CTA calls it (threads off the line pass the identity map
+// a = 0, b = 1), so the barrier inside is reached by all. Returns v_k.
+template <typename T>
+__device__ __forceinline__ T cta_line_scan(T a, T b, int lane, int wl, T *wA, T *wB) {
+    T A = a, B = b;
+    affine_scan(A, B, lane);  // now v_k = A + B v_{-1 of this warp}
+    if (lane == 31) {
+        wA[threadIdx.x >> 5] = A;
+        wB[threadIdx.x >> 5] = B;
     }
+    __syncthreads();
+    T carry = T(0);  // v just before this warp
+    const int w = threadIdx.x >> 5;
+    for (int u = w - wl; u < w; ++u) carry = fma(wB[u], carry, wA[u]);
+    return fma(B, carry, A);
 }
 
-constexpr int kLinesWarps = 4;  // blocks (warps) per CTA of the sweeps
-
 // mode 0: forward over the block's lines; 1: backward; 2: forward then
-// backward (the last colour). One warp per block; the block's values live in
-// shared memory while its lines are processed.
-template <typename T, typename TZ, int CPL>
-__global__ void __launch_bounds__(32 * kLinesWarps) lines_sweep_kernel(
-    int mode, int b0, int nblk, const int32_t *__restrict__ blk_start, const int32_t *__restrict__ blk_nsub, int nx,
+// backward (the last colour). One CTA per block, one thread per point: line q
+// is held by threads q * nxp ... q * nxp + nx - 1 (nxp = nx rounded up to a
+// whole warp), the block's values in shared memory. The contributions from
+// other blocks are gathered by every point at once; the lines then follow in
+// turn, each a scan over its threads.
+template <typename T, typename TZ>
+__global__ void __launch_bounds__(1024) lines_sweep_kernel(
+    int mode, int b0, const int32_t *__restrict__ blk_start, const int32_t *__restrict__ blk_nsub, int nx, int nxp,
     int c0, int m, int wl, const int32_t *__restrict__ lcol, const T *__restrict__ lval, int wli,
     const int16_t *__restrict__ lidx, const T *__restrict__ lvin, const T *__restrict__ lrec, int wu,
     const int32_t *__restrict__ ucol, const T *__restrict__ uval, int wui, const int16_t *__restrict__ uidx,
     const T *__restrict__ uvin, const T *__restrict__ urec, const T *__restrict__ udinv,
     const int32_t *__restrict__ rows, T *__restrict__ y, TZ *__restrict__ z) {
-    __shared__ T s_blk[kLinesWarps][4 * 32 * CPL];
+    extern __shared__ unsigned char s_raw[];
+    T *sm = reinterpret_cast<T *>(s_raw);  // [4 * nx]
+    T *wA = sm + 4 * nx, *wB = wA + 32;      // composed maps of the warps
     pdl_prologue();
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int wb = blockIdx.x * kLinesWarps + wid;
-    if (wb >= nblk) return;  // whole warps leave together
-    const int b = b0 + wb;
+    const int b = b0 + blockIdx.x;
     const int st = blk_start[b], nsub = blk_nsub[b];
-    T *sm = s_blk[wid];
+    const int q = threadIdx.x / nxp, xx = threadIdx.x - q * nxp, lane = threadIdx.x & 31;
+    const int wline = xx >> 5;     // this warp's place in its line
+    const bool on = q < nsub && xx < nx;
     if (mode != 1) {
-        // off-block part of every point of the block: s = r - sum_off L y
-        for (int q = 0; q < nsub; ++q)
-#pragma unroll
-            for (int t = 0; t < CPL; ++t) {
-                const int x = t * 32 + lane;
-                if (x < nx) {
-                    const int li = q * nx + x, r = st + li - c0;
-                    T acc = T(0);
-                    for (int j = 0; j < wl; ++j) acc = fma(lval[(long)j * m + r], y[lcol[(long)j * m + r]], acc);
-                    sm[li] = y[st + li] - acc;
-                }
+        if (on) {  // s = r - sum_off L y
+            const int li = q * nx + xx, r = st + li - c0;
+            T acc = T(0);
+            for (int j = 0; j < wl; ++j) acc = fma(lval[(long)j * m + r], y[lcol[(long)j * m + r]], acc);
+            sm[li] = y[st + li] - acc;
+        }
+        __syncthreads();
+        for (int qq = 0; qq < nsub; ++qq) {
+            T a = T(0), bb = T(1);
+            const int li = qq * nx + xx;
+            if (q == qq && xx < nx) {
+                const int r = st + li - c0;
+                T acc = sm[li];
+                for (int j = 0; j < wli; ++j) acc = fma(-lvin[(long)j * m + r], sm[lidx[(long)j * m + r]], acc);
+                a = acc;
+                bb = -lrec[st + li];
             }
-        __syncwarp();
-        for (int q = 0; q < nsub; ++q) {
-            T a[CPL], bb[CPL], out[CPL];
-#pragma unroll
-            for (int t = 0; t < CPL; ++t) {
-                const int x = t * 32 + lane;
-                a[t] = T(0);
-                bb[t] = T(1);  // identity past the end of the line
-                if (x < nx) {
-                    const int li = q * nx + x, r = st + li - c0;
-                    T acc = sm[li];
-                    for (int j = 0; j < wli; ++j) acc = fma(-lvin[(long)j * m + r], sm[lidx[(long)j * m + r]], acc);
-                    a[t] = acc;
-                    bb[t] = -lrec[st + li];
-                }
+            const T v = cta_line_scan<T>(a, bb, lane, wline, wA, wB);
+            if (q == qq && xx < nx) {
+                sm[li] = v;
+                y[st + li] = v;
             }
-            line_scan<T, CPL>(a, bb, nx, lane, out);
-#pragma unroll
-            for (int t = 0; t < CPL; ++t) {
-                const int x = t * 32 + lane;
-                if (x < nx) {
-                    sm[q * nx + x] = out[t];
-                    y[st + q * nx + x] = out[t];
-                }
-            }
-            __syncwarp();
+            __syncthreads();
         }
     } else {
-        for (int li = lane; li < nsub * nx; li += 32) sm[li] = y[st + li];
-        __syncwarp();
+        if (on) sm[q * nx + xx] = y[st + q * nx + xx];
+        __syncthreads();
     }
     if (mode == 0) return;
-    // backward: t = y - sum_off U e in place, then the lines from the last:
-    // e_x = udinv_x ((t_x - sum_in U e) - urec_x e_{x+1})
-    for (int q = 0; q < nsub; ++q)
-#pragma unroll
-        for (int t = 0; t < CPL; ++t) {
-            const int x = t * 32 + lane;
-            if (x < nx) {
-                const int li = q * nx + x, r = st + li - c0;
-                T acc = T(0);
-                for (int j = 0; j < wu; ++j) acc = fma(uval[(long)j * m + r], y[ucol[(long)j * m + r]], acc);
-                sm[li] -= acc;
-            }
+    // backward: t = y - sum_off U e in place; then the lines from the last, each
+    // from its end: e_x = udinv_x ((t_x - sum_in U e) - urec_x e_{x+1})
+    if (on) {
+        const int li = q * nx + xx, r = st + li - c0;
+        T acc = T(0);
+        for (int j = 0; j < wu; ++j) acc = fma(uval[(long)j * m + r], y[ucol[(long)j * m + r]], acc);
+        sm[li] -= acc;
+    }
+    __syncthreads();
+    for (int qq = nsub - 1; qq >= 0; --qq) {
+        T a = T(0), bb = T(1);
+        const int x = nx - 1 - xx;  // thread xx takes the xx-th point from the line's end
+        const int li = qq * nx + x;
+        if (q == qq && xx < nx) {
+            const int r = st + li - c0;
+            T acc = sm[li];
+            for (int j = 0; j < wui; ++j) acc = fma(-uvin[(long)j * m + r], sm[uidx[(long)j * m + r]], acc);
+            const T d = udinv[st + li];
+            a = d * acc;
+            bb = -d * urec[st + li];
         }
-    __syncwarp();
-    for (int q = nsub - 1; q >= 0; --q) {
-        T a[CPL], bb[CPL], out[CPL];
-#pragma unroll
-        for (int t = 0; t < CPL; ++t) {
-            const int k = t * 32 + lane, x = nx - 1 - k;  // chunks from the end of the line
-            a[t] = T(0);
-            bb[t] = T(1);
-            if (k < nx) {
-                const int li = q * nx + x, r = st + li - c0;
-                T acc = sm[li];
-                for (int j = 0; j < wui; ++j) acc = fma(-uvin[(long)j * m + r], sm[uidx[(long)j * m + r]], acc);
-                const T d = udinv[st + li];
-                a[t] = d * acc;
-                bb[t] = -d * urec[st + li];
-            }
+        const T v = cta_line_scan<T>(a, bb, lane, wline, wA, wB);
+        if (q == qq && xx < nx) {
+            sm[li] = v;
+            y[st + li] = v;
+            const int row = rows[st + li];
+            z[row] = TZ(z[row] + TZ(v));
         }
-        line_scan<T, CPL>(a, bb, nx, lane, out);
-#pragma unroll
-        for (int t = 0; t < CPL; ++t) {
-            const int k = t * 32 + lane;
-            if (k < nx) {
-                const int li = q * nx + nx - 1 - k;
-                sm[li] = out[t];
-                y[st + li] = out[t];
-                const int row = rows[st + li];
-                z[row] = TZ(z[row] + TZ(out[t]));
-            }
-        }
-        __syncwarp();
+        __syncthreads();
     }
 }
 
@@ -496,8 +497,14 @@ msrsb_status lines_setup(msrsb_handle *h, TF *lu, cudaStream_t s) {
     for (int c = 0; c < L.ncol; ++c) {
         const int nb = L.bptr[c + 1] - L.bptr[c];
         if (!nb) continue;
-        lines_factor_kernel<TF><<<nb, 128, 0, s>>>(L.bptr[c], L.blk_start, L.blk_nsub, nx, L.rows, A.rowptr, A.colidx,
-                                                   h->pos_of, dpos, lu, rdiag, status);
+        const int cnt = L.cptr[c + 1] - L.cptr[c];
+        if (c > 0) {
+            lines_factor_off_kernel<TF><<<ceil_div((long)cnt * 32, 128), 128, 0, s>>>(
+                L.cptr[c], cnt, L.rows, A.rowptr, A.colidx, h->pos_of, dpos, lu, rdiag, status);
+            MSRSB_LAUNCHED("lines_factor_off_kernel");
+        }
+        lines_factor_kernel<TF><<<nb, 128, 0, s>>>(L.cptr[c], L.bptr[c], L.blk_start, L.blk_nsub, nx, L.rows,
+                                                   A.rowptr, A.colidx, h->pos_of, dpos, lu, rdiag, status);
         MSRSB_LAUNCHED("lines_factor_kernel");
     }
     int hs = 0;
@@ -570,37 +577,29 @@ msrsb_status lines_setup(msrsb_handle *h, TF *lu, cudaStream_t s) {
 template msrsb_status lines_setup<double>(msrsb_handle *, double *, cudaStream_t);
 template msrsb_status lines_setup<float>(msrsb_handle *, float *, cudaStream_t);
 
-template <typename T, typename TZ, int CPL>
-static msrsb_status lines_apply_t(const msrsb_handle *h, T *ry, TZ *z, cudaStream_t s) {
+// z += U^-1 L^-1 r with r given in the line-block order in ry (overwritten):
+// 2 C - 1 launches for C colours, one CTA per line block
+template <typename T, typename TZ>
+msrsb_status lines_apply(const msrsb_handle *h, T *ry, TZ *z, cudaStream_t s) {
     const IluLines &L = h->lines;
-    const int last = L.ncol - 1;
+    const int last = L.ncol - 1, nxp = ((L.nx + 31) / 32) * 32;
+    const int nsub_max = L.ncol == 4 ? 4 : 2;
+    const size_t smem = (4 * (size_t)L.nx + 64) * sizeof(T);
     auto launch = [&](int mode, int c) -> msrsb_status {
         const int nb = L.bptr[c + 1] - L.bptr[c];
         if (!nb) return MSRSB_OK;
         const int m = L.cptr[c + 1] - L.cptr[c];
-        MSRSB_PDL((lines_sweep_kernel<T, TZ, CPL>), ceil_div(nb, kLinesWarps), 32 * kLinesWarps, 0, s, mode,
-                  L.bptr[c], nb, L.blk_start, L.blk_nsub, L.nx, L.cptr[c], m, L.wl[c], L.lcol + L.lbase[c],
-                  (const T *)L.lval + L.lbase[c], L.wli[c], L.lidx + L.libase[c], (const T *)L.lvin + L.libase[c],
-                  (const T *)L.lrec, L.wu[c], L.ucol + L.ubase[c], (const T *)L.uval + L.ubase[c], L.wui[c],
-                  L.uidx + L.uibase[c], (const T *)L.uvin + L.uibase[c], (const T *)L.urec, (const T *)L.udinv,
-                  L.rows, ry, z);
+        MSRSB_PDL((lines_sweep_kernel<T, TZ>), nb, nsub_max * nxp, smem, s, mode, L.bptr[c], L.blk_start,
+                  L.blk_nsub, L.nx, nxp, L.cptr[c], m, L.wl[c], L.lcol + L.lbase[c], (const T *)L.lval + L.lbase[c],
+                  L.wli[c], L.lidx + L.libase[c], (const T *)L.lvin + L.libase[c], (const T *)L.lrec, L.wu[c],
+                  L.ucol + L.ubase[c], (const T *)L.uval + L.ubase[c], L.wui[c], L.uidx + L.uibase[c],
+                  (const T *)L.uvin + L.uibase[c], (const T *)L.urec, (const T *)L.udinv, L.rows, ry, z);
         return MSRSB_OK;
     };
     for (int c = 0; c < last; ++c) MSRSB_TRY(launch(0, c));
     MSRSB_TRY(launch(2, last));
     for (int c = last - 1; c >= 0; --c) MSRSB_TRY(launch(1, c));
     return MSRSB_OK;
-}
-
-// z += U^-1 L^-1 r with r given in the line-block order in ry (overwritten):
-// 2 C - 1 launches for C colours
-template <typename T, typename TZ>
-msrsb_status lines_apply(const msrsb_handle *h, T *ry, TZ *z, cudaStream_t s) {
-    const int nx = h->lines.nx;
-    if (nx <= 32) return lines_apply_t<T, TZ, 1>(h, ry, z, s);
-    if (nx <= 64) return lines_apply_t<T, TZ, 2>(h, ry, z, s);
-    if (nx <= 128) return lines_apply_t<T, TZ, 4>(h, ry, z, s);
-    return lines_apply_t<T, TZ, 8>(h, ry, z, s);
 }
 template msrsb_status lines_apply<double, double>(const msrsb_handle *, double *, double *, cudaStream_t);
 template msrsb_status lines_apply<float, double>(const msrsb_handle *, float *, double *, cudaStream_t);

@@ -24,7 +24,7 @@ MSRSB_ORDER_LINES, MSRSB_ORDER_PARITY = 0, 1
 EXPORTS = ["msrsb_partition_size", "msrsb_partition", "msrsb_filter", "msrsb_build_basis", "msrsb_coarse_op",
            "msrsb_setup", "msrsb_apply", "msrsb_solve", "msrsb_get_setup", "msrsb_get_info", "msrsb_destroy",
            "msrsb_solve_host", "msrsb_profile", "msrsb_profile_read", "msrsb_wait_selftest", "msrsb_build_basis_noalloc",
-           "msrsb_solve_ensemble", "msrsb_transpose_values", "msrsb_pattern_outer", "msrsb_fma_rate", "msrsb_mpfa_assemble", "msrsb_mpfa_gradient", "msrsb_last_error"]
+           "msrsb_solve_ensemble", "msrsb_transpose_values", "msrsb_pattern_outer", "msrsb_fma_rate", "msrsb_mpfa_assemble", "msrsb_mpfa_gradient", "msrsb_spmv", "msrsb_last_error"]
 
 
 class MsrsbError(RuntimeError):
@@ -403,6 +403,13 @@ def msrsb_mpfa_gradient(g, K_hat, theta, wells, lam, p, stream=None):
                                       ctypes.c_void_p(wp.ctypes.data), _ptr(lam.contiguous()), _ptr(p.contiguous()),
                                       _ptr(grad), _stream(stream)))
     return grad
+
+
+def msrsb_spmv(A, x, y=None, stream=None):
+    """y = A x (device FP64 vectors)."""
+    y = torch.empty_like(x) if y is None else y
+    _check(load().msrsb_spmv(ctypes.byref(A.c()), _ptr(x), _ptr(y), _stream(stream)))
+    return y
 
 
 def msrsb_transpose_values(A, stream=None):

@@ -257,6 +257,36 @@ def anisotropic_tensors(logk, R, ratios):
     return k[..., None, None] * base
 
 
+def pattern27(dims):
+    """CSR pattern (int32) of every cell's in-grid 3x3x3 neighbours on a 3D
+    grid (cells x fastest), columns ascending: the structural pattern of the
+    MPFA-O operators above."""
+    nx, ny, nz = dims
+    n = nx * ny * nz
+    i = np.arange(n)
+    x, y, z = i % nx, (i // nx) % ny, i // (nx * ny)
+    cols = np.full((n, 27), -1, dtype=np.int64)
+    for q in range(27):
+        dx, dy, dz = q % 3 - 1, (q // 3) % 3 - 1, q // 9 - 1
+        ok = (x + dx >= 0) & (x + dx < nx) & (y + dy >= 0) & (y + dy < ny) & (z + dz >= 0) & (z + dz < nz)
+        cols[ok, q] = i[ok] + dx + nx * (dy + ny * dz)
+    rowptr = np.concatenate([[0], np.cumsum((cols >= 0).sum(axis=1))]).astype(np.int32)
+    return rowptr, cols[cols >= 0].astype(np.int32)
+
+
+def darcy_3d_field(dims, seed, sigma=3.0, corr_len=8.0):
+    """The inputs of the 3D MPFA-O case without its assembly: ln k (cells x
+    fastest; the Gaussian random field of darcy_3d_case from the same seed),
+    the unit anisotropy tensors K_hat [n][3][3] (10:1, rotated (20, 35, 0)
+    degrees) and the corner well pair, for assembling on the device."""
+    rng = np.random.default_rng(seed)
+    logk = gaussian_random_field(tuple(dims), corr_len, sigma, rng)
+    n = int(np.prod(dims))
+    K_hat = anisotropic_tensors(np.zeros(tuple(dims)), rotation_zyx(20.0, 35.0, 0.0), (1.0, 1.0, 0.1))
+    K_hat = np.ascontiguousarray(np.moveaxis(K_hat, [0, 1, 2], [2, 1, 0]).reshape(n, 3, 3))
+    return logk.ravel(order="F"), K_hat, [(0, 1.0), (n - 1, 0.0)]
+
+
 def darcy_2d_case(n=64, H=8, seed=1001):
     """2D MPFA-O case: ln k i.i.d. N(0,1), K = R(30) diag(k, 0.1k) R(30)^T,
     p = 1 at x = 0, p = 0 at x = n, no flow on the other sides."""
