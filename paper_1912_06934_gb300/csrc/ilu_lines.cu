@@ -338,12 +338,53 @@ __device__ __forceinline__ T cta_line_scan(T a, T b, int lane, int wl, T *wA, T 
     return fma(B, carry, A);
 }
 
+// In-block coefficients a thread keeps in registers (9 per direction for a
+// 27-point pattern); wider patterns read the rest from global memory.
+constexpr int kLinesInReg = 9;
+
+template <typename T>
+struct LineCoef {
+    T v[kLinesInReg];
+    int16_t ix[kLinesInReg];
+    T rec, d;
+};
+
+// The in-block coefficients of point li of the block (set-up data, so they
+// may be read before the wait on the preceding kernel).
+template <typename T>
+__device__ __forceinline__ void line_coef_load(LineCoef<T> &cf, bool on, int li, int st, int c0, int m, int w,
+                                               const int16_t *__restrict__ ix, const T *__restrict__ v,
+                                               const T *__restrict__ rec, const T *__restrict__ dinv) {
+    const int r = st + li - c0;
+#pragma unroll
+    for (int j = 0; j < kLinesInReg; ++j) {
+        const bool has = on && j < w;
+        cf.v[j] = has ? v[(long)j * m + r] : T(0);
+        cf.ix[j] = has ? ix[(long)j * m + r] : int16_t(0);
+    }
+    cf.rec = on ? rec[st + li] : T(0);
+    cf.d = on && dinv ? dinv[st + li] : T(1);
+}
+
+// sm[li] - sum_in coef * sm[idx] for the point of cf
+template <typename T>
+__device__ __forceinline__ T line_in_sum(const LineCoef<T> &cf, const T *sm, int li, int st, int c0, int m, int w,
+                                         const int16_t *__restrict__ ix, const T *__restrict__ v) {
+    T acc = sm[li];
+#pragma unroll
+    for (int j = 0; j < kLinesInReg; ++j) acc = fma(-cf.v[j], sm[cf.ix[j]], acc);
+    const int r = st + li - c0;
+    for (int j = kLinesInReg; j < w; ++j) acc = fma(-v[(long)j * m + r], sm[ix[(long)j * m + r]], acc);
+    return acc;
+}
+
 // mode 0: forward over the block's lines; 1: backward; 2: forward then
 // backward (the last colour). One CTA per block, one thread per point: line q
 // is held by threads q * nxp ... q * nxp + nx - 1 (nxp = nx rounded up to a
 // whole warp), the block's values in shared memory. The contributions from
 // other blocks are gathered by every point at once; the lines then follow in
-// turn, each a scan over its threads.
+// turn, each a scan over its threads, with each thread's in-block
+// coefficients already in registers.
 template <typename T, typename TZ>
 __global__ void __launch_bounds__(1024) lines_sweep_kernel(
     int mode, int b0, const int32_t *__restrict__ blk_start, const int32_t *__restrict__ blk_nsub, int nx, int nxp,
@@ -354,69 +395,70 @@ __global__ void __launch_bounds__(1024) lines_sweep_kernel(
     const int32_t *__restrict__ rows, T *__restrict__ y, TZ *__restrict__ z) {
     extern __shared__ unsigned char s_raw[];
     T *sm = reinterpret_cast<T *>(s_raw);  // [4 * nx]
-    T *wA = sm + 4 * nx, *wB = wA + 32;      // composed maps of the warps
-    pdl_prologue();
+    T *wA = sm + 4 * nx, *wB = wA + 32;    // composed maps of the warps
     const int b = b0 + blockIdx.x;
     const int st = blk_start[b], nsub = blk_nsub[b];
     const int q = threadIdx.x / nxp, xx = threadIdx.x - q * nxp, lane = threadIdx.x & 31;
-    const int wline = xx >> 5;     // this warp's place in its line
+    const int wline = xx >> 5;  // this warp's place in its line
     const bool on = q < nsub && xx < nx;
+    const int lf = q * nx + xx;           // the point of the forward sweep
+    const int lb = q * nx + (nx - 1 - xx);  // the point of the backward sweep (from the line's end)
+    LineCoef<T> cf;
+    if (mode != 1)
+        line_coef_load(cf, on, lf, st, c0, m, wli, lidx, lvin, lrec, (const T *)nullptr);
+    else
+        line_coef_load(cf, on, lb, st, c0, m, wui, uidx, uvin, urec, udinv);
+    pdl_prologue();
     if (mode != 1) {
         if (on) {  // s = r - sum_off L y
-            const int li = q * nx + xx, r = st + li - c0;
+            const int r = st + lf - c0;
             T acc = T(0);
             for (int j = 0; j < wl; ++j) acc = fma(lval[(long)j * m + r], y[lcol[(long)j * m + r]], acc);
-            sm[li] = y[st + li] - acc;
+            sm[lf] = y[st + lf] - acc;
         }
         __syncthreads();
         for (int qq = 0; qq < nsub; ++qq) {
+            const bool act = q == qq && xx < nx;
             T a = T(0), bb = T(1);
-            const int li = qq * nx + xx;
-            if (q == qq && xx < nx) {
-                const int r = st + li - c0;
-                T acc = sm[li];
-                for (int j = 0; j < wli; ++j) acc = fma(-lvin[(long)j * m + r], sm[lidx[(long)j * m + r]], acc);
-                a = acc;
-                bb = -lrec[st + li];
+            if (act) {
+                a = line_in_sum(cf, sm, lf, st, c0, m, wli, lidx, lvin);
+                bb = -cf.rec;
             }
             const T v = cta_line_scan<T>(a, bb, lane, wline, wA, wB);
-            if (q == qq && xx < nx) {
-                sm[li] = v;
-                y[st + li] = v;
+            if (act) {
+                sm[lf] = v;
+                y[st + lf] = v;
             }
             __syncthreads();
         }
+        if (mode == 0) return;
+        line_coef_load(cf, on, lb, st, c0, m, wui, uidx, uvin, urec, udinv);
     } else {
-        if (on) sm[q * nx + xx] = y[st + q * nx + xx];
+        if (on) sm[lf] = y[st + lf];
         __syncthreads();
     }
-    if (mode == 0) return;
     // backward: t = y - sum_off U e in place; then the lines from the last, each
     // from its end: e_x = udinv_x ((t_x - sum_in U e) - urec_x e_{x+1})
     if (on) {
-        const int li = q * nx + xx, r = st + li - c0;
+        const int r = st + lf - c0;
         T acc = T(0);
         for (int j = 0; j < wu; ++j) acc = fma(uval[(long)j * m + r], y[ucol[(long)j * m + r]], acc);
-        sm[li] -= acc;
+        sm[lf] -= acc;
     }
     __syncthreads();
     for (int qq = nsub - 1; qq >= 0; --qq) {
+        const bool act = q == qq && xx < nx;
         T a = T(0), bb = T(1);
-        const int x = nx - 1 - xx;  // thread xx takes the xx-th point from the line's end
-        const int li = qq * nx + x;
-        if (q == qq && xx < nx) {
-            const int r = st + li - c0;
-            T acc = sm[li];
-            for (int j = 0; j < wui; ++j) acc = fma(-uvin[(long)j * m + r], sm[uidx[(long)j * m + r]], acc);
-            const T d = udinv[st + li];
-            a = d * acc;
-            bb = -d * urec[st + li];
+        if (act) {
+            const T acc = line_in_sum(cf, sm, lb, st, c0, m, wui, uidx, uvin);
+            a = cf.d * acc;
+            bb = -cf.d * cf.rec;
         }
         const T v = cta_line_scan<T>(a, bb, lane, wline, wA, wB);
-        if (q == qq && xx < nx) {
-            sm[li] = v;
-            y[st + li] = v;
-            const int row = rows[st + li];
+        if (act) {
+            sm[lb] = v;
+            y[st + lb] = v;
+            const int row = rows[st + lb];
             z[row] = TZ(z[row] + TZ(v));
         }
         __syncthreads();

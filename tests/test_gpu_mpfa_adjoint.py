@@ -7,9 +7,12 @@ the interaction regions' local systems, on the 27-point Darcy workloads.
   the oracle's (1e-10 relative) for the same lambda and p.
 - dJ/d ln k of J = sum (p_obs - p)^2 over 64 observation cells (observations
   from a field perturbed by 0.1 N(0, 1)), through MsrsbMpfaSolve (MsRSB
-  solves of A and A^T to 1e-10, two steps of iterative refinement): against the oracle's adjoint gradient with direct
-  solves on 32^3 (1e-6 relative), and against central differences of J on 32
-  random cells of the 128^3 workload (sigma = 2; 1e-5 relative)."""
+  solves of A and A^T, each followed by two steps of iterative refinement
+  with FP64 residuals): against the oracle's adjoint gradient with direct
+  solves on 32^3 (1e-6 relative; solves to 1e-10), and against central
+  differences of J on the 128^3 workload (sigma = 2; 1e-5 relative; solves to
+  1e-8, where one Krylov solve stalls near 3e-10) along the 16 cells of
+  largest sensitivity and 4 random directions."""
 import numpy as np
 import pytest
 import scipy.sparse as sp
@@ -131,16 +134,20 @@ def test_mpfa_adjoint_gradient_matches_oracle_32(M):
     (g,) = torch.autograd.grad(J, th)
     A, b = _host_system(K_hat, theta, wells)
     Jr, gr, _ = O.mpfa_objective_gradient(K_hat, theta, wells, obs, p_obs, A, b)
-    assert abs(float(J) - Jr) <= 1e-8 * Jr
+    assert abs(float(J.detach()) - Jr) <= 1e-8 * Jr
     assert np.linalg.norm(g.cpu().numpy() - gr) <= 1e-6 * np.linalg.norm(gr)
 
 
 def test_mpfa_adjoint_gradient_matches_central_differences_128(M):
     """The 128^3 workload (2,097,152 cells, sigma = 2): the adjoint gradient
-    against central differences of J on 32 random cells, extrapolated
-    (4 D(h/2) - D(h)) / 3 with h = 1e-2 (truncation error O(h^4)), each J from
-    the GPU assembly and an MsRSB solve to 1e-10 with two steps of iterative
-    refinement."""
+    against central differences of J, extrapolated (4 D(h/2) - D(h)) / 3 with
+    h = 1e-2 (truncation error O(h^4)), each J from the GPU assembly and an
+    MsRSB solve to 1e-8 with two steps of iterative refinement (true relative
+    residual near 1e-11, the FP64 floor of b - A p). Checked along the unit
+    vectors of the 16 cells with the largest |dJ/dtheta| and along 4 random
+    N(0, 1) directions, which weigh every cell: 99.9 % of the cells have
+    |dJ/dtheta| below 1e-3 of the largest, too small for a central difference
+    of J in FP64 to resolve one by one."""
     dims = (128, 128, 128)
     theta, K_hat, wells, rng = _model(dims, 2.0, 1005)
     n = int(np.prod(dims))
@@ -152,21 +159,30 @@ def test_mpfa_adjoint_gradient_matches_central_differences_128(M):
     th_obs = torch.as_tensor(theta + 0.1 * rng.standard_normal(n), device="cuda")
     from paper_1912_06934_gb300.adjoint import msrsb_mpfa_solve_diff
     with torch.no_grad():
-        pobs_t = msrsb_mpfa_solve_diff(th_obs, model, o, rtol=1e-10, maxit=1000, refine=2)[obs_t].clone()
+        pobs_t = msrsb_mpfa_solve_diff(th_obs, model, o, rtol=1e-8, maxit=500, refine=2)[obs_t].clone()
     th = torch.as_tensor(theta, device="cuda").requires_grad_(True)
-    J = _J(M, th, model, obs_t, pobs_t, o, 1e-10)
+    J = _J(M, th, model, obs_t, pobs_t, o, 1e-8)
     (g,) = torch.autograd.grad(J, th)
-    g = g.cpu().numpy()
-    cells = rng.choice(n, 32, replace=False)
+    th = th.detach()
 
-    def D(c, h):
+    def D(v, h):
         with torch.no_grad():
-            tp, tm = th.detach().clone(), th.detach().clone()
-            tp[c] += h
-            tm[c] -= h
-            return (float(_J(M, tp, model, obs_t, pobs_t, o, 1e-10)) -
-                    float(_J(M, tm, model, obs_t, pobs_t, o, 1e-10))) / (2 * h)
+            return (float(_J(M, th + h * v, model, obs_t, pobs_t, o, 1e-8)) -
+                    float(_J(M, th - h * v, model, obs_t, pobs_t, o, 1e-8))) / (2 * h)
 
-    h = 1e-2
-    fd = np.array([(4 * D(c, h / 2) - D(c, h)) / 3 for c in cells])
-    assert np.linalg.norm(g[cells] - fd) <= 1e-5 * np.linalg.norm(fd)
+    def richardson(v, h=1e-2):
+        return (4 * D(v, h / 2) - D(v, h)) / 3
+
+    cells = torch.argsort(g.abs(), descending=True)[:16]
+    fd = []
+    for c in cells.tolist():
+        e = torch.zeros_like(th)
+        e[c] = 1.0
+        fd.append(richardson(e))
+    fd = np.array(fd)
+    assert np.linalg.norm(g[cells].cpu().numpy() - fd) <= 1e-5 * np.linalg.norm(fd)
+    for _ in range(4):
+        v = torch.as_tensor(rng.standard_normal(n), device="cuda")
+        gv = float(torch.dot(g, v))
+        fdv = richardson(v)
+        assert abs(gv - fdv) <= 1e-5 * abs(fdv)
