@@ -103,7 +103,11 @@ typedef struct {
                           pattern in the node colour order (equal to the
                           pointwise one in that order, since the pattern is
                           made of whole blocks); for scalar operators ILU(0),
-                          which is IC(0) for a symmetric A */
+                          which is IC(0) for a symmetric A. ILU0, GS and IC0
+                          sweep whole colours (or line blocks) at once: A's
+                          (block) pattern must lie within each point's
+                          3^dim neighbourhood on the grid, with at most 32
+                          entries a row, else set-up returns MSRSB_EINVAL */
     int32_t pre, post; /* enable the pre / post stage of Alg. 4; for
                           MSRSB_SMOOTH_L1JAC the number of sweeps of each */
     int32_t krylov;    /* msrsb_krylov */
@@ -127,7 +131,9 @@ typedef struct {
                           x-lines, 2 lines high in y (and 2 deep in z), the
                           blocks coloured by the parity of their y (z) index
                           (2 colours in 2D, 4 in 3D), natural order inside a
-                          block; grids with nx <= 256 (wider ones use PARITY).
+                          block; grids with nx <= 256 and patterns whose rows
+                          hold at most 32 entries coupling at most one point
+                          along x and two along y and z (others use PARITY).
                           PARITY: points coloured by coordinate parity (4 / 8
                           colours), natural order inside a colour. The paper
                           eliminates in the natural order; both are parallel

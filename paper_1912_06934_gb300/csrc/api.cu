@@ -127,6 +127,7 @@ msrsb_status ilu0_apply(const msrsb_handle *h, T *ry, TZ *z, cudaStream_t s);
 bool lines_fit(const msrsb_grid *g);
 template <typename TF>
 msrsb_status lines_setup(msrsb_handle *h, TF *lu, cudaStream_t s);
+msrsb_status stencil_check(const msrsb_mat *A, const msrsb_grid *g, cudaStream_t s);
 template <typename T, typename TZ>
 msrsb_status lines_apply(const msrsb_handle *h, T *ry, TZ *z, cudaStream_t s);
 void lines_free(IluLines *L, cudaStream_t s);
@@ -201,6 +202,9 @@ static msrsb_status setup_smoother(msrsb_handle *h, cudaStream_t s) {
         h->a_lo = alo;
     }
     const bool ilu = h->opts.smoother == MSRSB_SMOOTH_ILU0 || (h->opts.smoother == MSRSB_SMOOTH_IC0 && bd == 1);
+    // the ordered smoothers sweep a colour (or line block) per launch
+    if (ilu || h->opts.smoother == MSRSB_SMOOTH_IC0 || h->opts.smoother == MSRSB_SMOOTH_GS)
+        MSRSB_TRY(stencil_check(&A, &h->grid, s));
     if (h->opts.smoother == MSRSB_SMOOTH_IC0 && bd == 3) {
         // block IC(0) in the node colour order, factors in A's block pattern
         T *lu = nullptr, *uinv = nullptr;

@@ -261,19 +261,6 @@ __global__ void __launch_bounds__(kPlaneThreads) plane_factor_kernel(PlaneGeom G
     }
 }
 
-// Asynchronous global -> shared copies (cp.async) for the staged solve; the
-// waits are the hardware's group waits.
-__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-
 // Application w = A_c^-1 v through the plane factors. vc, wc: FP64 [np*m]
 // in coarse dof order; wc32 (nullable) an FP32 copy of w. Steps
 // s = 0 .. 2 np - 2: forward planes k = s, then backward planes
@@ -332,7 +319,7 @@ __global__ void __launch_bounds__(kPlaneThreads) plane_solve_kernel(PlaneGeom G,
     pdl_prologue();
     for (int st = 0; st < nsteps; ++st) {
         const int buf = st & 1;
-        cp_async_wait1();
+        cp_async_wait<1>();
         __syncthreads();
         const double *Mrows = stage ? mat + (long)buf * rw * m : nullptr;
         if (st < np) {  // ---- forward: y_k = X_k Pi_k (v_k - L_k y_{k-1}) ----

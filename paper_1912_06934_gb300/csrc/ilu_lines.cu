@@ -25,7 +25,6 @@
 
 namespace msrsb {
 
-constexpr int kLinesMaxCpl = 8;  // x-chunks of 32 points per line: nx <= 256
 
 void diag_pos_launch(int n, const int32_t *rowptr, const int32_t *colidx, int32_t *dpos, int *status, cudaStream_t s);
 
@@ -58,9 +57,8 @@ constexpr int kLBatch = 8;
 // (as a product with the stored 1 / u_kk), then every later entry (i, j) that
 // row k also holds gets a_ij -= l_ik u_kj.
 template <typename TF>
-__device__ void lines_eliminate(int i, int plo, int phi, bool last, const int32_t *__restrict__ rowptr,
-                                const int32_t *__restrict__ colidx, const int32_t *__restrict__ pos,
-                                const int32_t *__restrict__ dpos, TF *__restrict__ lu, TF *__restrict__ rdiag,
+__device__ void lines_eliminate(int i, int phi, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                                const int32_t *__restrict__ pos, TF *__restrict__ lu, const TF *__restrict__ rdiag,
                                 int *__restrict__ status, int32_t (*kc)[32], TF (*kv)[32]) {
     const int lane = threadIdx.x & 31;
     const int b = rowptr[i], len = rowptr[i + 1] - b;
@@ -73,10 +71,8 @@ __device__ void lines_eliminate(int i, int plo, int phi, bool last, const int32_
     const int pj = mine ? pos[j] : INT_MAX;
     const int pi_ = pos[i];
     TF a = mine ? lu[b + lane] : TF(0);
-    // this call eliminates the earlier entries with positions in
-    // [plo, min(pos[i], phi)); `last`: the row is then final and its 1 / u_ii
-    // is stored
-    const bool lower = mine && pj < min(pi_, phi) && pj >= plo;
+    // this call eliminates the earlier entries with positions below phi
+    const bool lower = mine && pj < min(pi_, phi);
     int rank = 0;  // place of this lower entry in the position order
     for (int o = 0; o < 32; ++o) {
         const int po = __shfl_sync(0xffffffffu, pj, o);
@@ -127,14 +123,6 @@ __device__ void lines_eliminate(int i, int plo, int phi, bool last, const int32_
         __syncwarp();  // the next batch overwrites the staged rows
     }
     if (mine) lu[b + lane] = a;
-    if (last) {
-        const int dq = dpos[i] - b;
-        const TF uii = __shfl_sync(0xffffffffu, a, dq);
-        if (lane == 0) {
-            if (uii == TF(0) || !isfinite((double)uii)) atomicCAS(status, 0, 1 + i);
-            rdiag[i] = TF(1) / uii;
-        }
-    }
     __syncwarp();
 }
 
@@ -145,41 +133,149 @@ template <typename TF>
 __global__ void __launch_bounds__(128) lines_factor_off_kernel(int c0, int cnt, const int32_t *__restrict__ rows,
                                                                const int32_t *__restrict__ rowptr,
                                                                const int32_t *__restrict__ colidx,
-                                                               const int32_t *__restrict__ pos,
-                                                               const int32_t *__restrict__ dpos, TF *__restrict__ lu,
-                                                               TF *__restrict__ rdiag, int *__restrict__ status) {
+                                                               const int32_t *__restrict__ pos, TF *__restrict__ lu,
+                                                               const TF *__restrict__ rdiag,
+                                                               int *__restrict__ status) {
     __shared__ int32_t s_kc[4][kLBatch][32];
     __shared__ TF s_kv[4][kLBatch][32];
     const int w = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5), q = threadIdx.x >> 5;
     if (w >= cnt) return;  // whole warps leave together
     const int i = rows[c0 + w];
-    lines_eliminate<TF>(i, 0, c0, false, rowptr, colidx, pos, dpos, lu, rdiag, status, s_kc[q], s_kv[q]);
+    lines_eliminate<TF>(i, c0, rowptr, colidx, pos, lu, rdiag, status, s_kc[q], s_kv[q]);
 }
 
-// Phase 2 of one colour: the in-block earlier entries (positions from c0 on).
-// CTA b0 + blockIdx.x handles one block, warp q its line q; at time step T
-// warp q finishes point x = T - 2 q of its line.
+// Phase 2 of one colour: the in-block earlier entries. CTA b0 + blockIdx.x
+// handles one block, warp q its line q; at time step T warp q finishes point
+// x = T - 2 q of its line. With couplings reaching at most one point along x,
+// point (q, x) needs the points (q', x - 1 .. x + 1) of the lines q' < q
+// (finished at steps up to T - 1) and (q, x - 1). A point's row is final
+// once finished and is then needed for at most 2 nsub more steps, so each
+// line keeps its last kRing rows in shared memory: a row is copied in
+// (cp.async) kAhead steps before its turn and written through to global
+// memory when finished. In-block tests come from the grid position of the
+// columns (the order's key), so no position gather sits on the critical path.
+constexpr int kRing = 16, kAhead = 4, kPivChunk = 12, kLinesMaxNx = 256;
+
 template <typename TF>
-__global__ void __launch_bounds__(128) lines_factor_kernel(int c0, int b0, const int32_t *__restrict__ blk_start,
-                                                           const int32_t *__restrict__ blk_nsub, int nx,
-                                                           const int32_t *__restrict__ rows,
-                                                           const int32_t *__restrict__ rowptr,
-                                                           const int32_t *__restrict__ colidx,
-                                                           const int32_t *__restrict__ pos,
-                                                           const int32_t *__restrict__ dpos, TF *__restrict__ lu,
-                                                           TF *__restrict__ rdiag, int *__restrict__ status) {
-    __shared__ int32_t s_kc[4][kLBatch][32];
-    __shared__ TF s_kv[4][kLBatch][32];
-    const int b = b0 + blockIdx.x, q = threadIdx.x >> 5;
-    const int start = blk_start[b], nsub = blk_nsub[b];
-    const int steps = nx + 2 * (nsub - 1);
-    for (int T = 0; T < steps; ++T) {
-        const int x = T - 2 * q;
-        if (q < nsub && x >= 0 && x < nx)
-            lines_eliminate<TF>(rows[start + q * nx + x], c0, INT_MAX, true, rowptr, colidx, pos, dpos, lu, rdiag,
-                                status, s_kc[q], s_kv[q]);
-        __syncthreads();  // points of this step are final before the next step reads them
+__global__ void __launch_bounds__(128) lines_factor_ring_kernel(
+    int c, int b0, const int32_t *__restrict__ blk_start, const int32_t *__restrict__ blk_nsub, int dim, int nx,
+    int ny, const int32_t *__restrict__ rows, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+    TF *__restrict__ lu, TF *__restrict__ rdiag, int *__restrict__ status) {
+    __shared__ TF s_val[4][kRing][32];
+    __shared__ int32_t s_col[4][kRing][32];
+    __shared__ TF s_rd[4][kRing];
+    __shared__ int32_t s_ri[4][kLinesMaxNx], s_rb[4][kLinesMaxNx], s_rl[4][kLinesMaxNx];
+    const int b = b0 + blockIdx.x, q = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int st = blk_start[b], nsub = blk_nsub[b];
+    for (int t = threadIdx.x; t < nsub * nx; t += blockDim.x) {
+        const int i = rows[st + t], rb = rowptr[i];
+        s_ri[t / nx][t % nx] = i;
+        s_rb[t / nx][t % nx] = rb;
+        s_rl[t / nx][t % nx] = rowptr[i + 1] - rb;
     }
+    __syncthreads();
+    const int y0 = ((s_ri[0][0] / nx) % ny) & ~1;
+    const int nyb = min(2, ny - y0);  // lines of the block along y
+    int yq = 0, zq = 0;
+    if (q < nsub) {
+        const int r = s_ri[q][0] / nx;
+        yq = r % ny;
+        zq = dim == 3 ? r / ny : 0;
+    }
+    const int kin_base = ((yq & 1) | ((zq & 1) << 1)) * nx;  // in-block order key of (q, 0)
+    const int steps = nx + 2 * (nsub - 1);
+    for (int T = -kAhead; T < steps; ++T) {
+        if (q < nsub) {
+            const int xl = T - 2 * q + kAhead;
+            if (xl >= 0 && xl < nx && lane < s_rl[q][xl]) {
+                const int e = s_rb[q][xl] + lane;
+                cp_async4(&s_col[q][xl & (kRing - 1)][lane], colidx + e);
+                cp_async_val(&s_val[q][xl & (kRing - 1)][lane], lu + e);
+            }
+        }
+        cp_async_commit();
+        if (T < 0) continue;  // uniform over the CTA
+        cp_async_wait<kAhead>();
+        const int x = T - 2 * q;
+        if (q < nsub && x >= 0 && x < nx) {
+            const int slot = x & (kRing - 1);
+            const int i = s_ri[q][x], len = s_rl[q][x];
+            const bool mine = lane < len;
+            const int j = mine ? s_col[q][slot][lane] : -1;
+            TF a = mine ? s_val[q][slot][lane] : TF(0);
+            int xj = 0, yj = 0, zj = 0;
+            if (mine) {
+                xj = j % nx;
+                const int r = j / nx;
+                yj = r % ny;
+                zj = dim == 3 ? r / ny : 0;
+            }
+            const bool inb = mine && (yj >> 1) == (yq >> 1) && (zj >> 1) == (zq >> 1);
+            const int kin_j = ((yj & 1) | ((zj & 1) << 1)) * nx + xj;
+            const int colj = ((yj >> 1) & 1) | (dim == 3 ? (((zj >> 1) & 1) << 1) : 0);
+            const bool piv = inb && kin_j < kin_base + x;
+            int rank = 0;  // place of this pivot in the order
+            for (int o = 0; o < 32; ++o) {
+                const int ko = __shfl_sync(0xffffffffu, kin_j, o);
+                const bool po = __shfl_sync(0xffffffffu, piv, o);
+                rank += (piv && po && ko < kin_j) ? 1 : 0;
+            }
+            const int np = __popc(__ballot_sync(0xffffffffu, piv));
+            for (int t0 = 0; t0 < np; t0 += kPivChunk) {
+                // the chunk's pivot rows are final: look up every match first
+                TF u[kPivChunk], rk[kPivChunk];
+                int ql[kPivChunk];
+#pragma unroll
+                for (int t = 0; t < kPivChunk; ++t) {
+                    u[t] = TF(0);
+                    rk[t] = TF(0);
+                    ql[t] = 0;
+                    if (t0 + t < np) {
+                        const unsigned bm = __ballot_sync(0xffffffffu, piv && rank == t0 + t);
+                        const int qq = __ffs(bm) - 1;
+                        ql[t] = qq;
+                        const int kin_k = __shfl_sync(0xffffffffu, kin_j, qq);
+                        const int xk = __shfl_sync(0xffffffffu, xj, qq);
+                        const int yk = __shfl_sync(0xffffffffu, yj, qq);
+                        const int zk = __shfl_sync(0xffffffffu, zj, qq);
+                        const int lk = (yk & 1) + (zk & 1) * nyb, sk = xk & (kRing - 1);
+                        const int lenk = s_rl[lk][xk];
+                        rk[t] = s_rd[lk][sk];
+                        const bool later = mine && (inb ? kin_j > kin_k : colj > c);
+                        const int32_t *rowk = s_col[lk][sk];
+                        int p = 0;  // entries of row k below column j
+#pragma unroll
+                        for (int w = 16; w >= 1; w >>= 1)
+                            if (p + w - 1 < lenk && rowk[p + w - 1] < j) p += w;
+                        if (later && p < lenk && rowk[p] == j) u[t] = s_val[lk][sk][p];
+                    }
+                }
+#pragma unroll
+                for (int t = 0; t < kPivChunk; ++t) {
+                    if (t0 + t < np) {
+                        const TF lik = __shfl_sync(0xffffffffu, a, ql[t]) * rk[t];
+                        if (lane == ql[t]) a = lik;
+                        else a = a - lik * u[t];
+                    }
+                }
+            }
+            if (mine) {
+                s_val[q][slot][lane] = a;
+                lu[s_rb[q][x] + lane] = a;
+            }
+            const unsigned dm = __ballot_sync(0xffffffffu, mine && j == i);
+            const TF uii = __shfl_sync(0xffffffffu, a, dm ? __ffs(dm) - 1 : 0);
+            if (lane == 0) {
+                const bool bad = !dm || uii == TF(0) || !isfinite((double)uii);
+                if (bad) atomicCAS(status, 0, 1 + i);
+                const TF rd = bad ? TF(0) : TF(1) / uii;
+                s_rd[q][slot] = rd;
+                rdiag[i] = rd;
+            }
+        }
+        __syncthreads();  // the step's rows are final before the next step reads them
+    }
+    cp_async_wait<0>();
 }
 
 // ---- factors for the sweeps -------------------------------------------------------------
@@ -201,29 +297,39 @@ __device__ __forceinline__ int block_first_row(int i, int nx, int ny) {
     return nx * ((y & ~1) + ny * (z & ~1));
 }
 
-__global__ void lines_width_kernel(int n, int nx, int ny, const int32_t *__restrict__ rowptr,
-                                   const int32_t *__restrict__ colidx, const int32_t *__restrict__ pos,
-                                   const int32_t *__restrict__ ccol, int *__restrict__ w) {
+// Per colour, the widest row of each of the four parts (off-block / in-block,
+// lower / upper): a maximum in shared memory per CTA, then one global atomic
+// per part and colour.
+__global__ void __launch_bounds__(256) lines_width_kernel(int n, int nx, int ny, const int32_t *__restrict__ rowptr,
+                                                          const int32_t *__restrict__ colidx,
+                                                          const int32_t *__restrict__ pos,
+                                                          const int32_t *__restrict__ ccol, int *__restrict__ w) {
+    __shared__ int s_w[16];
+    if (threadIdx.x < 16) s_w[threadIdx.x] = 0;
+    __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int p = pos[i], x = i % nx;
-    int nl = 0, nu = 0, nli = 0, nui = 0;
-    for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
-        const int k = colidx[e], pk = pos[k];
-        if (pk < p && !(k == i - 1 && x > 0)) {
-            if (same_block(i, k, nx, ny)) ++nli;
-            else ++nl;
+    if (i < n) {
+        const int p = pos[i], x = i % nx;
+        int nl = 0, nu = 0, nli = 0, nui = 0;
+        for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+            const int k = colidx[e], pk = pos[k];
+            if (pk < p && !(k == i - 1 && x > 0)) {
+                if (same_block(i, k, nx, ny)) ++nli;
+                else ++nl;
+            }
+            if (pk > p && !(k == i + 1 && x < nx - 1)) {
+                if (same_block(i, k, nx, ny)) ++nui;
+                else ++nu;
+            }
         }
-        if (pk > p && !(k == i + 1 && x < nx - 1)) {
-            if (same_block(i, k, nx, ny)) ++nui;
-            else ++nu;
-        }
+        const int c = ccol[i];
+        atomicMax(s_w + c, nl);
+        atomicMax(s_w + 4 + c, nu);
+        atomicMax(s_w + 8 + c, nli);
+        atomicMax(s_w + 12 + c, nui);
     }
-    const int c = ccol[i];
-    atomicMax(w + c, nl);
-    atomicMax(w + 4 + c, nu);
-    atomicMax(w + 8 + c, nli);
-    atomicMax(w + 12 + c, nui);
+    __syncthreads();
+    if (threadIdx.x < 16 && s_w[threadIdx.x] > 0) atomicMax(w + threadIdx.x, s_w[threadIdx.x]);
 }
 
 template <typename T>
@@ -467,10 +573,13 @@ __global__ void __launch_bounds__(1024) lines_sweep_kernel(
 
 // ---- host side ---------------------------------------------------------------------------------
 
-bool lines_fit(const msrsb_grid *g) { return g->nx >= 1 && g->nx <= 32 * kLinesMaxCpl && (g->dim == 2 || g->dim == 3); }
+bool lines_fit(const msrsb_grid *g) { return g->nx >= 1 && g->nx <= kLinesMaxNx && (g->dim == 2 || g->dim == 3); }
 
 // Order, block table and ILU(0) factors of a scalar operator in the
 // line-block order; lu holds A's values (TF) on entry and is overwritten.
+// A's pattern lies within every point's 3^dim neighbourhood (stencil_check):
+// blocks of one colour are then uncoupled and a point couples to its line
+// neighbours x - 1, x + 1 only.
 template <typename TF>
 msrsb_status lines_setup(msrsb_handle *h, TF *lu, cudaStream_t s) {
     const msrsb_mat &A = h->A;
@@ -542,12 +651,12 @@ msrsb_status lines_setup(msrsb_handle *h, TF *lu, cudaStream_t s) {
         const int cnt = L.cptr[c + 1] - L.cptr[c];
         if (c > 0) {
             lines_factor_off_kernel<TF><<<ceil_div((long)cnt * 32, 128), 128, 0, s>>>(
-                L.cptr[c], cnt, L.rows, A.rowptr, A.colidx, h->pos_of, dpos, lu, rdiag, status);
+                L.cptr[c], cnt, L.rows, A.rowptr, A.colidx, h->pos_of, lu, rdiag, status);
             MSRSB_LAUNCHED("lines_factor_off_kernel");
         }
-        lines_factor_kernel<TF><<<nb, 128, 0, s>>>(L.cptr[c], L.bptr[c], L.blk_start, L.blk_nsub, nx, L.rows,
-                                                   A.rowptr, A.colidx, h->pos_of, dpos, lu, rdiag, status);
-        MSRSB_LAUNCHED("lines_factor_kernel");
+        lines_factor_ring_kernel<TF><<<nb, 128, 0, s>>>(c, L.bptr[c], L.blk_start, L.blk_nsub, dim, nx, ny, L.rows,
+                                                        A.rowptr, A.colidx, lu, rdiag, status);
+        MSRSB_LAUNCHED("lines_factor_ring_kernel");
     }
     int hs = 0;
     MSRSB_CUDA(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, s));

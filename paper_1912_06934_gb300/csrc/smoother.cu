@@ -10,6 +10,45 @@
 
 namespace msrsb {
 
+// ---- pattern check ----------------------------------------------------------
+//
+// The ordered smoothers need A's (node) pattern inside every point's 3^dim
+// neighbourhood on the grid, with at most 32 entries a row: points of one
+// colour (or line blocks of one colour) are then uncoupled. flag bit 0: a
+// coupling beyond the neighbourhood; bit 1: a row of more than 32 entries.
+__global__ void __launch_bounds__(256) stencil_check_kernel(int n, int dim, int nx, int ny,
+                                                            const int32_t *__restrict__ rowptr,
+                                                            const int32_t *__restrict__ colidx, int *__restrict__ flag) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int bad = 0;
+    if (i < n) {
+        const int xi = i % nx, yi = (i / nx) % ny, zi = dim == 3 ? i / (nx * ny) : 0;
+        if (rowptr[i + 1] - rowptr[i] > 32) bad |= 2;
+        for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+            const int j = colidx[e];
+            const int xj = j % nx, yj = (j / nx) % ny, zj = dim == 3 ? j / (nx * ny) : 0;
+            if (abs(xj - xi) > 1 || abs(yj - yi) > 1 || abs(zj - zi) > 1) bad |= 1;
+        }
+    }
+    bad = __reduce_or_sync(0xffffffffu, bad);
+    if (bad && (threadIdx.x & 31) == 0) atomicOr(flag, bad);
+}
+
+msrsb_status stencil_check(const msrsb_mat *A, const msrsb_grid *g, cudaStream_t s) {
+    const int n = A->nrows;
+    int *flag = nullptr, hf = 0;
+    MSRSB_TRY(dalloc(&flag, 1, s));
+    MSRSB_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), s));
+    stencil_check_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, g->dim, g->nx, g->ny, A->rowptr, A->colidx, flag);
+    MSRSB_LAUNCHED("stencil_check_kernel");
+    MSRSB_CUDA(cudaMemcpyAsync(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MSRSB_CUDA(cudaStreamSynchronize(s));
+    dfree(flag, s);
+    if (hf & 1) return fail(MSRSB_EINVAL, "the smoother needs A's pattern within each point's 3^%d neighbourhood", g->dim);
+    if (hf & 2) return fail(MSRSB_EINVAL, "the smoother needs rows of at most 32 (block) entries");
+    return MSRSB_OK;
+}
+
 // ---- colour classes ---------------------------------------------------------
 
 __global__ void iota_kernel(int n, int32_t *__restrict__ v) {

@@ -226,6 +226,29 @@ def test_ilu0_orderings_match_oracle(M, case, ordering):
     h.destroy()
 
 
+@pytest.mark.parametrize("ordering", [0, 1])
+def test_ordered_smoothers_reject_wide_patterns(M, ordering):
+    """A coupling two points apart along x (outside the 3^d neighbourhood)
+    would couple points of one colour: set-up refuses it with MSRSB_EINVAL for
+    the ILU(0) smoother in either order, and l1-Jacobi (pointwise) accepts it."""
+    B = M.msrsb
+    c = darcy_2d_case(n=24, H=8)
+    Ah = sp.csr_matrix((c["data"], c["indices"], c["indptr"]))
+    n = Ah.shape[0]
+    i = np.arange(n)
+    far = (i % 24) < 22
+    W = sp.csr_matrix((np.full(far.sum(), -1e-3), (i[far], i[far] + 2)), shape=(n, n))
+    Aw = sp.csr_matrix(Ah + W + W.T + sp.diags(np.full(n, 2e-3)))
+    Aw.sort_indices()
+    A = M.Mat.from_host(Aw.indptr, Aw.indices, Aw.data)
+    g = M.grid(c["dims"], c["H"])
+    with pytest.raises(M.MsrsbError) as e:
+        M.msrsb_setup(A, g, M.opts(ordering=ordering))
+    assert e.value.status == B.MSRSB_EINVAL and "neighbourhood" in str(e.value)
+    h = M.msrsb_setup(A, g, M.opts(smoother=B.MSRSB_SMOOTH_L1JAC))
+    h.destroy()
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_paper_rough_grid_mpfa_case(M, prec):
     """The 2D MPFA-O test of Sec. 3.2 (100 x 100 rough cells on 20 m x 150 m,
