@@ -270,8 +270,14 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
     MSRSB_TRY(partition_launch(&h->grid, h->part, h->cnode, h->p_ids, h->skel, h->colour, s));
     MSRSB_TRY(mark(1));
     // the smoother set-up (independent of P) on a side stream, from a second
-    // host thread, while this thread builds the basis
-    if (!h->side) MSRSB_CUDA(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+    // host thread, while this thread builds the basis. The side stream has the
+    // highest priority: its kernels are latency-bound chains of few CTAs that
+    // would otherwise wait behind the basis kernels, which fill every SM.
+    if (!h->side) {
+        int least = 0, greatest = 0;
+        MSRSB_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        MSRSB_CUDA(cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, greatest));
+    }
     cudaEvent_t fork = nullptr, join = nullptr;
     MSRSB_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
     MSRSB_CUDA(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));

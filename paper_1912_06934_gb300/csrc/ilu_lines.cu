@@ -73,13 +73,13 @@ __device__ void lines_eliminate(int i, int phi, const int32_t *__restrict__ rowp
     TF a = mine ? lu[b + lane] : TF(0);
     // this call eliminates the earlier entries with positions below phi
     const bool lower = mine && pj < min(pi_, phi);
+    const unsigned lm = __ballot_sync(0xffffffffu, lower);
+    const int nlow = __popc(lm);
     int rank = 0;  // place of this lower entry in the position order
-    for (int o = 0; o < 32; ++o) {
-        const int po = __shfl_sync(0xffffffffu, pj, o);
-        const bool lo = __shfl_sync(0xffffffffu, lower, o);
-        rank += (lower && lo && po < pj) ? 1 : 0;
+    for (unsigned m = lm; m; m &= m - 1) {
+        const int po = __shfl_sync(0xffffffffu, pj, __ffs(m) - 1);
+        rank += (lower && po < pj) ? 1 : 0;
     }
-    const int nlow = __popc(__ballot_sync(0xffffffffu, lower));
     int kb = 0, kl = 0;
     TF rd = TF(0);
     if (lower) {
@@ -214,46 +214,43 @@ __global__ void __launch_bounds__(128) lines_factor_ring_kernel(
             const int kin_j = ((yj & 1) | ((zj & 1) << 1)) * nx + xj;
             const int colj = ((yj >> 1) & 1) | (dim == 3 ? (((zj >> 1) & 1) << 1) : 0);
             const bool piv = inb && kin_j < kin_base + x;
-            int rank = 0;  // place of this pivot in the order
-            for (int o = 0; o < 32; ++o) {
-                const int ko = __shfl_sync(0xffffffffu, kin_j, o);
-                const bool po = __shfl_sync(0xffffffffu, piv, o);
-                rank += (piv && po && ko < kin_j) ? 1 : 0;
-            }
-            const int np = __popc(__ballot_sync(0xffffffffu, piv));
+            // Inside one block the key (z & 1, y & 1, x) orders the points as
+            // their indices do, so the pivots come in lane (column) order.
+            const unsigned pm = __ballot_sync(0xffffffffu, piv);
+            const int np = __popc(pm);
+            const bool later_in = inb;  // in-block: later than pivot k when kin_j > kin_k
+            const bool later_off = mine && !inb && colj > c;
+            unsigned rest = pm;
             for (int t0 = 0; t0 < np; t0 += kPivChunk) {
-                // the chunk's pivot rows are final: look up every match first
+                // every match of the chunk first (the pivot rows are final), then
+                // the eliminations in order
                 TF u[kPivChunk], rk[kPivChunk];
                 int ql[kPivChunk];
 #pragma unroll
                 for (int t = 0; t < kPivChunk; ++t) {
-                    u[t] = TF(0);
-                    rk[t] = TF(0);
-                    ql[t] = 0;
-                    if (t0 + t < np) {
-                        const unsigned bm = __ballot_sync(0xffffffffu, piv && rank == t0 + t);
-                        const int qq = __ffs(bm) - 1;
-                        ql[t] = qq;
-                        const int kin_k = __shfl_sync(0xffffffffu, kin_j, qq);
-                        const int xk = __shfl_sync(0xffffffffu, xj, qq);
-                        const int yk = __shfl_sync(0xffffffffu, yj, qq);
-                        const int zk = __shfl_sync(0xffffffffu, zj, qq);
-                        const int lk = (yk & 1) + (zk & 1) * nyb, sk = xk & (kRing - 1);
-                        const int lenk = s_rl[lk][xk];
-                        rk[t] = s_rd[lk][sk];
-                        const bool later = mine && (inb ? kin_j > kin_k : colj > c);
-                        const int32_t *rowk = s_col[lk][sk];
-                        int p = 0;  // entries of row k below column j
+                    const bool on = rest != 0;  // uniform
+                    const int qq = on ? __ffs(rest) - 1 : 0;
+                    rest &= rest - 1;
+                    ql[t] = on ? qq : -1;
+                    const int kin_k = __shfl_sync(0xffffffffu, kin_j, qq);
+                    const int xk = __shfl_sync(0xffffffffu, xj, qq);
+                    const int yk = __shfl_sync(0xffffffffu, yj, qq);
+                    const int zk = __shfl_sync(0xffffffffu, zj, qq);
+                    const int lk = on ? (yk & 1) + (zk & 1) * nyb : q, sk = on ? xk & (kRing - 1) : slot;
+                    const int lenk = on ? s_rl[lk][xk] : 0;
+                    rk[t] = on ? s_rd[lk][sk] : TF(0);
+                    const bool later = on && (later_off || (later_in && kin_j > kin_k));
+                    const int32_t *rowk = s_col[lk][sk];
+                    int p = 0;  // entries of row k below column j
 #pragma unroll
-                        for (int w = 16; w >= 1; w >>= 1)
-                            if (p + w - 1 < lenk && rowk[p + w - 1] < j) p += w;
-                        if (later && p < lenk && rowk[p] == j) u[t] = s_val[lk][sk][p];
-                    }
+                    for (int w = 16; w >= 1; w >>= 1)
+                        if (p + w - 1 < lenk && rowk[p + w - 1] < j) p += w;
+                    u[t] = (later && p < lenk && rowk[p] == j) ? s_val[lk][sk][p] : TF(0);
                 }
 #pragma unroll
                 for (int t = 0; t < kPivChunk; ++t) {
-                    if (t0 + t < np) {
-                        const TF lik = __shfl_sync(0xffffffffu, a, ql[t]) * rk[t];
+                    const TF lik = __shfl_sync(0xffffffffu, a, ql[t] < 0 ? 0 : ql[t]) * rk[t];
+                    if (ql[t] >= 0) {  // uniform
                         if (lane == ql[t]) a = lik;
                         else a = a - lik * u[t];
                     }
