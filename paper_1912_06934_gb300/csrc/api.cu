@@ -294,11 +294,13 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
     std::promise<msrsb_status> tr_done;
     std::future<msrsb_status> tr_status = tr_done.get_future();
     std::string tr_err;
-    // The smoother set-up starts with the basis build: its factorisations are
-    // latency-bound chains of few CTAs, which on the high-priority side stream
-    // take SM slots as the bandwidth-bound smoothing passes free them. The
-    // main thread hands over an event recorded after the partition, or
-    // nullptr when it leaves early.
+    // The smoother set-up is held back until the main stream reaches the
+    // coarse factorisation: started with the basis build, its latency-bound
+    // factorisation kernels take SM slots from the bandwidth-bound smoothing
+    // passes and slow them by more than they save (measured at 64^3 and
+    // 128^3), while the coarse factorisation runs on one thread-block cluster
+    // and leaves the other SMs idle. The main thread hands over an event
+    // recorded at that point, or nullptr when it leaves early.
     std::promise<cudaEvent_t> go;
     std::future<cudaEvent_t> go_at = go.get_future();
     cudaEvent_t go_ev = nullptr;
@@ -338,8 +340,6 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
         }
         ~Release() { (*this)(nullptr); }
     } release{go};
-    MSRSB_CUDA(cudaEventRecord(go_ev, s));
-    release(go_ev);
     // filtered operator(s) streamed as sliced ELL, then Alg. 1 per component
     T *P = nullptr;
     MSRSB_TRY(dalloc(&P, nW * bd, s));
@@ -405,6 +405,8 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
         if (Pl != P) dfree(Pl, s);
     }
     MSRSB_TRY(mark(3));
+    MSRSB_CUDA(cudaEventRecord(go_ev, s));
+    release(go_ev);
     if (planes_fit(h->grid.dim, h->nb, bd)) {
         MSRSB_TRY(plane_factor(h->grid.dim, h->nb, bd, h->Acs, &h->planes, s));
         if (h->nC <= kDenseCoarseMax) {

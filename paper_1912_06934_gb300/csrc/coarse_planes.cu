@@ -89,13 +89,13 @@ __global__ void __launch_bounds__(kPlaneThreads) plane_factor_kernel(PlaneGeom G
     const int tid = threadIdx.x;
     extern __shared__ double sm[];
     double *Sown = sm;                       // own columns of S_k, column-major [cw][m]
-    double *F = Sown + (long)cw * m;         // panel columns [cw][m]: published (owner) or copied in
-    double *Xs = F + (long)cw * m;           // solved pivot rows of the own columns [cw][cw]
-    int *piv_hist = (int *)(Xs + (long)cw * cw);  // pivot row of every step [m]
+    double *fbuf = Sown + (long)cw * m;      // published pivot column, double buffered [2][m]
+    double *floc = fbuf + 2 * m;             // local copy of the pivot column [m]
+    int *piv_hist = (int *)(floc + m);       // pivot row of every step [m]
     int *pil = piv_hist + m;                 // gather pi [m]
     int *pinv = pil + m;                     // inverse of pi [m]
-    __shared__ double s_iv[kPlaneMaxCols], s_xk[kPlaneMaxCols];  // 1 / pivot of the panel's steps
-    __shared__ int s_pv[kPlaneMaxCols], s_bad;                     // pivot rows of the panel's steps
+    __shared__ double s_inv[2], s_xk[kPlaneMaxCols];
+    __shared__ int s_p[2], s_bad[2];
     __shared__ double s_best[8];
     __shared__ int s_idx[8];
     for (int k = 0; k < G.np; ++k) {
@@ -119,155 +119,97 @@ __global__ void __launch_bounds__(kPlaneThreads) plane_factor_kernel(PlaneGeom G
             Sown[(long)jl * m + i] = v;
         }
         __syncthreads();
-        // ---- Gauss-Jordan with partial pivoting, one panel of columns at a time ----
-        // Panel P is CTA P's column block [k0, k0 + nb). Its owner runs the
-        // panel's nb steps on its own columns alone and keeps each step's
-        // pivot column f_s (with the panel's later row interchanges applied)
-        // in F. For any other column c the panel's steps then amount to: the
-        // row interchanges, x = L^-1 c[k0 .. k0+nb) with L[s][t] = f_t[k0+s]
-        // (t <= s), then c[i] -= sum_t f_t[i] x_t off the panel rows and
-        // c[k0+s] = x_s - sum_{t>s} f_t[k0+s] x_t on them: one cluster
-        // barrier per panel instead of one per step.
-        for (int P = 0; P < nct; ++P) {
-            const int k0 = P * cw, nb = min(m, k0 + cw) - k0;
-            if (nb <= 0) break;  // uniform
-            if (rank == P) {
-                if (tid == 0) s_bad = 0;
-                for (int sp = 0; sp < nb; ++sp) {
-                    const int kk = k0 + sp;
-                    double *col = Sown + (long)sp * m;
-                    // largest |col[i]|, kk <= i < m, ties to the lowest index
-                    long long best = -1;
-                    int bi = m;
-                    for (int i = kk + tid; i < m; i += kPlaneThreads) {
-                        const long long v = __double_as_longlong(col[i]) & 0x7fffffffffffffffLL;
-                        if (v > best) {
-                            best = v;
-                            bi = i;
-                        }
+        // ---- Gauss-Jordan with partial pivoting, one pivot per step ----
+        for (int kk = 0; kk < m; ++kk) {
+            const int owner = kk / cw, buf = kk & 1;
+            if (rank == owner) {
+                double *col = Sown + (long)(kk - c0) * m;
+                // largest |col[i]|, kk <= i < m, ties to the lowest index
+                long long best = -1;
+                int bi = m;
+                for (int i = kk + tid; i < m; i += kPlaneThreads) {
+                    const long long v = __double_as_longlong(col[i]) & 0x7fffffffffffffffLL;
+                    if (v > best) {
+                        best = v;
+                        bi = i;
                     }
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        const long long b2 = __shfl_xor_sync(0xffffffffu, best, o);
-                        const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
-                        if (b2 > best || (b2 == best && i2 < bi)) {
-                            best = b2;
-                            bi = i2;
-                        }
-                    }
-                    long long *sb = reinterpret_cast<long long *>(s_best);
-                    if ((tid & 31) == 0) {
-                        sb[tid >> 5] = best;
-                        s_idx[tid >> 5] = bi;
-                    }
-                    __syncthreads();
-                    if (tid == 0) {
-                        long long bb = sb[0];
-                        int bj = s_idx[0];
-                        for (int w = 1; w < kPlaneThreads / 32; ++w)
-                            if (sb[w] > bb || (sb[w] == bb && s_idx[w] < bj)) {
-                                bb = sb[w];
-                                bj = s_idx[w];
-                            }
-                        const double pv = bj < m ? col[bj] : 0.0;
-                        const int bad = (bj >= m || pv == 0.0 || !isfinite(pv)) ? 1 : 0;
-                        if (!bad && bj != kk) {
-                            const double t = col[kk];
-                            col[kk] = col[bj];
-                            col[bj] = t;
-                        }
-                        s_pv[sp] = bad ? kk : bj;
-                        s_iv[sp] = bad ? 0.0 : 1.0 / pv;
-                        piv_hist[kk] = s_pv[sp];
-                        if (bad) s_bad = 1 + kk;
-                    }
-                    __syncthreads();
-                    if (s_bad) break;  // uniform
-                    const int p = s_pv[sp];
-                    const double inv = s_iv[sp];
-                    for (int i = tid; i < m; i += kPlaneThreads) F[(long)sp * m + i] = col[i];
-                    if (tid < nb && tid != sp) {  // row interchange and scaled pivot-row entry, own column tid
-                        double *cj = Sown + (long)tid * m;
-                        double x = cj[kk];
-                        if (p != kk) {
-                            const double y = cj[p];
-                            cj[p] = x;
-                            x = y;
-                        }
-                        x *= inv;
-                        cj[kk] = x;
-                        s_xk[tid] = x;
-                    }
-                    if (tid < sp && p != kk) {  // the interchange on the recorded pivot columns
-                        double *ft = F + (long)tid * m;
-                        const double t = ft[kk];
-                        ft[kk] = ft[p];
-                        ft[p] = t;
-                    }
-                    __syncthreads();
-                    const double *fs = F + (long)sp * m;
-                    for (int idx = tid; idx < nb * m; idx += kPlaneThreads) {
-                        const int jl = idx / m, i = idx - jl * m;
-                        double *cj = Sown + (long)jl * m;
-                        if (jl == sp)
-                            cj[i] = i == kk ? inv : -fs[i] * inv;
-                        else if (i != kk)
-                            cj[i] = fma(-fs[i], s_xk[jl], cj[i]);
-                    }
-                    __syncthreads();
                 }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const long long b2 = __shfl_xor_sync(0xffffffffu, best, o);
+                    const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+                    if (b2 > best || (b2 == best && i2 < bi)) {
+                        best = b2;
+                        bi = i2;
+                    }
+                }
+                long long *sb = reinterpret_cast<long long *>(s_best);
+                if ((tid & 31) == 0) {
+                    sb[tid >> 5] = best;
+                    s_idx[tid >> 5] = bi;
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    long long bb = sb[0];
+                    int bj = s_idx[0];
+                    for (int w = 1; w < kPlaneThreads / 32; ++w)
+                        if (sb[w] > bb || (sb[w] == bb && s_idx[w] < bj)) {
+                            bb = sb[w];
+                            bj = s_idx[w];
+                        }
+                    const double pv = bj < m ? col[bj] : 0.0;
+                    const int bad = (bj >= m || pv == 0.0 || !isfinite(pv)) ? 1 : 0;
+                    if (!bad && bj != kk) {
+                        const double t = col[kk];
+                        col[kk] = col[bj];
+                        col[bj] = t;
+                    }
+                    s_p[buf] = bj < m ? bj : kk;
+                    s_bad[buf] = bad;
+                    s_inv[buf] = bad ? 0.0 : 1.0 / pv;
+                }
+                __syncthreads();
+                for (int i = tid; i < m; i += kPlaneThreads) fbuf[buf * m + i] = col[i];
             }
-            cluster.sync();  // the owner's panel (F, pivots, 1 / pivots) is published
-            const int bad = *cluster.map_shared_rank(&s_bad, P);
+            cluster.sync();  // the owner's pivot column is published
+            const int *op = cluster.map_shared_rank(s_p, owner);
+            const int *ob = cluster.map_shared_rank(s_bad, owner);
+            const double *oi = cluster.map_shared_rank(s_inv, owner);
+            const double *of = cluster.map_shared_rank(fbuf, owner) + buf * m;
+            const int p = op[buf], bad = ob[buf];
+            const double inv = oi[buf];
             if (bad) {
-                if (rank == 0 && tid == 0) *status = 1 + k * m + bad - 1;
+                if (rank == 0 && tid == 0) *status = 1 + k * m + kk;
                 cluster.sync();  // no CTA leaves while another may still read its shared memory
                 return;
             }
-            if (rank != P) {
-                const double *of = cluster.map_shared_rank(F, P);
-                const int *op = cluster.map_shared_rank(s_pv, P);
-                const double *oi = cluster.map_shared_rank(s_iv, P);
-                for (int idx = tid; idx < nb * m; idx += kPlaneThreads) F[idx] = of[idx];
-                if (tid < nb) {
-                    s_pv[tid] = op[tid];
-                    s_iv[tid] = oi[tid];
-                    piv_hist[k0 + tid] = op[tid];
-                }
-                __syncthreads();
-                if (tid < ncol) {  // own column tid: interchanges, then the panel rows solved
+            for (int i = tid; i < m; i += kPlaneThreads) floc[i] = of[i];
+            if (tid == 0) piv_hist[kk] = p;
+            if (tid < ncol) {  // row interchange and scaled pivot-row entry of every own column but kk
+                const int j = c0 + tid;
+                if (j != kk) {
                     double *cj = Sown + (long)tid * m;
-                    for (int sp = 0; sp < nb; ++sp) {
-                        const int kk = k0 + sp, p = s_pv[sp];
-                        if (p != kk) {
-                            const double t = cj[kk];
-                            cj[kk] = cj[p];
-                            cj[p] = t;
-                        }
+                    double x = cj[kk];
+                    if (p != kk) {
+                        const double y = cj[p];
+                        cj[p] = x;
+                        x = y;
                     }
-                    for (int sp = 0; sp < nb; ++sp) {
-                        double x = cj[k0 + sp];
-                        for (int t = 0; t < sp; ++t) x = fma(-F[(long)t * m + k0 + sp], Xs[t * cw + tid], x);
-                        Xs[sp * cw + tid] = x * s_iv[sp];
-                    }
+                    x *= inv;
+                    cj[kk] = x;
+                    s_xk[tid] = x;
                 }
-                __syncthreads();
-                for (int idx = tid; idx < ncol * m; idx += kPlaneThreads) {
-                    const int jl = idx / m, i = idx - jl * m;
-                    double *cj = Sown + (long)jl * m;
-                    const int sp = i - k0;
-                    double v;
-                    if (sp >= 0 && sp < nb) {
-                        v = Xs[sp * cw + jl];
-                        for (int t = sp + 1; t < nb; ++t) v = fma(-F[(long)t * m + i], Xs[t * cw + jl], v);
-                    } else {
-                        v = cj[i];
-                        for (int t = 0; t < nb; ++t) v = fma(-F[(long)t * m + i], Xs[t * cw + jl], v);
-                    }
-                    cj[i] = v;
-                }
-                __syncthreads();
             }
+            __syncthreads();
+            for (int idx = tid; idx < ncol * m; idx += kPlaneThreads) {
+                const int jl = idx / m, i = idx - jl * m;
+                double *cj = Sown + (long)jl * m;
+                if (c0 + jl == kk)
+                    cj[i] = i == kk ? inv : -floc[i] * inv;
+                else if (i != kk)
+                    cj[i] = fma(-floc[i], s_xk[jl], cj[i]);
+            }
+            __syncthreads();
         }
         // ---- the gather pi_k and its inverse (every CTA, from the pivot history) ----
         if (tid == 0) {
@@ -518,7 +460,7 @@ __global__ void __launch_bounds__(kPlaneThreads) plane_inverse_kernel(PlaneGeom 
 
 static size_t factor_smem(int m, int nct) {
     const int cw = (m + nct - 1) / nct;
-    return (2 * (size_t)cw * m + (size_t)cw * cw) * sizeof(double) + 3 * (size_t)m * sizeof(int);
+    return (size_t)cw * m * sizeof(double) + 3 * (size_t)m * sizeof(double) + 3 * (size_t)m * sizeof(int);
 }
 static size_t solve_smem(int m) { return 4 * (size_t)m * sizeof(double); }
 // with the staged copies (see plane_solve_kernel)
