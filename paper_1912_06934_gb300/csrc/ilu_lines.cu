@@ -154,7 +154,11 @@ __global__ void __launch_bounds__(128) lines_factor_off_kernel(int c0, int cnt, 
 // (cp.async) kAhead steps before its turn and written through to global
 // memory when finished. In-block tests come from the grid position of the
 // columns (the order's key), so no position gather sits on the critical path.
-constexpr int kRing = 16, kAhead = 4, kPivChunk = 12, kLinesMaxNx = 256;
+// A row's entries lie at distinct offsets of the 3^dim stencil, in column
+// order, so a finished row also keeps the mask of its offsets (bit
+// (dx + 1) + 3 (dy + 1) + 9 (dz + 1)): entry (k, j) of a pivot row k is then
+// found by a popcount of the mask below j's offset from k.
+constexpr int kRing = 16, kAhead = 4, kPivChunk = 4, kLinesMaxNx = 256;
 
 template <typename TF>
 __global__ void __launch_bounds__(128) lines_factor_ring_kernel(
@@ -164,6 +168,7 @@ __global__ void __launch_bounds__(128) lines_factor_ring_kernel(
     __shared__ TF s_val[4][kRing][32];
     __shared__ int32_t s_col[4][kRing][32];
     __shared__ TF s_rd[4][kRing];
+    __shared__ unsigned s_mask[4][kRing];
     __shared__ int32_t s_ri[4][kLinesMaxNx], s_rb[4][kLinesMaxNx], s_rl[4][kLinesMaxNx];
     const int b = b0 + blockIdx.x, q = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int st = blk_start[b], nsub = blk_nsub[b];
@@ -210,18 +215,19 @@ __global__ void __launch_bounds__(128) lines_factor_ring_kernel(
                 yj = r % ny;
                 zj = dim == 3 ? r / ny : 0;
             }
+            // this entry's stencil offset from row i (zero-based per axis)
+            const int ox = xj - x + 1, oy = yj - yq + 1, oz = zj - zq + 1;
+            const unsigned mask_i = __reduce_or_sync(0xffffffffu, mine ? 1u << (ox + 3 * oy + 9 * oz) : 0u);
             const bool inb = mine && (yj >> 1) == (yq >> 1) && (zj >> 1) == (zq >> 1);
             const int kin_j = ((yj & 1) | ((zj & 1) << 1)) * nx + xj;
             const int colj = ((yj >> 1) & 1) | (dim == 3 ? (((zj >> 1) & 1) << 1) : 0);
             const bool piv = inb && kin_j < kin_base + x;
             // Inside one block the key (z & 1, y & 1, x) orders the points as
             // their indices do, so the pivots come in lane (column) order.
-            const unsigned pm = __ballot_sync(0xffffffffu, piv);
-            const int np = __popc(pm);
             const bool later_in = inb;  // in-block: later than pivot k when kin_j > kin_k
             const bool later_off = mine && !inb && colj > c;
-            unsigned rest = pm;
-            for (int t0 = 0; t0 < np; t0 += kPivChunk) {
+            unsigned rest = __ballot_sync(0xffffffffu, piv);
+            while (rest) {  // uniform
                 // every match of the chunk first (the pivot rows are final), then
                 // the eliminations in order
                 TF u[kPivChunk], rk[kPivChunk];
@@ -232,20 +238,20 @@ __global__ void __launch_bounds__(128) lines_factor_ring_kernel(
                     const int qq = on ? __ffs(rest) - 1 : 0;
                     rest &= rest - 1;
                     ql[t] = on ? qq : -1;
-                    const int kin_k = __shfl_sync(0xffffffffu, kin_j, qq);
-                    const int xk = __shfl_sync(0xffffffffu, xj, qq);
-                    const int yk = __shfl_sync(0xffffffffu, yj, qq);
-                    const int zk = __shfl_sync(0xffffffffu, zj, qq);
+                    // pivot k: its offset from row i, hence its grid position
+                    const int kx = __shfl_sync(0xffffffffu, ox, qq), ky = __shfl_sync(0xffffffffu, oy, qq),
+                              kz = __shfl_sync(0xffffffffu, oz, qq);
+                    const int xk = x + kx - 1, yk = yq + ky - 1, zk = zq + kz - 1;
+                    const int kin_k = ((yk & 1) | ((zk & 1) << 1)) * nx + xk;
                     const int lk = on ? (yk & 1) + (zk & 1) * nyb : q, sk = on ? xk & (kRing - 1) : slot;
-                    const int lenk = on ? s_rl[lk][xk] : 0;
                     rk[t] = on ? s_rd[lk][sk] : TF(0);
-                    const bool later = on && (later_off || (later_in && kin_j > kin_k));
-                    const int32_t *rowk = s_col[lk][sk];
-                    int p = 0;  // entries of row k below column j
-#pragma unroll
-                    for (int w = 16; w >= 1; w >>= 1)
-                        if (p + w - 1 < lenk && rowk[p + w - 1] < j) p += w;
-                    u[t] = (later && p < lenk && rowk[p] == j) ? s_val[lk][sk][p] : TF(0);
+                    const unsigned mk = on ? s_mask[lk][sk] : 0u;
+                    // j's offset from k
+                    const int dx = ox - kx + 1, dy = oy - ky + 1, dz = oz - kz + 1;
+                    const bool near = dx >= 0 && dx <= 2 && dy >= 0 && dy <= 2 && dz >= 0 && dz <= 2;
+                    const int o = near ? dx + 3 * dy + 9 * dz : 0;
+                    const bool hit = on && near && (later_off || (later_in && kin_j > kin_k)) && ((mk >> o) & 1u);
+                    u[t] = hit ? s_val[lk][sk][__popc(mk & ((1u << o) - 1u))] : TF(0);
                 }
 #pragma unroll
                 for (int t = 0; t < kPivChunk; ++t) {
@@ -267,6 +273,7 @@ __global__ void __launch_bounds__(128) lines_factor_ring_kernel(
                 if (bad) atomicCAS(status, 0, 1 + i);
                 const TF rd = bad ? TF(0) : TF(1) / uii;
                 s_rd[q][slot] = rd;
+                s_mask[q][slot] = mask_i;
                 rdiag[i] = rd;
             }
         }

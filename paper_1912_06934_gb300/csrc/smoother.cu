@@ -13,9 +13,10 @@ namespace msrsb {
 // ---- pattern check ----------------------------------------------------------
 //
 // The ordered smoothers need A's (node) pattern inside every point's 3^dim
-// neighbourhood on the grid, with at most 32 entries a row: points of one
-// colour (or line blocks of one colour) are then uncoupled. flag bit 0: a
-// coupling beyond the neighbourhood; bit 1: a row of more than 32 entries.
+// neighbourhood on the grid, with at most 32 entries a row in ascending
+// column order: points of one colour (or line blocks of one colour) are then
+// uncoupled. flag bit 0: a coupling beyond the neighbourhood; bit 1: a row of
+// more than 32 entries; bit 2: columns not strictly ascending.
 __global__ void __launch_bounds__(256) stencil_check_kernel(int n, int dim, int nx, int ny,
                                                             const int32_t *__restrict__ rowptr,
                                                             const int32_t *__restrict__ colidx, int *__restrict__ flag) {
@@ -28,6 +29,7 @@ __global__ void __launch_bounds__(256) stencil_check_kernel(int n, int dim, int 
             const int j = colidx[e];
             const int xj = j % nx, yj = (j / nx) % ny, zj = dim == 3 ? j / (nx * ny) : 0;
             if (abs(xj - xi) > 1 || abs(yj - yi) > 1 || abs(zj - zi) > 1) bad |= 1;
+            if (e > rowptr[i] && colidx[e - 1] >= j) bad |= 4;
         }
     }
     bad = __reduce_or_sync(0xffffffffu, bad);
@@ -46,6 +48,7 @@ msrsb_status stencil_check(const msrsb_mat *A, const msrsb_grid *g, cudaStream_t
     dfree(flag, s);
     if (hf & 1) return fail(MSRSB_EINVAL, "the smoother needs A's pattern within each point's 3^%d neighbourhood", g->dim);
     if (hf & 2) return fail(MSRSB_EINVAL, "the smoother needs rows of at most 32 (block) entries");
+    if (hf & 4) return fail(MSRSB_EINVAL, "the smoother needs each row's columns strictly ascending");
     return MSRSB_OK;
 }
 
