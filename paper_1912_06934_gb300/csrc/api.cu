@@ -157,18 +157,21 @@ msrsb_status prolong_op(const msrsb_handle *h, const TP *P, const double *wc, co
 template <typename TV>
 msrsb_status mdot(long N, int nvec, const TV *V, long ldv, const TV *w, double *partial, double *out, int accumulate,
                   cudaStream_t s, const int *gate = nullptr);
-template <typename TV>
-msrsb_status gs_update(long N, int nv, const TV *V, long ldv, const double *hs, TV *w, double *hcol, int *flag,
-                       int pass, cudaStream_t s);
 msrsb_status norm2(long N, const double *w, double *partial, double *out, cudaStream_t s);
 msrsb_status mvsub(long N, int nvec, const double *V, long ldv, const double *h, double *w, cudaStream_t s);
 template <typename TZ>
 msrsb_status mvadd(long N, int nvec, const TZ *Z, long ldz, const double *y, double *x, cudaStream_t s);
 msrsb_status df_scale(long N, const double *r, const double *beta, float *vh, float *vl, cudaStream_t s);
-msrsb_status mdot_df(long N, int nv, const float *Vh, const float *Vl, long ldv, const float *Wh, const float *Wl,
-                     double *partial, double *hs, cudaStream_t s, const int *gate = nullptr);
-msrsb_status gs_update_df(long N, int nv, const float *Vh, const float *Vl, long ldv, const double *hs, float *Wh,
-                          float *Wl, float *oh, float *ol, double *hcol, int *flag, int pass, cudaStream_t s);
+msrsb_status arnoldi_dots_df(long N, int nv, const float *Vh, const float *Vl, const float *Ph, const float *Pl,
+                             const float *Wh, const float *Wl, double *partial, double *d, cudaStream_t s);
+msrsb_status arnoldi_dots(long N, int nv, const double *V, const double *P, const double *Wv, double *partial,
+                          double *d, cudaStream_t s);
+msrsb_status arnoldi_scalar(int m, int j, int full, double *kh, cudaStream_t s);
+msrsb_status arnoldi_update_df(long N, int nv, int m, const float *Vh, const float *Vl, float *Ph, float *Pl,
+                               const float *Wh, const float *Wl, float *Oh, float *Ol, const double *kh,
+                               cudaStream_t s);
+msrsb_status arnoldi_update(long N, int nv, int m, const double *V, double *P, const double *Wv, double *O,
+                            const double *kh, cudaStream_t s);
 msrsb_status sell_spmv_df(const Sell &S, const double *val, const double *x, float *yh, float *yl, cudaStream_t s);
 msrsb_status df_split(long N, const double *w, float *wh, float *wl, cudaStream_t s);
 template <typename TY>
@@ -607,24 +610,6 @@ msrsb_status vadd(int n, const double *a, double *b, cudaStream_t s) {
     return MSRSB_OK;
 }
 
-// Krylov state on the device, m = restart length:
-// H[(m+1) x m] column-major | cs[m] | sn[m] | g[m+1] | est | beta | h2[m+2] | est_hist[m+1] | flag
-struct KhLayout {
-    long H, cs, sn, g, est, beta, h2, hist, flag, total;
-    __host__ __device__ explicit KhLayout(int m) {
-        H = 0;
-        cs = (long)(m + 1) * m;
-        sn = cs + m;
-        g = sn + m;
-        est = g + m + 1;
-        beta = est + 1;
-        h2 = beta + 1;
-        hist = h2 + m + 2;
-        flag = hist + m + 1;
-        total = flag + 8;
-    }
-};
-
 // Host-side pool of timing-free events (grows, kept per host thread).
 static cudaEvent_t *event_pool(int need) {
     static thread_local cudaEvent_t *pool = nullptr;
@@ -688,25 +673,30 @@ __global__ void givens_kernel(int m, int j, double *__restrict__ kh) {
     for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) hc[i] = col[i];
 }
 
-// back substitution H(0:k,0:k) y = g(0:k); y written over g. Column
-// oriented: once y_c is known, thread i < c removes H(i,c) y_c from g_i.
+// back substitution H(0:k,0:k) y = g(0:k), then R(0:k,0:k) u = y (R upper
+// triangular, column-major with leading dimension m: the basis the solution
+// update uses is Zhat = Z R); u written over g. Column oriented: once an
+// unknown is known, thread i < c removes its column's entry from row i.
 __global__ void hess_solve_kernel(int m, int k, double *__restrict__ kh) {
     pdl_prologue();
     const KhLayout L(m);
-    const double *H = kh + L.H;
     double *g = kh + L.g;
     __shared__ double gs[1024];
     __shared__ double yc;
     for (int i = threadIdx.x; i < k; i += blockDim.x) gs[i] = g[i];
     __syncthreads();
-    for (int c = k - 1; c >= 0; --c) {
-        const double *hc = H + (long)c * (m + 1);
-        if (threadIdx.x == 0) yc = gs[c] / hc[c];
-        __syncthreads();
-        const double y = yc;
-        for (int i = threadIdx.x; i < c; i += blockDim.x) gs[i] -= hc[i] * y;
-        if (threadIdx.x == 0) gs[c] = y;
-        __syncthreads();
+    for (int pass = 0; pass < 2; ++pass) {
+        const double *T = pass == 0 ? kh + L.H : kh + L.R;
+        const long ld = pass == 0 ? m + 1 : m;
+        for (int c = k - 1; c >= 0; --c) {
+            const double *tc = T + (long)c * ld;
+            if (threadIdx.x == 0) yc = gs[c] / tc[c];
+            __syncthreads();
+            const double y = yc;
+            for (int i = threadIdx.x; i < c; i += blockDim.x) gs[i] -= tc[i] * y;
+            if (threadIdx.x == 0) gs[c] = y;
+            __syncthreads();
+        }
     }
     for (int i = threadIdx.x; i < k; i += blockDim.x) g[i] = gs[i];
 }
@@ -735,8 +725,7 @@ static msrsb_status gmres_t(msrsb_handle *h, const double *b, double *x, double 
     const int m = h->krylov_m;
     double *kh = h->kh;
     const KhLayout L(m);
-    double *H = kh + L.H, *est = kh + L.est, *beta = kh + L.beta, *h2 = kh + L.h2;
-    int *reorth = (int *)(kh + L.flag);
+    double *est = kh + L.est, *beta = kh + L.beta;
     double *V = h->kv, *Z = h->kz;                    // FP64 basis (DFV = false)
     // double-float basis and work vector of the mixed form: [Vh | Vl | Wh | Wl]
     float *Vh = (float *)h->kv32, *Vl = Vh + (m + 1) * N, *Wh = Vl + (m + 1) * N, *Wl = Wh + N;
@@ -786,7 +775,9 @@ static msrsb_status gmres_t(msrsb_handle *h, const double *b, double *x, double 
         cudaStream_t gv = lagged && h->side ? h->side : s;
         cudaEvent_t fork_ev = evs ? evs[mm] : nullptr, join_ev = evs ? evs[mm + 1] : nullptr;
         int conv = -1, checked = 0, launched = 0;
-        for (int j = 0; j < mm; ++j) {
+        // Step j (DCGS2, see arnoldi.cu) finishes column j - 1; step mm only
+        // finishes column mm - 1.
+        for (int j = 0; j <= mm; ++j) {
             if (lagged) {
                 while (checked < launched) {
                     if (cudaEventQuery(evs[checked]) != cudaSuccess) {
@@ -804,53 +795,56 @@ static msrsb_status gmres_t(msrsb_handle *h, const double *b, double *x, double 
                 }
                 if (conv >= 0) break;
             }
-            double *Zj = Z + j * N, *hcol = H + (long)j * (m + 1);
+            const bool full = j < mm;
+            double *Zj = Z + (long)j * N;
             if (DFV) {
-                MSRSB_TRY((apply_t<float, float, double>(h, Vh + j * N, Zj, s)));
-                if (h->bdim == 1) {
-                    MSRSB_TRY(sell_spmv_df(h->asell, (const double *)h->asell.val[0], Zj, Wh, Wl, s));
-                } else {
-                    MSRSB_TRY(fine_spmv(h, Zj, nullptr, h->kv, false, s));
-                    MSRSB_TRY(df_split(N, h->kv, Wh, Wl, s));
+                float *ph = Vh + (long)j * N, *pl = Vl + (long)j * N;
+                if (full) {
+                    MSRSB_TRY((apply_t<float, float, double>(h, ph, Zj, s)));
+                    if (h->bdim == 1) {
+                        MSRSB_TRY(sell_spmv_df(h->asell, (const double *)h->asell.val[0], Zj, Wh, Wl, s));
+                    } else {
+                        MSRSB_TRY(fine_spmv(h, Zj, nullptr, h->kv, false, s));
+                        MSRSB_TRY(df_split(N, h->kv, Wh, Wl, s));
+                    }
                 }
-                // classical Gram-Schmidt with the DGKS test (see below), double-float vectors
-                float *oh = Vh + (j + 1) * N, *ol = Vl + (j + 1) * N;
-                MSRSB_TRY(mdot_df(N, j + 1, Vh, Vl, N, Wh, Wl, h->partial, h2, s));
-                MSRSB_TRY(gs_update_df(N, j + 1, Vh, Vl, N, h2, Wh, Wl, oh, ol, hcol, reorth, 1, s));
-                MSRSB_TRY(mdot_df(N, j + 1, Vh, Vl, N, Wh, Wl, h->partial, h2, s, reorth));
-                MSRSB_TRY(gs_update_df(N, j + 1, Vh, Vl, N, h2, Wh, Wl, oh, ol, hcol, reorth, 2, s));
+                MSRSB_TRY(arnoldi_dots_df(N, j, Vh, Vl, ph, pl, full ? Wh : nullptr, full ? Wl : nullptr, h->partial,
+                                          kh + L.d, s));
+                MSRSB_TRY(arnoldi_scalar(m, j, full, kh, s));
+                if (full)
+                    MSRSB_TRY(arnoldi_update_df(N, j, m, Vh, Vl, ph, pl, Wh, Wl, Vh + (long)(j + 1) * N,
+                                                Vl + (long)(j + 1) * N, kh, s));
             } else {
-                double *Vj = V + j * N, *w = V + (j + 1) * N;
-                MSRSB_TRY(apply_any(h, Vj, Zj, s));
-                MSRSB_TRY(fine_spmv(h, Zj, nullptr, w, false, s));
-                // classical Gram-Schmidt with the DGKS re-orthogonalisation test:
-                // one multi-dot pass (V_0..V_j and w itself, stored as V_{j+1})
-                // and one fused update + normalisation; the second pass runs on
-                // the device only when the first lost more than half of |w|^2
-                MSRSB_TRY(mdot<double>(N, j + 2, V, N, w, h->partial, h2, 0, s));
-                MSRSB_TRY(gs_update<double>(N, j + 1, V, N, h2, w, hcol, reorth, 1, s));
-                MSRSB_TRY(mdot<double>(N, j + 2, V, N, w, h->partial, h2, 0, s, reorth));
-                MSRSB_TRY(gs_update<double>(N, j + 1, V, N, h2, w, hcol, reorth, 2, s));
+                double *P = V + (long)j * N, *Wn = V + (long)(j + 1) * N;
+                if (full) {
+                    MSRSB_TRY(apply_any(h, P, Zj, s));
+                    MSRSB_TRY(fine_spmv(h, Zj, nullptr, Wn, false, s));
+                }
+                MSRSB_TRY(arnoldi_dots(N, j, V, P, full ? Wn : nullptr, h->partial, kh + L.d, s));
+                MSRSB_TRY(arnoldi_scalar(m, j, full, kh, s));
+                if (full) MSRSB_TRY(arnoldi_update(N, j, m, V, P, Wn, Wn, kh, s));
             }
+            if (j == 0) continue;
+            const int c = j - 1;  // the column this step finished
             if (gv != s) {
                 MSRSB_CUDA(cudaEventRecord(fork_ev, s));
                 MSRSB_CUDA(cudaStreamWaitEvent(gv, fork_ev, 0));
             }
             // launched without programmatic dependence: on the side stream it
             // follows a wait on the main stream's event, which must hold in full
-            givens_kernel<<<1, 32, 0, gv>>>(m, j, kh);
+            givens_kernel<<<1, 32, 0, gv>>>(m, c, kh);
             MSRSB_LAUNCHED("givens_kernel");
-            launched = j + 1;
+            launched = c + 1;
             if (lagged) {
-                MSRSB_CUDA(cudaMemcpyAsync(pin_est + j, kh + L.hist + j, sizeof(double), cudaMemcpyDeviceToHost, gv));
-                MSRSB_CUDA(cudaEventRecord(evs[j], gv));
+                MSRSB_CUDA(cudaMemcpyAsync(pin_est + c, kh + L.hist + c, sizeof(double), cudaMemcpyDeviceToHost, gv));
+                MSRSB_CUDA(cudaEventRecord(evs[c], gv));
             } else {
                 double e = 0.0;
                 MSRSB_TRY(read_scalar(est, &e, s));
                 if (!std::isfinite(e)) return fail(MSRSB_ENAN, "non-finite residual estimate in GMRES");
-                if (hist) hist[its + j + 1] = e / bnorm;
+                if (hist) hist[its + c + 1] = e / bnorm;
                 if (e <= stop) {
-                    conv = j;
+                    conv = c;
                     break;
                 }
             }

@@ -462,6 +462,12 @@ template msrsb_status mdot<double>(long, int, const double *, long, const double
 template msrsb_status mdot<float>(long, int, const float *, long, const float *, double *, double *, int, cudaStream_t,
                                   const int *);
 
+// out[j] = sum_b partial[j][b], b < nblk, j < nvec
+msrsb_status reduce_partials(int nvec, int nblk, const double *partial, double *out, cudaStream_t s) {
+    MSRSB_PDL((reduce_partials_kernel), nvec, 256, 0, s, nblk, partial, out, 0, 0, nullptr);
+    return MSRSB_OK;
+}
+
 msrsb_status norm2(long N, const double *w, double *partial, double *out, cudaStream_t s) {
     dim3 grid(kRedBlocks, 1);
     MSRSB_PDL((mdot_kernel<double>), grid, 256, 0, s, N, w, N, w, partial, nullptr);
@@ -469,70 +475,7 @@ msrsb_status norm2(long N, const double *w, double *partial, double *out, cudaSt
     return MSRSB_OK;
 }
 
-// Classical Gram-Schmidt update with the DGKS test, fused with the
-// normalisation. hs[0..nv-1] = V_q . w, hs[nv] = w . w (one multi-dot pass).
-// The squared norm after the projection is hs[nv] - sum_q hs[q]^2; if it kept
-// at least half of |w|^2 (no severe cancellation) the result is normalised in
-// the same pass and H(nv, col) is set, else it is left unnormalised and *flag
-// = 1 asks for a second pass (pass 2 always normalises). Pass 1 writes H(0..nv-1,
-// col) = hs, pass 2 adds its coefficients. Every CTA takes the same decision.
-template <typename TV>
-__global__ void __launch_bounds__(256) gs_update_kernel(long N, int nv, const TV *__restrict__ V, long ldv,
-                                                        const double *__restrict__ hs, TV *__restrict__ w,
-                                                        double *__restrict__ hcol, int *__restrict__ flag, int pass) {
-    pdl_prologue();
-    if (pass == 2 && !*flag) return;
-    __shared__ double hsh[1024];
-    __shared__ TV hst[1024];
-    __shared__ double s_scale;
-    __shared__ int s_norm;
-    for (int q = threadIdx.x; q < nv; q += blockDim.x) {
-        hsh[q] = hs[q];
-        hst[q] = TV(hs[q]);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double pr = 0.0;
-        for (int q = 0; q < nv; ++q) pr = fma(hsh[q], hsh[q], pr);
-        const double ww = hs[nv];
-        const double d2 = ww - pr;
-        const int norm = pass == 2 || d2 >= 0.5 * ww;
-        const double den = norm && d2 > 0.0 ? sqrt(d2) : 0.0;
-        s_norm = norm;
-        s_scale = den > 0.0 ? 1.0 / den : (norm ? 0.0 : 1.0);
-        if (blockIdx.x == 0) {
-            for (int q = 0; q < nv; ++q) hcol[q] = pass == 1 ? hsh[q] : hcol[q] + hsh[q];
-            if (norm) hcol[nv] = den;
-            if (pass == 1) *flag = !norm;
-        }
-    }
-    __syncthreads();
-    const TV sc = TV(s_scale);
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
-        TV a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-        int q = 0;
-        for (; q + 3 < nv; q += 4) {
-            a0 = fma(V[q * ldv + i], hst[q], a0);
-            a1 = fma(V[(q + 1) * ldv + i], hst[q + 1], a1);
-            a2 = fma(V[(q + 2) * ldv + i], hst[q + 2], a2);
-            a3 = fma(V[(q + 3) * ldv + i], hst[q + 3], a3);
-        }
-        for (; q < nv; ++q) a0 = fma(V[q * ldv + i], hst[q], a0);
-        w[i] = (w[i] - ((a0 + a1) + (a2 + a3))) * sc;
-    }
-}
 
-template <typename TV>
-msrsb_status gs_update(long N, int nv, const TV *V, long ldv, const double *hs, TV *w, double *hcol, int *flag,
-                       int pass, cudaStream_t s) {
-    MSRSB_PDL((gs_update_kernel<TV>), ceil_div(N, 256) < 2048 ? ceil_div(N, 256) : 2048, 256, 0, s, N, nv, V, ldv, hs,
-              w, hcol, flag, pass);
-    return MSRSB_OK;
-}
-template msrsb_status gs_update<double>(long, int, const double *, long, const double *, double *, double *, int *, int,
-                                        cudaStream_t);
-template msrsb_status gs_update<float>(long, int, const float *, long, const double *, float *, double *, int *, int,
-                                       cudaStream_t);
 
 // w -= sum_j V_j h[j]  (h staged in shared memory)
 __global__ void mvsub_kernel(long N, int nvec, const double *__restrict__ V, long ldv, const double *__restrict__ h,
@@ -661,59 +604,11 @@ template msrsb_status copy_cast<float, float>(long, const float *, float *, cuda
 
 }  // namespace msrsb
 
-// ---- double-float Krylov vectors (mixed form) ----------------------------------------
-//
-// A Krylov vector v is stored as two FP32 planes, v = hi + lo with |lo| <= ulp(hi)/2
-// (about 48 significant bits). Products are formed exactly as p + e
-// (e = fma(a, b, -p)) and summed with error-free additions (Knuth TwoSum), so
-// dot products and updates run on the FP32 pipe with close-to-FP64 accuracy;
-// only O(1) FP64 operations per element remain.
+// ---- double-float Krylov vectors (mixed form): arithmetic in df.cuh ------------------
+
+#include "df.cuh"
 
 namespace msrsb {
-
-struct DF {
-    float hi, lo;
-};
-
-// Double-float arithmetic (Dekker 1971; Knuth TAOCP vol. 2, 4.2.2): a value
-// is hi + lo with |lo| <= ulp(hi)/2. The _rn intrinsics keep the compiler
-// from contracting the error-free transformations into FMAs.
-__device__ __forceinline__ DF df_from(double x) {
-    float h = (float)x;
-    return DF{h, (float)(x - (double)h)};
-}
-__device__ __forceinline__ DF quick_two_sum(float a, float b) {  // |a| >= |b|
-    const float s = __fadd_rn(a, b);
-    return DF{s, __fadd_rn(b, -__fadd_rn(s, -a))};
-}
-__device__ __forceinline__ DF two_sum(float a, float b) {
-    const float s = __fadd_rn(a, b);
-    const float bb = __fadd_rn(s, -a);
-    return DF{s, __fadd_rn(__fadd_rn(a, -__fadd_rn(s, -bb)), __fadd_rn(b, -bb))};
-}
-__device__ __forceinline__ DF df_add(DF a, DF b) {
-    const DF t = two_sum(a.hi, b.hi);
-    return quick_two_sum(t.hi, __fadd_rn(t.lo, __fadd_rn(a.lo, b.lo)));
-}
-__device__ __forceinline__ DF df_mul(DF a, DF b) {
-    const float p = __fmul_rn(a.hi, b.hi);
-    float e = fmaf(a.hi, b.hi, -p);
-    e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
-    return quick_two_sum(p, e);
-}
-// s += a * b in double-float, renormalised after every step so that the low
-// word stays within half an ulp of the high word (an unnormalised low word
-// collects every rounding error and limits long sums to ~1e-13); the lo*lo
-// term is below the format's precision
-__device__ __forceinline__ void df_fma_acc(DF &s, float ah, float al, float bh, float bl) {
-    const float p = __fmul_rn(ah, bh);
-    const float e = fmaf(ah, bh, -p);
-    const DF t = two_sum(s.hi, p);
-    s = two_sum(t.hi, __fadd_rn(s.lo, __fadd_rn(t.lo, fmaf(ah, bl, fmaf(al, bh, e)))));
-}
-__device__ __forceinline__ DF df_shfl_down(DF v, int o) {
-    return DF{__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
-}
 
 // V_0 planes = r / beta
 __global__ void df_scale_kernel(long N, const double *__restrict__ r, const double *__restrict__ beta,
@@ -784,248 +679,8 @@ msrsb_status df_split(long N, const double *w, float *wh, float *wl, cudaStream_
     return MSRSB_OK;
 }
 
-// partial[q * gridDim.x + b] = sum over row chunk b of V_q . w (q < nv), and
-// for q = nv the squared norm of w; all vectors double-float, FP32 arithmetic
-// up to the per-warp results
-__global__ void __launch_bounds__(256) mdot_df_kernel(long N, int nv, const float *__restrict__ Vh,
-                                                      const float *__restrict__ Vl, long ldv,
-                                                      const float *__restrict__ Wh, const float *__restrict__ Wl,
-                                                      double *__restrict__ partial, const int *__restrict__ gate) {
-    pdl_prologue();
-    if (gate && !*gate) return;
-    __shared__ double red[8];
-    const int q = blockIdx.y;
-    const long chunk = (N + gridDim.x - 1) / gridDim.x;
-    const long b0 = blockIdx.x * chunk, b1 = b0 + chunk < N ? b0 + chunk : N;
-    const float *vh = q < nv ? Vh + q * ldv : Wh, *vl = q < nv ? Vl + q * ldv : Wl;
-    DF s0{0.f, 0.f}, s1{0.f, 0.f};
-    long i = b0 + threadIdx.x;
-    const long bd = blockDim.x;
-    for (; i + bd < b1; i += 2 * bd) {
-        df_fma_acc(s0, vh[i], vl[i], Wh[i], Wl[i]);
-        df_fma_acc(s1, vh[i + bd], vl[i + bd], Wh[i + bd], Wl[i + bd]);
-    }
-    if (i < b1) df_fma_acc(s0, vh[i], vl[i], Wh[i], Wl[i]);
-    DF t = df_add(two_sum(s0.hi, s0.lo), two_sum(s1.hi, s1.lo));
-    for (int o = 16; o > 0; o >>= 1) t = df_add(t, df_shfl_down(t, o));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)t.hi + (double)t.lo;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-        v = warp_sum(v);
-        if (threadIdx.x == 0) partial[(long)q * gridDim.x + blockIdx.x] = v;
-    }
-}
-
 __global__ void reduce_partials_kernel(int nblk, const double *__restrict__ partial, double *__restrict__ out,
                                        int accumulate, int sqrt_out, const int *__restrict__ gate);
 
-// As mdot_df_kernel with 16-byte loads: every thread takes four consecutive
-// elements of each plane per load (row chunks in units of four elements),
-// so that enough bytes are in flight to keep HBM busy. Requires N and ldv
-// divisible by 4 and 16-byte aligned planes.
-__global__ void __launch_bounds__(256) mdot_df4_kernel(long N4, int nv, const float4 *__restrict__ Vh,
-                                                       const float4 *__restrict__ Vl, long ldv4,
-                                                       const float4 *__restrict__ Wh, const float4 *__restrict__ Wl,
-                                                       double *__restrict__ partial, const int *__restrict__ gate) {
-    pdl_prologue();
-    if (gate && !*gate) return;
-    __shared__ double red[8];
-    const int q = blockIdx.y;
-    const long chunk = (N4 + gridDim.x - 1) / gridDim.x;
-    const long b0 = blockIdx.x * chunk, b1 = b0 + chunk < N4 ? b0 + chunk : N4;
-    const float4 *vh = q < nv ? Vh + q * ldv4 : Wh, *vl = q < nv ? Vl + q * ldv4 : Wl;
-    DF s0{0.f, 0.f}, s1{0.f, 0.f};
-    long i = b0 + threadIdx.x;
-    const long bd = blockDim.x;
-    for (; i + bd < b1; i += 2 * bd) {
-        const float4 a = __ldg(vh + i), al = __ldg(vl + i), w = __ldg(Wh + i), wl = __ldg(Wl + i);
-        const float4 c = __ldg(vh + i + bd), cl = __ldg(vl + i + bd), x = __ldg(Wh + i + bd), xl = __ldg(Wl + i + bd);
-        df_fma_acc(s0, a.x, al.x, w.x, wl.x);
-        df_fma_acc(s1, a.y, al.y, w.y, wl.y);
-        df_fma_acc(s0, a.z, al.z, w.z, wl.z);
-        df_fma_acc(s1, a.w, al.w, w.w, wl.w);
-        df_fma_acc(s0, c.x, cl.x, x.x, xl.x);
-        df_fma_acc(s1, c.y, cl.y, x.y, xl.y);
-        df_fma_acc(s0, c.z, cl.z, x.z, xl.z);
-        df_fma_acc(s1, c.w, cl.w, x.w, xl.w);
-    }
-    if (i < b1) {
-        const float4 a = __ldg(vh + i), al = __ldg(vl + i), w = __ldg(Wh + i), wl = __ldg(Wl + i);
-        df_fma_acc(s0, a.x, al.x, w.x, wl.x);
-        df_fma_acc(s1, a.y, al.y, w.y, wl.y);
-        df_fma_acc(s0, a.z, al.z, w.z, wl.z);
-        df_fma_acc(s1, a.w, al.w, w.w, wl.w);
-    }
-    DF t = df_add(two_sum(s0.hi, s0.lo), two_sum(s1.hi, s1.lo));
-    for (int o = 16; o > 0; o >>= 1) t = df_add(t, df_shfl_down(t, o));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)t.hi + (double)t.lo;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-        v = warp_sum(v);
-        if (threadIdx.x == 0) partial[(long)q * gridDim.x + blockIdx.x] = v;
-    }
-}
-
-static bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
-
-// hs[q] = V_q . w (q < nv), hs[nv] = w . w
-msrsb_status mdot_df(long N, int nv, const float *Vh, const float *Vl, long ldv, const float *Wh, const float *Wl,
-                     double *partial, double *hs, cudaStream_t s, const int *gate) {
-    dim3 grid(kRedBlocks, nv + 1);
-    if (N % 4 == 0 && ldv % 4 == 0 && aligned16(Vh) && aligned16(Vl) && aligned16(Wh) && aligned16(Wl))
-        MSRSB_PDL((mdot_df4_kernel), grid, 256, 0, s, N / 4, nv, (const float4 *)Vh, (const float4 *)Vl, ldv / 4,
-                  (const float4 *)Wh, (const float4 *)Wl, partial, gate);
-    else
-        MSRSB_PDL((mdot_df_kernel), grid, 256, 0, s, N, nv, Vh, Vl, ldv, Wh, Wl, partial, gate);
-    MSRSB_PDL((reduce_partials_kernel), nv + 1, 256, 0, s, kRedBlocks, partial, hs, 0, 0, gate);
-    return MSRSB_OK;
-}
-
-// Classical Gram-Schmidt update with the DGKS test (as gs_update_kernel) on
-// double-float vectors: w1 = w - sum_q V_q hs[q]; if normalised (pass 2, or
-// no severe cancellation) V_new = w1 / |w1|, else w1 goes back to w for the
-// second pass and *flag = 1.
-__global__ void __launch_bounds__(256) gs_update_df_kernel(long N, int nv, const float *__restrict__ Vh,
-                                                           const float *__restrict__ Vl, long ldv,
-                                                           const double *__restrict__ hs, float *__restrict__ Wh,
-                                                           float *__restrict__ Wl, float *__restrict__ oh,
-                                                           float *__restrict__ ol, double *__restrict__ hcol,
-                                                           int *__restrict__ flag, int pass) {
-    pdl_prologue();
-    if (pass == 2 && !*flag) return;
-    __shared__ float hh[1024], hl[1024];
-    __shared__ DF s_scale;
-    __shared__ int s_norm;
-    for (int q = threadIdx.x; q < nv; q += blockDim.x) {
-        const DF d = df_from(-hs[q]);
-        hh[q] = d.hi;
-        hl[q] = d.lo;
-    }
-    if (threadIdx.x == 0) {
-        double pr = 0.0;
-        for (int q = 0; q < nv; ++q) pr = fma(hs[q], hs[q], pr);
-        const double ww = hs[nv];
-        const double d2 = ww - pr;
-        const int norm = pass == 2 || d2 >= 0.5 * ww;
-        const double den = norm && d2 > 0.0 ? sqrt(d2) : 0.0;
-        s_norm = norm;
-        s_scale = df_from(den > 0.0 ? 1.0 / den : (norm ? 0.0 : 1.0));
-        if (blockIdx.x == 0) {
-            for (int q = 0; q < nv; ++q) hcol[q] = pass == 1 ? hs[q] : hcol[q] + hs[q];
-            if (norm) hcol[nv] = den;
-            if (pass == 1) *flag = !norm;
-        }
-    }
-    __syncthreads();
-    const DF sc = s_scale;
-    const bool norm = s_norm;
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
-        DF acc{Wh[i], Wl[i]};
-        for (int q = 0; q < nv; ++q) df_fma_acc(acc, Vh[q * ldv + i], Vl[q * ldv + i], hh[q], hl[q]);
-        const DF x = df_mul(two_sum(acc.hi, acc.lo), sc);
-        if (norm) {
-            oh[i] = x.hi;
-            ol[i] = x.lo;
-        } else {
-            Wh[i] = x.hi;
-            Wl[i] = x.lo;
-        }
-    }
-}
-
-// As gs_update_df_kernel with 16-byte loads, four consecutive elements per
-// thread (same arithmetic per element, so the same results), and the
-// projection's squared norm summed by one warp instead of one thread.
-// Requires N and ldv divisible by 4 and 16-byte aligned planes.
-__device__ __forceinline__ void df_out4(float4 &h, float4 &l, const DF *a, DF sc) {
-    DF x = df_mul(two_sum(a[0].hi, a[0].lo), sc);
-    h.x = x.hi, l.x = x.lo;
-    x = df_mul(two_sum(a[1].hi, a[1].lo), sc);
-    h.y = x.hi, l.y = x.lo;
-    x = df_mul(two_sum(a[2].hi, a[2].lo), sc);
-    h.z = x.hi, l.z = x.lo;
-    x = df_mul(two_sum(a[3].hi, a[3].lo), sc);
-    h.w = x.hi, l.w = x.lo;
-}
-
-__global__ void __launch_bounds__(256) gs_update_df4_kernel(long N4, int nv, const float4 *__restrict__ Vh,
-                                                            const float4 *__restrict__ Vl, long ldv4,
-                                                            const double *__restrict__ hs, float4 *Wh, float4 *Wl,
-                                                            float4 *__restrict__ oh, float4 *__restrict__ ol,
-                                                            double *__restrict__ hcol, int *__restrict__ flag,
-                                                            int pass) {
-    pdl_prologue();
-    if (pass == 2 && !*flag) return;
-    __shared__ float hh[1024], hl[1024];
-    __shared__ DF s_scale;
-    __shared__ int s_norm;
-    for (int q = threadIdx.x; q < nv; q += blockDim.x) {
-        const DF d = df_from(-hs[q]);
-        hh[q] = d.hi;
-        hl[q] = d.lo;
-    }
-    if (threadIdx.x < 32) {
-        double pr = 0.0;
-        for (int q = threadIdx.x; q < nv; q += 32) pr = fma(hs[q], hs[q], pr);
-        pr = warp_sum(pr);
-        const double ww = hs[nv];
-        const double d2 = ww - pr;
-        const int norm = pass == 2 || d2 >= 0.5 * ww;
-        const double den = norm && d2 > 0.0 ? sqrt(d2) : 0.0;
-        if (threadIdx.x == 0) {
-            s_norm = norm;
-            s_scale = df_from(den > 0.0 ? 1.0 / den : (norm ? 0.0 : 1.0));
-        }
-        if (blockIdx.x == 0) {
-            for (int q = threadIdx.x; q < nv; q += 32) hcol[q] = pass == 1 ? hs[q] : hcol[q] + hs[q];
-            if (threadIdx.x == 0) {
-                if (norm) hcol[nv] = den;
-                if (pass == 1) *flag = !norm;
-            }
-        }
-    }
-    __syncthreads();
-    const DF sc = s_scale;
-    const bool norm = s_norm;
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N4; i += (long)gridDim.x * blockDim.x) {
-        const float4 wh = Wh[i], wl = Wl[i];
-        DF a[4] = {{wh.x, wl.x}, {wh.y, wl.y}, {wh.z, wl.z}, {wh.w, wl.w}};
-#pragma unroll 2
-        for (int q = 0; q < nv; ++q) {
-            const float4 vh = __ldg(Vh + q * ldv4 + i), vl = __ldg(Vl + q * ldv4 + i);
-            const float ch = hh[q], cl = hl[q];
-            df_fma_acc(a[0], vh.x, vl.x, ch, cl);
-            df_fma_acc(a[1], vh.y, vl.y, ch, cl);
-            df_fma_acc(a[2], vh.z, vl.z, ch, cl);
-            df_fma_acc(a[3], vh.w, vl.w, ch, cl);
-        }
-        float4 h, l;
-        df_out4(h, l, a, sc);
-        if (norm) {
-            oh[i] = h;
-            ol[i] = l;
-        } else {
-            Wh[i] = h;
-            Wl[i] = l;
-        }
-    }
-}
-
-msrsb_status gs_update_df(long N, int nv, const float *Vh, const float *Vl, long ldv, const double *hs, float *Wh,
-                          float *Wl, float *oh, float *ol, double *hcol, int *flag, int pass, cudaStream_t s) {
-    if (N % 4 == 0 && ldv % 4 == 0 && aligned16(Vh) && aligned16(Vl) && aligned16(Wh) && aligned16(Wl) &&
-        aligned16(oh) && aligned16(ol)) {
-        const long N4 = N / 4;
-        const int grid = ceil_div(N4, 256) < 2048 ? (int)ceil_div(N4, 256) : 2048;
-        MSRSB_PDL((gs_update_df4_kernel), grid, 256, 0, s, N4, nv, (const float4 *)Vh, (const float4 *)Vl, ldv / 4,
-                  hs, (float4 *)Wh, (float4 *)Wl, (float4 *)oh, (float4 *)ol, hcol, flag, pass);
-        return MSRSB_OK;
-    }
-    const int grid = ceil_div(N, 256) < 2048 ? (int)ceil_div(N, 256) : 2048;
-    MSRSB_PDL((gs_update_df_kernel), grid, 256, 0, s, N, nv, Vh, Vl, ldv, hs, Wh, Wl, oh, ol, hcol, flag, pass);
-    return MSRSB_OK;
-}
 
 }  // namespace msrsb
