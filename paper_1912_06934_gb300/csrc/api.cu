@@ -163,10 +163,10 @@ template <typename TZ>
 msrsb_status mvadd(long N, int nvec, const TZ *Z, long ldz, const double *y, double *x, cudaStream_t s);
 msrsb_status df_scale(long N, const double *r, const double *beta, float *vh, float *vl, cudaStream_t s);
 msrsb_status arnoldi_dots_df(long N, int nv, const float *Vh, const float *Vl, const float *Ph, const float *Pl,
-                             const float *Wh, const float *Wl, double *partial, double *d, cudaStream_t s);
+                             const float *Wh, const float *Wl, double *partial, cudaStream_t s);
 msrsb_status arnoldi_dots(long N, int nv, const double *V, const double *P, const double *Wv, double *partial,
-                          double *d, cudaStream_t s);
-msrsb_status arnoldi_scalar(int m, int j, int full, double *kh, cudaStream_t s);
+                          cudaStream_t s);
+msrsb_status arnoldi_scalar(int m, int j, int full, const double *partial, double *kh, cudaStream_t s);
 msrsb_status arnoldi_update_df(long N, int nv, int m, const float *Vh, const float *Vl, float *Ph, float *Pl,
                                const float *Wh, const float *Wl, float *Oh, float *Ol, const double *kh,
                                cudaStream_t s);
@@ -809,8 +809,8 @@ static msrsb_status gmres_t(msrsb_handle *h, const double *b, double *x, double 
                     }
                 }
                 MSRSB_TRY(arnoldi_dots_df(N, j, Vh, Vl, ph, pl, full ? Wh : nullptr, full ? Wl : nullptr, h->partial,
-                                          kh + L.d, s));
-                MSRSB_TRY(arnoldi_scalar(m, j, full, kh, s));
+                                          s));
+                MSRSB_TRY(arnoldi_scalar(m, j, full, h->partial, kh, s));
                 if (full)
                     MSRSB_TRY(arnoldi_update_df(N, j, m, Vh, Vl, ph, pl, Wh, Wl, Vh + (long)(j + 1) * N,
                                                 Vl + (long)(j + 1) * N, kh, s));
@@ -820,8 +820,8 @@ static msrsb_status gmres_t(msrsb_handle *h, const double *b, double *x, double 
                     MSRSB_TRY(apply_any(h, P, Zj, s));
                     MSRSB_TRY(fine_spmv(h, Zj, nullptr, Wn, false, s));
                 }
-                MSRSB_TRY(arnoldi_dots(N, j, V, P, full ? Wn : nullptr, h->partial, kh + L.d, s));
-                MSRSB_TRY(arnoldi_scalar(m, j, full, kh, s));
+                MSRSB_TRY(arnoldi_dots(N, j, V, P, full ? Wn : nullptr, h->partial, s));
+                MSRSB_TRY(arnoldi_scalar(m, j, full, h->partial, kh, s));
                 if (full) MSRSB_TRY(arnoldi_update(N, j, m, V, P, Wn, Wn, kh, s));
             }
             if (j == 0) continue;

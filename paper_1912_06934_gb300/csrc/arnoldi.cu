@@ -26,8 +26,6 @@ namespace msrsb {
 
 constexpr int kArnBlocks = 76;  // row chunks of the dot products (fixed reduction order)
 
-msrsb_status reduce_partials(int nvec, int nblk, const double *partial, double *out, cudaStream_t s);
-
 // ---- pass 1: dot products ------------------------------------------------------------------
 
 template <int W>
@@ -131,30 +129,35 @@ __global__ void __launch_bounds__(256) dcgs2_dots_kernel(long N, int nv, const d
 
 // ---- the step's scalars (one CTA) ----------------------------------------------------------
 //
-// d = (s_0, t_0, s_1, t_1, ..., rho, sigma) of step j. Finishes column j-1 of
-// Hu (+= s, Hu[j][j-1] = alpha) and copies it to H for the Givens rotation;
-// with `full` also R[:, j] = (s, alpha), the provisional column j of Hu
+// Sums the dot products' row-chunk partials (d = (s_0, t_0, s_1, t_1, ...,
+// rho, sigma), one warp per product, fixed order) and finishes column j-1 of
+// Hu (+= s, Hu[j][j-1] = alpha), copied to H for the Givens rotation; with
+// `full` also R[:, j] = (s, alpha), the provisional column j of Hu
 // (V_j^T w_j) and the update coefficients cv = s / alpha (for v_j),
 // cp = H s / alpha + Hu[:, j] (for the next p), scal[0] = 1 / alpha.
-__global__ void __launch_bounds__(256) dcgs2_scalar_kernel(int m, int j, int full, double *__restrict__ kh) {
+__global__ void __launch_bounds__(256) dcgs2_scalar_kernel(int m, int j, int full, int nblk,
+                                                           const double *__restrict__ partial,
+                                                           double *__restrict__ kh) {
     pdl_prologue();
     const KhLayout L(m);
     double *H = kh + L.H, *Hu = kh + L.Hu, *R = kh + L.R;
-    const double *d = kh + L.d;
     double *cv = kh + L.cv, *cp = kh + L.cp, *sc = kh + L.scal;
-    __shared__ double s_s[512], s_t[512], s_hs[513];
+    __shared__ double s_d[2 * 513], s_hs[513];
     __shared__ double s_ss, s_st;
-    const int tid = threadIdx.x;
-    for (int q = tid; q < j; q += blockDim.x) {
-        s_s[q] = d[2 * q];
-        s_t[q] = d[2 * q + 1];
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (int row = tid >> 5; row < 2 * (j + 1); row += blockDim.x >> 5) {
+        double a = 0.0;
+        for (int b = lane; b < nblk; b += 32) a += partial[(long)row * nblk + b];
+        a = warp_sum(a);
+        if (lane == 0) s_d[row] = a;
     }
     __syncthreads();
+    const double *s_s = s_d;  // s_q = s_d[2q], t_q = s_d[2q + 1]
     if (tid < 32) {
         double a = 0.0, b = 0.0;
         for (int q = tid; q < j; q += 32) {
-            a = fma(s_s[q], s_s[q], a);
-            b = fma(s_s[q], s_t[q], b);
+            a = fma(s_d[2 * q], s_d[2 * q], a);
+            b = fma(s_d[2 * q], s_d[2 * q + 1], b);
         }
         a = warp_sum(a);
         b = warp_sum(b);
@@ -164,14 +167,14 @@ __global__ void __launch_bounds__(256) dcgs2_scalar_kernel(int m, int j, int ful
         }
     }
     __syncthreads();
-    const double rho = d[2 * j], sig = d[2 * j + 1];
+    const double rho = s_d[2 * j], sig = s_d[2 * j + 1];
     double alpha = 1.0;  // v_0 is a unit vector already
     if (j > 0) {
         const double a2 = rho - s_ss;
         alpha = a2 > 0.0 ? sqrt(a2) : 0.0;  // 0: breakdown, the Krylov space is invariant
         double *hu = Hu + (long)(j - 1) * (m + 1), *hc = H + (long)(j - 1) * (m + 1);
         for (int q = tid; q <= j; q += blockDim.x) {
-            const double v = q < j ? hu[q] + s_s[q] : alpha;
+            const double v = q < j ? hu[q] + s_s[2 * q] : alpha;
             hu[q] = v;
             hc[q] = v;
         }
@@ -179,21 +182,27 @@ __global__ void __launch_bounds__(256) dcgs2_scalar_kernel(int m, int j, int ful
     if (!full) return;
     const double inva = alpha > 0.0 ? 1.0 / alpha : 0.0;
     double *rc = R + (long)j * m;
-    for (int q = tid; q <= j; q += blockDim.x) rc[q] = q < j ? s_s[q] : alpha;
+    for (int q = tid; q <= j; q += blockDim.x) rc[q] = q < j ? s_s[2 * q] : alpha;
     __syncthreads();  // column j-1 of Hu is complete
-    // H s over the finished columns 0 .. j-1 (Hu[r][c] != 0 only for r <= c + 1)
+    // H s over the finished columns 0 .. j-1 (Hu[r][c] != 0 only for r <= c + 1),
+    // eight independent loads in flight per thread
     for (int r = tid; r <= j; r += blockDim.x) {
-        double acc = 0.0;
-        for (int c = r > 0 ? r - 1 : 0; c < j; ++c) acc = fma(Hu[(long)c * (m + 1) + r], s_s[c], acc);
-        s_hs[r] = acc;
+        double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        int c = r > 0 ? r - 1 : 0;
+        for (; c + 8 <= j; c += 8) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc[u] = fma(Hu[(long)(c + u) * (m + 1) + r], s_s[2 * (c + u)], acc[u]);
+        }
+        for (; c < j; ++c) acc[0] = fma(Hu[(long)c * (m + 1) + r], s_s[2 * c], acc[0]);
+        s_hs[r] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
     }
     __syncthreads();
     double *hn = Hu + (long)j * (m + 1);
     for (int q = tid; q < j; q += blockDim.x) {
-        const double h = (s_t[q] - s_hs[q]) * inva;
+        const double h = (s_d[2 * q + 1] - s_hs[q]) * inva;
         hn[q] = h;
         cp[q] = fma(s_hs[q], inva, h);
-        cv[q] = s_s[q] * inva;
+        cv[q] = s_d[2 * q] * inva;
     }
     if (tid == 0) {
         const double h = ((sig - s_st) * inva - s_hs[j]) * inva;
@@ -303,29 +312,30 @@ __global__ void __launch_bounds__(256) dcgs2_update_kernel(long N, int nv, const
 
 static bool al16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 
-// d = (V_q . p, V_q . w for q < nv; p . p, p . w): V holds nv vectors of N
-// with stride N; w may be null (its products are 0)
+// partials of (V_q . p, V_q . w for q < nv; p . p, p . w): V holds nv
+// vectors of N with stride N; w may be null (its products are 0)
 msrsb_status arnoldi_dots_df(long N, int nv, const float *Vh, const float *Vl, const float *Ph, const float *Pl,
-                             const float *Wh, const float *Wl, double *partial, double *d, cudaStream_t s) {
+                             const float *Wh, const float *Wl, double *partial, cudaStream_t s) {
     dim3 grid(kArnBlocks, nv + 1);
     const bool v4 = N % 4 == 0 && al16(Vh) && al16(Vl) && al16(Ph) && al16(Pl) && (!Wh || (al16(Wh) && al16(Wl)));
     if (v4)
-        MSRSB_PDL((dcgs2_dots_df_kernel<4>), grid, 256, 0, s, N / 4, nv, Vh, Vl, N / 4 * 4, Ph, Pl, Wh, Wl, partial);
+        MSRSB_PDL((dcgs2_dots_df_kernel<4>), grid, 256, 0, s, N / 4, nv, Vh, Vl, N, Ph, Pl, Wh, Wl, partial);
     else
         MSRSB_PDL((dcgs2_dots_df_kernel<1>), grid, 256, 0, s, N, nv, Vh, Vl, N, Ph, Pl, Wh, Wl, partial);
-    return reduce_partials(2 * (nv + 1), kArnBlocks, partial, d, s);
+    return MSRSB_OK;
 }
 
 msrsb_status arnoldi_dots(long N, int nv, const double *V, const double *P, const double *Wv, double *partial,
-                          double *d, cudaStream_t s) {
+                          cudaStream_t s) {
     dim3 grid(kArnBlocks, nv + 1);
     MSRSB_PDL((dcgs2_dots_kernel), grid, 256, 0, s, N, nv, V, N, P, Wv, partial);
-    return reduce_partials(2 * (nv + 1), kArnBlocks, partial, d, s);
+    return MSRSB_OK;
 }
 
-msrsb_status arnoldi_scalar(int m, int j, int full, double *kh, cudaStream_t s) {
+// the step's scalars from the partials the dots left in `partial`
+msrsb_status arnoldi_scalar(int m, int j, int full, const double *partial, double *kh, cudaStream_t s) {
     if (m > 512 || j > m) return fail(MSRSB_EINVAL, "Arnoldi step %d of %d", j, m);
-    MSRSB_PDL((dcgs2_scalar_kernel), 1, 256, 0, s, m, j, full, kh);
+    MSRSB_PDL((dcgs2_scalar_kernel), 1, 256, 0, s, m, j, full, kArnBlocks, partial, kh);
     return MSRSB_OK;
 }
 

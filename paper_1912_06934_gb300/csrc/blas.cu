@@ -462,12 +462,6 @@ template msrsb_status mdot<double>(long, int, const double *, long, const double
 template msrsb_status mdot<float>(long, int, const float *, long, const float *, double *, double *, int, cudaStream_t,
                                   const int *);
 
-// out[j] = sum_b partial[j][b], b < nblk, j < nvec
-msrsb_status reduce_partials(int nvec, int nblk, const double *partial, double *out, cudaStream_t s) {
-    MSRSB_PDL((reduce_partials_kernel), nvec, 256, 0, s, nblk, partial, out, 0, 0, nullptr);
-    return MSRSB_OK;
-}
-
 msrsb_status norm2(long N, const double *w, double *partial, double *out, cudaStream_t s) {
     dim3 grid(kRedBlocks, 1);
     MSRSB_PDL((mdot_kernel<double>), grid, 256, 0, s, N, w, N, w, partial, nullptr);

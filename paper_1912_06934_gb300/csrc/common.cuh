@@ -231,10 +231,10 @@ __device__ __forceinline__ double warp_max(double v) {
 // H[(m+1) x m] column-major (Givens-rotated in place) | cs[m] | sn[m] | g[m+1] |
 // est | beta | h2[m+2] | est_hist[m+1] | flag[8] | Hu[(m+1) x m] (the
 // Hessenberg matrix as the Arnoldi steps define it) | R[m x m] column-major
-// (upper triangular, Zhat = Z R) | d[2m+2] (one step's dot products) |
-// cv[m] | cp[m+1] | scal[4] (one step's update coefficients)
+// (upper triangular, Zhat = Z R) | cv[m] | cp[m+1] | scal[4] (one Arnoldi
+// step's update coefficients)
 struct KhLayout {
-    long H, cs, sn, g, est, beta, h2, hist, flag, Hu, R, d, cv, cp, scal, total;
+    long H, cs, sn, g, est, beta, h2, hist, flag, Hu, R, cv, cp, scal, total;
     __host__ __device__ explicit KhLayout(int m) {
         H = 0;
         cs = (long)(m + 1) * m;
@@ -247,8 +247,7 @@ struct KhLayout {
         flag = hist + m + 1;
         Hu = flag + 8;
         R = Hu + (long)(m + 1) * m;
-        d = R + (long)m * m;
-        cv = d + 2 * m + 2;
+        cv = R + (long)m * m;
         cp = cv + m;
         scal = cp + m + 1;
         total = scal + 4;
