@@ -24,7 +24,8 @@
 
 namespace msrsb {
 
-constexpr int kArnBlocks = 76;  // row chunks of the dot products (fixed reduction order)
+constexpr int kArnBlocks = 76;  // row chunks of the dot products (fixed reduction order; a multiple of 4)
+static_assert(kArnBlocks % 4 == 0, "the step's scalars sum the chunks in four fixed quarters");
 
 // ---- pass 1: dot products ------------------------------------------------------------------
 
@@ -135,7 +136,7 @@ __global__ void __launch_bounds__(256) dcgs2_dots_kernel(long N, int nv, const d
 // `full` also R[:, j] = (s, alpha), the provisional column j of Hu
 // (V_j^T w_j) and the update coefficients cv = s / alpha (for v_j),
 // cp = H s / alpha + Hu[:, j] (for the next p), scal[0] = 1 / alpha.
-__global__ void __launch_bounds__(256) dcgs2_scalar_kernel(int m, int j, int full, int nblk,
+__global__ void __launch_bounds__(256) dcgs2_scalar_kernel(int m, int j, int full,
                                                            const double *__restrict__ partial,
                                                            double *__restrict__ kh) {
     pdl_prologue();
@@ -144,12 +145,20 @@ __global__ void __launch_bounds__(256) dcgs2_scalar_kernel(int m, int j, int ful
     double *cv = kh + L.cv, *cp = kh + L.cp, *sc = kh + L.scal;
     __shared__ double s_d[2 * 513], s_hs[513];
     __shared__ double s_ss, s_st;
-    const int tid = threadIdx.x, lane = tid & 31;
-    for (int row = tid >> 5; row < 2 * (j + 1); row += blockDim.x >> 5) {
-        double a = 0.0;
-        for (int b = lane; b < nblk; b += 32) a += partial[(long)row * nblk + b];
-        a = warp_sum(a);
-        if (lane == 0) s_d[row] = a;
+    const int tid = threadIdx.x;
+    {  // four lanes per product, each a fixed quarter of the chunks, loads issued together
+        const int sub = tid & 3, nrows = 2 * (j + 1);
+        for (int row0 = 0; row0 < nrows; row0 += 64) {
+            const int row = row0 + (tid >> 2);
+            double a = 0.0;
+            if (row < nrows) {
+#pragma unroll
+                for (int k = 0; k < kArnBlocks / 4; ++k) a += partial[(long)row * kArnBlocks + sub + 4 * k];
+            }
+            a += __shfl_xor_sync(0xffffffffu, a, 1);
+            a += __shfl_xor_sync(0xffffffffu, a, 2);
+            if (sub == 0 && row < nrows) s_d[row] = a;
+        }
     }
     __syncthreads();
     const double *s_s = s_d;  // s_q = s_d[2q], t_q = s_d[2q + 1]
@@ -335,7 +344,7 @@ msrsb_status arnoldi_dots(long N, int nv, const double *V, const double *P, cons
 // the step's scalars from the partials the dots left in `partial`
 msrsb_status arnoldi_scalar(int m, int j, int full, const double *partial, double *kh, cudaStream_t s) {
     if (m > 512 || j > m) return fail(MSRSB_EINVAL, "Arnoldi step %d of %d", j, m);
-    MSRSB_PDL((dcgs2_scalar_kernel), 1, 256, 0, s, m, j, full, kArnBlocks, partial, kh);
+    MSRSB_PDL((dcgs2_scalar_kernel), 1, 256, 0, s, m, j, full, partial, kh);
     return MSRSB_OK;
 }
 
