@@ -249,10 +249,7 @@ msrsb_status msrsb_setup(const msrsb_mat *A, const msrsb_grid *g, const msrsb_op
                          msrsb_handle **out, cudaStream_t stream);
 
 /* Alg. 4 (with Alg. 3 inside) from z = 0: optional pre-smoothing, coarse
- * correction with the residual, optional post-smoothing. v, z: FP64[n*bdim].
- * Asynchronous on `stream`. The line-block ILU(0) sweeps run as one launch
- * whose blocks wait (bounded) on their neighbours; a wait that expires is
- * reported as MSRSB_ETIMEOUT by the handle's next msrsb_solve. */
+ * correction with the residual, optional post-smoothing. v, z: FP64[n*bdim]. */
 msrsb_status msrsb_apply(msrsb_handle *h, const double *v, double *z, cudaStream_t stream);
 
 /* Krylov solve of A x = b preconditioned by Alg. 4: right-preconditioned
@@ -262,8 +259,7 @@ msrsb_status msrsb_apply(msrsb_handle *h, const double *v, double *z, cudaStream
  * receive the iteration count and the final true relative residual; hist_h
  * (nullable, host, maxit+1 doubles) the relative residual estimate per
  * iteration. Returns MSRSB_ENOCONV, with x holding the last iterate, when
- * maxit is reached first, and MSRSB_ETIMEOUT when a bounded wait of the
- * ILU(0) sweeps expired (the result is then not valid). */
+ * maxit is reached first. */
 msrsb_status msrsb_solve(msrsb_handle *h, const double *b, double *x, double rtol, int32_t maxit,
                          int32_t *iters_h, double *relres_h, double *hist_h, cudaStream_t stream);
 

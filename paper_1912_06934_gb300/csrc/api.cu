@@ -130,7 +130,6 @@ msrsb_status lines_setup(msrsb_handle *h, TF *lu, cudaStream_t s);
 msrsb_status stencil_check(const msrsb_mat *A, const msrsb_grid *g, cudaStream_t s);
 template <typename T, typename TZ>
 msrsb_status lines_apply(const msrsb_handle *h, T *ry, TZ *z, cudaStream_t s);
-msrsb_status lines_check(const msrsb_handle *h, cudaStream_t s);
 void lines_free(IluLines *L, cudaStream_t s);
 // z += M^-1 r for the ILU(0) smoother, r in the smoother's order
 template <typename T, typename TZ>
@@ -1135,7 +1134,6 @@ extern "C" msrsb_status msrsb_solve(msrsb_handle *h, const double *b, double *x,
     if (iters_h) *iters_h = its;
     if (relres_h) *relres_h = rr;
     if (st == MSRSB_OK) MSRSB_CUDA(cudaStreamSynchronize(stream));
-    if (st == MSRSB_OK) st = lines_check(h, stream);
     return st;
 }
 

@@ -197,13 +197,6 @@ struct IluLines {
     int16_t *lidx = nullptr, *uidx = nullptr;  // in-block entries: index inside the block
     void *lval = nullptr, *uval = nullptr, *lvin = nullptr, *uvin = nullptr;
     void *lrec = nullptr, *urec = nullptr, *udinv = nullptr;
-    // dataflow application (lines_flow_kernel): block geometry and state
-    int dim = 0, nby = 0, nbz = 0, nblk = 0;
-    int32_t *blk_geo = nullptr;             // by | bz << 16 of every block
-    int32_t *grid_blk = nullptr;            // block at (by, bz): [bz * nby + by]
-    unsigned *done = nullptr;               // [2 nblk]: epoch of each block's finished forward / backward pass
-    unsigned long long *ticket = nullptr;   // [0] next item, [1] CTAs that finished, [2] launches so far
-    int *err = nullptr;                     // 1 when a wait gave up
 };
 
 // ---- device helpers -------------------------------------------------------

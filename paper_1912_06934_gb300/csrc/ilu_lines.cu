@@ -19,7 +19,6 @@
 // per block, one warp per line, on a wavefront: line q trails line q-1 by two
 // points, since (x, q) needs (x+1, q-1).
 #include "common.cuh"
-#include <atomic>
 #include <climits>
 #include <vector>
 #include <cub/device/device_radix_sort.cuh>
@@ -489,85 +488,50 @@ __device__ __forceinline__ T line_in_sum(const LineCoef<T> &cf, const T *sm, int
     return acc;
 }
 
-// One colour's sweep data.
-template <typename T>
-struct LineColour {
-    int c0, m, wl, wli, wu, wui;
-    const int32_t *lcol, *ucol;
-    const int16_t *lidx, *uidx;
-    const T *lval, *uval, *lvin, *uvin;
-};
-template <typename T>
-__device__ __forceinline__ LineColour<T> line_colour(const IluLines &L, int c) {
-    LineColour<T> C;
-    C.c0 = L.cptr[c];
-    C.m = L.cptr[c + 1] - L.cptr[c];
-    C.wl = L.wl[c];
-    C.wli = L.wli[c];
-    C.wu = L.wu[c];
-    C.wui = L.wui[c];
-    C.lcol = L.lcol + L.lbase[c];
-    C.ucol = L.ucol + L.ubase[c];
-    C.lidx = L.lidx + L.libase[c];
-    C.uidx = L.uidx + L.uibase[c];
-    C.lval = (const T *)L.lval + L.lbase[c];
-    C.uval = (const T *)L.uval + L.ubase[c];
-    C.lvin = (const T *)L.lvin + L.libase[c];
-    C.uvin = (const T *)L.uvin + L.uibase[c];
-    return C;
-}
-
-// Vector loads of values other CTAs of the same launch may have written
-// (CG: through L2, past this SM's L1).
-template <bool CG, typename T>
-__device__ __forceinline__ T ld_vec(const T *p) {
-    if constexpr (CG) return __ldcg(p);
-    else return *p;
-}
-
-// One line block's pass. mode 0: forward over the block's lines; 1:
-// backward; 2: forward then backward (the last colour). One thread per
-// point: line q is held by threads q * nxp ... q * nxp + nx - 1 (nxp = nx
-// rounded up to a whole warp), the block's values in shared memory (sm: 4 nx
-// values, then 64 for the scan). The contributions from other blocks are
-// gathered by every point at once; the lines then follow in turn, each a
-// scan over its threads, with each thread's in-block coefficients in
-// registers. wait() runs after the coefficients are loaded and before any
-// vector is read.
-template <typename T, typename TZ, bool CG, typename Wait>
-__device__ __forceinline__ void lines_block(int mode, int b, const LineColour<T> &C, const IluLines &L, int nxp,
-                                            T *__restrict__ y, TZ *__restrict__ z, T *sm, Wait wait) {
-    const int nx = L.nx;
-    T *wA = sm + 4 * nx, *wB = wA + 32;  // composed maps of the warps
-    const int st = L.blk_start[b], nsub = L.blk_nsub[b];
+// mode 0: forward over the block's lines; 1: backward; 2: forward then
+// backward (the last colour). One CTA per block, one thread per point: line q
+// is held by threads q * nxp ... q * nxp + nx - 1 (nxp = nx rounded up to a
+// whole warp), the block's values in shared memory. The contributions from
+// other blocks are gathered by every point at once; the lines then follow in
+// turn, each a scan over its threads, with each thread's in-block
+// coefficients already in registers.
+template <typename T, typename TZ>
+__global__ void __launch_bounds__(1024) lines_sweep_kernel(
+    int mode, int b0, const int32_t *__restrict__ blk_start, const int32_t *__restrict__ blk_nsub, int nx, int nxp,
+    int c0, int m, int wl, const int32_t *__restrict__ lcol, const T *__restrict__ lval, int wli,
+    const int16_t *__restrict__ lidx, const T *__restrict__ lvin, const T *__restrict__ lrec, int wu,
+    const int32_t *__restrict__ ucol, const T *__restrict__ uval, int wui, const int16_t *__restrict__ uidx,
+    const T *__restrict__ uvin, const T *__restrict__ urec, const T *__restrict__ udinv,
+    const int32_t *__restrict__ rows, T *__restrict__ y, TZ *__restrict__ z) {
+    extern __shared__ unsigned char s_raw[];
+    T *sm = reinterpret_cast<T *>(s_raw);  // [4 * nx]
+    T *wA = sm + 4 * nx, *wB = wA + 32;    // composed maps of the warps
+    const int b = b0 + blockIdx.x;
+    const int st = blk_start[b], nsub = blk_nsub[b];
     const int q = threadIdx.x / nxp, xx = threadIdx.x - q * nxp, lane = threadIdx.x & 31;
     const int wline = xx >> 5;  // this warp's place in its line
     const bool on = q < nsub && xx < nx;
-    const int lf = q * nx + xx;             // the point of the forward sweep
+    const int lf = q * nx + xx;           // the point of the forward sweep
     const int lb = q * nx + (nx - 1 - xx);  // the point of the backward sweep (from the line's end)
-    const T *lrec = (const T *)L.lrec, *urec = (const T *)L.urec, *udinv = (const T *)L.udinv;
-    const int c0 = C.c0, m = C.m;
-    LineColour<T> K = C;
     LineCoef<T> cf;
     if (mode != 1)
-        line_coef_load(cf, on, lf, st, c0, m, K.wli, K.lidx, K.lvin, lrec, (const T *)nullptr);
+        line_coef_load(cf, on, lf, st, c0, m, wli, lidx, lvin, lrec, (const T *)nullptr);
     else
-        line_coef_load(cf, on, lb, st, c0, m, K.wui, K.uidx, K.uvin, urec, udinv);
-    wait();
+        line_coef_load(cf, on, lb, st, c0, m, wui, uidx, uvin, urec, udinv);
+    pdl_prologue();
     if (mode != 1) {
         if (on) {  // s = r - sum_off L y
             const int r = st + lf - c0;
             T acc = T(0);
-            for (int j = 0; j < K.wl; ++j)
-                acc = fma(K.lval[(long)j * m + r], ld_vec<CG>(y + K.lcol[(long)j * m + r]), acc);
-            sm[lf] = ld_vec<CG>(y + st + lf) - acc;
+            for (int j = 0; j < wl; ++j) acc = fma(lval[(long)j * m + r], y[lcol[(long)j * m + r]], acc);
+            sm[lf] = y[st + lf] - acc;
         }
         __syncthreads();
         for (int qq = 0; qq < nsub; ++qq) {
             const bool act = q == qq && xx < nx;
             T a = T(0), bb = T(1);
             if (act) {
-                a = line_in_sum(cf, sm, lf, st, c0, m, K.wli, K.lidx, K.lvin);
+                a = line_in_sum(cf, sm, lf, st, c0, m, wli, lidx, lvin);
                 bb = -cf.rec;
             }
             const T v = cta_line_scan<T>(a, bb, lane, wline, wA, wB);
@@ -578,9 +542,9 @@ __device__ __forceinline__ void lines_block(int mode, int b, const LineColour<T>
             __syncthreads();
         }
         if (mode == 0) return;
-        line_coef_load(cf, on, lb, st, c0, m, K.wui, K.uidx, K.uvin, urec, udinv);
+        line_coef_load(cf, on, lb, st, c0, m, wui, uidx, uvin, urec, udinv);
     } else {
-        if (on) sm[lf] = ld_vec<CG>(y + st + lf);
+        if (on) sm[lf] = y[st + lf];
         __syncthreads();
     }
     // backward: t = y - sum_off U e in place; then the lines from the last, each
@@ -588,8 +552,7 @@ __device__ __forceinline__ void lines_block(int mode, int b, const LineColour<T>
     if (on) {
         const int r = st + lf - c0;
         T acc = T(0);
-        for (int j = 0; j < K.wu; ++j)
-            acc = fma(K.uval[(long)j * m + r], ld_vec<CG>(y + K.ucol[(long)j * m + r]), acc);
+        for (int j = 0; j < wu; ++j) acc = fma(uval[(long)j * m + r], y[ucol[(long)j * m + r]], acc);
         sm[lf] -= acc;
     }
     __syncthreads();
@@ -597,7 +560,7 @@ __device__ __forceinline__ void lines_block(int mode, int b, const LineColour<T>
         const bool act = q == qq && xx < nx;
         T a = T(0), bb = T(1);
         if (act) {
-            const T acc = line_in_sum(cf, sm, lb, st, c0, m, K.wui, K.uidx, K.uvin);
+            const T acc = line_in_sum(cf, sm, lb, st, c0, m, wui, uidx, uvin);
             a = cf.d * acc;
             bb = -cf.d * cf.rec;
         }
@@ -605,120 +568,10 @@ __device__ __forceinline__ void lines_block(int mode, int b, const LineColour<T>
         if (act) {
             sm[lb] = v;
             y[st + lb] = v;
-            const int row = L.rows[st + lb];
-            z[row] = TZ(ld_vec<CG>(z + row) + TZ(v));
+            const int row = rows[st + lb];
+            z[row] = TZ(z[row] + TZ(v));
         }
         __syncthreads();
-    }
-}
-
-// One colour per launch: CTA b0 + blockIdx.x handles block b0 + blockIdx.x.
-template <typename T, typename TZ>
-__global__ void __launch_bounds__(1024) lines_sweep_kernel(int mode, int c, const IluLines L, int nxp,
-                                                           T *__restrict__ y, TZ *__restrict__ z) {
-    extern __shared__ unsigned char s_raw[];
-    const LineColour<T> C = line_colour<T>(L, c);
-    lines_block<T, TZ, false>(mode, L.bptr[c] + blockIdx.x, C, L, nxp, y, z, reinterpret_cast<T *>(s_raw),
-                              [] { pdl_prologue(); });
-}
-
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-constexpr int kFlowSpin = 1 << 22;  // polls (each after a short sleep) before a wait gives up
-
-// Every colour's sweep in one persistent launch. Items, numbered in this
-// order and taken from a counter: the blocks' forward passes in block order
-// (colour by colour; the last colour's with its backward pass), then the
-// backward passes of colours ncol-2 .. 0. An item waits for the items whose
-// results it reads: a forward pass for the forward passes of its neighbour
-// blocks of lower colours, a backward pass for its own forward pass and the
-// backward passes of its neighbour blocks of higher colours (neighbours: the
-// blocks one step away in y and z, as the pattern lies within each point's
-// 3^dim neighbourhood). A neighbour's backward pass, which overwrites what a
-// forward pass reads, itself waits for that forward pass's block. Items only
-// wait for items of lower numbers, which running CTAs took, so the lowest
-// unfinished item can always proceed. A wait that gives up sets *err and the
-// item goes on (its result is then not valid). A launch marks finished items
-// with its number (epoch), so no flag is reset between launches; the last
-// CTA to finish resets the item counter and counts the launch.
-template <typename T, typename TZ>
-__global__ void __launch_bounds__(1024) lines_flow_kernel(const IluLines L, int nxp, T *__restrict__ y,
-                                                          TZ *__restrict__ z) {
-    extern __shared__ unsigned char s_raw[];
-    T *sm = reinterpret_cast<T *>(s_raw);
-    __shared__ int s_item;
-    pdl_prologue();
-    const unsigned epoch = (unsigned)__ldcg(L.ticket + 2) + 1u;
-    const int last = L.ncol - 1, nb = L.nblk, items = nb + L.bptr[last];
-    for (;;) {
-        if (threadIdx.x == 0) s_item = (int)atomicAdd(L.ticket, 1ull);
-        __syncthreads();
-        const int t = s_item;
-        __syncthreads();  // read before the next item overwrites it
-        if (t >= items) break;
-        int b, c, mode;
-        if (t < nb) {
-            b = t;
-            c = 0;
-            while (b >= L.bptr[c + 1]) ++c;
-            mode = c == last ? 2 : 0;
-        } else {
-            int u = t - nb;
-            c = last - 1;
-            while (u >= L.bptr[c + 1] - L.bptr[c]) {
-                u -= L.bptr[c + 1] - L.bptr[c];
-                --c;
-            }
-            b = L.bptr[c] + u;
-            mode = 1;
-        }
-        const LineColour<T> C = line_colour<T>(L, c);
-        auto wait = [&] {
-            if (threadIdx.x < 9) {  // thread k: the block at offset (k % 3 - 1, k / 3 - 1) in (y, z)
-                const int g = L.blk_geo[b], by = g & 0xffff, bz = g >> 16;
-                const int dy = (int)threadIdx.x % 3 - 1, dz = (int)threadIdx.x / 3 - 1;
-                const int ny2 = by + dy, nz2 = bz + dz;
-                const unsigned *flag = nullptr;
-                if (dy == 0 && dz == 0) {
-                    if (mode == 1) flag = L.done + 2 * b;  // own forward pass
-                } else if ((L.dim == 3 || dz == 0) && ny2 >= 0 && ny2 < L.nby && nz2 >= 0 && nz2 < L.nbz) {
-                    const int nbh = L.grid_blk[nz2 * L.nby + ny2];
-                    const int cn = (ny2 & 1) | (L.dim == 3 ? ((nz2 & 1) << 1) : 0);
-                    if (mode != 1 && cn < c) flag = L.done + 2 * nbh;
-                    if (mode == 1 && cn > c) flag = L.done + 2 * nbh + 1;
-                }
-                if (flag) {
-                    int it = 0;
-                    while (ld_acquire_u32(flag) != epoch) {
-                        if (++it > kFlowSpin) {
-                            atomicExch(L.err, 1);
-                            break;
-                        }
-                        __nanosleep(32);
-                    }
-                }
-            }
-            __syncthreads();
-        };
-        lines_block<T, TZ, true>(mode, b, C, L, nxp, y, z, sm, wait);
-        __syncthreads();  // every thread's stores are issued
-        if (threadIdx.x == 0) {
-            __threadfence();
-            if (mode != 1) st_release_u32(L.done + 2 * b, epoch);
-            if (mode != 0) st_release_u32(L.done + 2 * b + 1, epoch);
-        }
-    }
-    if (threadIdx.x == 0 && atomicAdd(L.ticket + 1, 1ull) == gridDim.x - 1) {  // every CTA has read the epoch
-        L.ticket[0] = 0;
-        L.ticket[1] = 0;
-        L.ticket[2] = epoch;
     }
 }
 
@@ -762,7 +615,7 @@ msrsb_status lines_setup(msrsb_handle *h, TF *lu, cudaStream_t s) {
     MSRSB_LAUNCHED("lines_pos_kernel");
     // ---- block table (host): blocks of each colour in block order ----
     const int nby = (ny + 1) / 2, nbz = dim == 3 ? (nz + 1) / 2 : 1;
-    std::vector<int32_t> bstart, bnsub, bgeo, gblk((size_t)nby * nbz);
+    std::vector<int32_t> bstart, bnsub;
     int run = 0;
     for (int c = 0; c < L.ncol; ++c) {
         L.cptr[c] = run;
@@ -772,17 +625,11 @@ msrsb_status lines_setup(msrsb_handle *h, TF *lu, cudaStream_t s) {
                 const int cc = (by & 1) | (dim == 3 ? ((bz & 1) << 1) : 0);
                 if (cc != c) continue;
                 const int sy = ny - 2 * by < 2 ? 1 : 2, sz = dim == 3 ? (nz - 2 * bz < 2 ? 1 : 2) : 1;
-                gblk[(size_t)bz * nby + by] = (int32_t)bstart.size();
-                bgeo.push_back(by | bz << 16);
                 bstart.push_back(run);
                 bnsub.push_back(sy * sz);
                 run += sy * sz * nx;
             }
     }
-    L.dim = dim;
-    L.nby = nby;
-    L.nbz = nbz;
-    L.nblk = (int)bstart.size();
     L.cptr[L.ncol] = run;
     L.bptr[L.ncol] = (int)bstart.size();
     if (run != n) return fail(MSRSB_ESHAPE, "line blocks cover %d of %d rows", run, n);
@@ -791,18 +638,6 @@ msrsb_status lines_setup(msrsb_handle *h, TF *lu, cudaStream_t s) {
     MSRSB_TRY(dalloc(&L.blk_nsub, nblk, s));
     MSRSB_CUDA(cudaMemcpyAsync(L.blk_start, bstart.data(), nblk * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     MSRSB_CUDA(cudaMemcpyAsync(L.blk_nsub, bnsub.data(), nblk * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-    // state of the persistent sweeps (lines_flow_kernel)
-    if (nby >= 65536 || nbz >= 32768) return fail(MSRSB_ESHAPE, "too many line blocks along y or z");
-    MSRSB_TRY(dalloc(&L.blk_geo, nblk, s));
-    MSRSB_TRY(dalloc(&L.grid_blk, (size_t)nby * nbz, s));
-    MSRSB_TRY(dalloc(&L.done, 2 * (size_t)nblk, s));
-    MSRSB_TRY(dalloc(&L.ticket, 3, s));
-    MSRSB_TRY(dalloc(&L.err, 1, s));
-    MSRSB_CUDA(cudaMemcpyAsync(L.blk_geo, bgeo.data(), nblk * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-    MSRSB_CUDA(cudaMemcpyAsync(L.grid_blk, gblk.data(), gblk.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-    MSRSB_CUDA(cudaMemsetAsync(L.done, 0, 2 * (size_t)nblk * sizeof(unsigned), s));
-    MSRSB_CUDA(cudaMemsetAsync(L.ticket, 0, 3 * sizeof(unsigned long long), s));
-    MSRSB_CUDA(cudaMemsetAsync(L.err, 0, sizeof(int), s));
     // ---- factorisation, colour by colour ----
     int *status = nullptr;
     TF *rdiag = nullptr;
@@ -899,44 +734,21 @@ template msrsb_status lines_setup<float>(msrsb_handle *, float *, cudaStream_t);
 
 // z += U^-1 L^-1 r with r given in the line-block order in ry (overwritten):
 // 2 C - 1 launches for C colours, one CTA per line block
-// CTAs of the persistent launch: as many as are resident at once, found
-// once per instantiation and block size.
-template <typename T, typename TZ>
-static int flow_grid(int threads, size_t smem) {
-    static std::atomic<unsigned long long> cache{0};  // threads << 32 | grid
-    const unsigned long long c = cache.load();
-    if (c && (int)(c >> 32) == threads) return (int)(c & 0xffffffffu);
-    int dev = 0, nsm = 0, per = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, lines_flow_kernel<T, TZ>, threads, smem) != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
-    }
-    const int g = nsm * per;
-    cache.store((unsigned long long)threads << 32 | (unsigned)g);
-    return g;
-}
-
-// z += U^-1 L^-1 r with r given in the line-block order in ry (overwritten):
-// one persistent launch over every colour (lines_flow_kernel), or, where
-// that cannot be resident, 2 C - 1 launches for C colours, one CTA per line
-// block.
 template <typename T, typename TZ>
 msrsb_status lines_apply(const msrsb_handle *h, T *ry, TZ *z, cudaStream_t s) {
     const IluLines &L = h->lines;
     const int last = L.ncol - 1, nxp = ((L.nx + 31) / 32) * 32;
-    const int threads = (L.ncol == 4 ? 4 : 2) * nxp;
+    const int nsub_max = L.ncol == 4 ? 4 : 2;
     const size_t smem = (4 * (size_t)L.nx + 64) * sizeof(T);
-    const int g = L.ticket ? flow_grid<T, TZ>(threads, smem) : 0;
-    if (g > 0) {
-        MSRSB_PDL((lines_flow_kernel<T, TZ>), g, threads, smem, s, L, nxp, ry, z);
-        return MSRSB_OK;
-    }
     auto launch = [&](int mode, int c) -> msrsb_status {
         const int nb = L.bptr[c + 1] - L.bptr[c];
         if (!nb) return MSRSB_OK;
-        MSRSB_PDL((lines_sweep_kernel<T, TZ>), nb, threads, smem, s, mode, c, L, nxp, ry, z);
+        const int m = L.cptr[c + 1] - L.cptr[c];
+        MSRSB_PDL((lines_sweep_kernel<T, TZ>), nb, nsub_max * nxp, smem, s, mode, L.bptr[c], L.blk_start,
+                  L.blk_nsub, L.nx, nxp, L.cptr[c], m, L.wl[c], L.lcol + L.lbase[c], (const T *)L.lval + L.lbase[c],
+                  L.wli[c], L.lidx + L.libase[c], (const T *)L.lvin + L.libase[c], (const T *)L.lrec, L.wu[c],
+                  L.ucol + L.ubase[c], (const T *)L.uval + L.ubase[c], L.wui[c], L.uidx + L.uibase[c],
+                  (const T *)L.uvin + L.uibase[c], (const T *)L.urec, (const T *)L.udinv, L.rows, ry, z);
         return MSRSB_OK;
     };
     for (int c = 0; c < last; ++c) MSRSB_TRY(launch(0, c));
@@ -944,26 +756,11 @@ msrsb_status lines_apply(const msrsb_handle *h, T *ry, TZ *z, cudaStream_t s) {
     for (int c = last - 1; c >= 0; --c) MSRSB_TRY(launch(1, c));
     return MSRSB_OK;
 }
-
-// MSRSB_ETIMEOUT if a wait of the persistent sweeps gave up since set-up
-msrsb_status lines_check(const msrsb_handle *h, cudaStream_t s) {
-    if (!h->use_lines || !h->lines.err) return MSRSB_OK;
-    int e = 0;
-    MSRSB_CUDA(cudaMemcpyAsync(&e, h->lines.err, sizeof(int), cudaMemcpyDeviceToHost, s));
-    MSRSB_CUDA(cudaStreamSynchronize(s));
-    if (e) return fail(MSRSB_ETIMEOUT, "ILU(0) sweeps: a wait for a neighbour block gave up");
-    return MSRSB_OK;
-}
 template msrsb_status lines_apply<double, double>(const msrsb_handle *, double *, double *, cudaStream_t);
 template msrsb_status lines_apply<float, double>(const msrsb_handle *, float *, double *, cudaStream_t);
 template msrsb_status lines_apply<float, float>(const msrsb_handle *, float *, float *, cudaStream_t);
 
 void lines_free(IluLines *L, cudaStream_t s) {
-    dfree(L->blk_geo, s);
-    dfree(L->grid_blk, s);
-    dfree(L->done, s);
-    dfree(L->ticket, s);
-    dfree(L->err, s);
     dfree(L->lidx, s);
     dfree(L->uidx, s);
     dfree(L->lvin, s);
