@@ -273,14 +273,12 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
     MSRSB_TRY(partition_launch(&h->grid, h->part, h->cnode, h->p_ids, h->skel, h->colour, s));
     MSRSB_TRY(mark(1));
     // the smoother set-up (independent of P) on a side stream, from a second
-    // host thread, while this thread builds the basis. The side stream has the
-    // highest priority: its kernels are latency-bound chains of few CTAs that
-    // would otherwise wait behind the basis kernels, which fill every SM.
-    if (!h->side) {
-        int least = 0, greatest = 0;
-        MSRSB_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
-        MSRSB_CUDA(cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, greatest));
-    }
+    // host thread, while this thread builds the basis. The side stream keeps
+    // the default priority: its latency-bound factorisation kernels then take
+    // the SM slots the bandwidth-bound smoothing passes leave (at the highest
+    // priority they held slots the passes needed and slowed them by more than
+    // they saved; measured at 64^3).
+    if (!h->side) MSRSB_CUDA(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
     cudaEvent_t fork = nullptr, join = nullptr;
     MSRSB_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
     MSRSB_CUDA(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
@@ -297,13 +295,9 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
     std::promise<msrsb_status> tr_done;
     std::future<msrsb_status> tr_status = tr_done.get_future();
     std::string tr_err;
-    // The smoother set-up is held back until the main stream reaches the
-    // coarse factorisation: started with the basis build, its latency-bound
-    // factorisation kernels take SM slots from the bandwidth-bound smoothing
-    // passes and slow them by more than they save (measured at 64^3 and
-    // 128^3), while the coarse factorisation runs on one thread-block cluster
-    // and leaves the other SMs idle. The main thread hands over an event
-    // recorded at that point, or nullptr when it leaves early.
+    // The smoother set-up starts with the basis build. The main thread hands
+    // over an event recorded after the partition, or nullptr when it leaves
+    // early.
     std::promise<cudaEvent_t> go;
     std::future<cudaEvent_t> go_at = go.get_future();
     cudaEvent_t go_ev = nullptr;
@@ -343,6 +337,8 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
         }
         ~Release() { (*this)(nullptr); }
     } release{go};
+    MSRSB_CUDA(cudaEventRecord(go_ev, s));
+    release(go_ev);
     // filtered operator(s) streamed as sliced ELL, then Alg. 1 per component
     T *P = nullptr;
     MSRSB_TRY(dalloc(&P, nW * bd, s));
@@ -408,8 +404,6 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
         if (Pl != P) dfree(Pl, s);
     }
     MSRSB_TRY(mark(3));
-    MSRSB_CUDA(cudaEventRecord(go_ev, s));
-    release(go_ev);
     if (planes_fit(h->grid.dim, h->nb, bd)) {
         MSRSB_TRY(plane_factor(h->grid.dim, h->nb, bd, h->Acs, &h->planes, s));
         if (h->nC <= kDenseCoarseMax) {
