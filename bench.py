@@ -152,11 +152,15 @@ def kept_entries(c, ids, comp=None):
     return n + int(share.sum()), matches
 
 
-# DRAM bytes (read + write) per launch of smooth_kernel<float,8> on the 64^3
-# workload, from one ncu capture, keyed by a hash of the kernel's source file
-# at the time of the capture; once the source changes the figure no longer
-# describes the kernel and the bench reports null.
-SMOOTH_TRAFFIC = {"basis.cu": ("e3b0c44298fc1c14", None)}
+# DRAM bytes (read + write) per launch of smooth_kernel<float,8>, per
+# workload, from one ncu capture of one launch (caches flushed, as ncu does),
+# keyed by a hash of the kernel's source file at the time of the capture; once
+# the source changes the figure no longer describes the kernel and the bench
+# reports null.
+SMOOTH_TRAFFIC = {
+    "darcy64": ("8ac28f3867c6d3c8", None),
+    "darcy128": ("8ac28f3867c6d3c8", None),
+}
 
 
 def source_hash(name):
@@ -165,8 +169,8 @@ def source_hash(name):
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def smooth_traffic():
-    h, traffic = SMOOTH_TRAFFIC["basis.cu"]
+def smooth_traffic(workload):
+    h, traffic = SMOOTH_TRAFFIC.get(workload, (None, None))
     return traffic if traffic is not None and source_hash("basis.cu") == h else None
 
 
@@ -360,17 +364,18 @@ def form_summary(f, steps):
             "smooth_us_per_launch": f["smooth_ms"] / f["smooth_launches"] * 1e3 if f["smooth_launches"] else None}
 
 
-def smooth_roofline(f, n, W, nnz_hat_list, esize, hbm, peak_kind):
+def smooth_roofline(f, n, W, nnz_hat_list, esize, hbm, peak_kind, traffic=None):
     """HBM roofline of the restricted-smoothing kernel from the profiled
     loops: algorithmic bytes per pass (mean over the basis families, which
-    run the same number of passes here) / mean event-timed pass."""
+    run the same number of passes here) / mean event-timed pass; `traffic`
+    the captured DRAM bytes per launch (or None)."""
     if not f["smooth_launches"]:
         return None
     per = float(np.mean([smooth_bytes(n, k, W, esize) for k in nnz_hat_list]))
     us = f["smooth_ms"] / f["smooth_launches"] * 1e3
     ach = per / (us * 1e-6) / 1e9
     return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-            "bytes_per_launch": per, "us_per_launch": us, "launches": f["smooth_launches"],
+            "bytes_per_launch": per, "us_per_launch": us, "launches": f["smooth_launches"], "traffic": traffic,
             "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"}
 
 
@@ -402,7 +407,8 @@ def run_extra_config(M, name, c, kind, flush, stream, dev, steps, warmup, hbm, p
         else:
             kept = [kept_entries(c, ids)]
             ab = apply_bytes(n, nnzb, nnz_p, info["nc"], W, coarse_apply_bytes(c)) if e == 4 else None
-        out[label]["smooth_roofline"] = smooth_roofline(f, n, W, [k[0] for k in kept], e, hbm, peak_kind)
+        out[label]["smooth_roofline"] = smooth_roofline(f, n, W, [k[0] for k in kept], e, hbm, peak_kind,
+                                                        smooth_traffic(name) if label == "mixed" else None)
         if e == 8 and f["smooth_launches"]:
             # the FP64 pass is bound by the FP64 pipe: multiply-adds of A_hat P
             # on the pattern plus the W-wide update per row
@@ -569,7 +575,7 @@ def gpu_arm(args, rank, world):
         "mixed_error_vs_fp64": mixed_err,
         "roofline": {"kernel": "smooth_kernel<float,8> (restricted smoothing, Alg. 1)", "bound": "hbm",
                      "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm if achieved else None, "traffic": smooth_traffic(),
+                     "frac": achieved / hbm if achieved else None, "traffic": smooth_traffic("darcy64"),
                      "bytes_per_launch": per_launch32, "filtered_entries": nnz_hat, "launches": sm_l32,
                      "us_per_launch": sm_ms32 / sm_l32 * 1e3 if sm_l32 else None,
                      "l2_resident": "the kept operator (28 MB) and both P buffers stay in L2 across the passes "
@@ -721,15 +727,21 @@ def reference_arm(args, rank, world):
 
 def profile_run(args):
     """Workloads for profilers (no timing output): 'solve' runs the mixed
-    set-up + GMRES solve of the benchmark twice; 'basis' runs three restricted
-    smoothing passes (FP32) on an N^3 grid twice (N = --grid; N = 64 is the
-    benchmark's operator, any other N uses the same generator at that size)."""
+    set-up + GMRES solve twice; 'basis' runs three restricted smoothing passes
+    (FP32) twice; on an N^3 grid (N = --grid; N = 64 is the benchmark's
+    operator, N = 128 the 128^3 configuration's, any other N the benchmark's
+    generator at that size)."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
     import paper_1912_06934_gb300 as M
     from synth.darcy import darcy_3d_case
-    c = make_problem() if args.grid == N_GRID else darcy_3d_case(n=args.grid, H=H_BLOCK, seed=SEED)
+    if args.grid == N_GRID:
+        c = make_problem()
+    elif args.grid == 128:
+        c = device_case(M, 128, 1005, 2.0)  # the 128^3 configuration's operator
+    else:
+        c = darcy_3d_case(n=args.grid, H=H_BLOCK, seed=SEED)
     A = M.Mat.from_host(c["indptr"], c["indices"], c["data"])
     g = M.grid(c["dims"], c["H"])
     if args.profile == "solve":
