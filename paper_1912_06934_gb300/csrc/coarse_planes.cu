@@ -5,19 +5,24 @@
 // step away on every axis (Eq. 3 with the support regions of Sec. 2.1).
 // Numbered plane by plane along the last grid axis (z in 3D, y in 2D), A_c is
 // block tridiagonal: D_k on the diagonal (the couplings inside plane k),
-// L_k = A_c[k][k-1] and U_k = A_c[k][k+1]. Its block LU factorisation
-//   S_0 = D_0,  S_k = D_k - L_k S_{k-1}^-1 U_{k-1},
-// needs only the inverse of each plane's dense Schur complement S_k (m x m,
-// m = nodes per plane x block size) and G_k = S_k^-1 U_k: np m^3 multiply-adds
-// instead of the (np m)^3 of a dense inverse. A_c^-1 v is then
-//   y_0 = S_0^-1 v_0,  y_k = S_k^-1 (v_k - L_k y_{k-1}),
-//   w_{np-1} = y_{np-1},  w_k = y_k - G_k w_{k+1},
-// that is 2 np - 1 dependent dense matrix-vector products.
+// L_k = A_c[k][k-1] and U_k = A_c[k][k+1]. It is factorised from both ends
+// towards the middle plane h = np / 2 (a twisted block factorisation), the
+// two ends concurrently on two thread-block clusters:
+//   planes k < h:  S_k = D_k - L_k G_{k-1},  G_k = S_k^-1 U_k;
+//   planes k > h:  S_k = D_k - U_k G_{k+1},  G_k = S_k^-1 L_k;
+//   plane h:       S_h = D_h - L_h G_{h-1} - U_h G_{h+1},
+// which needs only the inverse of each plane's dense Schur complement S_k
+// (m x m, m = nodes per plane x block size): np m^3 multiply-adds instead of
+// the (np m)^3 of a dense inverse, along a dependent chain of about np / 2
+// planes instead of np. A_c^-1 v is then
+//   y_k = S_k^-1 (v_k - L_k y_{k-1}) (k < h),  y_k = S_k^-1 (v_k - U_k y_{k+1}) (k > h),
+//   w_h = S_h^-1 (v_h - L_h y_{h-1} - U_h y_{h+1}),
+//   w_k = y_k - G_k w_{k+1} (k < h),  w_k = y_k - G_k w_{k-1} (k > h).
 //
 // Every S_k is inverted by Gauss-Jordan elimination with partial pivoting
 // inside the plane (ties to the lowest row; magnitudes compared through the
 // integer order of their FP64 bit patterns). Both the factorisation and the
-// application run as one thread-block cluster (up to 16 CTAs on 16 SMs) whose
+// application run as thread-block clusters (up to 16 CTAs on 16 SMs) whose
 // CTAs own contiguous columns (factorisation) or rows (application) and
 // exchange pivot columns and partial vectors through distributed shared
 // memory, with hardware cluster barriers between steps (no spin waits).
@@ -71,18 +76,39 @@ __device__ __forceinline__ double st_val(const double *__restrict__ Acs, const P
     return Acs[(((long)J * G.nq + q) * G.bd + l) * G.bd + c];
 }
 
+// v - sum over in-plane neighbours b and components c of the coupling of
+// (node J, component l) with plane p's node (stencil entries from `base`)
+// times vec[(neighbour * bd + c) * stride] (vec points at the column or row
+// of plane p wanted)
+__device__ __forceinline__ double sub_coupling(double v, const PlaneGeom &G, const double *__restrict__ Acs, int J,
+                                               int u, int l, int base, const double *vec, long stride) {
+    for (int b = 0; b < G.NI; ++b) {
+        const int tn = plane_nbr(G, u, b);
+        if (tn < 0) continue;
+        for (int c = 0; c < G.bd; ++c) v = fma(-st_val(Acs, G, J, b + base, l, c), vec[(tn * G.bd + c) * stride], v);
+    }
+    return v;
+}
+
 constexpr int kPlaneThreads = 256;
 constexpr int kPlaneMaxCols = 128;  // columns of a plane one CTA of the factorisation owns
 
-// Factorisation. Outputs (row-major m x m per plane): X_k with
-// S_k^-1 = X_k Pi_k (Pi_k the row interchanges of the elimination, kept as
-// the gather pi_k: (Pi_k v)[i] = v[pi_k[i]]), and G_k = S_k^-1 U_k.
+// Factorisation. With middle = 0 the grid holds one cluster per side (side 0:
+// planes 0 .. h-1 upwards, side 1: planes np-1 .. h+1 downwards); with
+// middle = 1 one cluster takes plane h. Outputs (row-major m x m per plane):
+// X_k with S_k^-1 = X_k Pi_k (Pi_k the row interchanges of the elimination,
+// kept as the gather pi_k: (Pi_k v)[i] = v[pi_k[i]]), and G_k for k != h.
 // status[0] = 1 + (global row) on a zero pivot.
-__global__ void __launch_bounds__(kPlaneThreads) plane_factor_kernel(PlaneGeom G, const double *__restrict__ Acs,
+__global__ void __launch_bounds__(kPlaneThreads, 1) plane_factor_kernel(PlaneGeom G, int h, int middle,
+                                                                     const double *__restrict__ Acs,
                                                                      double *__restrict__ X, double *__restrict__ Gm,
                                                                      int *__restrict__ pi, int *__restrict__ status) {
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank(), nct = (int)cluster.num_blocks();
+    // side 0: planes 0 .. h-1 upwards; side 1: planes np-1 .. h+1 downwards;
+    // middle: plane h with the Schur complements from both sides
+    const int side = middle ? 0 : (int)(blockIdx.x / nct);
+    const int nplanes = middle ? 1 : (side == 0 ? h : G.np - 1 - h);
     const int m = G.m, bd = G.bd, NI = G.NI;
     const int cw = (m + nct - 1) / nct;
     const int c0 = rank * cw, c1 = min(m, c0 + cw), ncol = max(0, c1 - c0);
@@ -98,24 +124,28 @@ __global__ void __launch_bounds__(kPlaneThreads) plane_factor_kernel(PlaneGeom G
     __shared__ int s_p[2], s_bad[2];
     __shared__ double s_best[8];
     __shared__ int s_idx[8];
-    for (int k = 0; k < G.np; ++k) {
-        // ---- S_k = D_k - L_k G_{k-1}, own columns ----
+    for (int st = 0; st < nplanes; ++st) {
+        const int k = middle ? h : (side == 0 ? st : G.np - 1 - st);
+        // ---- S_k = D_k - C_{k,p} G_p over the planes p finished before it, own columns ----
+        // (C_{k,p}: the couplings of plane k with plane p = k -+ 1, stencil entries from base 0 / 2 NI)
         const int Jbase = k * G.PN;
+        int pa = -1, pb = -1;  // planes p (their G_p) and stencil bases
+        int ba = 0, bb = 0;
+        if (middle) {
+            if (h > 0) pa = h - 1, ba = 0;
+            if (h + 1 < G.np) pb = h + 1, bb = 2 * NI;
+        } else if (st > 0) {
+            pa = side == 0 ? k - 1 : k + 1;
+            ba = side == 0 ? 0 : 2 * NI;
+        }
         for (int idx = tid; idx < ncol * m; idx += kPlaneThreads) {
             const int jl = idx / m, i = idx - jl * m;
             const int j = c0 + jl;
             const int ui = i / bd, l = i - ui * bd, uj = j / bd, mj = j - uj * bd;
             const int a = plane_offset(G, ui, uj);
             double v = a >= 0 ? st_val(Acs, G, Jbase + ui, a + NI, l, mj) : 0.0;
-            if (k > 0) {
-                const double *Gp = Gm + (long)(k - 1) * m * m;
-                for (int b = 0; b < NI; ++b) {
-                    const int t = plane_nbr(G, ui, b);
-                    if (t < 0) continue;
-                    for (int c = 0; c < bd; ++c)
-                        v = fma(-st_val(Acs, G, Jbase + ui, b, l, c), Gp[(long)(t * bd + c) * m + j], v);
-                }
-            }
+            if (pa >= 0) v = sub_coupling(v, G, Acs, Jbase + ui, ui, l, ba, Gm + (long)pa * m * m + j, m);
+            if (pb >= 0) v = sub_coupling(v, G, Acs, Jbase + ui, ui, l, bb, Gm + (long)pb * m * m + j, m);
             Sown[(long)jl * m + i] = v;
         }
         __syncthreads();
@@ -232,28 +262,28 @@ __global__ void __launch_bounds__(kPlaneThreads) plane_factor_kernel(PlaneGeom G
         if (rank == 0)
             for (int i = tid; i < m; i += kPlaneThreads) pi[(long)k * m + i] = pil[i];
         cluster.sync();  // every CTA's X_k columns are final
-        // ---- G_k = X_k Pi_k U_k, own columns j (rows of plane k+1) ----
-        if (k + 1 < G.np) {
+        // ---- G_k = X_k Pi_k C_{k,q}, q the plane after k on this side (k+1 on
+        // side 0, k-1 on side 1), own columns j (rows of plane q) ----
+        if (!middle) {
             double *Gk = Gm + (long)k * m * m;
-            const int Jnext = (k + 1) * G.PN;
+            const int qb = side == 0 ? 2 * NI : 0;  // stencil entries towards plane q
             for (int idx = tid; idx < ncol * m; idx += kPlaneThreads) {
                 const int i = idx / ncol, jl = idx - i * ncol;
                 const int j = c0 + jl, uj = j / bd, mj = j - uj * bd;
                 double v = 0.0;
-                // rows s of plane k with U_k[s][j] != 0: the in-plane neighbours of uj
+                // rows s of plane k with C_{k,q}[s][j] != 0: the in-plane neighbours of uj
                 for (int a = 0; a < NI; ++a) {
                     const int us = plane_nbr(G, uj, a);
                     if (us < 0) continue;
-                    const int q = plane_offset(G, us, uj) + 2 * NI;  // from s up to j: plane offset +1
+                    const int qq = plane_offset(G, us, uj) + qb;
                     for (int ls = 0; ls < bd; ++ls) {
-                        const double u = st_val(Acs, G, Jbase + us, q, ls, mj);
+                        const double u = st_val(Acs, G, Jbase + us, qq, ls, mj);
                         const int cc = pinv[us * bd + ls];
                         const int ow = cc / cw;
                         const double *xc = cluster.map_shared_rank(Sown, ow) + (long)(cc - ow * cw) * m;
                         v = fma(xc[i], u, v);
                     }
                 }
-                (void)Jnext;
                 Gk[(long)i * m + j] = v;
             }
         }
@@ -261,15 +291,27 @@ __global__ void __launch_bounds__(kPlaneThreads) plane_factor_kernel(PlaneGeom G
     }
 }
 
-// Application w = A_c^-1 v through the plane factors. vc, wc: FP64 [np*m]
-// in coarse dof order; wc32 (nullable) an FP32 copy of w. Steps
-// s = 0 .. 2 np - 2: forward planes k = s, then backward planes
-// k = 2 np - 2 - s. With stage set, every step's own rows of its matrix (a
-// contiguous block of the row-major X_k or G_k), the lower couplings of the
-// stencil and the gather pi_k are copied to shared memory asynchronously two
-// steps ahead (double buffered; they do not depend on the recurrence), so
-// that each step waits only on the cluster barrier and its own arithmetic.
-__global__ void __launch_bounds__(kPlaneThreads) plane_solve_kernel(PlaneGeom G, const double *__restrict__ Acs,
+// Application w = A_c^-1 v through the plane factors, in three launches
+// (phase): 0: the two sides' forward sweeps, y_k = X_k Pi_k (v_k - C y_p)
+// with p the plane before k on its side (side 0: planes 0 .. h-1, p = k-1;
+// side 1: planes np-1 .. h+1, p = k+1), one cluster each; 1: the middle
+// plane, w_h = X_h Pi_h (v_h - C y_{h-1} - C y_{h+1}); 2: the back
+// substitution outwards, w_k = y_k - G_k w_q (q = k+1 on side 0, k-1 on
+// side 1). vc, wc: FP64 [np*m] in coarse dof order (y is kept in wc); wc32
+// (nullable) an FP32 copy of w. With stage set, every step's own rows of its
+// matrix (a contiguous block of the row-major X_k or G_k), the step's
+// couplings and the gather pi_k are copied to shared memory asynchronously
+// two steps ahead (double buffered; they do not depend on the recurrence),
+// so that each step waits only on the cluster barrier and its own arithmetic.
+// the plane of step st of a solve launch (see plane_solve_kernel)
+__device__ __forceinline__ int solve_plane(int phase, int side, int h, int np, int st) {
+    if (phase == 1) return h;
+    if (phase == 0) return side == 0 ? st : np - 1 - st;
+    return side == 0 ? h - 1 - st : h + 1 + st;
+}
+
+__global__ void __launch_bounds__(kPlaneThreads, 1) plane_solve_kernel(PlaneGeom G, int h, int phase,
+                                                                    const double *__restrict__ Acs,
                                                                     const double *__restrict__ X,
                                                                     const double *__restrict__ Gm,
                                                                     const int *__restrict__ pi,
@@ -282,27 +324,29 @@ __global__ void __launch_bounds__(kPlaneThreads) plane_solve_kernel(PlaneGeom G,
     const int rw = (m + nct - 1) / nct;
     const int r0 = rank * rw, r1 = min(m, r0 + rw), nr = max(0, r1 - r0);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nsteps = 2 * np - 1;
-    const int lowc = NI * bd * bd;  // lower-coupling values per node, contiguous in the stencil
+    const int side = phase == 1 ? 0 : (int)(blockIdx.x / nct);
+    const int nsteps = phase == 1 ? 1 : (side == 0 ? h : np - 1 - h);
+    const bool fwd = phase != 2;
+    const int cb = side == 0 ? 0 : 2 * NI;  // stencil entries towards the plane before (phase 0)
+    const int lowc = NI * bd * bd;  // coupling values per node towards one plane, contiguous in the stencil
     extern __shared__ double sm[];
     double *ybuf = sm;          // full plane vector, double buffered [2][m] (written by every CTA)
     double *t = ybuf + 2 * m;   // right-hand side of the plane [m]
     double *tp = t + m;         // t gathered by pi [m]
     double *mat = tp + m;       // staged rows [2][rw*m]
-    double *stc = mat + 2 * (long)rw * m;             // staged lower couplings [2][PN*lowc]
+    double *stc = mat + 2 * (long)rw * m;             // staged couplings [2][PN*lowc]
     int *spi = (int *)(stc + 2 * (long)G.PN * lowc);  // staged pi [2][m]
     auto issue = [&](int st, int buf) {
         if (stage && st < nsteps) {
-            const bool fwd = st < np;
-            const int k = fwd ? st : 2 * np - 2 - st;
+            const int k = solve_plane(phase, side, h, np, st);
             const double *M = (fwd ? X : Gm) + (long)k * m * m + (long)r0 * m;
             double *dst = mat + (long)buf * rw * m;
             for (int q = tid; q < nr * m; q += kPlaneThreads) cp_async8(dst + q, M + q);
             if (fwd) {
                 for (int q = tid; q < m; q += kPlaneThreads) cp_async4(spi + buf * m + q, pi + (long)k * m + q);
-                if (k > 0) {
+                if (phase == 0 && st > 0) {
                     double *sd = stc + (long)buf * G.PN * lowc;
-                    const double *src = Acs + (long)k * G.PN * G.nq * bd * bd;
+                    const double *src = Acs + (long)k * G.PN * G.nq * bd * bd + (long)cb * bd * bd;
                     for (int q = tid; q < G.PN * lowc; q += kPlaneThreads) {
                         const int u = q / lowc, r = q - u * lowc;
                         cp_async8(sd + q, src + (long)u * G.nq * bd * bd + r);
@@ -318,28 +362,33 @@ __global__ void __launch_bounds__(kPlaneThreads) plane_solve_kernel(PlaneGeom G,
     issue(1, 1);
     pdl_prologue();
     for (int st = 0; st < nsteps; ++st) {
-        const int buf = st & 1;
+        const int buf = st & 1, k = solve_plane(phase, side, h, np, st);
         cp_async_wait<1>();
         __syncthreads();
         const double *Mrows = stage ? mat + (long)buf * rw * m : nullptr;
-        if (st < np) {  // ---- forward: y_k = X_k Pi_k (v_k - L_k y_{k-1}) ----
-            const int k = st;
-            const double *yprev = ybuf + ((k + 1) & 1) * m;
-            const int Jbase = k * G.PN;
+        const int Jbase = k * G.PN;
+        double *ynew = ybuf + buf * m;
+        const double *yprev = ybuf + (buf ^ 1) * m;
+        if (fwd) {  // ---- y_k = X_k Pi_k (v_k - couplings) ----
             const double *sl = stc + (long)buf * G.PN * lowc;
             for (int j = tid; j < m; j += kPlaneThreads) {
                 const int uj = j / bd, l = j - uj * bd;
                 double v = vc[(long)(Jbase + uj) * bd + l];
-                if (k > 0)
+                if (phase == 0 && st > 0) {  // the plane before, from the previous step
                     for (int b = 0; b < NI; ++b) {
                         const int tn = plane_nbr(G, uj, b);
                         if (tn < 0) continue;
                         for (int c = 0; c < bd; ++c) {
                             const double a = stage ? sl[(long)uj * lowc + (b * bd + l) * bd + c]
-                                                   : st_val(Acs, G, Jbase + uj, b, l, c);
+                                                   : st_val(Acs, G, Jbase + uj, b + cb, l, c);
                             v = fma(-a, yprev[tn * bd + c], v);
                         }
                     }
+                } else if (phase == 1) {  // both neighbour planes' y, from the sweeps' output
+                    if (h > 0) v = sub_coupling(v, G, Acs, Jbase + uj, uj, l, 0, wc + (long)(h - 1) * G.PN * bd, 1);
+                    if (h + 1 < np)
+                        v = sub_coupling(v, G, Acs, Jbase + uj, uj, l, 2 * NI, wc + (long)(h + 1) * G.PN * bd, 1);
+                }
                 t[j] = v;
             }
             __syncthreads();
@@ -347,7 +396,6 @@ __global__ void __launch_bounds__(kPlaneThreads) plane_solve_kernel(PlaneGeom G,
             for (int j = tid; j < m; j += kPlaneThreads) tp[j] = t[pk[j]];
             __syncthreads();
             const double *Xk = X + (long)k * m * m;
-            double *ynew = ybuf + (k & 1) * m;
             for (int i = r0 + warp; i < r1; i += kPlaneThreads / 32) {
                 const double *xr = stage ? Mrows + (long)(i - r0) * m : Xk + (long)i * m;
                 double s = 0.0;
@@ -357,24 +405,22 @@ __global__ void __launch_bounds__(kPlaneThreads) plane_solve_kernel(PlaneGeom G,
                     for (int r = 0; r < nct; ++r) cluster.map_shared_rank(ynew, r)[i] = s;
                     const long q = (long)(Jbase + i / bd) * bd + i % bd;
                     wc[q] = s;
-                    if (wc32 && k == np - 1) wc32[q] = (float)s;
+                    if (wc32 && phase == 1) wc32[q] = (float)s;
                 }
             }
-        } else {  // ---- backward: w_k = y_k - G_k w_{k+1} ----
-            const int k = 2 * np - 2 - st;
-            const double *wnext = ybuf + ((k + 1) & 1) * m;
-            double *wnew = ybuf + (k & 1) * m;
+        } else {  // ---- w_k = y_k - G_k w_q ----
+            const int kq = side == 0 ? k + 1 : k - 1;
             const double *Gk = Gm + (long)k * m * m;
-            const int Jbase = k * G.PN;
+            const double *wq = st > 0 ? yprev : wc + (long)kq * G.PN * bd;  // w_h from the middle launch
             for (int i = r0 + warp; i < r1; i += kPlaneThreads / 32) {
                 const double *gr = stage ? Mrows + (long)(i - r0) * m : Gk + (long)i * m;
                 double s = 0.0;
-                for (int j = lane; j < m; j += 32) s = fma(gr[j], wnext[j], s);
+                for (int j = lane; j < m; j += 32) s = fma(gr[j], wq[j], s);
                 s = warp_sum(s);
                 if (lane == 0) {
                     const long q = (long)(Jbase + i / bd) * bd + i % bd;
                     const double w = wc[q] - s;
-                    for (int r = 0; r < nct; ++r) cluster.map_shared_rank(wnew, r)[i] = w;
+                    for (int r = 0; r < nct; ++r) cluster.map_shared_rank(ynew, r)[i] = w;
                     wc[q] = w;
                     if (wc32) wc32[q] = (float)w;
                 }
@@ -394,62 +440,71 @@ __global__ void __launch_bounds__(kPlaneThreads) plane_solve_kernel(PlaneGeom G,
 // plane_solve_kernel applied to identity columns, independent across CTAs.
 constexpr int kInvCols = 4;
 
-__global__ void __launch_bounds__(kPlaneThreads) plane_inverse_kernel(PlaneGeom G, const double *__restrict__ Acs,
+// W_k = X_k Pi_k (e_k - C_{k,pa} W_pa - C_{k,pb} W_pb) for the CTA's columns
+// (planes pa / pb with stencil bases ba / bb; -1: none)
+__device__ __forceinline__ void inv_fwd_plane(const PlaneGeom &G, const double *__restrict__ Acs,
+                                              const double *__restrict__ X, const int *__restrict__ pi, double *Wc,
+                                              double *t, double *tp, int c0, int k, int pa, int ba, int pb, int bb) {
+    const int m = G.m, bd = G.bd, tid = threadIdx.x, Jbase = k * G.PN;
+    for (int idx = tid; idx < m * kInvCols; idx += kPlaneThreads) {
+        const int j = idx / kInvCols, q = idx - j * kInvCols;
+        const int uj = j / bd, l = j - uj * bd;
+        double v = (c0 + q == k * m + j) ? 1.0 : 0.0;
+        if (pa >= 0) v = sub_coupling(v, G, Acs, Jbase + uj, uj, l, ba, Wc + (long)pa * m * kInvCols + q, kInvCols);
+        if (pb >= 0) v = sub_coupling(v, G, Acs, Jbase + uj, uj, l, bb, Wc + (long)pb * m * kInvCols + q, kInvCols);
+        t[idx] = v;
+    }
+    __syncthreads();
+    const int *pk = pi + (long)k * m;
+    for (int idx = tid; idx < m * kInvCols; idx += kPlaneThreads) {
+        const int j = idx / kInvCols, q = idx - j * kInvCols;
+        tp[idx] = t[pk[j] * kInvCols + q];
+    }
+    __syncthreads();
+    const double *Xk = X + (long)k * m * m;
+    for (int idx = tid; idx < m * kInvCols; idx += kPlaneThreads) {
+        const int i = idx / kInvCols, q = idx - i * kInvCols;
+        const double *xr = Xk + (long)i * m;
+        double s = 0.0;
+        for (int j = 0; j < m; ++j) s = fma(__ldg(xr + j), tp[j * kInvCols + q], s);
+        Wc[((long)k * m + i) * kInvCols + q] = s;
+    }
+    __syncthreads();
+}
+
+// W_k -= G_k W_kq for the CTA's columns
+__device__ __forceinline__ void inv_back_plane(const PlaneGeom &G, const double *__restrict__ Gm, double *Wc, int k,
+                                               int kq) {
+    const int m = G.m, tid = threadIdx.x;
+    const double *Gk = Gm + (long)k * m * m;
+    for (int idx = tid; idx < m * kInvCols; idx += kPlaneThreads) {
+        const int i = idx / kInvCols, q = idx - i * kInvCols;
+        const double *gr = Gk + (long)i * m;
+        double s = 0.0;
+        for (int j = 0; j < m; ++j) s = fma(__ldg(gr + j), Wc[((long)kq * m + j) * kInvCols + q], s);
+        Wc[((long)k * m + i) * kInvCols + q] -= s;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kPlaneThreads) plane_inverse_kernel(PlaneGeom G, int h,
+                                                                      const double *__restrict__ Acs,
                                                                       const double *__restrict__ X,
                                                                       const double *__restrict__ Gm,
                                                                       const int *__restrict__ pi,
                                                                       double *__restrict__ Ainv) {
-    const int m = G.m, bd = G.bd, NI = G.NI, nC = G.np * m;
+    const int m = G.m, NI = G.NI, np = G.np, nC = np * m;
     const int c0 = blockIdx.x * kInvCols, ncols = min(kInvCols, nC - c0);
     const int tid = threadIdx.x;
     extern __shared__ double sm[];
     double *Wc = sm;                           // the columns being built, [nC][kInvCols]
     double *t = Wc + (long)nC * kInvCols;      // [m][kInvCols]
     double *tp = t + (long)m * kInvCols;       // [m][kInvCols]
-    for (int k = 0; k < G.np; ++k) {
-        const int Jbase = k * G.PN;
-        for (int idx = tid; idx < m * kInvCols; idx += kPlaneThreads) {
-            const int j = idx / kInvCols, q = idx - j * kInvCols;
-            const int uj = j / bd, l = j - uj * bd;
-            double v = (c0 + q == k * m + j) ? 1.0 : 0.0;
-            if (k > 0)
-                for (int b = 0; b < NI; ++b) {
-                    const int tn = plane_nbr(G, uj, b);
-                    if (tn < 0) continue;
-                    for (int c = 0; c < bd; ++c)
-                        v = fma(-st_val(Acs, G, Jbase + uj, b, l, c),
-                                Wc[((long)(k - 1) * m + tn * bd + c) * kInvCols + q], v);
-                }
-            t[idx] = v;
-        }
-        __syncthreads();
-        const int *pk = pi + (long)k * m;
-        for (int idx = tid; idx < m * kInvCols; idx += kPlaneThreads) {
-            const int j = idx / kInvCols, q = idx - j * kInvCols;
-            tp[idx] = t[pk[j] * kInvCols + q];
-        }
-        __syncthreads();
-        const double *Xk = X + (long)k * m * m;
-        for (int idx = tid; idx < m * kInvCols; idx += kPlaneThreads) {
-            const int i = idx / kInvCols, q = idx - i * kInvCols;
-            const double *xr = Xk + (long)i * m;
-            double s = 0.0;
-            for (int j = 0; j < m; ++j) s = fma(__ldg(xr + j), tp[j * kInvCols + q], s);
-            Wc[((long)k * m + i) * kInvCols + q] = s;
-        }
-        __syncthreads();
-    }
-    for (int k = G.np - 2; k >= 0; --k) {
-        const double *Gk = Gm + (long)k * m * m;
-        for (int idx = tid; idx < m * kInvCols; idx += kPlaneThreads) {
-            const int i = idx / kInvCols, q = idx - i * kInvCols;
-            const double *gr = Gk + (long)i * m;
-            double s = 0.0;
-            for (int j = 0; j < m; ++j) s = fma(__ldg(gr + j), Wc[((long)(k + 1) * m + j) * kInvCols + q], s);
-            Wc[((long)k * m + i) * kInvCols + q] -= s;
-        }
-        __syncthreads();
-    }
+    for (int k = 0; k < h; ++k) inv_fwd_plane(G, Acs, X, pi, Wc, t, tp, c0, k, k - 1, 0, -1, 0);
+    for (int k = np - 1; k > h; --k) inv_fwd_plane(G, Acs, X, pi, Wc, t, tp, c0, k, k + 1 < np ? k + 1 : -1, 2 * NI, -1, 0);
+    inv_fwd_plane(G, Acs, X, pi, Wc, t, tp, c0, h, h - 1, 0, h + 1 < np ? h + 1 : -1, 2 * NI);
+    for (int k = h - 1; k >= 0; --k) inv_back_plane(G, Gm, Wc, k, k + 1);
+    for (int k = h + 1; k < np; ++k) inv_back_plane(G, Gm, Wc, k, k - 1);
     for (int idx = tid; idx < nC * ncols; idx += kPlaneThreads) {
         const int row = idx / ncols, q = idx - row * ncols;
         Ainv[(long)row * nC + c0 + q] = Wc[(long)row * kInvCols + q];
@@ -566,21 +621,33 @@ msrsb_status plane_factor(int dim, const int nb[3], int bd, const double *Acs, C
         }
     }
     const long mm = (long)G.m * G.m;
+    const int h = G.np / 2;  // side 0: planes 0 .. h-1, side 1: np-1 .. h+1 (never longer than side 0)
+    cp->h = h;
     MSRSB_TRY(dalloc(&cp->X, (size_t)G.np * mm, s));
-    MSRSB_TRY(dalloc(&cp->G, (size_t)(G.np > 1 ? G.np - 1 : 1) * mm, s));
+    MSRSB_TRY(dalloc(&cp->G, (size_t)G.np * mm, s));
     MSRSB_TRY(dalloc(&cp->pi, (size_t)G.np * G.m, s));
     int *status = nullptr;
     MSRSB_TRY(dalloc(&status, 1, s));
     MSRSB_CUDA(cudaMemsetAsync(status, 0, sizeof(int), s));
-    cudaLaunchAttribute attr[2];
-    cudaLaunchConfig_t cfg = cluster_cfg(attr, nct, factor_smem(G.m, nct), s, false);
-    count_launch();
-    MSRSB_CUDA(cudaLaunchKernelEx(&cfg, plane_factor_kernel, G, Acs, cp->X, cp->G, cp->pi, status));
-    int h = 0;
-    MSRSB_CUDA(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    const size_t sf = factor_smem(G.m, nct);
+    if (h > 0) {  // the two sides, one cluster each, concurrently
+        cudaLaunchAttribute attr[2];
+        cudaLaunchConfig_t cfg = cluster_cfg(attr, nct, sf, s, false);
+        cfg.gridDim = dim3((G.np - 1 - h > 0 ? 2 : 1) * nct);
+        count_launch();
+        MSRSB_CUDA(cudaLaunchKernelEx(&cfg, plane_factor_kernel, G, h, 0, Acs, cp->X, cp->G, cp->pi, status));
+    }
+    {  // the middle plane
+        cudaLaunchAttribute attr[2];
+        cudaLaunchConfig_t cfg = cluster_cfg(attr, nct, sf, s, false);
+        count_launch();
+        MSRSB_CUDA(cudaLaunchKernelEx(&cfg, plane_factor_kernel, G, h, 1, Acs, cp->X, cp->G, cp->pi, status));
+    }
+    int bad = 0;
+    MSRSB_CUDA(cudaMemcpyAsync(&bad, status, sizeof(int), cudaMemcpyDeviceToHost, s));
     MSRSB_CUDA(cudaStreamSynchronize(s));
     dfree(status, s);
-    if (h) return fail(MSRSB_EBREAKDOWN, "coarse operator is singular (zero pivot at coarse row %d)", h - 1);
+    if (bad) return fail(MSRSB_EBREAKDOWN, "coarse operator is singular (zero pivot at coarse row %d)", bad - 1);
     return MSRSB_OK;
 }
 
@@ -588,20 +655,28 @@ msrsb_status plane_solve(int dim, const int nb[3], int bd, const double *Acs, co
                          const double *vc, double *wc, float *wc32, cudaStream_t s) {
     PlaneGeom G;
     plane_geom(dim, nb, bd, &G);
-    const int stage = cp->stage;
+    const int stage = cp->stage, h = cp->h;
     const size_t staged = solve_smem_staged(G, cp->nct);
-    cudaLaunchAttribute attr[2];
-    cudaLaunchConfig_t cfg = cluster_cfg(attr, cp->nct, stage ? staged : solve_smem(G.m), s, true);
-    count_launch();
-    cudaError_t e = cudaLaunchKernelEx(&cfg, plane_solve_kernel, G, Acs, (const double *)cp->X,
-                                       (const double *)cp->G, (const int *)cp->pi, vc, wc, wc32, stage);
-    if (e == cudaErrorNotSupported || e == cudaErrorInvalidValue) {  // programmatic serialisation refused
-        cudaGetLastError();
-        cfg.numAttrs = 1;
-        e = cudaLaunchKernelEx(&cfg, plane_solve_kernel, G, Acs, (const double *)cp->X, (const double *)cp->G,
-                               (const int *)cp->pi, vc, wc, wc32, stage);
-    }
-    MSRSB_CUDA(e);
+    auto launch = [&](int phase, int clusters) -> msrsb_status {
+        cudaLaunchAttribute attr[2];
+        cudaLaunchConfig_t cfg = cluster_cfg(attr, cp->nct, stage ? staged : solve_smem(G.m), s, true);
+        cfg.gridDim = dim3(clusters * cp->nct);
+        count_launch();
+        cudaError_t e = cudaLaunchKernelEx(&cfg, plane_solve_kernel, G, h, phase, Acs, (const double *)cp->X,
+                                           (const double *)cp->G, (const int *)cp->pi, vc, wc, wc32, stage);
+        if (e == cudaErrorNotSupported || e == cudaErrorInvalidValue) {  // programmatic serialisation refused
+            cudaGetLastError();
+            cfg.numAttrs = 1;
+            e = cudaLaunchKernelEx(&cfg, plane_solve_kernel, G, h, phase, Acs, (const double *)cp->X,
+                                   (const double *)cp->G, (const int *)cp->pi, vc, wc, wc32, stage);
+        }
+        MSRSB_CUDA(e);
+        return MSRSB_OK;
+    };
+    const int sides = G.np - 1 - h > 0 ? 2 : 1;
+    if (h > 0) MSRSB_TRY(launch(0, sides));
+    MSRSB_TRY(launch(1, 1));
+    if (h > 0) MSRSB_TRY(launch(2, sides));
     return MSRSB_OK;
 }
 
@@ -618,7 +693,8 @@ msrsb_status plane_inverse(int dim, const int nb[3], int bd, const double *Acs, 
         cudaFuncSetAttribute(plane_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPlaneSmemMax);
         cudaGetLastError();
     });
-    plane_inverse_kernel<<<ceil_div(nC, kInvCols), kPlaneThreads, smem, s>>>(G, Acs, cp->X, cp->G, cp->pi, Ainv);
+    plane_inverse_kernel<<<ceil_div(nC, kInvCols), kPlaneThreads, smem, s>>>(G, cp->h, Acs, cp->X, cp->G, cp->pi,
+                                                                             Ainv);
     MSRSB_LAUNCHED("plane_inverse_kernel");
     return MSRSB_OK;
 }

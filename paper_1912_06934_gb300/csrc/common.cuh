@@ -166,6 +166,7 @@ struct CoarseInverseWork {
 // the gather pi_k, and G_k = S_k^-1 U_k.
 struct CoarsePlanes {
     int m = 0, np = 0, nct = 0;
+    int h = 0;      // the middle plane: planes below it are eliminated upwards, those above downwards
     int stage = 0;  // the application stages its operands in shared memory
     double *X = nullptr, *G = nullptr;
     int *pi = nullptr;
