@@ -263,6 +263,22 @@ msrsb_status msrsb_apply(msrsb_handle *h, const double *v, double *z, cudaStream
 msrsb_status msrsb_solve(msrsb_handle *h, const double *b, double *x, double rtol, int32_t maxit,
                          int32_t *iters_h, double *relres_h, double *hist_h, cudaStream_t stream);
 
+/* msrsb_solve for nrhs right-hand sides of the handle's operator: B, X
+ * FP64 [nrhs][n*bdim] (right-hand side r at B + r*n*bdim; X: in initial
+ * guesses, out solutions); iters_h, relres_h host [nrhs]. In the
+ * configuration of the flow cases (scalar operator, GMRES, coarse stage, one
+ * ILU(0) post-sweep in the line-block order on grids of nx <= 128, no
+ * pre-smoother) up to 8 right-hand sides run in lockstep: every step applies
+ * the preconditioner and A to all of them with kernels that read A, P, the
+ * coarse inverse and the ILU(0) factors once for all; each right-hand side
+ * performs exactly the operations of its own msrsb_solve, so its iterations
+ * and solution are the same. Otherwise the right-hand sides are solved one
+ * after another. Synchronises `stream`. Returns the first failure
+ * (MSRSB_ENOCONV and others as msrsb_solve); the right-hand sides before it
+ * are solved. */
+msrsb_status msrsb_solve_multi(msrsb_handle *h, int32_t nrhs, const double *B, double *X, double rtol, int32_t maxit,
+                               int32_t *iters_h, double *relres_h, cudaStream_t stream);
+
 /* y = A x for a fine operator (FP64 CSR or 3x3 block CSR, device arrays;
  * x, y FP64 [nrows * bdim], not aliased). Stream-ordered. */
 msrsb_status msrsb_spmv(const msrsb_mat *A, const double *x, double *y, cudaStream_t stream);

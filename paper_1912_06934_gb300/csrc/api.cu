@@ -9,6 +9,8 @@
 #include <string>
 #include <thread>
 #include <future>
+#include <type_traits>
+#include <vector>
 
 namespace msrsb {
 
@@ -173,6 +175,23 @@ msrsb_status arnoldi_update_df(long N, int nv, int m, const float *Vh, const flo
 msrsb_status arnoldi_update(long N, int nv, int m, const double *V, double *P, const double *Wv, double *O,
                             const double *kh, cudaStream_t s);
 msrsb_status sell_spmv_df(const Sell &S, const double *val, const double *x, float *yh, float *yl, cudaStream_t s);
+template <typename TP, typename TV>
+msrsb_status restrict_multi(const msrsb_handle *h, int k, const TP *PT, Cols<const TV> v, Cols<double> vc,
+                            cudaStream_t s);
+msrsb_status gemm_multi(int n, int k, const double *M, Cols<const double> x, Cols<double> y, Cols<float> y32,
+                        cudaStream_t s);
+template <typename TP, typename TZ>
+msrsb_status prolong_multi(const msrsb_handle *h, int k, const TP *P, Cols<const double> wc, Cols<const float> wc32,
+                           Cols<TZ> z, Cols<float> z32, cudaStream_t s);
+template <typename TA, typename TX, typename TV, typename TY, typename TACC>
+msrsb_status resid_multi(const msrsb_handle *h, int k, const TA *sval, Cols<const TX> x, Cols<const TV> v, Cols<TY> y,
+                         const int32_t *operm, cudaStream_t s);
+msrsb_status spmv_df_multi(const msrsb_handle *h, int k, Cols<const double> x, Cols<float> yh, Cols<float> yl,
+                           cudaStream_t s);
+msrsb_status spmv_multi(const msrsb_handle *h, int k, Cols<const double> x, Cols<double> y, cudaStream_t s);
+template <typename T, typename TZ>
+msrsb_status lines_apply_multi(const msrsb_handle *h, int k, Cols<T> ry, Cols<TZ> z, cudaStream_t s);
+bool lines_multi_fit(const msrsb_handle *h);
 msrsb_status df_split(long N, const double *w, float *wh, float *wl, cudaStream_t s);
 template <typename TY>
 msrsb_status scale_by_inv(long N, const double *x, const double *den, TY *y, cudaStream_t s);
@@ -874,6 +893,300 @@ static msrsb_status gmres(msrsb_handle *h, const double *b, double *x, double rt
     return gmres_t<false>(h, b, x, rtol, maxit, iters, relres, hist, s);
 }
 
+// ---- several right-hand sides of one operator in lockstep -------------------------------------
+//
+// GMRES runs for up to kMaxRhs right-hand sides together: every Arnoldi step
+// applies the preconditioner and A to all of them with the multi-vector
+// kernels (A, P, Pt, the coarse inverse and the ILU(0) factors read once per
+// step for all), and the orthogonalisation, Givens rotations and updates per
+// right-hand side with the one-vector kernels. Each right-hand side follows
+// exactly the operations of its own gmres_t solve (a right-hand side that has
+// converged drops out of the later steps), so its iterations and solution are
+// those of msrsb_solve. Served configuration: scalar operator, GMRES, the
+// coarse stage, one ILU(0) post-sweep in the line-block order, no
+// pre-smoother; msrsb_solve_multi solves the right-hand sides one after
+// another otherwise.
+static bool multi_supported(const msrsb_handle *h) {
+    const msrsb_opts &o = h->opts;
+    const bool ilu = o.smoother == MSRSB_SMOOTH_ILU0 || o.smoother == MSRSB_SMOOTH_IC0;
+    return h->bdim == 1 && o.krylov == MSRSB_GMRES && ilu && h->use_lines && lines_multi_fit(h) && !o.pre &&
+           o.post == 1 && !o.no_coarse;
+}
+
+struct MultiScratch {
+    void *rt = nullptr;    // sweep-order residuals [k][N] (T)
+    float *z32 = nullptr;  // FP32 copies of z [k][N] (mixed form)
+    double *vc = nullptr, *wc = nullptr;  // coarse vectors [k][nC]
+    float *wc32 = nullptr;                // [k][nC]
+};
+
+// z_c = M^-1 v_c for c < k (Alg. 4 with Alg. 3, the served configuration)
+template <typename T, typename TVI, typename TZ>
+static msrsb_status apply_multi_t(msrsb_handle *h, int k, const TVI *const *v, TZ *const *z, const MultiScratch &w,
+                                  cudaStream_t s) {
+    const long N = h->n, nC = h->nC;
+    const bool f32 = sizeof(T) == 4;
+    const bool use_z32 = f32 && sizeof(TZ) == 8;
+    Cols<const TVI> vi{};
+    Cols<TZ> zo{};
+    Cols<double> vc{}, wc{};
+    Cols<const double> vcr{}, wcr{};
+    Cols<float> wc32{}, z32{};
+    Cols<const float> wc32r{}, z32r{};
+    Cols<T> rt{};
+    for (int c = 0; c < k; ++c) {
+        vi.p[c] = v[c];
+        zo.p[c] = z[c];
+        vc.p[c] = w.vc + c * nC;
+        vcr.p[c] = vc.p[c];
+        wc.p[c] = w.wc + c * nC;
+        wcr.p[c] = wc.p[c];
+        wc32.p[c] = f32 ? w.wc32 + c * nC : nullptr;
+        wc32r.p[c] = wc32.p[c];
+        z32.p[c] = use_z32 ? w.z32 + c * N : nullptr;
+        z32r.p[c] = z32.p[c];
+        rt.p[c] = (T *)w.rt + c * N;
+    }
+    MSRSB_TRY((restrict_multi<T, TVI>(h, k, (const T *)h->pt_val, vi, vc, s)));
+    if (h->Ainv) {
+        MSRSB_TRY(gemm_multi(h->nC, k, h->Ainv, vcr, wc, wc32, s));
+    } else {
+        for (int c = 0; c < k; ++c)
+            MSRSB_TRY(plane_solve(h->grid.dim, h->nb, h->bdim, h->Acs, &h->planes, vc.p[c], wc.p[c], wc32.p[c], s));
+    }
+    MSRSB_TRY((prolong_multi<T, TZ>(h, k, (const T *)h->p_val, wcr, wc32r, zo, z32, s)));
+    if constexpr (sizeof(T) == 4) {
+        if (use_z32)
+            MSRSB_TRY((resid_multi<float, float, TVI, float, float>(h, k, (const float *)h->asell.val[1], z32r, vi, rt,
+                                                                    h->pos_of, s)));
+        else
+            return fail(MSRSB_EINVAL, "multi-vector apply: unsupported precision combination");
+    } else {
+        Cols<const TZ> zr{};
+        for (int c = 0; c < k; ++c) zr.p[c] = z[c];
+        MSRSB_TRY((resid_multi<T, TZ, TVI, T, T>(h, k, (const T *)h->asell.val[0], zr, vi, rt, h->pos_of, s)));
+    }
+    return lines_apply_multi<T, TZ>(h, k, rt, zo, s);
+}
+
+template <bool DFV>
+static msrsb_status gmres_multi_t(msrsb_handle *h, int k, const double *B, double *X, double rtol, int maxit,
+                                  int *iters, double *relres, cudaStream_t s) {
+    using T = typename std::conditional<DFV, float, double>::type;
+    const long N = (long)h->n, nC = h->nC;
+    const int m = h->krylov_m;
+    const KhLayout L(m);
+    // per right-hand side: the Krylov basis (FP64, or double-float planes [Vh | Vl | Wh | Wl]), Zhat, the state block
+    std::vector<void *> owned;
+    struct Free {
+        std::vector<void *> &o;
+        cudaStream_t s;
+        ~Free() {
+            for (void *p : o) dfree(p, s);
+        }
+    } release{owned, s};
+    auto take = [&](auto **p, size_t count) -> msrsb_status {
+        MSRSB_TRY(dalloc(p, count, s));
+        owned.push_back((void *)*p);
+        return MSRSB_OK;
+    };
+    std::vector<double *> V(k), Z(k), KH(k);
+    std::vector<float *> Vh(k), Vl(k), Wh(k), Wl(k);
+    for (int r = 0; r < k; ++r) {
+        if (DFV) {
+            float *v32 = nullptr;
+            MSRSB_TRY(take(&v32, (size_t)2 * (m + 2) * N));
+            Vh[r] = v32;
+            Vl[r] = v32 + (m + 1) * N;
+            Wh[r] = Vl[r] + (m + 1) * N;
+            Wl[r] = Wh[r] + N;
+        } else {
+            MSRSB_TRY(take(&V[r], (size_t)(m + 1) * N));
+        }
+        MSRSB_TRY(take(&Z[r], (size_t)m * N));
+        MSRSB_TRY(take(&KH[r], (size_t)L.total));
+    }
+    MultiScratch w;
+    T *rt = nullptr;
+    MSRSB_TRY(take(&rt, (size_t)k * N));
+    w.rt = rt;
+    MSRSB_TRY(take(&w.vc, (size_t)k * nC));
+    MSRSB_TRY(take(&w.wc, (size_t)k * nC));
+    if (DFV) {
+        MSRSB_TRY(take(&w.z32, (size_t)k * N));
+        MSRSB_TRY(take(&w.wc32, (size_t)k * nC));
+    }
+    std::vector<double> bnorm(k, 0.0), stop(k, 0.0);
+    std::vector<int> its(k, 0), done(k, 0), mm(k, 0), conv(k, -1), launched(k, 0);
+    for (int r = 0; r < k; ++r) {
+        iters[r] = 0;
+        relres[r] = 0.0;
+        MSRSB_TRY(norm2(N, B + r * N, h->partial, KH[r] + L.beta, s));
+        MSRSB_TRY(read_scalar(KH[r] + L.beta, &bnorm[r], s));
+        if (bnorm[r] == 0.0) {
+            MSRSB_CUDA(cudaMemsetAsync(X + r * N, 0, N * sizeof(double), s));
+            done[r] = 1;
+        }
+    }
+    double *pin = pinned_scratch();
+    double *pin_est = pin ? pin + 16 : nullptr;
+    for (;;) {
+        std::vector<int> act;
+        for (int r = 0; r < k; ++r) {
+            if (done[r]) continue;
+            double *beta = KH[r] + L.beta;
+            MSRSB_TRY(fine_spmv(h, X + r * N, B + r * N, h->tmp_d, true, s));
+            MSRSB_TRY(norm2(N, h->tmp_d, h->partial, beta, s));
+            double bt = 0.0;
+            MSRSB_TRY(read_scalar(beta, &bt, s));
+            if (!std::isfinite(bt)) return fail(MSRSB_ENAN, "non-finite residual in GMRES (right-hand side %d)", r);
+            relres[r] = bt / bnorm[r];
+            if (bt <= rtol * bnorm[r]) {
+                done[r] = 1;
+                continue;
+            }
+            if (its[r] >= maxit)
+                return fail(MSRSB_ENOCONV, "GMRES reached %d iterations (right-hand side %d, relres %.3e)", its[r], r,
+                            bt / bnorm[r]);
+            if (DFV)
+                MSRSB_TRY(df_scale(N, h->tmp_d, beta, Vh[r], Vl[r], s));
+            else
+                MSRSB_TRY(scale_by_inv<double>(N, h->tmp_d, beta, V[r], s));
+            MSRSB_PDL((gmres_init_kernel), 1, 1, 0, s, m, KH[r], beta);
+            mm[r] = m < maxit - its[r] ? m : maxit - its[r];
+            stop[r] = rtol * bnorm[r];
+            conv[r] = -1;
+            launched[r] = 0;
+            act.push_back(r);
+        }
+        if (act.empty()) break;
+        int mmax = 0;
+        for (int r : act) mmax = mm[r] > mmax ? mm[r] : mmax;
+        cudaEvent_t *evs = event_pool(mmax + 2);
+        const bool lagged = pin_est && evs && (long)k * mmax <= kPinnedDoubles - 16;
+        cudaStream_t gv = lagged && h->side ? h->side : s;
+        cudaEvent_t fork_ev = evs ? evs[mmax] : nullptr, join_ev = evs ? evs[mmax + 1] : nullptr;
+        int checked = 0, steps = 0;  // columns finished by every step so far
+        auto live = [&](int r, int j) { return conv[r] < 0 && j <= mm[r]; };
+        for (int j = 0; j <= mmax; ++j) {
+            if (lagged) {  // residual estimates of finished columns, at most two steps late
+                while (checked < steps) {
+                    if (cudaEventQuery(evs[checked]) != cudaSuccess) {
+                        cudaGetLastError();
+                        if (steps - checked <= 2) break;
+                        MSRSB_CUDA(cudaEventSynchronize(evs[checked]));
+                    }
+                    for (int r : act) {
+                        if (conv[r] >= 0 || checked >= launched[r]) continue;
+                        const double e = ((volatile double *)pin_est)[(long)r * mmax + checked];
+                        if (!std::isfinite(e)) return fail(MSRSB_ENAN, "non-finite residual estimate in GMRES");
+                        if (e <= stop[r]) conv[r] = checked;
+                    }
+                    ++checked;
+                }
+            }
+            std::vector<int> cols, full;
+            for (int r : act)
+                if (live(r, j)) {
+                    cols.push_back(r);
+                    if (j < mm[r]) full.push_back(r);
+                }
+            if (cols.empty()) break;
+            const int kf = (int)full.size();
+            if (kf > 0) {
+                std::vector<const T *> vin(kf);
+                std::vector<double *> zo(kf);
+                for (int c = 0; c < kf; ++c) {
+                    const int r = full[c];
+                    vin[c] = DFV ? (const T *)(Vh[r] + (long)j * N) : (const T *)(V[r] + (long)j * N);
+                    zo[c] = Z[r] + (long)j * N;
+                }
+                MSRSB_TRY((apply_multi_t<T, T, double>(h, kf, vin.data(), zo.data(), w, s)));
+                Cols<const double> zc{};
+                for (int c = 0; c < kf; ++c) zc.p[c] = zo[c];
+                if (DFV) {
+                    Cols<float> yh{}, yl{};
+                    for (int c = 0; c < kf; ++c) {
+                        yh.p[c] = Wh[full[c]];
+                        yl.p[c] = Wl[full[c]];
+                    }
+                    MSRSB_TRY(spmv_df_multi(h, kf, zc, yh, yl, s));
+                } else {
+                    Cols<double> y{};
+                    for (int c = 0; c < kf; ++c) y.p[c] = V[full[c]] + (long)(j + 1) * N;
+                    MSRSB_TRY(spmv_multi(h, kf, zc, y, s));
+                }
+            }
+            for (int r : cols) {
+                const bool f = j < mm[r];
+                double *kh = KH[r];
+                if (DFV) {
+                    float *ph = Vh[r] + (long)j * N, *pl = Vl[r] + (long)j * N;
+                    MSRSB_TRY(arnoldi_dots_df(N, j, Vh[r], Vl[r], ph, pl, f ? Wh[r] : nullptr, f ? Wl[r] : nullptr,
+                                              h->partial, s));
+                    MSRSB_TRY(arnoldi_scalar(m, j, f, h->partial, kh, s));
+                    if (f)
+                        MSRSB_TRY(arnoldi_update_df(N, j, m, Vh[r], Vl[r], ph, pl, Wh[r], Wl[r],
+                                                    Vh[r] + (long)(j + 1) * N, Vl[r] + (long)(j + 1) * N, kh, s));
+                } else {
+                    double *P = V[r] + (long)j * N, *Wn = V[r] + (long)(j + 1) * N;
+                    MSRSB_TRY(arnoldi_dots(N, j, V[r], P, f ? Wn : nullptr, h->partial, s));
+                    MSRSB_TRY(arnoldi_scalar(m, j, f, h->partial, kh, s));
+                    if (f) MSRSB_TRY(arnoldi_update(N, j, m, V[r], P, Wn, Wn, kh, s));
+                }
+            }
+            if (j == 0) continue;
+            const int c = j - 1;  // the column this step finished
+            if (gv != s) {
+                MSRSB_CUDA(cudaEventRecord(fork_ev, s));
+                MSRSB_CUDA(cudaStreamWaitEvent(gv, fork_ev, 0));
+            }
+            for (int r : cols) {
+                givens_kernel<<<1, 32, 0, gv>>>(m, c, KH[r]);
+                MSRSB_LAUNCHED("givens_kernel");
+                launched[r] = c + 1;
+                if (lagged)
+                    MSRSB_CUDA(cudaMemcpyAsync(pin_est + (long)r * mmax + c, KH[r] + L.hist + c, sizeof(double),
+                                               cudaMemcpyDeviceToHost, gv));
+            }
+            steps = c + 1;
+            if (lagged) {
+                MSRSB_CUDA(cudaEventRecord(evs[c], gv));
+            } else {
+                for (int r : cols) {
+                    double e = 0.0;
+                    MSRSB_TRY(read_scalar(KH[r] + L.est, &e, s));
+                    if (!std::isfinite(e)) return fail(MSRSB_ENAN, "non-finite residual estimate in GMRES");
+                    if (e <= stop[r]) conv[r] = c;
+                }
+            }
+        }
+        if (gv != s) {
+            MSRSB_CUDA(cudaEventRecord(join_ev, gv));
+            MSRSB_CUDA(cudaStreamWaitEvent(s, join_ev, 0));
+        }
+        if (lagged) {
+            MSRSB_CUDA(cudaStreamSynchronize(s));
+            for (int r : act)
+                for (int q = 0; q < launched[r] && conv[r] < 0; ++q) {
+                    const double e = ((volatile double *)pin_est)[(long)r * mmax + q];
+                    if (q < checked) continue;
+                    if (!std::isfinite(e)) return fail(MSRSB_ENAN, "non-finite residual estimate in GMRES");
+                    if (e <= stop[r]) conv[r] = q;
+                }
+        }
+        for (int r : act) {
+            const int kk = conv[r] >= 0 ? conv[r] + 1 : launched[r];
+            its[r] += kk;
+            hess_solve_kernel<<<1, 256, 0, s>>>(m, kk, KH[r]);
+            MSRSB_LAUNCHED("hess_solve_kernel");
+            MSRSB_TRY(mvadd<double>(N, kk, Z[r], N, KH[r] + L.g, X + r * N, s));
+        }
+    }
+    for (int r = 0; r < k; ++r) iters[r] = its[r];
+    return MSRSB_OK;
+}
+
 // ---- PCG ------------------------------------------------------------------------
 
 static msrsb_status pcg(msrsb_handle *h, const double *b, double *x, double rtol, int maxit, int *iters,
@@ -1129,6 +1442,30 @@ extern "C" msrsb_status msrsb_solve(msrsb_handle *h, const double *b, double *x,
     if (relres_h) *relres_h = rr;
     if (st == MSRSB_OK) MSRSB_CUDA(cudaStreamSynchronize(stream));
     return st;
+}
+
+extern "C" msrsb_status msrsb_solve_multi(msrsb_handle *h, int32_t nrhs, const double *B, double *X, double rtol,
+                                          int32_t maxit, int32_t *iters_h, double *relres_h, cudaStream_t stream) {
+    if (!h || nrhs < 0 || (nrhs > 0 && (!B || !X || !iters_h || !relres_h))) return fail(MSRSB_EINVAL, "NULL argument");
+    if (!(rtol >= 0.0) || maxit < 0) return fail(MSRSB_EINVAL, "bad rtol or maxit");
+    const long N = (long)h->n * h->bdim;
+    if (!multi_supported(h)) {  // one right-hand side after another
+        for (int r = 0; r < nrhs; ++r)
+            MSRSB_TRY(msrsb_solve(h, B + r * N, X + r * N, rtol, maxit, iters_h + r, relres_h + r, nullptr, stream));
+        return MSRSB_OK;
+    }
+    for (int r0 = 0; r0 < nrhs; r0 += kMaxRhs) {
+        const int k = nrhs - r0 < kMaxRhs ? nrhs - r0 : kMaxRhs;
+        int its[kMaxRhs];
+        const msrsb_status st =
+            h->opts.prec == MSRSB_F32
+                ? gmres_multi_t<true>(h, k, B + r0 * N, X + r0 * N, rtol, maxit, its, relres_h + r0, stream)
+                : gmres_multi_t<false>(h, k, B + r0 * N, X + r0 * N, rtol, maxit, its, relres_h + r0, stream);
+        for (int c = 0; c < k; ++c) iters_h[r0 + c] = its[c];
+        if (st != MSRSB_OK) return st;
+    }
+    MSRSB_CUDA(cudaStreamSynchronize(stream));
+    return MSRSB_OK;
 }
 
 extern "C" msrsb_status msrsb_get_setup(msrsb_handle *h, int32_t *p_ids, void *p_val, double *Ac_dense,

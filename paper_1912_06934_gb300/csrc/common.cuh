@@ -228,6 +228,14 @@ __device__ __forceinline__ double warp_max(double v) {
     return v;
 }
 
+// Right-hand sides handled together by the multi-vector kernels, and the
+// vectors of one such launch: column c at p[c] (c < k), passed by value.
+constexpr int kMaxRhs = 8;
+template <typename T>
+struct Cols {
+    T *p[kMaxRhs];
+};
+
 // Krylov state on the device, m = restart length:
 // H[(m+1) x m] column-major (Givens-rotated in place) | cs[m] | sn[m] | g[m+1] |
 // est | beta | h2[m+2] | est_hist[m+1] | flag[8] | Hu[(m+1) x m] (the

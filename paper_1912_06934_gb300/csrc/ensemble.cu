@@ -1,7 +1,8 @@
 // Ensembles of independent problems (set-up of Alg. 2 and solves with
 // Alg. 4, per problem): a pool of host threads, each with a stream of its
 // own, takes problems in order from a shared counter, so the latency-bound
-// set-ups and solves of several problems overlap on the GPU.
+// set-ups and solves of several problems overlap on the GPU; a problem's
+// right-hand sides are solved together by msrsb_solve_multi.
 #include "common.cuh"
 #include <atomic>
 #include <string>
@@ -40,9 +41,8 @@ extern "C" msrsb_status msrsb_solve_ensemble(int32_t nprob, msrsb_problem *probs
             }
             msrsb_handle *h = nullptr;
             msrsb_status s = msrsb_setup(p.A, p.g, opts, nullptr, &h, st);
-            const long N = (long)p.A->nrows * p.A->bdim;
-            for (int r = 0; s == MSRSB_OK && r < p.nrhs; ++r)
-                s = msrsb_solve(h, p.b + r * N, p.x + r * N, rtol, maxit, p.iters_h + r, p.relres_h + r, nullptr, st);
+            if (s == MSRSB_OK && p.nrhs > 0)  // the right-hand sides together (msrsb_solve_multi)
+                s = msrsb_solve_multi(h, p.nrhs, p.b, p.x, rtol, maxit, p.iters_h, p.relres_h, st);
             if (s != MSRSB_OK) errs[i] = msrsb_last_error();
             if (h) {
                 const msrsb_status sd = msrsb_destroy(h);

@@ -575,6 +575,116 @@ __global__ void __launch_bounds__(1024) lines_sweep_kernel(
     }
 }
 
+// The same sweep for k right-hand sides (k <= kMaxRhs): each loaded factor
+// entry serves every vector; per vector the arithmetic and its order are
+// those of lines_sweep_kernel. Shared memory: per vector its block values
+// (4 nx) and the warp maps of its scans (64). At most 512 threads a CTA.
+constexpr int kLinesMultiThreads = 512;
+
+template <typename T, typename TZ>
+__global__ void __launch_bounds__(kLinesMultiThreads) lines_sweep_multi_kernel(
+    int mode, int k, int b0, const int32_t *__restrict__ blk_start, const int32_t *__restrict__ blk_nsub, int nx,
+    int nxp, int c0, int m, int wl, const int32_t *__restrict__ lcol, const T *__restrict__ lval, int wli,
+    const int16_t *__restrict__ lidx, const T *__restrict__ lvin, const T *__restrict__ lrec, int wu,
+    const int32_t *__restrict__ ucol, const T *__restrict__ uval, int wui, const int16_t *__restrict__ uidx,
+    const T *__restrict__ uvin, const T *__restrict__ urec, const T *__restrict__ udinv,
+    const int32_t *__restrict__ rows, Cols<T> y, Cols<TZ> z) {
+    extern __shared__ unsigned char s_raw[];
+    T *smb = reinterpret_cast<T *>(s_raw);  // [k][4 nx] block values, then [k][64] warp maps
+    T *wmb = smb + (long)k * 4 * nx;
+    const int b = b0 + blockIdx.x;
+    const int st = blk_start[b], nsub = blk_nsub[b];
+    const int q = threadIdx.x / nxp, xx = threadIdx.x - q * nxp, lane = threadIdx.x & 31;
+    const int wline = xx >> 5;
+    const bool on = q < nsub && xx < nx;
+    const int lf = q * nx + xx;
+    const int lb = q * nx + (nx - 1 - xx);
+    LineCoef<T> cf;
+    if (mode != 1)
+        line_coef_load(cf, on, lf, st, c0, m, wli, lidx, lvin, lrec, (const T *)nullptr);
+    else
+        line_coef_load(cf, on, lb, st, c0, m, wui, uidx, uvin, urec, udinv);
+    pdl_prologue();
+    T acc[kMaxRhs];
+    if (mode != 1) {
+        if (on) {  // s = r - sum_off L y
+            const int r = st + lf - c0;
+#pragma unroll
+            for (int c = 0; c < kMaxRhs; ++c) acc[c] = T(0);
+            for (int j = 0; j < wl; ++j) {
+                const T lv = lval[(long)j * m + r];
+                const int col = lcol[(long)j * m + r];
+#pragma unroll
+                for (int c = 0; c < kMaxRhs; ++c)
+                    if (c < k) acc[c] = fma(lv, y.p[c][col], acc[c]);
+            }
+#pragma unroll
+            for (int c = 0; c < kMaxRhs; ++c)
+                if (c < k) smb[(long)c * 4 * nx + lf] = y.p[c][st + lf] - acc[c];
+        }
+        __syncthreads();
+        for (int qq = 0; qq < nsub; ++qq) {
+            const bool act = q == qq && xx < nx;
+            for (int c = 0; c < k; ++c) {
+                T *sm = smb + (long)c * 4 * nx;
+                T a = T(0), bb = T(1);
+                if (act) {
+                    a = line_in_sum(cf, sm, lf, st, c0, m, wli, lidx, lvin);
+                    bb = -cf.rec;
+                }
+                const T v = cta_line_scan<T>(a, bb, lane, wline, wmb + 64 * c, wmb + 64 * c + 32);
+                if (act) {
+                    sm[lf] = v;
+                    y.p[c][st + lf] = v;
+                }
+            }
+            __syncthreads();
+        }
+        if (mode == 0) return;
+        line_coef_load(cf, on, lb, st, c0, m, wui, uidx, uvin, urec, udinv);
+    } else {
+        if (on)
+            for (int c = 0; c < k; ++c) smb[(long)c * 4 * nx + lf] = y.p[c][st + lf];
+        __syncthreads();
+    }
+    if (on) {  // backward: t = y - sum_off U e
+        const int r = st + lf - c0;
+#pragma unroll
+        for (int c = 0; c < kMaxRhs; ++c) acc[c] = T(0);
+        for (int j = 0; j < wu; ++j) {
+            const T uv = uval[(long)j * m + r];
+            const int col = ucol[(long)j * m + r];
+#pragma unroll
+            for (int c = 0; c < kMaxRhs; ++c)
+                if (c < k) acc[c] = fma(uv, y.p[c][col], acc[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < kMaxRhs; ++c)
+            if (c < k) smb[(long)c * 4 * nx + lf] -= acc[c];
+    }
+    __syncthreads();
+    for (int qq = nsub - 1; qq >= 0; --qq) {
+        const bool act = q == qq && xx < nx;
+        for (int c = 0; c < k; ++c) {
+            T *sm = smb + (long)c * 4 * nx;
+            T a = T(0), bb = T(1);
+            if (act) {
+                const T t = line_in_sum(cf, sm, lb, st, c0, m, wui, uidx, uvin);
+                a = cf.d * t;
+                bb = -cf.d * cf.rec;
+            }
+            const T v = cta_line_scan<T>(a, bb, lane, wline, wmb + 64 * c, wmb + 64 * c + 32);
+            if (act) {
+                sm[lb] = v;
+                y.p[c][st + lb] = v;
+                const int row = rows[st + lb];
+                z.p[c][row] = TZ(z.p[c][row] + TZ(v));
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // ---- host side ---------------------------------------------------------------------------------
 
 bool lines_fit(const msrsb_grid *g) { return g->nx >= 1 && g->nx <= kLinesMaxNx && (g->dim == 2 || g->dim == 3); }
@@ -759,6 +869,42 @@ msrsb_status lines_apply(const msrsb_handle *h, T *ry, TZ *z, cudaStream_t s) {
 template msrsb_status lines_apply<double, double>(const msrsb_handle *, double *, double *, cudaStream_t);
 template msrsb_status lines_apply<float, double>(const msrsb_handle *, float *, double *, cudaStream_t);
 template msrsb_status lines_apply<float, float>(const msrsb_handle *, float *, float *, cudaStream_t);
+
+// lines_apply for k right-hand sides (one launch per colour and direction,
+// as lines_apply); false in *ok when the blocks exceed the multi kernel's CTA
+bool lines_multi_fit(const msrsb_handle *h) {
+    const IluLines &L = h->lines;
+    const int nxp = ((L.nx + 31) / 32) * 32;
+    return (L.ncol == 4 ? 4 : 2) * nxp <= kLinesMultiThreads;
+}
+
+template <typename T, typename TZ>
+msrsb_status lines_apply_multi(const msrsb_handle *h, int k, Cols<T> ry, Cols<TZ> z, cudaStream_t s) {
+    const IluLines &L = h->lines;
+    const int last = L.ncol - 1, nxp = ((L.nx + 31) / 32) * 32;
+    const int threads = (L.ncol == 4 ? 4 : 2) * nxp;
+    if (threads > kLinesMultiThreads || k < 1 || k > kMaxRhs) return fail(MSRSB_EINVAL, "multi-vector sweep shape");
+    const size_t smem = (size_t)k * (4 * (size_t)L.nx + 64) * sizeof(T);
+    auto launch = [&](int mode, int c) -> msrsb_status {
+        const int nb = L.bptr[c + 1] - L.bptr[c];
+        if (!nb) return MSRSB_OK;
+        const int m = L.cptr[c + 1] - L.cptr[c];
+        MSRSB_PDL((lines_sweep_multi_kernel<T, TZ>), nb, threads, smem, s, mode, k, L.bptr[c], L.blk_start,
+                  L.blk_nsub, L.nx, nxp, L.cptr[c], m, L.wl[c], L.lcol + L.lbase[c], (const T *)L.lval + L.lbase[c],
+                  L.wli[c], L.lidx + L.libase[c], (const T *)L.lvin + L.libase[c], (const T *)L.lrec, L.wu[c],
+                  L.ucol + L.ubase[c], (const T *)L.uval + L.ubase[c], L.wui[c], L.uidx + L.uibase[c],
+                  (const T *)L.uvin + L.uibase[c], (const T *)L.urec, (const T *)L.udinv, L.rows, ry, z);
+        return MSRSB_OK;
+    };
+    for (int c = 0; c < last; ++c) MSRSB_TRY(launch(0, c));
+    MSRSB_TRY(launch(2, last));
+    for (int c = last - 1; c >= 0; --c) MSRSB_TRY(launch(1, c));
+    return MSRSB_OK;
+}
+template msrsb_status lines_apply_multi<double, double>(const msrsb_handle *, int, Cols<double>, Cols<double>,
+                                                        cudaStream_t);
+template msrsb_status lines_apply_multi<float, double>(const msrsb_handle *, int, Cols<float>, Cols<double>,
+                                                       cudaStream_t);
 
 void lines_free(IluLines *L, cudaStream_t s) {
     dfree(L->lidx, s);

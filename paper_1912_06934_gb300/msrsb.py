@@ -24,7 +24,7 @@ MSRSB_ORDER_LINES, MSRSB_ORDER_PARITY = 0, 1
 EXPORTS = ["msrsb_partition_size", "msrsb_partition", "msrsb_filter", "msrsb_build_basis", "msrsb_coarse_op",
            "msrsb_setup", "msrsb_apply", "msrsb_solve", "msrsb_get_setup", "msrsb_get_info", "msrsb_destroy",
            "msrsb_solve_host", "msrsb_profile", "msrsb_profile_read", "msrsb_wait_selftest", "msrsb_build_basis_noalloc",
-           "msrsb_solve_ensemble", "msrsb_transpose_values", "msrsb_pattern_outer", "msrsb_fma_rate", "msrsb_mpfa_assemble", "msrsb_mpfa_gradient", "msrsb_spmv", "msrsb_last_error"]
+           "msrsb_solve_ensemble", "msrsb_transpose_values", "msrsb_pattern_outer", "msrsb_fma_rate", "msrsb_mpfa_assemble", "msrsb_mpfa_gradient", "msrsb_spmv", "msrsb_solve_multi", "msrsb_last_error"]
 
 
 class MsrsbError(RuntimeError):
@@ -245,6 +245,18 @@ class Handle:
         if hist:
             out["hist"] = list(hbuf)[: it.value + 1]
         return out
+
+    def solve_multi(self, B, X=None, rtol=1e-8, maxit=200, stream=None):
+        """msrsb_solve_multi: B (nrhs, n*bdim) CUDA FP64, one right-hand side
+        per row; returns dict(x=(nrhs, n*bdim), iters=[...], relres=[...])."""
+        B = B.contiguous()
+        X = torch.zeros_like(B) if X is None else X
+        k = B.shape[0]
+        its = (ctypes.c_int32 * max(k, 1))()
+        rr = (ctypes.c_double * max(k, 1))()
+        _check(load().msrsb_solve_multi(self._h, ctypes.c_int32(k), _ptr(B), _ptr(X), ctypes.c_double(rtol),
+                                        ctypes.c_int32(maxit), its, rr, _stream(stream)))
+        return dict(x=X, iters=list(its)[:k], relres=list(rr)[:k])
 
     def get_setup(self, stream=None):
         inf = self.info()
