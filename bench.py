@@ -158,8 +158,8 @@ def kept_entries(c, ids, comp=None):
 # the source changes the figure no longer describes the kernel and the bench
 # reports null.
 SMOOTH_TRAFFIC = {
-    "darcy64": ("8ac28f3867c6d3c8", None),
-    "darcy128": ("8ac28f3867c6d3c8", None),
+    "darcy64": ("8ac28f3867c6d3c8", 40152320 + 33536),
+    "darcy128": ("8ac28f3867c6d3c8", 317547264 + 52004096),
 }
 
 
