@@ -358,7 +358,8 @@ def torch_as(a, dev):
 
 def form_summary(f, steps):
     r, inf = f["r"], f["info"]
-    return {"ms_per_step": sum(f["ms"]) / steps, "basis_iters": inf["basis_iters"], "krylov_iters": r["iters"],
+    return {"ms_per_step": sum(f["ms"]) / steps, "ms_steps": [float(x) for x in f["ms"]],
+            "basis_iters": inf["basis_iters"], "krylov_iters": r["iters"],
             "relres": r["relres"], "setup_ms": inf["setup_ms"], "solve_ms": inf["solve_ms"],
             "setup_phase_ms": dict(zip(PHASES, inf["phase_ms"])), "launches_per_step": f["launches"] / steps,
             "smooth_us_per_launch": f["smooth_ms"] / f["smooth_launches"] * 1e3 if f["smooth_launches"] else None}

@@ -292,11 +292,7 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
     MSRSB_TRY(partition_launch(&h->grid, h->part, h->cnode, h->p_ids, h->skel, h->colour, s));
     MSRSB_TRY(mark(1));
     // the smoother set-up (independent of P) on a side stream, from a second
-    // host thread, while this thread builds the basis. The side stream keeps
-    // the default priority: its latency-bound factorisation kernels then take
-    // the SM slots the bandwidth-bound smoothing passes leave (at the highest
-    // priority they held slots the passes needed and slowed them by more than
-    // they saved; measured at 64^3).
+    // host thread, while this thread builds the basis (default priority).
     if (!h->side) MSRSB_CUDA(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
     cudaEvent_t fork = nullptr, join = nullptr;
     MSRSB_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
@@ -314,9 +310,11 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
     std::promise<msrsb_status> tr_done;
     std::future<msrsb_status> tr_status = tr_done.get_future();
     std::string tr_err;
-    // The smoother set-up starts with the basis build. The main thread hands
-    // over an event recorded after the partition, or nullptr when it leaves
-    // early.
+    // The smoother set-up starts when the basis is built: beside the
+    // FP64-bound Galerkin product and the coarse factorisation on one cluster
+    // it finds idle SMs, while beside the bandwidth-bound smoothing passes it
+    // would slow them. The main thread hands over an event recorded at that
+    // point, or nullptr when it leaves early.
     std::promise<cudaEvent_t> go;
     std::future<cudaEvent_t> go_at = go.get_future();
     cudaEvent_t go_ev = nullptr;
@@ -356,8 +354,6 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
         }
         ~Release() { (*this)(nullptr); }
     } release{go};
-    MSRSB_CUDA(cudaEventRecord(go_ev, s));
-    release(go_ev);
     // filtered operator(s) streamed as sliced ELL, then Alg. 1 per component
     T *P = nullptr;
     MSRSB_TRY(dalloc(&P, nW * bd, s));
@@ -398,6 +394,8 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
     dfree(vmask, s);
     dfree(nzd, s);
     MSRSB_TRY(mark(2));
+    MSRSB_CUDA(cudaEventRecord(go_ev, s));
+    release(go_ev);
     // Galerkin coarse operator with the unfiltered A, and its inverse
     {
         const msrsb_status st = tr_status.get();
