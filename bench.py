@@ -39,7 +39,8 @@ N_GRID, H_BLOCK, SEED = 64, 8, 1002
 RTOL, MAXIT = 1e-8, 300
 ENS_MAXIT = 2000  # ensemble solves: random right-hand sides may need several GMRES(200) cycles
 BASIS = dict(tol=1e-3, n_it=10, max_iter=100)
-PHASES = ("partition", "filter_basis", "galerkin", "coarse_inverse", "workspace", "smoother_wait")
+PHASES = ("partition", "filter_basis", "galerkin", "coarse_inverse", "workspace", "smoother_wait",
+          "smoother_setup_side_stream")
 
 
 def make_problem():

@@ -148,10 +148,12 @@ typedef struct {
     double basis_e_it;                /* last e_it evaluated */
     int32_t n_zero_diag;              /* rows with D_hat_ii = 0 (update skipped) */
     int32_t ncolours;                 /* colour classes of the smoother */
-    double phase_ms[6];               /* set-up phases on the set-up stream, device time (only while
+    double phase_ms[7];               /* set-up phases on the set-up stream, device time (only while
                                          msrsb_profile(1) is on, else 0): partition, filter + basis,
                                          Galerkin, coarse inverse, workspaces, wait for the smoother
-                                         set-up (run on a side stream while the basis is built) */
+                                         set-up (run on a side stream beside the Galerkin product and
+                                         the coarse factorisation); then the smoother set-up's own span
+                                         on the side stream */
 } msrsb_info;
 
 /* Sizes implied by a grid: fine points n, coarse nodes nc, ELL width W.

@@ -333,7 +333,20 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
         } else if (cudaStreamWaitEvent(h->side, e, 0) != cudaSuccess) {
             side_st = fail(MSRSB_ECUDA, "stream wait failed");
         } else {
+            // profiling: the side stream's own span of the smoother set-up
+            cudaEvent_t s0 = nullptr, s1 = nullptr;
+            if (prof && (cudaEventCreate(&s0) != cudaSuccess || cudaEventCreate(&s1) != cudaSuccess)) s0 = s1 = nullptr;
+            if (s0) cudaEventRecord(s0, h->side);
             side_st = setup_smoother<T>(h, h->side);
+            if (s1) {
+                cudaEventRecord(s1, h->side);
+                float t = 0.f;
+                if (cudaEventSynchronize(s1) == cudaSuccess && cudaEventElapsedTime(&t, s0, s1) == cudaSuccess)
+                    h->phase_ms[6] = t;
+                cudaGetLastError();
+            }
+            if (s0) cudaEventDestroy(s0);
+            if (s1) cudaEventDestroy(s1);
         }
         if (side_st != MSRSB_OK) side_err = msrsb_last_error();
     });
@@ -1494,7 +1507,7 @@ extern "C" msrsb_status msrsb_get_info(const msrsb_handle *h, msrsb_info *info) 
     info->basis_e_it = h->basis_e_it;
     info->n_zero_diag = h->n_zero_diag;
     info->ncolours = h->ncolours;
-    for (int q = 0; q < 6; ++q) info->phase_ms[q] = h->phase_ms[q];
+    for (int q = 0; q < 7; ++q) info->phase_ms[q] = h->phase_ms[q];
     return MSRSB_OK;
 }
 

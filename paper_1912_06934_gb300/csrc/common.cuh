@@ -322,5 +322,5 @@ struct msrsb_handle {
     double basis_e_it = 0.0;
     int n_zero_diag = 0;
     int own_A = 0;  // set by msrsb_solve_host when it owns A's device copy
-    double phase_ms[6] = {0, 0, 0, 0, 0, 0};
+    double phase_ms[7] = {0, 0, 0, 0, 0, 0, 0};
 };

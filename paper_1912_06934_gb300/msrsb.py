@@ -57,7 +57,7 @@ class c_opts(ctypes.Structure):
 class c_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("bdim", ctypes.c_int32), ("nc", ctypes.c_int32), ("W", ctypes.c_int32),
                 ("basis_iters", ctypes.c_int32), ("basis_e_it", ctypes.c_double),
-                ("n_zero_diag", ctypes.c_int32), ("ncolours", ctypes.c_int32), ("phase_ms", ctypes.c_double * 6)]
+                ("n_zero_diag", ctypes.c_int32), ("ncolours", ctypes.c_int32), ("phase_ms", ctypes.c_double * 7)]
 
 
 class c_problem(ctypes.Structure):
