@@ -42,106 +42,109 @@ __global__ void line_key_kernel(int n, int dim, int nx, int ny, int nz, uint32_t
     idx[i] = i;
 }
 
-__global__ void lines_pos_kernel(int n, const int32_t *__restrict__ rows, int32_t *__restrict__ pos) {
+// pos[rows[p]] = p; and every row's stencil-offset mask: bit
+// (dx + 1) + 3 (dy + 1) + 9 (dz + 1) for each of its columns (the pattern
+// lies in the 3^dim neighbourhood with ascending columns, so entry e of a row
+// is the e-th set bit of its mask)
+__global__ void lines_pos_kernel(int n, int dim, int nx, int ny, const int32_t *__restrict__ rows,
+                                 const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                                 int32_t *__restrict__ pos, uint32_t *__restrict__ rmask) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p < n) pos[rows[p]] = p;
+    if (p >= n) return;
+    const int i = rows[p];
+    pos[i] = p;
+    const int xi = i % nx, yi = (i / nx) % ny, zi = dim == 3 ? i / (nx * ny) : 0;
+    uint32_t m = 0;
+    for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+        const int j = colidx[e];
+        const int xj = j % nx, yj = (j / nx) % ny, zj = dim == 3 ? j / (nx * ny) : 0;
+        m |= 1u << ((xj - xi + 1) + 3 * (yj - yi + 1) + 9 * (zj - zi + 1));
+    }
+    rmask[i] = m;
 }
 
 // ---- factorisation --------------------------------------------------------------------
 
-constexpr int kLBatch = 8;
+constexpr int kOffChunk = 4;
 
-// One row, one warp: lane l holds entry l of row i. The row's earlier
-// entries (position below pos[i]) are eliminated in position order: rows k
-// of up to kLBatch of them are staged in shared memory, l_ik = a_ik / u_kk
-// (as a product with the stored 1 / u_kk), then every later entry (i, j) that
-// row k also holds gets a_ij -= l_ik u_kj.
+// Phase 1 of one colour, every row at once (one warp per row, lane e holding
+// entry e): the earlier entries of earlier colours (positions below c0, all
+// final) come first in the order, so they are eliminated in parallel before
+// the in-block ones, in position order: l_ik = a_ik / u_kk (as a product with
+// the stored 1 / u_kk), then every later entry (i, j) that row k also holds
+// gets a_ij -= l_ik u_kj. Entry (k, j) is found from row k's stencil-offset
+// mask (lines_pos_kernel): a popcount gives its place in row k, read straight
+// from global memory, the chunk's reads issued together.
 template <typename TF>
-__device__ void lines_eliminate(int i, int phi, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
-                                const int32_t *__restrict__ pos, TF *__restrict__ lu, const TF *__restrict__ rdiag,
-                                int *__restrict__ status, int32_t (*kc)[32], TF (*kv)[32]) {
-    const int lane = threadIdx.x & 31;
-    const int b = rowptr[i], len = rowptr[i + 1] - b;
-    if (len > 32) {
-        if (lane == 0) atomicCAS(status, 0, -(1 + i));
-        return;
-    }
-    const bool mine = lane < len;
-    const int j = mine ? colidx[b + lane] : -1;
-    const int pj = mine ? pos[j] : INT_MAX;
-    const int pi_ = pos[i];
-    TF a = mine ? lu[b + lane] : TF(0);
-    // this call eliminates the earlier entries with positions below phi
-    const bool lower = mine && pj < min(pi_, phi);
-    const unsigned lm = __ballot_sync(0xffffffffu, lower);
-    const int nlow = __popc(lm);
-    int rank = 0;  // place of this lower entry in the position order
-    for (unsigned m = lm; m; m &= m - 1) {
-        const int po = __shfl_sync(0xffffffffu, pj, __ffs(m) - 1);
-        rank += (lower && po < pj) ? 1 : 0;
-    }
-    int kb = 0, kl = 0;
-    TF rd = TF(0);
-    if (lower) {
-        kb = rowptr[j];
-        kl = min(rowptr[j + 1] - kb, 32);
-        rd = rdiag[j];
-    }
-    for (int t0 = 0; t0 < nlow; t0 += kLBatch) {
-        const int nb = min(kLBatch, nlow - t0);
-        int qs[kLBatch];
-#pragma unroll
-        for (int u = 0; u < kLBatch; ++u) {
-            const unsigned bm = __ballot_sync(0xffffffffu, lower && rank == t0 + u);
-            qs[u] = bm ? __ffs(bm) - 1 : 0;
-        }
-#pragma unroll
-        for (int u = 0; u < kLBatch; ++u) {
-            if (u < nb) {
-                const int ub = __shfl_sync(0xffffffffu, kb, qs[u]), ul = __shfl_sync(0xffffffffu, kl, qs[u]);
-                kc[u][lane] = lane < ul ? colidx[ub + lane] : INT_MAX;
-                kv[u][lane] = lane < ul ? lu[ub + lane] : TF(0);
-            }
-        }
-        __syncwarp();
-#pragma unroll
-        for (int u = 0; u < kLBatch; ++u) {
-            if (u < nb) {
-                const int q = qs[u];
-                const TF lik = __shfl_sync(0xffffffffu, a, q) * __shfl_sync(0xffffffffu, rd, q);
-                const int pk = __shfl_sync(0xffffffffu, pj, q);
-                if (lane == q) a = lik;
-                const bool later = mine && pj > pk;
-                const int32_t *rk = kc[u];
-                int p = 0;
-#pragma unroll
-                for (int step = 16; step >= 1; step >>= 1)
-                    if (rk[p + step - 1] < j) p += step;
-                if (later && rk[p] == j) a = a - lik * kv[u][p];
-            }
-        }
-        __syncwarp();  // the next batch overwrites the staged rows
-    }
-    if (mine) lu[b + lane] = a;
-    __syncwarp();
-}
-
-// Phase 1 of one colour, every row at once (one warp per row): the earlier
-// entries of earlier colours (positions below c0, all final) come first in
-// the order, so they are eliminated in parallel before the in-block ones.
-template <typename TF>
-__global__ void __launch_bounds__(128) lines_factor_off_kernel(int c0, int cnt, const int32_t *__restrict__ rows,
+__global__ void __launch_bounds__(128) lines_factor_off_kernel(int c0, int cnt, int dim, int nx, int ny,
+                                                               const int32_t *__restrict__ rows,
                                                                const int32_t *__restrict__ rowptr,
                                                                const int32_t *__restrict__ colidx,
-                                                               const int32_t *__restrict__ pos, TF *__restrict__ lu,
-                                                               const TF *__restrict__ rdiag,
-                                                               int *__restrict__ status) {
-    __shared__ int32_t s_kc[4][kLBatch][32];
-    __shared__ TF s_kv[4][kLBatch][32];
-    const int w = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5), q = threadIdx.x >> 5;
+                                                               const int32_t *__restrict__ pos,
+                                                               const uint32_t *__restrict__ rmask,
+                                                               TF *__restrict__ lu, const TF *__restrict__ rdiag) {
+    const int w = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (w >= cnt) return;  // whole warps leave together
     const int i = rows[c0 + w];
-    lines_eliminate<TF>(i, c0, rowptr, colidx, pos, lu, rdiag, status, s_kc[q], s_kv[q]);
+    const int b = rowptr[i], len = rowptr[i + 1] - b;  // len <= 32 (set-up checks it)
+    const bool mine = lane < len;
+    const int j = mine ? colidx[b + lane] : 0;
+    const int pj = mine ? pos[j] : INT_MAX;
+    TF a = mine ? lu[b + lane] : TF(0);
+    const int xi = i % nx, yi = (i / nx) % ny, zi = dim == 3 ? i / (nx * ny) : 0;
+    int ox = 1, oy = 1, oz = 1;  // this entry's offset from row i, zero-based per axis
+    if (mine) {
+        ox = j % nx - xi + 1;
+        oy = (j / nx) % ny - yi + 1;
+        oz = dim == 3 ? j / (nx * ny) - zi + 1 : 1;
+    }
+    const bool lower = mine && pj < c0;
+    int kb = 0;
+    uint32_t km = 0;
+    TF rd = TF(0);
+    if (lower) {  // the pivot row's start, mask and 1 / u_kk
+        kb = rowptr[j];
+        km = rmask[j];
+        rd = rdiag[j];
+    }
+    const unsigned lm = __ballot_sync(0xffffffffu, lower);
+    const int nlow = __popc(lm);
+    int rank = 0;  // place of this pivot in the position order
+    for (unsigned mm = lm; mm; mm &= mm - 1) {
+        const int po = __shfl_sync(0xffffffffu, pj, __ffs(mm) - 1);
+        rank += (lower && po < pj) ? 1 : 0;
+    }
+    for (int t0 = 0; t0 < nlow; t0 += kOffChunk) {
+        TF u[kOffChunk], rk[kOffChunk];
+        int ql[kOffChunk];
+#pragma unroll
+        for (int t = 0; t < kOffChunk; ++t) {
+            const bool on = t0 + t < nlow;  // uniform
+            const unsigned bm = __ballot_sync(0xffffffffu, lower && rank == t0 + t);
+            const int qq = on ? __ffs(bm) - 1 : 0;
+            ql[t] = on ? qq : -1;
+            const int pk = __shfl_sync(0xffffffffu, pj, qq);
+            const int kx = __shfl_sync(0xffffffffu, ox, qq), ky = __shfl_sync(0xffffffffu, oy, qq),
+                      kz = __shfl_sync(0xffffffffu, oz, qq);
+            const int kbt = __shfl_sync(0xffffffffu, kb, qq);
+            const uint32_t kmt = __shfl_sync(0xffffffffu, km, qq);
+            rk[t] = __shfl_sync(0xffffffffu, rd, qq);
+            const int dx = ox - kx + 1, dy = oy - ky + 1, dz = oz - kz + 1;  // j's offset from k
+            const bool near = dx >= 0 && dx <= 2 && dy >= 0 && dy <= 2 && dz >= 0 && dz <= 2;
+            const int o = near ? dx + 3 * dy + 9 * dz : 0;
+            const bool hit = on && mine && pj > pk && near && ((kmt >> o) & 1u);
+            u[t] = hit ? lu[kbt + __popc(kmt & ((1u << o) - 1u))] : TF(0);
+        }
+#pragma unroll
+        for (int t = 0; t < kOffChunk; ++t) {
+            const TF lik = __shfl_sync(0xffffffffu, a, ql[t] < 0 ? 0 : ql[t]) * rk[t];
+            if (ql[t] >= 0) {  // uniform
+                if (lane == ql[t]) a = lik;
+                else a = a - lik * u[t];
+            }
+        }
+    }
+    if (mine) lu[b + lane] = a;
 }
 
 // Phase 2 of one colour: the in-block earlier entries. CTA b0 + blockIdx.x
@@ -721,7 +724,9 @@ msrsb_status lines_setup(msrsb_handle *h, TF *lu, cudaStream_t s) {
     dfree(key, s);
     dfree(key2, s);
     dfree(idx, s);
-    lines_pos_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, L.rows, h->pos_of);
+    uint32_t *rmask = nullptr;
+    MSRSB_TRY(dalloc(&rmask, n, s));
+    lines_pos_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, dim, nx, ny, L.rows, A.rowptr, A.colidx, h->pos_of, rmask);
     MSRSB_LAUNCHED("lines_pos_kernel");
     // ---- block table (host): blocks of each colour in block order ----
     const int nby = (ny + 1) / 2, nbz = dim == 3 ? (nz + 1) / 2 : 1;
@@ -765,7 +770,7 @@ msrsb_status lines_setup(msrsb_handle *h, TF *lu, cudaStream_t s) {
         const int cnt = L.cptr[c + 1] - L.cptr[c];
         if (c > 0) {
             lines_factor_off_kernel<TF><<<ceil_div((long)cnt * 32, 128), 128, 0, s>>>(
-                L.cptr[c], cnt, L.rows, A.rowptr, A.colidx, h->pos_of, lu, rdiag, status);
+                L.cptr[c], cnt, dim, nx, ny, L.rows, A.rowptr, A.colidx, h->pos_of, rmask, lu, rdiag);
             MSRSB_LAUNCHED("lines_factor_off_kernel");
         }
         lines_factor_ring_kernel<TF><<<nb, 128, 0, s>>>(c, L.bptr[c], L.blk_start, L.blk_nsub, dim, nx, ny, L.rows,
@@ -776,6 +781,7 @@ msrsb_status lines_setup(msrsb_handle *h, TF *lu, cudaStream_t s) {
     MSRSB_CUDA(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, s));
     MSRSB_CUDA(cudaStreamSynchronize(s));
     dfree(rdiag, s);
+    dfree(rmask, s);
     if (hs) {
         dfree(status, s);
         dfree(dpos, s);
