@@ -13,6 +13,7 @@ prints one JSON line with the max over ranks.
 """
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -613,6 +614,12 @@ def gpu_arm(args, rank, world):
                                   **ensemble_time(M, probs, 6, 1))
         del probs
         out["configs"] = cfg
+    # the launch shapes the smoothing passes settled on, per size class (timed
+    # in the warm-up steps; "us" = each shape's best trial pass)
+    out["autotune"] = M.msrsb_tune_table()
+    for t in out["autotune"]:
+        if t["value_bytes"] == 4 and t["W"] == 8 and t["n_log2"] == math.ceil(math.log2(64 ** 3)):
+            out["roofline"]["launch_shape"] = {"lanes_per_row": t["lanes"], "threads": t["threads"]}
     if rank == 0 and not args.no_cpu_baseline:
         out["_oracle_inputs"] = (c, vprobe_h, res)
     return out
@@ -856,7 +863,8 @@ def ensemble_run(args):
             "config": {"workload": ensemble_workload(args.ens_R, edges, sizes, rows, nnz),
                        "concurrency": args.ens_conc},
             "sequential": out[1], "concurrent": out[args.ens_conc],
-            "speedup_concurrent_vs_sequential": out[1]["s"] / out[args.ens_conc]["s"]}
+            "speedup_concurrent_vs_sequential": out[1]["s"] / out[args.ens_conc]["s"],
+            "autotune": M.msrsb_tune_table()}
     print(json.dumps(line))
 
 

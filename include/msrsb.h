@@ -375,6 +375,44 @@ msrsb_status msrsb_mpfa_gradient(const msrsb_grid *g, const double *K_hat, const
                                  const int32_t *well_cells_h, const double *well_pw_h, const double *lam,
                                  const double *p, double *grad, cudaStream_t stream);
 
+/* Launch-shape autotuner (no counterpart in the paper; the paper's method is
+ * unchanged by it). The restricted-smoothing pass of Eq. 6 / Alg. 1 has
+ * several launch shapes that give bit-identical results: 1, 2 or 4 lanes per
+ * fine row (32, 16 or 8 rows per warp; a lane gathers W/lanes of P's colour
+ * slots) and 256 or 128 threads per CTA, variants 0..5 in the order
+ * (1,256) (1,128) (2,256) (2,128) (4,256) (4,128). With MSRSB_TUNE_AUTO (the
+ * default) the first Alg. 1 loop of a new size class runs its first 12 passes
+ * round-robin over the 6 shapes, times each pass with CUDA events on the
+ * loop's stream (one host synchronisation) and uses the fastest shape for its
+ * remaining passes and for every later loop of the same class in the process.
+ * A class is (kernel, device, value size, W, ceil(log2 n), ceil(log2 of the
+ * operator's stored entries per row)); loops with max_iter < 12 use variant 0
+ * without tuning, and a loop that converges during its trial passes stores
+ * nothing. The table is process-wide and guarded for concurrent host threads.
+ * msrsb_tune_mode(m): m = MSRSB_TUNE_AUTO, or 0..5 to force that variant for
+ * every loop (no timing, no table update); EINVAL otherwise.
+ * msrsb_tune_reset(): empties the table. msrsb_tune_table(out, cap, count_h):
+ * writes min(cap, entries) entries to host array out (nullable when cap = 0)
+ * and the number of entries to *count_h. Host bookkeeping only. */
+#define MSRSB_TUNE_AUTO (-1)
+typedef enum { MSRSB_TUNE_SMOOTH = 0 } msrsb_tune_kernel;
+typedef struct {
+    int32_t kernel;      /* msrsb_tune_kernel */
+    int32_t device;      /* CUDA device ordinal */
+    int32_t value_bytes; /* 4 (FP32 basis) or 8 (FP64 basis) */
+    int32_t W;           /* colour slots per row (4 or 8) */
+    int32_t n_log2;      /* ceil(log2 n) */
+    int32_t width_log2;  /* ceil(log2 (stored entries / n)) */
+    int32_t variant;     /* the chosen shape */
+    int32_t lanes;       /* its lanes per row */
+    int32_t threads;     /* its threads per CTA */
+    int32_t n_variants;  /* shapes timed */
+    float us[8];         /* best trial time of each shape, microseconds */
+} msrsb_tune_entry;
+msrsb_status msrsb_tune_mode(int32_t mode);
+msrsb_status msrsb_tune_reset(void);
+msrsb_status msrsb_tune_table(msrsb_tune_entry *out, int32_t cap, int32_t *count_h);
+
 /* Measurement support (no counterpart in the paper). msrsb_profile(1)
  * resets the counters and brackets every Alg. 1 loop (the restricted-smoothing
  * passes of one basis family) with one pair of CUDA events on its stream, so

@@ -7,4 +7,5 @@ from .msrsb import (Mat, Handle, MsrsbError, grid, opts, basis_opts, load,  # no
                     msrsb_setup, msrsb_apply, msrsb_solve, msrsb_get_setup, msrsb_get_info, msrsb_destroy,
                     msrsb_solve_host, msrsb_profile, msrsb_profile_read, msrsb_fma_rate,
                     msrsb_build_basis_noalloc, msrsb_solve_ensemble, msrsb_transpose_values,
-                    msrsb_pattern_outer, msrsb_wait_selftest, msrsb_mpfa_assemble, msrsb_mpfa_gradient)
+                    msrsb_pattern_outer, msrsb_wait_selftest, msrsb_mpfa_assemble, msrsb_mpfa_gradient,
+                    msrsb_tune_mode, msrsb_tune_reset, msrsb_tune_table, MSRSB_TUNE_AUTO, MSRSB_TUNE_SMOOTH)

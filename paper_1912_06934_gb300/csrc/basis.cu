@@ -107,6 +107,138 @@ __global__ void __launch_bounds__(256) smooth_kernel(int n, const int32_t *__res
     }
 }
 
+// NC consecutive values of T in one vector access (4, 8, 16 or 32 bytes).
+template <typename T, int NC>
+__device__ __forceinline__ void load_part(const T *__restrict__ p, T (&out)[NC]) {
+    constexpr int B = NC * (int)sizeof(T);
+    if constexpr (B == 32) {
+        unsigned u[8];
+        ld_nc_v8(p, u);
+        memcpy(out, u, B);
+    } else if constexpr (B == 16) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p));
+        memcpy(out, &v, B);
+    } else if constexpr (B == 8) {
+        const uint2 v = __ldg(reinterpret_cast<const uint2 *>(p));
+        memcpy(out, &v, B);
+    } else {
+        static_assert(B == 4, "a part is 4, 8, 16 or 32 bytes");
+        const unsigned v = __ldg(reinterpret_cast<const unsigned *>(p));
+        memcpy(out, &v, B);
+    }
+}
+
+template <typename T, int NC>
+__device__ __forceinline__ void store_part(T *__restrict__ p, const T (&in)[NC]) {
+    constexpr int B = NC * (int)sizeof(T);
+    if constexpr (B == 32) {
+        uint4 v[2];
+        memcpy(v, in, B);
+        reinterpret_cast<uint4 *>(p)[0] = v[0];
+        reinterpret_cast<uint4 *>(p)[1] = v[1];
+    } else if constexpr (B == 16) {
+        uint4 v;
+        memcpy(&v, in, B);
+        *reinterpret_cast<uint4 *>(p) = v;
+    } else if constexpr (B == 8) {
+        uint2 v;
+        memcpy(&v, in, B);
+        *reinterpret_cast<uint2 *>(p) = v;
+    } else {
+        unsigned v;
+        memcpy(&v, in, B);
+        *reinterpret_cast<unsigned *>(p) = v;
+    }
+}
+
+// The same pass with L lanes per row: lane `sub` of a row's group owns the
+// W / L colour slots sub*W/L .. (sub+1)*W/L - 1, walks the whole row of A_hat
+// (the group's column and value loads hit the same words) and gathers only its
+// slots of P's rows, so the group keeps L times as many narrower gathers in
+// flight. Every slot's products are summed in the one-lane kernel's order; the
+// row sum is formed by every lane over all W slots in slot order after an
+// exchange of the updated values, so the result is bit for bit that of
+// smooth_kernel (the launch shape is a tuning choice, never a numerical one).
+template <typename T, int W, int L>
+__global__ void __launch_bounds__(256) smooth_lanes_kernel(int n, const int32_t *__restrict__ slice_ptr,
+                                                           const int32_t *__restrict__ scol,
+                                                           const T *__restrict__ sval, const T *__restrict__ scale,
+                                                           const uint8_t *__restrict__ vmask,
+                                                           const uint8_t *__restrict__ skel, const T *__restrict__ Pin,
+                                                           T *__restrict__ Pout, unsigned long long *__restrict__ emax,
+                                                           int check, const int *__restrict__ done,
+                                                           int *__restrict__ iters, int k_pass) {
+    static_assert(L == 2 || L == 4, "2 or 4 lanes per row");
+    constexpr int NC = W / L;
+    pdl_prologue();
+    if (*done) return;
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (int)(t / L);
+    if (t == 0) *iters = k_pass + 1;
+    double e_loc = 0.0;
+    if (i < n) {
+        const int sub = (int)(t & (L - 1));
+        const unsigned lane = threadIdx.x & 31u;
+        const unsigned gmask = ((1u << L) - 1u) << (lane & ~(unsigned)(L - 1));
+        const int c0 = sub * NC;
+        const int s = i >> 5, r = i & 31;
+        const int beg = slice_ptr[s];
+        const int width = (slice_ptr[s + 1] - beg) >> 5;
+        T acc[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c] = T(0);
+        const int32_t *cp = scol + beg + r;
+        const T *vp = sval + beg + r;
+        for (int j = 0; j < width; ++j) {
+            const unsigned pc = (unsigned)__ldg(cp + (j << 5));
+            const T a = __ldg(vp + (j << 5));
+            const unsigned m = (pc >> (kColShift + c0)) & ((1u << NC) - 1u);
+            if (m) {
+                T pk[NC];
+                load_part<T, NC>(Pin + (long)(pc & kColMask) * W + c0, pk);
+#pragma unroll
+                for (int c = 0; c < NC; ++c)
+                    if (m & (1u << c)) acc[c] = fma(a, pk[c], acc[c]);
+            }
+        }
+        T own[NC];
+        load_part<T, NC>(Pin + (long)i * W + c0, own);
+        const unsigned vm = vmask[i];
+        const T sc = scale[i];
+        T tl[NC];
+        T emx = T(0);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            if (vm & (1u << (c0 + c))) {
+                const T d = -sc * acc[c];
+                tl[c] = own[c] + d;
+                emx = fmax(emx, fabs(d));
+            } else {
+                tl[c] = T(0);
+            }
+        }
+        T sum = T(0);
+#pragma unroll
+        for (int q = 0; q < L; ++q)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const T v = __shfl_sync(gmask, tl[c], q, L);
+                if (vm & (1u << (q * NC + c))) sum += v;
+            }
+#pragma unroll
+        for (int o = 1; o < L; o <<= 1) emx = fmax(emx, __shfl_xor_sync(gmask, emx, o, L));
+        const T rs = T(1) / sum;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) tl[c] = (vm & (1u << (c0 + c))) ? tl[c] * rs : T(0);
+        store_part<T, NC>(Pout + (long)i * W + c0, tl);
+        if (check && !skel[i]) e_loc = (double)emx;
+    }
+    if (check) {
+        e_loc = warp_max(e_loc);
+        if ((threadIdx.x & 31) == 0 && e_loc > 0.0) atomicMax(emax, dbits(e_loc));
+    }
+}
+
 __global__ void basis_check_kernel(const unsigned long long *__restrict__ emax_k, double tol, int *__restrict__ done,
                                    double *__restrict__ e_last) {
     pdl_prologue();
@@ -148,12 +280,26 @@ double *pinned_scratch() {
 }
 
 template <typename T, int W>
-static msrsb_status launch_smooth(int n, const Sell &S, int comp, const T *scale, const uint8_t *vmask, const uint8_t *skel,
-                          const T *Pin, T *Pout, unsigned long long *emax, int check, const int *done, int *iters,
-                          int k, cudaStream_t s) {
-    int grid = ceil_div((long)S.nslices * kSell, 256);
-    MSRSB_PDL((smooth_kernel<T, W>), grid, 256, 0, s, n, S.slice_ptr, S.col, (const T *)S.val[comp], scale, vmask, skel,
-              Pin, Pout, emax, check, done, iters, k);
+static msrsb_status launch_smooth(int variant, int n, const Sell &S, int comp, const T *scale, const uint8_t *vmask,
+                                  const uint8_t *skel, const T *Pin, T *Pout, unsigned long long *emax, int check,
+                                  const int *done, int *iters, int k, cudaStream_t s) {
+    const T *val = (const T *)S.val[comp];
+    const SmoothShape sh = kSmoothShapes[variant];
+    const int grid = ceil_div((long)S.nslices * kSell * sh.lanes, sh.threads);
+    switch (sh.lanes) {
+        case 1:
+            MSRSB_PDL((smooth_kernel<T, W>), grid, sh.threads, 0, s, n, S.slice_ptr, S.col, val, scale, vmask, skel,
+                      Pin, Pout, emax, check, done, iters, k);
+            break;
+        case 2:
+            MSRSB_PDL((smooth_lanes_kernel<T, W, 2>), grid, sh.threads, 0, s, n, S.slice_ptr, S.col, val, scale,
+                      vmask, skel, Pin, Pout, emax, check, done, iters, k);
+            break;
+        default:
+            MSRSB_PDL((smooth_lanes_kernel<T, W, 4>), grid, sh.threads, 0, s, n, S.slice_ptr, S.col, val, scale,
+                      vmask, skel, Pin, Pout, emax, check, done, iters, k);
+            break;
+    }
     return MSRSB_OK;
 }
 
@@ -184,6 +330,26 @@ msrsb_status basis_loop(int n, int W, const Sell &S, int comp, const T *scale, c
     MSRSB_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     bool pending = false;
     T *buf[2] = {P, P2};
+    // launch shape (see msrsb_tune_mode): forced, cached for this size class,
+    // or timed on this loop's first passes
+    constexpr int kTrialPasses = 2 * kSmoothVariants;
+    TuneKey key;
+    key.kernel = MSRSB_TUNE_SMOOTH;
+    MSRSB_CUDA(cudaGetDevice(&key.device));
+    key.value_bytes = (int)sizeof(T);
+    key.W = W;
+    key.n_log2 = ceil_log2(n);
+    key.width_log2 = ceil_log2(n > 0 ? (S.entries + n - 1) / n : 1);
+    int variant = 0;
+    bool tuning = false;
+    const int mode = tune_mode();
+    if (mode >= 0)
+        variant = mode;
+    else if (!tune_lookup(key, &variant))
+        tuning = maxit >= kTrialPasses && n > 0;
+    cudaEvent_t trial_ev[2 * kTrialPasses] = {};
+    if (tuning)
+        for (int q = 0; q < 2 * kTrialPasses; ++q) MSRSB_CUDA(cudaEventCreate(&trial_ev[q]));
     // optional timing of the smoothing passes (profiling mode): one CUDA event
     // pair around the whole loop on s, so that consecutive passes keep their
     // programmatic overlap; the average pass = loop time / passes that worked
@@ -202,12 +368,16 @@ msrsb_status basis_loop(int n, int W, const Sell &S, int comp, const T *scale, c
             if (((volatile int *)pin)[0] != 0) break;  // converged at an earlier check
             pending = false;
         }
+        const bool trial = tuning && k < kTrialPasses;
+        const int v = trial ? k % kSmoothVariants : variant;
+        if (trial) MSRSB_CUDA(cudaEventRecord(trial_ev[2 * k], s));
         if (W == 4)
-            MSRSB_TRY((launch_smooth<T, 4>(n, S, comp, scale, vmask, skel, buf[k & 1], buf[(k + 1) & 1], emax + k,
-                                           check, flags, flags + 1, k, s)));
+            MSRSB_TRY((launch_smooth<T, 4>(v, n, S, comp, scale, vmask, skel, buf[k & 1], buf[(k + 1) & 1],
+                                           emax + k, check, flags, flags + 1, k, s)));
         else
-            MSRSB_TRY((launch_smooth<T, 8>(n, S, comp, scale, vmask, skel, buf[k & 1], buf[(k + 1) & 1], emax + k,
-                                           check, flags, flags + 1, k, s)));
+            MSRSB_TRY((launch_smooth<T, 8>(v, n, S, comp, scale, vmask, skel, buf[k & 1], buf[(k + 1) & 1],
+                                           emax + k, check, flags, flags + 1, k, s)));
+        if (trial) MSRSB_CUDA(cudaEventRecord(trial_ev[2 * k + 1], s));
         launched = k + 1;
         if (check) {
             MSRSB_PDL((basis_check_kernel), 1, 1, 0, s, emax + k, o->tol, flags, e_last);
@@ -218,6 +388,29 @@ msrsb_status basis_loop(int n, int W, const Sell &S, int comp, const T *scale, c
                 pending = true;
             }
         }
+        if (tuning && k == kTrialPasses - 1) {
+            // every shape has run twice: keep each one's faster pass, take the
+            // fastest shape (the lower index on a tie) for the rest of the loop
+            int h_done = 0;
+            MSRSB_CUDA(cudaMemcpyAsync(&h_done, flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+            MSRSB_CUDA(cudaStreamSynchronize(s));
+            float us[kSmoothVariants];
+            for (int q = 0; q < kSmoothVariants; ++q) us[q] = __builtin_inff();
+            for (int q = 0; q < kTrialPasses; ++q) {
+                float ms = 0.f;
+                MSRSB_CUDA(cudaEventElapsedTime(&ms, trial_ev[2 * q], trial_ev[2 * q + 1]));
+                const int vq = q % kSmoothVariants;
+                if (1e3f * ms < us[vq]) us[vq] = 1e3f * ms;
+            }
+            int best = 0;
+            for (int q = 1; q < kSmoothVariants; ++q)
+                if (us[q] < us[best]) best = q;
+            if (!h_done) {  // a converged loop's late passes leave at once: their times mean nothing
+                variant = best;
+                tune_store(key, best, kSmoothVariants, us);
+            }
+            tuning = false;
+        }
     }
     if (prof) MSRSB_CUDA(cudaEventRecord(tev[1], s));
     int h_flags[2] = {0, 0};
@@ -226,6 +419,8 @@ msrsb_status basis_loop(int n, int W, const Sell &S, int comp, const T *scale, c
     MSRSB_CUDA(cudaMemcpyAsync(&h_e, e_last, sizeof(double), cudaMemcpyDeviceToHost, s));
     MSRSB_CUDA(cudaStreamSynchronize(s));
     cudaEventDestroy(ev);
+    for (cudaEvent_t &e : trial_ev)
+        if (e) cudaEventDestroy(e);
     int iters = h_flags[1];
     if (prof) {
         // only the first `iters` launches did work; later ones left at once

@@ -107,6 +107,23 @@ inline cudaError_t pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
 bool profiling();
 void add_smooth_time(int launches, double ms);
 
+// launch-shape autotuner (tune.cu, msrsb_tune_*): a kernel's launch shapes
+// give bit-identical results; the fastest, timed on the problem itself, is
+// kept per (kernel, device, value size, W, size class)
+constexpr int kTuneMaxVariants = 8;
+struct TuneKey {
+    int kernel = 0, device = 0, value_bytes = 0, W = 0, n_log2 = 0, width_log2 = 0;
+};
+struct SmoothShape {
+    int lanes, threads;  // lanes per fine row, threads per CTA
+};
+constexpr int kSmoothVariants = 6;
+constexpr SmoothShape kSmoothShapes[kSmoothVariants] = {{1, 256}, {1, 128}, {2, 256}, {2, 128}, {4, 256}, {4, 128}};
+int tune_mode();                                   // MSRSB_TUNE_AUTO or a forced variant
+bool tune_lookup(const TuneKey &k, int *variant);  // cached choice, if any
+void tune_store(const TuneKey &k, int variant, int nvar, const float *us);
+int ceil_log2(long v);
+
 constexpr int kMaxW = 8;          // 2^3 coarse slots per fine row
 constexpr int kColShift = 24;     // packed column: col | mask << 24
 constexpr int32_t kColMask = (1 << kColShift) - 1;

@@ -20,11 +20,13 @@ MSRSB_SMOOTH_NONE, MSRSB_SMOOTH_ILU0, MSRSB_SMOOTH_GS, MSRSB_SMOOTH_L1JAC, MSRSB
 MSRSB_GMRES, MSRSB_PCG, MSRSB_RICHARDSON = 0, 1, 2
 MSRSB_RESTRICT_GALERKIN, MSRSB_RESTRICT_FV = 0, 1
 MSRSB_ORDER_LINES, MSRSB_ORDER_PARITY = 0, 1
+MSRSB_TUNE_AUTO, MSRSB_TUNE_SMOOTH = -1, 0
 
 EXPORTS = ["msrsb_partition_size", "msrsb_partition", "msrsb_filter", "msrsb_build_basis", "msrsb_coarse_op",
            "msrsb_setup", "msrsb_apply", "msrsb_solve", "msrsb_get_setup", "msrsb_get_info", "msrsb_destroy",
            "msrsb_solve_host", "msrsb_profile", "msrsb_profile_read", "msrsb_wait_selftest", "msrsb_build_basis_noalloc",
-           "msrsb_solve_ensemble", "msrsb_transpose_values", "msrsb_pattern_outer", "msrsb_fma_rate", "msrsb_mpfa_assemble", "msrsb_mpfa_gradient", "msrsb_spmv", "msrsb_solve_multi", "msrsb_last_error"]
+           "msrsb_solve_ensemble", "msrsb_transpose_values", "msrsb_pattern_outer", "msrsb_fma_rate", "msrsb_mpfa_assemble", "msrsb_mpfa_gradient", "msrsb_spmv", "msrsb_solve_multi", "msrsb_tune_mode", "msrsb_tune_reset",
+           "msrsb_tune_table", "msrsb_last_error"]
 
 
 class MsrsbError(RuntimeError):
@@ -323,6 +325,38 @@ def msrsb_fma_rate(prec, blocks_per_sm=8, stream=None):
     _check(load().msrsb_fma_rate(ctypes.c_int32(prec), ctypes.c_int32(blocks_per_sm), ctypes.byref(r),
                                  ctypes.byref(ms), _stream(stream)))
     return r.value, ms.value
+
+
+class c_tune_entry(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int32) for k in ("kernel", "device", "value_bytes", "W", "n_log2", "width_log2",
+                                              "variant", "lanes", "threads", "n_variants")] + \
+               [("us", ctypes.c_float * 8)]
+
+
+def msrsb_tune_mode(mode):
+    """MSRSB_TUNE_AUTO (time the launch shapes of a new size class) or a
+    forced shape index 0..5 (see include/msrsb.h)."""
+    _check(load().msrsb_tune_mode(ctypes.c_int32(mode)))
+
+
+def msrsb_tune_reset():
+    _check(load().msrsb_tune_reset())
+
+
+def msrsb_tune_table():
+    """The autotuner's decisions: one dict per size class."""
+    L = load()
+    cnt = ctypes.c_int32()
+    _check(L.msrsb_tune_table(None, ctypes.c_int32(0), ctypes.byref(cnt)))
+    n = cnt.value
+    arr = (c_tune_entry * max(n, 1))()
+    _check(L.msrsb_tune_table(arr, ctypes.c_int32(n), ctypes.byref(cnt)))
+    out = []
+    for e in arr[:min(n, cnt.value)]:
+        d = {k: getattr(e, k) for k, _ in c_tune_entry._fields_ if k != "us"}
+        d["us"] = [round(float(v), 3) for v in e.us[:e.n_variants]]
+        out.append(d)
+    return out
 
 
 def msrsb_profile_read():
