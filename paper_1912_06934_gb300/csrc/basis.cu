@@ -44,6 +44,38 @@ __device__ __forceinline__ void store_row(T *__restrict__ P, long k, const T (&i
     for (int q = 0; q < (int)(W * sizeof(T) / 16); ++q) dst[q] = src[q];
 }
 
+// Epilogue of a row's pass: dP = -scale_i (A_hat P)_i on the row's valid
+// slots, P_i + dP divided by its sum (one reciprocal), stored; sets
+// max |dP| over the row's slots in e_loc on check passes of non-skeleton rows.
+template <typename T, int W>
+__device__ __forceinline__ void smooth_epilogue(int i, const T (&acc)[W], const T *__restrict__ scale,
+                                                const uint8_t *__restrict__ vmask, const uint8_t *__restrict__ skel,
+                                                const T *__restrict__ Pin, T *__restrict__ Pout, int check,
+                                                double &e_loc) {
+    T own[W];
+    load_row<T, W>(Pin, i, own);
+    unsigned vm = vmask[i];
+    T sc = scale[i];
+    T t[W];
+    T sum = T(0), emx = T(0);
+#pragma unroll
+    for (int c = 0; c < W; ++c) {
+        if (vm & (1u << c)) {
+            T d = -sc * acc[c];
+            t[c] = own[c] + d;
+            sum += t[c];
+            emx = fmax(emx, fabs(d));
+        } else {
+            t[c] = T(0);
+        }
+    }
+    const T rs = T(1) / sum;  // one division per row (FP64 issue slots are scarce)
+#pragma unroll
+    for (int c = 0; c < W; ++c) t[c] = (vm & (1u << c)) ? t[c] * rs : T(0);
+    store_row<T, W>(Pout, i, t);
+    if (check && !skel[i]) e_loc = (double)emx;
+}
+
 template <typename T, int W>
 __global__ void __launch_bounds__(256) smooth_kernel(int n, const int32_t *__restrict__ slice_ptr,
                                                      const int32_t *__restrict__ scol, const T *__restrict__ sval,
@@ -100,6 +132,77 @@ __global__ void __launch_bounds__(256) smooth_kernel(int n, const int32_t *__res
         for (int c = 0; c < W; ++c) t[c] = (vm & (1u << c)) ? t[c] * rs : T(0);
         store_row<T, W>(Pout, i, t);
         if (check && !skel[i]) e_loc = (double)emx;
+    }
+    if (check) {
+        e_loc = warp_max(e_loc);
+        if ((threadIdx.x & 31) == 0 && e_loc > 0.0) atomicMax(emax, dbits(e_loc));
+    }
+}
+
+// The same pass with the column words and values of the next D entries of the
+// row loaded ahead of the current entry's gather of P (D + 1 entries' operator
+// loads in flight per thread for two registers each, where unrolling the
+// gathers themselves costs W registers per entry). CAP asks the compiler for
+// 8 (FP32) or 4 (FP64) CTAs of 256 threads per SM, the one-lane kernel's
+// occupancy, at the price of a few spilled registers. Same sums in the same
+// order: bit for bit smooth_kernel.
+template <typename T, int W, int D, bool CAP>
+__global__ void __launch_bounds__(256, CAP ? (sizeof(T) == 4 ? 8 : 4) : 1) smooth_pf_kernel(int n, const int32_t *__restrict__ slice_ptr,
+                                                        const int32_t *__restrict__ scol, const T *__restrict__ sval,
+                                                        const T *__restrict__ scale, const uint8_t *__restrict__ vmask,
+                                                        const uint8_t *__restrict__ skel, const T *__restrict__ Pin,
+                                                        T *__restrict__ Pout, unsigned long long *__restrict__ emax,
+                                                        int check, const int *__restrict__ done,
+                                                        int *__restrict__ iters, int k_pass) {
+    static_assert(D >= 1 && D <= 4, "prefetch 1 to 4 entries");
+    pdl_prologue();
+    if (*done) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) *iters = k_pass + 1;
+    double e_loc = 0.0;
+    if (i < n) {
+        int s = i >> 5, lane = i & 31;
+        int beg = slice_ptr[s];
+        int width = (slice_ptr[s + 1] - beg) >> 5;
+        T acc[W];
+#pragma unroll
+        for (int c = 0; c < W; ++c) acc[c] = T(0);
+        // 32-bit entry indices off the kernel's base pointers (no derived
+        // 64-bit pointers held across the loop: registers are the limit)
+        const int e0 = beg + lane, e_end = e0 + (width << 5);
+        unsigned pq[D];
+        T aq[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            pq[d] = 0u;
+            aq[d] = T(0);
+            if (d < width) {
+                pq[d] = (unsigned)__ldg(scol + e0 + (d << 5));
+                aq[d] = __ldg(sval + e0 + (d << 5));
+            }
+        }
+        for (int e = e0 + (D << 5); e < e_end + (D << 5); e += 32) {
+            const unsigned pc = pq[0];
+            const T a = aq[0];
+#pragma unroll
+            for (int d = 0; d + 1 < D; ++d) {
+                pq[d] = pq[d + 1];
+                aq[d] = aq[d + 1];
+            }
+            if (e < e_end) {
+                pq[D - 1] = (unsigned)__ldg(scol + e);
+                aq[D - 1] = __ldg(sval + e);
+            }
+            const unsigned m = pc >> kColShift;
+            if (m) {
+                T pk[W];
+                load_row<T, W>(Pin, (long)(pc & kColMask), pk);
+#pragma unroll
+                for (int c = 0; c < W; ++c)
+                    if (m & (1u << c)) acc[c] = fma(a, pk[c], acc[c]);
+            }
+        }
+        smooth_epilogue<T, W>(i, acc, scale, vmask, skel, Pin, Pout, check, e_loc);
     }
     if (check) {
         e_loc = warp_max(e_loc);
@@ -286,19 +389,37 @@ static msrsb_status launch_smooth(int variant, int n, const Sell &S, int comp, c
     const T *val = (const T *)S.val[comp];
     const SmoothShape sh = kSmoothShapes[variant];
     const int grid = ceil_div((long)S.nslices * kSell * sh.lanes, sh.threads);
-    switch (sh.lanes) {
-        case 1:
+    switch (sh.lanes * 16 + sh.prefetch * 2 + sh.cap) {
+        case 16:
             MSRSB_PDL((smooth_kernel<T, W>), grid, sh.threads, 0, s, n, S.slice_ptr, S.col, val, scale, vmask, skel,
                       Pin, Pout, emax, check, done, iters, k);
             break;
-        case 2:
+        case 20:
+            MSRSB_PDL((smooth_pf_kernel<T, W, 2, false>), grid, sh.threads, 0, s, n, S.slice_ptr, S.col, val, scale,
+                      vmask, skel, Pin, Pout, emax, check, done, iters, k);
+            break;
+        case 21:
+            MSRSB_PDL((smooth_pf_kernel<T, W, 2, true>), grid, sh.threads, 0, s, n, S.slice_ptr, S.col, val, scale,
+                      vmask, skel, Pin, Pout, emax, check, done, iters, k);
+            break;
+        case 23:
+            MSRSB_PDL((smooth_pf_kernel<T, W, 3, true>), grid, sh.threads, 0, s, n, S.slice_ptr, S.col, val, scale,
+                      vmask, skel, Pin, Pout, emax, check, done, iters, k);
+            break;
+        case 25:
+            MSRSB_PDL((smooth_pf_kernel<T, W, 4, true>), grid, sh.threads, 0, s, n, S.slice_ptr, S.col, val, scale,
+                      vmask, skel, Pin, Pout, emax, check, done, iters, k);
+            break;
+        case 32:
             MSRSB_PDL((smooth_lanes_kernel<T, W, 2>), grid, sh.threads, 0, s, n, S.slice_ptr, S.col, val, scale,
                       vmask, skel, Pin, Pout, emax, check, done, iters, k);
             break;
-        default:
+        case 64:
             MSRSB_PDL((smooth_lanes_kernel<T, W, 4>), grid, sh.threads, 0, s, n, S.slice_ptr, S.col, val, scale,
                       vmask, skel, Pin, Pout, emax, check, done, iters, k);
             break;
+        default:
+            return fail(MSRSB_EINVAL, "no smoothing kernel for %d lanes, prefetch %d", sh.lanes, sh.prefetch);
     }
     return MSRSB_OK;
 }

@@ -98,6 +98,8 @@ extern "C" msrsb_status msrsb_tune_table(msrsb_tune_entry *out, int32_t cap, int
         o.variant = e.variant;
         o.lanes = kSmoothShapes[e.variant].lanes;
         o.threads = kSmoothShapes[e.variant].threads;
+        o.ahead = kSmoothShapes[e.variant].prefetch;
+        o.capped = kSmoothShapes[e.variant].cap;
         o.n_variants = e.nvar;
         for (int v = 0; v < 8; ++v) o.us[v] = v < e.nvar ? e.us[v] : 0.f;
     }

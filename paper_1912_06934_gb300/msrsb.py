@@ -329,13 +329,13 @@ def msrsb_fma_rate(prec, blocks_per_sm=8, stream=None):
 
 class c_tune_entry(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int32) for k in ("kernel", "device", "value_bytes", "W", "n_log2", "width_log2",
-                                              "variant", "lanes", "threads", "n_variants")] + \
+                                              "variant", "lanes", "threads", "ahead", "capped", "n_variants")] + \
                [("us", ctypes.c_float * 8)]
 
 
 def msrsb_tune_mode(mode):
     """MSRSB_TUNE_AUTO (time the launch shapes of a new size class) or a
-    forced shape index 0..5 (see include/msrsb.h)."""
+    forced shape index 0..7 (see include/msrsb.h)."""
     _check(load().msrsb_tune_mode(ctypes.c_int32(mode)))
 
 

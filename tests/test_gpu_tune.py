@@ -1,6 +1,7 @@
 """The launch-shape autotuner of the restricted-smoothing pass (Alg. 1).
 
-Every launch shape (1, 2 or 4 lanes per row; 256 or 128 threads per CTA) must
+Every launch shape (1, 2 or 4 lanes per row; 256 or 128 threads per CTA; 0, 2,
+3 or 4 operator entries loaded ahead, registers free or capped) must
 give P bit for bit equal to the one-lane shape, in FP64 and FP32, for W = 8
 (3D) and W = 4 (2D), on grids whose row count is not a multiple of a warp or a
 CTA. In automatic mode a new size class is timed once, recorded in the table,
@@ -20,7 +21,9 @@ from synth.darcy import darcy_2d_case, darcy_3d_case  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-N_SHAPES = 6
+N_SHAPES = 8
+SHAPES = [(1, 256, 0, 0), (1, 128, 0, 0), (2, 256, 0, 0), (4, 256, 0, 0), (1, 256, 2, 0), (1, 256, 2, 1),
+          (1, 256, 3, 1), (1, 256, 4, 1)]
 
 
 @pytest.fixture(scope="module")
@@ -113,14 +116,14 @@ def test_auto_mode_records_a_class_and_keeps_the_result(M):
     assert t["n_variants"] == N_SHAPES and 0 <= t["variant"] < N_SHAPES
     assert all(u > 0 and math.isfinite(u) for u in t["us"])
     assert t["us"][t["variant"]] == min(t["us"])
-    assert (t["lanes"], t["threads"]) == [(1, 256), (1, 128), (2, 256), (2, 128), (4, 256), (4, 128)][t["variant"]]
+    assert (t["lanes"], t["threads"], t["ahead"], t["capped"]) == SHAPES[t["variant"]]
     # a second loop of the same class reuses the entry (no new row, same result)
     _, P2, _, _ = _basis(M, c, 1, 40)
     assert torch.equal(P2, P_ref)
     assert len(M.msrsb_tune_table()) == 1
     # a loop too short to time every shape twice records nothing
     M.msrsb_tune_reset()
-    _basis(M, c, 1, 11)
+    _basis(M, c, 1, 2 * N_SHAPES - 1)
     assert M.msrsb_tune_table() == []
 
 
