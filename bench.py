@@ -154,15 +154,19 @@ def kept_entries(c, ids, comp=None):
     return n + int(share.sum()), matches
 
 
-# DRAM bytes (read + write) per launch of smooth_kernel<float,8>, per
-# workload, from one ncu capture of one launch (caches flushed, as ncu does),
-# keyed by a hash of the kernel's source file at the time of the capture; once
-# the source changes the figure no longer describes the kernel and the bench
-# reports null.
+# DRAM bytes (read + write) per launch of the FP32 smoothing pass, per
+# workload and launch shape (the autotuner's variant index), from one ncu
+# capture of one launch (caches flushed, as ncu does), keyed by a hash of the
+# kernels' source file at the time of the capture; once the source changes, or
+# the tuner settles on another shape, the figure no longer describes the
+# kernel that ran and the bench reports null.
 SMOOTH_TRAFFIC = {
-    "darcy64": ("8ac28f3867c6d3c8", 40152320 + 33536),
-    "darcy128": ("8ac28f3867c6d3c8", 317547264 + 52004096),
+    ("darcy64", 0): ("9c418dcd555f5dd3", 40153600 + 37120),
+    ("darcy128", 6): ("9c418dcd555f5dd3", 317521920 + 51605760),
 }
+# the autotuner's shapes (lanes per row, threads, entries loaded ahead, capped)
+SMOOTH_SHAPES = [(1, 256, 0, 0), (1, 128, 0, 0), (2, 256, 0, 0), (4, 256, 0, 0), (1, 256, 2, 0), (1, 256, 2, 1),
+                 (1, 256, 3, 1), (1, 256, 4, 1)]
 
 
 def source_hash(name):
@@ -171,9 +175,28 @@ def source_hash(name):
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def smooth_traffic(workload):
-    h, traffic = SMOOTH_TRAFFIC.get(workload, (None, None))
+def smooth_traffic(workload, variant):
+    h, traffic = SMOOTH_TRAFFIC.get((workload, variant), (None, None))
     return traffic if traffic is not None and source_hash("basis.cu") == h else None
+
+
+def smooth_shape(M, n, W, esize):
+    """The launch shape the autotuner settled on for this size class (None
+    before any tuned loop of it ran)."""
+    nl = math.ceil(math.log2(max(n, 1)))
+    for t in M.msrsb_tune_table():
+        if t["value_bytes"] == esize and t["W"] == W and t["n_log2"] == nl:
+            ty = "float" if esize == 4 else "double"
+            lanes, thr, ahead, cap = SMOOTH_SHAPES[t["variant"]]
+            if lanes > 1:
+                kern = "smooth_lanes_kernel<%s,%d,%d>" % (ty, W, lanes)
+            elif ahead:
+                kern = "smooth_pf_kernel<%s,%d,%d,%s>" % (ty, W, ahead, "true" if cap else "false")
+            else:
+                kern = "smooth_kernel<%s,%d>" % (ty, W)
+            return {"variant": t["variant"], "kernel": kern, "lanes_per_row": lanes, "threads": thr,
+                    "entries_ahead": ahead, "registers_capped": bool(cap), "trial_us": t["us"]}
+    return None
 
 
 def apply_bytes(n, nnz, nnz_p, nc, W, coarse_bytes=None):
@@ -410,8 +433,12 @@ def run_extra_config(M, name, c, kind, flush, stream, dev, steps, warmup, hbm, p
         else:
             kept = [kept_entries(c, ids)]
             ab = apply_bytes(n, nnzb, nnz_p, info["nc"], W, coarse_apply_bytes(c)) if e == 4 else None
-        out[label]["smooth_roofline"] = smooth_roofline(f, n, W, [k[0] for k in kept], e, hbm, peak_kind,
-                                                        smooth_traffic(name) if label == "mixed" else None)
+        shape = smooth_shape(M, n, W, e)
+        out[label]["smooth_roofline"] = smooth_roofline(
+            f, n, W, [k[0] for k in kept], e, hbm, peak_kind,
+            smooth_traffic(name, shape["variant"]) if label == "mixed" and shape else None)
+        if out[label]["smooth_roofline"] is not None:
+            out[label]["smooth_roofline"]["launch_shape"] = shape
         if e == 8 and f["smooth_launches"]:
             # the FP64 pass is bound by the FP64 pipe: multiply-adds of A_hat P
             # on the pattern plus the W-wide update per row
@@ -556,6 +583,7 @@ def gpu_arm(args, rank, world):
                                 "fmas": coarse_fmas,
                                 "achieved_fma_per_s": coarse_fmas / (ci_ms * 1e-3) if ci_ms else None,
                                 "frac": coarse_fmas / (ci_ms * 1e-3) / pk["fp64_fma_per_s"] if ci_ms else None}
+    shape64 = smooth_shape(M, n, 8, 4)  # the FP32 pass's tuned shape for this size class
     out = {
         "metric": METRIC,
         "value": t32 / args.steps / 1e3,
@@ -576,9 +604,11 @@ def gpu_arm(args, rank, world):
         "fp64": fp64,
         "speedup_mixed_vs_fp64": t64 / t32,
         "mixed_error_vs_fp64": mixed_err,
-        "roofline": {"kernel": "smooth_kernel<float,8> (restricted smoothing, Alg. 1)", "bound": "hbm",
+        "roofline": {"kernel": (shape64["kernel"] if shape64 else "smooth_kernel<float,8>")
+                     + " (restricted smoothing, Alg. 1)", "bound": "hbm", "launch_shape": shape64,
                      "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm if achieved else None, "traffic": smooth_traffic("darcy64"),
+                     "frac": achieved / hbm if achieved else None,
+                     "traffic": smooth_traffic("darcy64", shape64["variant"]) if shape64 else None,
                      "bytes_per_launch": per_launch32, "filtered_entries": nnz_hat, "launches": sm_l32,
                      "us_per_launch": sm_ms32 / sm_l32 * 1e3 if sm_l32 else None,
                      "l2_resident": "the kept operator (28 MB) and both P buffers stay in L2 across the passes "
@@ -617,9 +647,6 @@ def gpu_arm(args, rank, world):
     # the launch shapes the smoothing passes settled on, per size class (timed
     # in the warm-up steps; "us" = each shape's best trial pass)
     out["autotune"] = M.msrsb_tune_table()
-    for t in out["autotune"]:
-        if t["value_bytes"] == 4 and t["W"] == 8 and t["n_log2"] == math.ceil(math.log2(64 ** 3)):
-            out["roofline"]["launch_shape"] = {"lanes_per_row": t["lanes"], "threads": t["threads"]}
     if rank == 0 and not args.no_cpu_baseline:
         out["_oracle_inputs"] = (c, vprobe_h, res)
     return out
@@ -746,7 +773,7 @@ def profile_run(args):
     set-up + GMRES solve twice; 'basis' runs three restricted smoothing passes
     (FP32) twice; on an N^3 grid (N = --grid; N = 64 is the benchmark's
     operator, N = 128 the 128^3 configuration's, any other N the benchmark's
-    generator at that size)."""
+    generator at that size); --shape forces the smoothing pass's launch shape."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -760,6 +787,8 @@ def profile_run(args):
         c = darcy_3d_case(n=args.grid, H=H_BLOCK, seed=SEED)
     A = M.Mat.from_host(c["indptr"], c["indices"], c["data"])
     g = M.grid(c["dims"], c["H"])
+    if args.shape is not None:
+        M.msrsb_tune_mode(args.shape)
     if args.profile == "solve":
         b = torch.as_tensor(c["b"], device="cuda")
         o = M.opts(prec=M.msrsb.MSRSB_F32, **BASIS)
@@ -880,6 +909,8 @@ def main():
     ap.add_argument("--profile", choices=["solve", "basis"], default=None,
                     help="run a workload for a profiler instead of the benchmark")
     ap.add_argument("--grid", type=int, default=N_GRID, help="grid edge for --profile")
+    ap.add_argument("--shape", type=int, default=None,
+                    help="for --profile: force this smoothing launch shape (autotuner variant index)")
     ap.add_argument("--ensemble", action="store_true", help="ensemble throughput instead of the benchmark")
     ap.add_argument("--ens-R", type=int, default=64)
     ap.add_argument("--ens-edges", default="32,48,64,80,96")
