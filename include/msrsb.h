@@ -377,22 +377,25 @@ msrsb_status msrsb_mpfa_gradient(const msrsb_grid *g, const double *K_hat, const
 
 /* Launch-shape autotuner (no counterpart in the paper; the paper's method is
  * unchanged by it). The restricted-smoothing pass of Eq. 6 / Alg. 1 has
- * several launch shapes that give bit-identical results: 1, 2 or 4 lanes per
- * fine row (32, 16 or 8 rows per warp; a lane gathers W/lanes of P's colour
- * slots), 256 or 128 threads per CTA, 0, 2, 3 or 4 of the row's operator
- * entries loaded ahead of the current entry's gather, and for the latter
- * registers left free or capped at the one-lane kernel's occupancy. Variants
- * 0..7 are (lanes, threads, ahead, capped) = (1,256,0,0) (1,128,0,0)
- * (2,256,0,0) (4,256,0,0) (1,256,2,0) (1,256,2,1) (1,256,3,1) (1,256,4,1). With
- * MSRSB_TUNE_AUTO (the default) the first Alg. 1 loop of a new size class
- * runs its first 16 passes round-robin over the 8 shapes, times each pass with CUDA events on the loop's stream (one
- * host synchronisation) and uses the fastest shape for its remaining passes
- * and for every later loop of the same class in the process. A class is
+ * several launch shapes that give bit-identical results: 1 or 2 lanes per
+ * fine row (32 or 16 rows per warp; a lane gathers W/lanes of P's colour
+ * slots), 256 or 128 threads per CTA, and 0, 2 or 3 of the row's operator
+ * entries loaded ahead of the current entry's gather, with registers left
+ * free or capped at the one-lane kernel's occupancy. Variants 0..5 are
+ * (lanes, threads, ahead, capped) = (1,256,0,0) (1,128,0,0) (2,256,0,0)
+ * (1,256,2,0) (1,256,2,1) (1,256,3,1). With MSRSB_TUNE_AUTO (the default)
+ * the first Alg. 1 loop of a new size class runs each shape in turn for a
+ * warm pass (leaving the caches as that shape leaves them) and two passes
+ * timed together by one pair of CUDA events on the loop's stream, so that the
+ * second overlaps the first's tail as in the loop (a pair never starts on a
+ * check pass: one more warm pass instead); one host synchronisation at the
+ * end; it then uses the shape with the fastest timed pair for its remaining
+ * passes and for every later loop of the same class in the process. A class is
  * (kernel, device, value size, W, ceil(log2 n), ceil(log2 of the operator's
- * stored entries per row)); loops with max_iter < 16 use variant 0 without
+ * stored entries per row)); loops with max_iter < 27 use variant 0 without
  * tuning, and a loop that converges during its trial passes stores nothing.
  * The table is process-wide and guarded for concurrent host threads.
- * msrsb_tune_mode(m): m = MSRSB_TUNE_AUTO, or 0..7 to force that variant for
+ * msrsb_tune_mode(m): m = MSRSB_TUNE_AUTO, or 0..5 to force that variant for
  * every loop (no timing, no table update); EINVAL otherwise.
  * msrsb_tune_reset(): empties the table. msrsb_tune_table(out, cap, count_h):
  * writes min(cap, entries) entries to host array out (nullable when cap = 0)
@@ -412,7 +415,7 @@ typedef struct {
     int32_t ahead;       /* its operator entries loaded ahead */
     int32_t capped;      /* its registers capped for occupancy */
     int32_t n_variants;  /* shapes timed */
-    float us[8];         /* best trial time of each shape, microseconds */
+    float us[8];         /* each shape's timed pair, microseconds per pass */
 } msrsb_tune_entry;
 msrsb_status msrsb_tune_mode(int32_t mode);
 msrsb_status msrsb_tune_reset(void);

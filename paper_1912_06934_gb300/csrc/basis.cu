@@ -147,13 +147,12 @@ __global__ void __launch_bounds__(256) smooth_kernel(int n, const int32_t *__res
 // occupancy, at the price of a few spilled registers. Same sums in the same
 // order: bit for bit smooth_kernel.
 template <typename T, int W, int D, bool CAP>
-__global__ void __launch_bounds__(256, CAP ? (sizeof(T) == 4 ? 8 : 4) : 1) smooth_pf_kernel(int n, const int32_t *__restrict__ slice_ptr,
-                                                        const int32_t *__restrict__ scol, const T *__restrict__ sval,
-                                                        const T *__restrict__ scale, const uint8_t *__restrict__ vmask,
-                                                        const uint8_t *__restrict__ skel, const T *__restrict__ Pin,
-                                                        T *__restrict__ Pout, unsigned long long *__restrict__ emax,
-                                                        int check, const int *__restrict__ done,
-                                                        int *__restrict__ iters, int k_pass) {
+__global__ void __launch_bounds__(256, CAP ? (sizeof(T) == 4 ? 8 : 4) : 1)
+    smooth_pf_kernel(int n, const int32_t *__restrict__ slice_ptr, const int32_t *__restrict__ scol,
+                     const T *__restrict__ sval, const T *__restrict__ scale, const uint8_t *__restrict__ vmask,
+                     const uint8_t *__restrict__ skel, const T *__restrict__ Pin, T *__restrict__ Pout,
+                     unsigned long long *__restrict__ emax, int check, const int *__restrict__ done,
+                     int *__restrict__ iters, int k_pass) {
     static_assert(D >= 1 && D <= 4, "prefetch 1 to 4 entries");
     pdl_prologue();
     if (*done) return;
@@ -395,27 +394,19 @@ static msrsb_status launch_smooth(int variant, int n, const Sell &S, int comp, c
                       Pin, Pout, emax, check, done, iters, k);
             break;
         case 20:
-            MSRSB_PDL((smooth_pf_kernel<T, W, 2, false>), grid, sh.threads, 0, s, n, S.slice_ptr, S.col, val, scale,
-                      vmask, skel, Pin, Pout, emax, check, done, iters, k);
+            MSRSB_PDL((smooth_pf_kernel<T, W, 2, false>), grid, sh.threads, 0, s, n, S.slice_ptr, S.col, val,
+                      scale, vmask, skel, Pin, Pout, emax, check, done, iters, k);
             break;
         case 21:
-            MSRSB_PDL((smooth_pf_kernel<T, W, 2, true>), grid, sh.threads, 0, s, n, S.slice_ptr, S.col, val, scale,
-                      vmask, skel, Pin, Pout, emax, check, done, iters, k);
+            MSRSB_PDL((smooth_pf_kernel<T, W, 2, true>), grid, sh.threads, 0, s, n, S.slice_ptr, S.col, val,
+                      scale, vmask, skel, Pin, Pout, emax, check, done, iters, k);
             break;
         case 23:
-            MSRSB_PDL((smooth_pf_kernel<T, W, 3, true>), grid, sh.threads, 0, s, n, S.slice_ptr, S.col, val, scale,
-                      vmask, skel, Pin, Pout, emax, check, done, iters, k);
-            break;
-        case 25:
-            MSRSB_PDL((smooth_pf_kernel<T, W, 4, true>), grid, sh.threads, 0, s, n, S.slice_ptr, S.col, val, scale,
-                      vmask, skel, Pin, Pout, emax, check, done, iters, k);
+            MSRSB_PDL((smooth_pf_kernel<T, W, 3, true>), grid, sh.threads, 0, s, n, S.slice_ptr, S.col, val,
+                      scale, vmask, skel, Pin, Pout, emax, check, done, iters, k);
             break;
         case 32:
             MSRSB_PDL((smooth_lanes_kernel<T, W, 2>), grid, sh.threads, 0, s, n, S.slice_ptr, S.col, val, scale,
-                      vmask, skel, Pin, Pout, emax, check, done, iters, k);
-            break;
-        case 64:
-            MSRSB_PDL((smooth_lanes_kernel<T, W, 4>), grid, sh.threads, 0, s, n, S.slice_ptr, S.col, val, scale,
                       vmask, skel, Pin, Pout, emax, check, done, iters, k);
             break;
         default:
@@ -453,7 +444,11 @@ msrsb_status basis_loop(int n, int W, const Sell &S, int comp, const T *scale, c
     T *buf[2] = {P, P2};
     // launch shape (see msrsb_tune_mode): forced, cached for this size class,
     // or timed on this loop's first passes
-    constexpr int kTrialPasses = 2 * kSmoothVariants;
+    // each shape runs a warm pass (the caches as that shape leaves them), then
+    // two passes timed together by one event pair, so that the second overlaps
+    // the first's tail as in the loop; a pair never starts on a check pass
+    // (its check kernel would sit inside the pair)
+    constexpr int kTrialPasses = 3 * kSmoothVariants;
     TuneKey key;
     key.kernel = MSRSB_TUNE_SMOOTH;
     MSRSB_CUDA(cudaGetDevice(&key.device));
@@ -467,10 +462,11 @@ msrsb_status basis_loop(int n, int W, const Sell &S, int comp, const T *scale, c
     if (mode >= 0)
         variant = mode;
     else if (!tune_lookup(key, &variant))
-        tuning = maxit >= kTrialPasses && n > 0;
-    cudaEvent_t trial_ev[2 * kTrialPasses] = {};
+        tuning = maxit >= kTrialPasses + kTrialPasses / 2 && n > 0;
+    int t_var = 0, t_phase = 0;  // shape under trial; its pass: 0 warm, 1 and 2 timed
+    cudaEvent_t trial_ev[2 * kSmoothVariants] = {};
     if (tuning)
-        for (int q = 0; q < 2 * kTrialPasses; ++q) MSRSB_CUDA(cudaEventCreate(&trial_ev[q]));
+        for (int q = 0; q < 2 * kSmoothVariants; ++q) MSRSB_CUDA(cudaEventCreate(&trial_ev[q]));
     // optional timing of the smoothing passes (profiling mode): one CUDA event
     // pair around the whole loop on s, so that consecutive passes keep their
     // programmatic overlap; the average pass = loop time / passes that worked
@@ -489,16 +485,16 @@ msrsb_status basis_loop(int n, int W, const Sell &S, int comp, const T *scale, c
             if (((volatile int *)pin)[0] != 0) break;  // converged at an earlier check
             pending = false;
         }
-        const bool trial = tuning && k < kTrialPasses;
-        const int v = trial ? k % kSmoothVariants : variant;
-        if (trial) MSRSB_CUDA(cudaEventRecord(trial_ev[2 * k], s));
+        if (tuning && t_phase == 1 && check && o->n_it > 1) t_phase = 0;  // one more warm pass
+        const int v = tuning ? t_var : variant;
+        if (tuning && t_phase == 1) MSRSB_CUDA(cudaEventRecord(trial_ev[2 * t_var], s));
         if (W == 4)
             MSRSB_TRY((launch_smooth<T, 4>(v, n, S, comp, scale, vmask, skel, buf[k & 1], buf[(k + 1) & 1],
                                            emax + k, check, flags, flags + 1, k, s)));
         else
             MSRSB_TRY((launch_smooth<T, 8>(v, n, S, comp, scale, vmask, skel, buf[k & 1], buf[(k + 1) & 1],
                                            emax + k, check, flags, flags + 1, k, s)));
-        if (trial) MSRSB_CUDA(cudaEventRecord(trial_ev[2 * k + 1], s));
+        if (tuning && t_phase == 2) MSRSB_CUDA(cudaEventRecord(trial_ev[2 * t_var + 1], s));
         launched = k + 1;
         if (check) {
             MSRSB_PDL((basis_check_kernel), 1, 1, 0, s, emax + k, o->tol, flags, e_last);
@@ -509,19 +505,22 @@ msrsb_status basis_loop(int n, int W, const Sell &S, int comp, const T *scale, c
                 pending = true;
             }
         }
-        if (tuning && k == kTrialPasses - 1) {
-            // every shape has run twice: keep each one's faster pass, take the
-            // fastest shape (the lower index on a tie) for the rest of the loop
+        if (tuning && ++t_phase == 3) {
+            t_phase = 0;
+            ++t_var;
+        }
+        if (tuning && t_var == kSmoothVariants) {
+            // every shape has run: take the one with the fastest timed pair (the
+            // lower index on a tie) for the rest of the loop
             int h_done = 0;
             MSRSB_CUDA(cudaMemcpyAsync(&h_done, flags, sizeof(int), cudaMemcpyDeviceToHost, s));
             MSRSB_CUDA(cudaStreamSynchronize(s));
             float us[kSmoothVariants];
             for (int q = 0; q < kSmoothVariants; ++q) us[q] = __builtin_inff();
-            for (int q = 0; q < kTrialPasses; ++q) {
+            for (int q = 0; q < kSmoothVariants; ++q) {
                 float ms = 0.f;
                 MSRSB_CUDA(cudaEventElapsedTime(&ms, trial_ev[2 * q], trial_ev[2 * q + 1]));
-                const int vq = q % kSmoothVariants;
-                if (1e3f * ms < us[vq]) us[vq] = 1e3f * ms;
+                us[q] = 1e3f * ms / 2.f;  // per pass
             }
             int best = 0;
             for (int q = 1; q < kSmoothVariants; ++q)

@@ -115,13 +115,12 @@ struct TuneKey {
     int kernel = 0, device = 0, value_bytes = 0, W = 0, n_log2 = 0, width_log2 = 0;
 };
 struct SmoothShape {
-    int lanes, threads, prefetch, cap;  // lanes per fine row, threads per CTA, operator entries loaded
-                                        // ahead, registers capped for the one-lane kernel's occupancy
+    int lanes, threads;  // lanes per fine row, threads per CTA
+    int prefetch, cap;   // operator entries loaded ahead; registers capped for the one-lane kernel's occupancy
 };
-constexpr int kSmoothVariants = 8;
+constexpr int kSmoothVariants = 6;
 constexpr SmoothShape kSmoothShapes[kSmoothVariants] = {{1, 256, 0, 0}, {1, 128, 0, 0}, {2, 256, 0, 0},
-                                                        {4, 256, 0, 0}, {1, 256, 2, 0}, {1, 256, 2, 1},
-                                                        {1, 256, 3, 1}, {1, 256, 4, 1}};
+                                                        {1, 256, 2, 0}, {1, 256, 2, 1}, {1, 256, 3, 1}};
 int tune_mode();                                   // MSRSB_TUNE_AUTO or a forced variant
 bool tune_lookup(const TuneKey &k, int *variant);  // cached choice, if any
 void tune_store(const TuneKey &k, int variant, int nvar, const float *us);

@@ -335,7 +335,7 @@ class c_tune_entry(ctypes.Structure):
 
 def msrsb_tune_mode(mode):
     """MSRSB_TUNE_AUTO (time the launch shapes of a new size class) or a
-    forced shape index 0..7 (see include/msrsb.h)."""
+    forced shape index 0..5 (see include/msrsb.h)."""
     _check(load().msrsb_tune_mode(ctypes.c_int32(mode)))
 
 

@@ -1,7 +1,7 @@
 """The launch-shape autotuner of the restricted-smoothing pass (Alg. 1).
 
-Every launch shape (1, 2 or 4 lanes per row; 256 or 128 threads per CTA; 0, 2,
-3 or 4 operator entries loaded ahead, registers free or capped) must
+Every launch shape (1 or 2 lanes per row; 256 or 128 threads per CTA; 0, 2 or 3
+operator entries loaded ahead, registers free or capped) must
 give P bit for bit equal to the one-lane shape, in FP64 and FP32, for W = 8
 (3D) and W = 4 (2D), on grids whose row count is not a multiple of a warp or a
 CTA. In automatic mode a new size class is timed once, recorded in the table,
@@ -21,9 +21,8 @@ from synth.darcy import darcy_2d_case, darcy_3d_case  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-N_SHAPES = 8
-SHAPES = [(1, 256, 0, 0), (1, 128, 0, 0), (2, 256, 0, 0), (4, 256, 0, 0), (1, 256, 2, 0), (1, 256, 2, 1),
-          (1, 256, 3, 1), (1, 256, 4, 1)]
+N_SHAPES = 6
+SHAPES = [(1, 256, 0, 0), (1, 128, 0, 0), (2, 256, 0, 0), (1, 256, 2, 0), (1, 256, 2, 1), (1, 256, 3, 1)]
 
 
 @pytest.fixture(scope="module")
@@ -121,9 +120,9 @@ def test_auto_mode_records_a_class_and_keeps_the_result(M):
     _, P2, _, _ = _basis(M, c, 1, 40)
     assert torch.equal(P2, P_ref)
     assert len(M.msrsb_tune_table()) == 1
-    # a loop too short to time every shape twice records nothing
+    # a loop too short to time every shape records nothing
     M.msrsb_tune_reset()
-    _basis(M, c, 1, 2 * N_SHAPES - 1)
+    _basis(M, c, 1, 3 * N_SHAPES + 3 * N_SHAPES // 2 - 1)
     assert M.msrsb_tune_table() == []
 
 
