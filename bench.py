@@ -161,8 +161,11 @@ def kept_entries(c, ids, comp=None):
 # the tuner settles on another shape, the figure no longer describes the
 # kernel that ran and the bench reports null.
 SMOOTH_TRAFFIC = {
-    ("darcy64", 0): ("9c418dcd555f5dd3", 40153600 + 37120),
-    ("darcy128", 5): ("9c418dcd555f5dd3", 317521920 + 51605760),
+    ("darcy64", 0): ("ef9de7061bb3e2aa", 40151808 + 19456),
+    ("darcy64", 4): ("ef9de7061bb3e2aa", 40152832 + 22016),
+    ("darcy64", 5): ("ef9de7061bb3e2aa", 40152576 + 33024),
+    ("darcy128", 4): ("ef9de7061bb3e2aa", 317530368 + 51627264),
+    ("darcy128", 5): ("ef9de7061bb3e2aa", 317522944 + 51881728),
 }
 # the autotuner's shapes (lanes per row, threads, entries loaded ahead,
 # registers capped)
