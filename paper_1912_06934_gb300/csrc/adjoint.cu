@@ -65,8 +65,7 @@ extern "C" msrsb_status msrsb_transpose_values(const msrsb_mat *A, double *val_t
                                                                          A->val, val_t, st);
     MSRSB_LAUNCHED("transpose_values_kernel");
     int h = 0;
-    MSRSB_CUDA(cudaMemcpyAsync(&h, st, sizeof(int), cudaMemcpyDeviceToHost, stream));
-    MSRSB_CUDA(cudaStreamSynchronize(stream));
+    MSRSB_TRY(read_back(&h, st, sizeof(int), stream));
     dfree(st, stream);
     if (h) return fail(MSRSB_ESHAPE, "pattern is not symmetric (row %d has an entry without its mirror)", h - 1);
     return MSRSB_OK;

@@ -310,11 +310,11 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
     std::promise<msrsb_status> tr_done;
     std::future<msrsb_status> tr_status = tr_done.get_future();
     std::string tr_err;
-    // The smoother set-up starts when the basis is built: beside the
-    // FP64-bound Galerkin product and the coarse factorisation on one cluster
-    // it finds idle SMs, while beside the bandwidth-bound smoothing passes it
-    // would slow them. The main thread hands over an event recorded at that
-    // point, or nullptr when it leaves early.
+    // The smoother set-up starts after the basis is built (see below): beside
+    // the FP64-bound Galerkin product and the coarse factorisation on two
+    // clusters it finds idle SMs, while beside the bandwidth-bound smoothing
+    // passes it would slow them. The main thread hands over an event recorded
+    // at that point, or nullptr when it leaves early.
     std::promise<cudaEvent_t> go;
     std::future<cudaEvent_t> go_at = go.get_future();
     cudaEvent_t go_ev = nullptr;
@@ -367,6 +367,12 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
         }
         ~Release() { (*this)(nullptr); }
     } release{go};
+    // the scalar ILU(0) factorisation (a long latency-bound chain) starts when
+    // the basis is built, beside the Galerkin product and the coarse
+    // factorisation; the short set-ups of the other smoothers (bandwidth-bound
+    // copies and block inverses) wait for the Galerkin product, which they
+    // would only slow
+    const bool ilu_chain = h->opts.smoother == MSRSB_SMOOTH_ILU0 || (h->opts.smoother == MSRSB_SMOOTH_IC0 && bd == 1);
     // filtered operator(s) streamed as sliced ELL, then Alg. 1 per component
     T *P = nullptr;
     MSRSB_TRY(dalloc(&P, nW * bd, s));
@@ -402,13 +408,13 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
         if (l == 0 || e > h->basis_e_it) h->basis_e_it = e;
         sell_free(&S, s);
     }
-    MSRSB_CUDA(cudaMemcpyAsync(&h->n_zero_diag, nzd, sizeof(int), cudaMemcpyDeviceToHost, s));
     dfree(scale, s);
     dfree(vmask, s);
-    dfree(nzd, s);
     MSRSB_TRY(mark(2));
-    MSRSB_CUDA(cudaEventRecord(go_ev, s));
-    release(go_ev);
+    if (ilu_chain) {
+        MSRSB_CUDA(cudaEventRecord(go_ev, s));
+        release(go_ev);
+    }
     // Galerkin coarse operator with the unfiltered A, and its inverse
     {
         const msrsb_status st = tr_status.get();
@@ -434,6 +440,10 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
         if (Pl != P) dfree(Pl, s);
     }
     MSRSB_TRY(mark(3));
+    if (!ilu_chain) {
+        MSRSB_CUDA(cudaEventRecord(go_ev, s));
+        release(go_ev);
+    }
     if (planes_fit(h->grid.dim, h->nb, bd)) {
         MSRSB_TRY(plane_factor(h->grid.dim, h->nb, bd, h->Acs, &h->planes, s));
         if (h->nC <= kDenseCoarseMax) {
@@ -477,7 +487,8 @@ static msrsb_status setup_t(msrsb_handle *h, const void *p_init, cudaStream_t s)
     cudaEventDestroy(tr_ev);
     cudaEventDestroy(go_ev);
     MSRSB_TRY(mark(6));
-    MSRSB_CUDA(cudaStreamSynchronize(s));
+    MSRSB_TRY(read_back(&h->n_zero_diag, nzd, sizeof(int), s));  // read once everything has run
+    dfree(nzd, s);
     if (prof) {
         for (int q = 0; q < 6; ++q) {
             float t = 0.f;

@@ -341,6 +341,8 @@ __global__ void __launch_bounds__(256) smooth_lanes_kernel(int n, const int32_t 
     }
 }
 
+__global__ void set_value_kernel(double *__restrict__ p, double v) { *p = v; }
+
 __global__ void basis_check_kernel(const unsigned long long *__restrict__ emax_k, double tol, int *__restrict__ done,
                                    double *__restrict__ e_last) {
     pdl_prologue();
@@ -379,6 +381,58 @@ double *pinned_scratch() {
         }
     }
     return p;
+}
+
+// Device-to-host read of a few bytes that the host needs before it goes on:
+// staged through a pinned buffer of this host thread, then the stream is
+// synchronised. A copy straight into pageable memory blocks inside the copy
+// call until the stream reaches it, and while it waits, launches from the
+// library's other host threads (the smoother set-up's thread, concurrent
+// ensemble members) stall behind it.
+msrsb_status read_back(void *dst, const void *src, size_t bytes, cudaStream_t s) {
+    constexpr size_t kCap = 4096;
+    static thread_local unsigned char *buf = nullptr;
+    if (!buf && bytes <= kCap && cudaHostAlloc((void **)&buf, kCap, cudaHostAllocPortable) != cudaSuccess) {
+        cudaGetLastError();
+        buf = nullptr;
+    }
+    if (buf && bytes <= kCap) {
+        MSRSB_CUDA(cudaMemcpyAsync(buf, src, bytes, cudaMemcpyDeviceToHost, s));
+        MSRSB_CUDA(cudaStreamSynchronize(s));
+        memcpy(dst, buf, bytes);
+        return MSRSB_OK;
+    }
+    MSRSB_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s));
+    MSRSB_CUDA(cudaStreamSynchronize(s));
+    return MSRSB_OK;
+}
+
+// Host-to-device copy of a host-built table through a pinned buffer of this
+// host thread (grown on demand), for the same reason; the stream is
+// synchronised before the buffer can be reused.
+msrsb_status upload(void *dst, const void *src, size_t bytes, cudaStream_t s) {
+    static thread_local unsigned char *buf = nullptr;
+    static thread_local size_t cap = 0;
+    if (bytes > cap) {
+        if (buf) cudaFreeHost(buf);
+        buf = nullptr;
+        cap = 0;
+        if (cudaHostAlloc((void **)&buf, bytes, cudaHostAllocPortable) != cudaSuccess) {
+            cudaGetLastError();
+            buf = nullptr;
+        } else {
+            cap = bytes;
+        }
+    }
+    if (!buf) {
+        MSRSB_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s));
+        MSRSB_CUDA(cudaStreamSynchronize(s));
+        return MSRSB_OK;
+    }
+    memcpy(buf, src, bytes);
+    MSRSB_CUDA(cudaMemcpyAsync(dst, buf, bytes, cudaMemcpyHostToDevice, s));
+    MSRSB_CUDA(cudaStreamSynchronize(s));
+    return MSRSB_OK;
 }
 
 template <typename T, int W>
@@ -434,8 +488,10 @@ msrsb_status basis_loop(int n, int W, const Sell &S, int comp, const T *scale, c
     MSRSB_TRY(dalloc(&e_last, 1, s));
     MSRSB_CUDA(cudaMemsetAsync(emax, 0, (maxit + 1) * sizeof(unsigned long long), s));
     MSRSB_CUDA(cudaMemsetAsync(flags, 0, 2 * sizeof(int), s));
-    double inf = __builtin_inf();
-    MSRSB_CUDA(cudaMemcpyAsync(e_last, &inf, sizeof(double), cudaMemcpyHostToDevice, s));
+    // e_last = +inf (no check yet), set on the device: a copy from pageable
+    // host memory would wait for the stream inside the call
+    set_value_kernel<<<1, 1, 0, s>>>(e_last, __builtin_inf());
+    MSRSB_LAUNCHED("set_value_kernel");
     double *pin = pinned_scratch();
     if (pin) ((volatile int *)pin)[0] = 0;
     cudaEvent_t ev = nullptr;
@@ -513,8 +569,7 @@ msrsb_status basis_loop(int n, int W, const Sell &S, int comp, const T *scale, c
             // every shape has run: take the one with the fastest timed pair (the
             // lower index on a tie) for the rest of the loop
             int h_done = 0;
-            MSRSB_CUDA(cudaMemcpyAsync(&h_done, flags, sizeof(int), cudaMemcpyDeviceToHost, s));
-            MSRSB_CUDA(cudaStreamSynchronize(s));
+            MSRSB_TRY(read_back(&h_done, flags, sizeof(int), s));
             float us[kSmoothVariants];
             for (int q = 0; q < kSmoothVariants; ++q) us[q] = __builtin_inff();
             for (int q = 0; q < kSmoothVariants; ++q) {
@@ -535,9 +590,8 @@ msrsb_status basis_loop(int n, int W, const Sell &S, int comp, const T *scale, c
     if (prof) MSRSB_CUDA(cudaEventRecord(tev[1], s));
     int h_flags[2] = {0, 0};
     double h_e = 0.0;
-    MSRSB_CUDA(cudaMemcpyAsync(h_flags, flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
-    MSRSB_CUDA(cudaMemcpyAsync(&h_e, e_last, sizeof(double), cudaMemcpyDeviceToHost, s));
-    MSRSB_CUDA(cudaStreamSynchronize(s));
+    MSRSB_TRY(read_back(h_flags, flags, 2 * sizeof(int), s));
+    MSRSB_TRY(read_back(&h_e, e_last, sizeof(double), s));
     cudaEventDestroy(ev);
     for (cudaEvent_t &e : trial_ev)
         if (e) cudaEventDestroy(e);

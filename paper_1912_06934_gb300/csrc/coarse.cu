@@ -510,8 +510,7 @@ msrsb_status coarse_inverse_finish(CoarseInverseWork *w, cudaStream_t s) {
         MSRSB_CUDA(cudaStreamSynchronize(s));
         w->h_status = *(volatile int *)w->pin_status;
     } else {
-        MSRSB_CUDA(cudaMemcpyAsync(&w->h_status, w->status, sizeof(int), cudaMemcpyDeviceToHost, s));
-        MSRSB_CUDA(cudaStreamSynchronize(s));
+        MSRSB_TRY(read_back(&w->h_status, w->status, sizeof(int), s));
     }
     dfree(w->X, s);
     dfree(w->Xres, s);
@@ -584,8 +583,7 @@ msrsb_status wait_selftest(double limit_ms, cudaStream_t s) {
     wait_selftest_kernel<<<1, 32, 0, s>>>(d, d + 1, (unsigned long long)(limit_ms * 1e6));
     MSRSB_LAUNCHED("wait_selftest_kernel");
     int h[2] = {0, 0};
-    MSRSB_CUDA(cudaMemcpyAsync(h, d, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
-    MSRSB_CUDA(cudaStreamSynchronize(s));
+    MSRSB_TRY(read_back(h, d, 2 * sizeof(int), s));
     dfree(d, s);
     if (h[1] == kGjTimeout && h[0] == -1) return fail(MSRSB_ETIMEOUT, "bounded wait expired as expected");
     return fail(MSRSB_EINVAL, "bounded wait self-test: status %d, counter %d", h[1], h[0]);

@@ -644,8 +644,7 @@ msrsb_status plane_factor(int dim, const int nb[3], int bd, const double *Acs, C
         MSRSB_CUDA(cudaLaunchKernelEx(&cfg, plane_factor_kernel, G, h, 1, Acs, cp->X, cp->G, cp->pi, status));
     }
     int bad = 0;
-    MSRSB_CUDA(cudaMemcpyAsync(&bad, status, sizeof(int), cudaMemcpyDeviceToHost, s));
-    MSRSB_CUDA(cudaStreamSynchronize(s));
+    MSRSB_TRY(read_back(&bad, status, sizeof(int), s));
     dfree(status, s);
     if (bad) return fail(MSRSB_EBREAKDOWN, "coarse operator is singular (zero pivot at coarse row %d)", bad - 1);
     return MSRSB_OK;

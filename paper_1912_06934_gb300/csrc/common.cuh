@@ -103,6 +103,12 @@ inline cudaError_t pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
         if (s_ != MSRSB_OK) return s_;        \
     } while (0)
 
+// bytes (<= 4 KiB staged through pinned memory) from device to host, then
+// the stream synchronised (basis.cu)
+msrsb_status read_back(void *dst, const void *src, size_t bytes, cudaStream_t s);
+// host-built bytes to the device through pinned memory, stream synchronised
+msrsb_status upload(void *dst, const void *src, size_t bytes, cudaStream_t s);
+
 // profiling of the restricted-smoothing kernel (see msrsb_profile)
 bool profiling();
 void add_smooth_time(int launches, double ms);

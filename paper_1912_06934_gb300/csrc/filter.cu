@@ -171,8 +171,7 @@ msrsb_status sell_structure(int n, const int32_t *rowptr, Sell *S, cudaStream_t 
     MSRSB_TRY(dalloc((char **)&tbuf, tmp, s));
     MSRSB_CUDA(cub::DeviceScan::ExclusiveSum(tbuf, tmp, sizes, S->slice_ptr, S->nslices + 1, s));
     int32_t total = 0;
-    MSRSB_CUDA(cudaMemcpyAsync(&total, S->slice_ptr + S->nslices, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    MSRSB_CUDA(cudaStreamSynchronize(s));
+    MSRSB_TRY(read_back(&total, S->slice_ptr + S->nslices, sizeof(int32_t), s));
     S->entries = total;
     dfree(tbuf, s);
     dfree(sizes, s);
@@ -265,8 +264,7 @@ extern "C" msrsb_status msrsb_filter(const msrsb_mat *A, int32_t comp, double *a
     MSRSB_LAUNCHED("filter_kernel");
     if (n_zero_diag_h) {
         int h = 0;
-        MSRSB_CUDA(cudaMemcpyAsync(&h, nz, sizeof(int), cudaMemcpyDeviceToHost, stream));
-        MSRSB_CUDA(cudaStreamSynchronize(stream));
+        MSRSB_TRY(read_back(&h, nz, sizeof(int), stream));
         *n_zero_diag_h = h;
         dfree(nz, stream);
     }

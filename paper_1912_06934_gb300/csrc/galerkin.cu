@@ -64,8 +64,7 @@ msrsb_status build_transpose(int n, int W, int nc, const int32_t *p_ids, int32_t
     MSRSB_CUDA(cub::DeviceRadixSort::SortPairs(tmp, tmp1, keys, keys2, vals, vals2, nW, 0, 32, s));
     MSRSB_CUDA(cub::DeviceScan::ExclusiveSum(tmp, tmp2, count, *pt_ptr, nc + 1, s));
     int32_t nnzp = 0;
-    MSRSB_CUDA(cudaMemcpyAsync(&nnzp, *pt_ptr + nc, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    MSRSB_CUDA(cudaStreamSynchronize(s));
+    MSRSB_TRY(read_back(&nnzp, *pt_ptr + nc, sizeof(int32_t), s));
     MSRSB_TRY(dalloc(pt_rows, nnzp, s));
     if (nnzp_out) *nnzp_out = nnzp;
     MSRSB_CUDA(cudaMemcpyAsync(*pt_rows, vals2, (size_t)nnzp * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));

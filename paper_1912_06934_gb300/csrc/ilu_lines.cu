@@ -751,8 +751,8 @@ msrsb_status lines_setup(msrsb_handle *h, TF *lu, cudaStream_t s) {
     const int nblk = (int)bstart.size();
     MSRSB_TRY(dalloc(&L.blk_start, nblk, s));
     MSRSB_TRY(dalloc(&L.blk_nsub, nblk, s));
-    MSRSB_CUDA(cudaMemcpyAsync(L.blk_start, bstart.data(), nblk * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-    MSRSB_CUDA(cudaMemcpyAsync(L.blk_nsub, bnsub.data(), nblk * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    MSRSB_TRY(upload(L.blk_start, bstart.data(), nblk * sizeof(int32_t), s));
+    MSRSB_TRY(upload(L.blk_nsub, bnsub.data(), nblk * sizeof(int32_t), s));
     // ---- factorisation, colour by colour ----
     int *status = nullptr;
     TF *rdiag = nullptr;
@@ -778,8 +778,7 @@ msrsb_status lines_setup(msrsb_handle *h, TF *lu, cudaStream_t s) {
         MSRSB_LAUNCHED("lines_factor_ring_kernel");
     }
     int hs = 0;
-    MSRSB_CUDA(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, s));
-    MSRSB_CUDA(cudaStreamSynchronize(s));
+    MSRSB_TRY(read_back(&hs, status, sizeof(int), s));
     dfree(rdiag, s);
     dfree(rmask, s);
     if (hs) {
@@ -798,8 +797,7 @@ msrsb_status lines_setup(msrsb_handle *h, TF *lu, cudaStream_t s) {
     lines_width_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, nx, ny, A.rowptr, A.colidx, h->pos_of, ccol, w);
     MSRSB_LAUNCHED("lines_width_kernel");
     int hw[16];
-    MSRSB_CUDA(cudaMemcpyAsync(hw, w, 16 * sizeof(int), cudaMemcpyDeviceToHost, s));
-    MSRSB_CUDA(cudaStreamSynchronize(s));
+    MSRSB_TRY(read_back(hw, w, 16 * sizeof(int), s));
     dfree(w, s);
     long lt = 0, ut = 0, lit = 0, uit = 0;
     for (int c = 0; c < L.ncol; ++c) {

@@ -43,8 +43,7 @@ msrsb_status stencil_check(const msrsb_mat *A, const msrsb_grid *g, cudaStream_t
     MSRSB_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), s));
     stencil_check_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, g->dim, g->nx, g->ny, A->rowptr, A->colidx, flag);
     MSRSB_LAUNCHED("stencil_check_kernel");
-    MSRSB_CUDA(cudaMemcpyAsync(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
-    MSRSB_CUDA(cudaStreamSynchronize(s));
+    MSRSB_TRY(read_back(&hf, flag, sizeof(int), s));
     dfree(flag, s);
     if (hf & 1) return fail(MSRSB_EINVAL, "the smoother needs A's pattern within each point's 3^%d neighbourhood", g->dim);
     if (hf & 2) return fail(MSRSB_EINVAL, "the smoother needs rows of at most 32 (block) entries");
@@ -90,8 +89,7 @@ msrsb_status colour_classes(int n, const uint8_t *colour, int ncol, int32_t **ro
     MSRSB_TRY(dalloc(&tb, tmp, s));
     MSRSB_CUDA(cub::DeviceRadixSort::SortPairs(tb, tmp, colour, keys2, idx, *rows, n, 0, 8, s));
     int32_t cnt[16];
-    MSRSB_CUDA(cudaMemcpyAsync(cnt, count, 16 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    MSRSB_CUDA(cudaStreamSynchronize(s));
+    MSRSB_TRY(read_back(cnt, count, 16 * sizeof(int32_t), s));
     ptr_h[0] = 0;
     for (int c = 0; c < ncol; ++c) ptr_h[c + 1] = ptr_h[c] + cnt[c];
     dfree(tb, s);
@@ -264,8 +262,7 @@ msrsb_status ilu0_factor(const msrsb_mat *A, const uint8_t *colour, int ncol, co
     MSRSB_LAUNCHED("diag_pos_kernel");
     {
         int h0 = 0;
-        MSRSB_CUDA(cudaMemcpyAsync(&h0, status, sizeof(int), cudaMemcpyDeviceToHost, s));
-        MSRSB_CUDA(cudaStreamSynchronize(s));
+        MSRSB_TRY(read_back(&h0, status, sizeof(int), s));
         if (h0) {
             dfree(status, s);
             dfree(rdiag, s);
@@ -280,8 +277,7 @@ msrsb_status ilu0_factor(const msrsb_mat *A, const uint8_t *colour, int ncol, co
         MSRSB_LAUNCHED("ilu0_colour_kernel");
     }
     int h = 0;
-    MSRSB_CUDA(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s));
-    MSRSB_CUDA(cudaStreamSynchronize(s));
+    MSRSB_TRY(read_back(&h, status, sizeof(int), s));
     dfree(status, s);
     dfree(rdiag, s);
     if (h < 0) return fail(MSRSB_EINVAL, "ILU(0): row %d has more than 32 entries", -h - 1);
@@ -506,8 +502,7 @@ msrsb_status ilu_build_ell(msrsb_handle *h, const T *lu, cudaStream_t s) {
     ilu_width_kernel<<<ceil_div(n, 1024), 1024, 0, s>>>(n, A.rowptr, A.colidx, h->colour, w, w + 16);
     MSRSB_LAUNCHED("ilu_width_kernel");
     int hw[32];
-    MSRSB_CUDA(cudaMemcpyAsync(hw, w, 32 * sizeof(int), cudaMemcpyDeviceToHost, s));
-    MSRSB_CUDA(cudaStreamSynchronize(s));
+    MSRSB_TRY(read_back(hw, w, 32 * sizeof(int), s));
     dfree(w, s);
     long lt = 0, ut = 0;
     for (int c = 0; c < ncol; ++c) {
@@ -609,8 +604,7 @@ msrsb_status block_diag_inverse(const msrsb_mat *A, T *dinv, cudaStream_t s) {
                                                                      status);
     MSRSB_LAUNCHED("block_diag_inv_kernel");
     int h = 0;
-    MSRSB_CUDA(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s));
-    MSRSB_CUDA(cudaStreamSynchronize(s));
+    MSRSB_TRY(read_back(&h, status, sizeof(int), s));
     dfree(status, s);
     if (h) return fail(MSRSB_EBREAKDOWN, "singular or missing 3x3 diagonal block at node %d", h - 1);
     return MSRSB_OK;
@@ -801,8 +795,7 @@ msrsb_status bic0_factor(const msrsb_handle *h, T *lu, T *uinv, cudaStream_t s) 
         MSRSB_LAUNCHED("bic0_factor_kernel");
     }
     int hs = 0;
-    MSRSB_CUDA(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, s));
-    MSRSB_CUDA(cudaStreamSynchronize(s));
+    MSRSB_TRY(read_back(&hs, status, sizeof(int), s));
     dfree(status, s);
     if (hs) return fail(MSRSB_EBREAKDOWN, "IC(0): singular pivot block at node %d", hs - 1);
     return MSRSB_OK;
