@@ -161,11 +161,11 @@ def kept_entries(c, ids, comp=None):
 # the tuner settles on another shape, the figure no longer describes the
 # kernel that ran and the bench reports null.
 SMOOTH_TRAFFIC = {
-    ("darcy64", 0): ("ef9de7061bb3e2aa", 40151808 + 19456),
-    ("darcy64", 4): ("ef9de7061bb3e2aa", 40152832 + 22016),
-    ("darcy64", 5): ("ef9de7061bb3e2aa", 40152576 + 33024),
-    ("darcy128", 4): ("ef9de7061bb3e2aa", 317530368 + 51627264),
-    ("darcy128", 5): ("ef9de7061bb3e2aa", 317522944 + 51881728),
+    ("darcy64", 0): ("72778b6d91348552", 40152320 + 25344),
+    ("darcy64", 4): ("72778b6d91348552", 40152576 + 28416),
+    ("darcy64", 5): ("72778b6d91348552", 40152832 + 32512),
+    ("darcy128", 4): ("72778b6d91348552", 317567232 + 52011520),
+    ("darcy128", 5): ("72778b6d91348552", 317523968 + 52135424),
 }
 # the autotuner's shapes (lanes per row, threads, entries loaded ahead,
 # registers capped)
