@@ -161,11 +161,11 @@ def kept_entries(c, ids, comp=None):
 # the tuner settles on another shape, the figure no longer describes the
 # kernel that ran and the bench reports null.
 SMOOTH_TRAFFIC = {
-    ("darcy64", 0): ("72778b6d91348552", 40152320 + 25344),
-    ("darcy64", 4): ("72778b6d91348552", 40152576 + 28416),
-    ("darcy64", 5): ("72778b6d91348552", 40152832 + 32512),
-    ("darcy128", 4): ("72778b6d91348552", 317567232 + 52011520),
-    ("darcy128", 5): ("72778b6d91348552", 317523968 + 52135424),
+    ("darcy64", 0): ("de0b0da3234c1a41", 40152320 + 13824),
+    ("darcy64", 4): ("de0b0da3234c1a41", 40152576 + 40704),
+    ("darcy64", 5): ("de0b0da3234c1a41", 40155136 + 39424),
+    ("darcy128", 4): ("de0b0da3234c1a41", 317593600 + 52034560),
+    ("darcy128", 5): ("de0b0da3234c1a41", 317522688 + 51706624),
 }
 # the autotuner's shapes (lanes per row, threads, entries loaded ahead,
 # registers capped)

@@ -371,70 +371,6 @@ msrsb_status indicator(int n, int W, const int32_t *part, const int32_t *p_ids, 
 template msrsb_status indicator<double>(int, int, const int32_t *, const int32_t *, double *, cudaStream_t);
 template msrsb_status indicator<float>(int, int, const int32_t *, const int32_t *, float *, cudaStream_t);
 
-// Small pinned scratch for host reads of device scalars (per host thread).
-double *pinned_scratch() {
-    static thread_local double *p = nullptr;
-    if (!p) {
-        if (cudaHostAlloc((void **)&p, 8192 * sizeof(double), cudaHostAllocPortable) != cudaSuccess) {
-            cudaGetLastError();
-            p = nullptr;
-        }
-    }
-    return p;
-}
-
-// Device-to-host read of a few bytes that the host needs before it goes on:
-// staged through a pinned buffer of this host thread, then the stream is
-// synchronised. A copy straight into pageable memory blocks inside the copy
-// call until the stream reaches it, and while it waits, launches from the
-// library's other host threads (the smoother set-up's thread, concurrent
-// ensemble members) stall behind it.
-msrsb_status read_back(void *dst, const void *src, size_t bytes, cudaStream_t s) {
-    constexpr size_t kCap = 4096;
-    static thread_local unsigned char *buf = nullptr;
-    if (!buf && bytes <= kCap && cudaHostAlloc((void **)&buf, kCap, cudaHostAllocPortable) != cudaSuccess) {
-        cudaGetLastError();
-        buf = nullptr;
-    }
-    if (buf && bytes <= kCap) {
-        MSRSB_CUDA(cudaMemcpyAsync(buf, src, bytes, cudaMemcpyDeviceToHost, s));
-        MSRSB_CUDA(cudaStreamSynchronize(s));
-        memcpy(dst, buf, bytes);
-        return MSRSB_OK;
-    }
-    MSRSB_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s));
-    MSRSB_CUDA(cudaStreamSynchronize(s));
-    return MSRSB_OK;
-}
-
-// Host-to-device copy of a host-built table through a pinned buffer of this
-// host thread (grown on demand), for the same reason; the stream is
-// synchronised before the buffer can be reused.
-msrsb_status upload(void *dst, const void *src, size_t bytes, cudaStream_t s) {
-    static thread_local unsigned char *buf = nullptr;
-    static thread_local size_t cap = 0;
-    if (bytes > cap) {
-        if (buf) cudaFreeHost(buf);
-        buf = nullptr;
-        cap = 0;
-        if (cudaHostAlloc((void **)&buf, bytes, cudaHostAllocPortable) != cudaSuccess) {
-            cudaGetLastError();
-            buf = nullptr;
-        } else {
-            cap = bytes;
-        }
-    }
-    if (!buf) {
-        MSRSB_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s));
-        MSRSB_CUDA(cudaStreamSynchronize(s));
-        return MSRSB_OK;
-    }
-    memcpy(buf, src, bytes);
-    MSRSB_CUDA(cudaMemcpyAsync(dst, buf, bytes, cudaMemcpyHostToDevice, s));
-    MSRSB_CUDA(cudaStreamSynchronize(s));
-    return MSRSB_OK;
-}
-
 template <typename T, int W>
 static msrsb_status launch_smooth(int variant, int n, const Sell &S, int comp, const T *scale, const uint8_t *vmask,
                                   const uint8_t *skel, const T *Pin, T *Pout, unsigned long long *emax, int check,

@@ -103,8 +103,11 @@ inline cudaError_t pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
         if (s_ != MSRSB_OK) return s_;        \
     } while (0)
 
-// bytes (<= 4 KiB staged through pinned memory) from device to host, then
-// the stream synchronised (basis.cu)
+// per-host-thread pinned scratch of 8192 doubles for lagged reads of device
+// scalars (host_io.cu)
+double *pinned_scratch();
+// bytes from device to host through pinned staging, then the stream
+// synchronised (host_io.cu)
 msrsb_status read_back(void *dst, const void *src, size_t bytes, cudaStream_t s);
 // host-built bytes to the device through pinned memory, stream synchronised
 msrsb_status upload(void *dst, const void *src, size_t bytes, cudaStream_t s);
