@@ -7,16 +7,40 @@
 
 namespace msrsb {
 
-// Small pinned scratch for host reads of device scalars (per host thread).
+// Small pinned scratch for lagged host reads of device scalars, one per host
+// thread while it lives: a thread's scratch goes back to a process-wide free
+// list when the thread ends (pool threads of the ensemble, for instance), so
+// new threads reuse it instead of allocating pinned memory again.
+namespace {
+std::mutex g_scratch_mu;
+std::vector<double *> g_scratch_free;
+
+struct ScratchHolder {
+    double *p = nullptr;
+    ~ScratchHolder() {
+        if (!p) return;
+        std::lock_guard<std::mutex> lock(g_scratch_mu);
+        g_scratch_free.push_back(p);
+    }
+};
+}  // namespace
+
 double *pinned_scratch() {
-    static thread_local double *p = nullptr;
-    if (!p) {
-        if (cudaHostAlloc((void **)&p, 8192 * sizeof(double), cudaHostAllocPortable) != cudaSuccess) {
+    static thread_local ScratchHolder h;
+    if (!h.p) {
+        {
+            std::lock_guard<std::mutex> lock(g_scratch_mu);
+            if (!g_scratch_free.empty()) {
+                h.p = g_scratch_free.back();
+                g_scratch_free.pop_back();
+            }
+        }
+        if (!h.p && cudaHostAlloc((void **)&h.p, 8192 * sizeof(double), cudaHostAllocPortable) != cudaSuccess) {
             cudaGetLastError();
-            p = nullptr;
+            h.p = nullptr;
         }
     }
-    return p;
+    return h.p;
 }
 
 // Pinned staging buffers shared by every host thread of the process: a
