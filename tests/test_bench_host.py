@@ -96,3 +96,41 @@ def test_max_over_ranks_with_two_gloo_ranks():
             p.join(timeout=120)
             assert p.exitcode == 0
         assert out[0] == [2.0, 10.0] and out[1] == [2.0, 10.0]
+
+
+class _FakeTuneLib:
+    """Stands in for the binding's msrsb_tune_table (no GPU)."""
+
+    def __init__(self, rows):
+        self.rows = rows
+
+    def msrsb_tune_table(self):
+        return self.rows
+
+
+def _tune_row(variant, n_log2, value_bytes=4, W=8):
+    lanes, threads, ahead, capped = bench.SMOOTH_SHAPES[variant]
+    return {"kernel": 0, "device": 0, "value_bytes": value_bytes, "W": W, "n_log2": n_log2, "width_log2": 4,
+            "variant": variant, "lanes": lanes, "threads": threads, "ahead": ahead, "capped": capped,
+            "n_variants": len(bench.SMOOTH_SHAPES), "us": [1.0] * len(bench.SMOOTH_SHAPES)}
+
+
+def test_smooth_shape_names_the_tuned_kernel():
+    M = _FakeTuneLib([_tune_row(4, 18), _tune_row(5, 21), _tune_row(2, 17, value_bytes=8)])
+    s64 = bench.smooth_shape(M, 64 ** 3, 8, 4)
+    assert s64["variant"] == 4 and s64["kernel"] == "smooth_pf_kernel<float,8,2,true>"
+    assert (s64["lanes_per_row"], s64["threads"], s64["entries_ahead"], s64["registers_capped"]) == (1, 256, 2, True)
+    assert bench.smooth_shape(M, 128 ** 3, 8, 4)["kernel"] == "smooth_pf_kernel<float,8,3,true>"
+    assert bench.smooth_shape(M, 117649, 8, 8)["kernel"] == "smooth_lanes_kernel<double,8,2>"
+    assert bench.smooth_shape(M, 32 ** 3, 8, 4) is None  # size class never tuned
+    assert bench.smooth_shape(_FakeTuneLib([_tune_row(0, 18)]), 64 ** 3, 8, 4)["kernel"] == "smooth_kernel<float,8>"
+
+
+def test_smooth_traffic_is_reported_only_for_the_captured_source_and_shape(monkeypatch):
+    h = bench.source_hash("basis.cu")
+    table = {("darcy64", 4): (h, 123), ("darcy128", 5): ("0" * 16, 456)}
+    monkeypatch.setattr(bench, "SMOOTH_TRAFFIC", table)
+    assert bench.smooth_traffic("darcy64", 4) == 123      # captured on this source, this shape
+    assert bench.smooth_traffic("darcy64", 0) is None     # another shape
+    assert bench.smooth_traffic("darcy128", 5) is None    # captured on another source
+    assert bench.smooth_traffic("elastic48", 0) is None   # never captured
