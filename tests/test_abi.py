@@ -38,6 +38,35 @@ def test_partition_size_host_only():
     assert B.msrsb_partition_size(B.grid((64, 64), (8, 8))) == (4096, 64, 4)
 
 
+def test_tune_calls_are_host_only():
+    # the autotuner's mode and table are host bookkeeping: callable without a GPU
+    from paper_1912_06934_gb300 import msrsb as B
+    # the binding's struct mirrors the header's field for field
+    hdr = open(os.path.join(ROOT, "include", "msrsb.h")).read()
+    body = re.search(r"typedef struct \{([^}]*)\} msrsb_tune_entry;", hdr).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"(int32_t|float)\s+(\w+)(\[\d+\])?;", body)
+    assert [f[1] for f in fields] == [f[0] for f in B.c_tune_entry._fields_]
+    assert ctypes.sizeof(B.c_tune_entry) == sum(4 * (int(f[2][1:-1]) if f[2] else 1) for f in fields)
+    B.msrsb_tune_reset()
+    assert B.msrsb_tune_table() == []
+    for mode in (B.MSRSB_TUNE_AUTO, 0, 5):
+        B.msrsb_tune_mode(mode)
+    for bad in (-2, 6, 1000):
+        try:
+            B.msrsb_tune_mode(bad)
+        except B.MsrsbError as e:
+            assert e.status == 1  # MSRSB_EINVAL
+        else:
+            raise AssertionError("mode %d accepted" % bad)
+    B.msrsb_tune_mode(B.MSRSB_TUNE_AUTO)
+    lib = B.load()
+    cnt = ctypes.c_int32(-1)
+    assert lib.msrsb_tune_table(None, ctypes.c_int32(-1), ctypes.byref(cnt)) == 1  # negative capacity
+    assert lib.msrsb_tune_table(None, ctypes.c_int32(4), ctypes.byref(cnt)) == 1   # no array for 4 entries
+    assert lib.msrsb_tune_table(None, ctypes.c_int32(0), ctypes.byref(cnt)) == 0 and cnt.value == 0
+
+
 def test_product_path_has_no_oracle_import():
     pkg = os.path.join(ROOT, "paper_1912_06934_gb300")
     for dp, _, files in os.walk(pkg):
