@@ -686,14 +686,22 @@ def oracle_step(c, vprobe=None):
     return out, res
 
 
-def _oracle_subprocess(threads):
+# workloads the oracle can be timed on: the 2D 64^2 case (MPFA-O 9-point,
+# seed 1001) and the 64^3 benchmark workload
+ORACLE_WORKLOADS = {
+    "darcy2d64": lambda: __import__("synth.darcy", fromlist=["darcy_2d_case"]).darcy_2d_case(n=64, H=8, seed=1001),
+    "darcy64": lambda: make_problem(),
+}
+
+
+def _oracle_subprocess(threads, workload="darcy64"):
     """The oracle step in a fresh process whose BLAS pools use `threads`
     threads (their size is fixed when numpy loads)."""
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[v] = str(threads)
-    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--oracle-step"], env=env,
-                       capture_output=True, text=True, timeout=1200)
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--oracle-step",
+                        "--oracle-workload", workload], env=env, capture_output=True, text=True, timeout=1200)
     if r.returncode != 0:
         return {"error": r.stderr[-500:]}
     return json.loads(r.stdout.strip().splitlines()[-1])
@@ -900,6 +908,29 @@ def ensemble_run(args):
     print(json.dumps(line))
 
 
+def oracle_timing_run(args):
+    """The oracle's own timing (no GPU): for each workload of
+    --oracle-workloads and for one thread and every host core,
+    --oracle-repeats full runs, each in a fresh process; the best time of each
+    phase. Prints one JSON line."""
+    cores = os.cpu_count() or 1
+    out = {"metric": "FP64 oracle: MsRSB set-up + GMRES solve to 1e-8, seconds (best of %d per phase)"
+                     % args.oracle_repeats, "unit": "s", "cores": cores, "workloads": {}}
+    for wl in args.oracle_workloads.split(","):
+        per = {}
+        for threads in sorted({1, cores}):
+            runs = [_oracle_subprocess(threads, wl) for _ in range(args.oracle_repeats)]
+            ok = [r for r in runs if "error" not in r]
+            if not ok:
+                per[str(threads)] = {"error": runs[-1].get("error")}
+                continue
+            per[str(threads)] = {"setup_s": min(r["setup_s"] for r in ok), "solve_s": min(r["solve_s"] for r in ok),
+                                 "runs": len(ok), "basis_iters": ok[0]["basis_iters"],
+                                 "krylov_iters": ok[0]["krylov_iters"], "relres": ok[0]["relres"]}
+        out["workloads"][wl] = per
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -909,6 +940,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-configs", action="store_true", help="time only the 64^3 workload")
     ap.add_argument("--oracle-step", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-workload", default="darcy64", choices=sorted(ORACLE_WORKLOADS), help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-timing", action="store_true",
+                    help="time the FP64 oracle alone: best of --oracle-repeats full set-up + solve runs per phase, "
+                         "one thread and every host core, on the 2D 64^2 and 3D 64^3 workloads")
+    ap.add_argument("--oracle-repeats", type=int, default=3)
+    ap.add_argument("--oracle-workloads", default="darcy2d64,darcy64")
     ap.add_argument("--profile", choices=["solve", "basis"], default=None,
                     help="run a workload for a profiler instead of the benchmark")
     ap.add_argument("--grid", type=int, default=N_GRID, help="grid edge for --profile")
@@ -920,7 +957,10 @@ def main():
     ap.add_argument("--ens-conc", type=int, default=6)
     args = ap.parse_args()
     if args.oracle_step:  # cpu_baseline leg in a process of its own (thread count from the environment)
-        print(json.dumps(oracle_step(make_problem())[0]))
+        print(json.dumps(oracle_step(ORACLE_WORKLOADS[args.oracle_workload]())[0]))
+        return
+    if args.oracle_timing:
+        oracle_timing_run(args)
         return
     if args.profile:
         profile_run(args)

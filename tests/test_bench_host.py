@@ -134,3 +134,16 @@ def test_smooth_traffic_is_reported_only_for_the_captured_source_and_shape(monke
     assert bench.smooth_traffic("darcy64", 0) is None     # another shape
     assert bench.smooth_traffic("darcy128", 5) is None    # captured on another source
     assert bench.smooth_traffic("elastic48", 0) is None   # never captured
+
+
+def test_oracle_timing_runs_on_the_host(capsys):
+    # the oracle's own timing needs no GPU: best of the runs per phase, per thread count
+    import argparse
+    import json
+    bench.oracle_timing_run(argparse.Namespace(oracle_workloads="darcy2d64", oracle_repeats=1))
+    out = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    per = out["workloads"]["darcy2d64"]
+    assert "1" in per and str(out["cores"]) in per
+    for r in per.values():
+        assert r["setup_s"] > 0 and r["solve_s"] > 0 and r["runs"] == 1
+        assert r["basis_iters"] <= 100 and r["relres"] <= 1e-8
