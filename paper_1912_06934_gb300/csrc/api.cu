@@ -9,6 +9,7 @@
 #include <string>
 #include <thread>
 #include <future>
+#include <mutex>
 #include <type_traits>
 #include <vector>
 
@@ -645,24 +646,52 @@ msrsb_status vadd(int n, const double *a, double *b, cudaStream_t s) {
     return MSRSB_OK;
 }
 
-// Host-side pool of timing-free events (grows, kept per host thread).
+// Host-side pools of timing-free events, one per host thread while it lives
+// (grown on demand); a thread's pool goes back to a process-wide free list
+// when the thread ends, so threads created per call (the ensemble's workers)
+// reuse events instead of creating more.
+namespace {
+struct EventSet {
+    cudaEvent_t *ev = nullptr;
+    int cap = 0;
+};
+std::mutex g_evset_mu;
+std::vector<EventSet> g_evset_free;
+struct EventSetHolder {
+    EventSet set;
+    ~EventSetHolder() {
+        if (!set.ev) return;
+        std::lock_guard<std::mutex> lock(g_evset_mu);
+        g_evset_free.push_back(set);
+    }
+};
+}  // namespace
+
 static cudaEvent_t *event_pool(int need) {
-    static thread_local cudaEvent_t *pool = nullptr;
-    static thread_local int cap = 0;
-    if (need > cap) {
+    static thread_local EventSetHolder h;
+    EventSet &p = h.set;
+    if (!p.ev) {
+        std::lock_guard<std::mutex> lock(g_evset_mu);
+        if (!g_evset_free.empty()) {
+            p = g_evset_free.back();
+            g_evset_free.pop_back();
+        }
+    }
+    if (need > p.cap) {
         cudaEvent_t *np = new cudaEvent_t[need];
-        for (int q = 0; q < cap; ++q) np[q] = pool[q];
-        for (int q = cap; q < need; ++q)
+        for (int q = 0; q < p.cap; ++q) np[q] = p.ev[q];
+        for (int q = p.cap; q < need; ++q)
             if (cudaEventCreateWithFlags(&np[q], cudaEventDisableTiming) != cudaSuccess) {
                 cudaGetLastError();
+                for (int r = p.cap; r < q; ++r) cudaEventDestroy(np[r]);
                 delete[] np;
                 return nullptr;
             }
-        delete[] pool;
-        pool = np;
-        cap = need;
+        delete[] p.ev;
+        p.ev = np;
+        p.cap = need;
     }
-    return pool;
+    return p.ev;
 }
 
 // ---- GMRES (right preconditioned, flexible: Z_j = M^-1 V_j kept) ------------------------
